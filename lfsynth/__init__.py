@@ -1,0 +1,282 @@
+"""Seeded synthetic light fields shaped like the method's workloads.
+
+This module only makes inputs: it renders piecewise-planar scenes into a
+``views[v][u][y][x]`` float32 array and returns the method's parameters for the
+workload.  It holds none of the depth method's arithmetic and is shared by the
+oracle side (tests, CPU baseline) and the CUDA side (tests, bench, smoke).
+
+Geometry convention: a scene point seen at reference pixel (x, y) with
+disparity d appears in view (u, v) at (x + (u-uc) d, y + (v-vc) d).  A view
+pixel (X, Y) is rendered by solving, for every plane, for the reference point
+that lands on it, keeping the nearest plane (largest d) whose back-projected
+point lies inside its own region (the farthest plane fills holes), and sampling
+that plane's texture there bilinearly.  Then Gaussian noise, an optional
+vignetting gain and a clip to [0, 1] are applied.
+
+Seeds: ``np.random.SeedSequence(seed).spawn(3)`` gives the texture, geometry and
+noise streams; the workloads use ``seed = 1000 * workload_index + lf_index``.
+"""
+from __future__ import annotations
+
+import dataclasses
+import math
+
+import numpy as np
+
+
+@dataclasses.dataclass
+class LFParams:
+    """Sizes and method parameters of one workload (names follow the paper)."""
+    U: int
+    V: int
+    H: int
+    W: int
+    census_w: int
+    dmin: float
+    dmax: float
+    coarse_labels: int          # Lc, inclusive grid over [dmin, dmax]
+    fine_labels: int            # G, inclusive grid over [dmin, dmax]
+    fine_radius: int            # lambda in fine labels (window = 2R+1 labels)
+    init_views: int = 1         # 1: whole cross arms, 0: the 4 extreme views
+    phi: float = 3.0            # fusion threshold (coarse labels)
+    fill_passes: int = 2
+    w_l2: float = 1.0
+    w_census: float = -1.0      # -1 -> 1 / census bits
+    p1_frac: float = 0.05
+    p2_frac: float = 0.5
+    subpixel: int = 1
+    softmin_tau: float = 0.1
+    uc: int = -1
+    vc: int = -1
+    name: str = ""
+
+    def __post_init__(self):
+        if self.uc < 0:
+            self.uc = (self.U - 1) // 2
+        if self.vc < 0:
+            self.vc = (self.V - 1) // 2
+        if self.w_census < 0:
+            self.w_census = 1.0 / (self.census_w * self.census_w - 1)
+
+    @property
+    def N(self) -> int:
+        return self.H * self.W
+
+    @property
+    def fine_step(self) -> float:
+        return (self.dmax - self.dmin) / (self.fine_labels - 1)
+
+
+@dataclasses.dataclass
+class Plane:
+    a: float          # disparity at the centre (cx, cy)
+    b: float = 0.0    # slope over the image width
+    c: float = 0.0    # slope over the image height
+
+    def disp(self, x, y, W, H):
+        return self.a + self.b * (x - 0.5 * (W - 1)) / W + self.c * (y - 0.5 * (H - 1)) / H
+
+
+def _blur121(t: np.ndarray) -> np.ndarray:
+    p = np.pad(t, 1, mode="edge")
+    t = 0.25 * p[:-2, 1:-1] + 0.5 * p[1:-1, 1:-1] + 0.25 * p[2:, 1:-1]
+    p = np.pad(t, ((0, 0), (1, 1)), mode="edge")
+    return 0.25 * p[:, :-2] + 0.5 * p[:, 1:-1] + 0.25 * p[:, 2:]
+
+
+def _sample(tex: np.ndarray, margin: int, x: np.ndarray, y: np.ndarray) -> np.ndarray:
+    """Bilinear texture lookup at reference coordinates (clamped to the texture)."""
+    th, tw = tex.shape
+    gx = np.clip(x + margin, 0.0, tw - 1.000001)
+    gy = np.clip(y + margin, 0.0, th - 1.000001)
+    x0 = np.floor(gx).astype(np.int64)
+    y0 = np.floor(gy).astype(np.int64)
+    fx = gx - x0
+    fy = gy - y0
+    t00 = tex[y0, x0]
+    t10 = tex[y0, x0 + 1]
+    t01 = tex[y0 + 1, x0]
+    t11 = tex[y0 + 1, x0 + 1]
+    return (1 - fy) * ((1 - fx) * t00 + fx * t10) + fy * ((1 - fx) * t01 + fx * t11)
+
+
+def render(p: LFParams, planes, region, textures, margin, noise_rng, sigma, vignette=False,
+           views_mask=None):
+    """Render views[v][u][y][x] (float32) and the reference-view disparity (float64).
+
+    ``region(i, x, y)`` -> bool array: is reference point (x, y) on plane i.
+    ``textures[i]``: texture of plane i on the reference grid plus ``margin``."""
+    U, V, H, W = p.U, p.V, p.H, p.W
+    Y, X = np.mgrid[0:H, 0:W].astype(np.float64)
+    views = np.zeros((V, U, H, W), np.float32)
+    gt = None
+    for v in range(V):
+        for u in range(U):
+            if views_mask is not None and not views_mask(u, v):
+                continue
+            a, b = u - p.uc, v - p.vc
+            best_d = np.full((H, W), -np.inf)
+            best_val = np.zeros((H, W))
+            far_d = np.full((H, W), np.inf)
+            far_val = np.zeros((H, W))
+            for i, pl in enumerate(planes):
+                # X = x + a*d(x,y), Y = y + b*d(x,y), with d affine in (x, y): 2x2 solve
+                kx, ky = pl.b / W, pl.c / H
+                k0 = pl.a - kx * 0.5 * (W - 1) - ky * 0.5 * (H - 1)
+                m00, m01 = 1.0 + a * kx, a * ky
+                m10, m11 = b * kx, 1.0 + b * ky
+                r0, r1 = X - a * k0, Y - b * k0
+                det = m00 * m11 - m01 * m10
+                x = (m11 * r0 - m01 * r1) / det
+                y = (m00 * r1 - m10 * r0) / det
+                d = pl.disp(x, y, W, H)
+                val = _sample(textures[i], margin, x, y)
+                ok = region(i, x, y)
+                take = ok & (d > best_d)
+                best_d = np.where(take, d, best_d)
+                best_val = np.where(take, val, best_val)
+                fall = d < far_d
+                far_d = np.where(fall, d, far_d)
+                far_val = np.where(fall, val, far_val)
+            hole = ~np.isfinite(best_d)
+            img = np.where(hole, far_val, best_val)
+            if a == 0 and b == 0:
+                gt = np.where(hole, far_d, best_d)
+            if sigma > 0:
+                img = img + noise_rng.normal(0.0, sigma, size=img.shape)
+            if vignette:
+                rho2 = (a * a + b * b) / float(max(p.uc, 1) ** 2 + max(p.vc, 1) ** 2)
+                r2 = ((X - 0.5 * (W - 1)) ** 2 + (Y - 0.5 * (H - 1)) ** 2) / (
+                    (0.5 * (W - 1)) ** 2 + (0.5 * (H - 1)) ** 2)
+                img = img * (1.0 - 0.3 * rho2 * (0.5 + 0.5 * r2))
+            views[v, u] = np.clip(img, 0.0, 1.0).astype(np.float32)
+    return views, gt
+
+
+def _streams(seed: int):
+    ss = np.random.SeedSequence(seed).spawn(3)
+    return [np.random.default_rng(s) for s in ss]
+
+
+# ------------------------------------------------------------------ workloads
+def tiny_params(**kw) -> LFParams:
+    """5x5 x 64x64, census 5x5, coarse 32 labels on [-2,2], fine +-0.25 by 0.05."""
+    d = dict(U=5, V=5, H=64, W=64, census_w=5, dmin=-2.0, dmax=2.0, coarse_labels=32,
+             fine_labels=81, fine_radius=5, name="tiny 5x5x64x64")
+    d.update(kw)
+    return LFParams(**d)
+
+
+def bench_params(**kw) -> LFParams:
+    """9x9 x 512x512, census 7x7, coarse 100 labels on [-4,4] over 17 cross views,
+    fine +-0.3 px by 0.02 px (31 labels, 401 on the whole range)."""
+    d = dict(U=9, V=9, H=512, W=512, census_w=7, dmin=-4.0, dmax=4.0, coarse_labels=100,
+             fine_labels=401, fine_radius=15, name="bench 9x9x512x512")
+    d.update(kw)
+    return LFParams(**d)
+
+
+def plenoptic_params(**kw) -> LFParams:
+    """15x15 x 434x625, census 7x7, coarse 64 labels on [-1.5,1.5] over 29 cross views,
+    fine +-0.15 px by 0.01 px (31 labels, 301 on the whole range)."""
+    d = dict(U=15, V=15, H=434, W=625, census_w=7, dmin=-1.5, dmax=1.5, coarse_labels=64,
+             fine_labels=301, fine_radius=15, name="plenoptic 15x15x434x625")
+    d.update(kw)
+    return LFParams(**d)
+
+
+def tiny(lf_index: int = 0, params: LFParams | None = None):
+    """Uniform-noise texture on 3 fronto-parallel planes (-1.5 background, 0.25 centre
+    rectangle, 1.75 inner rectangle), noise sigma 0.01."""
+    p = params or tiny_params()
+    tex_rng, geo_rng, noise_rng = _streams(1000 * 0 + lf_index)
+    margin = int(math.ceil(max(abs(p.dmin), abs(p.dmax)) * max(p.U, p.V))) + 2
+    th, tw = p.H + 2 * margin, p.W + 2 * margin
+    textures = [tex_rng.uniform(0.05, 0.95, size=(th, tw)) for _ in range(3)]
+    planes = [Plane(-1.5), Plane(0.25), Plane(1.75)]
+    H, W = p.H, p.W
+    rects = [None, (W * 0.25, H * 0.25, W * 0.75, H * 0.75), (W * 0.40, H * 0.375, W * 0.60, H * 0.625)]
+
+    def region(i, x, y):
+        if rects[i] is None:
+            return np.ones(x.shape, bool)
+        x0, y0, x1, y1 = rects[i]
+        return (x >= x0) & (x < x1) & (y >= y0) & (y < y1)
+
+    views, gt = render(p, planes, region, textures, margin, noise_rng, 0.01)
+    return views, gt, p
+
+
+def voronoi_scene(p: LFParams, seed: int, n_planes: int, a_range, slope, clamp, sigma,
+                  vignette=False):
+    tex_rng, geo_rng, noise_rng = _streams(seed)
+    margin = int(math.ceil(max(abs(p.dmin), abs(p.dmax)) * max(p.U, p.V))) + 2
+    th, tw = p.H + 2 * margin, p.W + 2 * margin
+    textures = [_blur121(tex_rng.uniform(0.0, 1.0, size=(th, tw))) for _ in range(n_planes)]
+    sites = np.stack([geo_rng.uniform(0, p.W, n_planes), geo_rng.uniform(0, p.H, n_planes)], 1)
+    planes = []
+    for _ in range(n_planes):
+        a = geo_rng.uniform(*a_range)
+        b = geo_rng.uniform(-slope, slope)
+        c = geo_rng.uniform(-slope, slope)
+        # keep the plane inside [-clamp, clamp] over the image
+        ext = 0.5 * (abs(b) + abs(c))
+        a = float(np.clip(a, -clamp + ext, clamp - ext))
+        planes.append(Plane(a, b, c))
+
+    def region(i, x, y):
+        d2 = [(x - sites[j, 0]) ** 2 + (y - sites[j, 1]) ** 2 for j in range(n_planes)]
+        best = np.argmin(np.stack(d2), axis=0)
+        return best == i
+
+    views, gt = render(p, planes, region, textures, margin, noise_rng, sigma, vignette)
+    return views, gt
+
+
+def bench(lf_index: int = 0, params: LFParams | None = None):
+    """8 slanted textured planes on the Voronoi cells of 8 seeded sites, disparity in
+    [-4, 4] px, texture = uniform noise blurred by [1,2,1]/4, noise sigma 0.01."""
+    p = params or bench_params()
+    views, gt = voronoi_scene(p, 1000 * 1 + lf_index, 8, (-3.4, 3.4), 0.5, 4.0, 0.01)
+    return views, gt, p
+
+
+def plenoptic(lf_index: int = 0, params: LFParams | None = None):
+    """8 planes, disparity in [-1.5, 1.5] px, noise sigma 0.02, vignetting on outer views."""
+    p = params or plenoptic_params()
+    views, gt = voronoi_scene(p, 1000 * 2 + lf_index, 8, (-1.2, 1.2), 0.3, 1.5, 0.02, vignette=True)
+    return views, gt, p
+
+
+def integer_planes(U=5, V=5, H=48, W=48, disps=(-1.0, 0.0, 1.0), seed=7, **kw):
+    """Noise-free fronto-parallel planes with integer disparity: every view is an exact
+    integer shift of a seeded uniform texture (nested rectangles, one per plane)."""
+    d = dict(U=U, V=V, H=H, W=W, census_w=5, dmin=-2.0, dmax=2.0, coarse_labels=33,
+             fine_labels=81, fine_radius=5, name=f"integer planes {U}x{V}x{H}x{W}")
+    d.update(kw)
+    p = LFParams(**d)
+    tex_rng, _, noise_rng = _streams(seed)
+    margin = int(math.ceil(max(abs(p.dmin), abs(p.dmax)) * max(p.U, p.V))) + 2
+    th, tw = p.H + 2 * margin, p.W + 2 * margin
+    textures = [tex_rng.uniform(0.05, 0.95, size=(th, tw)) for _ in disps]
+    order = np.argsort(disps)
+    planes = [Plane(float(disps[i])) for i in order]
+    n = len(planes)
+
+    def region(i, x, y):
+        if i == 0:
+            return np.ones(x.shape, bool)
+        f = 0.5 * i / n
+        return (x >= W * f) & (x < W * (1 - f)) & (y >= H * f) & (y < H * (1 - f))
+
+    views, gt = render(p, planes, region, textures, margin, noise_rng, 0.0)
+    return views, gt, p
+
+
+def random_views(U, V, H, W, seed=0, lo=0.0, hi=1.0):
+    """Plain i.i.d. uniform views (for stage-level tests that need no scene)."""
+    rng = np.random.default_rng(seed)
+    return rng.uniform(lo, hi, size=(V, U, H, W)).astype(np.float32)
+
+
+WORKLOADS = {"tiny": tiny, "bench": bench, "plenoptic": plenoptic}

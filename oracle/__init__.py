@@ -1,0 +1,304 @@
+"""FP64 CPU oracle of the light-field SGM depth method (Anisimov, Wasenmueller,
+Stricker, ICCP 2019) -- TEST INFRASTRUCTURE.
+
+Only ``tests/``, ``__graft_entry__.smoke()`` and the CPU-baseline leg of
+``bench.py`` may import this package.  It shares no code with the CUDA library
+(``paper_1907_13449_gb300``): the arithmetic lives in ``lfsgm_oracle.c`` (plain
+loops, double precision, built with ``-ffp-contract=off``), and this module only
+marshals numpy arrays and composes the stages in the paper's order
+(Sec. III-D initial map -> Sec. III-E final map -> Sec. III-F post-processing).
+
+Every function here either calls one C stage or chains stages exactly as the
+paper orders them; see ``lfsgm_oracle.c`` for the per-equation citations.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "lfsgm_oracle.c")
+_LIB = os.path.join(_HERE, "_liboracle.so")
+_lock = threading.Lock()
+_lib = None
+
+DIRECTIONS = ((1, 0), (-1, 0), (0, 1), (0, -1), (1, 1), (-1, -1), (1, -1), (-1, 1))
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle with gcc (no FMA contraction, no fast-math)."""
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+        tmp = _LIB + f".{os.getpid()}.tmp"
+        subprocess.check_call(["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fno-fast-math",
+                               "-fPIC", "-shared", "-o", tmp, _SRC, "-lm"])
+        os.replace(tmp, _LIB)
+    return _LIB
+
+
+class Cfg(C.Structure):
+    _fields_ = [("U", C.c_int32), ("V", C.c_int32), ("H", C.c_int32), ("W", C.c_int32),
+                ("uc", C.c_int32), ("vc", C.c_int32), ("census_w", C.c_int32),
+                ("dmin", C.c_double), ("dmax", C.c_double), ("Lc", C.c_int32),
+                ("init_views", C.c_int32), ("phi", C.c_double), ("fill_passes", C.c_int32),
+                ("G", C.c_int32), ("R", C.c_int32), ("w_l2", C.c_double), ("w_census", C.c_double)]
+
+
+def make_cfg(p) -> Cfg:
+    """Oracle config from any object with the method's parameter names
+    (``lfsynth.LFParams`` or the library's config dataclass)."""
+    return Cfg(U=p.U, V=p.V, H=p.H, W=p.W, uc=p.uc, vc=p.vc, census_w=p.census_w,
+               dmin=p.dmin, dmax=p.dmax, Lc=p.coarse_labels, init_views=p.init_views,
+               phi=p.phi, fill_passes=p.fill_passes, G=p.fine_labels, R=p.fine_radius,
+               w_l2=p.w_l2, w_census=p.w_census)
+
+
+def _ptr(a, t):
+    return a.ctypes.data_as(C.POINTER(t))
+
+
+def lib():
+    global _lib
+    with _lock:
+        if _lib is None:
+            _lib = C.CDLL(build())
+            L = _lib
+            P = C.POINTER
+            L.or_label_disp.restype = C.c_double
+            L.or_label_disp.argtypes = [C.c_double, C.c_double, C.c_int, C.c_int]
+            L.or_shift.argtypes = [C.c_int, C.c_double, P(C.c_int), P(C.c_double), P(C.c_int)]
+            L.or_census.argtypes = [P(C.c_float), C.c_int, C.c_int, C.c_int, P(C.c_uint64)]
+            L.or_hamming.restype = C.c_int
+            L.or_hamming.argtypes = [C.c_uint64, C.c_uint64]
+            L.or_census_all.argtypes = [P(Cfg), P(C.c_float), P(C.c_uint64)]
+            L.or_arm_views.restype = C.c_int
+            L.or_arm_views.argtypes = [P(Cfg), C.c_int, P(C.c_int)]
+            L.or_coarse_cost.restype = C.c_int
+            L.or_coarse_cost.argtypes = [P(Cfg), P(C.c_uint64), C.c_int, P(C.c_int64)]
+            L.or_int_penalties.argtypes = [C.c_int64, C.c_int64, C.c_double, C.c_double,
+                                           P(C.c_int64), P(C.c_int64)]
+            L.or_sgm_int_path.argtypes = [C.c_int, C.c_int, C.c_int, P(C.c_int64), C.c_int64,
+                                          C.c_int64, C.c_int, P(C.c_int64)]
+            L.or_sgm_int.argtypes = [C.c_int, C.c_int, C.c_int, P(C.c_int64), C.c_int64, C.c_int64,
+                                     P(C.c_int64)]
+            L.or_wta_int.argtypes = [C.c_size_t, C.c_int, P(C.c_int64), P(C.c_int32)]
+            L.or_fuse.argtypes = [C.c_size_t, C.c_int, P(C.c_int32), C.c_double, P(C.c_double)]
+            L.or_hole_fill.argtypes = [C.c_int, C.c_int, C.c_int, P(C.c_double)]
+            L.or_windows.argtypes = [P(Cfg), C.c_size_t, P(C.c_double), P(C.c_int32), P(C.c_int32)]
+            L.or_cost_volume.argtypes = [P(Cfg), P(C.c_float), P(C.c_uint64), P(C.c_int32),
+                                         P(C.c_int32), P(C.c_int64), P(C.c_double)]
+            L.or_sgm_bounded_path.argtypes = [C.c_int, C.c_int, P(C.c_int32), P(C.c_int32),
+                                              P(C.c_int64), P(C.c_double), C.c_double, C.c_double,
+                                              C.c_int, C.c_int, P(C.c_double)]
+            L.or_sgm_bounded.argtypes = [C.c_int, C.c_int, P(C.c_int32), P(C.c_int32), P(C.c_int64),
+                                         P(C.c_double), C.c_double, C.c_double, P(C.c_double)]
+            L.or_wta_subpixel.argtypes = [P(Cfg), C.c_size_t, P(C.c_int32), P(C.c_int32),
+                                          P(C.c_int64), P(C.c_double), C.c_int, C.c_double,
+                                          P(C.c_int32), P(C.c_double), P(C.c_double)]
+    return _lib
+
+
+# ----------------------------------------------------------------- small helpers
+def label_disp(dmin: float, dmax: float, L: int, k: int) -> float:
+    return lib().or_label_disp(dmin, dmax, L, k)
+
+
+def shift(a: int, d: float):
+    """(ox, fx, nx) of the shift a*d under the oracle's shift rule."""
+    o, n, f = C.c_int(), C.c_int(), C.c_double()
+    lib().or_shift(a, d, C.byref(o), C.byref(f), C.byref(n))
+    return o.value, f.value, n.value
+
+
+def census(img: np.ndarray, w: int) -> np.ndarray:
+    img = np.ascontiguousarray(img, dtype=np.float32)
+    H, W = img.shape
+    out = np.zeros((H, W), np.uint64)
+    lib().or_census(_ptr(img, C.c_float), H, W, w, _ptr(out, C.c_uint64))
+    return out
+
+
+def hamming(a: int, b: int) -> int:
+    return lib().or_hamming(int(a), int(b))
+
+
+def census_all(cfg: Cfg, views: np.ndarray) -> np.ndarray:
+    views = np.ascontiguousarray(views, dtype=np.float32)
+    out = np.zeros(views.shape, np.uint64)
+    lib().or_census_all(C.byref(cfg), _ptr(views, C.c_float), _ptr(out, C.c_uint64))
+    return out
+
+
+def arm_views(cfg: Cfg, arm: int):
+    buf = (C.c_int * 1024)()
+    n = lib().or_arm_views(C.byref(cfg), arm, buf)
+    return [(buf[2 * i], buf[2 * i + 1]) for i in range(n)]
+
+
+def coarse_cost(cfg: Cfg, cen: np.ndarray, arm: int):
+    """int64 [H*W, Lc] arm cost (Eq. 7) or None for an empty arm."""
+    out = np.zeros((cfg.H * cfg.W, cfg.Lc), np.int64)
+    n = lib().or_coarse_cost(C.byref(cfg), _ptr(cen, C.c_uint64), arm, _ptr(out, C.c_int64))
+    return out if n > 0 else None
+
+
+def int_penalties(total: int, count: int, p1f: float, p2f: float):
+    a, b = C.c_int64(), C.c_int64()
+    lib().or_int_penalties(int(total), int(count), p1f, p2f, C.byref(a), C.byref(b))
+    return a.value, b.value
+
+
+def sgm_int_path(H, W, Cv: np.ndarray, P1: int, P2: int, direction: int) -> np.ndarray:
+    Cv = np.ascontiguousarray(Cv, dtype=np.int64)
+    out = np.zeros_like(Cv)
+    lib().or_sgm_int_path(H, W, Cv.shape[-1], _ptr(Cv, C.c_int64), P1, P2, direction,
+                          _ptr(out, C.c_int64))
+    return out
+
+
+def sgm_int(H, W, Cv: np.ndarray, P1: int, P2: int) -> np.ndarray:
+    Cv = np.ascontiguousarray(Cv, dtype=np.int64)
+    out = np.zeros_like(Cv)
+    lib().or_sgm_int(H, W, Cv.shape[-1], _ptr(Cv, C.c_int64), P1, P2, _ptr(out, C.c_int64))
+    return out
+
+
+def wta_int(Cs: np.ndarray) -> np.ndarray:
+    Cs = np.ascontiguousarray(Cs, dtype=np.int64)
+    out = np.zeros(Cs.shape[0], np.int32)
+    lib().or_wta_int(Cs.shape[0], Cs.shape[1], _ptr(Cs, C.c_int64), _ptr(out, C.c_int32))
+    return out
+
+
+def fuse(maps: np.ndarray, phi: float) -> np.ndarray:
+    maps = np.ascontiguousarray(maps, dtype=np.int32)
+    n, N = maps.shape
+    out = np.zeros(N, np.float64)
+    lib().or_fuse(N, n, _ptr(maps, C.c_int32), phi, _ptr(out, C.c_double))
+    return out
+
+
+def hole_fill(dinit: np.ndarray, H: int, W: int, passes: int) -> np.ndarray:
+    d = np.array(dinit, dtype=np.float64, copy=True).reshape(-1)
+    lib().or_hole_fill(H, W, passes, _ptr(d, C.c_double))
+    return d
+
+
+def windows(cfg: Cfg, dinit: np.ndarray):
+    d = np.ascontiguousarray(dinit, dtype=np.float64).reshape(-1)
+    lo = np.zeros(d.size, np.int32)
+    cnt = np.zeros(d.size, np.int32)
+    lib().or_windows(C.byref(cfg), d.size, _ptr(d, C.c_double), _ptr(lo, C.c_int32),
+                     _ptr(cnt, C.c_int32))
+    return lo, cnt
+
+
+def offsets(cnt: np.ndarray) -> np.ndarray:
+    off = np.zeros(cnt.size + 1, np.int64)
+    np.cumsum(cnt.reshape(-1), out=off[1:])
+    return off
+
+
+def cost_volume(cfg: Cfg, views: np.ndarray, lo: np.ndarray, cnt: np.ndarray, cen=None):
+    """(off, cost) with cost[off[p] + j] = C(p, lo[p] + j) (Eq. 12 + Eq. 15)."""
+    views = np.ascontiguousarray(views, dtype=np.float32)
+    if cen is None:
+        cen = census_all(cfg, views)
+    lo = np.ascontiguousarray(lo, dtype=np.int32).reshape(-1)
+    cnt = np.ascontiguousarray(cnt, dtype=np.int32).reshape(-1)
+    off = offsets(cnt)
+    cost = np.zeros(int(off[-1]), np.float64)
+    lib().or_cost_volume(C.byref(cfg), _ptr(views, C.c_float), _ptr(cen, C.c_uint64),
+                         _ptr(lo, C.c_int32), _ptr(cnt, C.c_int32), _ptr(off, C.c_int64),
+                         _ptr(cost, C.c_double))
+    return off, cost
+
+
+def sgm_bounded_path(H, W, lo, cnt, off, cost, P1, P2, direction, normalised=True):
+    lo = np.ascontiguousarray(lo, dtype=np.int32).reshape(-1)
+    cnt = np.ascontiguousarray(cnt, dtype=np.int32).reshape(-1)
+    off = np.ascontiguousarray(off, dtype=np.int64)
+    cost = np.ascontiguousarray(cost, dtype=np.float64)
+    out = np.zeros_like(cost)
+    lib().or_sgm_bounded_path(H, W, _ptr(lo, C.c_int32), _ptr(cnt, C.c_int32), _ptr(off, C.c_int64),
+                              _ptr(cost, C.c_double), float(P1), float(P2), direction,
+                              1 if normalised else 0, _ptr(out, C.c_double))
+    return out
+
+
+def sgm_bounded(H, W, lo, cnt, off, cost, P1, P2):
+    lo = np.ascontiguousarray(lo, dtype=np.int32).reshape(-1)
+    cnt = np.ascontiguousarray(cnt, dtype=np.int32).reshape(-1)
+    off = np.ascontiguousarray(off, dtype=np.int64)
+    cost = np.ascontiguousarray(cost, dtype=np.float64)
+    out = np.zeros_like(cost)
+    lib().or_sgm_bounded(H, W, _ptr(lo, C.c_int32), _ptr(cnt, C.c_int32), _ptr(off, C.c_int64),
+                         _ptr(cost, C.c_double), float(P1), float(P2), _ptr(out, C.c_double))
+    return out
+
+
+def wta_subpixel(cfg: Cfg, lo, cnt, off, Cs, mode=1, tau=0.1):
+    lo = np.ascontiguousarray(lo, dtype=np.int32).reshape(-1)
+    cnt = np.ascontiguousarray(cnt, dtype=np.int32).reshape(-1)
+    off = np.ascontiguousarray(off, dtype=np.int64)
+    Cs = np.ascontiguousarray(Cs, dtype=np.float64)
+    N = lo.size
+    label = np.zeros(N, np.int32)
+    disp = np.zeros(N, np.float64)
+    gap = np.zeros(N, np.float64)
+    lib().or_wta_subpixel(C.byref(cfg), N, _ptr(lo, C.c_int32), _ptr(cnt, C.c_int32),
+                          _ptr(off, C.c_int64), _ptr(Cs, C.c_double), mode, tau,
+                          _ptr(label, C.c_int32), _ptr(disp, C.c_double), _ptr(gap, C.c_double))
+    return label, disp, gap
+
+
+# --------------------------------------------------------- composed stages
+def initial_disparity(cfg: Cfg, views: np.ndarray, penalties=None, p1f=0.05, p2f=0.5, cen=None):
+    """Sec. III-D in order: census of the cross views, per-arm cost (Eq. 7), SGM per
+    arm (Eq. 8-9), WTA (Eq. 10), fusion with threshold phi, median hole filling,
+    borders (Eq. 11).  ``penalties``: None -> per-arm (P1, P2) derived from the arm's
+    mean cost with fractions (p1f, p2f); or a list of one (P1, P2) per arm."""
+    views = np.ascontiguousarray(views, dtype=np.float32)
+    if cen is None:
+        cen = census_all(cfg, views)
+    H, W, N = cfg.H, cfg.W, cfg.H * cfg.W
+    maps, pens, arms = [], [], []
+    for arm in range(4):
+        ca = coarse_cost(cfg, cen, arm)
+        if ca is None:
+            continue
+        if penalties is None:
+            P1, P2 = int_penalties(int(ca.sum()), ca.size, p1f, p2f)
+        else:
+            P1, P2 = penalties[arm]
+        Cs = sgm_int(H, W, ca, P1, P2)
+        maps.append(wta_int(Cs))
+        pens.append((P1, P2))
+        arms.append(arm)
+    maps = np.stack(maps)
+    fused = fuse(maps, cfg.phi)
+    filled = hole_fill(fused, H, W, cfg.fill_passes)
+    lo, cnt = windows(cfg, filled)
+    return {"maps": maps, "arms": arms, "penalties": pens, "fused": fused,
+            "dinit": filled, "lo": lo, "cnt": cnt, "census": cen}
+
+
+def depth(cfg: Cfg, views: np.ndarray, fine_penalties=None, p1f=0.05, p2f=0.5, mode=1, tau=0.1,
+          coarse_penalties=None):
+    """The whole method: initial map, bounded cost (Eq. 12 + 15), bounded SGM, WTA and
+    sub-pixel refinement.  ``fine_penalties``: None -> (p1f, p2f) x mean active cost."""
+    init = initial_disparity(cfg, views, coarse_penalties, p1f, p2f)
+    off, cost = cost_volume(cfg, views, init["lo"], init["cnt"], init["census"])
+    if fine_penalties is None:
+        mean = float(cost.mean())
+        P1, P2 = p1f * mean, p2f * mean
+    else:
+        P1, P2 = fine_penalties
+    Cs = sgm_bounded(cfg.H, cfg.W, init["lo"], init["cnt"], off, cost, P1, P2)
+    label, disp, gap = wta_subpixel(cfg, init["lo"], init["cnt"], off, Cs, mode, tau)
+    out = dict(init)
+    out.update(off=off, cost=cost, P1=P1, P2=P2, Cs=Cs, label=label, disp=disp, gap=gap)
+    return out
