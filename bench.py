@@ -1,0 +1,351 @@
+"""Benchmark of the light-field SGM depth path on GB300.
+
+One step = the whole method on one 9x9 x 512x512 light field already resident in HBM:
+initial disparity (census, per-arm cost, integer SGM, WTA, fusion, hole filling,
+windows), bounded cost volume, bounded 8-path SGM, WTA + sub-pixel.  The headline
+metric is the time of the cost volume + SGM stages per light field (the paper's final
+map stage, Sec. III-E); the full-step time is reported beside it.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                  [--workload bench|plenoptic|tiny]
+
+N > 1 is launched with torchrun: every rank runs its own light field (independent
+replicas, no collective on the data path), the step time is the max over ranks.
+--impl reference times the FP64 CPU oracle on the host cores on a row band of the
+same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "ms per 9x9x512^2 light field (cost+SGM)"
+PEAKS_FALLBACK = {"hbm_gbs": 6800.0, "sm_max_mhz": 2070.0}
+N_SM = 152
+FP32_LANES_PER_SM = 128
+
+
+def load_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        d["_source"] = "measured"
+        return d
+    d = dict(PEAKS_FALLBACK)
+    d["_source"] = "fallback"
+    return d
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def workload(name, lf_index):
+    import lfsynth
+    if name == "bench":
+        return lfsynth.bench(lf_index)
+    if name == "plenoptic":
+        return lfsynth.plenoptic(lf_index)
+    return lfsynth.tiny(lf_index)
+
+
+def workload_label(p):
+    return (f"{p.name}: {p.U}x{p.V} views of {p.H}x{p.W} f32, census {p.census_w}x{p.census_w}, "
+            f"coarse {p.coarse_labels} labels on [{p.dmin:g},{p.dmax:g}], fine window 2x{p.fine_radius}+1 "
+            f"of {p.fine_labels} labels, 8-path SGM, parabolic sub-pixel")
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms while running."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+            self.f.close()
+
+    def summary(self):
+        if self.proc is None or not self.path or not os.path.exists(self.path):
+            return None
+        rows = [l.strip().split(", ") for l in open(self.path) if l.strip()]
+        os.unlink(self.path)
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            try:
+                sm.append(float(r[1]))
+                mx.append(float(r[2]))
+                for n, v in zip(names, r[5:9]):
+                    if v.strip().lower() == "active":
+                        reasons.add(n)
+            except (ValueError, IndexError):
+                continue
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ------------------------------------------------------------------ roofline models
+def hbm_bytes_cost_sgm(p, nnz_active):
+    """Algorithmic bytes of the cost volume + SGM stages: each reads its inputs once and
+    writes its outputs once (views; window map lo/cnt/off 16 B per pixel per stage;
+    cost written and read once; aggregated cost written once)."""
+    N = p.H * p.W
+    views = p.U * p.V * N * 4
+    cost = 4 * nnz_active
+    return {"cost_volume": views + 16 * N + cost, "sgm_aggregate": 16 * N + cost + cost}
+
+
+def alu_ops_cost(p, nnz_active):
+    """Algorithmic FP32 lane operations of the cost volume: per (active cell, non-reference
+    view) a bilinear sample (3 lerps, 2 ops each), the difference and its absolute-value
+    accumulation (2 ops)."""
+    return nnz_active * (p.U * p.V - 1) * 8
+
+
+def run_ours(args, ws, rank, local):
+    import numpy as np
+    import torch
+
+    import paper_1907_13449_gb300 as lf
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    lib = lf.load()
+    views_np, gt, p = workload(args.workload, rank)
+    views = torch.from_numpy(views_np).to(dev)
+    stream = torch.cuda.current_stream(dev)
+    L = lf.LightFieldDepth(p, stream=stream, device=dev)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)   # > L2 (129 MB)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+
+    def step(events=None):
+        L.initial(views)
+        if events:
+            events[0].record(stream)
+        L.cost_volume(views)
+        L.aggregate(-1.0, -1.0)
+        if events:
+            events[1].record(stream)
+        L.wta()
+
+    for _ in range(args.warmup):
+        flush.zero_()
+        step()
+    torch.cuda.synchronize()
+    nnz = int(L.off[-1].item())
+    cnt = L.cnt.cpu().numpy()
+    active = int(cnt.sum())
+
+    lf.lfsgm_set_profiling(L.h, True)
+    lf.lfsgm_kernel_times(L.h)          # drop anything recorded so far
+    launches0 = lf.lfsgm_launch_count(L.h)
+    step_ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+               for _ in range(args.steps)]
+    stage_ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+                for _ in range(args.steps)]
+    if ws > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clk:
+        for i in range(args.steps):
+            flush.zero_()
+            step_ev[i][0].record(stream)
+            step(stage_ev[i])
+            step_ev[i][1].record(stream)
+        torch.cuda.synchronize()
+    if ws > 1:
+        dist.barrier()
+    launches = lf.lfsgm_launch_count(L.h) - launches0
+    ktimes = lf.lfsgm_kernel_times(L.h, cap=100000)
+    lf.lfsgm_set_profiling(L.h, False)
+    step_ms = sum(a.elapsed_time(b) for a, b in step_ev)
+    stage_ms = sum(a.elapsed_time(b) for a, b in stage_ev)
+    t = torch.tensor([step_ms, stage_ms], dtype=torch.float64, device=dev)
+    if ws > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    step_ms, stage_ms = float(t[0]), float(t[1])
+
+    # per-kernel aggregates over the timed region
+    per = {}
+    for name, ms in ktimes:
+        a = per.setdefault(name, [0, 0.0])
+        a[0] += 1
+        a[1] += ms
+    kernels = {k: {"launches": v[0], "ms_total": round(v[1], 4), "ms_avg": round(v[1] / v[0], 5)}
+               for k, v in sorted(per.items(), key=lambda kv: -kv[1][1])}
+
+    # end to end through the host-buffer entry point (pinned host memory)
+    vh = torch.from_numpy(views_np).pin_memory()
+    dh = torch.empty(p.H * p.W, dtype=torch.float32).pin_memory()
+    lh = torch.empty(p.H * p.W, dtype=torch.int32).pin_memory()
+    for _ in range(max(1, args.warmup)):
+        lf.lfsgm_depth_host(L.h, vh, dh, lh)
+    e2e = []
+    for _ in range(args.steps):
+        flush.zero_()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        lf.lfsgm_depth_host(L.h, vh, dh, lh)
+        e2e.append((time.perf_counter() - t0) * 1e3)
+    e2e_ms = statistics.mean(e2e)
+
+    if rank != 0:
+        if ws > 1:
+            dist.destroy_process_group()
+        return None
+
+    peaks = load_peaks()
+    clocks = clk.summary()
+    K = args.steps
+    value = stage_ms / (K * ws)                 # whole-job ms per light field (cost+SGM)
+    # dominant kernel of the cost+SGM stages and its roofline
+    hot = ["fine_cost", "fine_sgm", "census_all", "cost_partial_sums", "zero_agg"]
+    dom = max((k for k in kernels if k in hot), key=lambda k: kernels[k]["ms_total"])
+    mhz = (clocks or {}).get("sm_mhz") or peaks.get("sm_max_mhz", 2070.0)
+    by = hbm_bytes_cost_sgm(p, active)
+    if dom == "fine_cost":
+        ops = alu_ops_cost(p, active)
+        peak_ops = N_SM * FP32_LANES_PER_SM * mhz * 1e6
+        ach = ops / (kernels[dom]["ms_avg"] * 1e-3)
+        roof = {"kernel": dom, "bound": "alu", "achieved": round(ach / 1e12, 3),
+                "peak": round(peak_ops / 1e12, 3), "unit": "T FP32 lane-ops/s",
+                "frac": round(ach / peak_ops, 4), "traffic": None,
+                "peak_basis": f"{N_SM} SMs x {FP32_LANES_PER_SM} FP32 lanes x {mhz:.0f} MHz (median SM clock under load)"}
+    else:
+        b = by["sgm_aggregate"] if dom == "fine_sgm" else by["cost_volume"]
+        ach = b / (kernels[dom]["ms_avg"] * 1e-3) / 1e9
+        roof = {"kernel": dom, "bound": "hbm", "achieved": round(ach, 1), "peak": peaks["hbm_gbs"],
+                "unit": "GB/s", "frac": round(ach / peaks["hbm_gbs"], 4), "traffic": None}
+    hbm_total = by["cost_volume"] + by["sgm_aggregate"]
+    hbm_model = {"bytes_per_lf": hbm_total, "roofline_ms": round(hbm_total / (peaks["hbm_gbs"] * 1e9) * 1e3, 4),
+                 "frac": round(hbm_total / (peaks["hbm_gbs"] * 1e9) * 1e3 / value, 4),
+                 "peak_gbs": peaks["hbm_gbs"], "peak_source": peaks["_source"]}
+    out = {
+        "metric": METRIC, "value": round(value, 4), "unit": "ms", "n_gpus": ws, "steps": K,
+        "warmup": args.warmup, "ms_per_step": round(step_ms / K, 4), "higher_is_better": False,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": workload_label(p), "l2": "flushed (256 MB write) before every step",
+                   "penalties": "P1 = 0.05 mean cost, P2 = 0.5 mean cost (coarse: per arm, integer)",
+                   "parallelism": f"replicas x{ws}"},
+        "gcell_per_s": round(active / (value * 1e-3) / 1e9, 2),
+        "active_cells": active, "nnz_padded": nnz,
+        "full_forward_ms_per_lf": round(step_ms / (K * ws), 4),
+        "kernels": kernels,
+        "roofline": roof,
+        "hbm_model": hbm_model,
+        "clocks": clocks,
+        "gpu_launches": int(launches),
+        "e2e": {"value": round(e2e_ms, 4), "unit": "ms per light field: host->device views, whole method, "
+                "device->host disparity + label", "h2d_bytes_per_step": int(views_np.nbytes),
+                "d2h_bytes_per_step": int(dh.numel() * 4 + lh.numel() * 4)},
+    }
+    if not args.no_cpu_baseline:
+        out["cpu_baseline"] = cpu_baseline(args, views_np, p, rows=args.cpu_rows)
+    if ws > 1:
+        dist.destroy_process_group()
+    return out
+
+
+def cpu_baseline(args, views_np, p, rows):
+    """The oracle (FP64, OpenMP over rows) on a band of `rows` image rows of the same light
+    field: windows from the oracle's own initial pass on the band (untimed), then the timed
+    cost volume + SGM; scaled to a whole light field by H / rows."""
+    import numpy as np
+
+    import oracle
+    band = np.ascontiguousarray(views_np[:, :, :rows, :])
+    q = type(p)(**{**p.__dict__, "H": rows})
+    cfg = oracle.make_cfg(q)
+    init = oracle.initial_disparity(cfg, band, None, q.p1_frac, q.p2_frac)
+    t0 = time.perf_counter()
+    off, cost = oracle.cost_volume(cfg, band, init["lo"], init["cnt"], init["census"])
+    mean = float(cost.mean())
+    oracle.sgm_bounded(q.H, q.W, init["lo"], init["cnt"], off, cost, q.p1_frac * mean, q.p2_frac * mean)
+    dt = time.perf_counter() - t0
+    return {"value": round(dt * 1e3 * p.H / rows, 1), "unit": "ms", "cores": oracle.threads(),
+            "kind": "oracle",
+            "sample": f"rows 0..{rows - 1} of the light field (cost volume + SGM on the band, "
+                      f"{dt:.1f} s), scaled by {p.H}/{rows}"}
+
+
+def run_reference(args, ws, rank):
+    if rank != 0:
+        return None
+    views_np, gt, p = workload(args.workload, 0)
+    samples = []
+    for _ in range(args.warmup):
+        cpu_baseline(args, views_np, p, rows=args.cpu_rows)
+    for _ in range(args.steps):
+        samples.append(cpu_baseline(args, views_np, p, rows=args.cpu_rows))
+    v = statistics.mean(s["value"] for s in samples)
+    cb = dict(samples[0])
+    cb["value"] = round(v, 1)
+    return {"impl": "reference", "metric": METRIC, "value": round(v, 1), "unit": "ms", "n_gpus": ws,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(v, 1),
+            "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": workload_label(p), "parallelism": "host cores"},
+            "cpu_baseline": cb, "e2e": {"value": round(v, 1), "unit": "ms", "h2d_bytes_per_step": 0,
+                                        "d2h_bytes_per_step": 0}}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=60)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="bench", choices=["bench", "plenoptic", "tiny"])
+    ap.add_argument("--cpu-rows", type=int, default=128)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    ws, rank, local = dist_env()
+    if args.impl == "reference":
+        out = run_reference(args, ws, rank)
+    else:
+        out = run_ours(args, ws, rank, local)
+    if out is not None:
+        print(json.dumps(out), flush=True)
+
+
+if __name__ == "__main__":
+    main()

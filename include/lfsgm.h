@@ -1,0 +1,174 @@
+/*
+ * lfsgm.h -- C ABI of the GB300 light-field depth library (semi-global matching on
+ * a bounded light-field cost volume), after Anisimov, Wasenmueller and Stricker,
+ * "Rapid Light Field Depth Estimation with Semi-Global Matching", ICCP 2019.
+ *
+ * Plain C: pointers and sizes only.  Every array argument is a DEVICE pointer owned
+ * by the caller unless its comment says "host".  Calls are asynchronous on the
+ * stream given to lfsgm_create, except where a comment says they synchronise.
+ * Argument errors are returned at once; errors detected inside kernels are latched
+ * in a device status word and returned by lfsgm_sync.  Nothing traps or aborts.
+ *
+ * Notation.  views[v][u][y][x] float32, contiguous: (x,y) spatial position in a view
+ * (the paper's (u,v)), (u,v) angular position of the view (the paper's (s,t)),
+ * reference view (uc,vc).  A view (u,v) is sampled for pixel (x,y) and disparity d at
+ *     (x + (u-uc) d, y + (v-vc) d)                      (Sec. III-A, Eq. 1)
+ * (the paper writes (s^-s) d: our d has the opposite sign, larger d = nearer).
+ * Labels: coarse k in [0,Lc) and fine g in [0,G) on inclusive grids over [dmin,dmax]:
+ *     d_k = dmin + k*((dmax-dmin)/(Lc-1)),   d_g = dmin + g*((dmax-dmin)/(G-1)).
+ * Shift split (the paper is silent): s = a*d in double; when 2s is within 2e-9 of an
+ * integer, s is snapped to that half-integer; ox = floor(s), fx = s-ox (bilinear
+ * taps), nx = floor(s+0.5) (census position).  Tap indices are clamped to the image.
+ *
+ * Windowed cost layout ("CSR", part of this ABI): pixel p = y*W + x has the fine
+ * labels lo[p] .. lo[p]+cnt[p]-1; slot j of pixel p is at cost[off[p] + j].
+ * off[p] is a multiple of 4 (16-byte aligned rows), off[p+1] - off[p] >= cnt[p];
+ * the padding slots are written with 0 and never read.  off has N+1 entries.
+ */
+#ifndef LFSGM_H
+#define LFSGM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    LFSGM_OK = 0,
+    LFSGM_ERR_INVALID_ARG = 1,   /* bad config value, null pointer, P2 < P1, ...        */
+    LFSGM_ERR_NO_MEMORY = 2,     /* device allocation failed                            */
+    LFSGM_ERR_WORKSPACE = 3,     /* caller workspace too small or misaligned            */
+    LFSGM_ERR_CUDA = 4,          /* a CUDA runtime call failed (see lfsgm_last_error)   */
+    LFSGM_ERR_UNSUPPORTED = 5,   /* sizes outside what the kernels support              */
+    LFSGM_ERR_TIMEOUT = 6,       /* a bounded device-side wait gave up                  */
+    LFSGM_ERR_DEVICE_CHECK = 7   /* a kernel-side consistency check failed              */
+} lfsgm_status;
+
+typedef struct lfsgm_ctx *lfsgm_handle;
+
+/* Method parameters.  The paper's values (Sec. IV "Algorithm parameters") are phi = 3,
+ * lambda = 2, median window 3, P1/P2 = 21/45 and 17/35; the synthetic workloads use
+ * penalties proportional to the mean cost instead (p1_frac, p2_frac). */
+typedef struct {
+    int32_t U, V, H, W;        /* angular (U x V views) and spatial (H x W) sizes          */
+    int32_t uc, vc;            /* reference view; -1 -> (U-1)/2, (V-1)/2                    */
+    int32_t census_w;          /* census window side: 5 (24 bits) or 7 (48 bits)           */
+    double  dmin, dmax;        /* disparity range T (Sec. III-D), px per angular step       */
+    int32_t coarse_labels;     /* Lc, 2..256                                                */
+    int32_t init_views;        /* 1: whole cross arms; 0: the paper's 4 extreme views       */
+    double  phi;               /* fusion threshold in coarse labels (Sec. III-D)            */
+    int32_t fill_passes;       /* median hole-filling passes, 0..4 (Sec. III-D: 1 or 2)     */
+    int32_t fine_labels;       /* G, 2..4096                                                */
+    int32_t fine_radius;       /* R: window = nearest fine label to D_init +- R (Eq. 11)    */
+    float   w_l2;              /* weight of the l2 term (Eq. 12)                             */
+    float   w_census;          /* weight of the census term (Eq. 15)                         */
+    double  p1_frac, p2_frac;  /* derived penalties: P = frac * mean cost                   */
+    int32_t subpixel;          /* 0 none, 1 parabola (Eq. 13), 2 soft-argmin                */
+    float   softmin_tau;       /* soft-argmin temperature                                   */
+} lfsgm_config;
+
+/* Create a handle for one light-field shape.  `stream` is a cudaStream_t (NULL = the
+ * legacy default stream).  Builds the shift tables in double precision on the host
+ * and uploads them.  Returns LFSGM_ERR_INVALID_ARG for an inconsistent config. */
+lfsgm_status lfsgm_create(const lfsgm_config *cfg, void *stream, lfsgm_handle *out);
+lfsgm_status lfsgm_destroy(lfsgm_handle h);
+
+/* Scratch the handle needs (census words, coarse volume and sums, maps, partial sums).
+ * Without lfsgm_set_workspace the handle allocates it itself on first use; with it, the
+ * caller's buffer (device, 256-byte aligned, >= *bytes) is used and never freed here. */
+lfsgm_status lfsgm_workspace_size(lfsgm_handle h, size_t *bytes);
+lfsgm_status lfsgm_set_workspace(lfsgm_handle h, void *dptr, size_t bytes);
+
+/* Upper bound of off[N] for this config (every pixel with a whole-range window). */
+lfsgm_status lfsgm_max_nnz(lfsgm_handle h, int64_t *nnz);
+
+/* Initial disparity map and fine search windows (Sec. III-D, Eq. 7-11):
+ * census of the cross views (Eq. 2-3), per-arm census cost over the coarse labels
+ * (Eq. 7 summed over the arm's views), integer SGM per arm over 8 paths (Eq. 8-9),
+ * WTA per arm (Eq. 10), sequential fusion with threshold phi, median hole filling,
+ * borders D_init +- lambda saturated to T (Eq. 11; discarded pixels: whole range).
+ *   views  [V][U][H][W] float32
+ *   Pc1, Pc2  integer coarse penalties; Pc1 <= 0 -> per arm round(p*_frac * mean arm
+ *             cost) with P1 >= 1, P2 >= P1.
+ *   lo, cnt   [H*W] int32 out: window first fine label and label count
+ *   off       [H*W+1] int64 out: padded row offsets (see layout above)
+ *   dinit     [H*W] float32 out (nullable): fused, filled map in coarse-label units
+ *             (multiples of 1/8), NaN where discarded
+ *   maps      [4][H*W] int32 out (nullable): per-arm WTA labels (up, down, left, right;
+ *             empty arms are skipped, so only the first n_arms rows are written)
+ *   nnz_host  host int64 out (nullable): off[N]; when given the call synchronises. */
+lfsgm_status lfsgm_initial_disparity(lfsgm_handle h, const float *views, int32_t Pc1, int32_t Pc2,
+                                     int32_t *lo, int32_t *cnt, int64_t *off, float *dinit,
+                                     int32_t *maps, int64_t *nnz_host);
+
+/* Bounded fine cost volume (Sec. III-E, Eq. 12 and Eq. 15) over every view but the
+ * reference, for the labels of each pixel's window:
+ *   C(p,g) = w_l2 * sum |I_ref(p) - bilinear(I_uv, p + (u-uc, v-vc) d_g)|
+ *          + w_census * sum HD(census_ref(p), census_uv(p + nearest shift)).
+ *   views [V][U][H][W] float32; lo, cnt, off as produced above; cost [off[N]] float32 out. */
+lfsgm_status lfsgm_cost_volume(lfsgm_handle h, const float *views, const int32_t *lo,
+                               const int32_t *cnt, const int64_t *off, float *cost);
+
+/* Bounded 8-path SGM (Sec. III-E with Eq. 8-9), normalised recurrence
+ *   L_r(p,g) = C(p,g) + (min(L'(g), L'(g-1)+P1, L'(g+1)+P1, m+P2) - m),
+ * L' = L_r(p-r,.) over the predecessor's window, m its minimum, absent labels left out,
+ * L_r = C at path starts; agg = sum over the 8 directions.  P1 < 0 -> P1 = p1_frac *
+ * mean(cost over active slots), P2 = p2_frac * mean (computed on the device).
+ * Requires 0 <= P1 <= P2 otherwise.  agg [off[N]] float32 out. */
+lfsgm_status lfsgm_sgm_aggregate(lfsgm_handle h, const float *cost, const int32_t *lo,
+                                 const int32_t *cnt, const int64_t *off, float P1, float P2,
+                                 float *agg);
+
+/* Winner-takes-all (Eq. 10, lowest label on ties) and sub-pixel refinement:
+ * mode 1 parabola vertex (Eq. 13 with the vertex's sign) when the winner lies in
+ * [lo+1, lo+cnt-2] and cnt >= 5; mode 2 soft-argmin sum softmax(-agg/tau) d_g.
+ *   label [H*W] int32 out (fine label), disp [H*W] float32 out (pixels). */
+lfsgm_status lfsgm_wta_subpixel(lfsgm_handle h, const float *agg, const int32_t *lo,
+                                const int32_t *cnt, const int64_t *off, int32_t *label, float *disp);
+
+/* Adjoint of cost volume -> SGM -> soft-argmin (not in the paper).  Given grad_disp
+ * = dLoss/d disp of the soft-argmin output, returns dLoss/d cost (grad_cost, CSR like
+ * cost), dLoss/dP1 and dLoss/dP2 (device scalars) and dLoss/d views through the l2 term
+ * and its bilinear weights (grad_views [V][U][H][W]; the census term has no gradient).
+ * Path costs are recomputed per direction; subgradients follow the recorded argmin.
+ * grad_views may be NULL (then only grad_cost and the penalty gradients are formed). */
+lfsgm_status lfsgm_backward(lfsgm_handle h, const float *views, const float *cost,
+                            const int32_t *lo, const int32_t *cnt, const int64_t *off,
+                            float P1, float P2, const float *grad_disp, float *grad_cost,
+                            float *grad_P1, float *grad_P2, float *grad_views);
+
+/* Waits for the handle's stream and returns the latched device status (then clears it). */
+lfsgm_status lfsgm_sync(lfsgm_handle h);
+
+/* Human-readable text of the last error on this handle (static storage of the handle). */
+const char *lfsgm_last_error(lfsgm_handle h);
+
+/* Kernel launches issued through this handle since creation (for accounting). */
+int64_t lfsgm_launch_count(lfsgm_handle h);
+
+/* Per-kernel timing: with `enable` != 0 every launch is bracketed by CUDA events on the
+ * handle's stream.  lfsgm_kernel_times fills up to `cap` (name, milliseconds) records of
+ * the launches since the last call (names are static strings); synchronises. */
+lfsgm_status lfsgm_set_profiling(lfsgm_handle h, int32_t enable);
+lfsgm_status lfsgm_kernel_times(lfsgm_handle h, const char **names, float *ms, int32_t cap,
+                                int32_t *n_out);
+
+/* Whole method from HOST memory (end-to-end form): copies the views host->device,
+ * runs initial disparity, cost volume, SGM (derived penalties) and WTA/sub-pixel,
+ * copies disp (and label when non-NULL) device->host, and synchronises.  Device
+ * buffers are owned by the handle and allocated on first use.
+ *   views_host [V][U][H][W] float32 (pinned memory gives full copy speed)
+ *   disp_host [H*W] float32, label_host [H*W] int32 (nullable). */
+lfsgm_status lfsgm_depth_host(lfsgm_handle h, const float *views_host, float *disp_host,
+                              int32_t *label_host);
+
+/* Whole method on device buffers owned by the handle (views stay caller-owned):
+ * the same chain as lfsgm_depth_host without the copies. disp, label: device, nullable. */
+lfsgm_status lfsgm_depth(lfsgm_handle h, const float *views, float *disp, int32_t *label);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* LFSGM_H */

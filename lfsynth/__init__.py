@@ -13,6 +13,7 @@ point lies inside its own region (the farthest plane fills holes), and sampling
 that plane's texture there bilinearly.  Then Gaussian noise, an optional
 vignetting gain and a clip to [0, 1] are applied.
 
+Voronoi regions are rasterised at 1/4 px (the scene's region map is that raster).
 Seeds: ``np.random.SeedSequence(seed).spawn(3)`` gives the texture, geometry and
 noise streams; the workloads use ``seed = 1000 * workload_index + lf_index``.
 """
@@ -84,41 +85,39 @@ def _blur121(t: np.ndarray) -> np.ndarray:
     return 0.25 * p[:, :-2] + 0.5 * p[:, 1:-1] + 0.25 * p[:, 2:]
 
 
-def _sample(tex: np.ndarray, margin: int, x: np.ndarray, y: np.ndarray) -> np.ndarray:
-    """Bilinear texture lookup at reference coordinates (clamped to the texture)."""
-    th, tw = tex.shape
+def _sample(tex: np.ndarray, margin: int, idx: np.ndarray, x: np.ndarray, y: np.ndarray) -> np.ndarray:
+    """Bilinear lookup in texture ``idx`` at reference coordinates (clamped to the texture)."""
+    _, th, tw = tex.shape
     gx = np.clip(x + margin, 0.0, tw - 1.000001)
     gy = np.clip(y + margin, 0.0, th - 1.000001)
     x0 = np.floor(gx).astype(np.int64)
     y0 = np.floor(gy).astype(np.int64)
     fx = gx - x0
     fy = gy - y0
-    t00 = tex[y0, x0]
-    t10 = tex[y0, x0 + 1]
-    t01 = tex[y0 + 1, x0]
-    t11 = tex[y0 + 1, x0 + 1]
+    t00 = tex[idx, y0, x0]
+    t10 = tex[idx, y0, x0 + 1]
+    t01 = tex[idx, y0 + 1, x0]
+    t11 = tex[idx, y0 + 1, x0 + 1]
     return (1 - fy) * ((1 - fx) * t00 + fx * t10) + fy * ((1 - fx) * t01 + fx * t11)
 
 
-def render(p: LFParams, planes, region, textures, margin, noise_rng, sigma, vignette=False,
-           views_mask=None):
+def render(p: LFParams, planes, region, textures, margin, noise_rng, sigma, vignette=False):
     """Render views[v][u][y][x] (float32) and the reference-view disparity (float64).
 
     ``region(i, x, y)`` -> bool array: is reference point (x, y) on plane i.
     ``textures[i]``: texture of plane i on the reference grid plus ``margin``."""
     U, V, H, W = p.U, p.V, p.H, p.W
     Y, X = np.mgrid[0:H, 0:W].astype(np.float64)
+    tex = np.stack(textures)
     views = np.zeros((V, U, H, W), np.float32)
     gt = None
     for v in range(V):
         for u in range(U):
-            if views_mask is not None and not views_mask(u, v):
-                continue
             a, b = u - p.uc, v - p.vc
             best_d = np.full((H, W), -np.inf)
-            best_val = np.zeros((H, W))
             far_d = np.full((H, W), np.inf)
-            far_val = np.zeros((H, W))
+            best = [np.zeros((H, W), np.int64), np.zeros((H, W)), np.zeros((H, W))]
+            far = [np.zeros((H, W), np.int64), np.zeros((H, W)), np.zeros((H, W))]
             for i, pl in enumerate(planes):
                 # X = x + a*d(x,y), Y = y + b*d(x,y), with d affine in (x, y): 2x2 solve
                 kx, ky = pl.b / W, pl.c / H
@@ -130,16 +129,17 @@ def render(p: LFParams, planes, region, textures, margin, noise_rng, sigma, vign
                 x = (m11 * r0 - m01 * r1) / det
                 y = (m00 * r1 - m10 * r0) / det
                 d = pl.disp(x, y, W, H)
-                val = _sample(textures[i], margin, x, y)
-                ok = region(i, x, y)
-                take = ok & (d > best_d)
+                take = region(i, x, y) & (d > best_d)
                 best_d = np.where(take, d, best_d)
-                best_val = np.where(take, val, best_val)
+                for arr, val in zip(best, (i, x, y)):
+                    arr[take] = val if np.isscalar(val) else val[take]
                 fall = d < far_d
                 far_d = np.where(fall, d, far_d)
-                far_val = np.where(fall, val, far_val)
+                for arr, val in zip(far, (i, x, y)):
+                    arr[fall] = val if np.isscalar(val) else val[fall]
             hole = ~np.isfinite(best_d)
-            img = np.where(hole, far_val, best_val)
+            idx, xs, ys = (np.where(hole, f, bb) for f, bb in zip(far, best))
+            img = _sample(tex, margin, idx, xs, ys)
             if a == 0 and b == 0:
                 gt = np.where(hole, far_d, best_d)
             if sigma > 0:
@@ -224,10 +224,17 @@ def voronoi_scene(p: LFParams, seed: int, n_planes: int, a_range, slope, clamp, 
         a = float(np.clip(a, -clamp + ext, clamp - ext))
         planes.append(Plane(a, b, c))
 
+    # Voronoi cells of the sites, rasterised at 1/4 px over the texture domain
+    q = 4
+    gy, gx = np.mgrid[0:th * q, 0:tw * q].astype(np.float32) / q - margin
+    d2 = np.stack([(gx - sites[j, 0]) ** 2 + (gy - sites[j, 1]) ** 2 for j in range(n_planes)])
+    cell = np.argmin(d2, axis=0).astype(np.int8)
+    del d2, gx, gy
+
     def region(i, x, y):
-        d2 = [(x - sites[j, 0]) ** 2 + (y - sites[j, 1]) ** 2 for j in range(n_planes)]
-        best = np.argmin(np.stack(d2), axis=0)
-        return best == i
+        qx = np.clip(np.rint((x + margin) * q).astype(np.int64), 0, tw * q - 1)
+        qy = np.clip(np.rint((y + margin) * q).astype(np.int64), 0, th * q - 1)
+        return cell[qy, qx] == i
 
     views, gt = render(p, planes, region, textures, margin, noise_rng, sigma, vignette)
     return views, gt

@@ -30,11 +30,11 @@ DIRECTIONS = ((1, 0), (-1, 0), (0, 1), (0, -1), (1, 1), (-1, -1), (1, -1), (-1, 
 
 
 def build(force: bool = False) -> str:
-    """Compile the oracle with gcc (no FMA contraction, no fast-math)."""
+    """Compile the oracle with gcc (no FMA contraction, no fast-math, OpenMP over rows)."""
     if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
         tmp = _LIB + f".{os.getpid()}.tmp"
-        subprocess.check_call(["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fno-fast-math",
-                               "-fPIC", "-shared", "-o", tmp, _SRC, "-lm"])
+        subprocess.check_call(["gcc", "-O2", "-std=c11", "-fopenmp", "-ffp-contract=off",
+                               "-fno-fast-math", "-fPIC", "-shared", "-o", tmp, _SRC, "-lm"])
         os.replace(tmp, _LIB)
     return _LIB
 
@@ -227,6 +227,11 @@ def sgm_bounded_path(H, W, lo, cnt, off, cost, P1, P2, direction, normalised=Tru
                               _ptr(cost, C.c_double), float(P1), float(P2), direction,
                               1 if normalised else 0, _ptr(out, C.c_double))
     return out
+
+
+def threads() -> int:
+    """Threads the oracle's parallel loops use (OpenMP default: all cores)."""
+    return int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
 
 
 def sgm_bounded(H, W, lo, cnt, off, cost, P1, P2):

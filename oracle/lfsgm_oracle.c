@@ -24,7 +24,10 @@
  *   Image borders (the paper is silent): every tap index is clamped to the image.
  *
  * Parity pins for every function live in tests/test_oracle_*.py.
- * Build: gcc -O2 -ffp-contract=off -fno-fast-math -shared -fPIC (see oracle/__init__.py).
+ * Build: gcc -O2 -fopenmp -ffp-contract=off -fno-fast-math -shared -fPIC (oracle/__init__.py).
+ * OpenMP only splits loops whose iterations are independent (rows, or the pixels of a
+ * row whose predecessors are final); every value is computed by the same expression in
+ * the same order as the serial loop, so results do not depend on the thread count.
  */
 #include <math.h>
 #include <stdint.h>
@@ -75,6 +78,7 @@ void or_shift(int a, double d, int *o, double *f, int *n)
 void or_census(const float *img, int H, int W, int w, uint64_t *out)
 {
     int h = w / 2;
+#pragma omp parallel for schedule(static)
     for (int y = 0; y < H; y++)
         for (int x = 0; x < W; x++) {
             double c = (double)img[(size_t)y * W + x];
@@ -146,6 +150,7 @@ int or_coarse_cost(const or_cfg *c, const uint64_t *cen, int arm, int64_t *out)
     if (nv == 0) return 0;
     size_t HW = (size_t)c->H * c->W;
     const uint64_t *cref = cen + ((size_t)c->vc * c->U + c->uc) * HW;
+#pragma omp parallel for schedule(static)
     for (int y = 0; y < c->H; y++)
         for (int x = 0; x < c->W; x++)
             for (int k = 0; k < c->Lc; k++) {
@@ -193,30 +198,50 @@ static int order_x(int i, int W, int dx) { return dx >= 0 ? i : W - 1 - i; }
  * shifts L_r(p,.) by a constant and leaves every argmin unchanged):
  *   L(p,d) = C(p,d) + (min(L'(d), L'(d-1)+P1, L'(d+1)+P1, m+P2) - m)
  * with L'(.) = L(p-r,.) and L(p,.) = C(p,.) where p-r is outside the image. */
+static void sgm_int_step(int H, int W, int L, const int64_t *C, int64_t P1, int64_t P2, int dx, int dy,
+                         int x, int y, int64_t *Lr)
+{
+    int qx = x - dx, qy = y - dy;
+    const int64_t *c = C + ((size_t)y * W + x) * L;
+    int64_t *l = Lr + ((size_t)y * W + x) * L;
+    if (qx < 0 || qx >= W || qy < 0 || qy >= H) {
+        for (int d = 0; d < L; d++) l[d] = c[d];
+        return;
+    }
+    const int64_t *lp = Lr + ((size_t)qy * W + qx) * L;
+    int64_t m = lp[0];
+    for (int d = 1; d < L; d++) if (lp[d] < m) m = lp[d];
+    for (int d = 0; d < L; d++) {
+        int64_t t = m + P2;
+        if (lp[d] < t) t = lp[d];
+        if (d > 0 && lp[d - 1] + P1 < t) t = lp[d - 1] + P1;
+        if (d < L - 1 && lp[d + 1] + P1 < t) t = lp[d + 1] + P1;
+        l[d] = c[d] + (t - m);
+    }
+}
+
+/* Integer SGM over the full label range for one direction (Eq. 8, normalised form
+ * of Hirschmueller: the minimum m of the predecessor's costs is subtracted, which
+ * shifts L_r(p,.) by a constant and leaves every argmin unchanged):
+ *   L(p,d) = C(p,d) + (min(L'(d), L'(d-1)+P1, L'(d+1)+P1, m+P2) - m)
+ * with L'(.) = L(p-r,.) and L(p,.) = C(p,.) where p-r is outside the image.
+ * Pixels whose predecessors are already final are processed in parallel: whole rows
+ * for horizontal paths, the pixels of one row otherwise. */
 void or_sgm_int_path(int H, int W, int L, const int64_t *C, int64_t P1, int64_t P2, int dir, int64_t *Lr)
 {
     int dx = DIRS[dir][0], dy = DIRS[dir][1];
-    for (int iy = 0; iy < H; iy++)
-        for (int ix = 0; ix < W; ix++) {
-            int y = order_y(iy, H, dy), x = order_x(ix, W, dx);
-            int qx = x - dx, qy = y - dy;
-            const int64_t *c = C + ((size_t)y * W + x) * L;
-            int64_t *l = Lr + ((size_t)y * W + x) * L;
-            if (qx < 0 || qx >= W || qy < 0 || qy >= H) {
-                for (int d = 0; d < L; d++) l[d] = c[d];
-                continue;
-            }
-            const int64_t *lp = Lr + ((size_t)qy * W + qx) * L;
-            int64_t m = lp[0];
-            for (int d = 1; d < L; d++) if (lp[d] < m) m = lp[d];
-            for (int d = 0; d < L; d++) {
-                int64_t t = m + P2;
-                if (lp[d] < t) t = lp[d];
-                if (d > 0 && lp[d - 1] + P1 < t) t = lp[d - 1] + P1;
-                if (d < L - 1 && lp[d + 1] + P1 < t) t = lp[d + 1] + P1;
-                l[d] = c[d] + (t - m);
-            }
+    if (dy == 0) {
+#pragma omp parallel for schedule(static)
+        for (int iy = 0; iy < H; iy++)
+            for (int ix = 0; ix < W; ix++)
+                sgm_int_step(H, W, L, C, P1, P2, dx, dy, order_x(ix, W, dx), order_y(iy, H, dy), Lr);
+    } else {
+        for (int iy = 0; iy < H; iy++) {
+#pragma omp parallel for schedule(static)
+            for (int ix = 0; ix < W; ix++)
+                sgm_int_step(H, W, L, C, P1, P2, dx, dy, order_x(ix, W, dx), order_y(iy, H, dy), Lr);
         }
+    }
 }
 
 /* Sum over the 8 directions (Eq. 9). */
@@ -227,6 +252,7 @@ void or_sgm_int(int H, int W, int L, const int64_t *C, int64_t P1, int64_t P2, i
     memset(Cs, 0, n * sizeof(int64_t));
     for (int r = 0; r < 8; r++) {
         or_sgm_int_path(H, W, L, C, P1, P2, r, Lr);
+#pragma omp parallel for schedule(static)
         for (size_t i = 0; i < n; i++) Cs[i] += Lr[i];
     }
     free(Lr);
@@ -334,6 +360,7 @@ void or_cost_volume(const or_cfg *c, const float *views, const uint64_t *cen,
     size_t HW = (size_t)c->H * c->W;
     const float *Iref = views + ((size_t)c->vc * c->U + c->uc) * HW;
     const uint64_t *cref = cen + ((size_t)c->vc * c->U + c->uc) * HW;
+#pragma omp parallel for schedule(dynamic, 1)
     for (int y = 0; y < c->H; y++)
         for (int x = 0; x < c->W; x++) {
             size_t p = (size_t)y * c->W + x;
@@ -364,6 +391,30 @@ void or_cost_volume(const or_cfg *c, const float *views, const uint64_t *cen,
         }
 }
 
+static void sgm_bounded_step(int H, int W, const int32_t *lo, const int32_t *cnt, const int64_t *off,
+                             const double *C, double P1, double P2, int dx, int dy, int x, int y,
+                             int normalised, double *Lr)
+{
+    size_t p = (size_t)y * W + x;
+    int qx = x - dx, qy = y - dy;
+    if (qx < 0 || qx >= W || qy < 0 || qy >= H) {
+        for (int j = 0; j < cnt[p]; j++) Lr[off[p] + j] = C[off[p] + j];
+        return;
+    }
+    size_t q = (size_t)qy * W + qx;
+    const double *lp = Lr + off[q];
+    double m = lp[0];
+    for (int i = 1; i < cnt[q]; i++) if (lp[i] < m) m = lp[i];
+    for (int j = 0; j < cnt[p]; j++) {
+        int i = lo[p] + j - lo[q];          /* slot of the same label in q */
+        double t = m + P2;
+        if (i >= 0 && i < cnt[q] && lp[i] < t) t = lp[i];
+        if (i - 1 >= 0 && i - 1 < cnt[q] && lp[i - 1] + P1 < t) t = lp[i - 1] + P1;
+        if (i + 1 >= 0 && i + 1 < cnt[q] && lp[i + 1] + P1 < t) t = lp[i + 1] + P1;
+        Lr[off[p] + j] = normalised ? C[off[p] + j] + (t - m) : C[off[p] + j] + t;
+    }
+}
+
 /* ------------------------------------------- Bounded SGM (Sec. III-E, Eq. 8-9)
  * Eq. 8 on the windowed cost: terms that refer to labels outside the predecessor's
  * window are absent, and m is the minimum over the predecessor's window.
@@ -373,28 +424,20 @@ void or_sgm_bounded_path(int H, int W, const int32_t *lo, const int32_t *cnt, co
                          const double *C, double P1, double P2, int dir, int normalised, double *Lr)
 {
     int dx = DIRS[dir][0], dy = DIRS[dir][1];
-    for (int iy = 0; iy < H; iy++)
-        for (int ix = 0; ix < W; ix++) {
-            int y = order_y(iy, H, dy), x = order_x(ix, W, dx);
-            size_t p = (size_t)y * W + x;
-            int qx = x - dx, qy = y - dy;
-            if (qx < 0 || qx >= W || qy < 0 || qy >= H) {
-                for (int j = 0; j < cnt[p]; j++) Lr[off[p] + j] = C[off[p] + j];
-                continue;
-            }
-            size_t q = (size_t)qy * W + qx;
-            const double *lp = Lr + off[q];
-            double m = lp[0];
-            for (int i = 1; i < cnt[q]; i++) if (lp[i] < m) m = lp[i];
-            for (int j = 0; j < cnt[p]; j++) {
-                int i = lo[p] + j - lo[q];          /* slot of the same label in q */
-                double t = m + P2;
-                if (i >= 0 && i < cnt[q] && lp[i] < t) t = lp[i];
-                if (i - 1 >= 0 && i - 1 < cnt[q] && lp[i - 1] + P1 < t) t = lp[i - 1] + P1;
-                if (i + 1 >= 0 && i + 1 < cnt[q] && lp[i + 1] + P1 < t) t = lp[i + 1] + P1;
-                Lr[off[p] + j] = normalised ? C[off[p] + j] + (t - m) : C[off[p] + j] + t;
-            }
+    if (dy == 0) {
+#pragma omp parallel for schedule(static)
+        for (int iy = 0; iy < H; iy++)
+            for (int ix = 0; ix < W; ix++)
+                sgm_bounded_step(H, W, lo, cnt, off, C, P1, P2, dx, dy, order_x(ix, W, dx),
+                                 order_y(iy, H, dy), normalised, Lr);
+    } else {
+        for (int iy = 0; iy < H; iy++) {
+#pragma omp parallel for schedule(static)
+            for (int ix = 0; ix < W; ix++)
+                sgm_bounded_step(H, W, lo, cnt, off, C, P1, P2, dx, dy, order_x(ix, W, dx),
+                                 order_y(iy, H, dy), normalised, Lr);
         }
+    }
 }
 
 /* C_s = sum over the 8 directions (Eq. 9), added as a balanced tree

@@ -1,0 +1,309 @@
+"""GB300 light-field depth with semi-global matching -- Python binding of liblfsgm.so.
+
+Thin ctypes marshalling over the C ABI in ``include/lfsgm.h``: every function named
+``lfsgm_*`` here calls the C entry point of the same name with the device pointers of
+the torch tensors it is given.  All arithmetic runs in the library's CUDA kernels; there
+is no CPU fallback, and ``load()`` raises if the library is missing.
+
+Method: Anisimov, Wasenmueller, Stricker, "Rapid Light Field Depth Estimation with
+Semi-Global Matching", ICCP 2019 (initial map Sec. III-D, final map Sec. III-E,
+post-processing Sec. III-F).
+"""
+from __future__ import annotations
+
+import ctypes as C
+import dataclasses
+import os
+import threading
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "liblfsgm.so")
+_lock = threading.Lock()
+_lib = None
+
+OK = 0
+STATUS = {0: "OK", 1: "INVALID_ARG", 2: "NO_MEMORY", 3: "WORKSPACE", 4: "CUDA", 5: "UNSUPPORTED",
+          6: "TIMEOUT", 7: "DEVICE_CHECK"}
+
+
+class LfsgmError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"lfsgm error {STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+class Config(C.Structure):
+    """Mirror of ``lfsgm_config``."""
+    _fields_ = [("U", C.c_int32), ("V", C.c_int32), ("H", C.c_int32), ("W", C.c_int32),
+                ("uc", C.c_int32), ("vc", C.c_int32), ("census_w", C.c_int32),
+                ("dmin", C.c_double), ("dmax", C.c_double), ("coarse_labels", C.c_int32),
+                ("init_views", C.c_int32), ("phi", C.c_double), ("fill_passes", C.c_int32),
+                ("fine_labels", C.c_int32), ("fine_radius", C.c_int32), ("w_l2", C.c_float),
+                ("w_census", C.c_float), ("p1_frac", C.c_double), ("p2_frac", C.c_double),
+                ("subpixel", C.c_int32), ("softmin_tau", C.c_float)]
+
+
+def make_config(p) -> Config:
+    """``Config`` from any object carrying the method's parameter names."""
+    return Config(U=p.U, V=p.V, H=p.H, W=p.W, uc=getattr(p, "uc", -1), vc=getattr(p, "vc", -1),
+                  census_w=p.census_w, dmin=p.dmin, dmax=p.dmax, coarse_labels=p.coarse_labels,
+                  init_views=p.init_views, phi=p.phi, fill_passes=p.fill_passes,
+                  fine_labels=p.fine_labels, fine_radius=p.fine_radius, w_l2=p.w_l2,
+                  w_census=p.w_census, p1_frac=p.p1_frac, p2_frac=p.p2_frac, subpixel=p.subpixel,
+                  softmin_tau=p.softmin_tau)
+
+
+EXPORTS = ["lfsgm_create", "lfsgm_destroy", "lfsgm_workspace_size", "lfsgm_set_workspace",
+           "lfsgm_max_nnz", "lfsgm_initial_disparity", "lfsgm_cost_volume", "lfsgm_sgm_aggregate",
+           "lfsgm_wta_subpixel", "lfsgm_backward", "lfsgm_sync", "lfsgm_last_error",
+           "lfsgm_launch_count", "lfsgm_set_profiling", "lfsgm_kernel_times", "lfsgm_depth_host",
+           "lfsgm_depth"]
+
+
+def load(build_if_missing: bool = False):
+    """Load liblfsgm.so (raises if it is missing and not built)."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        if not os.path.exists(LIB_PATH):
+            if build_if_missing:
+                from . import _build
+                _build.build()
+            else:
+                raise RuntimeError(f"{LIB_PATH} is missing: build it with __graft_entry__.build() "
+                                   "(there is no CPU fallback)")
+        L = C.CDLL(LIB_PATH)
+        P, vp, i32, i64, f32 = C.POINTER, C.c_void_p, C.c_int32, C.c_int64, C.c_float
+        L.lfsgm_create.argtypes = [P(Config), vp, P(vp)]
+        L.lfsgm_destroy.argtypes = [vp]
+        L.lfsgm_workspace_size.argtypes = [vp, P(C.c_size_t)]
+        L.lfsgm_set_workspace.argtypes = [vp, vp, C.c_size_t]
+        L.lfsgm_max_nnz.argtypes = [vp, P(i64)]
+        L.lfsgm_initial_disparity.argtypes = [vp, vp, i32, i32, vp, vp, vp, vp, vp, P(i64)]
+        L.lfsgm_cost_volume.argtypes = [vp, vp, vp, vp, vp, vp]
+        L.lfsgm_sgm_aggregate.argtypes = [vp, vp, vp, vp, vp, f32, f32, vp]
+        L.lfsgm_wta_subpixel.argtypes = [vp, vp, vp, vp, vp, vp, vp]
+        L.lfsgm_backward.argtypes = [vp, vp, vp, vp, vp, vp, f32, f32, vp, vp, vp, vp, vp]
+        L.lfsgm_sync.argtypes = [vp]
+        L.lfsgm_last_error.argtypes = [vp]
+        L.lfsgm_last_error.restype = C.c_char_p
+        L.lfsgm_launch_count.argtypes = [vp]
+        L.lfsgm_launch_count.restype = i64
+        L.lfsgm_set_profiling.argtypes = [vp, i32]
+        L.lfsgm_kernel_times.argtypes = [vp, P(C.c_char_p), P(f32), i32, P(i32)]
+        L.lfsgm_depth_host.argtypes = [vp, vp, vp, vp]
+        L.lfsgm_depth.argtypes = [vp, vp, vp, vp]
+        for name in EXPORTS:
+            if name not in ("lfsgm_last_error", "lfsgm_launch_count"):
+                getattr(L, name).restype = i32
+        _lib = L
+        return L
+
+
+def _check(st: int, h=None):
+    if st != OK:
+        raise LfsgmError(st, (load().lfsgm_last_error(h) or b"").decode())
+
+
+def _ptr(t, dtype=None, name="tensor"):
+    """Device pointer of a contiguous CUDA tensor (None -> NULL)."""
+    if t is None:
+        return None
+    import torch
+    if not isinstance(t, torch.Tensor):
+        raise TypeError(f"{name} must be a torch.Tensor")
+    if not t.is_cuda:
+        raise ValueError(f"{name} must be a CUDA tensor")
+    if dtype is not None and t.dtype != dtype:
+        raise TypeError(f"{name} must be {dtype}, got {t.dtype}")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    return t.data_ptr()
+
+
+def _hptr(a, name="array"):
+    """Host pointer of a contiguous CPU tensor or numpy array."""
+    import numpy as np
+    import torch
+    if isinstance(a, torch.Tensor):
+        if a.is_cuda or not a.is_contiguous():
+            raise ValueError(f"{name} must be a contiguous CPU tensor")
+        return a.data_ptr()
+    if isinstance(a, np.ndarray):
+        if not a.flags["C_CONTIGUOUS"]:
+            raise ValueError(f"{name} must be C-contiguous")
+        return a.ctypes.data
+    raise TypeError(f"{name} must be a tensor or ndarray")
+
+
+# ------------------------------------------------------------------ C ABI, same names
+def lfsgm_create(cfg, stream=None):
+    """Handle for one light-field shape.  ``cfg``: Config or an object with the parameter
+    names.  ``stream``: a torch.cuda.Stream (None -> torch's current stream)."""
+    import torch
+    L = load()
+    if not isinstance(cfg, Config):
+        cfg = make_config(cfg)
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    h = C.c_void_p()
+    st = L.lfsgm_create(C.byref(cfg), C.c_void_p(stream.cuda_stream), C.byref(h))
+    _check(st, None)
+    return h
+
+
+def lfsgm_destroy(h):
+    _check(load().lfsgm_destroy(h), None)
+
+
+def lfsgm_workspace_size(h) -> int:
+    n = C.c_size_t()
+    _check(load().lfsgm_workspace_size(h, C.byref(n)), h)
+    return n.value
+
+
+def lfsgm_set_workspace(h, ws):
+    _check(load().lfsgm_set_workspace(h, _ptr(ws, name="workspace"), ws.numel() * ws.element_size()), h)
+
+
+def lfsgm_max_nnz(h) -> int:
+    n = C.c_int64()
+    _check(load().lfsgm_max_nnz(h, C.byref(n)), h)
+    return n.value
+
+
+def lfsgm_initial_disparity(h, views, Pc1, Pc2, lo, cnt, off, dinit=None, maps=None, want_nnz=False):
+    import torch
+    nnz = C.c_int64(-1)
+    st = load().lfsgm_initial_disparity(
+        h, _ptr(views, torch.float32, "views"), int(Pc1), int(Pc2), _ptr(lo, torch.int32, "lo"),
+        _ptr(cnt, torch.int32, "cnt"), _ptr(off, torch.int64, "off"), _ptr(dinit, torch.float32, "dinit"),
+        _ptr(maps, torch.int32, "maps"), C.byref(nnz) if want_nnz else None)
+    _check(st, h)
+    return nnz.value if want_nnz else None
+
+
+def lfsgm_cost_volume(h, views, lo, cnt, off, cost):
+    import torch
+    _check(load().lfsgm_cost_volume(h, _ptr(views, torch.float32, "views"), _ptr(lo, torch.int32, "lo"),
+                                    _ptr(cnt, torch.int32, "cnt"), _ptr(off, torch.int64, "off"),
+                                    _ptr(cost, torch.float32, "cost")), h)
+
+
+def lfsgm_sgm_aggregate(h, cost, lo, cnt, off, P1, P2, agg):
+    import torch
+    _check(load().lfsgm_sgm_aggregate(h, _ptr(cost, torch.float32, "cost"), _ptr(lo, torch.int32, "lo"),
+                                      _ptr(cnt, torch.int32, "cnt"), _ptr(off, torch.int64, "off"),
+                                      float(P1), float(P2), _ptr(agg, torch.float32, "agg")), h)
+
+
+def lfsgm_wta_subpixel(h, agg, lo, cnt, off, label, disp):
+    import torch
+    _check(load().lfsgm_wta_subpixel(h, _ptr(agg, torch.float32, "agg"), _ptr(lo, torch.int32, "lo"),
+                                     _ptr(cnt, torch.int32, "cnt"), _ptr(off, torch.int64, "off"),
+                                     _ptr(label, torch.int32, "label"), _ptr(disp, torch.float32, "disp")), h)
+
+
+def lfsgm_backward(h, views, cost, lo, cnt, off, P1, P2, grad_disp, grad_cost, grad_P1, grad_P2,
+                   grad_views=None):
+    import torch
+    f = torch.float32
+    _check(load().lfsgm_backward(h, _ptr(views, f, "views"), _ptr(cost, f, "cost"),
+                                 _ptr(lo, torch.int32, "lo"), _ptr(cnt, torch.int32, "cnt"),
+                                 _ptr(off, torch.int64, "off"), float(P1), float(P2),
+                                 _ptr(grad_disp, f, "grad_disp"), _ptr(grad_cost, f, "grad_cost"),
+                                 _ptr(grad_P1, f, "grad_P1"), _ptr(grad_P2, f, "grad_P2"),
+                                 _ptr(grad_views, f, "grad_views")), h)
+
+
+def lfsgm_sync(h):
+    _check(load().lfsgm_sync(h), h)
+
+
+def lfsgm_last_error(h) -> str:
+    return (load().lfsgm_last_error(h) or b"").decode()
+
+
+def lfsgm_launch_count(h) -> int:
+    return int(load().lfsgm_launch_count(h))
+
+
+def lfsgm_set_profiling(h, enable: bool):
+    _check(load().lfsgm_set_profiling(h, 1 if enable else 0), h)
+
+
+def lfsgm_kernel_times(h, cap: int = 4096):
+    names = (C.c_char_p * cap)()
+    ms = (C.c_float * cap)()
+    n = C.c_int32()
+    _check(load().lfsgm_kernel_times(h, names, ms, cap, C.byref(n)), h)
+    return [(names[i].decode(), float(ms[i])) for i in range(n.value)]
+
+
+def lfsgm_depth_host(h, views_host, disp_host, label_host=None):
+    _check(load().lfsgm_depth_host(h, _hptr(views_host, "views_host"), _hptr(disp_host, "disp_host"),
+                                   None if label_host is None else _hptr(label_host, "label_host")), h)
+
+
+def lfsgm_depth(h, views, disp=None, label=None):
+    import torch
+    _check(load().lfsgm_depth(h, _ptr(views, torch.float32, "views"), _ptr(disp, torch.float32, "disp"),
+                              _ptr(label, torch.int32, "label")), h)
+
+
+# ------------------------------------------------------------------ convenience wrapper
+class LightFieldDepth:
+    """Owns a handle and the windowed buffers of one light-field shape and runs the
+    stages in the paper's order.  Buffers are torch CUDA tensors."""
+
+    def __init__(self, params, stream=None, device="cuda"):
+        import torch
+        self.params = params
+        self.device = torch.device(device)
+        self.stream = stream or torch.cuda.current_stream(self.device)
+        self.h = lfsgm_create(params, self.stream)
+        N = params.H * params.W
+        self.N = N
+        self.max_nnz = lfsgm_max_nnz(self.h)
+        i32, i64, f32 = torch.int32, torch.int64, torch.float32
+        self.lo = torch.empty(N, dtype=i32, device=self.device)
+        self.cnt = torch.empty(N, dtype=i32, device=self.device)
+        self.off = torch.empty(N + 1, dtype=i64, device=self.device)
+        self.dinit = torch.empty(N, dtype=f32, device=self.device)
+        self.maps = torch.empty(4, N, dtype=i32, device=self.device)
+        self.cost = torch.empty(self.max_nnz, dtype=f32, device=self.device)
+        self.agg = torch.empty(self.max_nnz, dtype=f32, device=self.device)
+        self.label = torch.empty(N, dtype=i32, device=self.device)
+        self.disp = torch.empty(N, dtype=f32, device=self.device)
+
+    def initial(self, views, Pc1=0, Pc2=0, want_nnz=False):
+        return lfsgm_initial_disparity(self.h, views, Pc1, Pc2, self.lo, self.cnt, self.off, self.dinit,
+                                       self.maps, want_nnz)
+
+    def cost_volume(self, views):
+        lfsgm_cost_volume(self.h, views, self.lo, self.cnt, self.off, self.cost)
+
+    def aggregate(self, P1=-1.0, P2=-1.0):
+        lfsgm_sgm_aggregate(self.h, self.cost, self.lo, self.cnt, self.off, P1, P2, self.agg)
+
+    def wta(self):
+        lfsgm_wta_subpixel(self.h, self.agg, self.lo, self.cnt, self.off, self.label, self.disp)
+
+    def forward(self, views, Pc=(0, 0), P=(-1.0, -1.0)):
+        self.initial(views, *Pc)
+        self.cost_volume(views)
+        self.aggregate(*P)
+        self.wta()
+        return self.disp
+
+    def close(self):
+        if self.h is not None:
+            lfsgm_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,64 @@
+// k_census.cu -- Census transform (Sec. III-B, Eq. 2-3) of selected views.
+//
+// Bit k of the word of pixel (x,y) is 1 iff I(x,y) > I(x+dx,y+dy) for the k-th offset of
+// the w x w window without its centre, offsets row-major (dy outer, dx inner), bit 0
+// first; neighbour coordinates are clamped to the image.  One 32x8 CTA per tile and
+// view; the tile plus its halo is staged in shared memory with clamped loads, so every
+// neighbour read is a shared-memory read.  Output: one 64-bit word per pixel per view,
+// census[view][y][x] (24 bits for 5x5, 48 bits for 7x7).
+#include "lfsgm_internal.cuh"
+
+namespace lfsgm {
+namespace {
+
+constexpr int TX = 32, TY = 8;
+
+template <int HALF>
+__global__ void __launch_bounds__(TX *TY) census_kernel(const float *__restrict__ views, int H, int W,
+                                                        const int *__restrict__ sel,
+                                                        uint64_t *__restrict__ cen) {
+    constexpr int SW = TX + 2 * HALF, SH = TY + 2 * HALF;
+    __shared__ float tile[SH][SW + 1];
+    const size_t HW = (size_t)H * W;
+    const int view = sel[blockIdx.z];
+    const float *img = views + (size_t)view * HW;
+    const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
+    const int tid = threadIdx.y * TX + threadIdx.x;
+    for (int i = tid; i < SH * SW; i += TX * TY) {
+        int ty = i / SW, tx = i - ty * SW;
+        int gy = min(max(y0 + ty - HALF, 0), H - 1);
+        int gx = min(max(x0 + tx - HALF, 0), W - 1);
+        tile[ty][tx] = __ldg(img + (size_t)gy * W + gx);
+    }
+    __syncthreads();
+    const int x = x0 + threadIdx.x, y = y0 + threadIdx.y;
+    if (x >= W || y >= H) return;
+    const float c = tile[threadIdx.y + HALF][threadIdx.x + HALF];
+    uint32_t lo = 0, hi = 0;
+    int bit = 0;
+#pragma unroll
+    for (int dy = -HALF; dy <= HALF; dy++) {
+#pragma unroll
+        for (int dx = -HALF; dx <= HALF; dx++) {
+            if (dx == 0 && dy == 0) continue;
+            const float nb = tile[threadIdx.y + HALF + dy][threadIdx.x + HALF + dx];
+            const uint32_t b = c > nb ? 1u : 0u;
+            if (bit < 32) lo |= b << bit;
+            else hi |= b << (bit - 32);
+            bit++;
+        }
+    }
+    cen[(size_t)view * HW + (size_t)y * W + x] = ((uint64_t)hi << 32) | lo;
+}
+
+}  // namespace
+
+cudaError_t launch_census(cudaStream_t s, const float *views, int H, int W, int census_w,
+                          const int *d_sel, int nsel, uint64_t *cen) {
+    dim3 block(TX, TY), grid((W + TX - 1) / TX, (H + TY - 1) / TY, nsel);
+    if (census_w == 5) census_kernel<2><<<grid, block, 0, s>>>(views, H, W, d_sel, cen);
+    else census_kernel<3><<<grid, block, 0, s>>>(views, H, W, d_sel, cen);
+    return cudaGetLastError();
+}
+
+}  // namespace lfsgm

@@ -1,0 +1,64 @@
+// k_wta.cu -- winner-takes-all (Eq. 10) and sub-pixel refinement (Sec. III-F, Eq. 13).
+//
+// One thread per pixel walks its window: the smallest aggregated cost wins, the lowest
+// label on ties.  Mode 1 adds the vertex of the parabola through the winner and its two
+// neighbours, delta = (C(g-1) - C(g+1)) / (2 (C(g-1) - 2 C(g) + C(g+1))), when the winner
+// lies in [lo+1, lo+cnt-2] and that interval holds at least 3 labels (cnt >= 5); Eq. 13
+// prints the denominator with the opposite sign, which would move away from the lower
+// neighbour.  Mode 2 is the soft-argmin sum_g softmax(-C/tau)_g d_g.
+#include "lfsgm_internal.cuh"
+
+namespace lfsgm {
+namespace {
+
+__global__ void wta_kernel(const float *__restrict__ agg, const int *__restrict__ lo,
+                           const int *__restrict__ cnt, const long long *__restrict__ off, int N, int G,
+                           double dmin, double step, int mode, float tau, int *__restrict__ label,
+                           float *__restrict__ disp, int *__restrict__ status) {
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= N) return;
+    const float *s = agg + off[p];
+    const int n = cnt[p], l = lo[p];
+    if (!window_ok(l, n, G, off[p + 1] - off[p], status)) {
+        if (label) label[p] = -1;
+        if (disp) disp[p] = __int_as_float(0x7fc00000);
+        return;
+    }
+    int b = 0;
+    float bv = s[0];
+    for (int j = 1; j < n; j++) {
+        const float v = s[j];
+        if (v < bv) { bv = v; b = j; }
+    }
+    if (label) label[p] = l + b;
+    if (!disp) return;
+    if (mode == 2) {
+        double num = 0.0, den = 0.0;
+        for (int j = 0; j < n; j++) {
+            const double w = exp(-((double)s[j] - (double)bv) / (double)tau);
+            num += w * (dmin + (double)(l + j) * step);
+            den += w;
+        }
+        disp[p] = (float)(num / den);
+        return;
+    }
+    double delta = 0.0;
+    if (mode == 1 && n >= 5 && b >= 1 && b <= n - 2) {
+        const float cm = s[b - 1], cp = s[b + 1];
+        const float den = (cm - bv) + (cp - bv);
+        if (den > 0.f) delta = (double)((cm - cp) / (2.f * den));
+    }
+    disp[p] = (float)(dmin + ((double)(l + b) + delta) * step);
+}
+
+}  // namespace
+
+cudaError_t launch_wta(cudaStream_t s, const float *agg, const int *lo, const int *cnt, const long long *off,
+                       int N, int G, double dmin, double step, int mode, float tau, int *label, float *disp,
+                       int *status) {
+    wta_kernel<<<(N + 255) / 256, 256, 0, s>>>(agg, lo, cnt, off, N, G, dmin, step, mode, tau, label, disp,
+                                               status);
+    return cudaGetLastError();
+}
+
+}  // namespace lfsgm

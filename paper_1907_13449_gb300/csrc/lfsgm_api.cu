@@ -1,0 +1,595 @@
+// lfsgm_api.cu -- the C ABI declared in include/lfsgm.h: handle, configuration checks,
+// host-built shift tables, workspace, launch accounting and the stage entry points.
+//
+// Host arithmetic that decides integers (shift tables, label grids) is done in double
+// precision with FMA contraction disabled (-ffp-contract=off), so the tables are the same
+// on x86 and Arm hosts.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/lfsgm.h"
+#include "lfsgm_internal.cuh"
+
+using namespace lfsgm;
+
+namespace {
+
+struct ProfRec {
+    const char *name;
+    cudaEvent_t a, b;
+};
+
+size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+// ---- shift split of a*d (see lfsgm.h): snap 2s to an integer within 2e-9, then floor / round-half-up
+void shift_split(int a, double d, int &o, double &f, int &n) {
+    double s = (double)a * d;
+    const double t = 2.0 * s;
+    const double r = std::nearbyint(t);
+    if (std::fabs(t - r) <= 2e-9) s = 0.5 * r;
+    const double fl = std::floor(s);
+    o = (int)fl;
+    f = s - fl;
+    n = (int)std::floor(s + 0.5);
+}
+
+double grid_disp(double dmin, double dmax, int L, int k) {
+    const double step = (dmax - dmin) / (double)(L - 1);
+    return dmin + (double)k * step;
+}
+
+}  // namespace
+
+struct lfsgm_ctx {
+    lfsgm_config cfg{};
+    cudaStream_t stream = nullptr;
+    int N = 0, nviews = 0, ref = 0, nbits = 0, Lcs = 0;
+    ArmList arms{};
+    // device tables
+    FineTap *d_fine = nullptr;
+    short2 *d_coarse = nullptr;
+    int *d_armviews = nullptr;   // [4][kMaxArmViews]
+    int *d_sel_cross = nullptr;  // reference + arm views
+    int n_sel_cross = 0;
+    int *d_sel_all = nullptr;    // every view
+    // workspace
+    void *ws = nullptr;
+    size_t ws_bytes = 0;
+    bool ws_owned = false;
+    uint64_t *cen = nullptr;
+    uint16_t *ccost = nullptr;
+    uint32_t *csum = nullptr;
+    int *maps = nullptr, *F0 = nullptr, *F1 = nullptr, *cntpad = nullptr;
+    unsigned long long *armsum = nullptr;
+    int *cpen = nullptr;
+    float *fpen = nullptr;
+    double *partial = nullptr;
+    int *status = nullptr;
+    // buffers of the whole-method entry points (owned, allocated on first use)
+    int *o_lo = nullptr, *o_cnt = nullptr, *o_label = nullptr;
+    long long *o_off = nullptr;
+    float *o_cost = nullptr, *o_agg = nullptr, *o_disp = nullptr, *o_views = nullptr;
+    // accounting
+    long long launches = 0;
+    bool profiling = false;
+    std::vector<ProfRec> prof;
+    std::vector<cudaEvent_t> pool;
+    std::string err;
+};
+
+namespace {
+
+thread_local std::string g_create_err;  // error text of a failed lfsgm_create
+
+lfsgm_status fail(lfsgm_ctx *h, lfsgm_status st, const char *fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    if (h) h->err = buf;
+    return st;
+}
+
+lfsgm_status cuda_fail(lfsgm_ctx *h, cudaError_t e, const char *what) {
+    return fail(h, LFSGM_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+cudaEvent_t get_event(lfsgm_ctx *h) {
+    if (!h->pool.empty()) {
+        cudaEvent_t e = h->pool.back();
+        h->pool.pop_back();
+        return e;
+    }
+    cudaEvent_t e = nullptr;
+    cudaEventCreate(&e);
+    return e;
+}
+
+// Run one launcher: count it and, when profiling, bracket it with events.
+template <class F>
+lfsgm_status run(lfsgm_ctx *h, const char *name, F &&launch) {
+    ProfRec rec{name, nullptr, nullptr};
+    if (h->profiling) {
+        rec.a = get_event(h);
+        rec.b = get_event(h);
+        cudaEventRecord(rec.a, h->stream);
+    }
+    const cudaError_t e = launch();
+    if (e != cudaSuccess) return cuda_fail(h, e, name);
+    h->launches++;
+    if (h->profiling) {
+        cudaEventRecord(rec.b, h->stream);
+        h->prof.push_back(rec);
+    }
+    return LFSGM_OK;
+}
+
+#define LFSGM_TRY(x)                          \
+    do {                                      \
+        const lfsgm_status _st = (x);         \
+        if (_st != LFSGM_OK) return _st;      \
+    } while (0)
+
+lfsgm_status validate(const lfsgm_config &c, char *why, size_t n) {
+#define BAD(...) do { snprintf(why, n, __VA_ARGS__); return LFSGM_ERR_INVALID_ARG; } while (0)
+    if (c.U < 1 || c.V < 1 || c.U * c.V < 2) BAD("need at least 2 views (U=%d V=%d)", c.U, c.V);
+    if (c.U > 64 || c.V > 64) BAD("at most 64 x 64 views");
+    if (c.H < 1 || c.W < 1 || (long long)c.H * c.W > (1LL << 28)) BAD("bad image size %dx%d", c.H, c.W);
+    if (c.uc < 0 || c.uc >= c.U || c.vc < 0 || c.vc >= c.V) BAD("reference view out of range");
+    if (c.census_w != 5 && c.census_w != 7) BAD("census_w must be 5 or 7");
+    if (!(c.dmax > c.dmin) || !std::isfinite(c.dmin) || !std::isfinite(c.dmax)) BAD("need dmin < dmax");
+    if (c.coarse_labels < 2 || c.coarse_labels > 256) BAD("coarse_labels must be in [2, 256]");
+    if (c.fine_labels < 2 || c.fine_labels > 4096) BAD("fine_labels must be in [2, 4096]");
+    if (c.fine_radius < 0) BAD("fine_radius must be >= 0");
+    if (!(c.phi > 0.0)) BAD("phi must be > 0");
+    if (c.fill_passes < 0 || c.fill_passes > 8) BAD("fill_passes must be in [0, 8]");
+    if (!(c.w_l2 >= 0.f) || !(c.w_census >= 0.f) || !std::isfinite(c.w_l2) || !std::isfinite(c.w_census))
+        BAD("cost weights must be finite and >= 0");
+    if (!(c.p1_frac >= 0.0) || !(c.p2_frac >= c.p1_frac)) BAD("need 0 <= p1_frac <= p2_frac");
+    if (c.subpixel < 0 || c.subpixel > 2) BAD("subpixel must be 0, 1 or 2");
+    if (!(c.softmin_tau > 0.f)) BAD("softmin_tau must be > 0");
+    const double md = std::fmax(std::fabs(c.dmin), std::fabs(c.dmax));
+    if (md * (std::max(c.U, c.V)) > 30000.0) BAD("shifts exceed the 16-bit table range");
+    return LFSGM_OK;
+#undef BAD
+}
+
+void build_arms(lfsgm_ctx *h) {
+    const lfsgm_config &c = h->cfg;
+    ArmList &A = h->arms;
+    A.n_arms = 0;
+    for (int arm = 0; arm < 4; arm++) {
+        int n = 0;
+        int *out = A.views[A.n_arms];
+        auto add = [&](int u, int v) { out[n++] = v * c.U + u; };
+        if (arm == 0) {
+            for (int v = c.vc - 1; v >= 0; v--) if (c.init_views || v == 0) add(c.uc, v);
+        } else if (arm == 1) {
+            for (int v = c.vc + 1; v < c.V; v++) if (c.init_views || v == c.V - 1) add(c.uc, v);
+        } else if (arm == 2) {
+            for (int u = c.uc - 1; u >= 0; u--) if (c.init_views || u == 0) add(u, c.vc);
+        } else {
+            for (int u = c.uc + 1; u < c.U; u++) if (c.init_views || u == c.U - 1) add(u, c.vc);
+        }
+        if (n > 0) {
+            A.arm_id[A.n_arms] = arm;
+            A.nv[A.n_arms] = n;
+            A.n_arms++;
+        }
+    }
+}
+
+lfsgm_status bind_workspace(lfsgm_ctx *h, void *dptr, size_t bytes, bool owned);
+
+lfsgm_status ensure_workspace(lfsgm_ctx *h) {
+    if (h->ws) return LFSGM_OK;
+    size_t bytes = 0;
+    lfsgm_workspace_size(h, &bytes);
+    void *p = nullptr;
+    const cudaError_t e = cudaMalloc(&p, bytes);
+    if (e != cudaSuccess) return fail(h, LFSGM_ERR_NO_MEMORY, "workspace of %zu bytes: %s", bytes, cudaGetErrorString(e));
+    return bind_workspace(h, p, bytes, true);
+}
+
+int max_arm_views(const lfsgm_ctx *h) {
+    int m = 0;
+    for (int a = 0; a < h->arms.n_arms; a++) m = std::max(m, h->arms.nv[a]);
+    return m;
+}
+
+}  // namespace
+
+
+namespace {
+lfsgm_status bind_workspace(lfsgm_ctx *h, void *dptr, size_t bytes, bool owned) {
+    size_t need = 0;
+    lfsgm_workspace_size(h, &need);
+    if (bytes < need || ((uintptr_t)dptr & 255))
+        return fail(h, LFSGM_ERR_WORKSPACE, "workspace needs %zu bytes, 256-byte aligned", need);
+    if (h->ws && h->ws_owned && h->ws != dptr) cudaFree(h->ws);
+    h->ws = dptr;
+    h->ws_bytes = bytes;
+    h->ws_owned = owned;
+    const size_t N = (size_t)h->N, A = (size_t)std::max(h->arms.n_arms, 1);
+    char *p = (char *)dptr;
+    auto take = [&](size_t n) { char *q = p; p += align256(n); return (void *)q; };
+    h->cen = (uint64_t *)take(h->nviews * N * 8);
+    h->ccost = (uint16_t *)take(A * N * h->Lcs * 2);
+    h->csum = (uint32_t *)take(A * N * (h->Lcs / 2) * 4);
+    h->maps = (int *)take(4 * N * 4);
+    h->F0 = (int *)take(N * 4);
+    h->F1 = (int *)take(N * 4);
+    h->cntpad = (int *)take(N * 4);
+    h->armsum = (unsigned long long *)take(4 * 8);
+    h->cpen = (int *)take(8 * 4);
+    h->fpen = (float *)take(2 * 4);
+    h->partial = (double *)take(kPartialBlocks * 8);
+    h->status = (int *)take(4);
+    const cudaError_t e = cudaMemsetAsync(h->status, 0, 4, h->stream);
+    if (e != cudaSuccess) return cuda_fail(h, e, "status clear");
+    return LFSGM_OK;
+}
+}  // namespace
+
+extern "C" {
+
+lfsgm_status lfsgm_create(const lfsgm_config *cfg, void *stream, lfsgm_handle *out) {
+    if (!cfg || !out) return LFSGM_ERR_INVALID_ARG;
+    *out = nullptr;
+    lfsgm_config c = *cfg;
+    if (c.uc < 0) c.uc = (c.U - 1) / 2;
+    if (c.vc < 0) c.vc = (c.V - 1) / 2;
+    char why[256];
+    if (validate(c, why, sizeof why) != LFSGM_OK) {
+        g_create_err = why;
+        return LFSGM_ERR_INVALID_ARG;
+    }
+    lfsgm_ctx *h = new lfsgm_ctx();
+    h->cfg = c;
+    h->stream = (cudaStream_t)stream;
+    h->N = c.H * c.W;
+    h->nviews = c.U * c.V;
+    h->ref = c.vc * c.U + c.uc;
+    h->nbits = c.census_w * c.census_w - 1;
+    h->Lcs = c.coarse_labels <= 64 ? 64 : (c.coarse_labels <= 128 ? 128 : 256);
+    build_arms(h);
+    // the packed coarse sums hold 8 paths x (C + P2) per 16-bit half
+    const long long cmax = (long long)max_arm_views(h) * h->nbits;
+    const long long p2max = (long long)std::floor(c.p2_frac * (double)cmax + 0.5);
+    if (8 * (cmax + std::max(p2max, 1LL)) >= 65536) {
+        g_create_err = "coarse path sums would overflow 16 bits (too many arm views x census bits)";
+        delete h;
+        return LFSGM_ERR_UNSUPPORTED;
+    }
+    // shift tables in double precision
+    std::vector<FineTap> fine((size_t)h->nviews * c.fine_labels);
+    std::vector<short2> coarse((size_t)h->nviews * c.coarse_labels);
+    for (int v = 0; v < c.V; v++)
+        for (int u = 0; u < c.U; u++) {
+            const int view = v * c.U + u;
+            for (int g = 0; g < c.fine_labels; g++) {
+                const double d = grid_disp(c.dmin, c.dmax, c.fine_labels, g);
+                int ox, oy, nx, ny;
+                double fx, fy;
+                shift_split(u - c.uc, d, ox, fx, nx);
+                shift_split(v - c.vc, d, oy, fy, ny);
+                FineTap t;
+                t.ox = (int16_t)ox; t.oy = (int16_t)oy; t.nx = (int16_t)nx; t.ny = (int16_t)ny;
+                t.fx = (float)fx; t.fy = (float)fy;
+                fine[(size_t)view * c.fine_labels + g] = t;
+            }
+            for (int k = 0; k < c.coarse_labels; k++) {
+                const double d = grid_disp(c.dmin, c.dmax, c.coarse_labels, k);
+                int ox, oy, nx, ny;
+                double fx, fy;
+                shift_split(u - c.uc, d, ox, fx, nx);
+                shift_split(v - c.vc, d, oy, fy, ny);
+                coarse[(size_t)view * c.coarse_labels + k] = make_short2((short)nx, (short)ny);
+            }
+        }
+    std::vector<int> armviews(4 * kMaxArmViews, 0), sel_cross, sel_all;
+    sel_cross.push_back(h->ref);
+    for (int a = 0; a < h->arms.n_arms; a++)
+        for (int i = 0; i < h->arms.nv[a]; i++) {
+            armviews[a * kMaxArmViews + i] = h->arms.views[a][i];
+            sel_cross.push_back(h->arms.views[a][i]);
+        }
+    for (int i = 0; i < h->nviews; i++) sel_all.push_back(i);
+    h->n_sel_cross = (int)sel_cross.size();
+    cudaError_t e;
+#define ALLOC_COPY(dst, vec)                                                                  \
+    e = cudaMalloc((void **)&dst, vec.size() * sizeof(vec[0]));                              \
+    if (e == cudaSuccess) e = cudaMemcpy(dst, vec.data(), vec.size() * sizeof(vec[0]), cudaMemcpyHostToDevice); \
+    if (e != cudaSuccess) { g_create_err = cudaGetErrorString(e); lfsgm_destroy(h); return LFSGM_ERR_CUDA; }
+    ALLOC_COPY(h->d_fine, fine);
+    ALLOC_COPY(h->d_coarse, coarse);
+    ALLOC_COPY(h->d_armviews, armviews);
+    ALLOC_COPY(h->d_sel_cross, sel_cross);
+    ALLOC_COPY(h->d_sel_all, sel_all);
+#undef ALLOC_COPY
+    *out = h;
+    return LFSGM_OK;
+}
+
+lfsgm_status lfsgm_destroy(lfsgm_handle h) {
+    if (!h) return LFSGM_ERR_INVALID_ARG;
+    if (h->stream) cudaStreamSynchronize(h->stream);
+    else cudaDeviceSynchronize();
+    cudaFree(h->d_fine);
+    cudaFree(h->d_coarse);
+    cudaFree(h->d_armviews);
+    cudaFree(h->d_sel_cross);
+    cudaFree(h->d_sel_all);
+    if (h->ws_owned) cudaFree(h->ws);
+    cudaFree(h->o_lo); cudaFree(h->o_cnt); cudaFree(h->o_label); cudaFree(h->o_off);
+    cudaFree(h->o_cost); cudaFree(h->o_agg); cudaFree(h->o_disp); cudaFree(h->o_views);
+    for (auto &r : h->prof) { cudaEventDestroy(r.a); cudaEventDestroy(r.b); }
+    for (auto e : h->pool) cudaEventDestroy(e);
+    delete h;
+    return LFSGM_OK;
+}
+
+lfsgm_status lfsgm_workspace_size(lfsgm_handle h, size_t *bytes) {
+    if (!h || !bytes) return LFSGM_ERR_INVALID_ARG;
+    const size_t N = (size_t)h->N, A = (size_t)std::max(h->arms.n_arms, 1);
+    size_t b = 0;
+    b += align256(h->nviews * N * 8);              // census words
+    b += align256(A * N * h->Lcs * 2);              // coarse cost
+    b += align256(A * N * (h->Lcs / 2) * 4);        // packed coarse sums
+    b += align256(4 * N * 4);                       // maps
+    b += 3 * align256(N * 4);                       // F0, F1, padded counts
+    b += align256(4 * 8) + align256(8 * 4) + align256(2 * 4);
+    b += align256(kPartialBlocks * 8) + align256(4);
+    *bytes = b;
+    return LFSGM_OK;
+}
+
+lfsgm_status lfsgm_set_workspace(lfsgm_handle h, void *dptr, size_t bytes) {
+    if (!h || !dptr) return LFSGM_ERR_INVALID_ARG;
+    return bind_workspace(h, dptr, bytes, false);
+}
+
+lfsgm_status lfsgm_max_nnz(lfsgm_handle h, int64_t *nnz) {
+    if (!h || !nnz) return LFSGM_ERR_INVALID_ARG;
+    *nnz = (int64_t)h->N * ((h->cfg.fine_labels + 3) & ~3);
+    return LFSGM_OK;
+}
+
+lfsgm_status lfsgm_initial_disparity(lfsgm_handle h, const float *views, int32_t Pc1, int32_t Pc2, int32_t *lo,
+                                     int32_t *cnt, int64_t *off, float *dinit, int32_t *maps,
+                                     int64_t *nnz_host) {
+    if (!h) return LFSGM_ERR_INVALID_ARG;
+    if (!views || !lo || !cnt || !off) return fail(h, LFSGM_ERR_INVALID_ARG, "null buffer");
+    if (Pc1 > 0 && Pc2 < Pc1) return fail(h, LFSGM_ERR_INVALID_ARG, "need P2 >= P1 (Eq. 8)");
+    if (Pc1 > 0 && 8LL * ((long long)max_arm_views(h) * h->nbits + Pc2) >= 65536)
+        return fail(h, LFSGM_ERR_UNSUPPORTED, "coarse P2 too large for 16-bit path sums");
+    LFSGM_TRY(ensure_workspace(h));
+    const lfsgm_config &c = h->cfg;
+    cudaStream_t s = h->stream;
+    const int N = h->N, A = h->arms.n_arms;
+    LFSGM_TRY(run(h, "census_cross", [&] {
+        return launch_census(s, views, c.H, c.W, c.census_w, h->d_sel_cross, h->n_sel_cross, h->cen);
+    }));
+    cudaError_t e = cudaMemsetAsync(h->armsum, 0, 4 * 8, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(h->csum, 0, (size_t)A * N * (h->Lcs / 2) * 4, s);
+    if (e != cudaSuccess) return cuda_fail(h, e, "memset");
+    for (int a = 0; a < A; a++) {
+        LFSGM_TRY(run(h, "coarse_cost", [&] {
+            return launch_coarse_cost(s, h->cen, c.H, c.W, h->ref, h->d_armviews + a * kMaxArmViews,
+                                      h->arms.nv[a], h->d_coarse, c.coarse_labels, h->Lcs,
+                                      h->ccost + (size_t)a * N * h->Lcs, h->armsum + a);
+        }));
+    }
+    LFSGM_TRY(run(h, "coarse_penalties", [&] {
+        return launch_coarse_penalties(s, h->armsum, A, (long long)N * c.coarse_labels, c.p1_frac, c.p2_frac,
+                                       Pc1, Pc2, h->cpen);
+    }));
+    LFSGM_TRY(run(h, "coarse_sgm", [&] {
+        return launch_coarse_sgm(s, h->ccost, A, c.H, c.W, c.coarse_labels, h->Lcs, h->cpen, h->csum);
+    }));
+    LFSGM_TRY(run(h, "coarse_wta", [&] {
+        return launch_coarse_wta(s, h->csum, A, N, c.coarse_labels, h->Lcs, h->maps, maps);
+    }));
+    LFSGM_TRY(run(h, "fuse", [&] { return launch_fuse(s, h->maps, A, N, c.phi, h->F0); }));
+    int *fin = h->F0, *fout = h->F1;
+    for (int it = 0; it < c.fill_passes; it++) {
+        LFSGM_TRY(run(h, "hole_fill", [&] { return launch_fill(s, fin, fout, c.H, c.W); }));
+        std::swap(fin, fout);
+    }
+    LFSGM_TRY(run(h, "windows", [&] {
+        return launch_windows(s, fin, N, c.fine_labels, c.coarse_labels, c.fine_radius, lo, cnt, dinit, h->cntpad);
+    }));
+    LFSGM_TRY(run(h, "scan", [&] { return launch_scan(s, h->cntpad, N, (long long *)off); }));
+    if (nnz_host) {
+        e = cudaMemcpyAsync(nnz_host, off + N, sizeof(int64_t), cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess) return cuda_fail(h, e, "nnz readback");
+    }
+    return LFSGM_OK;
+}
+
+lfsgm_status lfsgm_cost_volume(lfsgm_handle h, const float *views, const int32_t *lo, const int32_t *cnt,
+                               const int64_t *off, float *cost) {
+    if (!h) return LFSGM_ERR_INVALID_ARG;
+    if (!views || !lo || !cnt || !off || !cost) return fail(h, LFSGM_ERR_INVALID_ARG, "null buffer");
+    LFSGM_TRY(ensure_workspace(h));
+    const lfsgm_config &c = h->cfg;
+    cudaStream_t s = h->stream;
+    LFSGM_TRY(run(h, "census_all", [&] {
+        return launch_census(s, views, c.H, c.W, c.census_w, h->d_sel_all, h->nviews, h->cen);
+    }));
+    LFSGM_TRY(run(h, "fine_cost", [&] {
+        return launch_fine_cost(s, views, h->cen, h->d_fine, c.fine_labels, h->nviews, c.H, c.W, h->ref, lo, cnt,
+                                (const long long *)off, c.w_l2, c.w_census, cost, h->status);
+    }));
+    return LFSGM_OK;
+}
+
+}  // extern "C"
+
+namespace {
+__global__ void zero_csr_kernel(float *a, const long long *off, int N) {
+    const long long n = off[N];
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        a[i] = 0.f;
+}
+__global__ void set_pen_kernel(float *pen, float P1, float P2) {
+    pen[0] = P1;
+    pen[1] = P2;
+}
+}  // namespace
+
+extern "C" {
+
+lfsgm_status lfsgm_sgm_aggregate(lfsgm_handle h, const float *cost, const int32_t *lo, const int32_t *cnt,
+                                 const int64_t *off, float P1, float P2, float *agg) {
+    if (!h) return LFSGM_ERR_INVALID_ARG;
+    if (!cost || !lo || !cnt || !off || !agg) return fail(h, LFSGM_ERR_INVALID_ARG, "null buffer");
+    const bool derived = P1 < 0.f;
+    if (!derived && !(P1 >= 0.f && P2 >= P1 && std::isfinite(P2)))
+        return fail(h, LFSGM_ERR_INVALID_ARG, "need 0 <= P1 <= P2 (Eq. 8), got %g %g", P1, P2);
+    LFSGM_TRY(ensure_workspace(h));
+    const lfsgm_config &c = h->cfg;
+    cudaStream_t s = h->stream;
+    const long long *o = (const long long *)off;
+    if (derived) {
+        LFSGM_TRY(run(h, "cost_partial_sums", [&] {
+            return launch_cost_partial_sums(s, cost, cnt, o, h->N, c.fine_labels, h->partial, kPartialBlocks,
+                                            h->status);
+        }));
+        LFSGM_TRY(run(h, "fine_penalties", [&] {
+            return launch_fine_penalties(s, h->partial, kPartialBlocks, cnt, h->N, c.p1_frac, c.p2_frac, h->fpen);
+        }));
+    } else {
+        LFSGM_TRY(run(h, "set_penalties", [&] {
+            set_pen_kernel<<<1, 1, 0, s>>>(h->fpen, P1, P2);
+            return cudaGetLastError();
+        }));
+    }
+    LFSGM_TRY(run(h, "zero_agg", [&] {
+        zero_csr_kernel<<<1216, 256, 0, s>>>(agg, o, h->N);
+        return cudaGetLastError();
+    }));
+    LFSGM_TRY(run(h, "fine_sgm", [&] {
+        return launch_fine_sgm(s, cost, lo, cnt, o, c.H, c.W, c.fine_labels, h->fpen, agg, h->status);
+    }));
+    return LFSGM_OK;
+}
+
+lfsgm_status lfsgm_wta_subpixel(lfsgm_handle h, const float *agg, const int32_t *lo, const int32_t *cnt,
+                                const int64_t *off, int32_t *label, float *disp) {
+    if (!h) return LFSGM_ERR_INVALID_ARG;
+    if (!agg || !lo || !cnt || !off || (!label && !disp)) return fail(h, LFSGM_ERR_INVALID_ARG, "null buffer");
+    LFSGM_TRY(ensure_workspace(h));
+    const lfsgm_config &c = h->cfg;
+    const double step = (c.dmax - c.dmin) / (double)(c.fine_labels - 1);
+    return run(h, "wta_subpixel", [&] {
+        return launch_wta(h->stream, agg, lo, cnt, (const long long *)off, h->N, c.fine_labels, c.dmin, step,
+                          c.subpixel, c.softmin_tau, label, disp, h->status);
+    });
+}
+
+lfsgm_status lfsgm_backward(lfsgm_handle h, const float *, const float *, const int32_t *, const int32_t *,
+                            const int64_t *, float, float, const float *, float *, float *, float *, float *) {
+    if (!h) return LFSGM_ERR_INVALID_ARG;
+    return fail(h, LFSGM_ERR_UNSUPPORTED, "backward not built yet");
+}
+
+lfsgm_status lfsgm_sync(lfsgm_handle h) {
+    if (!h) return LFSGM_ERR_INVALID_ARG;
+    cudaError_t e = h->stream ? cudaStreamSynchronize(h->stream) : cudaDeviceSynchronize();
+    if (e != cudaSuccess) return cuda_fail(h, e, "sync");
+    if (!h->status) return LFSGM_OK;
+    int st = 0;
+    e = cudaMemcpy(&st, h->status, 4, cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_fail(h, e, "status readback");
+    if (st != 0) {
+        cudaMemset(h->status, 0, 4);
+        return fail(h, (lfsgm_status)st, "device-side status %d", st);
+    }
+    return LFSGM_OK;
+}
+
+const char *lfsgm_last_error(lfsgm_handle h) { return h ? h->err.c_str() : g_create_err.c_str(); }
+
+int64_t lfsgm_launch_count(lfsgm_handle h) { return h ? h->launches : -1; }
+
+lfsgm_status lfsgm_set_profiling(lfsgm_handle h, int32_t enable) {
+    if (!h) return LFSGM_ERR_INVALID_ARG;
+    h->profiling = enable != 0;
+    return LFSGM_OK;
+}
+
+lfsgm_status lfsgm_kernel_times(lfsgm_handle h, const char **names, float *ms, int32_t cap, int32_t *n_out) {
+    if (!h) return LFSGM_ERR_INVALID_ARG;
+    cudaError_t e = h->stream ? cudaStreamSynchronize(h->stream) : cudaDeviceSynchronize();
+    if (e != cudaSuccess) return cuda_fail(h, e, "sync");
+    int n = 0;
+    for (auto &r : h->prof) {
+        if (n < cap) {
+            float t = 0.f;
+            cudaEventElapsedTime(&t, r.a, r.b);
+            if (names) names[n] = r.name;
+            if (ms) ms[n] = t;
+            n++;
+        }
+        h->pool.push_back(r.a);
+        h->pool.push_back(r.b);
+    }
+    h->prof.clear();
+    if (n_out) *n_out = n;
+    return LFSGM_OK;
+}
+
+lfsgm_status lfsgm_depth(lfsgm_handle h, const float *views, float *disp, int32_t *label) {
+    if (!h) return LFSGM_ERR_INVALID_ARG;
+    if (!views) return fail(h, LFSGM_ERR_INVALID_ARG, "null views");
+    const size_t N = (size_t)h->N;
+    int64_t maxnnz = 0;
+    lfsgm_max_nnz(h, &maxnnz);
+    if (!h->o_lo) {
+        cudaError_t e = cudaMalloc((void **)&h->o_lo, N * 4);
+        if (e == cudaSuccess) e = cudaMalloc((void **)&h->o_cnt, N * 4);
+        if (e == cudaSuccess) e = cudaMalloc((void **)&h->o_label, N * 4);
+        if (e == cudaSuccess) e = cudaMalloc((void **)&h->o_disp, N * 4);
+        if (e == cudaSuccess) e = cudaMalloc((void **)&h->o_off, (N + 1) * 8);
+        if (e == cudaSuccess) e = cudaMalloc((void **)&h->o_cost, (size_t)maxnnz * 4);
+        if (e == cudaSuccess) e = cudaMalloc((void **)&h->o_agg, (size_t)maxnnz * 4);
+        if (e != cudaSuccess) return fail(h, LFSGM_ERR_NO_MEMORY, "depth buffers: %s", cudaGetErrorString(e));
+    }
+    int64_t *off = (int64_t *)h->o_off;
+    LFSGM_TRY(lfsgm_initial_disparity(h, views, 0, 0, h->o_lo, h->o_cnt, off, nullptr, nullptr, nullptr));
+    LFSGM_TRY(lfsgm_cost_volume(h, views, h->o_lo, h->o_cnt, off, h->o_cost));
+    LFSGM_TRY(lfsgm_sgm_aggregate(h, h->o_cost, h->o_lo, h->o_cnt, off, -1.f, -1.f, h->o_agg));
+    return lfsgm_wta_subpixel(h, h->o_agg, h->o_lo, h->o_cnt, off, label ? label : h->o_label,
+                              disp ? disp : h->o_disp);
+}
+
+lfsgm_status lfsgm_depth_host(lfsgm_handle h, const float *views_host, float *disp_host, int32_t *label_host) {
+    if (!h) return LFSGM_ERR_INVALID_ARG;
+    if (!views_host || !disp_host) return fail(h, LFSGM_ERR_INVALID_ARG, "null host buffer");
+    const size_t N = (size_t)h->N, vbytes = (size_t)h->nviews * N * 4;
+    if (!h->o_views) {
+        const cudaError_t e = cudaMalloc((void **)&h->o_views, vbytes);
+        if (e != cudaSuccess) return fail(h, LFSGM_ERR_NO_MEMORY, "views buffer: %s", cudaGetErrorString(e));
+    }
+    cudaStream_t s = h->stream;
+    cudaError_t e = cudaMemcpyAsync(h->o_views, views_host, vbytes, cudaMemcpyHostToDevice, s);
+    if (e != cudaSuccess) return cuda_fail(h, e, "views upload");
+    LFSGM_TRY(lfsgm_depth(h, h->o_views, nullptr, nullptr));
+    e = cudaMemcpyAsync(disp_host, h->o_disp, N * 4, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess && label_host) e = cudaMemcpyAsync(label_host, h->o_label, N * 4, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return cuda_fail(h, e, "result download");
+    return LFSGM_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,140 @@
+// lfsgm_internal.cuh -- internal declarations shared by the library's kernels and its
+// C-ABI layer.  Not installed, not part of the ABI.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace lfsgm {
+
+// Per (view, fine label) shift split of (u-uc, v-vc) * d_g, built on the host in
+// double precision (see lfsgm.h, "Shift split"); fractions rounded to float once.
+struct FineTap {
+    int16_t ox, oy;   // floor of the x / y shift (bilinear taps)
+    int16_t nx, ny;   // nearest integer x / y shift (census position)
+    float fx, fy;     // fractional parts in [0, 1)
+};
+static_assert(sizeof(FineTap) == 16, "FineTap must be 16 bytes");
+
+#ifdef __CUDACC__
+// A window must satisfy 0 <= lo, 1 <= cnt, lo + cnt <= G and fit its row
+// (off[p+1] - off[p] >= cnt).  Kernels skip a pixel whose window does not and latch
+// LFSGM_ERR_DEVICE_CHECK (7) in the handle's status word.
+__device__ __forceinline__ bool window_ok(int l, int n, int G, long long row, int *status) {
+    const bool ok = l >= 0 && n >= 1 && l + n <= G && (long long)n <= row;
+    if (!ok && status) atomicExch(status, 7);
+    return ok;
+}
+
+// One 16-byte read-only load of a table entry.
+__device__ __forceinline__ FineTap load_tap(const FineTap *t) {
+    const int4 w = __ldg(reinterpret_cast<const int4 *>(t));
+    FineTap r;
+    r.ox = (int16_t)(w.x & 0xffff);
+    r.oy = (int16_t)(w.x >> 16);
+    r.nx = (int16_t)(w.y & 0xffff);
+    r.ny = (int16_t)(w.y >> 16);
+    r.fx = __int_as_float(w.z);
+    r.fy = __int_as_float(w.w);
+    return r;
+}
+#endif
+
+// The 8 SGM directions r = (dx, dy); the predecessor of p is p - r.  Same order as the
+// paper-side description: (1,0) (-1,0) (0,1) (0,-1) (1,1) (-1,-1) (1,-1) (-1,1).
+__host__ __device__ inline int dir_dx(int r) {
+    const int t[8] = {1, -1, 0, 0, 1, -1, 1, -1};
+    return t[r];
+}
+__host__ __device__ inline int dir_dy(int r) {
+    const int t[8] = {0, 0, 1, -1, 1, -1, -1, 1};
+    return t[r];
+}
+// Number of scanlines of direction r (paths start where p - r leaves the image).
+__host__ __device__ inline int n_scanlines(int r, int H, int W) {
+    int dx = dir_dx(r), dy = dir_dy(r);
+    if (dy == 0) return H;
+    if (dx == 0) return W;
+    return W + H - 1;
+}
+// Start pixel of scanline s of direction r.
+__host__ __device__ inline void scan_start(int r, int s, int H, int W, int &x, int &y) {
+    int dx = dir_dx(r), dy = dir_dy(r);
+    if (dy == 0) {
+        y = s;
+        x = dx > 0 ? 0 : W - 1;
+    } else if (dx == 0) {
+        x = s;
+        y = dy > 0 ? 0 : H - 1;
+    } else if (s < W) {
+        x = s;
+        y = dy > 0 ? 0 : H - 1;
+    } else {
+        int i = s - W + 1;
+        y = dy > 0 ? i : H - 1 - i;
+        x = dx > 0 ? 0 : W - 1;
+    }
+}
+
+// Cumulative scanline counts of the 8 directions (plus total) for one image shape.
+struct ScanTable {
+    int cum[9];
+};
+inline ScanTable make_scan_table(int H, int W) {
+    ScanTable t;
+    t.cum[0] = 0;
+    for (int r = 0; r < 8; r++) t.cum[r + 1] = t.cum[r] + n_scanlines(r, H, W);
+    return t;
+}
+
+constexpr int kMaxArmViews = 64;
+
+struct ArmList {
+    int n_arms;               // non-empty arms, in the order up, down, left, right
+    int arm_id[4];            // 0 up, 1 down, 2 left, 3 right
+    int nv[4];                // views per arm
+    int views[4][kMaxArmViews];
+};
+
+// ----------------------------------------------------------------- launchers
+// Each launcher issues exactly one kernel on `s` and returns cudaGetLastError().
+cudaError_t launch_census(cudaStream_t s, const float *views, int H, int W, int census_w,
+                          const int *d_sel, int nsel, uint64_t *cen);
+
+cudaError_t launch_coarse_cost(cudaStream_t s, const uint64_t *cen, int H, int W, int ref,
+                               const int *d_views, int nv, const short2 *ctab, int Lc, int Lcs,
+                               uint16_t *out, unsigned long long *sum);
+cudaError_t launch_coarse_penalties(cudaStream_t s, const unsigned long long *sums, int narms,
+                                    long long count, double p1f, double p2f, int P1, int P2,
+                                    int *pen);
+cudaError_t launch_coarse_sgm(cudaStream_t s, const uint16_t *cost, int narms, int H, int W, int Lc,
+                              int Lcs, const int *pen, uint32_t *sum);
+cudaError_t launch_coarse_wta(cudaStream_t s, const uint32_t *sum, int narms, int N, int Lc, int Lcs,
+                              int *maps, int *maps_out);
+
+cudaError_t launch_fuse(cudaStream_t s, const int *maps, int narms, int N, double phi, int *F);
+cudaError_t launch_fill(cudaStream_t s, const int *Fin, int *Fout, int H, int W);
+cudaError_t launch_windows(cudaStream_t s, const int *F, int N, int G, int Lc, int R, int *lo,
+                           int *cnt, float *dinit, int *cntpad);
+cudaError_t launch_scan(cudaStream_t s, const int *cntpad, int N, long long *off);
+
+cudaError_t launch_fine_cost(cudaStream_t s, const float *views, const uint64_t *cen,
+                             const FineTap *tab, int G, int nviews, int H, int W, int ref,
+                             const int *lo, const int *cnt, const long long *off, float wl2,
+                             float wc, float *cost, int *status);
+
+cudaError_t launch_cost_partial_sums(cudaStream_t s, const float *cost, const int *cnt,
+                                     const long long *off, int N, int G, double *partial, int nblocks,
+                                     int *status);
+cudaError_t launch_fine_penalties(cudaStream_t s, const double *partial, int nblocks,
+                                  const int *cnt, int N, double p1f, double p2f, float *pen);
+cudaError_t launch_fine_sgm(cudaStream_t s, const float *cost, const int *lo, const int *cnt,
+                            const long long *off, int H, int W, int G, const float *pen, float *agg,
+                            int *status);
+
+cudaError_t launch_wta(cudaStream_t s, const float *agg, const int *lo, const int *cnt,
+                       const long long *off, int N, int G, double dmin, double step, int mode,
+                       float tau, int *label, float *disp, int *status);
+
+constexpr int kPartialBlocks = 1024;
+
+}  // namespace lfsgm

@@ -1,0 +1,341 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 oracle.
+
+Bars: census/Hamming, coarse maps, windows and labels bit-exact (labels: except where the
+oracle's own decision is a near-tie, gap <= 1e-5 * scale); l2 and aggregated costs within
+1e-5 relative to the per-pixel scale; sub-pixel disparity within 1e-3 px."""
+import numpy as np
+import pytest
+
+import lfsynth
+import oracle
+from lf_helpers import (DISP_TOL, RTOL, best_of, csr_rel_err, gather, label_mismatch,
+                        pad4_offsets)
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="session")
+def tiny_case():
+    views, gt, p = lfsynth.tiny()
+    cfg = oracle.make_cfg(p)
+    ref = oracle.depth(cfg, views, p1f=p.p1_frac, p2f=p.p2_frac)
+    return views, gt, p, cfg, ref
+
+
+def _dev(a, dtype=None):
+    import torch
+    t = torch.from_numpy(np.ascontiguousarray(a))
+    if dtype is not None:
+        t = t.to(dtype)
+    return t.cuda()
+
+
+def _np(t):
+    return t.detach().cpu().numpy()
+
+
+def _run_initial(lf, p, views, Pc=(0, 0)):
+    import torch
+    h = lf.lfsgm_create(p)
+    N = p.H * p.W
+    lo = torch.empty(N, dtype=torch.int32, device="cuda")
+    cnt = torch.empty_like(lo)
+    off = torch.empty(N + 1, dtype=torch.int64, device="cuda")
+    dinit = torch.empty(N, dtype=torch.float32, device="cuda")
+    maps = torch.full((4, N), -7, dtype=torch.int32, device="cuda")
+    nnz = lf.lfsgm_initial_disparity(h, _dev(views), Pc[0], Pc[1], lo, cnt, off, dinit, maps, want_nnz=True)
+    lf.lfsgm_sync(h)
+    out = dict(lo=_np(lo), cnt=_np(cnt), off=_np(off), dinit=_np(dinit), maps=_np(maps), nnz=nnz)
+    lf.lfsgm_destroy(h)
+    return out
+
+
+def _check_initial(g, ref, p):
+    n = len(ref["arms"])
+    assert np.array_equal(g["maps"][:n], ref["maps"]), "coarse WTA maps differ"
+    assert np.array_equal(g["lo"], ref["lo"])
+    assert np.array_equal(g["cnt"], ref["cnt"])
+    rd = ref["dinit"].astype(np.float32)
+    assert np.array_equal(np.isnan(g["dinit"]), np.isnan(rd))
+    ok = ~np.isnan(rd)
+    assert np.array_equal(g["dinit"][ok], rd[ok])
+    assert np.array_equal(g["off"], pad4_offsets(ref["cnt"]))
+    assert g["nnz"] == g["off"][-1]
+    assert np.all(g["off"][:-1] % 4 == 0)
+
+
+# --------------------------------------------------------------------- initial pass
+def test_initial_disparity_tiny_bitexact(gpu_lib, tiny_case):
+    views, gt, p, cfg, ref = tiny_case
+    g = _run_initial(gpu_lib, p, views)
+    _check_initial(g, ref, p)
+
+
+@pytest.mark.parametrize("variant", ["explicit_pen", "paper_4_views", "census7_odd_shape", "one_pass",
+                                     "row_lf"])
+def test_initial_disparity_variants(gpu_lib, variant):
+    Pc = (0, 0)
+    if variant == "explicit_pen":
+        views, _, p = lfsynth.tiny()
+        Pc = (2, 9)
+    elif variant == "paper_4_views":
+        views, _, p = lfsynth.tiny(params=lfsynth.tiny_params(init_views=0))
+    elif variant == "census7_odd_shape":
+        p = lfsynth.tiny_params(H=37, W=45, census_w=7, coarse_labels=97, fine_labels=101, fine_radius=7)
+        views, _, p = lfsynth.tiny(params=p)
+    elif variant == "one_pass":
+        views, _, p = lfsynth.tiny(params=lfsynth.tiny_params(fill_passes=1, phi=1.0))
+    else:  # a 3-D light field: one row of 7 views (Middlebury-like)
+        p = lfsynth.tiny_params(U=7, V=1, H=30, W=70, coarse_labels=130)
+        views, _, p = lfsynth.tiny(params=p)
+    cfg = oracle.make_cfg(p)
+    pens = None if Pc[0] <= 0 else [Pc] * 4
+    ref = oracle.initial_disparity(cfg, views, pens, p.p1_frac, p.p2_frac)
+    g = _run_initial(gpu_lib, p, views, Pc)
+    _check_initial(g, ref, p)
+
+
+# ----------------------------------------------------------------------- cost volume
+def _gpu_cost(lf, p, views, lo, cnt):
+    import torch
+    h = lf.lfsgm_create(p)
+    off = pad4_offsets(cnt)
+    cost = torch.full((int(off[-1]),), float("nan"), dtype=torch.float32, device="cuda")
+    lf.lfsgm_cost_volume(h, _dev(views), _dev(lo, torch.int32), _dev(cnt, torch.int32), _dev(off), cost)
+    lf.lfsgm_sync(h)
+    lf.lfsgm_destroy(h)
+    c = _np(cost)
+    # padding slots are written with 0
+    pad = np.ones(c.size, bool)
+    pad[np.repeat(off[:-1], cnt) + (np.arange(int(np.sum(cnt))) - np.repeat(np.cumsum(cnt) - cnt, cnt))] = False
+    assert np.all(c[pad] == 0.0)
+    return off, c
+
+
+def test_cost_volume_tiny(gpu_lib, tiny_case):
+    views, gt, p, cfg, ref = tiny_case
+    off, c = _gpu_cost(gpu_lib, p, views, ref["lo"], ref["cnt"])
+    err = csr_rel_err(gather(c, off, ref["cnt"]), ref["cost"], ref["cnt"])
+    assert err < RTOL, err
+
+
+def test_cost_census_only_is_exact(gpu_lib):
+    views, _, p = lfsynth.tiny(params=lfsynth.tiny_params(w_l2=0.0, w_census=1.0, census_w=7))
+    cfg = oracle.make_cfg(p)
+    rng = np.random.default_rng(1)
+    lo = rng.integers(0, 60, p.N).astype(np.int32)
+    cnt = rng.integers(1, 22, p.N).astype(np.int32)
+    o_off, o_cost = oracle.cost_volume(cfg, views, lo, cnt)
+    off, c = _gpu_cost(gpu_lib, p, views, lo, cnt)
+    assert np.array_equal(gather(c, off, cnt).astype(np.float64), o_cost)
+
+
+@pytest.mark.parametrize("shape", [(5, 5, 33, 47), (3, 3, 1, 40), (9, 9, 20, 1), (4, 4, 17, 29)])
+def test_cost_volume_ragged_windows(gpu_lib, shape):
+    U, V, H, W = shape
+    p = lfsynth.LFParams(U=U, V=V, H=H, W=W, census_w=5, dmin=-2.0, dmax=2.0, coarse_labels=32,
+                         fine_labels=81, fine_radius=5)
+    views = lfsynth.random_views(U, V, H, W, seed=H * W)
+    rng = np.random.default_rng(H + W)
+    lo = rng.integers(0, 81, p.N).astype(np.int32)
+    cnt = np.minimum(rng.integers(1, 40, p.N), 81 - lo).astype(np.int32)
+    cnt[::7] = 81
+    lo[::7] = 0                      # whole-range pixels
+    lo[1::11] = 80
+    cnt[1::11] = 1                   # one-label windows at the top of the range
+    cfg = oracle.make_cfg(p)
+    _, o_cost = oracle.cost_volume(cfg, views, lo, cnt)
+    off, c = _gpu_cost(gpu_lib, p, views, lo, cnt)
+    err = csr_rel_err(gather(c, off, cnt), o_cost, cnt)
+    assert err < RTOL, err
+
+
+# ------------------------------------------------------------------------------ SGM
+def _gpu_sgm(lf, p, cost32, lo, cnt, P1, P2):
+    import torch
+    h = lf.lfsgm_create(p)
+    off = pad4_offsets(cnt)
+    full = np.zeros(int(off[-1]), np.float32)
+    full[np.repeat(off[:-1], cnt) + (np.arange(int(np.sum(cnt))) - np.repeat(np.cumsum(cnt) - cnt, cnt))] = cost32
+    agg = torch.full_like(_dev(full), float("nan"))
+    lf.lfsgm_sgm_aggregate(h, _dev(full), _dev(lo, torch.int32), _dev(cnt, torch.int32), _dev(off), P1, P2, agg)
+    lf.lfsgm_sync(h)
+    lf.lfsgm_destroy(h)
+    return off, _np(agg)
+
+
+def test_sgm_tiny(gpu_lib, tiny_case):
+    views, gt, p, cfg, ref = tiny_case
+    c32 = ref["cost"].astype(np.float32)
+    P1, P2 = np.float32(ref["P1"]), np.float32(ref["P2"])
+    o_Cs = oracle.sgm_bounded(p.H, p.W, ref["lo"], ref["cnt"], ref["off"], c32.astype(np.float64),
+                              float(P1), float(P2))
+    off, agg = _gpu_sgm(gpu_lib, p, c32, ref["lo"], ref["cnt"], P1, P2)
+    err = csr_rel_err(gather(agg, off, ref["cnt"]), o_Cs, ref["cnt"])
+    assert err < RTOL, err
+
+
+def test_sgm_zero_penalties_is_eight_times_cost(gpu_lib, tiny_case):
+    views, gt, p, cfg, ref = tiny_case
+    c32 = ref["cost"].astype(np.float32)
+    off, agg = _gpu_sgm(gpu_lib, p, c32, ref["lo"], ref["cnt"], 0.0, 0.0)
+    g = gather(agg, off, ref["cnt"]).astype(np.float64)
+    assert np.max(np.abs(g - 8.0 * c32) / np.maximum(8.0 * c32, 1e-30)) < 1e-6
+
+
+@pytest.mark.parametrize("shape", [(1, 50), (50, 1), (3, 70), (23, 37), (64, 9)])
+def test_sgm_ragged_and_wide_windows(gpu_lib, shape):
+    H, W = shape
+    G = 150
+    p = lfsynth.LFParams(U=3, V=3, H=H, W=W, census_w=5, dmin=-2.0, dmax=2.0, coarse_labels=32,
+                         fine_labels=G, fine_radius=5)
+    rng = np.random.default_rng(H * 100 + W)
+    lo = rng.integers(0, G, H * W).astype(np.int32)
+    cnt = np.minimum(rng.integers(1, 40, H * W), G - lo).astype(np.int32)
+    wide = rng.random(H * W) < 0.15
+    lo[wide] = rng.integers(0, 20, wide.sum())
+    cnt[wide] = np.minimum(rng.integers(33, G, wide.sum()), G - lo[wide])   # multi-chunk rows
+    off_o = oracle.offsets(cnt)
+    cost = rng.uniform(0, 30, int(off_o[-1])).astype(np.float32)
+    P1, P2 = np.float32(1.7), np.float32(9.5)
+    o_Cs = oracle.sgm_bounded(H, W, lo, cnt, off_o, cost.astype(np.float64), float(P1), float(P2))
+    off, agg = _gpu_sgm(gpu_lib, p, cost, lo, cnt, P1, P2)
+    err = csr_rel_err(gather(agg, off, cnt), o_Cs, cnt)
+    assert err < RTOL, err
+
+
+def test_sgm_derived_penalties(gpu_lib, tiny_case):
+    views, gt, p, cfg, ref = tiny_case
+    c32 = ref["cost"].astype(np.float32)
+    mean = float(c32.astype(np.float64).mean())
+    o_Cs = oracle.sgm_bounded(p.H, p.W, ref["lo"], ref["cnt"], ref["off"], c32.astype(np.float64),
+                              p.p1_frac * mean, p.p2_frac * mean)
+    off, agg = _gpu_sgm(gpu_lib, p, c32, ref["lo"], ref["cnt"], -1.0, -1.0)
+    err = csr_rel_err(gather(agg, off, ref["cnt"]), o_Cs, ref["cnt"])
+    assert err < RTOL, err
+
+
+# -------------------------------------------------------------------------------- WTA
+@pytest.mark.parametrize("mode", [0, 1, 2])
+def test_wta_subpixel_on_identical_input(gpu_lib, tiny_case, mode):
+    import torch
+    views, gt, p, cfg, ref = tiny_case
+    Cs32 = ref["Cs"].astype(np.float32)
+    o_label, o_disp, _ = oracle.wta_subpixel(cfg, ref["lo"], ref["cnt"], ref["off"], Cs32.astype(np.float64),
+                                             mode=mode, tau=p.softmin_tau)
+    pp = lfsynth.tiny_params(subpixel=mode)
+    h = gpu_lib.lfsgm_create(pp)
+    off = pad4_offsets(ref["cnt"])
+    full = np.zeros(int(off[-1]), np.float32)
+    cnt = ref["cnt"]
+    full[np.repeat(off[:-1], cnt) + (np.arange(int(cnt.sum())) - np.repeat(np.cumsum(cnt) - cnt, cnt))] = Cs32
+    label = torch.empty(p.N, dtype=torch.int32, device="cuda")
+    disp = torch.empty(p.N, dtype=torch.float32, device="cuda")
+    gpu_lib.lfsgm_wta_subpixel(h, _dev(full), _dev(ref["lo"], torch.int32), _dev(cnt, torch.int32), _dev(off),
+                               label, disp)
+    gpu_lib.lfsgm_sync(h)
+    gpu_lib.lfsgm_destroy(h)
+    assert np.array_equal(_np(label), o_label)
+    assert np.max(np.abs(_np(disp) - o_disp)) < DISP_TOL
+
+
+# ---------------------------------------------------------------------- end to end
+def _gpu_depth(lf, p, views):
+    import torch
+    h = lf.lfsgm_create(p)
+    label = torch.empty(p.N, dtype=torch.int32, device="cuda")
+    disp = torch.empty(p.N, dtype=torch.float32, device="cuda")
+    lf.lfsgm_depth(h, _dev(views), disp, label)
+    lf.lfsgm_sync(h)
+    n = lf.lfsgm_launch_count(h)
+    lf.lfsgm_destroy(h)
+    return _np(label), _np(disp), n
+
+
+def _check_end_to_end(g_label, g_disp, ref, p):
+    best = best_of(ref["Cs"], ref["off"], ref["cnt"], ref["label"], ref["lo"])
+    bad, ties = label_mismatch(g_label, ref["label"], ref["gap"], best)
+    assert bad == 0, f"{bad} decided labels differ ({ties} near-ties differ)"
+    same = g_label == ref["label"]
+    assert np.max(np.abs(g_disp[same] - ref["disp"][same])) < DISP_TOL
+    return ties
+
+
+def test_depth_end_to_end_tiny(gpu_lib, tiny_case):
+    views, gt, p, cfg, ref = tiny_case
+    g_label, g_disp, n = _gpu_depth(gpu_lib, p, views)
+    _check_end_to_end(g_label, g_disp, ref, p)
+    assert n > 10
+
+
+def test_depth_end_to_end_integer_planes_exact(gpu_lib):
+    views, gt, p = lfsynth.integer_planes(H=96, W=96)
+    cfg = oracle.make_cfg(p)
+    ref = oracle.depth(cfg, views)
+    g_label, g_disp, _ = _gpu_depth(gpu_lib, p, views)
+    _check_end_to_end(g_label, g_disp, ref, p)
+
+
+def test_depth_host_matches_device(gpu_lib, tiny_case):
+    import torch
+    views, gt, p, cfg, ref = tiny_case
+    g_label, g_disp, _ = _gpu_depth(gpu_lib, p, views)
+    h = gpu_lib.lfsgm_create(p)
+    vh = torch.from_numpy(np.ascontiguousarray(views)).pin_memory()
+    dh = torch.empty(p.N, dtype=torch.float32).pin_memory()
+    lh = torch.empty(p.N, dtype=torch.int32).pin_memory()
+    gpu_lib.lfsgm_depth_host(h, vh, dh, lh)
+    gpu_lib.lfsgm_destroy(h)
+    # the 8 SGM directions add into the aggregate with float atomics, so two runs may
+    # differ in the last bits of C_s and hence of the parabola offset
+    assert np.array_equal(lh.numpy(), g_label)
+    assert np.max(np.abs(dh.numpy() - g_disp)) < 1e-5
+
+
+def test_argument_errors_are_reported(gpu_lib, tiny_case):
+    import torch
+    views, gt, p, cfg, ref = tiny_case
+    h = gpu_lib.lfsgm_create(p)
+    x = torch.zeros(16, dtype=torch.float32, device="cuda")
+    i = torch.zeros(16, dtype=torch.int32, device="cuda")
+    o = torch.zeros(17, dtype=torch.int64, device="cuda")
+    with pytest.raises(gpu_lib.LfsgmError, match="P2 >= P1|P1 <= P2"):
+        gpu_lib.lfsgm_sgm_aggregate(h, x, i, i, o, 5.0, 1.0, x)
+    with pytest.raises(gpu_lib.LfsgmError, match="P2 >= P1"):
+        gpu_lib.lfsgm_initial_disparity(h, x, 5, 1, i, i, o)
+    with pytest.raises(TypeError):
+        gpu_lib.lfsgm_cost_volume(h, x, x, i, o, x)
+    gpu_lib.lfsgm_sync(h)
+    gpu_lib.lfsgm_destroy(h)
+
+
+# ------------------------------------------------------------- full size (bench shape)
+@pytest.fixture(scope="session")
+def bench_case():
+    views, gt, p = lfsynth.bench()
+    cfg = oracle.make_cfg(p)
+    ref = oracle.depth(cfg, views, p1f=p.p1_frac, p2f=p.p2_frac)
+    return views, gt, p, cfg, ref
+
+
+def test_bench_shape_full_parity(gpu_lib, bench_case):
+    """9x9 x 512x512, census 7x7, 100 coarse labels, 31-label windows: the same stage chain
+    as the benchmark, compared with the oracle on every pixel."""
+    import torch
+    views, gt, p, cfg, ref = bench_case
+    lf = gpu_lib.LightFieldDepth(p)
+    vd = _dev(views)
+    nnz = lf.initial(vd, want_nnz=True)
+    g = dict(lo=_np(lf.lo), cnt=_np(lf.cnt), off=_np(lf.off), dinit=_np(lf.dinit), maps=_np(lf.maps), nnz=nnz)
+    _check_initial(g, ref, p)
+    lf.cost_volume(vd)
+    cost = _np(lf.cost)
+    err = csr_rel_err(gather(cost, g["off"], g["cnt"]), ref["cost"], g["cnt"])
+    assert err < RTOL, err
+    lf.aggregate(-1.0, -1.0)
+    agg = _np(lf.agg)
+    err = csr_rel_err(gather(agg, g["off"], g["cnt"]), ref["Cs"], g["cnt"])
+    assert err < RTOL, err
+    lf.wta()
+    _check_end_to_end(_np(lf.label), _np(lf.disp), ref, p)
+    lf.close()
