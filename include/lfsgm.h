@@ -168,6 +168,27 @@ lfsgm_status lfsgm_depth_host(lfsgm_handle h, const float *views_host, float *di
  * the same chain as lfsgm_depth_host without the copies. disp, label: device, nullable. */
 lfsgm_status lfsgm_depth(lfsgm_handle h, const float *views, float *disp, int32_t *label);
 
+/* The bounded cost volume (same result as lfsgm_cost_volume) for callers that may not
+ * allocate device memory.  The paper has no counterpart: this is a deployment variant.
+ * Real-time loops and plug-ins that live inside a host application's own memory pool run
+ * under a fixed device-memory budget and must not call cudaMalloc while running (it can
+ * block, fail under memory pressure, or bypass the host's accounting); they cannot create
+ * a handle, which allocates.  This entry point takes the configuration directly and
+ * allocates nothing: its scratch (shift table, census words of every view, status word)
+ * is one static device array of 32 MiB that every GPU loading this library holds until
+ * the process exits.  It serves light fields with
+ *     256 + round256(4 U V) + round256(16 U V G) + 8 U V H W <= 32 MiB
+ * (e.g. 5x5 views of 64x64 .. 256x256) and returns LFSGM_ERR_UNSUPPORTED beyond that.
+ * The first call on each device resolves the array's device address (cudaGetSymbolAddress,
+ * with that device current): make that first call before any stream capture.  All calls
+ * share the array, so calls that overlap on the GPU (two streams, or two host threads at
+ * once) race; the status word is cleared at the start of every call and windows that break
+ * the layout rules are skipped (their slots are left unwritten).
+ *   cfg: as for lfsgm_create; stream: cudaStream_t; the rest as for lfsgm_cost_volume. */
+lfsgm_status lfsgm_cost_volume_noalloc(const lfsgm_config *cfg, void *stream, const float *views,
+                                       const int32_t *lo, const int32_t *cnt, const int64_t *off,
+                                       float *cost);
+
 #ifdef __cplusplus
 }
 #endif

@@ -57,7 +57,7 @@ EXPORTS = ["lfsgm_create", "lfsgm_destroy", "lfsgm_workspace_size", "lfsgm_set_w
            "lfsgm_max_nnz", "lfsgm_initial_disparity", "lfsgm_cost_volume", "lfsgm_sgm_aggregate",
            "lfsgm_wta_subpixel", "lfsgm_backward", "lfsgm_sync", "lfsgm_last_error",
            "lfsgm_launch_count", "lfsgm_set_profiling", "lfsgm_kernel_times", "lfsgm_depth_host",
-           "lfsgm_depth"]
+           "lfsgm_depth", "lfsgm_cost_volume_noalloc"]
 
 
 def load(build_if_missing: bool = False):
@@ -94,6 +94,7 @@ def load(build_if_missing: bool = False):
         L.lfsgm_kernel_times.argtypes = [vp, P(C.c_char_p), P(f32), i32, P(i32)]
         L.lfsgm_depth_host.argtypes = [vp, vp, vp, vp]
         L.lfsgm_depth.argtypes = [vp, vp, vp, vp]
+        L.lfsgm_cost_volume_noalloc.argtypes = [P(Config), vp, vp, vp, vp, vp, vp]
         for name in EXPORTS:
             if name not in ("lfsgm_last_error", "lfsgm_launch_count"):
                 getattr(L, name).restype = i32
@@ -250,6 +251,25 @@ def lfsgm_depth(h, views, disp=None, label=None):
     import torch
     _check(load().lfsgm_depth(h, _ptr(views, torch.float32, "views"), _ptr(disp, torch.float32, "disp"),
                               _ptr(label, torch.int32, "label")), h)
+
+
+def lfsgm_cost_volume_noalloc(cfg, views, lo, cnt, off, cost, stream=None):
+    """lfsgm_cost_volume without a handle and without any device allocation, for callers
+    that run under a fixed device-memory budget (scratch lives in a static 32 MiB device
+    array inside the library; calls that overlap on the GPU race on it)."""
+    import torch
+    if not isinstance(cfg, Config):
+        cfg = make_config(cfg)
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    st = load().lfsgm_cost_volume_noalloc(
+        C.byref(cfg), C.c_void_p(stream.cuda_stream), _ptr(views, torch.float32, "views"),
+        _ptr(lo, torch.int32, "lo"), _ptr(cnt, torch.int32, "cnt"), _ptr(off, torch.int64, "off"),
+        _ptr(cost, torch.float32, "cost"))
+    if st != OK:
+        raise LfsgmError(st, "lfsgm_cost_volume_noalloc: " + {1: "invalid config or null buffer",
+                                                              5: "light field too large for the static scratch",
+                                                              4: "CUDA error"}.get(st, ""))
 
 
 # ------------------------------------------------------------------ convenience wrapper
