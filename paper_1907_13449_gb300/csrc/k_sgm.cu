@@ -7,7 +7,7 @@
 // the predecessor's window are absent from the minimum (Sec. III-E).  The step is the
 // normalised recurrence
 //   L(p,g) = C(p,g) + (min(L'(g), L'(g-1)+P1, L'(g+1)+P1, m+P2) - m),   m = min L',
-// and the predecessor minimum m is one redux.sync per pixel.  The 8 directions run
+// and the predecessor minimum m is one redux.sync.min.f32 per pixel.  The 8 directions run
 // concurrently and add into agg (zeroed by the caller) with float atomics.
 //
 // Derived penalties: per-block partial sums (double) of the active slots, then one block
@@ -19,9 +19,10 @@ namespace {
 
 constexpr int kSgmWarps = 4;
 
-__device__ __forceinline__ float warp_min_nonneg(float v) {
-    // costs are >= 0, so the float order equals the unsigned order of the bit patterns
-    return __uint_as_float(__reduce_min_sync(0xffffffffu, __float_as_uint(v)));
+__device__ __forceinline__ float warp_min(float v) {
+    float r;
+    asm volatile("redux.sync.min.f32 %0, %1, 0xffffffff;" : "=f"(r) : "f"(v));
+    return r;
 }
 
 __global__ void __launch_bounds__(32 * kSgmWarps) fine_sgm_kernel(const float *__restrict__ cost,
@@ -75,7 +76,7 @@ __global__ void __launch_bounds__(32 * kSgmWarps) fine_sgm_kernel(const float *_
             lmin = fminf(lmin, Lv);
             atomicAdd(agg + o + j, Lv);
         }
-        m = warp_min_nonneg(lmin);
+        m = warp_min(lmin);
         __syncwarp();
         if (n == 0) {
             x += dx;
@@ -93,43 +94,63 @@ __global__ void __launch_bounds__(32 * kSgmWarps) fine_sgm_kernel(const float *_
     }
 }
 
+// Per-block sums of the active costs and slot counts (rows are 16-byte aligned, read as float4;
+// slots past cnt are masked).  Each thread adds its pixels in a fixed order, the block adds its
+// warps in a fixed order: the partials, and hence the mean, are deterministic.
 __global__ void cost_partial_kernel(const float *__restrict__ cost, const int *__restrict__ cnt,
                                     const long long *__restrict__ off, int N, int G,
                                     double *__restrict__ partial, int *__restrict__ status) {
-    double s = 0.0;
+    double s = 0.0, c = 0.0;
     for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < N; p += gridDim.x * blockDim.x) {
         const long long o = off[p];
         const int n = cnt[p];
         if (!window_ok(0, n, G, off[p + 1] - o, status)) continue;
-        for (int j = 0; j < n; j++) s += (double)cost[o + j];
+        const float4 *r = reinterpret_cast<const float4 *>(cost + o);
+        float ps = 0.f;
+        for (int j = 0; j < n; j += 4) {
+            const float4 v = __ldg(r + (j >> 2));
+            ps += v.x + (j + 1 < n ? v.y : 0.f) + (j + 2 < n ? v.z : 0.f) + (j + 3 < n ? v.w : 0.f);
+        }
+        s += (double)ps;
+        c += n;
     }
-    for (int k = 16; k > 0; k >>= 1) s += __shfl_down_sync(0xffffffffu, s, k);
-    __shared__ double ws[32];
+    for (int k = 16; k > 0; k >>= 1) {
+        s += __shfl_down_sync(0xffffffffu, s, k);
+        c += __shfl_down_sync(0xffffffffu, c, k);
+    }
+    __shared__ double ws[32], wc[32];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    if (lane == 0) ws[wid] = s;
+    if (lane == 0) {
+        ws[wid] = s;
+        wc[wid] = c;
+    }
     __syncthreads();
     if (threadIdx.x == 0) {
-        double b = 0.0;
-        for (int i = 0; i < (int)(blockDim.x >> 5); i++) b += ws[i];
+        double b = 0.0, bc = 0.0;
+        for (int i = 0; i < (int)(blockDim.x >> 5); i++) {
+            b += ws[i];
+            bc += wc[i];
+        }
         partial[blockIdx.x] = b;
+        partial[gridDim.x + blockIdx.x] = bc;
     }
 }
 
-__global__ void fine_penalty_kernel(const double *__restrict__ partial, int nblocks, const int *__restrict__ cnt,
-                                    int N, double p1f, double p2f, float *__restrict__ pen) {
-    // count of active slots (exact), then the mean in a fixed order
-    __shared__ long long cs[32];
-    long long c = 0;
-    for (int p = threadIdx.x; p < N; p += blockDim.x) c += cnt[p];
-    for (int k = 16; k > 0; k >>= 1) c += __shfl_down_sync(0xffffffffu, c, k);
-    if ((threadIdx.x & 31) == 0) cs[threadIdx.x >> 5] = c;
-    __syncthreads();
+// Mean over the active slots: one warp adds the partials (lane-strided, then a fixed
+// shuffle tree), so the result does not depend on timing.
+__global__ void fine_penalty_kernel(const double *__restrict__ partial, int nblocks, double p1f, double p2f,
+                                    float *__restrict__ pen) {
+    double s = 0.0, c = 0.0;
+    for (int i = threadIdx.x; i < nblocks; i += 32) {
+        s += partial[i];
+        c += partial[nblocks + i];
+    }
+    for (int k = 16; k > 0; k >>= 1) {
+        s += __shfl_down_sync(0xffffffffu, s, k);
+        c += __shfl_down_sync(0xffffffffu, c, k);
+    }
     if (threadIdx.x == 0) {
-        long long tot = 0;
-        for (int i = 0; i < (int)(blockDim.x >> 5); i++) tot += cs[i];
-        double s = 0.0;
-        for (int i = 0; i < nblocks; i++) s += partial[i];
-        const double mean = s / (double)tot;
+        const double mean = c > 0.0 ? s / c : 0.0;
         pen[0] = (float)(p1f * mean);
         pen[1] = (float)(p2f * mean);
     }
@@ -143,9 +164,9 @@ cudaError_t launch_cost_partial_sums(cudaStream_t s, const float *cost, const in
     return cudaGetLastError();
 }
 
-cudaError_t launch_fine_penalties(cudaStream_t s, const double *partial, int nblocks, const int *cnt,
-                                  int N, double p1f, double p2f, float *pen) {
-    fine_penalty_kernel<<<1, 1024, 0, s>>>(partial, nblocks, cnt, N, p1f, p2f, pen);
+cudaError_t launch_fine_penalties(cudaStream_t s, const double *partial, int nblocks, double p1f, double p2f,
+                                  float *pen) {
+    fine_penalty_kernel<<<1, 32, 0, s>>>(partial, nblocks, p1f, p2f, pen);
     return cudaGetLastError();
 }
 

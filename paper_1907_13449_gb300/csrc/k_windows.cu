@@ -76,16 +76,13 @@ __global__ void windows_kernel(const int *__restrict__ F, int N, int G, int Lc, 
     cntpad[p] = (n + 3) & ~3;
 }
 
-// Exclusive scan of the padded counts (one CTA of 1024 threads, contiguous chunks).
-__global__ void __launch_bounds__(1024) scan_kernel(const int *__restrict__ cntpad, int N, long long *__restrict__ off) {
-    __shared__ long long wsum[32];
+// Exclusive scan of the padded counts in three phases over tiles of 1024 entries:
+// per-tile sums, a scan of the tile sums (one CTA), then per-tile scans plus the tile offset.
+constexpr int kScanTile = 1024;
+
+__device__ __forceinline__ long long block_exclusive_scan(long long v, long long *wsum, long long *total) {
     const int t = threadIdx.x, lane = t & 31, wid = t >> 5;
-    const int chunk = (N + 1023) / 1024;
-    const int b = min(N, t * chunk), e = min(N, b + chunk);
-    long long s = 0;
-    for (int i = b; i < e; i++) s += cntpad[i];
-    // inclusive warp scan
-    long long inc = s;
+    long long inc = v;
     for (int o = 1; o < 32; o <<= 1) {
         const long long y = __shfl_up_sync(0xffffffffu, inc, o);
         if (lane >= o) inc += y;
@@ -93,7 +90,7 @@ __global__ void __launch_bounds__(1024) scan_kernel(const int *__restrict__ cntp
     if (lane == 31) wsum[wid] = inc;
     __syncthreads();
     if (wid == 0) {
-        long long w = wsum[lane];
+        long long w = lane < (int)(blockDim.x >> 5) ? wsum[lane] : 0;
         for (int o = 1; o < 32; o <<= 1) {
             const long long y = __shfl_up_sync(0xffffffffu, w, o);
             if (lane >= o) w += y;
@@ -101,12 +98,48 @@ __global__ void __launch_bounds__(1024) scan_kernel(const int *__restrict__ cntp
         wsum[lane] = w;
     }
     __syncthreads();
-    long long run = inc - s + (wid > 0 ? wsum[wid - 1] : 0);
-    for (int i = b; i < e; i++) {
-        off[i] = run;
-        run += cntpad[i];
+    const long long ex = inc - v + (wid > 0 ? wsum[wid - 1] : 0);
+    if (total) *total = wsum[(blockDim.x >> 5) - 1];
+    __syncthreads();
+    return ex;
+}
+
+__global__ void __launch_bounds__(kScanTile) scan_tile_sums(const int *__restrict__ cntpad, int N, long long *__restrict__ tsum) {
+    __shared__ long long wsum[32];
+    const int i = blockIdx.x * kScanTile + threadIdx.x;
+    long long v = i < N ? cntpad[i] : 0;
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    if ((threadIdx.x & 31) == 0) wsum[threadIdx.x >> 5] = v;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        long long s = 0;
+        for (int w = 0; w < kScanTile / 32; w++) s += wsum[w];
+        tsum[blockIdx.x] = s;
     }
-    if (t == 1023) off[N] = wsum[31];
+}
+
+__global__ void __launch_bounds__(kScanTile) scan_tile_offsets(long long *__restrict__ tsum, int ntiles) {
+    __shared__ long long wsum[32];
+    long long carry = 0;
+    for (int base = 0; base < ntiles; base += kScanTile) {
+        const int i = base + threadIdx.x;
+        const long long v = i < ntiles ? tsum[i] : 0;
+        long long total;
+        const long long ex = block_exclusive_scan(v, wsum, &total);
+        if (i < ntiles) tsum[i] = carry + ex;
+        carry += total;
+    }
+}
+
+__global__ void __launch_bounds__(kScanTile) scan_apply(const int *__restrict__ cntpad, int N, const long long *__restrict__ toff,
+                                                        long long *__restrict__ off) {
+    __shared__ long long wsum[32];
+    const int i = blockIdx.x * kScanTile + threadIdx.x;
+    const long long v = i < N ? cntpad[i] : 0;
+    const long long ex = block_exclusive_scan(v, wsum, nullptr);
+    const long long o = toff[blockIdx.x] + ex;
+    if (i < N) off[i] = o;
+    if (i == N - 1) off[N] = o + v;
 }
 
 }  // namespace
@@ -124,8 +157,18 @@ cudaError_t launch_windows(cudaStream_t s, const int *F, int N, int G, int Lc, i
     windows_kernel<<<(N + 255) / 256, 256, 0, s>>>(F, N, G, Lc, R, lo, cnt, dinit, cntpad);
     return cudaGetLastError();
 }
-cudaError_t launch_scan(cudaStream_t s, const int *cntpad, int N, long long *off) {
-    scan_kernel<<<1, 1024, 0, s>>>(cntpad, N, off);
+int scan_tiles(int N) { return (N + kScanTile - 1) / kScanTile; }
+
+cudaError_t launch_scan_sums(cudaStream_t s, const int *cntpad, int N, long long *tsum) {
+    scan_tile_sums<<<scan_tiles(N), kScanTile, 0, s>>>(cntpad, N, tsum);
+    return cudaGetLastError();
+}
+cudaError_t launch_scan_top(cudaStream_t s, long long *tsum, int N) {
+    scan_tile_offsets<<<1, kScanTile, 0, s>>>(tsum, scan_tiles(N));
+    return cudaGetLastError();
+}
+cudaError_t launch_scan_apply(cudaStream_t s, const int *cntpad, int N, const long long *tsum, long long *off) {
+    scan_apply<<<scan_tiles(N), kScanTile, 0, s>>>(cntpad, N, tsum, off);
     return cudaGetLastError();
 }
 

@@ -67,10 +67,13 @@ struct lfsgm_ctx {
     uint16_t *ccost = nullptr;
     uint32_t *csum = nullptr;
     int *maps = nullptr, *F0 = nullptr, *F1 = nullptr, *cntpad = nullptr;
+    int *wide_list = nullptr, *wide_count = nullptr;
+    int rf_cap = 0, rc_cap = 0, seg_cap = 0, tiled_warp_bytes = 0;
     unsigned long long *armsum = nullptr;
     int *cpen = nullptr;
     float *fpen = nullptr;
     double *partial = nullptr;
+    long long *tsum = nullptr;
     int *status = nullptr;
     // buffers of the whole-method entry points (owned, allocated on first use)
     int *o_lo = nullptr, *o_cnt = nullptr, *o_label = nullptr;
@@ -228,11 +231,14 @@ lfsgm_status bind_workspace(lfsgm_ctx *h, void *dptr, size_t bytes, bool owned) 
     h->F0 = (int *)take(N * 4);
     h->F1 = (int *)take(N * 4);
     h->cntpad = (int *)take(N * 4);
+    h->wide_list = (int *)take(N * 4);
+    h->wide_count = (int *)take(4);
     h->armsum = (unsigned long long *)take(4 * 8);
     h->cpen = (int *)take(8 * 4);
     h->fpen = (float *)take(2 * 4);
-    h->partial = (double *)take(kPartialBlocks * 8);
+    h->partial = (double *)take(2 * kPartialBlocks * 8);
     h->status = (int *)take(4);
+    h->tsum = (long long *)take((size_t)scan_tiles(h->N) * 8);
     const cudaError_t e = cudaMemsetAsync(h->status, 0, 4, h->stream);
     if (e != cudaSuccess) return cuda_fail(h, e, "status clear");
     return LFSGM_OK;
@@ -260,6 +266,8 @@ lfsgm_status lfsgm_create(const lfsgm_config *cfg, void *stream, lfsgm_handle *o
     h->ref = c.vc * c.U + c.uc;
     h->nbits = c.census_w * c.census_w - 1;
     h->Lcs = c.coarse_labels <= 64 ? 64 : (c.coarse_labels <= 128 ? 128 : 256);
+    h->tiled_warp_bytes = fine_cost_tiled_caps(c.U, c.V, c.uc, c.vc, c.fine_labels, c.dmin, c.dmax, &h->rf_cap,
+                                               &h->rc_cap, &h->seg_cap);
     build_arms(h);
     // the packed coarse sums hold 8 paths x (C + P2) per 16-bit half
     const long long cmax = (long long)max_arm_views(h) * h->nbits;
@@ -345,9 +353,11 @@ lfsgm_status lfsgm_workspace_size(lfsgm_handle h, size_t *bytes) {
     b += align256(A * N * h->Lcs * 2);              // coarse cost
     b += align256(A * N * (h->Lcs / 2) * 4);        // packed coarse sums
     b += align256(4 * N * 4);                       // maps
-    b += 3 * align256(N * 4);                       // F0, F1, padded counts
+    b += 4 * align256(N * 4);                       // F0, F1, padded counts, wide-pixel list
+    b += align256(4);                               // wide-pixel count
     b += align256(4 * 8) + align256(8 * 4) + align256(2 * 4);
-    b += align256(kPartialBlocks * 8) + align256(4);
+    b += align256(2 * kPartialBlocks * 8) + align256(4);
+    b += align256((size_t)scan_tiles(h->N) * 8);    // offset-scan tile sums
     *bytes = b;
     return LFSGM_OK;
 }
@@ -407,7 +417,9 @@ lfsgm_status lfsgm_initial_disparity(lfsgm_handle h, const float *views, int32_t
     LFSGM_TRY(run(h, "windows", [&] {
         return launch_windows(s, fin, N, c.fine_labels, c.coarse_labels, c.fine_radius, lo, cnt, dinit, h->cntpad);
     }));
-    LFSGM_TRY(run(h, "scan", [&] { return launch_scan(s, h->cntpad, N, (long long *)off); }));
+    LFSGM_TRY(run(h, "scan_sums", [&] { return launch_scan_sums(s, h->cntpad, N, h->tsum); }));
+    LFSGM_TRY(run(h, "scan_top", [&] { return launch_scan_top(s, h->tsum, N); }));
+    LFSGM_TRY(run(h, "scan_apply", [&] { return launch_scan_apply(s, h->cntpad, N, h->tsum, (long long *)off); }));
     if (nnz_host) {
         e = cudaMemcpyAsync(nnz_host, off + N, sizeof(int64_t), cudaMemcpyDeviceToHost, s);
         if (e == cudaSuccess) e = cudaStreamSynchronize(s);
@@ -426,6 +438,22 @@ lfsgm_status lfsgm_cost_volume(lfsgm_handle h, const float *views, const int32_t
     LFSGM_TRY(run(h, "census_all", [&] {
         return launch_census(s, views, c.H, c.W, c.census_w, h->d_sel_all, h->nviews, h->cen);
     }));
+    if (h->tiled_warp_bytes > 0 && h->tiled_warp_bytes <= 24 * 1024) {
+        cudaError_t e = cudaMemsetAsync(h->wide_count, 0, 4, s);
+        if (e != cudaSuccess) return cuda_fail(h, e, "memset");
+        LFSGM_TRY(run(h, "fine_cost", [&] {
+            return launch_fine_cost_tiled(s, views, h->cen, h->d_fine, c.fine_labels, c.U, c.V, c.H, c.W, h->ref, lo,
+                                          cnt, (const long long *)off, c.w_l2, c.w_census, cost, h->status,
+                                          h->wide_list, h->wide_count, h->rf_cap, h->rc_cap, h->seg_cap,
+                                          (float)((c.dmax - c.dmin) / (double)(c.fine_labels - 1)));
+        }));
+        LFSGM_TRY(run(h, "fine_cost_wide", [&] {
+            return launch_fine_cost_list(s, views, h->cen, h->d_fine, c.fine_labels, h->nviews, c.H, c.W, h->ref, lo,
+                                         cnt, (const long long *)off, c.w_l2, c.w_census, cost, h->wide_list,
+                                         h->wide_count);
+        }));
+        return LFSGM_OK;
+    }
     LFSGM_TRY(run(h, "fine_cost", [&] {
         return launch_fine_cost(s, views, h->cen, h->d_fine, c.fine_labels, h->nviews, c.H, c.W, h->ref, lo, cnt,
                                 (const long long *)off, c.w_l2, c.w_census, cost, h->status);
@@ -466,7 +494,7 @@ lfsgm_status lfsgm_sgm_aggregate(lfsgm_handle h, const float *cost, const int32_
                                             h->status);
         }));
         LFSGM_TRY(run(h, "fine_penalties", [&] {
-            return launch_fine_penalties(s, h->partial, kPartialBlocks, cnt, h->N, c.p1_frac, c.p2_frac, h->fpen);
+            return launch_fine_penalties(s, h->partial, kPartialBlocks, c.p1_frac, c.p2_frac, h->fpen);
         }));
     } else {
         LFSGM_TRY(run(h, "set_penalties", [&] {

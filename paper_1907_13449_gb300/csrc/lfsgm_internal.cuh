@@ -115,18 +115,36 @@ cudaError_t launch_fuse(cudaStream_t s, const int *maps, int narms, int N, doubl
 cudaError_t launch_fill(cudaStream_t s, const int *Fin, int *Fout, int H, int W);
 cudaError_t launch_windows(cudaStream_t s, const int *F, int N, int G, int Lc, int R, int *lo,
                            int *cnt, float *dinit, int *cntpad);
-cudaError_t launch_scan(cudaStream_t s, const int *cntpad, int N, long long *off);
+int scan_tiles(int N);   // tiles of the offset scan (tile sums buffer length)
+cudaError_t launch_scan_sums(cudaStream_t s, const int *cntpad, int N, long long *tsum);
+cudaError_t launch_scan_top(cudaStream_t s, long long *tsum, int N);
+cudaError_t launch_scan_apply(cudaStream_t s, const int *cntpad, int N, const long long *tsum, long long *off);
 
 cudaError_t launch_fine_cost(cudaStream_t s, const float *views, const uint64_t *cen,
                              const FineTap *tab, int G, int nviews, int H, int W, int ref,
                              const int *lo, const int *cnt, const long long *off, float wl2,
                              float wc, float *cost, int *status);
 
+// Tiled cost volume (narrow windows) + list kernel (wide windows).  fine_cost_tiled_caps
+// returns the shared memory per warp and the region capacities for this configuration.
+int fine_cost_tiled_caps(int U, int V, int uc, int vc, int G, double dmin, double dmax, int *rf_cap,
+                         int *rc_cap, int *seg_cap);
+cudaError_t launch_fine_cost_tiled(cudaStream_t s, const float *views, const uint64_t *cen,
+                                   const FineTap *tab, int G, int U, int V, int H, int W, int ref,
+                                   const int *lo, const int *cnt, const long long *off, float wl2,
+                                   float wc, float *cost, int *status, int *wide_list, int *wide_count,
+                                   int rf_cap, int rc_cap, int seg_cap, float fstep);
+cudaError_t launch_fine_cost_list(cudaStream_t s, const float *views, const uint64_t *cen,
+                                  const FineTap *tab, int G, int nviews, int H, int W, int ref,
+                                  const int *lo, const int *cnt, const long long *off, float wl2,
+                                  float wc, float *cost, const int *list, const int *count);
+
+// partial: nblocks sums of the active costs followed by nblocks counts of active slots
 cudaError_t launch_cost_partial_sums(cudaStream_t s, const float *cost, const int *cnt,
                                      const long long *off, int N, int G, double *partial, int nblocks,
                                      int *status);
 cudaError_t launch_fine_penalties(cudaStream_t s, const double *partial, int nblocks,
-                                  const int *cnt, int N, double p1f, double p2f, float *pen);
+                                  double p1f, double p2f, float *pen);
 cudaError_t launch_fine_sgm(cudaStream_t s, const float *cost, const int *lo, const int *cnt,
                             const long long *off, int H, int W, int G, const float *pen, float *agg,
                             int *status);
