@@ -51,7 +51,67 @@ __global__ void __launch_bounds__(TX *TY) census_kernel(const float *__restrict_
     cen[(size_t)view * HW + (size_t)y * W + x] = ((uint64_t)hi << 32) | lo;
 }
 
+// Same transform, written into edge-replicated padded images: word and value of pixel (x,y) go to
+// (x+P, y+P), and border pixels also fill the padding rows/columns next to them, so that a read
+// at any padded position (xp, yp) returns the word/value of pixel (clamp(xp-P), clamp(yp-P)) --
+// exactly the clamped read of the unpadded image.  Padded row stride Wp, Hp rows per view.
+template <int HALF>
+__global__ void __launch_bounds__(TX *TY) census_pad_kernel(const float *__restrict__ views, int H, int W, int P,
+                                                            int Wp, int Hp, const int *__restrict__ sel,
+                                                            uint64_t *__restrict__ cen_pad,
+                                                            float *__restrict__ views_pad) {
+    constexpr int SW = TX + 2 * HALF, SH = TY + 2 * HALF;
+    __shared__ float tile[SH][SW + 1];
+    const size_t HW = (size_t)H * W, HWp = (size_t)Hp * Wp;
+    const int view = sel[blockIdx.z];
+    const float *img = views + (size_t)view * HW;
+    const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
+    const int tid = threadIdx.y * TX + threadIdx.x;
+    for (int i = tid; i < SH * SW; i += TX * TY) {
+        int ty = i / SW, tx = i - ty * SW;
+        int gy = min(max(y0 + ty - HALF, 0), H - 1);
+        int gx = min(max(x0 + tx - HALF, 0), W - 1);
+        tile[ty][tx] = __ldg(img + (size_t)gy * W + gx);
+    }
+    __syncthreads();
+    const int x = x0 + threadIdx.x, y = y0 + threadIdx.y;
+    if (x >= W || y >= H) return;
+    const float c = tile[threadIdx.y + HALF][threadIdx.x + HALF];
+    uint32_t lo = 0, hi = 0;
+    int bit = 0;
+#pragma unroll
+    for (int dy = -HALF; dy <= HALF; dy++) {
+#pragma unroll
+        for (int dx = -HALF; dx <= HALF; dx++) {
+            if (dx == 0 && dy == 0) continue;
+            const float nb = tile[threadIdx.y + HALF + dy][threadIdx.x + HALF + dx];
+            const uint32_t b = c > nb ? 1u : 0u;
+            if (bit < 32) lo |= b << bit;
+            else hi |= b << (bit - 32);
+            bit++;
+        }
+    }
+    const uint64_t w = ((uint64_t)hi << 32) | lo;
+    const int xa = x == 0 ? 0 : x + P, xb = x == W - 1 ? Wp - 1 : x + P;
+    const int ya = y == 0 ? 0 : y + P, yb = y == H - 1 ? Hp - 1 : y + P;
+    uint64_t *cp = cen_pad + (size_t)view * HWp;
+    float *vp = views_pad + (size_t)view * HWp;
+    for (int yy = ya; yy <= yb; yy++)
+        for (int xx = xa; xx <= xb; xx++) {
+            cp[(size_t)yy * Wp + xx] = w;
+            vp[(size_t)yy * Wp + xx] = c;
+        }
+}
+
 }  // namespace
+
+cudaError_t launch_census_pad(cudaStream_t s, const float *views, int H, int W, int census_w, int P, int Wp, int Hp,
+                              const int *d_sel, int nsel, uint64_t *cen_pad, float *views_pad) {
+    dim3 block(TX, TY), grid((W + TX - 1) / TX, (H + TY - 1) / TY, nsel);
+    if (census_w == 5) census_pad_kernel<2><<<grid, block, 0, s>>>(views, H, W, P, Wp, Hp, d_sel, cen_pad, views_pad);
+    else census_pad_kernel<3><<<grid, block, 0, s>>>(views, H, W, P, Wp, Hp, d_sel, cen_pad, views_pad);
+    return cudaGetLastError();
+}
 
 cudaError_t launch_census(cudaStream_t s, const float *views, int H, int W, int census_w,
                           const int *d_sel, int nsel, uint64_t *cen) {

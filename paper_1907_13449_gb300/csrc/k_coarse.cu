@@ -16,7 +16,7 @@ namespace {
 
 constexpr int kBig = 1 << 28;   // an absent label (outside [0, Lc))
 
-__global__ void coarse_cost_kernel(const uint64_t *__restrict__ cen, int H, int W, int ref,
+__global__ void coarse_cost_kernel(const uint64_t *__restrict__ cen_pad, int P, int Wp, int Hp, int H, int W, int ref,
                                    const int *__restrict__ views, int nv,
                                    const short2 *__restrict__ ctab, int Lc, int lcs_log2,
                                    uint16_t *__restrict__ out, unsigned long long *__restrict__ sum) {
@@ -29,12 +29,13 @@ __global__ void coarse_cost_kernel(const uint64_t *__restrict__ cen, int H, int 
         const int k = (int)(t & ((1u << lcs_log2) - 1));
         if (k < Lc) {
             const int x = p % W, y = p / W;
-            const uint64_t r = __ldg(cen + (size_t)ref * N + p);
+            const size_t HWp = (size_t)Hp * Wp;
+            const uint64_t r = __ldg(cen_pad + (size_t)ref * HWp + (size_t)(y + P) * Wp + (x + P));
             for (int i = 0; i < nv; i++) {
                 const int view = __ldg(views + i);
                 const short2 n = __ldg(ctab + (size_t)view * Lc + k);
                 const int xx = min(max(x + n.x, 0), W - 1), yy = min(max(y + n.y, 0), H - 1);
-                v += __popcll(r ^ __ldg(cen + (size_t)view * N + (size_t)yy * W + xx));
+                v += __popcll(r ^ __ldg(cen_pad + (size_t)view * HWp + (size_t)(yy + P) * Wp + (xx + P)));
             }
         }
         out[t] = (uint16_t)v;
@@ -202,7 +203,7 @@ __global__ void coarse_wta_kernel(const uint32_t *__restrict__ sum, int narms, i
 
 }  // namespace
 
-cudaError_t launch_coarse_cost(cudaStream_t s, const uint64_t *cen, int H, int W, int ref,
+cudaError_t launch_coarse_cost(cudaStream_t s, const uint64_t *cen_pad, int P, int Wp, int Hp, int H, int W, int ref,
                                const int *d_views, int nv, const short2 *ctab, int Lc, int Lcs,
                                uint16_t *out, unsigned long long *sum) {
     int lg = 0;
@@ -210,7 +211,7 @@ cudaError_t launch_coarse_cost(cudaStream_t s, const uint64_t *cen, int H, int W
     const size_t total = ((size_t)H * W) << lg;
     const int block = 256;
     const unsigned grid = (unsigned)((total + block - 1) / block);
-    coarse_cost_kernel<<<grid, block, 0, s>>>(cen, H, W, ref, d_views, nv, ctab, Lc, lg, out, sum);
+    coarse_cost_kernel<<<grid, block, 0, s>>>(cen_pad, P, Wp, Hp, H, W, ref, d_views, nv, ctab, Lc, lg, out, sum);
     return cudaGetLastError();
 }
 

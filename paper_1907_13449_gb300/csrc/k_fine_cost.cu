@@ -9,6 +9,12 @@
 // split of every (view, label) comes from the host-built FineTap table; taps and census
 // words are read through the read-only cache.  Output rows are written coalesced,
 // padding slots with 0.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+
+#include <cmath>
+#include <cstring>
+
 #include "lfsgm_internal.cuh"
 
 namespace lfsgm {
@@ -72,40 +78,63 @@ __global__ void __launch_bounds__(256) fine_cost_generic(const float *__restrict
 // inside the range; the others (and the whole-range windows of discarded pixels) go to a
 // list that fine_cost_list handles pixel by pixel.
 //
-// Per view the warp stages the table entries of its KW labels, the view region its samples
-// can touch and the census words there in its slice of shared memory.  The range splits into
-// segments at the labels where the bilinear cell (integer shift) or the nearest census
-// position changes.  Inside a segment the fractional shift grows linearly with the label
-// (a*d is linear in d), so the bilinear sample is a quadratic polynomial in the label index i,
-// s(i) = A + i (B + i C), and the census term is a constant.  A short loop over the segments
-// writes each lane's (A, B, C, w_census * HD) to shared memory; the label loop is then
-// branch-free: per label one broadcast load of the segment offset, one 16-byte load of the
-// lane's coefficients, two FMAs for the sample and two for |I_ref - s| and the sum.
+// Staging.  The views and census words are read from edge-replicated padded copies (a read at
+// a padded position equals the clamped read), so every tile a warp needs lies inside the padded
+// image.  Per view, one lane issues two TMA tile loads (a box of view values and a box of census
+// words around the row segment, x rounded down to the 16-byte boundary) and a bulk copy of the
+// KW table entries, all completing on one mbarrier; two stages are in flight, so view v+1 streams
+// in while view v is computed.  Waits are bounded: on expiry LFSGM_ERR_TIMEOUT is latched.
+//
+// Compute.  The range splits into segments at the labels where the bilinear cell (integer shift)
+// changes.  Inside a segment the fractional shift grows linearly with the label (a*d is linear in
+// d), so the bilinear sample is a quadratic polynomial in the label index i,
+// s(i) = A + i (B + i C).  A short loop over the segments writes each lane's (A, B, C) to shared
+// memory; the label loop is branch-free: per label one broadcast load of the segment offset, one
+// 16-byte load of the lane's coefficients, two FMAs for the sample, two for |I_ref - s| and the
+// sum.  The census term is a step function of the label: its Hamming distances are added as
+// integer differences at the census breakpoints and prefix-summed once at the end.
+struct RowPlan {
+    int P, Wp, Hp;                    // padding and padded sizes
+    int bwf, bhf, bwc, bhc;           // TMA boxes (elements): view values, census words
+    int seg_cap;
+    int o_rf[2], o_rc[2], o_ts[2];    // byte offsets of the stage buffers in a warp's slice
+    int o_segoff, o_coef, o_cdiff, o_mbar, warp_bytes;
+};
+
+__device__ __forceinline__ unsigned smem_u32(const void *p) { return (unsigned)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ bool mbar_wait(unsigned mbar, unsigned parity) {
+    for (int it = 0; it < (1 << 20); it++) {
+        unsigned done;
+        asm volatile("{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+                     : "=r"(done) : "r"(mbar), "r"(parity) : "memory");
+        if (done) return true;
+    }
+    return false;
+}
+
 template <int KW>
-__global__ void __launch_bounds__(256, 2) fine_cost_rows(const float *__restrict__ views,
-                                                         const uint64_t *__restrict__ cen,
+__global__ void __launch_bounds__(128, 3) fine_cost_rows(const __grid_constant__ CUtensorMap tm_v,
+                                                         const __grid_constant__ CUtensorMap tm_c,
                                                          const FineTap *__restrict__ tab, int G, int U, int V,
                                                          int H, int W, int ref, const int *__restrict__ lo,
                                                          const int *__restrict__ cnt,
-                                                         const long long *__restrict__ off, float wl2, float wc,
-                                                         float fstep, float *__restrict__ cost,
+                                                         const long long *__restrict__ off,
+                                                         const float *__restrict__ views_pad,
+                                                         const uint64_t *__restrict__ cen_pad, float wl2, float wc,
+                                                         float dmin, float fstep, float *__restrict__ cost,
                                                          int *__restrict__ status, int *__restrict__ list,
-                                                         int *__restrict__ list_count, int rf_cap, int rc_cap,
-                                                         int seg_cap) {
+                                                         int *__restrict__ list_count, RowPlan pl) {
     static_assert(KW > 32 && KW <= 64, "two 32-bit masks cover the label range");
-    extern __shared__ __align__(16) unsigned char smem[];
+    extern __shared__ __align__(128) unsigned char smem[];
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5, wpb = blockDim.x >> 5;
-    const size_t warp_bytes = (size_t)seg_cap * 512 + (size_t)KW * 128 + (size_t)KW * 20 + (size_t)rc_cap * 8 +
-                              (size_t)rf_cap * 4;
-    unsigned char *wbase = smem + wib * warp_bytes;
-    float4 *coef = (float4 *)wbase;                                             // [seg_cap][32]
-    int *cdiff = (int *)(wbase + (size_t)seg_cap * 512);                        // [KW][32] census steps
-    FineTap *ts = (FineTap *)(wbase + (size_t)seg_cap * 512 + (size_t)KW * 128); // [KW]
-    int *segoff = (int *)((unsigned char *)ts + (size_t)KW * 16);                // [KW]
-    uint64_t *rc = (uint64_t *)((unsigned char *)segoff + (size_t)KW * 4);
-    float *rf = (float *)((unsigned char *)rc + (size_t)rc_cap * 8);
-    const size_t N = (size_t)H * W;
+    unsigned char *wb = smem + (size_t)wib * pl.warp_bytes;
+    int *segoff = (int *)(wb + pl.o_segoff);
+    float4 *coef = (float4 *)(wb + pl.o_coef);
+    int *cdiff = (int *)(wb + pl.o_cdiff);
+    const unsigned mbar0 = smem_u32(wb + pl.o_mbar);
     const int nviews = U * V, uc = ref % U, vc = ref / U;
+    const size_t HWp = (size_t)pl.Hp * pl.Wp;
     const int tiles_x = (W + 31) >> 5;
     const int task = blockIdx.x * wpb + wib;
     if (task >= tiles_x * H) return;
@@ -124,15 +153,6 @@ __global__ void __launch_bounds__(256, 2) fine_cost_rows(const float *__restrict
             else list[atomicAdd(list_count, 1)] = p;
         }
     }
-    float Iref = 0.f;
-    uint64_t cr = 0;
-    if (nar) {
-        const int p = y * W + x;
-        Iref = __ldg(views + (size_t)ref * N + p);
-        cr = __ldg(cen + (size_t)ref * N + p);
-        const int npad = (int)min((long long)((n + 3) & ~3), row);
-        for (int j = n; j < npad; j++) cost[o + j] = 0.f;
-    }
     // the label range covering the most windows (ties: the lowest start); the others go to the list
     int g0 = 0, best_fit = -1;
     for (int c = 0; c < 32; c++) {
@@ -145,125 +165,165 @@ __global__ void __launch_bounds__(256, 2) fine_cost_rows(const float *__restrict
         }
     }
     if (best_fit <= 0) return;
-    {
-        const bool fits = nar && l >= g0 && l + n <= g0 + KW;
-        if (nar && !fits) list[atomicAdd(list_count, 1)] = y * W + x;
-        float acc[KW];
+    const bool fits = nar && l >= g0 && l + n <= g0 + KW;
+    if (nar && !fits) list[atomicAdd(list_count, 1)] = y * W + x;
+    float Iref = 0.f;
+    uint64_t cr = 0;
+    if (fits) {
+        const size_t pp = (size_t)(y + pl.P) * pl.Wp + (x + pl.P);
+        Iref = __ldg(views_pad + (size_t)ref * HWp + pp);
+        cr = __ldg(cen_pad + (size_t)ref * HWp + pp);
+        const int npad = (int)min((long long)((n + 3) & ~3), row);
+        for (int j = n; j < npad; j++) cost[o + j] = 0.f;
+    }
+    const int nvalid = min(KW, G - g0);
+    const float d0 = fmaf((float)g0, fstep, dmin), d1 = fmaf((float)(g0 + nvalid - 1), fstep, dmin);
+    if (lane == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(mbar0));
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(mbar0 + 8));
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncwarp();
+    // uniform tile origins of a view (x rounded down to 16 bytes), with one label of slack
+    auto origins = [&](int view, int &xf, int &yf, int &xc, int &yc) {
+        const float a = (float)(view % U - uc), b = (float)(view / U - vc);
+        const float sx0 = a * d0, sx1 = a * d1, sy0 = b * d0, sy1 = b * d1;
+        xf = (x0 + (int)floorf(fminf(sx0, sx1)) - 1 + pl.P) & ~3;
+        yf = y + (int)floorf(fminf(sy0, sy1)) - 1 + pl.P;
+        xc = (x0 + (int)floorf(fminf(sx0, sx1) + 0.5f) - 1 + pl.P) & ~1;
+        yc = y + (int)floorf(fminf(sy0, sy1) + 0.5f) - 1 + pl.P;
+    };
+    const unsigned tx_bytes = (unsigned)(pl.bwf * pl.bhf * 4 + pl.bwc * pl.bhc * 8 + nvalid * 16);
+    auto issue = [&](int view, int st) {
+        if (lane != 0) return;
+        int xf, yf, xc, yc;
+        origins(view, xf, yf, xc, yc);
+        const unsigned mb = mbar0 + 8 * st;
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(mb), "r"(tx_bytes) : "memory");
+        asm volatile("cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];"
+                     ::"r"(smem_u32(wb + pl.o_rf[st])), "l"((unsigned long long)&tm_v), "r"(xf), "r"(yf), "r"(view), "r"(mb)
+                     : "memory");
+        asm volatile("cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];"
+                     ::"r"(smem_u32(wb + pl.o_rc[st])), "l"((unsigned long long)&tm_c), "r"(xc), "r"(yc), "r"(view), "r"(mb)
+                     : "memory");
+        asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+                     ::"r"(smem_u32(wb + pl.o_ts[st])), "l"(tab + (size_t)view * G + g0), "r"(nvalid * 16), "r"(mb)
+                     : "memory");
+    };
+    float acc[KW];
+#pragma unroll
+    for (int i = 0; i < KW; i++) {
+        acc[i] = 0.f;
+        cdiff[i * 32 + lane] = 0;
+    }
+    const int nv = nviews - 1;                      // every view but the reference
+    issue(ref == 0 ? 1 : 0, 0);
+    bool ok = true;
+    for (int vi = 0; vi < nv; vi++) {
+        const int view = vi + (vi >= ref);
+        const int st = vi & 1;
+        if (vi + 1 < nv) issue(vi + 1 + (vi + 1 >= ref), st ^ 1);
+        if (!mbar_wait(mbar0 + 8 * st, (unsigned)(vi >> 1) & 1u)) {
+            if (lane == 0) atomicExch(status, 6);
+            // let the copies still in flight land (bounded) before the warp's shared memory is released
+            if (vi + 1 < nv) mbar_wait(mbar0 + 8 * (st ^ 1), (unsigned)((vi + 1) >> 1) & 1u);
+            ok = false;
+            break;
+        }
+        const float *rf = (const float *)(wb + pl.o_rf[st]);
+        const uint64_t *rc = (const uint64_t *)(wb + pl.o_rc[st]);
+        const int4 *t4 = (const int4 *)(wb + pl.o_ts[st]);
+        int xf, yf, xc, yc;
+        origins(view, xf, yf, xc, yc);
+        const FineTap ta = *(const FineTap *)&t4[0], tb = *(const FineTap *)&t4[nvalid - 1];
+        const int oxlo = min(ta.ox, tb.ox), oxhi = max(ta.ox, tb.ox);
+        const int oylo = min(ta.oy, tb.oy), oyhi = max(ta.oy, tb.oy);
+        const int nxlo = min(ta.nx, tb.nx), nxhi = max(ta.nx, tb.nx);
+        const int nylo = min(ta.ny, tb.ny), nyhi = max(ta.ny, tb.ny);
+        // tile coordinates of the taps / census words of lane 0 at shift (0, 0)
+        const int bxf = x0 + pl.P - xf, byf = y + pl.P - yf, bxc = x0 + pl.P - xc, byc = y + pl.P - yc;
+        const int i1 = min(lane + 32, nvalid - 1);
+        const int4 e0 = t4[min(lane, nvalid - 1)], p0 = t4[min(max(lane - 1, 0), nvalid - 1)];
+        const int4 e1 = t4[i1], p1 = t4[max(i1 - 1, 0)];
+        const unsigned sm0 = __ballot_sync(0xffffffffu, lane == 0 || e0.x != p0.x);
+        const unsigned sm1 = __ballot_sync(0xffffffffu, lane + 32 < nvalid && e1.x != p1.x);
+        const unsigned cm0 = __ballot_sync(0xffffffffu, lane == 0 || e0.y != p0.y);
+        const unsigned cm1 = __ballot_sync(0xffffffffu, lane + 32 < nvalid && e1.y != p1.y);
+        const int nseg = __popc(sm0) + __popc(sm1);
+        if (bxf + oxlo < 0 || bxf + 32 + oxhi >= pl.bwf || byf + oylo < 0 || byf + oyhi + 1 >= pl.bhf ||
+            bxc + nxlo < 0 || bxc + 31 + nxhi >= pl.bwc || byc + nylo < 0 || byc + nyhi >= pl.bhc || nseg > pl.seg_cap) {
+            if (lane == 0) atomicExch(status, 7);      // cannot happen with host-sized boxes
+            __syncwarp();
+            continue;
+        }
+        segoff[lane] = (__popc(sm0 & (0xffffffffu >> (31 - lane))) - 1) * 32;
+        if (lane + 32 < KW) segoff[lane + 32] = (__popc(sm0) + __popc(sm1 & (0xffffffffu >> (31 - lane))) - 1) * 32;
+        // census: integer steps at the census breakpoints
+        {
+            unsigned m0 = cm0, m1 = cm1;
+            int prev = 0;
+            while (m0 | m1) {
+                int i;
+                if (m0) {
+                    i = __ffs(m0) - 1;
+                    m0 &= m0 - 1;
+                } else {
+                    i = 32 + __ffs(m1) - 1;
+                    m1 &= m1 - 1;
+                }
+                const int wy = t4[i].y;
+                const int tnx = (int16_t)(wy & 0xffff), tny = wy >> 16;
+                const int h = __popcll(cr ^ rc[(byc + tny) * pl.bwc + (bxc + lane + tnx)]);
+                cdiff[i * 32 + lane] += h - prev;
+                prev = h;
+            }
+        }
+        // l2 term: per cell segment this lane's sample polynomial in the absolute label index
+        const float ax = (float)(view % U - uc) * fstep, ay = (float)(view / U - vc) * fstep;
+        {
+            unsigned m0 = sm0, m1 = sm1;
+            for (int sgi = 0; sgi < nseg; sgi++) {
+                int i;
+                if (m0) {
+                    i = __ffs(m0) - 1;
+                    m0 &= m0 - 1;
+                } else {
+                    i = 32 + __ffs(m1) - 1;
+                    m1 &= m1 - 1;
+                }
+                const int4 w = t4[i];
+                const int tox = (int16_t)(w.x & 0xffff), toy = w.x >> 16;
+                const float tfx = __int_as_float(w.z), tfy = __int_as_float(w.w);
+                const float *q = rf + (byf + toy) * pl.bwf + (bxf + lane + tox);
+                const float i00 = q[0], i10 = q[1], i01 = q[pl.bwf], i11 = q[pl.bwf + 1];
+                const float c1 = i10 - i00, c2 = i01 - i00, c3 = (i11 - i01) - c1;
+                // s(t) = c0 + c1 fx + c2 fy + c3 fx fy, fx = fx0 + ax t, fy = fy0 + ay t, t = i' - i
+                const float a0 = fmaf(c3 * tfx, tfy, fmaf(c2, tfy, fmaf(c1, tfx, i00)));
+                const float b0 = fmaf(c3, fmaf(tfx, ay, tfy * ax), fmaf(c2, ay, c1 * ax));
+                const float Cq = c3 * ax * ay;
+                const float fi = (float)i;
+                coef[sgi * 32 + lane] = make_float4(fmaf(fi, fmaf(fi, Cq, -b0), a0), fmaf(-2.f * fi, Cq, b0), Cq, 0.f);
+            }
+        }
+        __syncwarp();
 #pragma unroll
         for (int i = 0; i < KW; i++) {
-            acc[i] = 0.f;
-            cdiff[i * 32 + lane] = 0;
+            const float4 k = coef[segoff[i] + lane];
+            const float fi = (float)i;
+            const float smp = fmaf(fi, fmaf(fi, k.z, k.y), k.x);
+            acc[i] = fmaf(wl2, fabsf(Iref - smp), acc[i]);
         }
-        for (int view = 0; view < nviews; view++) {
-            if (view == ref) continue;
-            const FineTap *tv = tab + (size_t)view * G;
-            // table entries of the range (labels past G - 1 repeat the last one and are never stored)
-            for (int i = lane; i < KW; i += 32)
-                reinterpret_cast<int4 *>(ts)[i] = __ldg(reinterpret_cast<const int4 *>(tv + min(g0 + i, G - 1)));
-            __syncwarp();
-            const FineTap ta = ts[0], tb = ts[KW - 1];
-            const int oxlo = min(ta.ox, tb.ox), oxhi = max(ta.ox, tb.ox);
-            const int oylo = min(ta.oy, tb.oy), oyhi = max(ta.oy, tb.oy);
-            const int nxlo = min(ta.nx, tb.nx), nxhi = max(ta.nx, tb.nx);
-            const int nylo = min(ta.ny, tb.ny), nyhi = max(ta.ny, tb.ny);
-            const int rw = 33 + oxhi - oxlo, rh = 2 + oyhi - oylo;
-            const int cw = 32 + nxhi - nxlo, ch = 1 + nyhi - nylo;
-            // breakpoints: where the bilinear cell changes (segments) and where the census position changes
-            const int4 *t4 = reinterpret_cast<const int4 *>(ts);
-            const int i1 = min(lane + 32, KW - 1);
-            const int4 e0 = t4[lane], p0 = t4[lane > 0 ? lane - 1 : 0];
-            const int4 e1 = t4[i1], p1 = t4[i1 - 1];
-            const unsigned sm0 = __ballot_sync(0xffffffffu, lane == 0 || e0.x != p0.x);
-            const unsigned sm1 = __ballot_sync(0xffffffffu, lane + 32 < KW && e1.x != p1.x);
-            const unsigned cm0 = __ballot_sync(0xffffffffu, lane == 0 || e0.y != p0.y);
-            const unsigned cm1 = __ballot_sync(0xffffffffu, lane + 32 < KW && e1.y != p1.y);
-            const int nseg = __popc(sm0) + __popc(sm1);
-            if (rw * rh > rf_cap || cw * ch > rc_cap || nseg > seg_cap) {   // cannot happen with host-sized caps
-                if (lane == 0) atomicExch(status, 7);
-                __syncwarp();
-                continue;
-            }
-            segoff[lane] = (__popc(sm0 & (0xffffffffu >> (31 - lane))) - 1) * 32;
-            if (lane + 32 < KW)
-                segoff[lane + 32] = (__popc(sm0) + __popc(sm1 & (0xffffffffu >> (31 - lane))) - 1) * 32;
-            const float *img = views + (size_t)view * N;
-            const uint64_t *cimg = cen + (size_t)view * N;
-            for (int yy = 0; yy < rh; yy++) {
-                const float *src = img + (size_t)min(max(y + oylo + yy, 0), H - 1) * W;
-                float *dst = rf + yy * rw;
-                for (int xx = lane; xx < rw; xx += 32) dst[xx] = __ldg(src + min(max(x0 + oxlo + xx, 0), W - 1));
-            }
-            for (int yy = 0; yy < ch; yy++) {
-                const uint64_t *src = cimg + (size_t)min(max(y + nylo + yy, 0), H - 1) * W;
-                uint64_t *dst = rc + yy * cw;
-                for (int xx = lane; xx < cw; xx += 32) dst[xx] = __ldg(src + min(max(x0 + nxlo + xx, 0), W - 1));
-            }
-            __syncwarp();
-            // census: a step function of the label, added as integer differences at its breakpoints
-            {
-                unsigned m0 = cm0, m1 = cm1;
-                int prev = 0;
-                while (m0 | m1) {
-                    int i;
-                    if (m0) {
-                        i = __ffs(m0) - 1;
-                        m0 &= m0 - 1;
-                    } else {
-                        i = 32 + __ffs(m1) - 1;
-                        m1 &= m1 - 1;
-                    }
-                    const int wy = t4[i].y;
-                    const int tnx = (int16_t)(wy & 0xffff), tny = wy >> 16;
-                    const int h = __popcll(cr ^ rc[(tny - nylo) * cw + (lane + tnx - nxlo)]);
-                    cdiff[i * 32 + lane] += h - prev;
-                    prev = h;
-                }
-            }
-            // l2 term: per cell segment this lane's sample polynomial in the absolute label index
-            const float ax = (float)(view % U - uc) * fstep, ay = (float)(view / U - vc) * fstep;
-            {
-                unsigned m0 = sm0, m1 = sm1;
-                for (int sgi = 0; sgi < nseg; sgi++) {
-                    int i;
-                    if (m0) {
-                        i = __ffs(m0) - 1;
-                        m0 &= m0 - 1;
-                    } else {
-                        i = 32 + __ffs(m1) - 1;
-                        m1 &= m1 - 1;
-                    }
-                    const int4 w = t4[i];
-                    const int tox = (int16_t)(w.x & 0xffff), toy = w.x >> 16;
-                    const float tfx = __int_as_float(w.z), tfy = __int_as_float(w.w);
-                    const float *q = rf + (toy - oylo) * rw + (lane + tox - oxlo);
-                    const float i00 = q[0], i10 = q[1], i01 = q[rw], i11 = q[rw + 1];
-                    const float c1 = i10 - i00, c2 = i01 - i00, c3 = (i11 - i01) - c1;
-                    // s(t) = c0 + c1 fx + c2 fy + c3 fx fy, fx = fx0 + ax t, fy = fy0 + ay t, t = i' - i
-                    const float a0 = fmaf(c3 * tfx, tfy, fmaf(c2, tfy, fmaf(c1, tfx, i00)));
-                    const float b0 = fmaf(c3, fmaf(tfx, ay, tfy * ax), fmaf(c2, ay, c1 * ax));
-                    const float Cq = c3 * ax * ay;
-                    const float fi = (float)i;
-                    coef[sgi * 32 + lane] = make_float4(fmaf(fi, fmaf(fi, Cq, -b0), a0), fmaf(-2.f * fi, Cq, b0), Cq, 0.f);
-                }
-            }
-            __syncwarp();
+        __syncwarp();
+    }
+    if (!ok) return;
+    if (fits) {
+        int run = 0;
 #pragma unroll
-            for (int i = 0; i < KW; i++) {
-                const float4 k = coef[segoff[i] + lane];
-                const float fi = (float)i;
-                const float smp = fmaf(fi, fmaf(fi, k.z, k.y), k.x);
-                acc[i] = fmaf(wl2, fabsf(Iref - smp), acc[i]);
-            }
-            __syncwarp();
-        }
-        if (fits) {
-            int run = 0;
-#pragma unroll
-            for (int i = 0; i < KW; i++) {
-                run += cdiff[i * 32 + lane];
-                const int g = g0 + i;
-                if (g >= l && g < l + n) cost[o + (g - l)] = fmaf(wc, (float)run, acc[i]);
-            }
+        for (int i = 0; i < KW; i++) {
+            run += cdiff[i * 32 + lane];
+            const int g = g0 + i;
+            if (g >= l && g < l + n) cost[o + (g - l)] = fmaf(wc, (float)run, acc[i]);
         }
     }
 }
@@ -272,7 +332,7 @@ __global__ void __launch_bounds__(256, 2) fine_cost_rows(const float *__restrict
 // one warp per (pixel, chunk of 32 labels), lane = label, the view loop unrolled so that
 // several independent table -> tap load chains are in flight.
 __global__ void __launch_bounds__(256) fine_cost_list(const float *__restrict__ views,
-                                                      const uint64_t *__restrict__ cen,
+                                                      const uint64_t *__restrict__ cen_pad, int P, int Wp, int Hp,
                                                       const FineTap *__restrict__ tab, int G, int nviews,
                                                       int H, int W, int ref, const int *__restrict__ lo,
                                                       const int *__restrict__ cnt,
@@ -281,7 +341,7 @@ __global__ void __launch_bounds__(256) fine_cost_list(const float *__restrict__ 
                                                       const int *__restrict__ count) {
     const int lane = threadIdx.x & 31;
     const int warps = (gridDim.x * blockDim.x) >> 5;
-    const size_t N = (size_t)H * W;
+    const size_t N = (size_t)H * W, HWp = (size_t)Hp * Wp;
     const int chunks = (G + 31) >> 5;
     const long long total = (long long)(*count) * chunks;
     for (long long t = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; t < total; t += warps) {
@@ -294,7 +354,7 @@ __global__ void __launch_bounds__(256) fine_cost_list(const float *__restrict__ 
         if (chunk * 32 >= npad) continue;
         const int x = p % W, y = p / W;
         const float Iref = __ldg(views + (size_t)ref * N + p);
-        const uint64_t cr = __ldg(cen + (size_t)ref * N + p);
+        const uint64_t cr = __ldg(cen_pad + (size_t)ref * HWp + (size_t)(y + P) * Wp + (x + P));
         float sl2 = 0.f;
         int sc = 0;
         if (j < n) {
@@ -313,7 +373,7 @@ __global__ void __launch_bounds__(256) fine_cost_list(const float *__restrict__ 
                 const float smp = (1.f - t.fy) * top + t.fy * bot;
                 sl2 += fabsf(Iref - smp);
                 const int xn = min(max(x + t.nx, 0), W - 1), yn = min(max(y + t.ny, 0), H - 1);
-                sc += __popcll(cr ^ __ldg(cen + (size_t)view * N + (size_t)yn * W + xn));
+                sc += __popcll(cr ^ __ldg(cen_pad + (size_t)view * HWp + (size_t)(yn + P) * Wp + (xn + P)));
             }
         }
         if (j < npad) cost[o + j] = (j < n) ? wl2 * sl2 + wc * (float)sc : 0.f;
@@ -322,51 +382,126 @@ __global__ void __launch_bounds__(256) fine_cost_list(const float *__restrict__ 
 
 constexpr int kRowKW = 36;
 
-}  // namespace
-
-int fine_cost_tiled_caps(int U, int V, int uc, int vc, int G, double dmin, double dmax, int *rf_cap, int *rc_cap,
-                         int *seg_cap) {
-    // the largest integer-shift span of KW consecutive labels, per axis, and the most segments
-    // (every integer and half-integer crossing of either shift starts one)
-    const double step = (dmax - dmin) / (double)(G - 1);
-    const int ax = (uc > U - 1 - uc ? uc : U - 1 - uc), ay = (vc > V - 1 - vc ? vc : V - 1 - vc);
-    const double spx = ax * step * (kRowKW - 1), spy = ay * step * (kRowKW - 1);
-    const int sx = (int)ceil(spx) + 2, sy = (int)ceil(spy) + 2;
-    *rf_cap = ((33 + sx) * (2 + sy) + 3) & ~3;
-    *rc_cap = (32 + sx) * (1 + sy);
-    *seg_cap = 1 + ((int)ceil(spx) + 1) + ((int)ceil(spy) + 1);
-    if (*seg_cap > kRowKW) *seg_cap = kRowKW;
-    return (int)((size_t)*seg_cap * 512 + (size_t)kRowKW * 148 + (size_t)*rc_cap * 8 + (size_t)*rf_cap * 4);
+__global__ void list_all_kernel(int *list, int *count, int N) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < N) list[i] = i;
+    if (i == 0) *count = N;
 }
 
-cudaError_t launch_fine_cost_tiled(cudaStream_t s, const float *views, const uint64_t *cen, const FineTap *tab,
-                                   int G, int U, int V, int H, int W, int ref, const int *lo, const int *cnt,
-                                   const long long *off, float wl2, float wc, float *cost, int *status,
-                                   int *wide_list, int *wide_count, int rf_cap, int rc_cap, int seg_cap,
-                                   float fstep) {
-    const int wpb = 8;
-    const size_t smem = (size_t)wpb * ((size_t)seg_cap * 512 + (size_t)kRowKW * 148 + (size_t)rc_cap * 8 +
-                                       (size_t)rf_cap * 4);
-    cudaError_t e = cudaFuncSetAttribute(fine_cost_rows<kRowKW>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)smem);
+int r128(int x) { return (x + 127) & ~127; }
+
+}  // namespace
+
+// Padding, TMA boxes and the per-warp shared-memory layout of the row kernel for one config.
+bool plan_fine_rows(int U, int V, int uc, int vc, int H, int W, int G, double dmin, double dmax, RowPlanHost *out) {
+    RowPlan pl{};
+    const double md = fmax(fabs(dmin), fabs(dmax));
+    const int amax = max(max(uc, U - 1 - uc), max(vc, V - 1 - vc));
+    pl.P = (int)ceil(amax * md) + 3;
+    pl.Wp = (W + 2 * pl.P + 3) & ~3;
+    pl.Hp = H + 2 * pl.P;
+    const double step = (dmax - dmin) / (double)(G - 1);
+    const int ax = max(uc, U - 1 - uc), ay = max(vc, V - 1 - vc);
+    const int spx = (int)ceil(ax * step * (kRowKW - 1)), spy = (int)ceil(ay * step * (kRowKW - 1));
+    pl.bwf = (33 + spx + 6 + 3) & ~3;
+    pl.bhf = 5 + spy;
+    pl.bwc = (32 + spx + 4 + 1) & ~1;
+    pl.bhc = 4 + spy;
+    pl.seg_cap = min(kRowKW, 2 + spx + spy + 2);
+    int o = 0;
+    pl.o_mbar = o;
+    o += 128;
+    for (int st = 0; st < 2; st++) {
+        pl.o_rf[st] = o;
+        o += r128(pl.bwf * pl.bhf * 4);
+        pl.o_rc[st] = o;
+        o += r128(pl.bwc * pl.bhc * 8);
+        pl.o_ts[st] = o;
+        o += r128(kRowKW * 16);
+    }
+    pl.o_segoff = o;
+    o += r128(kRowKW * 4);
+    pl.o_coef = o;
+    o += pl.seg_cap * 512;
+    pl.o_cdiff = o;
+    o += kRowKW * 128;
+    pl.warp_bytes = o;
+    out->ok = pl.bwf <= 256 && pl.bwc <= 256 && pl.bhf <= 256 && pl.bhc <= 256 && pl.warp_bytes <= 48 * 1024;
+    static_assert(sizeof(RowPlan) <= sizeof(out->raw), "plan storage");
+    memcpy(out->raw, &pl, sizeof(pl));
+    out->P = pl.P;
+    out->Wp = pl.Wp;
+    out->Hp = pl.Hp;
+    return out->ok;
+}
+
+// Tensor maps of the padded views (float) and census words (uint64), 3-D [view][Hp][Wp].
+bool encode_fine_rows_maps(RowPlanHost *ph, const float *views_pad, const uint64_t *cen_pad, int nviews) {
+    RowPlan pl;
+    memcpy(&pl, ph->raw, sizeof(pl));
+    static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
+    if (!encode) {
+        cudaDriverEntryPointQueryResult q;
+        void *fn = nullptr;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+            q != cudaDriverEntryPointSuccess || !fn)
+            return false;
+        encode = (PFN_cuTensorMapEncodeTiled_v12000)fn;
+    }
+    const cuuint32_t estr[3] = {1, 1, 1};
+    {
+        const cuuint64_t dims[3] = {(cuuint64_t)pl.Wp, (cuuint64_t)pl.Hp, (cuuint64_t)nviews};
+        const cuuint64_t strides[2] = {(cuuint64_t)pl.Wp * 4, (cuuint64_t)pl.Wp * pl.Hp * 4};
+        const cuuint32_t box[3] = {(cuuint32_t)pl.bwf, (cuuint32_t)pl.bhf, 1};
+        if (encode((CUtensorMap *)ph->tm_v, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, (void *)views_pad, dims, strides, box,
+                   estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                   CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+            return false;
+    }
+    {
+        const cuuint64_t dims[3] = {(cuuint64_t)pl.Wp, (cuuint64_t)pl.Hp, (cuuint64_t)nviews};
+        const cuuint64_t strides[2] = {(cuuint64_t)pl.Wp * 8, (cuuint64_t)pl.Wp * pl.Hp * 8};
+        const cuuint32_t box[3] = {(cuuint32_t)pl.bwc, (cuuint32_t)pl.bhc, 1};
+        if (encode((CUtensorMap *)ph->tm_c, CU_TENSOR_MAP_DATA_TYPE_UINT64, 3, (void *)cen_pad, dims, strides, box,
+                   estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                   CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+            return false;
+    }
+    return true;
+}
+
+cudaError_t launch_fine_cost_rows(cudaStream_t s, const RowPlanHost *ph, const float *views_pad,
+                                  const uint64_t *cen_pad, const FineTap *tab, int G, int U, int V, int H, int W, int ref,
+                                  const int *lo, const int *cnt, const long long *off, float wl2, float wc, float dmin,
+                                  float fstep, float *cost, int *status, int *list, int *list_count) {
+    RowPlan pl;
+    memcpy(&pl, ph->raw, sizeof(pl));
+    const int wpb = 4;
+    const size_t smem = (size_t)wpb * pl.warp_bytes;
+    cudaError_t e = cudaFuncSetAttribute(fine_cost_rows<kRowKW>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     const long long tasks = (long long)((W + 31) / 32) * H;
     const unsigned grid = (unsigned)((tasks + wpb - 1) / wpb);
-    fine_cost_rows<kRowKW><<<grid, 32 * wpb, smem, s>>>(views, cen, tab, G, U, V, H, W, ref, lo, cnt, off, wl2, wc,
-                                                        fstep, cost, status, wide_list, wide_count, rf_cap, rc_cap,
-                                                        seg_cap);
+    fine_cost_rows<kRowKW><<<grid, 32 * wpb, smem, s>>>(*(const CUtensorMap *)ph->tm_v, *(const CUtensorMap *)ph->tm_c,
+                                                        tab, G, U, V, H, W, ref, lo, cnt, off, views_pad, cen_pad, wl2,
+                                                        wc, dmin, fstep, cost, status, list, list_count, pl);
     return cudaGetLastError();
 }
 
-cudaError_t launch_fine_cost_list(cudaStream_t s, const float *views, const uint64_t *cen, const FineTap *tab,
-                                  int G, int nviews, int H, int W, int ref, const int *lo, const int *cnt,
-                                  const long long *off, float wl2, float wc, float *cost, const int *list,
-                                  const int *count) {
+cudaError_t launch_list_all(cudaStream_t s, int *list, int *count, int N) {
+    list_all_kernel<<<(N + 255) / 256, 256, 0, s>>>(list, count, N);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_fine_cost_list(cudaStream_t s, const float *views, const uint64_t *cen_pad, int P, int Wp, int Hp,
+                                  const FineTap *tab, int G, int nviews, int H, int W, int ref, const int *lo,
+                                  const int *cnt, const long long *off, float wl2, float wc, float *cost,
+                                  const int *list, const int *count) {
     int dev = 0, sms = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    fine_cost_list<<<sms * 8, 256, 0, s>>>(views, cen, tab, G, nviews, H, W, ref, lo, cnt, off, wl2, wc, cost,
-                                           list, count);
+    fine_cost_list<<<sms * 8, 256, 0, s>>>(views, cen_pad, P, Wp, Hp, tab, G, nviews, H, W, ref, lo, cnt, off, wl2, wc,
+                                           cost, list, count);
     return cudaGetLastError();
 }
 

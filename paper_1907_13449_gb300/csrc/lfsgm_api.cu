@@ -63,12 +63,14 @@ struct lfsgm_ctx {
     void *ws = nullptr;
     size_t ws_bytes = 0;
     bool ws_owned = false;
-    uint64_t *cen = nullptr;
     uint16_t *ccost = nullptr;
     uint32_t *csum = nullptr;
     int *maps = nullptr, *F0 = nullptr, *F1 = nullptr, *cntpad = nullptr;
     int *wide_list = nullptr, *wide_count = nullptr;
-    int rf_cap = 0, rc_cap = 0, seg_cap = 0, tiled_warp_bytes = 0;
+    RowPlanHost rows{};                // row-sweep cost kernel plan + tensor maps
+    bool rows_maps = false;            // tensor maps encoded for the bound workspace
+    float *views_pad = nullptr;        // edge-replicated padded copies (workspace)
+    uint64_t *cen_pad = nullptr;
     unsigned long long *armsum = nullptr;
     int *cpen = nullptr;
     float *fpen = nullptr;
@@ -224,7 +226,10 @@ lfsgm_status bind_workspace(lfsgm_ctx *h, void *dptr, size_t bytes, bool owned) 
     const size_t N = (size_t)h->N, A = (size_t)std::max(h->arms.n_arms, 1);
     char *p = (char *)dptr;
     auto take = [&](size_t n) { char *q = p; p += align256(n); return (void *)q; };
-    h->cen = (uint64_t *)take(h->nviews * N * 8);
+    const size_t HWp = (size_t)h->rows.Hp * h->rows.Wp;
+    h->cen_pad = (uint64_t *)take(h->nviews * HWp * 8);
+    h->views_pad = (float *)take(h->nviews * HWp * 4);
+    h->rows_maps = h->rows.ok && encode_fine_rows_maps(&h->rows, h->views_pad, h->cen_pad, h->nviews);
     h->ccost = (uint16_t *)take(A * N * h->Lcs * 2);
     h->csum = (uint32_t *)take(A * N * (h->Lcs / 2) * 4);
     h->maps = (int *)take(4 * N * 4);
@@ -266,8 +271,7 @@ lfsgm_status lfsgm_create(const lfsgm_config *cfg, void *stream, lfsgm_handle *o
     h->ref = c.vc * c.U + c.uc;
     h->nbits = c.census_w * c.census_w - 1;
     h->Lcs = c.coarse_labels <= 64 ? 64 : (c.coarse_labels <= 128 ? 128 : 256);
-    h->tiled_warp_bytes = fine_cost_tiled_caps(c.U, c.V, c.uc, c.vc, c.fine_labels, c.dmin, c.dmax, &h->rf_cap,
-                                               &h->rc_cap, &h->seg_cap);
+    plan_fine_rows(c.U, c.V, c.uc, c.vc, c.H, c.W, c.fine_labels, c.dmin, c.dmax, &h->rows);
     build_arms(h);
     // the packed coarse sums hold 8 paths x (C + P2) per 16-bit half
     const long long cmax = (long long)max_arm_views(h) * h->nbits;
@@ -349,7 +353,9 @@ lfsgm_status lfsgm_workspace_size(lfsgm_handle h, size_t *bytes) {
     if (!h || !bytes) return LFSGM_ERR_INVALID_ARG;
     const size_t N = (size_t)h->N, A = (size_t)std::max(h->arms.n_arms, 1);
     size_t b = 0;
-    b += align256(h->nviews * N * 8);              // census words
+    const size_t HWp = (size_t)h->rows.Hp * h->rows.Wp;
+    b += align256(h->nviews * HWp * 8);            // census words, edge-replicated padding
+    b += align256(h->nviews * HWp * 4);            // views, edge-replicated padding
     b += align256(A * N * h->Lcs * 2);              // coarse cost
     b += align256(A * N * (h->Lcs / 2) * 4);        // packed coarse sums
     b += align256(4 * N * 4);                       // maps
@@ -386,14 +392,16 @@ lfsgm_status lfsgm_initial_disparity(lfsgm_handle h, const float *views, int32_t
     cudaStream_t s = h->stream;
     const int N = h->N, A = h->arms.n_arms;
     LFSGM_TRY(run(h, "census_cross", [&] {
-        return launch_census(s, views, c.H, c.W, c.census_w, h->d_sel_cross, h->n_sel_cross, h->cen);
+        return launch_census_pad(s, views, c.H, c.W, c.census_w, h->rows.P, h->rows.Wp, h->rows.Hp, h->d_sel_cross,
+                                 h->n_sel_cross, h->cen_pad, h->views_pad);
     }));
     cudaError_t e = cudaMemsetAsync(h->armsum, 0, 4 * 8, s);
     if (e == cudaSuccess) e = cudaMemsetAsync(h->csum, 0, (size_t)A * N * (h->Lcs / 2) * 4, s);
     if (e != cudaSuccess) return cuda_fail(h, e, "memset");
     for (int a = 0; a < A; a++) {
         LFSGM_TRY(run(h, "coarse_cost", [&] {
-            return launch_coarse_cost(s, h->cen, c.H, c.W, h->ref, h->d_armviews + a * kMaxArmViews,
+            return launch_coarse_cost(s, h->cen_pad, h->rows.P, h->rows.Wp, h->rows.Hp, c.H, c.W, h->ref,
+                                      h->d_armviews + a * kMaxArmViews,
                                       h->arms.nv[a], h->d_coarse, c.coarse_labels, h->Lcs,
                                       h->ccost + (size_t)a * N * h->Lcs, h->armsum + a);
         }));
@@ -436,27 +444,26 @@ lfsgm_status lfsgm_cost_volume(lfsgm_handle h, const float *views, const int32_t
     const lfsgm_config &c = h->cfg;
     cudaStream_t s = h->stream;
     LFSGM_TRY(run(h, "census_all", [&] {
-        return launch_census(s, views, c.H, c.W, c.census_w, h->d_sel_all, h->nviews, h->cen);
+        return launch_census_pad(s, views, c.H, c.W, c.census_w, h->rows.P, h->rows.Wp, h->rows.Hp, h->d_sel_all,
+                                 h->nviews, h->cen_pad, h->views_pad);
     }));
-    if (h->tiled_warp_bytes > 0 && h->tiled_warp_bytes <= 24 * 1024) {
-        cudaError_t e = cudaMemsetAsync(h->wide_count, 0, 4, s);
-        if (e != cudaSuccess) return cuda_fail(h, e, "memset");
+    const cudaError_t e = cudaMemsetAsync(h->wide_count, 0, 4, s);
+    if (e != cudaSuccess) return cuda_fail(h, e, "memset");
+    const float fstep = (float)((c.dmax - c.dmin) / (double)(c.fine_labels - 1));
+    if (h->rows_maps) {
         LFSGM_TRY(run(h, "fine_cost", [&] {
-            return launch_fine_cost_tiled(s, views, h->cen, h->d_fine, c.fine_labels, c.U, c.V, c.H, c.W, h->ref, lo,
-                                          cnt, (const long long *)off, c.w_l2, c.w_census, cost, h->status,
-                                          h->wide_list, h->wide_count, h->rf_cap, h->rc_cap, h->seg_cap,
-                                          (float)((c.dmax - c.dmin) / (double)(c.fine_labels - 1)));
+            return launch_fine_cost_rows(s, &h->rows, h->views_pad, h->cen_pad, h->d_fine, c.fine_labels, c.U, c.V,
+                                         c.H, c.W, h->ref, lo, cnt, (const long long *)off, c.w_l2, c.w_census,
+                                         (float)c.dmin, fstep, cost, h->status, h->wide_list, h->wide_count);
         }));
-        LFSGM_TRY(run(h, "fine_cost_wide", [&] {
-            return launch_fine_cost_list(s, views, h->cen, h->d_fine, c.fine_labels, h->nviews, c.H, c.W, h->ref, lo,
-                                         cnt, (const long long *)off, c.w_l2, c.w_census, cost, h->wide_list,
-                                         h->wide_count);
-        }));
-        return LFSGM_OK;
+    } else {
+        // shapes whose row tiles do not fit the TMA boxes: every pixel through the list kernel
+        LFSGM_TRY(run(h, "fine_cost_all_list", [&] { return launch_list_all(s, h->wide_list, h->wide_count, h->N); }));
     }
-    LFSGM_TRY(run(h, "fine_cost", [&] {
-        return launch_fine_cost(s, views, h->cen, h->d_fine, c.fine_labels, h->nviews, c.H, c.W, h->ref, lo, cnt,
-                                (const long long *)off, c.w_l2, c.w_census, cost, h->status);
+    LFSGM_TRY(run(h, "fine_cost_wide", [&] {
+        return launch_fine_cost_list(s, views, h->cen_pad, h->rows.P, h->rows.Wp, h->rows.Hp, h->d_fine, c.fine_labels,
+                                     h->nviews, c.H, c.W, h->ref, lo, cnt, (const long long *)off, c.w_l2, c.w_census,
+                                     cost, h->wide_list, h->wide_count);
     }));
     return LFSGM_OK;
 }

@@ -100,7 +100,7 @@ struct ArmList {
 cudaError_t launch_census(cudaStream_t s, const float *views, int H, int W, int census_w,
                           const int *d_sel, int nsel, uint64_t *cen);
 
-cudaError_t launch_coarse_cost(cudaStream_t s, const uint64_t *cen, int H, int W, int ref,
+cudaError_t launch_coarse_cost(cudaStream_t s, const uint64_t *cen_pad, int P, int Wp, int Hp, int H, int W, int ref,
                                const int *d_views, int nv, const short2 *ctab, int Lc, int Lcs,
                                uint16_t *out, unsigned long long *sum);
 cudaError_t launch_coarse_penalties(cudaStream_t s, const unsigned long long *sums, int narms,
@@ -125,17 +125,27 @@ cudaError_t launch_fine_cost(cudaStream_t s, const float *views, const uint64_t 
                              const int *lo, const int *cnt, const long long *off, float wl2,
                              float wc, float *cost, int *status);
 
-// Tiled cost volume (narrow windows) + list kernel (wide windows).  fine_cost_tiled_caps
-// returns the shared memory per warp and the region capacities for this configuration.
-int fine_cost_tiled_caps(int U, int V, int uc, int vc, int G, double dmin, double dmax, int *rf_cap,
-                         int *rc_cap, int *seg_cap);
-cudaError_t launch_fine_cost_tiled(cudaStream_t s, const float *views, const uint64_t *cen,
-                                   const FineTap *tab, int G, int U, int V, int H, int W, int ref,
-                                   const int *lo, const int *cnt, const long long *off, float wl2,
-                                   float wc, float *cost, int *status, int *wide_list, int *wide_count,
-                                   int rf_cap, int rc_cap, int seg_cap, float fstep);
-cudaError_t launch_fine_cost_list(cudaStream_t s, const float *views, const uint64_t *cen,
-                                  const FineTap *tab, int G, int nviews, int H, int W, int ref,
+// Row-sweep cost volume (regular windows, TMA-staged from padded copies of the views and census
+// words) + per-pixel list kernel (windows that do not fit a row's label range).
+struct RowPlanHost {
+    alignas(64) unsigned char tm_v[128];   // CUtensorMap of the padded views
+    alignas(64) unsigned char tm_c[128];   // CUtensorMap of the padded census words
+    unsigned char raw[128];                // kernel-side plan
+    bool ok;
+    int P, Wp, Hp;                         // padding and padded sizes
+};
+bool plan_fine_rows(int U, int V, int uc, int vc, int H, int W, int G, double dmin, double dmax, RowPlanHost *out);
+bool encode_fine_rows_maps(RowPlanHost *ph, const float *views_pad, const uint64_t *cen_pad, int nviews);
+cudaError_t launch_census_pad(cudaStream_t s, const float *views, int H, int W, int census_w, int P, int Wp,
+                              int Hp, const int *d_sel, int nsel, uint64_t *cen_pad, float *views_pad);
+cudaError_t launch_fine_cost_rows(cudaStream_t s, const RowPlanHost *ph, const float *views_pad,
+                                  const uint64_t *cen_pad, const FineTap *tab, int G, int U, int V, int H,
+                                  int W, int ref, const int *lo, const int *cnt, const long long *off,
+                                  float wl2, float wc, float dmin, float fstep, float *cost, int *status,
+                                  int *list, int *list_count);
+cudaError_t launch_list_all(cudaStream_t s, int *list, int *count, int N);
+cudaError_t launch_fine_cost_list(cudaStream_t s, const float *views, const uint64_t *cen_pad, int P, int Wp,
+                                  int Hp, const FineTap *tab, int G, int nviews, int H, int W, int ref,
                                   const int *lo, const int *cnt, const long long *off, float wl2,
                                   float wc, float *cost, const int *list, const int *count);
 
