@@ -97,7 +97,7 @@ struct RowPlan {
     int P, Wp, Hp;                    // padding and padded sizes
     int bwf, bhf, bwc, bhc;           // TMA boxes (elements): view values, census words
     int seg_cap;
-    int o_rf[2], o_rc[2], o_ts[2];    // byte offsets of the stage buffers in a warp's slice
+    int o_rf, o_rc, o_ts, stage;      // byte offsets of stage 0's buffers in a warp's slice; stage 1 at +stage
     int o_segoff, o_coef, o_cdiff, o_mbar, warp_bytes;
 };
 
@@ -113,8 +113,16 @@ __device__ __forceinline__ bool mbar_wait(unsigned mbar, unsigned parity) {
     return false;
 }
 
+// Append (pixel, chunk of 32 labels) work items for a window of n labels (rounded up to whole
+// 4-slot groups, which the list kernel pads with zeros).
+__device__ __forceinline__ void push_chunks(int2 *list, int *count, int p, int n) {
+    const int nch = (n + 31) >> 5;
+    const int k = atomicAdd(count, nch);
+    for (int c = 0; c < nch; c++) list[k + c] = make_int2(p, c);
+}
+
 template <int KW>
-__global__ void __launch_bounds__(128, 3) fine_cost_rows(const __grid_constant__ CUtensorMap tm_v,
+__global__ void __launch_bounds__(128, 4) fine_cost_rows(const __grid_constant__ CUtensorMap tm_v,
                                                          const __grid_constant__ CUtensorMap tm_c,
                                                          const FineTap *__restrict__ tab, int G, int U, int V,
                                                          int H, int W, int ref, const int *__restrict__ lo,
@@ -123,15 +131,17 @@ __global__ void __launch_bounds__(128, 3) fine_cost_rows(const __grid_constant__
                                                          const float *__restrict__ views_pad,
                                                          const uint64_t *__restrict__ cen_pad, float wl2, float wc,
                                                          float dmin, float fstep, float *__restrict__ cost,
-                                                         int *__restrict__ status, int *__restrict__ list,
+                                                         int *__restrict__ status, int2 *__restrict__ list,
                                                          int *__restrict__ list_count, RowPlan pl) {
     static_assert(KW > 32 && KW <= 64, "two 32-bit masks cover the label range");
     extern __shared__ __align__(128) unsigned char smem[];
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5, wpb = blockDim.x >> 5;
     unsigned char *wb = smem + (size_t)wib * pl.warp_bytes;
     int *segoff = (int *)(wb + pl.o_segoff);
-    float4 *coef = (float4 *)(wb + pl.o_coef);
-    int *cdiff = (int *)(wb + pl.o_cdiff);
+    float *cA = (float *)(wb + pl.o_coef);                  // [seg_cap][32] polynomial coefficients
+    float *cB = cA + pl.seg_cap * 32;
+    float *cC = cB + pl.seg_cap * 32;
+    short *cdiff = (short *)(wb + pl.o_cdiff);              // [KW][32] census steps (|sum| <= views x 48)
     const unsigned mbar0 = smem_u32(wb + pl.o_mbar);
     const int nviews = U * V, uc = ref % U, vc = ref / U;
     const size_t HWp = (size_t)pl.Hp * pl.Wp;
@@ -150,7 +160,7 @@ __global__ void __launch_bounds__(128, 3) fine_cost_rows(const __grid_constant__
         row = __ldg(off + p + 1) - o;
         if (window_ok(l, n, G, row, status)) {
             if (n <= 32) nar = true;
-            else list[atomicAdd(list_count, 1)] = p;
+            else push_chunks(list, list_count, p, n);
         }
     }
     // the label range covering the most windows (ties: the lowest start); the others go to the list
@@ -166,7 +176,7 @@ __global__ void __launch_bounds__(128, 3) fine_cost_rows(const __grid_constant__
     }
     if (best_fit <= 0) return;
     const bool fits = nar && l >= g0 && l + n <= g0 + KW;
-    if (nar && !fits) list[atomicAdd(list_count, 1)] = y * W + x;
+    if (nar && !fits) push_chunks(list, list_count, y * W + x, n);
     float Iref = 0.f;
     uint64_t cr = 0;
     if (fits) {
@@ -202,13 +212,13 @@ __global__ void __launch_bounds__(128, 3) fine_cost_rows(const __grid_constant__
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(mb), "r"(tx_bytes) : "memory");
         asm volatile("cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];"
-                     ::"r"(smem_u32(wb + pl.o_rf[st])), "l"((unsigned long long)&tm_v), "r"(xf), "r"(yf), "r"(view), "r"(mb)
+                     ::"r"(smem_u32(wb + pl.o_rf + st * pl.stage)), "l"((unsigned long long)&tm_v), "r"(xf), "r"(yf), "r"(view), "r"(mb)
                      : "memory");
         asm volatile("cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];"
-                     ::"r"(smem_u32(wb + pl.o_rc[st])), "l"((unsigned long long)&tm_c), "r"(xc), "r"(yc), "r"(view), "r"(mb)
+                     ::"r"(smem_u32(wb + pl.o_rc + st * pl.stage)), "l"((unsigned long long)&tm_c), "r"(xc), "r"(yc), "r"(view), "r"(mb)
                      : "memory");
         asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
-                     ::"r"(smem_u32(wb + pl.o_ts[st])), "l"(tab + (size_t)view * G + g0), "r"(nvalid * 16), "r"(mb)
+                     ::"r"(smem_u32(wb + pl.o_ts + st * pl.stage)), "l"(tab + (size_t)view * G + g0), "r"(nvalid * 16), "r"(mb)
                      : "memory");
     };
     float acc[KW];
@@ -231,9 +241,9 @@ __global__ void __launch_bounds__(128, 3) fine_cost_rows(const __grid_constant__
             ok = false;
             break;
         }
-        const float *rf = (const float *)(wb + pl.o_rf[st]);
-        const uint64_t *rc = (const uint64_t *)(wb + pl.o_rc[st]);
-        const int4 *t4 = (const int4 *)(wb + pl.o_ts[st]);
+        const float *rf = (const float *)(wb + pl.o_rf + st * pl.stage);
+        const uint64_t *rc = (const uint64_t *)(wb + pl.o_rc + st * pl.stage);
+        const int4 *t4 = (const int4 *)(wb + pl.o_ts + st * pl.stage);
         int xf, yf, xc, yc;
         origins(view, xf, yf, xc, yc);
         const FineTap ta = *(const FineTap *)&t4[0], tb = *(const FineTap *)&t4[nvalid - 1];
@@ -275,7 +285,7 @@ __global__ void __launch_bounds__(128, 3) fine_cost_rows(const __grid_constant__
                 const int wy = t4[i].y;
                 const int tnx = (int16_t)(wy & 0xffff), tny = wy >> 16;
                 const int h = __popcll(cr ^ rc[(byc + tny) * pl.bwc + (bxc + lane + tnx)]);
-                cdiff[i * 32 + lane] += h - prev;
+                cdiff[i * 32 + lane] += (short)(h - prev);
                 prev = h;
             }
         }
@@ -303,15 +313,17 @@ __global__ void __launch_bounds__(128, 3) fine_cost_rows(const __grid_constant__
                 const float b0 = fmaf(c3, fmaf(tfx, ay, tfy * ax), fmaf(c2, ay, c1 * ax));
                 const float Cq = c3 * ax * ay;
                 const float fi = (float)i;
-                coef[sgi * 32 + lane] = make_float4(fmaf(fi, fmaf(fi, Cq, -b0), a0), fmaf(-2.f * fi, Cq, b0), Cq, 0.f);
+                cA[sgi * 32 + lane] = fmaf(fi, fmaf(fi, Cq, -b0), a0);
+                cB[sgi * 32 + lane] = fmaf(-2.f * fi, Cq, b0);
+                cC[sgi * 32 + lane] = Cq;
             }
         }
         __syncwarp();
 #pragma unroll
         for (int i = 0; i < KW; i++) {
-            const float4 k = coef[segoff[i] + lane];
+            const int so = segoff[i] + lane;
             const float fi = (float)i;
-            const float smp = fmaf(fi, fmaf(fi, k.z, k.y), k.x);
+            const float smp = fmaf(fi, fmaf(fi, cC[so], cB[so]), cA[so]);
             acc[i] = fmaf(wl2, fabsf(Iref - smp), acc[i]);
         }
         __syncwarp();
@@ -328,33 +340,34 @@ __global__ void __launch_bounds__(128, 3) fine_cost_rows(const __grid_constant__
     }
 }
 
-// The per-pixel form over a list of pixels (the whole-range windows left by fine_cost_rows):
-// one warp per (pixel, chunk of 32 labels), lane = label, the view loop unrolled so that
-// several independent table -> tap load chains are in flight.
-__global__ void __launch_bounds__(256) fine_cost_list(const float *__restrict__ views,
+// The per-pixel form over a list of (pixel, chunk) items (the windows left by fine_cost_rows):
+// one warp per item, lane = label of the chunk, taps read from the padded views and census words
+// (no clamping needed), the view loop unrolled so that several independent table -> tap load
+// chains are in flight.
+__global__ void __launch_bounds__(256) fine_cost_list(const float *__restrict__ views_pad,
                                                       const uint64_t *__restrict__ cen_pad, int P, int Wp, int Hp,
                                                       const FineTap *__restrict__ tab, int G, int nviews,
                                                       int H, int W, int ref, const int *__restrict__ lo,
                                                       const int *__restrict__ cnt,
                                                       const long long *__restrict__ off, float wl2, float wc,
-                                                      float *__restrict__ cost, const int *__restrict__ list,
+                                                      float *__restrict__ cost, const int2 *__restrict__ list,
                                                       const int *__restrict__ count) {
     const int lane = threadIdx.x & 31;
     const int warps = (gridDim.x * blockDim.x) >> 5;
-    const size_t N = (size_t)H * W, HWp = (size_t)Hp * Wp;
-    const int chunks = (G + 31) >> 5;
-    const long long total = (long long)(*count) * chunks;
-    for (long long t = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; t < total; t += warps) {
-        const int p = list[t / chunks];
-        const int chunk = (int)(t % chunks);
+    const size_t HWp = (size_t)Hp * Wp;
+    const int total = *count;
+    for (int t = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; t < total; t += warps) {
+        const int2 item = list[t];
+        const int p = item.x, chunk = item.y;
         const int l0 = __ldg(lo + p), n = __ldg(cnt + p);
         const long long o = __ldg(off + p), row = __ldg(off + p + 1) - o;
+        if (!window_ok(l0, n, G, row, nullptr)) continue;      // items are pushed for valid windows only
         const int npad = (int)min((long long)((n + 3) & ~3), row);
         const int j = chunk * 32 + lane;
-        if (chunk * 32 >= npad) continue;
         const int x = p % W, y = p / W;
-        const float Iref = __ldg(views + (size_t)ref * N + p);
-        const uint64_t cr = __ldg(cen_pad + (size_t)ref * HWp + (size_t)(y + P) * Wp + (x + P));
+        const size_t base = (size_t)(y + P) * Wp + (x + P);
+        const float Iref = __ldg(views_pad + (size_t)ref * HWp + base);
+        const uint64_t cr = __ldg(cen_pad + (size_t)ref * HWp + base);
         float sl2 = 0.f;
         int sc = 0;
         if (j < n) {
@@ -363,17 +376,14 @@ __global__ void __launch_bounds__(256) fine_cost_list(const float *__restrict__ 
             for (int vi = 0; vi < nviews - 1; vi++) {
                 const int view = vi + (vi >= ref);
                 const FineTap t = load_tap(tab + (size_t)view * G + g);
-                const float *I = views + (size_t)view * N;
-                const int x0 = min(max(x + t.ox, 0), W - 1), x1 = min(max(x + t.ox + 1, 0), W - 1);
-                const int y0 = min(max(y + t.oy, 0), H - 1), y1 = min(max(y + t.oy + 1, 0), H - 1);
-                const float i00 = __ldg(I + (size_t)y0 * W + x0), i10 = __ldg(I + (size_t)y0 * W + x1);
-                const float i01 = __ldg(I + (size_t)y1 * W + x0), i11 = __ldg(I + (size_t)y1 * W + x1);
+                const float *I = views_pad + (size_t)view * HWp + base;
+                const float *q = I + (ptrdiff_t)t.oy * Wp + t.ox;
+                const float i00 = __ldg(q), i10 = __ldg(q + 1), i01 = __ldg(q + Wp), i11 = __ldg(q + Wp + 1);
                 const float top = (1.f - t.fx) * i00 + t.fx * i10;
                 const float bot = (1.f - t.fx) * i01 + t.fx * i11;
                 const float smp = (1.f - t.fy) * top + t.fy * bot;
                 sl2 += fabsf(Iref - smp);
-                const int xn = min(max(x + t.nx, 0), W - 1), yn = min(max(y + t.ny, 0), H - 1);
-                sc += __popcll(cr ^ __ldg(cen_pad + (size_t)view * HWp + (size_t)(yn + P) * Wp + (xn + P)));
+                sc += __popcll(cr ^ __ldg(cen_pad + (size_t)view * HWp + base + (ptrdiff_t)t.ny * Wp + t.nx));
             }
         }
         if (j < npad) cost[o + j] = (j < n) ? wl2 * sl2 + wc * (float)sc : 0.f;
@@ -382,10 +392,11 @@ __global__ void __launch_bounds__(256) fine_cost_list(const float *__restrict__ 
 
 constexpr int kRowKW = 36;
 
-__global__ void list_all_kernel(int *list, int *count, int N) {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < N) list[i] = i;
-    if (i == 0) *count = N;
+__global__ void list_all_kernel(const int *__restrict__ lo, const int *__restrict__ cnt,
+                                const long long *__restrict__ off, int G, int2 *list, int *count, int N,
+                                int *status) {
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p < N && window_ok(lo[p], cnt[p], G, off[p + 1] - off[p], status)) push_chunks(list, count, p, cnt[p]);
 }
 
 int r128(int x) { return (x + 127) & ~127; }
@@ -403,28 +414,27 @@ bool plan_fine_rows(int U, int V, int uc, int vc, int H, int W, int G, double dm
     const double step = (dmax - dmin) / (double)(G - 1);
     const int ax = max(uc, U - 1 - uc), ay = max(vc, V - 1 - vc);
     const int spx = (int)ceil(ax * step * (kRowKW - 1)), spy = (int)ceil(ay * step * (kRowKW - 1));
-    pl.bwf = (33 + spx + 6 + 3) & ~3;
-    pl.bhf = 5 + spy;
-    pl.bwc = (32 + spx + 4 + 1) & ~1;
-    pl.bhc = 4 + spy;
-    pl.seg_cap = min(kRowKW, 2 + spx + spy + 2);
+    // taps: columns x0+oxlo .. x0+32+oxhi, rows y+oylo .. y+oyhi+1, with oxhi-oxlo <= spx, one label of
+    // slack below the FP32 origin estimate and up to 3 (floats) / 1 (words) columns of 16-byte rounding
+    pl.bwf = (spx + 38 + 3) & ~3;
+    pl.bhf = spy + 4;
+    pl.bwc = (spx + 35 + 1) & ~1;
+    pl.bhc = spy + 3;
+    pl.seg_cap = min(kRowKW, spx + spy + 3);
     int o = 0;
     pl.o_mbar = o;
     o += 128;
-    for (int st = 0; st < 2; st++) {
-        pl.o_rf[st] = o;
-        o += r128(pl.bwf * pl.bhf * 4);
-        pl.o_rc[st] = o;
-        o += r128(pl.bwc * pl.bhc * 8);
-        pl.o_ts[st] = o;
-        o += r128(kRowKW * 16);
-    }
+    pl.o_rf = o;
+    pl.o_rc = pl.o_rf + r128(pl.bwf * pl.bhf * 4);
+    pl.o_ts = pl.o_rc + r128(pl.bwc * pl.bhc * 8);
+    pl.stage = pl.o_ts + r128(kRowKW * 16) - pl.o_rf;
+    o = pl.o_rf + 2 * pl.stage;
     pl.o_segoff = o;
     o += r128(kRowKW * 4);
     pl.o_coef = o;
-    o += pl.seg_cap * 512;
+    o += r128(pl.seg_cap * 3 * 128);
     pl.o_cdiff = o;
-    o += kRowKW * 128;
+    o += r128(kRowKW * 64);
     pl.warp_bytes = o;
     out->ok = pl.bwf <= 256 && pl.bwc <= 256 && pl.bhf <= 256 && pl.bhc <= 256 && pl.warp_bytes <= 48 * 1024;
     static_assert(sizeof(RowPlan) <= sizeof(out->raw), "plan storage");
@@ -473,7 +483,7 @@ bool encode_fine_rows_maps(RowPlanHost *ph, const float *views_pad, const uint64
 cudaError_t launch_fine_cost_rows(cudaStream_t s, const RowPlanHost *ph, const float *views_pad,
                                   const uint64_t *cen_pad, const FineTap *tab, int G, int U, int V, int H, int W, int ref,
                                   const int *lo, const int *cnt, const long long *off, float wl2, float wc, float dmin,
-                                  float fstep, float *cost, int *status, int *list, int *list_count) {
+                                  float fstep, float *cost, int *status, int2 *list, int *list_count) {
     RowPlan pl;
     memcpy(&pl, ph->raw, sizeof(pl));
     const int wpb = 4;
@@ -488,20 +498,21 @@ cudaError_t launch_fine_cost_rows(cudaStream_t s, const RowPlanHost *ph, const f
     return cudaGetLastError();
 }
 
-cudaError_t launch_list_all(cudaStream_t s, int *list, int *count, int N) {
-    list_all_kernel<<<(N + 255) / 256, 256, 0, s>>>(list, count, N);
+cudaError_t launch_list_all(cudaStream_t s, const int *lo, const int *cnt, const long long *off, int G, int2 *list,
+                            int *count, int N, int *status) {
+    list_all_kernel<<<(N + 255) / 256, 256, 0, s>>>(lo, cnt, off, G, list, count, N, status);
     return cudaGetLastError();
 }
 
-cudaError_t launch_fine_cost_list(cudaStream_t s, const float *views, const uint64_t *cen_pad, int P, int Wp, int Hp,
-                                  const FineTap *tab, int G, int nviews, int H, int W, int ref, const int *lo,
+cudaError_t launch_fine_cost_list(cudaStream_t s, const float *views_pad, const uint64_t *cen_pad, int P, int Wp,
+                                  int Hp, const FineTap *tab, int G, int nviews, int H, int W, int ref, const int *lo,
                                   const int *cnt, const long long *off, float wl2, float wc, float *cost,
-                                  const int *list, const int *count) {
+                                  const int2 *list, const int *count) {
     int dev = 0, sms = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    fine_cost_list<<<sms * 8, 256, 0, s>>>(views, cen_pad, P, Wp, Hp, tab, G, nviews, H, W, ref, lo, cnt, off, wl2, wc,
-                                           cost, list, count);
+    fine_cost_list<<<sms * 8, 256, 0, s>>>(views_pad, cen_pad, P, Wp, Hp, tab, G, nviews, H, W, ref, lo, cnt, off,
+                                           wl2, wc, cost, list, count);
     return cudaGetLastError();
 }
 

@@ -1,10 +1,12 @@
 // k_sgm.cu -- bounded 8-path SGM on the windowed fine cost (Sec. III-E with Eq. 8-9).
 //
-// One warp per (direction, scanline).  Lane j owns slot j of the current pixel's window
-// (chunks of 32 for wide windows).  The predecessor's path costs L' sit in a per-warp
-// shared-memory buffer indexed by the predecessor's slot, so the ragged-window alignment
-// (slot i = lo(p) + j - lo(p-r)) is a plain indexed read with bounds checks: labels outside
-// the predecessor's window are absent from the minimum (Sec. III-E).  The step is the
+// One warp per (direction, scanline).  Lane j owns slot j of the current pixel's window.
+// When this window and the predecessor's are both at most 32 labels wide (the regular case),
+// the predecessor's path costs L' stay in registers, one slot per lane, and the ragged-window
+// alignment (slot i = lo(p) + j - lo(p-r)) is three shuffles with bounds checks: labels outside
+// the predecessor's window are absent from the minimum (Sec. III-E).  Wider windows take the
+// general form with L' in a per-warp shared-memory row (chunks of 32 slots).  Window metadata
+// is fetched 32 pixels at a time (one per lane) and the next cost row one step ahead.  The step is the
 // normalised recurrence
 //   L(p,g) = C(p,g) + (min(L'(g), L'(g-1)+P1, L'(g+1)+P1, m+P2) - m),   m = min L',
 // and the predecessor minimum m is one redux.sync.min.f32 per pixel.  The 8 directions run
@@ -41,56 +43,114 @@ __global__ void __launch_bounds__(32 * kSgmWarps) fine_sgm_kernel(const float *_
     while (gw >= st.cum[r + 1]) r++;
     const int s = gw - st.cum[r];
     const int dx = dir_dx(r), dy = dir_dy(r);
-    int x, y;
-    scan_start(r, s, H, W, x, y);
-    float *bufA = sm + (size_t)wib * 2 * Gs;
-    float *bufB = bufA + Gs;
+    int x0, y0;
+    scan_start(r, s, H, W, x0, y0);
+    const int lx = dx > 0 ? W - x0 : (dx < 0 ? x0 + 1 : 0x7fffffff);
+    const int ly = dy > 0 ? H - y0 : (dy < 0 ? y0 + 1 : 0x7fffffff);
+    const int len = min(lx, ly);
+    float *bufA = sm + (size_t)wib * 2 * Gs;   // predecessor's path costs (by slot)
+    float *bufB = bufA + Gs;                   // this pixel's
     const float P1 = __ldg(pen), P2 = __ldg(pen + 1);
-    int plo = 0, pcnt = 0;
-    float m = 0.f;
-    bool first = true;
-    while (x >= 0 && x < W && y >= 0 && y < H) {
-        const int p = y * W + x;
-        int l = __ldg(lo + p), n = __ldg(cnt + p);
-        const long long o = __ldg(off + p);
-        if (!window_ok(l, n, G, __ldg(off + p + 1) - o, status)) {
-            l = 0;      // an invalid window takes no part: the path restarts after it
-            n = 0;
-            first = true;
+    const float INF = __int_as_float(0x7f800000);
+    // window metadata of the 32 pixels starting at step k0, one pixel per lane: (lo | cnt << 16)
+    // with cnt = 0 for an invalid window, and the row offset in units of 4 slots
+    int mwin = 0, mofs = 0;
+    auto prefetch = [&](int k0) {
+        const int k = k0 + lane;
+        mwin = 0;
+        if (k < len) {
+            const int p = (y0 + k * dy) * W + (x0 + k * dx);
+            const int l_ = __ldg(lo + p), n_ = __ldg(cnt + p);
+            const long long o_ = __ldg(off + p);
+            if (window_ok(l_, n_, G, __ldg(off + p + 1) - o_, status) && (o_ & 3) == 0 && (o_ >> 2) < 0x7fffffff) {
+                mwin = l_ | (n_ << 16);
+                mofs = (int)(o_ >> 2);
+            } else if ((o_ & 3) != 0 && status) {
+                atomicExch(status, 7);
+            }
         }
-        float lmin = __int_as_float(0x7f800000);
-        for (int j = lane; j < n; j += 32) {
-            const float c = __ldg(cost + o + j);
-            float Lv;
-            if (first) {
-                Lv = c;
-            } else {
-                const int i = l + j - plo;
+    };
+    prefetch(0);
+    int win = __shfl_sync(0xffffffffu, mwin, 0), ofs = __shfl_sync(0xffffffffu, mofs, 0);
+    int l = win & 0xffff, n = win >> 16;
+    float c = (n <= 32 && lane < n) ? __ldg(cost + 4ll * ofs + lane) : 0.f;
+    int plo = 0, pn = 0;
+    float prev = INF, m = 0.f;
+    bool first = true;
+    for (int k = 0; k < len; k++) {
+        // metadata and (narrow) cost row of the next pixel, fetched before this step's work
+        int win1 = 0, ofs1 = 0;
+        float c1 = 0.f;
+        if (k + 1 < len) {
+            if (((k + 1) & 31) == 0) prefetch(k + 1);
+            win1 = __shfl_sync(0xffffffffu, mwin, (k + 1) & 31);
+            ofs1 = __shfl_sync(0xffffffffu, mofs, (k + 1) & 31);
+            const int n1 = win1 >> 16;
+            if (n1 <= 32 && lane < n1) c1 = __ldg(cost + 4ll * ofs1 + lane);
+        }
+        const long long o = 4ll * ofs;
+        if (n == 0) {
+            first = true;      // an invalid window takes no part: the path restarts after it
+        } else if (n <= 32 && (first || pn <= 32)) {
+            // narrow step: the predecessor's costs are in registers, one slot per lane
+            float Lv = c;
+            if (!first) {
+                const int s0 = lane + (l - plo);                 // slot of this label in the predecessor
+                const float v0 = __shfl_sync(0xffffffffu, prev, s0 & 31);
+                const float vm = __shfl_sync(0xffffffffu, prev, (s0 - 1) & 31);
+                const float vp = __shfl_sync(0xffffffffu, prev, (s0 + 1) & 31);
                 float t = m + P2;
-                if (i >= 0 && i < pcnt) t = fminf(t, bufA[i]);
-                if (i >= 1 && i - 1 < pcnt) t = fminf(t, bufA[i - 1] + P1);
-                if (i + 1 >= 0 && i + 1 < pcnt) t = fminf(t, bufA[i + 1] + P1);
+                if ((unsigned)s0 < (unsigned)pn) t = fminf(t, v0);
+                if ((unsigned)(s0 - 1) < (unsigned)pn) t = fminf(t, vm + P1);
+                if ((unsigned)(s0 + 1) < (unsigned)pn) t = fminf(t, vp + P1);
                 Lv = c + (t - m);
             }
-            bufB[j] = Lv;
-            lmin = fminf(lmin, Lv);
-            atomicAdd(agg + o + j, Lv);
+            const bool act = lane < n;
+            if (act) {
+                atomicAdd(agg + o + lane, Lv);
+                bufB[lane] = Lv;
+            }
+            prev = act ? Lv : INF;
+            m = warp_min(prev);
+            first = false;
+        } else {
+            // general step (a window wider than 32 labels on either side): costs by slot in shared memory
+            float lmin = INF;
+            for (int j = lane; j < n; j += 32) {
+                const float cc = __ldg(cost + o + j);
+                float Lv;
+                if (first) {
+                    Lv = cc;
+                } else {
+                    const int i = l + j - plo;
+                    float t = m + P2;
+                    if ((unsigned)i < (unsigned)pn) t = fminf(t, bufA[i]);
+                    if ((unsigned)(i - 1) < (unsigned)pn) t = fminf(t, bufA[i - 1] + P1);
+                    if ((unsigned)(i + 1) < (unsigned)pn) t = fminf(t, bufA[i + 1] + P1);
+                    Lv = cc + (t - m);
+                }
+                bufB[j] = Lv;
+                lmin = fminf(lmin, Lv);
+                atomicAdd(agg + o + j, Lv);
+            }
+            m = warp_min(lmin);
+            __syncwarp();
+            prev = (lane < n) ? bufB[lane] : INF;     // for a following narrow step
+            first = false;
         }
-        m = warp_min(lmin);
         __syncwarp();
-        if (n == 0) {
-            x += dx;
-            y += dy;
-            continue;
+        if (n != 0) {
+            float *tmp = bufA;
+            bufA = bufB;
+            bufB = tmp;
+            plo = l;
+            pn = n;
         }
-        float *tmp = bufA;
-        bufA = bufB;
-        bufB = tmp;
-        plo = l;
-        pcnt = n;
-        first = false;
-        x += dx;
-        y += dy;
+        win = win1;
+        ofs = ofs1;
+        l = win & 0xffff;
+        n = win >> 16;
+        c = c1;
     }
 }
 

@@ -66,7 +66,8 @@ struct lfsgm_ctx {
     uint16_t *ccost = nullptr;
     uint32_t *csum = nullptr;
     int *maps = nullptr, *F0 = nullptr, *F1 = nullptr, *cntpad = nullptr;
-    int *wide_list = nullptr, *wide_count = nullptr;
+    int2 *wide_list = nullptr;         // (pixel, 32-label chunk) items for the list kernel
+    int *wide_count = nullptr;
     RowPlanHost rows{};                // row-sweep cost kernel plan + tensor maps
     bool rows_maps = false;            // tensor maps encoded for the bound workspace
     float *views_pad = nullptr;        // edge-replicated padded copies (workspace)
@@ -236,7 +237,7 @@ lfsgm_status bind_workspace(lfsgm_ctx *h, void *dptr, size_t bytes, bool owned) 
     h->F0 = (int *)take(N * 4);
     h->F1 = (int *)take(N * 4);
     h->cntpad = (int *)take(N * 4);
-    h->wide_list = (int *)take(N * 4);
+    h->wide_list = (int2 *)take(N * (size_t)((h->cfg.fine_labels + 31) / 32) * 8);
     h->wide_count = (int *)take(4);
     h->armsum = (unsigned long long *)take(4 * 8);
     h->cpen = (int *)take(8 * 4);
@@ -359,7 +360,8 @@ lfsgm_status lfsgm_workspace_size(lfsgm_handle h, size_t *bytes) {
     b += align256(A * N * h->Lcs * 2);              // coarse cost
     b += align256(A * N * (h->Lcs / 2) * 4);        // packed coarse sums
     b += align256(4 * N * 4);                       // maps
-    b += 4 * align256(N * 4);                       // F0, F1, padded counts, wide-pixel list
+    b += 3 * align256(N * 4);                       // F0, F1, padded counts
+    b += align256(N * (size_t)((h->cfg.fine_labels + 31) / 32) * 8);   // (pixel, chunk) list
     b += align256(4);                               // wide-pixel count
     b += align256(4 * 8) + align256(8 * 4) + align256(2 * 4);
     b += align256(2 * kPartialBlocks * 8) + align256(4);
@@ -458,10 +460,13 @@ lfsgm_status lfsgm_cost_volume(lfsgm_handle h, const float *views, const int32_t
         }));
     } else {
         // shapes whose row tiles do not fit the TMA boxes: every pixel through the list kernel
-        LFSGM_TRY(run(h, "fine_cost_all_list", [&] { return launch_list_all(s, h->wide_list, h->wide_count, h->N); }));
+        LFSGM_TRY(run(h, "fine_cost_all_list", [&] {
+            return launch_list_all(s, lo, cnt, (const long long *)off, c.fine_labels, h->wide_list, h->wide_count,
+                                   h->N, h->status);
+        }));
     }
     LFSGM_TRY(run(h, "fine_cost_wide", [&] {
-        return launch_fine_cost_list(s, views, h->cen_pad, h->rows.P, h->rows.Wp, h->rows.Hp, h->d_fine, c.fine_labels,
+        return launch_fine_cost_list(s, h->views_pad, h->cen_pad, h->rows.P, h->rows.Wp, h->rows.Hp, h->d_fine, c.fine_labels,
                                      h->nviews, c.H, c.W, h->ref, lo, cnt, (const long long *)off, c.w_l2, c.w_census,
                                      cost, h->wide_list, h->wide_count);
     }));

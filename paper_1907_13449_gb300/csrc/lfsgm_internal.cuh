@@ -142,12 +142,13 @@ cudaError_t launch_fine_cost_rows(cudaStream_t s, const RowPlanHost *ph, const f
                                   const uint64_t *cen_pad, const FineTap *tab, int G, int U, int V, int H,
                                   int W, int ref, const int *lo, const int *cnt, const long long *off,
                                   float wl2, float wc, float dmin, float fstep, float *cost, int *status,
-                                  int *list, int *list_count);
-cudaError_t launch_list_all(cudaStream_t s, int *list, int *count, int N);
-cudaError_t launch_fine_cost_list(cudaStream_t s, const float *views, const uint64_t *cen_pad, int P, int Wp,
+                                  int2 *list, int *list_count);
+cudaError_t launch_list_all(cudaStream_t s, const int *lo, const int *cnt, const long long *off, int G,
+                            int2 *list, int *count, int N, int *status);
+cudaError_t launch_fine_cost_list(cudaStream_t s, const float *views_pad, const uint64_t *cen_pad, int P, int Wp,
                                   int Hp, const FineTap *tab, int G, int nviews, int H, int W, int ref,
                                   const int *lo, const int *cnt, const long long *off, float wl2,
-                                  float wc, float *cost, const int *list, const int *count);
+                                  float wc, float *cost, const int2 *list, const int *count);
 
 // partial: nblocks sums of the active costs followed by nblocks counts of active slots
 cudaError_t launch_cost_partial_sums(cudaStream_t s, const float *cost, const int *cnt,
