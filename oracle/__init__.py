@@ -70,10 +70,10 @@ def lib():
             L.or_label_disp.restype = C.c_double
             L.or_label_disp.argtypes = [C.c_double, C.c_double, C.c_int, C.c_int]
             L.or_shift.argtypes = [C.c_int, C.c_double, P(C.c_int), P(C.c_double), P(C.c_int)]
-            L.or_census.argtypes = [P(C.c_float), C.c_int, C.c_int, C.c_int, P(C.c_uint64)]
+            L.or_census.argtypes = [P(C.c_double), C.c_int, C.c_int, C.c_int, P(C.c_uint64)]
             L.or_hamming.restype = C.c_int
             L.or_hamming.argtypes = [C.c_uint64, C.c_uint64]
-            L.or_census_all.argtypes = [P(Cfg), P(C.c_float), P(C.c_uint64)]
+            L.or_census_all.argtypes = [P(Cfg), P(C.c_double), P(C.c_uint64)]
             L.or_arm_views.restype = C.c_int
             L.or_arm_views.argtypes = [P(Cfg), C.c_int, P(C.c_int)]
             L.or_coarse_cost.restype = C.c_int
@@ -88,8 +88,16 @@ def lib():
             L.or_fuse.argtypes = [C.c_size_t, C.c_int, P(C.c_int32), C.c_double, P(C.c_double)]
             L.or_hole_fill.argtypes = [C.c_int, C.c_int, C.c_int, P(C.c_double)]
             L.or_windows.argtypes = [P(Cfg), C.c_size_t, P(C.c_double), P(C.c_int32), P(C.c_int32)]
-            L.or_cost_volume.argtypes = [P(Cfg), P(C.c_float), P(C.c_uint64), P(C.c_int32),
+            L.or_cost_volume.argtypes = [P(Cfg), P(C.c_double), P(C.c_uint64), P(C.c_int32),
                                          P(C.c_int32), P(C.c_int64), P(C.c_double)]
+            L.or_softargmin_backward.argtypes = [P(Cfg), C.c_size_t, P(C.c_int32), P(C.c_int32), P(C.c_int64),
+                                                 P(C.c_double), P(C.c_double), C.c_double, P(C.c_double)]
+            L.or_sgm_bounded_path_backward.argtypes = [C.c_int, C.c_int, P(C.c_int32), P(C.c_int32),
+                                                       P(C.c_int64), P(C.c_double), C.c_double, C.c_double,
+                                                       C.c_int, P(C.c_double), P(C.c_double), P(C.c_double),
+                                                       P(C.c_double)]
+            L.or_cost_backward_views.argtypes = [P(Cfg), P(C.c_double), P(C.c_int32), P(C.c_int32),
+                                                 P(C.c_int64), P(C.c_double), P(C.c_double)]
             L.or_sgm_bounded_path.argtypes = [C.c_int, C.c_int, P(C.c_int32), P(C.c_int32),
                                               P(C.c_int64), P(C.c_double), C.c_double, C.c_double,
                                               C.c_int, C.c_int, P(C.c_double)]
@@ -114,10 +122,10 @@ def shift(a: int, d: float):
 
 
 def census(img: np.ndarray, w: int) -> np.ndarray:
-    img = np.ascontiguousarray(img, dtype=np.float32)
+    img = np.ascontiguousarray(img, dtype=np.float64)
     H, W = img.shape
     out = np.zeros((H, W), np.uint64)
-    lib().or_census(_ptr(img, C.c_float), H, W, w, _ptr(out, C.c_uint64))
+    lib().or_census(_ptr(img, C.c_double), H, W, w, _ptr(out, C.c_uint64))
     return out
 
 
@@ -126,9 +134,9 @@ def hamming(a: int, b: int) -> int:
 
 
 def census_all(cfg: Cfg, views: np.ndarray) -> np.ndarray:
-    views = np.ascontiguousarray(views, dtype=np.float32)
+    views = np.ascontiguousarray(views, dtype=np.float64)
     out = np.zeros(views.shape, np.uint64)
-    lib().or_census_all(C.byref(cfg), _ptr(views, C.c_float), _ptr(out, C.c_uint64))
+    lib().or_census_all(C.byref(cfg), _ptr(views, C.c_double), _ptr(out, C.c_uint64))
     return out
 
 
@@ -203,15 +211,16 @@ def offsets(cnt: np.ndarray) -> np.ndarray:
 
 
 def cost_volume(cfg: Cfg, views: np.ndarray, lo: np.ndarray, cnt: np.ndarray, cen=None):
-    """(off, cost) with cost[off[p] + j] = C(p, lo[p] + j) (Eq. 12 + Eq. 15)."""
-    views = np.ascontiguousarray(views, dtype=np.float32)
+    """(off, cost) with cost[off[p] + j] = C(p, lo[p] + j) (Eq. 12 + Eq. 15).  Views are
+    taken in double precision (float32 inputs convert exactly)."""
+    views = np.ascontiguousarray(views, dtype=np.float64)
     if cen is None:
         cen = census_all(cfg, views)
     lo = np.ascontiguousarray(lo, dtype=np.int32).reshape(-1)
     cnt = np.ascontiguousarray(cnt, dtype=np.int32).reshape(-1)
     off = offsets(cnt)
     cost = np.zeros(int(off[-1]), np.float64)
-    lib().or_cost_volume(C.byref(cfg), _ptr(views, C.c_float), _ptr(cen, C.c_uint64),
+    lib().or_cost_volume(C.byref(cfg), _ptr(views, C.c_double), _ptr(cen, C.c_uint64),
                          _ptr(lo, C.c_int32), _ptr(cnt, C.c_int32), _ptr(off, C.c_int64),
                          _ptr(cost, C.c_double))
     return off, cost
@@ -307,3 +316,67 @@ def depth(cfg: Cfg, views: np.ndarray, fine_penalties=None, p1f=0.05, p2f=0.5, m
     out = dict(init)
     out.update(off=off, cost=cost, P1=P1, P2=P2, Cs=Cs, label=label, disp=disp, gap=gap)
     return out
+
+
+# ------------------------------------------------------- adjoint (not in the paper)
+def softargmin(cfg: Cfg, lo, cnt, off, Cs, tau):
+    _, disp, _ = wta_subpixel(cfg, lo, cnt, off, Cs, mode=2, tau=tau)
+    return disp
+
+
+def softargmin_backward(cfg: Cfg, lo, cnt, off, Cs, gd, tau):
+    lo = np.ascontiguousarray(lo, dtype=np.int32).reshape(-1)
+    cnt = np.ascontiguousarray(cnt, dtype=np.int32).reshape(-1)
+    off = np.ascontiguousarray(off, dtype=np.int64)
+    Cs = np.ascontiguousarray(Cs, dtype=np.float64)
+    gd = np.ascontiguousarray(gd, dtype=np.float64).reshape(-1)
+    out = np.zeros_like(Cs)
+    lib().or_softargmin_backward(C.byref(cfg), lo.size, _ptr(lo, C.c_int32), _ptr(cnt, C.c_int32),
+                                 _ptr(off, C.c_int64), _ptr(Cs, C.c_double), _ptr(gd, C.c_double), tau,
+                                 _ptr(out, C.c_double))
+    return out
+
+
+def sgm_backward(H, W, lo, cnt, off, cost, P1, P2, gCs):
+    """(dLoss/dcost, dLoss/dP1, dLoss/dP2) from dLoss/dC_s, one direction at a time."""
+    lo = np.ascontiguousarray(lo, dtype=np.int32).reshape(-1)
+    cnt = np.ascontiguousarray(cnt, dtype=np.int32).reshape(-1)
+    off = np.ascontiguousarray(off, dtype=np.int64)
+    cost = np.ascontiguousarray(cost, dtype=np.float64)
+    gCs = np.ascontiguousarray(gCs, dtype=np.float64)
+    gC = np.zeros_like(cost)
+    g1, g2 = C.c_double(0.0), C.c_double(0.0)
+    for r in range(8):
+        lib().or_sgm_bounded_path_backward(H, W, _ptr(lo, C.c_int32), _ptr(cnt, C.c_int32), _ptr(off, C.c_int64),
+                                           _ptr(cost, C.c_double), float(P1), float(P2), r, _ptr(gCs, C.c_double),
+                                           _ptr(gC, C.c_double), C.byref(g1), C.byref(g2))
+    return gC, g1.value, g2.value
+
+
+def cost_backward_views(cfg: Cfg, views, lo, cnt, off, gcost):
+    views = np.ascontiguousarray(views, dtype=np.float64)
+    lo = np.ascontiguousarray(lo, dtype=np.int32).reshape(-1)
+    cnt = np.ascontiguousarray(cnt, dtype=np.int32).reshape(-1)
+    off = np.ascontiguousarray(off, dtype=np.int64)
+    gcost = np.ascontiguousarray(gcost, dtype=np.float64)
+    out = np.zeros(views.shape, np.float64)
+    lib().or_cost_backward_views(C.byref(cfg), _ptr(views, C.c_double), _ptr(lo, C.c_int32), _ptr(cnt, C.c_int32),
+                                 _ptr(off, C.c_int64), _ptr(gcost, C.c_double), _ptr(out, C.c_double))
+    return out
+
+
+def loss_from_cost(cfg: Cfg, lo, cnt, cost, P1, P2, gd, tau):
+    """Loss = sum_p gd(p) dhat(p) with dhat the soft-argmin of the SGM-aggregated cost."""
+    off = offsets(cnt)
+    Cs = sgm_bounded(cfg.H, cfg.W, lo, cnt, off, cost, P1, P2)
+    return float(np.dot(np.asarray(gd, np.float64).reshape(-1), softargmin(cfg, lo, cnt, off, Cs, tau)))
+
+
+def backward(cfg: Cfg, views, lo, cnt, cost, P1, P2, gd, tau):
+    """All gradients of Loss = sum_p gd(p) dhat(p): (dcost, dP1, dP2, dviews)."""
+    off = offsets(cnt)
+    Cs = sgm_bounded(cfg.H, cfg.W, lo, cnt, off, cost, P1, P2)
+    gCs = softargmin_backward(cfg, lo, cnt, off, Cs, gd, tau)
+    gC, g1, g2 = sgm_backward(cfg.H, cfg.W, lo, cnt, off, cost, P1, P2, gCs)
+    gV = cost_backward_views(cfg, views, lo, cnt, off, gC)
+    return gC, g1, g2, gV

@@ -75,7 +75,7 @@ void or_shift(int a, double d, int *o, double *f, int *n)
  * Bit k of the word of pixel (x,y) is xi(I(x,y), I(x+dx,y+dy)) for the k-th offset of
  * the w x w window without its centre, offsets in row-major order (dy outer, dx inner),
  * bit 0 first; xi(p1,p2) = 1 iff p1 > p2 (Eq. 3).  Neighbours are clamped. */
-void or_census(const float *img, int H, int W, int w, uint64_t *out)
+void or_census(const double *img, int H, int W, int w, uint64_t *out)
 {
     int h = w / 2;
 #pragma omp parallel for schedule(static)
@@ -106,7 +106,7 @@ int or_hamming(uint64_t a, uint64_t b)
 }
 
 /* Census words of every view: out[(v*U+u)*H*W + y*W + x]. */
-void or_census_all(const or_cfg *c, const float *views, uint64_t *out)
+void or_census_all(const or_cfg *c, const double *views, uint64_t *out)
 {
     size_t HW = (size_t)c->H * c->W;
     for (int v = 0; v < c->V; v++)
@@ -354,11 +354,11 @@ void or_windows(const or_cfg *c, size_t N, const double *dinit, int32_t *lo, int
  *   C(p,g) = w_l2 * S_l2 + w_census * S_c.
  * Bilinear: (1-fy)[(1-fx) I(x0,y0) + fx I(x0+1,y0)] + fy[(1-fx) I(x0,y0+1) + fx I(x0+1,y0+1)]
  * with every tap index clamped.  Output: cost[off[p] + j] for slot j = g - lo[p]. */
-void or_cost_volume(const or_cfg *c, const float *views, const uint64_t *cen,
+void or_cost_volume(const or_cfg *c, const double *views, const uint64_t *cen,
                     const int32_t *lo, const int32_t *cnt, const int64_t *off, double *cost)
 {
     size_t HW = (size_t)c->H * c->W;
-    const float *Iref = views + ((size_t)c->vc * c->U + c->uc) * HW;
+    const double *Iref = views + ((size_t)c->vc * c->U + c->uc) * HW;
     const uint64_t *cref = cen + ((size_t)c->vc * c->U + c->uc) * HW;
 #pragma omp parallel for schedule(dynamic, 1)
     for (int y = 0; y < c->H; y++)
@@ -371,7 +371,7 @@ void or_cost_volume(const or_cfg *c, const float *views, const uint64_t *cen,
                 for (int v = 0; v < c->V; v++)
                     for (int u = 0; u < c->U; u++) {
                         if (u == c->uc && v == c->vc) continue;
-                        const float *I = views + ((size_t)v * c->U + u) * HW;
+                        const double *I = views + ((size_t)v * c->U + u) * HW;
                         int ox, oy, nx, ny;
                         double fx, fy;
                         or_shift(u - c->uc, d, &ox, &fx, &nx);
@@ -500,4 +500,151 @@ void or_wta_subpixel(const or_cfg *c, size_t N, const int32_t *lo, const int32_t
         }
         disp[p] = c->dmin + ((double)(lo[p] + b) + delta) * step;
     }
+}
+
+/* ------------------------------------------------ adjoint (not in the paper)
+ * Gradients of Loss = sum_p gd(p) * dhat(p), dhat the soft-argmin of the aggregated cost,
+ * with respect to the cost volume, P1, P2 and the view intensities. */
+
+/* Soft-argmin: dhat = sum_j w_j d_j, w = softmax(-Cs/tau) over the window, so
+ * d dhat / d Cs_j = -(1/tau) w_j (d_j - dhat). */
+void or_softargmin_backward(const or_cfg *c, size_t N, const int32_t *lo, const int32_t *cnt, const int64_t *off,
+                            const double *Cs, const double *gd, double tau, double *gCs)
+{
+    double step = (c->dmax - c->dmin) / (double)(c->G - 1);
+    for (size_t p = 0; p < N; p++) {
+        const double *s = Cs + off[p];
+        int n = cnt[p];
+        double mn = s[0];
+        for (int j = 1; j < n; j++) if (s[j] < mn) mn = s[j];
+        double z = 0.0, num = 0.0;
+        for (int j = 0; j < n; j++) {
+            double w = exp(-(s[j] - mn) / tau);
+            z += w;
+            num += w * (c->dmin + (double)(lo[p] + j) * step);
+        }
+        double dh = num / z;
+        for (int j = 0; j < n; j++) {
+            double w = exp(-(s[j] - mn) / tau) / z;
+            double d = c->dmin + (double)(lo[p] + j) * step;
+            gCs[off[p] + j] = gd[p] * (-1.0 / tau) * w * (d - dh);
+        }
+    }
+}
+
+/* Adjoint of one direction of the bounded, normalised recurrence (Eq. 8):
+ *   L(p,g) = C(p,g) + t(p,g) - m,  t = min over the branches {L'(g), L'(g-1)+P1, L'(g+1)+P1, m+P2},
+ *   m = min L'.
+ * The forward pass is recomputed recording the winning branch of every cell (ties: P2 first, then
+ * same, g-1, g+1, as the minimum is taken in that order with strict comparisons) and the argmin
+ * slot of every pixel; the reverse pass routes lambda = dLoss/dL along the winning branches, adds
+ * -sum lambda (the -m term) plus the P2-branch lambdas to the predecessor's argmin slot, and sums
+ * the branch lambdas into dP1 / dP2.  gLr: dLoss/dL_r (= dLoss/dC_s), gC accumulates dLoss/dC. */
+void or_sgm_bounded_path_backward(int H, int W, const int32_t *lo, const int32_t *cnt, const int64_t *off,
+                                  const double *C, double P1, double P2, int dir, const double *gLr,
+                                  double *gC, double *gP1, double *gP2)
+{
+    int dx = DIRS[dir][0], dy = DIRS[dir][1];
+    size_t N = (size_t)H * W, nnz = (size_t)off[N];
+    double *L = (double *)malloc(nnz * sizeof(double));
+    unsigned char *code = (unsigned char *)malloc(nnz);
+    int32_t *amin = (int32_t *)malloc(N * sizeof(int32_t));
+    double *inc = (double *)calloc(nnz, sizeof(double));
+    /* forward, in the visiting order of or_sgm_bounded_path */
+    for (int iy = 0; iy < H; iy++)
+        for (int ix = 0; ix < W; ix++) {
+            int y = order_y(iy, H, dy), x = order_x(ix, W, dx);
+            size_t p = (size_t)y * W + x;
+            int qx = x - dx, qy = y - dy;
+            if (qx < 0 || qx >= W || qy < 0 || qy >= H) {
+                for (int j = 0; j < cnt[p]; j++) { L[off[p] + j] = C[off[p] + j]; code[off[p] + j] = 4; }
+            } else {
+                size_t q = (size_t)qy * W + qx;
+                const double *lp = L + off[q];
+                double m = lp[amin[q]];
+                for (int j = 0; j < cnt[p]; j++) {
+                    int i = lo[p] + j - lo[q];
+                    double t = m + P2;
+                    unsigned char cd = 3;
+                    if (i >= 0 && i < cnt[q] && lp[i] < t) { t = lp[i]; cd = 0; }
+                    if (i - 1 >= 0 && i - 1 < cnt[q] && lp[i - 1] + P1 < t) { t = lp[i - 1] + P1; cd = 1; }
+                    if (i + 1 >= 0 && i + 1 < cnt[q] && lp[i + 1] + P1 < t) { t = lp[i + 1] + P1; cd = 2; }
+                    L[off[p] + j] = C[off[p] + j] + (t - m);
+                    code[off[p] + j] = cd;
+                }
+            }
+            int b = 0;
+            for (int j = 1; j < cnt[p]; j++) if (L[off[p] + j] < L[off[p] + b]) b = j;
+            amin[p] = b;
+        }
+    /* reverse: successors before predecessors */
+    for (int iy = H - 1; iy >= 0; iy--)
+        for (int ix = W - 1; ix >= 0; ix--) {
+            int y = order_y(iy, H, dy), x = order_x(ix, W, dx);
+            size_t p = (size_t)y * W + x;
+            int qx = x - dx, qy = y - dy;
+            int has_q = !(qx < 0 || qx >= W || qy < 0 || qy >= H);
+            size_t q = has_q ? (size_t)qy * W + qx : 0;
+            double dm = 0.0;
+            for (int j = 0; j < cnt[p]; j++) {
+                double lam = gLr[off[p] + j] + inc[off[p] + j];
+                gC[off[p] + j] += lam;
+                if (!has_q) continue;
+                int i = lo[p] + j - lo[q];
+                switch (code[off[p] + j]) {
+                case 0: inc[off[q] + i] += lam; break;
+                case 1: inc[off[q] + i - 1] += lam; *gP1 += lam; break;
+                case 2: inc[off[q] + i + 1] += lam; *gP1 += lam; break;
+                default: dm += lam; *gP2 += lam; break;
+                }
+                dm -= lam;
+            }
+            if (has_q) inc[off[q] + amin[q]] += dm;
+        }
+    free(L);
+    free(code);
+    free(amin);
+    free(inc);
+}
+
+/* Adjoint of the cost volume w.r.t. the views through the l2 term (Eq. 6, Eq. 12):
+ *   d C / d I_ref(p) = w_l2 sum_v sign(I_ref(p) - B_v),  d C / d I_v(tap) = -w_l2 sign(.) w_tap,
+ * sign(0) = 0, taps clamped as in the forward; the census term is piecewise constant (no gradient). */
+void or_cost_backward_views(const or_cfg *c, const double *views, const int32_t *lo, const int32_t *cnt,
+                            const int64_t *off, const double *gcost, double *gviews)
+{
+    size_t HW = (size_t)c->H * c->W;
+    const double *Iref = views + ((size_t)c->vc * c->U + c->uc) * HW;
+    double *gref = gviews + ((size_t)c->vc * c->U + c->uc) * HW;
+    for (int y = 0; y < c->H; y++)
+        for (int x = 0; x < c->W; x++) {
+            size_t p = (size_t)y * c->W + x;
+            for (int j = 0; j < cnt[p]; j++) {
+                double gcv = gcost[off[p] + j];
+                if (gcv == 0.0) continue;
+                double d = or_label_disp(c->dmin, c->dmax, c->G, lo[p] + j);
+                for (int v = 0; v < c->V; v++)
+                    for (int u = 0; u < c->U; u++) {
+                        if (u == c->uc && v == c->vc) continue;
+                        const double *I = views + ((size_t)v * c->U + u) * HW;
+                        double *gI = gviews + ((size_t)v * c->U + u) * HW;
+                        int ox, oy, nx, ny;
+                        double fx, fy;
+                        or_shift(u - c->uc, d, &ox, &fx, &nx);
+                        or_shift(v - c->vc, d, &oy, &fy, &ny);
+                        int x0 = clampi(x + ox, 0, c->W - 1), x1 = clampi(x + ox + 1, 0, c->W - 1);
+                        int y0 = clampi(y + oy, 0, c->H - 1), y1 = clampi(y + oy + 1, 0, c->H - 1);
+                        double smp = (1.0 - fy) * ((1.0 - fx) * I[(size_t)y0 * c->W + x0] + fx * I[(size_t)y0 * c->W + x1])
+                                   + fy * ((1.0 - fx) * I[(size_t)y1 * c->W + x0] + fx * I[(size_t)y1 * c->W + x1]);
+                        double delta = Iref[p] - smp;
+                        double sg = delta > 0.0 ? 1.0 : (delta < 0.0 ? -1.0 : 0.0);
+                        double g = gcv * c->w_l2 * sg;
+                        gref[p] += g;
+                        gI[(size_t)y0 * c->W + x0] -= g * (1.0 - fy) * (1.0 - fx);
+                        gI[(size_t)y0 * c->W + x1] -= g * (1.0 - fy) * fx;
+                        gI[(size_t)y1 * c->W + x0] -= g * fy * (1.0 - fx);
+                        gI[(size_t)y1 * c->W + x1] -= g * fy * fx;
+                    }
+            }
+        }
 }
