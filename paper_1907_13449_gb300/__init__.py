@@ -272,6 +272,76 @@ def lfsgm_cost_volume_noalloc(cfg, views, lo, cnt, off, cost, stream=None):
                                                               4: "CUDA error"}.get(st, ""))
 
 
+# ------------------------------------------------------------------ differentiation (not in the paper)
+def _autograd():
+    import torch
+
+    class SGMSoftArgmin(torch.autograd.Function):
+        """disp = soft-argmin(SGM(cost; P1, P2)) on the windows held by ``L`` (a LightFieldDepth
+        created with subpixel=2); backward = lfsgm_backward (grad wrt cost, P1, P2)."""
+
+        @staticmethod
+        def forward(ctx, cost, P1, P2, L):
+            p1, p2 = float(P1), float(P2)
+            agg = torch.empty_like(cost)
+            lfsgm_sgm_aggregate(L.h, cost, L.lo, L.cnt, L.off, p1, p2, agg)
+            disp = torch.empty(L.N, dtype=torch.float32, device=cost.device)
+            lfsgm_wta_subpixel(L.h, agg, L.lo, L.cnt, L.off, None, disp)
+            ctx.save_for_backward(cost)
+            ctx.pen, ctx.L = (p1, p2), L
+            return disp
+
+        @staticmethod
+        def backward(ctx, gdisp):
+            (cost,) = ctx.saved_tensors
+            L = ctx.L
+            gcost = torch.empty_like(cost)
+            gp = torch.zeros(2, dtype=torch.float32, device=cost.device)
+            lfsgm_backward(L.h, None, cost, L.lo, L.cnt, L.off, ctx.pen[0], ctx.pen[1], gdisp.contiguous(), gcost,
+                           gp[0:1], gp[1:2], None)
+            return gcost, gp[0], gp[1], None
+
+    class DepthFromViews(torch.autograd.Function):
+        """disp = soft-argmin(SGM(cost_volume(views); P1, P2)) on the windows held by ``L``;
+        backward = lfsgm_backward (grad wrt views through the l2 term, P1, P2)."""
+
+        @staticmethod
+        def forward(ctx, views, P1, P2, L):
+            p1, p2 = float(P1), float(P2)
+            L.cost_volume(views)
+            cost = L.cost
+            agg = torch.empty_like(cost)
+            lfsgm_sgm_aggregate(L.h, cost, L.lo, L.cnt, L.off, p1, p2, agg)
+            disp = torch.empty(L.N, dtype=torch.float32, device=views.device)
+            lfsgm_wta_subpixel(L.h, agg, L.lo, L.cnt, L.off, None, disp)
+            ctx.save_for_backward(views, cost.clone())
+            ctx.pen, ctx.L = (p1, p2), L
+            return disp
+
+        @staticmethod
+        def backward(ctx, gdisp):
+            views, cost = ctx.saved_tensors
+            L = ctx.L
+            gcost = torch.empty_like(cost)
+            gviews = torch.empty_like(views)
+            gp = torch.zeros(2, dtype=torch.float32, device=views.device)
+            lfsgm_backward(L.h, views, cost, L.lo, L.cnt, L.off, ctx.pen[0], ctx.pen[1], gdisp.contiguous(), gcost,
+                           gp[0:1], gp[1:2], gviews)
+            return gviews, gp[0], gp[1], None
+
+    return SGMSoftArgmin, DepthFromViews
+
+
+def sgm_softargmin(cost, P1, P2, L):
+    """Differentiable soft-argmin disparity of the SGM-aggregated cost (see SGMSoftArgmin)."""
+    return _autograd()[0].apply(cost, P1, P2, L)
+
+
+def depth_from_views(views, P1, P2, L):
+    """Differentiable soft-argmin disparity from the views on fixed windows (see DepthFromViews)."""
+    return _autograd()[1].apply(views, P1, P2, L)
+
+
 # ------------------------------------------------------------------ convenience wrapper
 class LightFieldDepth:
     """Owns a handle and the windowed buffers of one light-field shape and runs the

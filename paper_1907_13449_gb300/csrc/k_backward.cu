@@ -1,0 +1,307 @@
+// k_backward.cu -- adjoint of cost volume -> bounded 8-path SGM -> soft-argmin (not in the paper).
+//
+// Loss gradients arrive as grad_disp = dLoss/d dhat(p) for the soft-argmin disparity
+// dhat = sum_g softmax(-C_s/tau)_g d_g.  Three kernels:
+//  * softargmin_backward: dLoss/dC_s(p,g) = grad_disp(p) (-1/tau) w_g (d_g - dhat).
+//  * sgm_backward: one warp per (direction, scanline).  The path is recomputed forward, recording
+//    for every cell the winning branch of the normalised recurrence (P2 first, then same, g-1,
+//    g+1, taken with strict comparisons in that order) and for every pixel the slot of its
+//    minimum; the reverse sweep carries lambda = dLoss/dL_r along the path: it adds lambda into
+//    dLoss/dC, gathers the predecessor's incoming adjoint from the three slots whose branch points
+//    at it, routes (P2-branch lambdas - all lambdas) to the predecessor's minimum (the -m term),
+//    and sums the branch lambdas into dLoss/dP1, dLoss/dP2.  Path costs are recomputed per
+//    direction instead of being stored for all 8.
+//  * views_backward: one thread per pixel; dC/dI_ref = w_l2 sum sign(I_ref - B), dC/dI_v(tap) =
+//    -w_l2 sign(.) w_tap (taps clamped as in the forward); tap gradients are summed in registers
+//    while the bilinear cell stays the same and added to the view with atomics when it changes.
+//    The census term is piecewise constant and has no gradient.
+#include "lfsgm_internal.cuh"
+
+namespace lfsgm {
+namespace {
+
+constexpr int kBwdWarps = 4;
+
+__device__ __forceinline__ float warp_sum(float v) {
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+__global__ void softargmin_backward_kernel(const float *__restrict__ agg, const int *__restrict__ lo,
+                                           const int *__restrict__ cnt, const long long *__restrict__ off, int N,
+                                           int G, double dmin, double step, float tau,
+                                           const float *__restrict__ gdisp, float *__restrict__ gCs,
+                                           float *__restrict__ gcost, int *__restrict__ status) {
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= N) return;
+    const long long o = off[p];
+    const int n = cnt[p], l = lo[p];
+    if (!window_ok(l, n, G, off[p + 1] - o, status)) return;
+    const int npad = (int)min((long long)((n + 3) & ~3), off[p + 1] - o);
+    const float *s = agg + o;
+    float mn = s[0];
+    for (int j = 1; j < n; j++) mn = fminf(mn, s[j]);
+    double z = 0.0, num = 0.0;
+    for (int j = 0; j < n; j++) {
+        const double w = exp(-((double)s[j] - (double)mn) / (double)tau);
+        z += w;
+        num += w * (dmin + (double)(l + j) * step);
+    }
+    const double dh = num / z, gd = (double)gdisp[p];
+    for (int j = 0; j < npad; j++) {
+        float g = 0.f;
+        if (j < n) {
+            const double w = exp(-((double)s[j] - (double)mn) / (double)tau) / z;
+            g = (float)(gd * (-1.0 / (double)tau) * w * ((dmin + (double)(l + j) * step) - dh));
+        }
+        gCs[o + j] = g;
+        gcost[o + j] = 0.f;
+    }
+}
+
+// Branch codes: 0 same label, 1 label-1 (+P1), 2 label+1 (+P1), 3 m+P2, 4 path start.
+__global__ void __launch_bounds__(32 * kBwdWarps) sgm_backward_kernel(
+    const float *__restrict__ cost, const int *__restrict__ lo, const int *__restrict__ cnt,
+    const long long *__restrict__ off, int H, int W, int G, int Gs, float P1, float P2, ScanTable st,
+    const float *__restrict__ gCs, unsigned char *__restrict__ codes, int *__restrict__ amin, size_t nnz_cap,
+    float *__restrict__ gcost, float *__restrict__ gP, int *__restrict__ status) {
+    extern __shared__ float sm[];
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    const int gw = blockIdx.x * kBwdWarps + wib;
+    if (gw >= st.cum[8]) return;
+    int r = 0;
+    while (gw >= st.cum[r + 1]) r++;
+    const int s = gw - st.cum[r];
+    const int dx = dir_dx(r), dy = dir_dy(r);
+    int x0, y0;
+    scan_start(r, s, H, W, x0, y0);
+    const int lx = dx > 0 ? W - x0 : (dx < 0 ? x0 + 1 : 0x7fffffff);
+    const int ly = dy > 0 ? H - y0 : (dy < 0 ? y0 + 1 : 0x7fffffff);
+    const int len = min(lx, ly);
+    unsigned char *code = codes + (size_t)r * nnz_cap;
+    int *am = amin + (size_t)r * H * W;
+    float *bufA = sm + (size_t)wib * 4 * Gs;   // forward: predecessor's L;  reverse: incoming adjoint of p
+    float *bufB = bufA + Gs;                   // forward: this pixel's L;    reverse: incoming adjoint of q
+    float *lam = bufB + Gs;                    // reverse: lambda of p by slot
+    unsigned char *cds = (unsigned char *)(lam + Gs);
+    const float INF = __int_as_float(0x7f800000);
+
+    // forward recompute: branch codes and argmin slots
+    int plo = 0, pn = 0;
+    float m = 0.f;
+    bool first = true;
+    for (int k = 0; k < len; k++) {
+        const int p = (y0 + k * dy) * W + (x0 + k * dx);
+        const int l = lo[p], n = cnt[p];
+        const long long o = off[p];
+        if (!window_ok(l, n, G, off[p + 1] - o, status)) {
+            first = true;
+            continue;
+        }
+        float bv = INF;
+        int bj = 0x7fffffff;
+        for (int j = lane; j < n; j += 32) {
+            const float c = cost[o + j];
+            float Lv;
+            unsigned char cd = 4;
+            if (first) {
+                Lv = c;
+            } else {
+                const int i = l + j - plo;
+                float t = m + P2;
+                cd = 3;
+                if ((unsigned)i < (unsigned)pn && bufA[i] < t) { t = bufA[i]; cd = 0; }
+                if ((unsigned)(i - 1) < (unsigned)pn && bufA[i - 1] + P1 < t) { t = bufA[i - 1] + P1; cd = 1; }
+                if ((unsigned)(i + 1) < (unsigned)pn && bufA[i + 1] + P1 < t) { t = bufA[i + 1] + P1; cd = 2; }
+                Lv = c + (t - m);
+            }
+            bufB[j] = Lv;
+            code[o + j] = cd;
+            if (Lv < bv) { bv = Lv; bj = j; }
+        }
+        // minimum and its lowest slot
+        float mv;
+        asm volatile("redux.sync.min.f32 %0, %1, 0xffffffff;" : "=f"(mv) : "f"(bv));
+        const int cand = (bv == mv) ? bj : 0x7fffffff;
+        const int slot = __reduce_min_sync(0xffffffffu, (unsigned)cand);
+        if (lane == 0) am[p] = slot;
+        m = mv;
+        __syncwarp();
+        float *tmp = bufA;
+        bufA = bufB;
+        bufB = tmp;
+        plo = l;
+        pn = n;
+        first = false;
+    }
+    __syncwarp();
+
+    // reverse sweep
+    float gp1 = 0.f, gp2 = 0.f;
+    bool have_inc = false;       // bufA holds the incoming adjoint of the current pixel
+    for (int k = len - 1; k >= 0; k--) {
+        const int p = (y0 + k * dy) * W + (x0 + k * dx);
+        const int l = lo[p], n = cnt[p];
+        const long long o = off[p];
+        if (!window_ok(l, n, G, off[p + 1] - o, nullptr)) {
+            have_inc = false;
+            continue;
+        }
+        // predecessor on the path (valid window, inside the image)
+        int q = -1, ql = 0, qn = 0;
+        if (k > 0) {
+            const int qq = (y0 + (k - 1) * dy) * W + (x0 + (k - 1) * dx);
+            const int l2 = lo[qq], n2 = cnt[qq];
+            if (window_ok(l2, n2, G, off[qq + 1] - off[qq], nullptr)) {
+                q = qq;
+                ql = l2;
+                qn = n2;
+            }
+        }
+        float dm = 0.f;
+        for (int j = lane; j < n; j += 32) {
+            const float lv = gCs[o + j] + (have_inc ? bufA[j] : 0.f);
+            atomicAdd(gcost + o + j, lv);
+            const unsigned char cd = code[o + j];
+            lam[j] = lv;
+            cds[j] = cd;
+            if (cd == 1 || cd == 2) gp1 += lv;
+            if (cd == 3) {
+                gp2 += lv;
+                dm += lv;
+            }
+            dm -= lv;
+        }
+        dm = warp_sum(dm);
+        __syncwarp();
+        if (q >= 0) {
+            // gather q's incoming adjoint: label h receives from p's labels h (same), h+1 (-1 branch), h-1 (+1 branch)
+            const int qa = am[q];
+            for (int i = lane; i < qn; i += 32) {
+                const int h = ql + i;
+                float v = 0.f;
+                const int j0 = h - l, j1 = h + 1 - l, j2 = h - 1 - l;
+                if ((unsigned)j0 < (unsigned)n && cds[j0] == 0) v += lam[j0];
+                if ((unsigned)j1 < (unsigned)n && cds[j1] == 1) v += lam[j1];
+                if ((unsigned)j2 < (unsigned)n && cds[j2] == 2) v += lam[j2];
+                if (i == qa) v += dm;
+                bufB[i] = v;
+            }
+            __syncwarp();
+            float *tmp = bufA;
+            bufA = bufB;
+            bufB = tmp;
+            have_inc = true;
+        } else {
+            have_inc = false;
+        }
+        __syncwarp();
+    }
+    gp1 = warp_sum(gp1);
+    gp2 = warp_sum(gp2);
+    if (lane == 0) {
+        if (gp1 != 0.f) atomicAdd(gP, gp1);
+        if (gp2 != 0.f) atomicAdd(gP + 1, gp2);
+    }
+}
+
+__global__ void views_backward_kernel(const float *__restrict__ views, const FineTap *__restrict__ tab, int G,
+                                      int nviews, int H, int W, int ref, const int *__restrict__ lo,
+                                      const int *__restrict__ cnt, const long long *__restrict__ off, float wl2,
+                                      const float *__restrict__ gcost, float *__restrict__ gviews) {
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    const size_t N = (size_t)H * W;
+    if (p >= (int)N) return;
+    const int l = lo[p], n = cnt[p];
+    const long long o = off[p];
+    if (!window_ok(l, n, G, off[p + 1] - o, nullptr)) return;
+    const int x = p % W, y = p / W;
+    const float Iref = views[(size_t)ref * N + p];
+    float gref = 0.f;
+    for (int vi = 0; vi < nviews - 1; vi++) {
+        const int view = vi + (vi >= ref);
+        const float *I = views + (size_t)view * N;
+        float *gI = gviews + (size_t)view * N;
+        int cx = 0x7fffffff, cy = 0;
+        float a00 = 0.f, a10 = 0.f, a01 = 0.f, a11 = 0.f;
+        int i00 = 0, i10 = 0, i01 = 0, i11 = 0;
+        for (int j = 0; j < n; j++) {
+            const float gc = gcost[o + j];
+            const FineTap t = load_tap(tab + (size_t)view * G + l + j);
+            if (t.ox != cx || t.oy != cy) {
+                if (cx != 0x7fffffff) {
+                    atomicAdd(gI + i00, a00);
+                    atomicAdd(gI + i10, a10);
+                    atomicAdd(gI + i01, a01);
+                    atomicAdd(gI + i11, a11);
+                }
+                cx = t.ox;
+                cy = t.oy;
+                const int x0 = min(max(x + t.ox, 0), W - 1), x1 = min(max(x + t.ox + 1, 0), W - 1);
+                const int y0 = min(max(y + t.oy, 0), H - 1), y1 = min(max(y + t.oy + 1, 0), H - 1);
+                i00 = y0 * W + x0;
+                i10 = y0 * W + x1;
+                i01 = y1 * W + x0;
+                i11 = y1 * W + x1;
+                a00 = a10 = a01 = a11 = 0.f;
+            }
+            if (gc == 0.f) continue;
+            const float top = (1.f - t.fx) * I[i00] + t.fx * I[i10];
+            const float bot = (1.f - t.fx) * I[i01] + t.fx * I[i11];
+            const float smp = (1.f - t.fy) * top + t.fy * bot;
+            const float d = Iref - smp;
+            const float sg = d > 0.f ? 1.f : (d < 0.f ? -1.f : 0.f);
+            const float g = gc * wl2 * sg;
+            gref += g;
+            a00 -= g * (1.f - t.fy) * (1.f - t.fx);
+            a10 -= g * (1.f - t.fy) * t.fx;
+            a01 -= g * t.fy * (1.f - t.fx);
+            a11 -= g * t.fy * t.fx;
+        }
+        if (cx != 0x7fffffff) {
+            atomicAdd(gI + i00, a00);
+            atomicAdd(gI + i10, a10);
+            atomicAdd(gI + i01, a01);
+            atomicAdd(gI + i11, a11);
+        }
+    }
+    gviews[(size_t)ref * N + p] = gref;   // the reference view only receives its own pixels' terms
+}
+
+}  // namespace
+
+cudaError_t launch_softargmin_backward(cudaStream_t s, const float *agg, const int *lo, const int *cnt,
+                                       const long long *off, int N, int G, double dmin, double step, float tau,
+                                       const float *gdisp, float *gCs, float *gcost, int *status) {
+    softargmin_backward_kernel<<<(N + 255) / 256, 256, 0, s>>>(agg, lo, cnt, off, N, G, dmin, step, tau, gdisp, gCs,
+                                                               gcost, status);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_sgm_backward(cudaStream_t s, const float *cost, const int *lo, const int *cnt, const long long *off,
+                                int H, int W, int G, float P1, float P2, const float *gCs, unsigned char *codes,
+                                int *amin, size_t nnz_cap, float *gcost, float *gP, int *status) {
+    const ScanTable st = make_scan_table(H, W);
+    const int Gs = (G + 31) & ~31;
+    const size_t smem = (size_t)kBwdWarps * 4 * Gs * sizeof(float);   // bufA, bufB, lambda, codes per warp
+    const unsigned grid = (unsigned)((st.cum[8] + kBwdWarps - 1) / kBwdWarps);
+    if (smem > 48 * 1024) {
+        const cudaError_t e = cudaFuncSetAttribute(sgm_backward_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                   (int)smem);
+        if (e != cudaSuccess) return e;
+    }
+    sgm_backward_kernel<<<grid, 32 * kBwdWarps, smem, s>>>(cost, lo, cnt, off, H, W, G, Gs, P1, P2, st, gCs, codes,
+                                                           amin, nnz_cap, gcost, gP, status);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_views_backward(cudaStream_t s, const float *views, const FineTap *tab, int G, int nviews, int H,
+                                  int W, int ref, const int *lo, const int *cnt, const long long *off, float wl2,
+                                  const float *gcost, float *gviews) {
+    const int N = H * W;
+    views_backward_kernel<<<(N + 127) / 128, 128, 0, s>>>(views, tab, G, nviews, H, W, ref, lo, cnt, off, wl2, gcost,
+                                                          gviews);
+    return cudaGetLastError();
+}
+
+}  // namespace lfsgm

@@ -82,6 +82,11 @@ struct lfsgm_ctx {
     int *o_lo = nullptr, *o_cnt = nullptr, *o_label = nullptr;
     long long *o_off = nullptr;
     float *o_cost = nullptr, *o_agg = nullptr, *o_disp = nullptr, *o_views = nullptr;
+    // backward scratch (allocated on the first lfsgm_backward): aggregate, dLoss/dC_s, branch codes
+    // of the 8 directions, argmin slots, penalty gradients
+    float *b_agg = nullptr, *b_gcs = nullptr, *b_gp = nullptr;
+    unsigned char *b_codes = nullptr;
+    int *b_amin = nullptr;
     // accounting
     long long launches = 0;
     bool profiling = false;
@@ -344,6 +349,7 @@ lfsgm_status lfsgm_destroy(lfsgm_handle h) {
     if (h->ws_owned) cudaFree(h->ws);
     cudaFree(h->o_lo); cudaFree(h->o_cnt); cudaFree(h->o_label); cudaFree(h->o_off);
     cudaFree(h->o_cost); cudaFree(h->o_agg); cudaFree(h->o_disp); cudaFree(h->o_views);
+    cudaFree(h->b_agg); cudaFree(h->b_gcs); cudaFree(h->b_gp); cudaFree(h->b_codes); cudaFree(h->b_amin);
     for (auto &r : h->prof) { cudaEventDestroy(r.a); cudaEventDestroy(r.b); }
     for (auto e : h->pool) cudaEventDestroy(e);
     delete h;
@@ -537,10 +543,53 @@ lfsgm_status lfsgm_wta_subpixel(lfsgm_handle h, const float *agg, const int32_t 
     });
 }
 
-lfsgm_status lfsgm_backward(lfsgm_handle h, const float *, const float *, const int32_t *, const int32_t *,
-                            const int64_t *, float, float, const float *, float *, float *, float *, float *) {
+lfsgm_status lfsgm_backward(lfsgm_handle h, const float *views, const float *cost, const int32_t *lo,
+                            const int32_t *cnt, const int64_t *off, float P1, float P2, const float *grad_disp,
+                            float *grad_cost, float *grad_P1, float *grad_P2, float *grad_views) {
     if (!h) return LFSGM_ERR_INVALID_ARG;
-    return fail(h, LFSGM_ERR_UNSUPPORTED, "backward not built yet");
+    if (!cost || !lo || !cnt || !off || !grad_disp || !grad_cost || !grad_P1 || !grad_P2 || (grad_views && !views))
+        return fail(h, LFSGM_ERR_INVALID_ARG, "null buffer");
+    if (!(P1 >= 0.f && P2 >= P1 && std::isfinite(P2)))
+        return fail(h, LFSGM_ERR_INVALID_ARG, "backward needs explicit penalties 0 <= P1 <= P2, got %g %g", P1, P2);
+    LFSGM_TRY(ensure_workspace(h));
+    const lfsgm_config &c = h->cfg;
+    cudaStream_t s = h->stream;
+    const size_t N = (size_t)h->N;
+    int64_t cap = 0;
+    lfsgm_max_nnz(h, &cap);
+    if (!h->b_agg) {
+        cudaError_t e = cudaMalloc((void **)&h->b_agg, (size_t)cap * 4);
+        if (e == cudaSuccess) e = cudaMalloc((void **)&h->b_gcs, (size_t)cap * 4);
+        if (e == cudaSuccess) e = cudaMalloc((void **)&h->b_codes, (size_t)cap * 8);
+        if (e == cudaSuccess) e = cudaMalloc((void **)&h->b_amin, N * 8 * 4);
+        if (e == cudaSuccess) e = cudaMalloc((void **)&h->b_gp, 2 * 4);
+        if (e != cudaSuccess) return fail(h, LFSGM_ERR_NO_MEMORY, "backward scratch: %s", cudaGetErrorString(e));
+    }
+    const long long *o = (const long long *)off;
+    const double step = (c.dmax - c.dmin) / (double)(c.fine_labels - 1);
+    // aggregate (the forward of the SGM, recomputed)
+    LFSGM_TRY(lfsgm_sgm_aggregate(h, cost, lo, cnt, off, P1, P2, h->b_agg));
+    LFSGM_TRY(run(h, "softargmin_backward", [&] {
+        return launch_softargmin_backward(s, h->b_agg, lo, cnt, o, h->N, c.fine_labels, c.dmin, step, c.softmin_tau,
+                                          grad_disp, h->b_gcs, grad_cost, h->status);
+    }));
+    cudaError_t e = cudaMemsetAsync(h->b_gp, 0, 8, s);
+    if (e == cudaSuccess && grad_views) e = cudaMemsetAsync(grad_views, 0, (size_t)h->nviews * N * 4, s);
+    if (e != cudaSuccess) return cuda_fail(h, e, "memset");
+    LFSGM_TRY(run(h, "sgm_backward", [&] {
+        return launch_sgm_backward(s, cost, lo, cnt, o, c.H, c.W, c.fine_labels, P1, P2, h->b_gcs, h->b_codes,
+                                   h->b_amin, (size_t)cap, grad_cost, h->b_gp, h->status);
+    }));
+    if (grad_views) {
+        LFSGM_TRY(run(h, "views_backward", [&] {
+            return launch_views_backward(s, views, h->d_fine, c.fine_labels, h->nviews, c.H, c.W, h->ref, lo, cnt, o,
+                                         c.w_l2, grad_cost, grad_views);
+        }));
+    }
+    e = cudaMemcpyAsync(grad_P1, h->b_gp, 4, cudaMemcpyDeviceToDevice, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(grad_P2, h->b_gp + 1, 4, cudaMemcpyDeviceToDevice, s);
+    if (e != cudaSuccess) return cuda_fail(h, e, "penalty gradients");
+    return LFSGM_OK;
 }
 
 lfsgm_status lfsgm_sync(lfsgm_handle h) {

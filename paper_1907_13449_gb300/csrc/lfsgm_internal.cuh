@@ -164,6 +164,17 @@ cudaError_t launch_wta(cudaStream_t s, const float *agg, const int *lo, const in
                        const long long *off, int N, int G, double dmin, double step, int mode,
                        float tau, int *label, float *disp, int *status);
 
+cudaError_t launch_softargmin_backward(cudaStream_t s, const float *agg, const int *lo, const int *cnt,
+                                       const long long *off, int N, int G, double dmin, double step, float tau,
+                                       const float *gdisp, float *gCs, float *gcost, int *status);
+cudaError_t launch_sgm_backward(cudaStream_t s, const float *cost, const int *lo, const int *cnt,
+                                const long long *off, int H, int W, int G, float P1, float P2, const float *gCs,
+                                unsigned char *codes, int *amin, size_t nnz_cap, float *gcost, float *gP,
+                                int *status);
+cudaError_t launch_views_backward(cudaStream_t s, const float *views, const FineTap *tab, int G, int nviews,
+                                  int H, int W, int ref, const int *lo, const int *cnt, const long long *off,
+                                  float wl2, const float *gcost, float *gviews);
+
 constexpr int kPartialBlocks = 1024;
 
 }  // namespace lfsgm
