@@ -9,6 +9,9 @@ map stage, Sec. III-E); the full-step time is reported beside it.
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
                   [--workload bench|plenoptic|tiny]
 
+Beside it: the training pattern (forward + hand-written backward, soft-argmin) and the
+serving pattern (64 mixed light fields as one CUDA-graph launch against sequential launches).
+
 N > 1 is launched with torchrun: every rank runs its own light field (independent
 replicas, no collective on the data path), the step time is the max over ranks.
 --impl reference times the FP64 CPU oracle on the host cores on a row band of the
@@ -279,11 +282,150 @@ def run_ours(args, ws, rank, local):
                 "device->host disparity + label", "h2d_bytes_per_step": int(views_np.nbytes),
                 "d2h_bytes_per_step": int(dh.numel() * 4 + lh.numel() * 4)},
     }
+    if args.backward:
+        out["backward"] = run_backward(args, dev, views, p)
+    if args.batch_lfs > 0:
+        out["batch"] = run_batch(args, dev)
     if not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(args, views_np, p, rows=args.cpu_rows)
     if ws > 1:
         dist.destroy_process_group()
     return out
+
+
+def run_backward(args, dev, views, p):
+    """Training pattern: forward (cost volume, SGM with fixed penalties, soft-argmin) and the
+    hand-written backward (grad wrt cost, P1, P2 and views) on the same light field, against the
+    plain forward.  L2 flushed before every step."""
+    import dataclasses
+
+    import torch
+
+    import paper_1907_13449_gb300 as lf
+    q = dataclasses.replace(p, subpixel=2)
+    L = lf.LightFieldDepth(q, device=dev)
+    stream = L.stream
+    L.initial(views)
+    L.cost_volume(views)
+    torch.cuda.synchronize()
+    nnz = int(L.off[-1].item())
+    active = int(L.cnt.sum().item())
+    mean = float(L.cost[:nnz].double().sum().item()) / active     # padding slots hold 0
+    P1, P2 = q.p1_frac * mean, q.p2_frac * mean
+    gdisp = torch.randn(L.N, generator=torch.Generator(device=dev).manual_seed(5), device=dev)
+    gcost = torch.empty_like(L.cost)
+    gviews = torch.empty_like(views)
+    gp = torch.zeros(2, dtype=torch.float32, device=dev)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+
+    def fwd():
+        L.cost_volume(views)
+        L.aggregate(P1, P2)
+        lf.lfsgm_wta_subpixel(L.h, L.agg, L.lo, L.cnt, L.off, None, L.disp)
+
+    def bwd():
+        lf.lfsgm_backward(L.h, views, L.cost, L.lo, L.cnt, L.off, P1, P2, gdisp, gcost, gp[0:1], gp[1:2], gviews)
+
+    for _ in range(args.warmup):
+        flush.zero_()
+        fwd()
+        bwd()
+    K = max(3, args.steps // 4)
+    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(K)]
+    torch.cuda.synchronize()
+    for i in range(K):
+        flush.zero_()
+        ev[i][0].record(stream)
+        fwd()
+        ev[i][1].record(stream)
+        bwd()
+        ev[i][2].record(stream)
+    torch.cuda.synchronize()
+    f = statistics.mean(e[0].elapsed_time(e[1]) for e in ev)
+    b = statistics.mean(e[1].elapsed_time(e[2]) for e in ev)
+    ok = bool(torch.isfinite(gviews).all().item() and torch.isfinite(gp).all().item())
+    L.close()
+    return {"config": "9x9x512x512, 31-label windows, soft-argmin tau 0.1, fixed P1/P2 = 0.05/0.5 mean cost",
+            "forward_ms": round(f, 4), "backward_ms": round(b, 4), "steps": K,
+            "backward_over_forward": round(b / f, 3), "grads_finite": ok,
+            "grads": "cost volume, P1, P2, views (l2 term through the bilinear weights)"}
+
+
+def run_batch(args, dev):
+    """Serving pattern: the mixed batch (4 shape classes, census 5/7, coarse labels 16..128)
+    as one CUDA-graph launch, against the same light fields launched one after another."""
+    import numpy as np
+    import torch
+
+    import lfsynth
+    import paper_1907_13449_gb300 as lf
+    n = args.batch_lfs
+    t0 = time.perf_counter()
+    lfs = [lfsynth.batch_lf(i, device=dev) for i in range(n)]
+    gen_s = time.perf_counter() - t0
+    params = [p for _, p in lfs]
+    views = [v for v, _ in lfs]
+    stream = torch.cuda.current_stream(dev)
+    t0 = time.perf_counter()
+    B = lf.LightFieldBatch(params, views, branches=args.batch_branches, stream=stream)
+    tune_s = time.perf_counter() - t0
+    for _ in range(2):
+        B.run()
+    torch.cuda.synchronize()
+    R = max(3, args.steps // 10)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(R)]
+    done, flight = [], []
+    for i in range(R):
+        ev[i][0].record(stream)
+        B.run()
+        ev[i][1].record(stream)
+        s, e, k = B.times()
+        done.append(e)
+        flight.append(e - s)
+    batch_ms = statistics.mean(a.elapsed_time(b) for a, b in ev)
+    done = np.concatenate(done)
+    flight = np.concatenate(flight)
+    disp_b = [d.clone() for d in B.disp]
+    nodes = B.kernel_nodes
+    B.close()
+
+    # sequential single-light-field launches on one stream (buffers allocated beforehand)
+    hs = [lf.lfsgm_create(p, stream) for p in params]
+    outs = [torch.empty(p.H * p.W, dtype=torch.float32, device=dev) for p in params]
+    for h, v, o in zip(hs, views, outs):
+        lf.lfsgm_depth(h, v, o, None)
+    torch.cuda.synchronize()
+    seq_total, seq_each, seq_done = [], [], []
+    for _ in range(R):
+        evs = [torch.cuda.Event(enable_timing=True) for _ in range(n + 1)]
+        evs[0].record(stream)
+        for i, (h, v, o) in enumerate(zip(hs, views, outs)):
+            lf.lfsgm_depth(h, v, o, None)
+            evs[i + 1].record(stream)
+        torch.cuda.synchronize()
+        each = [evs[i].elapsed_time(evs[i + 1]) for i in range(n)]
+        seq_each += each
+        seq_done += list(np.cumsum(each))
+        seq_total.append(evs[0].elapsed_time(evs[n]))
+    for h in hs:
+        lf.lfsgm_destroy(h)
+    # the batch and the sequential launches agree where the decision is clear
+    diff = max(float(torch.quantile(torch.abs(a - b), 0.999).item()) for a, b in zip(disp_b, outs))
+    seq_ms = statistics.mean(seq_total)
+    pct = lambda a, q: round(float(np.percentile(a, q)), 3)
+    return {"lfs": n, "classes": [c["name"] for c in lfsynth.BATCH_CLASSES],
+            "branches": int(k), "graph_kernel_nodes": int(nodes), "runs": R,
+            "lf_per_s": round(n / (batch_ms * 1e-3), 1), "ms_per_batch": round(batch_ms, 3),
+            "p50_ms": pct(done, 50), "p99_ms": pct(done, 99),
+            "latency": "completion time of each light field after the batch starts (all submitted at once)",
+            "in_flight_p50_ms": pct(flight, 50), "in_flight_p99_ms": pct(flight, 99),
+            "sequential": {"lf_per_s": round(n / (seq_ms * 1e-3), 1), "ms_total": round(seq_ms, 3),
+                           "p50_ms": pct(seq_done, 50), "p99_ms": pct(seq_done, 99),
+                           "per_lf_p50_ms": pct(seq_each, 50), "per_lf_p99_ms": pct(seq_each, 99)},
+            "speedup_vs_sequential": round(seq_ms / batch_ms, 3),
+            "disp_diff_p999_px": diff,
+            "inputs": f"{sum(v.numel() for v in views) * 4 / 1e9:.2f} GB of views (larger than L2), "
+                      f"rendered on the GPU in {gen_s:.1f} s; autotune + capture {tune_s:.1f} s"}
 
 
 def cpu_baseline(args, views_np, p, rows):
@@ -337,6 +479,9 @@ def main():
     ap.add_argument("--workload", default="bench", choices=["bench", "plenoptic", "tiny"])
     ap.add_argument("--cpu-rows", type=int, default=128)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--batch-lfs", type=int, default=64, help="light fields in the mixed batch (0: skip)")
+    ap.add_argument("--batch-branches", type=int, default=0, help="concurrent branches (0: autotune)")
+    ap.add_argument("--no-backward", dest="backward", action="store_false")
     args = ap.parse_args()
     ws, rank, local = dist_env()
     if args.impl == "reference":

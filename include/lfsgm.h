@@ -168,6 +168,27 @@ lfsgm_status lfsgm_depth_host(lfsgm_handle h, const float *views_host, float *di
  * the same chain as lfsgm_depth_host without the copies. disp, label: device, nullable. */
 lfsgm_status lfsgm_depth(lfsgm_handle h, const float *views, float *disp, int32_t *label);
 
+/* Batches (not in the paper): n light fields of mixed shape run as ONE CUDA-graph launch.
+ * Each light field i has its own configuration cfgs[i], views[i] ([V][U][H][W] float32, device)
+ * and output disp[i] ([H*W] float32, device); the pointers are baked into the graph at creation.
+ * The pipeline of lfsgm_depth (derived penalties) runs for every light field; light fields are
+ * spread over `branches` concurrent streams forked from `stream` (longest work first), branches
+ * <= 0 lets an autotuner time K in {1,2,4,8,16} and keep the fastest.  Scratch is allocated at
+ * creation (per branch, sized for its largest member).  lfsgm_batch_run enqueues one graph launch;
+ * lfsgm_batch_times synchronises and returns, per light field, the start and end of its pipeline
+ * in ms after the batch started (%globaltimer stamps inside the graph), and the branch count.
+ * The light fields of one branch share one device status word (offset 0 of the branch's
+ * workspace): a device-side check that fails in any of them is reported by lfsgm_batch_times
+ * and stays latched for later runs of the batch. */
+typedef struct lfsgm_batch_ctx *lfsgm_batch;
+lfsgm_status lfsgm_batch_create(int32_t n, const lfsgm_config *cfgs, const float *const *views,
+                                float *const *disp, void *stream, int32_t branches, lfsgm_batch *out);
+lfsgm_status lfsgm_batch_run(lfsgm_batch b);
+lfsgm_status lfsgm_batch_times(lfsgm_batch b, double *start_ms, double *end_ms, int32_t *branches);
+int64_t lfsgm_batch_kernel_nodes(lfsgm_batch b);    /* kernel nodes in the batch's graph */
+const char *lfsgm_batch_last_error(lfsgm_batch b);  /* NULL: error of the last failed create */
+lfsgm_status lfsgm_batch_destroy(lfsgm_batch b);
+
 /* The bounded cost volume (same result as lfsgm_cost_volume) for callers that may not
  * allocate device memory.  The paper has no counterpart: this is a deployment variant.
  * Real-time loops and plug-ins that live inside a host application's own memory pool run

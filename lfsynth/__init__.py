@@ -287,3 +287,144 @@ def random_views(U, V, H, W, seed=0, lo=0.0, hi=1.0):
 
 
 WORKLOADS = {"tiny": tiny, "bench": bench, "plenoptic": plenoptic}
+
+
+# ------------------------------------------------------------------ device-side rendering
+def _scene(p: LFParams, seed: int, n_planes: int, a_range, slope, clamp):
+    """Textures, Voronoi sites and planes of a Voronoi scene (the draws of ``voronoi_scene``)."""
+    tex_rng, geo_rng, _ = _streams(seed)
+    margin = int(math.ceil(max(abs(p.dmin), abs(p.dmax)) * max(p.U, p.V))) + 2
+    th, tw = p.H + 2 * margin, p.W + 2 * margin
+    textures = [_blur121(tex_rng.uniform(0.0, 1.0, size=(th, tw))) for _ in range(n_planes)]
+    sites = np.stack([geo_rng.uniform(0, p.W, n_planes), geo_rng.uniform(0, p.H, n_planes)], 1)
+    planes = []
+    for _ in range(n_planes):
+        a = geo_rng.uniform(*a_range)
+        b = geo_rng.uniform(-slope, slope)
+        c = geo_rng.uniform(-slope, slope)
+        ext = 0.5 * (abs(b) + abs(c))
+        planes.append(Plane(float(np.clip(a, -clamp + ext, clamp - ext)), b, c))
+    return textures, sites, planes, margin
+
+
+def voronoi_scene_torch(p: LFParams, seed: int, n_planes: int, a_range, slope, clamp, sigma,
+                        vignette=False, device="cpu", noise_seed=None):
+    """The scene of ``voronoi_scene`` rendered with torch on ``device`` (float64 geometry).
+
+    Same textures, sites and planes; the Voronoi cell of a point is that of its nearest 1/4-px
+    raster position, computed directly instead of through the raster.  The noise comes from a
+    ``torch.Generator`` seeded with ``noise_seed`` (default: ``seed``), so it differs from the
+    NumPy stream of ``voronoi_scene``; with ``sigma = 0`` both renderers agree up to rounding.
+    Returns views [V][U][H][W] float32 on ``device``."""
+    import torch
+    dev = torch.device(device)
+    f64 = torch.float64
+    textures, sites, planes, margin = _scene(p, seed, n_planes, a_range, slope, clamp)
+    U, V, H, W = p.U, p.V, p.H, p.W
+    tex = torch.from_numpy(np.stack(textures)).to(dev)
+    ntex, th, tw = tex.shape
+    flat = tex.reshape(-1)
+    sx = torch.tensor(sites[:, 0], dtype=f64, device=dev).view(-1, 1, 1)
+    sy = torch.tensor(sites[:, 1], dtype=f64, device=dev).view(-1, 1, 1)
+    Y, X = torch.meshgrid(torch.arange(H, dtype=f64, device=dev), torch.arange(W, dtype=f64, device=dev),
+                          indexing="ij")
+    gen = torch.Generator(device=dev)
+    gen.manual_seed(seed if noise_seed is None else noise_seed)
+    q = 4
+
+    def cell(x, y):
+        qx = torch.clamp(torch.round((x + margin) * q), 0, tw * q - 1) / q - margin
+        qy = torch.clamp(torch.round((y + margin) * q), 0, th * q - 1) / q - margin
+        d2 = (qx.unsqueeze(0) - sx) ** 2 + (qy.unsqueeze(0) - sy) ** 2
+        return torch.argmin(d2, dim=0)
+
+    def sample(idx, x, y):
+        gx = torch.clamp(x + margin, 0.0, tw - 1.000001)
+        gy = torch.clamp(y + margin, 0.0, th - 1.000001)
+        x0 = torch.floor(gx)
+        y0 = torch.floor(gy)
+        fx, fy = gx - x0, gy - y0
+        base = idx * (th * tw) + y0.long() * tw + x0.long()
+        t00, t10 = flat[base], flat[base + 1]
+        t01, t11 = flat[base + tw], flat[base + tw + 1]
+        return (1 - fy) * ((1 - fx) * t00 + fx * t10) + fy * ((1 - fx) * t01 + fx * t11)
+
+    views = torch.empty((V, U, H, W), dtype=torch.float32, device=dev)
+    inf = torch.tensor(float("inf"), dtype=f64, device=dev)
+    for v in range(V):
+        for u in range(U):
+            a, b = u - p.uc, v - p.vc
+            best_d = torch.full((H, W), -float("inf"), dtype=f64, device=dev)
+            far_d = torch.full((H, W), float("inf"), dtype=f64, device=dev)
+            bi = torch.zeros((H, W), dtype=torch.long, device=dev)
+            fi = torch.zeros_like(bi)
+            bx, by, fxv, fyv = (torch.zeros((H, W), dtype=f64, device=dev) for _ in range(4))
+            for i, pl in enumerate(planes):
+                kx, ky = pl.b / W, pl.c / H
+                k0 = pl.a - kx * 0.5 * (W - 1) - ky * 0.5 * (H - 1)
+                m00, m01 = 1.0 + a * kx, a * ky
+                m10, m11 = b * kx, 1.0 + b * ky
+                r0, r1 = X - a * k0, Y - b * k0
+                det = m00 * m11 - m01 * m10
+                x = (m11 * r0 - m01 * r1) / det
+                y = (m00 * r1 - m10 * r0) / det
+                d = pl.disp(x, y, W, H)
+                take = (cell(x, y) == i) & (d > best_d)
+                best_d = torch.where(take, d, best_d)
+                bi = torch.where(take, torch.full_like(bi, i), bi)
+                bx = torch.where(take, x, bx)
+                by = torch.where(take, y, by)
+                fall = d < far_d
+                far_d = torch.where(fall, d, far_d)
+                fi = torch.where(fall, torch.full_like(fi, i), fi)
+                fxv = torch.where(fall, x, fxv)
+                fyv = torch.where(fall, y, fyv)
+            hole = ~torch.isfinite(best_d)
+            img = sample(torch.where(hole, fi, bi), torch.where(hole, fxv, bx), torch.where(hole, fyv, by))
+            if sigma > 0:
+                img = img + sigma * torch.randn((H, W), generator=gen, dtype=f64, device=dev)
+            if vignette:
+                rho2 = (a * a + b * b) / float(max(p.uc, 1) ** 2 + max(p.vc, 1) ** 2)
+                r2 = ((X - 0.5 * (W - 1)) ** 2 + (Y - 0.5 * (H - 1)) ** 2) / (
+                    (0.5 * (W - 1)) ** 2 + (0.5 * (H - 1)) ** 2)
+                img = img * (1.0 - 0.3 * rho2 * (0.5 + 0.5 * r2))
+            views[v, u] = torch.clamp(img, 0.0, 1.0).to(torch.float32)
+    del inf
+    return views
+
+
+# Shape classes of the mixed batch: 5x5 x 256^2, 9x9 x 512^2, 4x4 camera-array frames of
+# 1280x720 and 15x15 x 434x625 plenoptic images, each with its own disparity range, fine grid
+# and scene statistics.
+BATCH_CLASSES = (
+    dict(U=5, V=5, H=256, W=256, dmin=-2.0, dmax=2.0, fine_labels=201, fine_radius=10,
+         scene=((-1.7, 1.7), 0.4, 2.0, 0.01, False), name="5x5x256x256"),
+    dict(U=9, V=9, H=512, W=512, dmin=-4.0, dmax=4.0, fine_labels=401, fine_radius=15,
+         scene=((-3.4, 3.4), 0.5, 4.0, 0.01, False), name="9x9x512x512"),
+    dict(U=4, V=4, H=720, W=1280, dmin=-6.0, dmax=6.0, fine_labels=241, fine_radius=8,
+         scene=((-5.0, 5.0), 0.8, 6.0, 0.01, False), name="4x4x720x1280"),
+    dict(U=15, V=15, H=434, W=625, dmin=-1.5, dmax=1.5, fine_labels=301, fine_radius=15,
+         scene=((-1.2, 1.2), 0.3, 1.5, 0.02, True), name="15x15x434x625"),
+)
+
+
+def batch_params(i: int) -> LFParams:
+    """Light field i of the mixed batch: shape class i mod 4, census 5x5 / 7x7 alternating
+    every 4 light fields, coarse labels cycling 16, 32, 64, 128 every 8."""
+    c = BATCH_CLASSES[i % 4]
+    census = (5, 7)[(i // 4) % 2]
+    lc = (16, 32, 64, 128)[(i // 8) % 4]
+    return LFParams(U=c["U"], V=c["V"], H=c["H"], W=c["W"], census_w=census, dmin=c["dmin"], dmax=c["dmax"],
+                    coarse_labels=lc, fine_labels=c["fine_labels"], fine_radius=c["fine_radius"],
+                    name=f'{c["name"]} census {census} Lc {lc}')
+
+
+def batch_lf(i: int, device="cpu", scale: float = 1.0):
+    """Views of light field i of the mixed batch (seed 1000 * 4 + i), rendered on ``device``.
+    ``scale`` < 1 shrinks H and W (for tests)."""
+    p = batch_params(i)
+    if scale != 1.0:
+        p = dataclasses.replace(p, H=max(16, int(round(p.H * scale))), W=max(16, int(round(p.W * scale))))
+    a_range, slope, clamp, sigma, vig = BATCH_CLASSES[i % 4]["scene"]
+    views = voronoi_scene_torch(p, 1000 * 4 + i, 8, a_range, slope, clamp, sigma, vig, device=device)
+    return views, p

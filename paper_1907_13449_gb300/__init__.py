@@ -57,7 +57,9 @@ EXPORTS = ["lfsgm_create", "lfsgm_destroy", "lfsgm_workspace_size", "lfsgm_set_w
            "lfsgm_max_nnz", "lfsgm_initial_disparity", "lfsgm_cost_volume", "lfsgm_sgm_aggregate",
            "lfsgm_wta_subpixel", "lfsgm_backward", "lfsgm_sync", "lfsgm_last_error",
            "lfsgm_launch_count", "lfsgm_set_profiling", "lfsgm_kernel_times", "lfsgm_depth_host",
-           "lfsgm_depth", "lfsgm_cost_volume_noalloc"]
+           "lfsgm_depth", "lfsgm_cost_volume_noalloc", "lfsgm_batch_create", "lfsgm_batch_run",
+           "lfsgm_batch_times", "lfsgm_batch_kernel_nodes", "lfsgm_batch_last_error",
+           "lfsgm_batch_destroy"]
 
 
 def load(build_if_missing: bool = False):
@@ -95,8 +97,17 @@ def load(build_if_missing: bool = False):
         L.lfsgm_depth_host.argtypes = [vp, vp, vp, vp]
         L.lfsgm_depth.argtypes = [vp, vp, vp, vp]
         L.lfsgm_cost_volume_noalloc.argtypes = [P(Config), vp, vp, vp, vp, vp, vp]
+        L.lfsgm_batch_create.argtypes = [i32, P(Config), P(vp), P(vp), vp, i32, P(vp)]
+        L.lfsgm_batch_run.argtypes = [vp]
+        L.lfsgm_batch_times.argtypes = [vp, P(C.c_double), P(C.c_double), P(i32)]
+        L.lfsgm_batch_kernel_nodes.argtypes = [vp]
+        L.lfsgm_batch_kernel_nodes.restype = i64
+        L.lfsgm_batch_last_error.argtypes = [vp]
+        L.lfsgm_batch_last_error.restype = C.c_char_p
+        L.lfsgm_batch_destroy.argtypes = [vp]
         for name in EXPORTS:
-            if name not in ("lfsgm_last_error", "lfsgm_launch_count"):
+            if name not in ("lfsgm_last_error", "lfsgm_launch_count", "lfsgm_batch_kernel_nodes",
+                            "lfsgm_batch_last_error"):
                 getattr(L, name).restype = i32
         _lib = L
         return L
@@ -270,6 +281,95 @@ def lfsgm_cost_volume_noalloc(cfg, views, lo, cnt, off, cost, stream=None):
         raise LfsgmError(st, "lfsgm_cost_volume_noalloc: " + {1: "invalid config or null buffer",
                                                               5: "light field too large for the static scratch",
                                                               4: "CUDA error"}.get(st, ""))
+
+
+# ------------------------------------------------------------------ batches (not in the paper)
+def _bcheck(st: int, b=None):
+    if st != OK:
+        raise LfsgmError(st, (load().lfsgm_batch_last_error(b) or b"").decode())
+
+
+def lfsgm_batch_create(cfgs, views, disp, stream=None, branches=0):
+    """One CUDA graph running the whole depth pipeline of every light field.  ``cfgs``: list of
+    Config (or parameter objects); ``views``/``disp``: lists of device float32 tensors
+    ([V,U,H,W] and [H*W]) whose addresses are baked into the graph.  ``branches`` <= 0 lets the
+    library time 1, 2, 4, 8, 16 concurrent branches and keep the fastest."""
+    import torch
+    n = len(cfgs)
+    if n < 1 or len(views) != n or len(disp) != n:
+        raise ValueError("need equally long, non-empty cfgs, views and disp")
+    arr = (Config * n)(*[c if isinstance(c, Config) else make_config(c) for c in cfgs])
+    vptr = (C.c_void_p * n)(*[_ptr(v, torch.float32, "views") for v in views])
+    dptr = (C.c_void_p * n)(*[_ptr(d, torch.float32, "disp") for d in disp])
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    b = C.c_void_p()
+    _bcheck(load().lfsgm_batch_create(n, arr, vptr, dptr, C.c_void_p(stream.cuda_stream), int(branches),
+                                      C.byref(b)), None)
+    return b
+
+
+def lfsgm_batch_run(b):
+    _bcheck(load().lfsgm_batch_run(b), b)
+
+
+def lfsgm_batch_times(b, n):
+    """(start_ms, end_ms, branches): per light field, when its pipeline started and ended
+    relative to the start of the last batch run (synchronises)."""
+    import numpy as np
+    s = np.zeros(n, np.float64)
+    e = np.zeros(n, np.float64)
+    k = C.c_int32()
+    _bcheck(load().lfsgm_batch_times(b, s.ctypes.data_as(C.POINTER(C.c_double)),
+                                     e.ctypes.data_as(C.POINTER(C.c_double)), C.byref(k)), b)
+    return s, e, k.value
+
+
+def lfsgm_batch_kernel_nodes(b) -> int:
+    return int(load().lfsgm_batch_kernel_nodes(b))
+
+
+def lfsgm_batch_last_error(b) -> str:
+    return (load().lfsgm_batch_last_error(b) or b"").decode()
+
+
+def lfsgm_batch_destroy(b):
+    _bcheck(load().lfsgm_batch_destroy(b), None)
+
+
+class LightFieldBatch:
+    """Owns the batch graph, the output disparity maps and references to the input views."""
+
+    def __init__(self, params, views, branches=0, stream=None):
+        import torch
+        self.params = list(params)
+        self.views = [v.contiguous() for v in views]
+        self.disp = [torch.empty(p.H * p.W, dtype=torch.float32, device=v.device)
+                     for p, v in zip(self.params, self.views)]
+        self.b = lfsgm_batch_create(self.params, self.views, self.disp, stream, branches)
+        self.n = len(self.params)
+
+    def run(self):
+        lfsgm_batch_run(self.b)
+        return self.disp
+
+    def times(self):
+        return lfsgm_batch_times(self.b, self.n)
+
+    @property
+    def kernel_nodes(self):
+        return lfsgm_batch_kernel_nodes(self.b)
+
+    def close(self):
+        if self.b is not None:
+            lfsgm_batch_destroy(self.b)
+            self.b = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 # ------------------------------------------------------------------ differentiation (not in the paper)

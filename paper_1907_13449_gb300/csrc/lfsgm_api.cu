@@ -13,6 +13,7 @@
 #include <cstring>
 #include <string>
 #include <vector>
+#include <string>
 
 #include "../../include/lfsgm.h"
 #include "lfsgm_internal.cuh"
@@ -232,6 +233,8 @@ lfsgm_status bind_workspace(lfsgm_ctx *h, void *dptr, size_t bytes, bool owned) 
     const size_t N = (size_t)h->N, A = (size_t)std::max(h->arms.n_arms, 1);
     char *p = (char *)dptr;
     auto take = [&](size_t n) { char *q = p; p += align256(n); return (void *)q; };
+    // the status word comes first, so handles that share one workspace (a batch branch) share it
+    h->status = (int *)take(4);
     const size_t HWp = (size_t)h->rows.Hp * h->rows.Wp;
     h->cen_pad = (uint64_t *)take(h->nviews * HWp * 8);
     h->views_pad = (float *)take(h->nviews * HWp * 4);
@@ -248,7 +251,6 @@ lfsgm_status bind_workspace(lfsgm_ctx *h, void *dptr, size_t bytes, bool owned) 
     h->cpen = (int *)take(8 * 4);
     h->fpen = (float *)take(2 * 4);
     h->partial = (double *)take(2 * kPartialBlocks * 8);
-    h->status = (int *)take(4);
     h->tsum = (long long *)take((size_t)scan_tiles(h->N) * 8);
     const cudaError_t e = cudaMemsetAsync(h->status, 0, 4, h->stream);
     if (e != cudaSuccess) return cuda_fail(h, e, "status clear");
@@ -339,8 +341,7 @@ lfsgm_status lfsgm_create(const lfsgm_config *cfg, void *stream, lfsgm_handle *o
 
 lfsgm_status lfsgm_destroy(lfsgm_handle h) {
     if (!h) return LFSGM_ERR_INVALID_ARG;
-    if (h->stream) cudaStreamSynchronize(h->stream);
-    else cudaDeviceSynchronize();
+    cudaDeviceSynchronize();
     cudaFree(h->d_fine);
     cudaFree(h->d_coarse);
     cudaFree(h->d_armviews);
@@ -678,6 +679,313 @@ lfsgm_status lfsgm_depth_host(lfsgm_handle h, const float *views_host, float *di
     if (e == cudaSuccess && label_host) e = cudaMemcpyAsync(label_host, h->o_label, N * 4, cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) return cuda_fail(h, e, "result download");
+    return LFSGM_OK;
+}
+
+}  // extern "C"
+
+// ------------------------------------------------------------------------------------------
+// Batches (not in the paper): many light fields of mixed shape in one CUDA-graph launch.
+//
+// One handle per light field (its own tables and configuration).  The light fields are split
+// over K branches (streams forked from the caller's stream); within a branch they run one after
+// another and share one set of scratch buffers sized for the branch's largest member.  The whole
+// batch -- every stage of every light field plus a %globaltimer stamp before and after each light
+// field -- is captured once into a CUDA graph, so a batch is one graph launch.  Branch count and
+// assignment come from a small autotuner: longest-job-first assignment for each candidate K in
+// {1, 2, 4, 8, 16}, each timed on the device, the fastest kept (or K given by the caller).
+
+namespace {
+
+__global__ void stamp_kernel(unsigned long long *t) {
+    unsigned long long v;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(v));
+    *t = v;
+}
+
+struct BranchBufs {
+    void *ws = nullptr;
+    size_t ws_bytes = 0;
+    int *lo = nullptr, *cnt = nullptr, *label = nullptr;
+    long long *off = nullptr;
+    float *cost = nullptr, *agg = nullptr;
+};
+
+}  // namespace
+
+struct lfsgm_batch_ctx {
+    int n = 0;
+    std::vector<lfsgm_ctx *> h;
+    std::vector<const float *> views;
+    std::vector<float *> disp;
+    std::vector<double> work;           // work estimate per light field (scheduling)
+    cudaStream_t main = nullptr;       // the caller's stream: graph launches go here
+    cudaStream_t cap = nullptr;        // private stream the graph is captured from
+    int branches = 0;
+    std::vector<std::vector<int>> plan;  // light fields of each branch, in order
+    std::vector<cudaStream_t> bs;
+    std::vector<cudaEvent_t> join;
+    cudaEvent_t fork = nullptr;
+    std::vector<BranchBufs> bb;
+    unsigned long long *stamps = nullptr;   // [1 + 2n]: batch start, then (start, end) per light field
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    long long kernel_nodes = 0;
+    std::string err;
+};
+
+namespace {
+
+lfsgm_status bfail(lfsgm_batch_ctx *b, lfsgm_status st, const char *fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    if (b) b->err = buf;
+    return st;
+}
+
+void batch_release_plan(lfsgm_batch_ctx *b) {
+    if (b->exec) cudaGraphExecDestroy(b->exec);
+    if (b->graph) cudaGraphDestroy(b->graph);
+    b->exec = nullptr;
+    b->graph = nullptr;
+    for (auto &x : b->bb) {
+        cudaFree(x.ws);
+        cudaFree(x.lo); cudaFree(x.cnt); cudaFree(x.label); cudaFree(x.off); cudaFree(x.cost); cudaFree(x.agg);
+    }
+    b->bb.clear();
+    for (auto s : b->bs) cudaStreamDestroy(s);
+    for (auto e : b->join) cudaEventDestroy(e);
+    b->bs.clear();
+    b->join.clear();
+    for (auto *h : b->h) {          // the handles no longer own or see any workspace
+        h->ws = nullptr;
+        h->ws_owned = false;
+    }
+}
+
+// Longest-job-first assignment of the light fields to K branches, then buffers, streams and graph.
+lfsgm_status batch_build(lfsgm_batch_ctx *b, int K) {
+    batch_release_plan(b);
+    b->branches = K;
+    b->plan.assign(K, {});
+    std::vector<int> idx(b->n);
+    for (int i = 0; i < b->n; i++) idx[i] = i;
+    std::sort(idx.begin(), idx.end(), [&](int a, int c) { return b->work[a] > b->work[c]; });
+    std::vector<double> load(K, 0.0);
+    for (int i : idx) {
+        const int k = (int)(std::min_element(load.begin(), load.end()) - load.begin());
+        b->plan[k].push_back(i);
+        load[k] += b->work[i];
+    }
+    b->bb.assign(K, BranchBufs());
+    b->bs.assign(K, nullptr);
+    b->join.assign(K, nullptr);
+    for (int k = 0; k < K; k++) {
+        size_t ws = 0, N = 0;
+        int64_t nnz = 0;
+        for (int i : b->plan[k]) {
+            size_t w = 0;
+            lfsgm_workspace_size(b->h[i], &w);
+            int64_t m = 0;
+            lfsgm_max_nnz(b->h[i], &m);
+            ws = std::max(ws, w);
+            N = std::max(N, (size_t)b->h[i]->N);
+            nnz = std::max(nnz, m);
+        }
+        BranchBufs &x = b->bb[k];
+        cudaError_t e = cudaStreamCreateWithFlags(&b->bs[k], cudaStreamNonBlocking);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->join[k], cudaEventDisableTiming);
+        if (ws > 0 && e == cudaSuccess) e = cudaMalloc(&x.ws, ws);
+        if (N > 0 && e == cudaSuccess) e = cudaMalloc((void **)&x.lo, N * 4);
+        if (N > 0 && e == cudaSuccess) e = cudaMalloc((void **)&x.cnt, N * 4);
+        if (N > 0 && e == cudaSuccess) e = cudaMalloc((void **)&x.label, N * 4);
+        if (N > 0 && e == cudaSuccess) e = cudaMalloc((void **)&x.off, (N + 1) * 8);
+        if (nnz > 0 && e == cudaSuccess) e = cudaMalloc((void **)&x.cost, (size_t)nnz * 4);
+        if (nnz > 0 && e == cudaSuccess) e = cudaMalloc((void **)&x.agg, (size_t)nnz * 4);
+        if (e != cudaSuccess) return bfail(b, LFSGM_ERR_NO_MEMORY, "batch buffers: %s", cudaGetErrorString(e));
+        x.ws_bytes = ws;
+        for (int i : b->plan[k]) {
+            b->h[i]->stream = b->bs[k];
+            const lfsgm_status st = bind_workspace(b->h[i], x.ws, x.ws_bytes, false);
+            if (st != LFSGM_OK) return bfail(b, st, "workspace of light field %d: %s", i, b->h[i]->err.c_str());
+        }
+    }
+    // capture
+    cudaError_t e = cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeRelaxed);
+    if (e != cudaSuccess) return bfail(b, LFSGM_ERR_CUDA, "begin capture: %s", cudaGetErrorString(e));
+    lfsgm_status st = LFSGM_OK;
+    stamp_kernel<<<1, 1, 0, b->cap>>>(b->stamps);
+    cudaEventRecord(b->fork, b->cap);
+    for (int k = 0; k < K && st == LFSGM_OK; k++) {
+        cudaStreamWaitEvent(b->bs[k], b->fork, 0);
+        BranchBufs &x = b->bb[k];
+        for (int i : b->plan[k]) {
+            lfsgm_ctx *h = b->h[i];
+            stamp_kernel<<<1, 1, 0, b->bs[k]>>>(b->stamps + 1 + 2 * i);
+            int64_t *off = (int64_t *)x.off;
+            st = lfsgm_initial_disparity(h, b->views[i], 0, 0, x.lo, x.cnt, off, nullptr, nullptr, nullptr);
+            if (st == LFSGM_OK) st = lfsgm_cost_volume(h, b->views[i], x.lo, x.cnt, off, x.cost);
+            if (st == LFSGM_OK) st = lfsgm_sgm_aggregate(h, x.cost, x.lo, x.cnt, off, -1.f, -1.f, x.agg);
+            if (st == LFSGM_OK) st = lfsgm_wta_subpixel(h, x.agg, x.lo, x.cnt, off, x.label, b->disp[i]);
+            if (st != LFSGM_OK) {
+                bfail(b, st, "light field %d: %s", i, h->err.c_str());
+                break;
+            }
+            stamp_kernel<<<1, 1, 0, b->bs[k]>>>(b->stamps + 2 + 2 * i);
+        }
+        cudaEventRecord(b->join[k], b->bs[k]);
+        cudaStreamWaitEvent(b->cap, b->join[k], 0);
+    }
+    cudaGraph_t g = nullptr;
+    e = cudaStreamEndCapture(b->cap, &g);
+    if (st != LFSGM_OK) {
+        if (g) cudaGraphDestroy(g);
+        return st;
+    }
+    if (e != cudaSuccess) return bfail(b, LFSGM_ERR_CUDA, "end capture: %s", cudaGetErrorString(e));
+    b->graph = g;
+    e = cudaGraphInstantiate(&b->exec, g, 0);
+    if (e != cudaSuccess) return bfail(b, LFSGM_ERR_CUDA, "instantiate: %s", cudaGetErrorString(e));
+    size_t nn = 0;
+    cudaGraphGetNodes(g, nullptr, &nn);
+    std::vector<cudaGraphNode_t> nodes(nn);
+    cudaGraphGetNodes(g, nodes.data(), &nn);
+    b->kernel_nodes = 0;
+    for (auto nd : nodes) {
+        cudaGraphNodeType t;
+        if (cudaGraphNodeGetType(nd, &t) == cudaSuccess && t == cudaGraphNodeTypeKernel) b->kernel_nodes++;
+    }
+    return LFSGM_OK;
+}
+
+float batch_time_ms(lfsgm_batch_ctx *b, int reps) {
+    cudaEvent_t a, c;
+    cudaEventCreate(&a);
+    cudaEventCreate(&c);
+    float best = 1e30f;
+    for (int r = 0; r < reps; r++) {
+        cudaEventRecord(a, b->main);
+        cudaGraphLaunch(b->exec, b->main);
+        cudaEventRecord(c, b->main);
+        cudaEventSynchronize(c);
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, a, c);
+        best = std::min(best, ms);
+    }
+    cudaEventDestroy(a);
+    cudaEventDestroy(c);
+    return best;
+}
+
+}  // namespace
+
+extern "C" {
+
+lfsgm_status lfsgm_batch_create(int32_t n, const lfsgm_config *cfgs, const float *const *views, float *const *disp,
+                                void *stream, int32_t branches, lfsgm_batch *out) {
+    if (!out) return LFSGM_ERR_INVALID_ARG;
+    *out = nullptr;
+    if (n < 1 || !cfgs || !views || !disp) return LFSGM_ERR_INVALID_ARG;
+    lfsgm_batch_ctx *b = new lfsgm_batch_ctx();
+    b->n = n;
+    b->main = (cudaStream_t)stream;
+    for (int i = 0; i < n; i++) {
+        if (!views[i] || !disp[i]) {
+            g_create_err = "null views or disp pointer";
+            lfsgm_batch_destroy(b);
+            return LFSGM_ERR_INVALID_ARG;
+        }
+        lfsgm_handle h = nullptr;
+        const lfsgm_status st = lfsgm_create(&cfgs[i], stream, &h);
+        if (st != LFSGM_OK) {
+            g_create_err = "light field " + std::to_string(i) + ": " + g_create_err;
+            lfsgm_batch_destroy(b);
+            return st;
+        }
+        b->h.push_back(h);
+        b->views.push_back(views[i]);
+        b->disp.push_back(disp[i]);
+        const lfsgm_config &c = h->cfg;
+        b->work.push_back((double)h->N * ((double)h->nviews * (2 * c.fine_radius + 1) + 4.0 * c.coarse_labels));
+    }
+    cudaError_t e = cudaMalloc((void **)&b->stamps, (1 + 2 * (size_t)n) * 8);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaMemset(b->stamps, 0, (1 + 2 * (size_t)n) * 8);
+    if (e != cudaSuccess) {
+        g_create_err = cudaGetErrorString(e);
+        lfsgm_batch_destroy(b);
+        return LFSGM_ERR_CUDA;
+    }
+    lfsgm_status st;
+    if (branches > 0) {
+        st = batch_build(b, std::min(branches, n));
+    } else {
+        int bestK = 1;
+        float best = 1e30f;
+        for (int K : {1, 2, 4, 8, 16}) {
+            if (K > n) break;
+            st = batch_build(b, K);
+            if (st != LFSGM_OK) break;
+            batch_time_ms(b, 1);                      // warm-up
+            const float ms = batch_time_ms(b, 2);
+            if (ms < best) {
+                best = ms;
+                bestK = K;
+            }
+        }
+        st = batch_build(b, bestK);
+    }
+    if (st != LFSGM_OK) {
+        g_create_err = b->err;
+        lfsgm_batch_destroy(b);
+        return st;
+    }
+    *out = b;
+    return LFSGM_OK;
+}
+
+lfsgm_status lfsgm_batch_run(lfsgm_batch b) {
+    if (!b || !b->exec) return LFSGM_ERR_INVALID_ARG;
+    const cudaError_t e = cudaGraphLaunch(b->exec, b->main);
+    if (e != cudaSuccess) return bfail(b, LFSGM_ERR_CUDA, "graph launch: %s", cudaGetErrorString(e));
+    return LFSGM_OK;
+}
+
+lfsgm_status lfsgm_batch_times(lfsgm_batch b, double *start_ms, double *end_ms, int32_t *branches) {
+    if (!b) return LFSGM_ERR_INVALID_ARG;
+    cudaError_t e = cudaStreamSynchronize(b->main);
+    std::vector<unsigned long long> t(1 + 2 * (size_t)b->n);
+    if (e == cudaSuccess) e = cudaMemcpy(t.data(), b->stamps, t.size() * 8, cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return bfail(b, LFSGM_ERR_CUDA, "stamps: %s", cudaGetErrorString(e));
+    for (int i = 0; i < b->n; i++) {
+        if (start_ms) start_ms[i] = (double)(long long)(t[1 + 2 * i] - t[0]) * 1e-6;
+        if (end_ms) end_ms[i] = (double)(long long)(t[2 + 2 * i] - t[0]) * 1e-6;
+    }
+    if (branches) *branches = b->branches;
+    for (auto *h : b->h) {
+        const lfsgm_status st = lfsgm_sync(h);
+        if (st != LFSGM_OK) return bfail(b, st, "%s", h->err.c_str());
+    }
+    return LFSGM_OK;
+}
+
+int64_t lfsgm_batch_kernel_nodes(lfsgm_batch b) { return b ? b->kernel_nodes : -1; }
+
+const char *lfsgm_batch_last_error(lfsgm_batch b) { return b ? b->err.c_str() : g_create_err.c_str(); }
+
+lfsgm_status lfsgm_batch_destroy(lfsgm_batch b) {
+    if (!b) return LFSGM_ERR_INVALID_ARG;
+    if (!b->h.empty() || b->stamps) cudaDeviceSynchronize();
+    batch_release_plan(b);
+    for (auto *h : b->h) lfsgm_destroy(h);
+    cudaFree(b->stamps);
+    if (b->fork) cudaEventDestroy(b->fork);
+    if (b->cap) cudaStreamDestroy(b->cap);
+    delete b;
     return LFSGM_OK;
 }
 

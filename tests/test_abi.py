@@ -106,3 +106,20 @@ def test_null_arguments_rejected(lib):
     assert lib.lfsgm_destroy(None) == 1
     assert lib.lfsgm_sync(None) == 1
     assert lib.lfsgm_launch_count(None) == -1
+
+
+def test_batch_arguments_rejected_before_any_cuda_call(lib):
+    import lfsynth
+    import paper_1907_13449_gb300 as lf
+    out = C.c_void_p(123)
+    assert lib.lfsgm_batch_create(0, None, None, None, None, 0, C.byref(out)) == 1
+    assert out.value is None
+    assert lib.lfsgm_batch_run(None) == 1
+    assert lib.lfsgm_batch_destroy(None) == 1
+    assert lib.lfsgm_batch_kernel_nodes(None) == -1
+    cfgs = (lf.Config * 2)(lf.make_config(lfsynth.tiny_params(fine_labels=1)),
+                           lf.make_config(lfsynth.tiny_params()))
+    ptrs = (C.c_void_p * 2)(16, 32)          # never dereferenced: validation fails first
+    assert lib.lfsgm_batch_create(2, cfgs, ptrs, ptrs, None, 0, C.byref(out)) == 1
+    msg = lib.lfsgm_batch_last_error(None).decode()
+    assert msg.startswith("light field 0") and "fine_labels" in msg

@@ -1,0 +1,108 @@
+"""The batch runner (one CUDA graph for many light fields of mixed shape) against the oracle
+and against one-light-field launches.
+
+Eight light fields of the mixed batch, shrunk to 15% of their size: all four shape classes,
+census 5x5 and 7x7, coarse label counts 16, 32, 64 and 128.  A batch returns sub-pixel
+disparities only, so a pixel is checked where the oracle's WTA decision is not a near-tie
+(gap > 1e-5 * scale): there the disparity must agree within 1e-3 px."""
+import numpy as np
+import pytest
+
+import lfsynth
+import oracle
+from lf_helpers import DISP_TOL, TIE_REL, best_of
+
+pytestmark = pytest.mark.gpu
+
+PICK = (0, 5, 10, 15, 16, 21, 26, 31)
+
+
+@pytest.fixture(scope="module")
+def mix():
+    out = []
+    for i in PICK:
+        views, p = lfsynth.batch_lf(i, device="cpu", scale=0.15)
+        views = views.numpy()
+        cfg = oracle.make_cfg(p)
+        ref = oracle.depth(cfg, views, p1f=p.p1_frac, p2f=p.p2_frac)
+        best = best_of(ref["Cs"], ref["off"], ref["cnt"], ref["label"], ref["lo"])
+        decided = ref["gap"] > TIE_REL * np.maximum(1.0, np.abs(best))
+        out.append((p, views, ref, decided))
+    return out
+
+
+def _batch(lf, mix, branches):
+    import torch
+    views = [torch.from_numpy(v).cuda() for _, v, _, _ in mix]
+    b = lf.LightFieldBatch([m[0] for m in mix], views, branches=branches)
+    disp = [d.cpu().numpy() for d in b.run()]
+    torch.cuda.synchronize()
+    start, end, k = b.times()
+    nodes = b.kernel_nodes
+    b.close()
+    return disp, start, end, k, nodes
+
+
+def _check_vs_oracle(disp, mix):
+    for d, (p, _, ref, decided) in zip(disp, mix):
+        err = np.abs(d - ref["disp"])[decided]
+        assert err.size > 0.9 * p.N, p.name
+        assert np.max(err) < DISP_TOL, (p.name, float(np.max(err)))
+
+
+def test_batch_matches_oracle(gpu_lib, mix):
+    disp, start, end, k, nodes = _batch(gpu_lib, mix, branches=3)
+    assert k == 3
+    _check_vs_oracle(disp, mix)
+    assert nodes > 10 * len(mix)
+
+
+def test_batch_single_branch_reuses_buffers_across_shapes(gpu_lib, mix):
+    """One branch: every light field runs in the scratch buffers of the largest one."""
+    disp, start, end, k, _ = _batch(gpu_lib, mix, branches=1)
+    assert k == 1
+    _check_vs_oracle(disp, mix)
+    order = np.argsort(start)
+    # on one branch the light fields run one after another
+    assert np.all(start[order][1:] >= end[order][:-1])
+
+
+def test_batch_autotuned_times_are_consistent(gpu_lib, mix):
+    disp, start, end, k, _ = _batch(gpu_lib, mix, branches=0)
+    assert k in (1, 2, 4, 8)
+    _check_vs_oracle(disp, mix)
+    assert np.all(start >= 0.0) and np.all(end > start)
+
+
+def test_batch_matches_single_light_field_launches(gpu_lib, mix):
+    import torch
+    disp, *_ = _batch(gpu_lib, mix, branches=2)
+    for d, (p, views, ref, decided) in zip(disp, mix):
+        h = gpu_lib.lfsgm_create(p)
+        one = torch.empty(p.N, dtype=torch.float32, device="cuda")
+        gpu_lib.lfsgm_depth(h, torch.from_numpy(views).cuda(), one, None)
+        gpu_lib.lfsgm_sync(h)
+        gpu_lib.lfsgm_destroy(h)
+        # float atomics in the SGM sum: equal up to the last bits where the decision is clear
+        assert np.max(np.abs(one.cpu().numpy() - d)[decided]) < 1e-4, p.name
+
+
+def test_batch_runs_repeatedly(gpu_lib, mix):
+    import torch
+    views = [torch.from_numpy(v).cuda() for _, v, _, _ in mix[:3]]
+    b = gpu_lib.LightFieldBatch([m[0] for m in mix[:3]], views, branches=2)
+    first = [d.clone() for d in b.run()]
+    for _ in range(3):
+        b.run()
+    b.times()
+    for a, c, (_, _, _, decided) in zip(first, b.disp, mix[:3]):
+        assert torch.max(torch.abs(a - c)[torch.from_numpy(decided).cuda()]).item() < 1e-4
+    b.close()
+
+
+def test_batch_rejects_an_invalid_member(gpu_lib, mix):
+    import torch
+    bad = lfsynth.tiny_params(census_w=9)
+    views = [torch.from_numpy(mix[0][1]).cuda(), torch.zeros(25 * 64 * 64, device="cuda")]
+    with pytest.raises(gpu_lib.LfsgmError, match="light field 1"):
+        gpu_lib.LightFieldBatch([mix[0][0], bad], views, branches=1)
