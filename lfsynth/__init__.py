@@ -324,8 +324,8 @@ def voronoi_scene_torch(p: LFParams, seed: int, n_planes: int, a_range, slope, c
     tex = torch.from_numpy(np.stack(textures)).to(dev)
     ntex, th, tw = tex.shape
     flat = tex.reshape(-1)
-    sx = torch.tensor(sites[:, 0], dtype=f64, device=dev).view(-1, 1, 1)
-    sy = torch.tensor(sites[:, 1], dtype=f64, device=dev).view(-1, 1, 1)
+    sx = torch.tensor(sites[:, 0], dtype=f64, device=dev).view(-1, 1, 1, 1)
+    sy = torch.tensor(sites[:, 1], dtype=f64, device=dev).view(-1, 1, 1, 1)
     Y, X = torch.meshgrid(torch.arange(H, dtype=f64, device=dev), torch.arange(W, dtype=f64, device=dev),
                           indexing="ij")
     gen = torch.Generator(device=dev)
@@ -350,46 +350,45 @@ def voronoi_scene_torch(p: LFParams, seed: int, n_planes: int, a_range, slope, c
         return (1 - fy) * ((1 - fx) * t00 + fx * t10) + fy * ((1 - fx) * t01 + fx * t11)
 
     views = torch.empty((V, U, H, W), dtype=torch.float32, device=dev)
-    inf = torch.tensor(float("inf"), dtype=f64, device=dev)
+    a = (torch.arange(U, dtype=f64, device=dev) - p.uc).view(U, 1, 1)     # one row of views at a time
+    if vignette:
+        r2 = ((X - 0.5 * (W - 1)) ** 2 + (Y - 0.5 * (H - 1)) ** 2) / ((0.5 * (W - 1)) ** 2 + (0.5 * (H - 1)) ** 2)
     for v in range(V):
-        for u in range(U):
-            a, b = u - p.uc, v - p.vc
-            best_d = torch.full((H, W), -float("inf"), dtype=f64, device=dev)
-            far_d = torch.full((H, W), float("inf"), dtype=f64, device=dev)
-            bi = torch.zeros((H, W), dtype=torch.long, device=dev)
-            fi = torch.zeros_like(bi)
-            bx, by, fxv, fyv = (torch.zeros((H, W), dtype=f64, device=dev) for _ in range(4))
-            for i, pl in enumerate(planes):
-                kx, ky = pl.b / W, pl.c / H
-                k0 = pl.a - kx * 0.5 * (W - 1) - ky * 0.5 * (H - 1)
-                m00, m01 = 1.0 + a * kx, a * ky
-                m10, m11 = b * kx, 1.0 + b * ky
-                r0, r1 = X - a * k0, Y - b * k0
-                det = m00 * m11 - m01 * m10
-                x = (m11 * r0 - m01 * r1) / det
-                y = (m00 * r1 - m10 * r0) / det
-                d = pl.disp(x, y, W, H)
-                take = (cell(x, y) == i) & (d > best_d)
-                best_d = torch.where(take, d, best_d)
-                bi = torch.where(take, torch.full_like(bi, i), bi)
-                bx = torch.where(take, x, bx)
-                by = torch.where(take, y, by)
-                fall = d < far_d
-                far_d = torch.where(fall, d, far_d)
-                fi = torch.where(fall, torch.full_like(fi, i), fi)
-                fxv = torch.where(fall, x, fxv)
-                fyv = torch.where(fall, y, fyv)
-            hole = ~torch.isfinite(best_d)
-            img = sample(torch.where(hole, fi, bi), torch.where(hole, fxv, bx), torch.where(hole, fyv, by))
-            if sigma > 0:
-                img = img + sigma * torch.randn((H, W), generator=gen, dtype=f64, device=dev)
-            if vignette:
-                rho2 = (a * a + b * b) / float(max(p.uc, 1) ** 2 + max(p.vc, 1) ** 2)
-                r2 = ((X - 0.5 * (W - 1)) ** 2 + (Y - 0.5 * (H - 1)) ** 2) / (
-                    (0.5 * (W - 1)) ** 2 + (0.5 * (H - 1)) ** 2)
-                img = img * (1.0 - 0.3 * rho2 * (0.5 + 0.5 * r2))
-            views[v, u] = torch.clamp(img, 0.0, 1.0).to(torch.float32)
-    del inf
+        b = float(v - p.vc)
+        best_d = torch.full((U, H, W), -float("inf"), dtype=f64, device=dev)
+        far_d = torch.full((U, H, W), float("inf"), dtype=f64, device=dev)
+        bi = torch.zeros((U, H, W), dtype=torch.long, device=dev)
+        fi = torch.zeros_like(bi)
+        bx, by, fxv, fyv = (torch.zeros((U, H, W), dtype=f64, device=dev) for _ in range(4))
+        for i, pl in enumerate(planes):
+            # X = x + a*d(x,y), Y = y + b*d(x,y), with d affine in (x, y): 2x2 solve per view
+            kx, ky = pl.b / W, pl.c / H
+            k0 = pl.a - kx * 0.5 * (W - 1) - ky * 0.5 * (H - 1)
+            m00, m01 = 1.0 + a * kx, a * ky
+            m10, m11 = b * kx, 1.0 + b * ky
+            r0, r1 = X - a * k0, Y - b * k0
+            det = m00 * m11 - m01 * m10
+            x = (m11 * r0 - m01 * r1) / det
+            y = (m00 * r1 - m10 * r0) / det
+            d = pl.disp(x, y, W, H)
+            take = (cell(x, y) == i) & (d > best_d)
+            best_d = torch.where(take, d, best_d)
+            bi = torch.where(take, torch.full_like(bi, i), bi)
+            bx = torch.where(take, x, bx)
+            by = torch.where(take, y, by)
+            fall = d < far_d
+            far_d = torch.where(fall, d, far_d)
+            fi = torch.where(fall, torch.full_like(fi, i), fi)
+            fxv = torch.where(fall, x, fxv)
+            fyv = torch.where(fall, y, fyv)
+        hole = ~torch.isfinite(best_d)
+        img = sample(torch.where(hole, fi, bi), torch.where(hole, fxv, bx), torch.where(hole, fyv, by))
+        if sigma > 0:
+            img = img + sigma * torch.randn((U, H, W), generator=gen, dtype=f64, device=dev)
+        if vignette:
+            rho2 = (a * a + b * b) / float(max(p.uc, 1) ** 2 + max(p.vc, 1) ** 2)
+            img = img * (1.0 - 0.3 * rho2 * (0.5 + 0.5 * r2))
+        views[v] = torch.clamp(img, 0.0, 1.0).to(torch.float32)
     return views
 
 
