@@ -51,11 +51,12 @@ double grid_disp(double dmin, double dmax, int L, int k) {
 struct lfsgm_ctx {
     lfsgm_config cfg{};
     cudaStream_t stream = nullptr;
-    int N = 0, nviews = 0, ref = 0, nbits = 0, Lcs = 0;
+    int N = 0, nviews = 0, ref = 0, nbits = 0, Lcd = 0;
     ArmList arms{};
     // device tables
     FineTap *d_fine = nullptr;
-    short2 *d_coarse = nullptr;
+    int *d_otab = nullptr;       // coarse census offsets per (arm view, label), see CoarseArms
+    CoarseArms ca{};
     int *d_armviews = nullptr;   // [4][kMaxArmViews]
     int *d_sel_cross = nullptr;  // reference + arm views
     int n_sel_cross = 0;
@@ -65,7 +66,7 @@ struct lfsgm_ctx {
     size_t ws_bytes = 0;
     bool ws_owned = false;
     uint16_t *ccost = nullptr;
-    uint32_t *csum = nullptr;
+    uint16_t *csum = nullptr;
     int *maps = nullptr, *F0 = nullptr, *F1 = nullptr, *cntpad = nullptr;
     int2 *wide_list = nullptr;         // (pixel, 32-label chunk) items for the list kernel
     int *wide_count = nullptr;
@@ -239,8 +240,8 @@ lfsgm_status bind_workspace(lfsgm_ctx *h, void *dptr, size_t bytes, bool owned) 
     h->cen_pad = (uint64_t *)take(h->nviews * HWp * 8);
     h->views_pad = (float *)take(h->nviews * HWp * 4);
     h->rows_maps = h->rows.ok && encode_fine_rows_maps(&h->rows, h->views_pad, h->cen_pad, h->nviews);
-    h->ccost = (uint16_t *)take(A * N * h->Lcs * 2);
-    h->csum = (uint32_t *)take(A * N * (h->Lcs / 2) * 4);
+    h->ccost = (uint16_t *)take(A * N * h->Lcd * 2);
+    h->csum = (uint16_t *)take(A * N * h->Lcd * 2);
     h->maps = (int *)take(4 * N * 4);
     h->F0 = (int *)take(N * 4);
     h->F1 = (int *)take(N * 4);
@@ -278,7 +279,7 @@ lfsgm_status lfsgm_create(const lfsgm_config *cfg, void *stream, lfsgm_handle *o
     h->nviews = c.U * c.V;
     h->ref = c.vc * c.U + c.uc;
     h->nbits = c.census_w * c.census_w - 1;
-    h->Lcs = c.coarse_labels <= 64 ? 64 : (c.coarse_labels <= 128 ? 128 : 256);
+    h->Lcd = coarse_stride(c.coarse_labels);
     plan_fine_rows(c.U, c.V, c.uc, c.vc, c.H, c.W, c.fine_labels, c.dmin, c.dmax, &h->rows);
     build_arms(h);
     // the packed coarse sums hold 8 paths x (C + P2) per 16-bit half
@@ -323,6 +324,21 @@ lfsgm_status lfsgm_create(const lfsgm_config *cfg, void *stream, lfsgm_handle *o
             sel_cross.push_back(h->arms.views[a][i]);
         }
     for (int i = 0; i < h->nviews; i++) sel_all.push_back(i);
+    // per arm: [nv][Lcd] linear offsets ny * Wp + nx of the nearest coarse shifts (0 = padding)
+    std::vector<int> otab;
+    h->ca.n_arms = h->arms.n_arms;
+    for (int a = 0; a < h->arms.n_arms; a++) {
+        h->ca.nv[a] = h->arms.nv[a];
+        h->ca.tab_off[a] = (int)otab.size();
+        for (int i = 0; i < h->arms.nv[a]; i++) {
+            const int view = h->arms.views[a][i];
+            for (int k = 0; k < h->Lcd; k++) {
+                const short2 n = k < c.coarse_labels ? coarse[(size_t)view * c.coarse_labels + k] : make_short2(0, 0);
+                otab.push_back((int)n.y * h->rows.Wp + (int)n.x);
+            }
+        }
+    }
+    if (otab.empty()) otab.push_back(0);
     h->n_sel_cross = (int)sel_cross.size();
     cudaError_t e;
 #define ALLOC_COPY(dst, vec)                                                                  \
@@ -330,7 +346,7 @@ lfsgm_status lfsgm_create(const lfsgm_config *cfg, void *stream, lfsgm_handle *o
     if (e == cudaSuccess) e = cudaMemcpy(dst, vec.data(), vec.size() * sizeof(vec[0]), cudaMemcpyHostToDevice); \
     if (e != cudaSuccess) { g_create_err = cudaGetErrorString(e); lfsgm_destroy(h); return LFSGM_ERR_CUDA; }
     ALLOC_COPY(h->d_fine, fine);
-    ALLOC_COPY(h->d_coarse, coarse);
+    ALLOC_COPY(h->d_otab, otab);
     ALLOC_COPY(h->d_armviews, armviews);
     ALLOC_COPY(h->d_sel_cross, sel_cross);
     ALLOC_COPY(h->d_sel_all, sel_all);
@@ -343,7 +359,7 @@ lfsgm_status lfsgm_destroy(lfsgm_handle h) {
     if (!h) return LFSGM_ERR_INVALID_ARG;
     cudaDeviceSynchronize();
     cudaFree(h->d_fine);
-    cudaFree(h->d_coarse);
+    cudaFree(h->d_otab);
     cudaFree(h->d_armviews);
     cudaFree(h->d_sel_cross);
     cudaFree(h->d_sel_all);
@@ -364,8 +380,8 @@ lfsgm_status lfsgm_workspace_size(lfsgm_handle h, size_t *bytes) {
     const size_t HWp = (size_t)h->rows.Hp * h->rows.Wp;
     b += align256(h->nviews * HWp * 8);            // census words, edge-replicated padding
     b += align256(h->nviews * HWp * 4);            // views, edge-replicated padding
-    b += align256(A * N * h->Lcs * 2);              // coarse cost
-    b += align256(A * N * (h->Lcs / 2) * 4);        // packed coarse sums
+    b += align256(A * N * h->Lcd * 2);              // coarse cost
+    b += align256(A * N * h->Lcd * 2);              // coarse 8-path sums
     b += align256(4 * N * 4);                       // maps
     b += 3 * align256(N * 4);                       // F0, F1, padded counts
     b += align256(N * (size_t)((h->cfg.fine_labels + 31) / 32) * 8);   // (pixel, chunk) list
@@ -405,25 +421,21 @@ lfsgm_status lfsgm_initial_disparity(lfsgm_handle h, const float *views, int32_t
                                  h->n_sel_cross, h->cen_pad, h->views_pad);
     }));
     cudaError_t e = cudaMemsetAsync(h->armsum, 0, 4 * 8, s);
-    if (e == cudaSuccess) e = cudaMemsetAsync(h->csum, 0, (size_t)A * N * (h->Lcs / 2) * 4, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(h->csum, 0, (size_t)A * N * h->Lcd * 2, s);
     if (e != cudaSuccess) return cuda_fail(h, e, "memset");
-    for (int a = 0; a < A; a++) {
-        LFSGM_TRY(run(h, "coarse_cost", [&] {
-            return launch_coarse_cost(s, h->cen_pad, h->rows.P, h->rows.Wp, h->rows.Hp, c.H, c.W, h->ref,
-                                      h->d_armviews + a * kMaxArmViews,
-                                      h->arms.nv[a], h->d_coarse, c.coarse_labels, h->Lcs,
-                                      h->ccost + (size_t)a * N * h->Lcs, h->armsum + a);
-        }));
-    }
+    LFSGM_TRY(run(h, "coarse_cost", [&] {
+        return launch_coarse_cost(s, h->cen_pad, h->rows.P, h->rows.Wp, h->rows.Hp, c.H, c.W, h->ref, h->d_armviews,
+                                  h->d_otab, h->ca, c.coarse_labels, h->ccost, h->armsum);
+    }));
     LFSGM_TRY(run(h, "coarse_penalties", [&] {
         return launch_coarse_penalties(s, h->armsum, A, (long long)N * c.coarse_labels, c.p1_frac, c.p2_frac,
                                        Pc1, Pc2, h->cpen);
     }));
     LFSGM_TRY(run(h, "coarse_sgm", [&] {
-        return launch_coarse_sgm(s, h->ccost, A, c.H, c.W, c.coarse_labels, h->Lcs, h->cpen, h->csum);
+        return launch_coarse_sgm(s, h->ccost, A, c.H, c.W, c.coarse_labels, h->cpen, h->csum);
     }));
     LFSGM_TRY(run(h, "coarse_wta", [&] {
-        return launch_coarse_wta(s, h->csum, A, N, c.coarse_labels, h->Lcs, h->maps, maps);
+        return launch_coarse_wta(s, h->csum, A, N, c.coarse_labels, h->maps, maps);
     }));
     LFSGM_TRY(run(h, "fuse", [&] { return launch_fuse(s, h->maps, A, N, c.phi, h->F0); }));
     int *fin = h->F0, *fout = h->F1;

@@ -100,16 +100,25 @@ struct ArmList {
 cudaError_t launch_census(cudaStream_t s, const float *views, int H, int W, int census_w,
                           const int *d_sel, int nsel, uint64_t *cen);
 
+// Coarse arms as the cost kernel sees them: views per arm and the start of each arm's
+// [nv][Lcd] table of linear census offsets (ny * Wp + nx) in the offset table.
+struct CoarseArms {
+    int n_arms;
+    int nv[4];
+    int tab_off[4];
+};
+int coarse_lpt(int Lc);       // labels per lane: 2, 4, 8 for Lc <= 64, 128, 256
+int coarse_stride(int Lc);    // Lcd: label stride of the coarse cost and sums
 cudaError_t launch_coarse_cost(cudaStream_t s, const uint64_t *cen_pad, int P, int Wp, int Hp, int H, int W, int ref,
-                               const int *d_views, int nv, const short2 *ctab, int Lc, int Lcs,
-                               uint16_t *out, unsigned long long *sum);
+                               const int *armviews, const int *otab, const CoarseArms &ca, int Lc,
+                               uint16_t *out, unsigned long long *armsum);
 cudaError_t launch_coarse_penalties(cudaStream_t s, const unsigned long long *sums, int narms,
                                     long long count, double p1f, double p2f, int P1, int P2,
                                     int *pen);
 cudaError_t launch_coarse_sgm(cudaStream_t s, const uint16_t *cost, int narms, int H, int W, int Lc,
-                              int Lcs, const int *pen, uint32_t *sum);
-cudaError_t launch_coarse_wta(cudaStream_t s, const uint32_t *sum, int narms, int N, int Lc, int Lcs,
-                              int *maps, int *maps_out);
+                              const int *pen, uint16_t *sum);
+cudaError_t launch_coarse_wta(cudaStream_t s, const uint16_t *sum, int narms, int N, int Lc, int *maps,
+                              int *maps_out);
 
 cudaError_t launch_fuse(cudaStream_t s, const int *maps, int narms, int N, double phi, int *F);
 cudaError_t launch_fill(cudaStream_t s, const int *Fin, int *Fout, int H, int W);
