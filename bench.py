@@ -377,11 +377,23 @@ def run_backward(args, dev, views, p):
     torch.cuda.synchronize()
     f = statistics.mean(e[0].elapsed_time(e[1]) for e in ev)
     b = statistics.mean(e[1].elapsed_time(e[2]) for e in ev)
+    # per-kernel split of forward + backward (separate, untimed pass with the library's events)
+    lf.lfsgm_set_profiling(L.h, True)
+    lf.lfsgm_kernel_times(L.h)
+    for _ in range(3):
+        fwd()
+        bwd()
+    torch.cuda.synchronize()
+    per = {}
+    for name, ms in lf.lfsgm_kernel_times(L.h, cap=100000):
+        per[name] = per.get(name, 0.0) + ms / 3
+    lf.lfsgm_set_profiling(L.h, False)
     ok = bool(torch.isfinite(gviews).all().item() and torch.isfinite(gp).all().item())
     L.close()
     return {"config": "9x9x512x512, 31-label windows, soft-argmin tau 0.1, fixed P1/P2 = 0.05/0.5 mean cost",
             "forward_ms": round(f, 4), "backward_ms": round(b, 4), "steps": K,
             "backward_over_forward": round(b / f, 3), "grads_finite": ok,
+            "kernels_ms": {k: round(v, 4) for k, v in sorted(per.items(), key=lambda kv: -kv[1])},
             "grads": "cost volume, P1, P2, views (l2 term through the bilinear weights)"}
 
 

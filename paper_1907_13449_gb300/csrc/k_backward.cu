@@ -11,9 +11,9 @@
 //    at it, routes (P2-branch lambdas - all lambdas) to the predecessor's minimum (the -m term),
 //    and sums the branch lambdas into dLoss/dP1, dLoss/dP2.  Path costs are recomputed per
 //    direction instead of being stored for all 8.
-//  * views_backward: one thread per pixel; dC/dI_ref = w_l2 sum sign(I_ref - B), dC/dI_v(tap) =
-//    -w_l2 sign(.) w_tap (taps clamped as in the forward); tap gradients are summed in registers
-//    while the bilinear cell stays the same and added to the view with atomics when it changes.
+//  * views_backward: one warp per (pixel, 32-label chunk); dC/dI_ref = w_l2 sum sign(I_ref - B),
+//    dC/dI_v(tap) = -w_l2 sign(.) w_tap (taps clamped as in the forward); lanes of one bilinear
+//    cell are summed by a segmented shuffle and added to the view with four atomics per cell.
 //    The census term is piecewise constant and has no gradient.
 #include "lfsgm_internal.cuh"
 
@@ -41,19 +41,19 @@ __global__ void softargmin_backward_kernel(const float *__restrict__ agg, const 
     const float *s = agg + o;
     float mn = s[0];
     for (int j = 1; j < n; j++) mn = fminf(mn, s[j]);
-    double z = 0.0, num = 0.0;
+    // FP32 weights after subtracting the minimum; d_g - dhat = (j - jbar) * step
+    const float it = 1.f / tau;
+    float z = 0.f, num = 0.f;
     for (int j = 0; j < n; j++) {
-        const double w = exp(-((double)s[j] - (double)mn) / (double)tau);
+        const float w = expf((mn - s[j]) * it);
         z += w;
-        num += w * (dmin + (double)(l + j) * step);
+        num = fmaf(w, (float)j, num);
     }
-    const double dh = num / z, gd = (double)gdisp[p];
+    const float jbar = num / z;
+    const float k = gdisp[p] * (-it) * (float)step / z;
     for (int j = 0; j < npad; j++) {
         float g = 0.f;
-        if (j < n) {
-            const double w = exp(-((double)s[j] - (double)mn) / (double)tau) / z;
-            g = (float)(gd * (-1.0 / (double)tau) * w * ((dmin + (double)(l + j) * step) - dh));
-        }
+        if (j < n) g = k * expf((mn - s[j]) * it) * ((float)j - jbar);
         gCs[o + j] = g;
         gcost[o + j] = 0.f;
     }
@@ -205,67 +205,209 @@ __global__ void __launch_bounds__(32 * kBwdWarps) sgm_backward_kernel(
     }
 }
 
-__global__ void views_backward_kernel(const float *__restrict__ views, const FineTap *__restrict__ tab, int G,
-                                      int nviews, int H, int W, int ref, const int *__restrict__ lo,
-                                      const int *__restrict__ cnt, const long long *__restrict__ off, float wl2,
-                                      const float *__restrict__ gcost, float *__restrict__ gviews) {
-    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+// One warp per (pixel, 32-label chunk) item, lane = label: the lane's tap and bilinear sample are
+// recomputed as in the forward (clamped taps), g = dLoss/dC * w_l2 * sign(I_ref - B) goes to the
+// reference pixel and -g * (bilinear weight) to the four taps.  Lanes whose labels share a
+// bilinear cell form contiguous runs (the integer shift is monotone in the label), so a segmented
+// shuffle sum leaves each run's total in its first lane, which issues the four atomics.
+__global__ void __launch_bounds__(256) views_backward_kernel(const float *__restrict__ views,
+                                                             const FineTap *__restrict__ tab, int G, int nviews,
+                                                             int H, int W, int ref, const int *__restrict__ lo,
+                                                             const int *__restrict__ cnt,
+                                                             const long long *__restrict__ off, float wl2,
+                                                             const float *__restrict__ gcost,
+                                                             float *__restrict__ gviews, const int2 *__restrict__ list,
+                                                             const int *__restrict__ count) {
+    const int lane = threadIdx.x & 31;
+    const int warps = (gridDim.x * blockDim.x) >> 5;
     const size_t N = (size_t)H * W;
-    if (p >= (int)N) return;
-    const int l = lo[p], n = cnt[p];
-    const long long o = off[p];
-    if (!window_ok(l, n, G, off[p + 1] - o, nullptr)) return;
-    const int x = p % W, y = p / W;
-    const float Iref = views[(size_t)ref * N + p];
+    const int total = *count;
+    for (int it = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; it < total; it += warps) {
+        const int2 item = list[it];
+        const int p = item.x, chunk = item.y;
+        const int l0 = __ldg(lo + p), n = __ldg(cnt + p);
+        const long long o = __ldg(off + p);
+        if (!window_ok(l0, n, G, __ldg(off + p + 1) - o, nullptr)) continue;   // uniform per item
+        const int j = chunk * 32 + lane;
+        const bool act = j < n;
+        const int x = p % W, y = p / W;
+        const float Iref = __ldg(views + (size_t)ref * N + p);
+        const float gc = act ? wl2 * __ldg(gcost + o + j) : 0.f;
+        float gref = 0.f;
+        for (int vi = 0; vi < nviews - 1; vi++) {
+            const int view = vi + (vi >= ref);
+            FineTap t;
+            t.ox = t.oy = 0;
+            t.fx = t.fy = 0.f;
+            if (act) t = load_tap(tab + (size_t)view * G + l0 + j);
+            const float *I = views + (size_t)view * N;
+            const int x0 = min(max(x + t.ox, 0), W - 1), x1 = min(max(x + t.ox + 1, 0), W - 1);
+            const int y0 = min(max(y + t.oy, 0), H - 1), y1 = min(max(y + t.oy + 1, 0), H - 1);
+            float g = 0.f;
+            if (act && gc != 0.f) {
+                const float top = (1.f - t.fx) * __ldg(I + y0 * W + x0) + t.fx * __ldg(I + y0 * W + x1);
+                const float bot = (1.f - t.fx) * __ldg(I + y1 * W + x0) + t.fx * __ldg(I + y1 * W + x1);
+                const float d = Iref - ((1.f - t.fy) * top + t.fy * bot);
+                g = d > 0.f ? gc : (d < 0.f ? -gc : 0.f);
+            }
+            gref += g;
+            float a00 = -g * (1.f - t.fy) * (1.f - t.fx), a10 = -g * (1.f - t.fy) * t.fx;
+            float a01 = -g * t.fy * (1.f - t.fx), a11 = -g * t.fy * t.fx;
+            // runs of equal bilinear cells; inactive lanes (the chunk's tail) form their own run
+            const int key = act ? (((int)t.oy << 16) ^ ((int)t.ox & 0xffff)) : 0x7fffffff;
+            const int kprev = __shfl_up_sync(0xffffffffu, key, 1);
+            const bool head = lane == 0 || key != kprev;
+            const unsigned heads = __ballot_sync(0xffffffffu, head);
+            const unsigned later = lane == 31 ? 0u : (heads & (0xfffffffeu << lane));
+            const int end = later ? __ffs(later) - 2 : 31;
+#pragma unroll
+            for (int d = 1; d < 32; d <<= 1) {
+                const float b00 = __shfl_down_sync(0xffffffffu, a00, d);
+                const float b10 = __shfl_down_sync(0xffffffffu, a10, d);
+                const float b01 = __shfl_down_sync(0xffffffffu, a01, d);
+                const float b11 = __shfl_down_sync(0xffffffffu, a11, d);
+                if (lane + d <= end) {
+                    a00 += b00;
+                    a10 += b10;
+                    a01 += b01;
+                    a11 += b11;
+                }
+            }
+            if (head && act) {
+                float *gI = gviews + (size_t)view * N;
+                if (a00 != 0.f) atomicAdd(gI + y0 * W + x0, a00);
+                if (a10 != 0.f) atomicAdd(gI + y0 * W + x1, a10);
+                if (a01 != 0.f) atomicAdd(gI + y1 * W + x0, a01);
+                if (a11 != 0.f) atomicAdd(gI + y1 * W + x1, a11);
+            }
+        }
+        gref = warp_sum(gref);
+        if (lane == 0 && gref != 0.f) atomicAdd(gviews + (size_t)ref * N + p, gref);
+    }
+}
+
+// Narrow windows (cnt <= 32) by tiles of 32 x 8 pixels, one warp per row and a lane per pixel:
+// for every view the lanes walk their windows, sum the tap gradients in registers while the
+// bilinear cell stays the same, and add them into a shared-memory box covering the tile's tap
+// footprint (the tile's label range [gmin, gmax] fixes it: the integer shift is monotone in the
+// label); the box is then added to the view with one atomic per non-zero element.  Taps outside
+// the box (a tile whose label range is too wide for it) go to global memory directly.
+constexpr int kVbRows = 8, kVbBoxW = 96, kVbBoxH = 24;
+
+__global__ void __launch_bounds__(32 * kVbRows) views_backward_tile_kernel(
+    const float *__restrict__ views, const FineTap *__restrict__ tab, int G, int nviews, int H, int W, int ref,
+    const int *__restrict__ lo, const int *__restrict__ cnt, const long long *__restrict__ off, float wl2,
+    const float *__restrict__ gcost, float *__restrict__ gviews) {
+    __shared__ float box[kVbBoxH * kVbBoxW];
+    __shared__ float gcs[kVbRows][32][32];        // [row][label][lane]
+    __shared__ int red[2][kVbRows];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int x0 = blockIdx.x * 32, ty0 = blockIdx.y * kVbRows;
+    const int x = x0 + lane, y = ty0 + w;
+    const size_t N = (size_t)H * W;
+    bool act = false;
+    int l = 0, n = 0;
+    size_t p = 0;
+    if (x < W && y < H) {
+        p = (size_t)y * W + x;
+        l = __ldg(lo + p);
+        n = __ldg(cnt + p);
+        const long long o = __ldg(off + p);
+        act = n <= 32 && window_ok(l, n, G, __ldg(off + p + 1) - o, nullptr);
+        for (int j = 0; j < 32; j++) gcs[w][j][lane] = (act && j < n) ? wl2 * __ldg(gcost + o + j) : 0.f;
+    } else {
+        for (int j = 0; j < 32; j++) gcs[w][j][lane] = 0.f;
+    }
+    int gmn = act ? l : 0x7fffffff, gmx = act ? l + n - 1 : -1;
+    for (int o = 16; o > 0; o >>= 1) {
+        gmn = min(gmn, __shfl_xor_sync(0xffffffffu, gmn, o));
+        gmx = max(gmx, __shfl_xor_sync(0xffffffffu, gmx, o));
+    }
+    if (lane == 0) {
+        red[0][w] = gmn;
+        red[1][w] = gmx;
+    }
+    for (int e = threadIdx.x; e < kVbBoxH * kVbBoxW; e += blockDim.x) box[e] = 0.f;
+    __syncthreads();
+    gmn = red[0][0];
+    gmx = red[1][0];
+    for (int k = 1; k < kVbRows; k++) {
+        gmn = min(gmn, red[0][k]);
+        gmx = max(gmx, red[1][k]);
+    }
+    if (gmx < 0) return;                               // no narrow window in the tile (uniform)
+    const float Iref = act ? __ldg(views + (size_t)ref * N + p) : 0.f;
     float gref = 0.f;
     for (int vi = 0; vi < nviews - 1; vi++) {
         const int view = vi + (vi >= ref);
+        const FineTap ta = load_tap(tab + (size_t)view * G + gmn), tb = load_tap(tab + (size_t)view * G + gmx);
+        const int bx0 = x0 + min(ta.ox, tb.ox), by0 = ty0 + min(ta.oy, tb.oy);
+        const int bw = 32 + abs(tb.ox - ta.ox) + 1, bh = kVbRows + abs(tb.oy - ta.oy) + 1;
+        const bool use_box = bw <= kVbBoxW && bh <= kVbBoxH;
         const float *I = views + (size_t)view * N;
         float *gI = gviews + (size_t)view * N;
-        int cx = 0x7fffffff, cy = 0;
-        float a00 = 0.f, a10 = 0.f, a01 = 0.f, a11 = 0.f;
-        int i00 = 0, i10 = 0, i01 = 0, i11 = 0;
-        for (int j = 0; j < n; j++) {
-            const float gc = gcost[o + j];
-            const FineTap t = load_tap(tab + (size_t)view * G + l + j);
-            if (t.ox != cx || t.oy != cy) {
-                if (cx != 0x7fffffff) {
-                    atomicAdd(gI + i00, a00);
-                    atomicAdd(gI + i10, a10);
-                    atomicAdd(gI + i01, a01);
-                    atomicAdd(gI + i11, a11);
+        auto add = [&](int xc, int yc, float v) {
+            if (v == 0.f) return;
+            const int bx = xc - bx0, by = yc - by0;
+            if (use_box && (unsigned)bx < (unsigned)bw && (unsigned)by < (unsigned)bh)
+                atomicAdd(&box[by * kVbBoxW + bx], v);
+            else
+                atomicAdd(gI + (size_t)yc * W + xc, v);
+        };
+        if (act) {
+            int cx = 0x7fffffff, cy = 0, xa = 0, xb = 0, ya = 0, yb = 0;
+            float a00 = 0.f, a10 = 0.f, a01 = 0.f, a11 = 0.f;
+            const FineTap *tt = tab + (size_t)view * G + l;
+            for (int j = 0; j < n; j++) {
+                const FineTap t = load_tap(tt + j);
+                if (t.ox != cx || t.oy != cy) {
+                    if (cx != 0x7fffffff) {
+                        add(xa, ya, a00);
+                        add(xb, ya, a10);
+                        add(xa, yb, a01);
+                        add(xb, yb, a11);
+                    }
+                    cx = t.ox;
+                    cy = t.oy;
+                    xa = min(max(x + cx, 0), W - 1);
+                    xb = min(max(x + cx + 1, 0), W - 1);
+                    ya = min(max(y + cy, 0), H - 1);
+                    yb = min(max(y + cy + 1, 0), H - 1);
+                    a00 = a10 = a01 = a11 = 0.f;
                 }
-                cx = t.ox;
-                cy = t.oy;
-                const int x0 = min(max(x + t.ox, 0), W - 1), x1 = min(max(x + t.ox + 1, 0), W - 1);
-                const int y0 = min(max(y + t.oy, 0), H - 1), y1 = min(max(y + t.oy + 1, 0), H - 1);
-                i00 = y0 * W + x0;
-                i10 = y0 * W + x1;
-                i01 = y1 * W + x0;
-                i11 = y1 * W + x1;
-                a00 = a10 = a01 = a11 = 0.f;
+                const float gc = gcs[w][j][lane];
+                if (gc == 0.f) continue;
+                const float top = (1.f - t.fx) * __ldg(I + (size_t)ya * W + xa) + t.fx * __ldg(I + (size_t)ya * W + xb);
+                const float bot = (1.f - t.fx) * __ldg(I + (size_t)yb * W + xa) + t.fx * __ldg(I + (size_t)yb * W + xb);
+                const float d = Iref - ((1.f - t.fy) * top + t.fy * bot);
+                const float g = d > 0.f ? gc : (d < 0.f ? -gc : 0.f);
+                gref += g;
+                a00 -= g * (1.f - t.fy) * (1.f - t.fx);
+                a10 -= g * (1.f - t.fy) * t.fx;
+                a01 -= g * t.fy * (1.f - t.fx);
+                a11 -= g * t.fy * t.fx;
             }
-            if (gc == 0.f) continue;
-            const float top = (1.f - t.fx) * I[i00] + t.fx * I[i10];
-            const float bot = (1.f - t.fx) * I[i01] + t.fx * I[i11];
-            const float smp = (1.f - t.fy) * top + t.fy * bot;
-            const float d = Iref - smp;
-            const float sg = d > 0.f ? 1.f : (d < 0.f ? -1.f : 0.f);
-            const float g = gc * wl2 * sg;
-            gref += g;
-            a00 -= g * (1.f - t.fy) * (1.f - t.fx);
-            a10 -= g * (1.f - t.fy) * t.fx;
-            a01 -= g * t.fy * (1.f - t.fx);
-            a11 -= g * t.fy * t.fx;
+            if (cx != 0x7fffffff) {
+                add(xa, ya, a00);
+                add(xb, ya, a10);
+                add(xa, yb, a01);
+                add(xb, yb, a11);
+            }
         }
-        if (cx != 0x7fffffff) {
-            atomicAdd(gI + i00, a00);
-            atomicAdd(gI + i10, a10);
-            atomicAdd(gI + i01, a01);
-            atomicAdd(gI + i11, a11);
+        __syncthreads();
+        if (use_box) {
+            for (int e = threadIdx.x; e < bw * bh; e += blockDim.x) {
+                const int by = e / bw, bx = e - by * bw;
+                const float v = box[by * kVbBoxW + bx];
+                if (v != 0.f) {
+                    atomicAdd(gI + (size_t)(by0 + by) * W + (bx0 + bx), v);
+                    box[by * kVbBoxW + bx] = 0.f;
+                }
+            }
         }
+        __syncthreads();
     }
-    gviews[(size_t)ref * N + p] = gref;   // the reference view only receives its own pixels' terms
+    if (act && gref != 0.f) atomicAdd(gviews + (size_t)ref * N + p, gref);
 }
 
 }  // namespace
@@ -297,10 +439,18 @@ cudaError_t launch_sgm_backward(cudaStream_t s, const float *cost, const int *lo
 
 cudaError_t launch_views_backward(cudaStream_t s, const float *views, const FineTap *tab, int G, int nviews, int H,
                                   int W, int ref, const int *lo, const int *cnt, const long long *off, float wl2,
-                                  const float *gcost, float *gviews) {
-    const int N = H * W;
-    views_backward_kernel<<<(N + 127) / 128, 128, 0, s>>>(views, tab, G, nviews, H, W, ref, lo, cnt, off, wl2, gcost,
-                                                          gviews);
+                                  const float *gcost, float *gviews, const int2 *list, const int *count) {
+    dim3 grid((W + 31) / 32, (H + kVbRows - 1) / kVbRows);
+    views_backward_tile_kernel<<<grid, 32 * kVbRows, 0, s>>>(views, tab, G, nviews, H, W, ref, lo, cnt, off, wl2, gcost,
+                                                             gviews);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    // windows wider than 32 labels (the list holds their chunks)
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    views_backward_kernel<<<sms * 8, 256, 0, s>>>(views, tab, G, nviews, H, W, ref, lo, cnt, off, wl2, gcost, gviews,
+                                                  list, count);
     return cudaGetLastError();
 }
 

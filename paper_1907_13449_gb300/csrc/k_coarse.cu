@@ -20,8 +20,6 @@
 namespace lfsgm {
 namespace {
 
-constexpr int kBig = 1 << 28;   // an absent label (outside [0, Lc))
-constexpr int kCoarseRun = 16;  // pixels of a row per warp in the cost kernel
 
 template <int LPT>
 struct CVec;
@@ -82,7 +80,9 @@ __device__ __forceinline__ void load_offsets(const int *p, int *o) {
 
 // Eq. 7 per arm: C_a(p, k) = sum over the arm's views of the Hamming distance between the
 // reference census word at p and the view's word at p + n(view, k) (nearest shift, clamped --
-// the padded census repeats the border words, so the linear offset needs no clamping).
+// the padded census repeats the border words, so the linear offset needs no clamping).  A warp
+// takes a run of RUN = 32 / LPT pixels; views are the outer loop, so a view's label offsets are
+// read once and the RUN x LPT census loads of the view are independent of each other.
 template <int LPT>
 __global__ void __launch_bounds__(128) coarse_cost_kernel(const uint64_t *__restrict__ cen_pad, size_t HWp, int Wp,
                                                           int P, int H, int W, int ref,
@@ -91,41 +91,51 @@ __global__ void __launch_bounds__(128) coarse_cost_kernel(const uint64_t *__rest
                                                           int Lcd, uint16_t *__restrict__ out,
                                                           unsigned long long *__restrict__ armsum) {
     using V = CVec<LPT>;
+    constexpr int RUN = 32 / LPT;
     const int a = blockIdx.y;
     const int lane = threadIdx.x & 31;
-    const int runs_x = (W + kCoarseRun - 1) / kCoarseRun;
+    const int runs_x = (W + RUN - 1) / RUN;
     const int task = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
     if (task >= runs_x * H) return;
-    const int y = task / runs_x, xs = (task - y * runs_x) * kCoarseRun, xe = min(xs + kCoarseRun, W);
+    const int y = task / runs_x, xs = (task - y * runs_x) * RUN;
     const int k0 = lane * LPT;
     const bool act = k0 < Lcd;
     const int nv = ca.nv[a];
     const int *views = armviews + a * kMaxArmViews;
     const int *ot = otab + ca.tab_off[a] + k0;
     const size_t N = (size_t)H * W;
-    uint16_t *O = out + (size_t)a * N * Lcd + k0;
-    const size_t rowoff = (size_t)(y + P) * Wp + P;
-    const uint64_t *refrow = cen_pad + (size_t)ref * HWp + rowoff;
+    const size_t rowoff = (size_t)(y + P) * Wp + P + xs;
     unsigned long long total = 0;
-    for (int x = xs; x < xe; x++) {
-        if (!act) continue;
-        const uint64_t r = __ldg(refrow + x);
-        int c[LPT];
+    if (act) {
+        uint64_t r[RUN];
+        const uint64_t *refrow = cen_pad + (size_t)ref * HWp + rowoff;
 #pragma unroll
-        for (int j = 0; j < LPT; j++) c[j] = 0;
-        for (int i = 0; i < nv; i++) {
-            const uint64_t *base = cen_pad + (size_t)__ldg(views + i) * HWp + rowoff + x;
+        for (int i = 0; i < RUN; i++) r[i] = __ldg(refrow + i);     // padded: in bounds past W too
+        int c[RUN][LPT];
+#pragma unroll
+        for (int i = 0; i < RUN; i++)
+#pragma unroll
+            for (int j = 0; j < LPT; j++) c[i][j] = 0;
+        for (int v = 0; v < nv; v++) {
+            const uint64_t *base = cen_pad + (size_t)__ldg(views + v) * HWp + rowoff;
             int o[LPT];
-            load_offsets<LPT>(ot + i * Lcd, o);
+            load_offsets<LPT>(ot + v * Lcd, o);
 #pragma unroll
-            for (int j = 0; j < LPT; j++) c[j] += __popcll(r ^ __ldg(base + o[j]));
-        }
+            for (int i = 0; i < RUN; i++)
 #pragma unroll
-        for (int j = 0; j < LPT; j++) {
-            if (k0 + j >= Lc) c[j] = 0;
-            total += (unsigned)c[j];
+                for (int j = 0; j < LPT; j++) c[i][j] += __popcll(r[i] ^ __ldg(base + i + o[j]));
         }
-        *reinterpret_cast<typename V::T *>(O + ((size_t)y * W + x) * Lcd) = V::pack(c);
+        uint16_t *O = out + ((size_t)a * N + (size_t)y * W + xs) * Lcd + k0;
+#pragma unroll
+        for (int i = 0; i < RUN; i++) {
+            if (xs + i >= W) break;
+#pragma unroll
+            for (int j = 0; j < LPT; j++) {
+                if (k0 + j >= Lc) c[i][j] = 0;
+                total += (unsigned)c[i][j];
+            }
+            *reinterpret_cast<typename V::T *>(O + (size_t)i * Lcd) = V::pack(c[i]);
+        }
     }
     for (int o = 16; o > 0; o >>= 1) total += __shfl_down_sync(0xffffffffu, total, o);
     if (lane == 0 && total) atomicAdd(armsum + a, total);
@@ -154,28 +164,47 @@ __global__ void coarse_penalty_kernel(const unsigned long long *sums, int narms,
 }
 
 template <int LPT>
-__device__ __forceinline__ void red_packed(uint16_t *dst, const int *v) {
+__device__ __forceinline__ void words_of(const typename CVec<LPT>::T &w, uint32_t *c) {
     if constexpr (LPT == 2) {
-        atomicAdd(reinterpret_cast<unsigned int *>(dst), (unsigned)v[0] | ((unsigned)v[1] << 16));
+        c[0] = w;
+    } else if constexpr (LPT == 4) {
+        c[0] = w.x;
+        c[1] = w.y;
+    } else {
+        c[0] = w.x;
+        c[1] = w.y;
+        c[2] = w.z;
+        c[3] = w.w;
+    }
+}
+
+template <int LPT>
+__device__ __forceinline__ void red_words(uint16_t *dst, const uint32_t *v) {
+    if constexpr (LPT == 2) {
+        atomicAdd(reinterpret_cast<unsigned int *>(dst), v[0]);
     } else {
 #pragma unroll
-        for (int j = 0; j < LPT; j += 4) {
-            const unsigned long long w = (unsigned long long)v[j] | ((unsigned long long)v[j + 1] << 16) |
-                                         ((unsigned long long)v[j + 2] << 32) | ((unsigned long long)v[j + 3] << 48);
-            atomicAdd(reinterpret_cast<unsigned long long *>(dst + j), w);
-        }
+        for (int j = 0; j < LPT / 2; j += 2)
+            atomicAdd(reinterpret_cast<unsigned long long *>(dst + 2 * j),
+                      (unsigned long long)v[j] | ((unsigned long long)v[j + 1] << 32));
     }
 }
 
 // One warp per (arm, direction, scanline): Eq. 8 in the normalised form
 //   L(p,k) = C(p,k) + (min(L'(k), L'(k-1)+P1, L'(k+1)+P1, m+P2) - m),  m = min_k L'(k),
 // L = C where the predecessor is outside the image; sum over directions (Eq. 9).
+// A lane's labels are held as 16-bit pairs in 32-bit words: the minima are per-halfword
+// (__vminu2) and the additions and the subtraction of m are plain 32-bit operations, exact
+// because every present value stays below 2^13 (the host bounds 8 (C + P2) < 2^16) and is at
+// least m, so no halfword carries or borrows.  An absent label (k >= Lc) holds 0x7fff, above
+// any present value and below 2^16 - P1.
 template <int LPT>
 __global__ void __launch_bounds__(128) coarse_sgm_kernel(const uint16_t *__restrict__ cost, int H, int W, int Lc,
                                                          int Lcd, const int *__restrict__ pen, ScanTable st,
                                                          int narms, uint16_t *__restrict__ sum) {
-    using V = CVec<LPT>;
-    using T = typename V::T;
+    using T = typename CVec<LPT>::T;
+    constexpr int NP = LPT / 2;
+    constexpr uint32_t SENT = 0x7fff7fffu;
     const int lane = threadIdx.x & 31;
     const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int per_arm = st.cum[8];
@@ -198,7 +227,12 @@ __global__ void __launch_bounds__(128) coarse_sgm_kernel(const uint16_t *__restr
     const bool act = k0 < Lcd;
     const uint16_t *C = cost + (size_t)arm * N * Lcd + k0;
     uint16_t *S = sum + (size_t)arm * N * Lcd + k0;
-    const int P1 = __ldg(pen + 2 * arm), P2 = __ldg(pen + 2 * arm + 1);
+    const uint32_t P1 = (uint32_t)__ldg(pen + 2 * arm), P2 = (uint32_t)__ldg(pen + 2 * arm + 1);
+    const uint32_t P1P1 = P1 * 0x10001u;
+    uint32_t pm[NP];                     // 0xffff in the halfwords of present labels
+#pragma unroll
+    for (int j = 0; j < NP; j++)
+        pm[j] = (k0 + 2 * j < Lc ? 0x0000ffffu : 0u) | (k0 + 2 * j + 1 < Lc ? 0xffff0000u : 0u);
     const long long dp = (long long)dy * W + dx;
     long long p = (long long)y * W + x;
     auto ld = [&](long long q) {
@@ -211,47 +245,49 @@ __global__ void __launch_bounds__(128) coarse_sgm_kernel(const uint16_t *__restr
     if (steps > 1) r1 = ld(p + dp);
     if (steps > 2) r2 = ld(p + 2 * dp);
     if (steps > 3) r3 = ld(p + 3 * dp);
-    int L[LPT];
-    int m = 0;
+    uint32_t L[NP];
+    uint32_t m = 0;
     for (int t = 0; t < steps; t++, p += dp) {
         const T cur = r0;
         r0 = r1;
         r1 = r2;
         r2 = r3;
         if (t + 4 < steps) r3 = ld(p + 4 * dp);
-        int c[LPT];
-        V::unpack(cur, c);
-        int Ln[LPT];
+        uint32_t c[NP];
+        words_of<LPT>(cur, c);
+        uint32_t Ln[NP];
         if (t == 0) {
 #pragma unroll
-            for (int i = 0; i < LPT; i++) Ln[i] = (k0 + i < Lc) ? c[i] : kBig;
+            for (int j = 0; j < NP; j++) Ln[j] = (c[j] & pm[j]) | (SENT & ~pm[j]);
         } else {
-            int left = __shfl_up_sync(0xffffffffu, L[LPT - 1], 1);
-            int right = __shfl_down_sync(0xffffffffu, L[0], 1);
-            if (lane == 0) left = kBig;
-            if (lane == 31) right = kBig;
-            const int mp2 = m + P2;
+            uint32_t left = __shfl_up_sync(0xffffffffu, L[NP - 1], 1);
+            uint32_t right = __shfl_down_sync(0xffffffffu, L[0], 1);
+            if (lane == 0) left = SENT;
+            if (lane == 31) right = SENT;
+            const uint32_t mm = m * 0x10001u, mp2 = (m + P2) * 0x10001u;
 #pragma unroll
-            for (int i = 0; i < LPT; i++) {
-                const int lm = (i == 0) ? left : L[i - 1];
-                const int rp = (i == LPT - 1) ? right : L[i + 1];
-                int u = min(L[i], min(lm, rp) + P1);
-                u = min(u, mp2);
-                Ln[i] = (k0 + i < Lc) ? c[i] + (u - m) : kBig;
+            for (int j = 0; j < NP; j++) {
+                const uint32_t pw = (j == 0) ? left : L[j - 1];
+                const uint32_t nw = (j == NP - 1) ? right : L[j + 1];
+                const uint32_t lm = __byte_perm(pw, L[j], 0x5432);    // labels 2j-1, 2j
+                const uint32_t rp = __byte_perm(L[j], nw, 0x5432);    // labels 2j+1, 2j+2
+                uint32_t u = __vminu2(L[j], __vminu2(lm, rp) + P1P1);
+                u = __vminu2(u, mp2);
+                Ln[j] = ((c[j] + (u - mm)) & pm[j]) | (SENT & ~pm[j]);
             }
         }
-        int lmin = Ln[0];
+        uint32_t q = Ln[0];
 #pragma unroll
-        for (int i = 1; i < LPT; i++) lmin = min(lmin, Ln[i]);
-        m = __reduce_min_sync(0xffffffffu, lmin);
+        for (int j = 1; j < NP; j++) q = __vminu2(q, Ln[j]);
+        m = __reduce_min_sync(0xffffffffu, min(q & 0xffffu, q >> 16));
         if (act) {
-            int v[LPT];
+            uint32_t v[NP];
 #pragma unroll
-            for (int i = 0; i < LPT; i++) v[i] = (k0 + i < Lc) ? Ln[i] : 0;
-            red_packed<LPT>(S + p * Lcd, v);
+            for (int j = 0; j < NP; j++) v[j] = Ln[j] & pm[j];
+            red_words<LPT>(S + p * Lcd, v);
         }
 #pragma unroll
-        for (int i = 0; i < LPT; i++) L[i] = Ln[i];
+        for (int j = 0; j < NP; j++) L[j] = Ln[j];
     }
 }
 
@@ -292,7 +328,8 @@ cudaError_t launch_coarse_cost(cudaStream_t s, const uint64_t *cen_pad, int P, i
                                uint16_t *out, unsigned long long *armsum) {
     const int Lcd = coarse_stride(Lc);
     const size_t HWp = (size_t)Hp * Wp;
-    const long long tasks = (long long)((W + kCoarseRun - 1) / kCoarseRun) * H;
+    const int run = 32 / coarse_lpt(Lc);
+    const long long tasks = (long long)((W + run - 1) / run) * H;
     dim3 grid((unsigned)((tasks + 3) / 4), (unsigned)ca.n_arms);
     switch (coarse_lpt(Lc)) {
     case 2: coarse_cost_kernel<2><<<grid, 128, 0, s>>>(cen_pad, HWp, Wp, P, H, W, ref, armviews, otab, ca, Lc, Lcd, out, armsum); break;

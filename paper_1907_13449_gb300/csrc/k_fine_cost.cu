@@ -394,9 +394,10 @@ constexpr int kRowKW = 36;
 
 __global__ void list_all_kernel(const int *__restrict__ lo, const int *__restrict__ cnt,
                                 const long long *__restrict__ off, int G, int2 *list, int *count, int N,
-                                int *status) {
+                                int *status, int min_cnt) {
     const int p = blockIdx.x * blockDim.x + threadIdx.x;
-    if (p < N && window_ok(lo[p], cnt[p], G, off[p + 1] - off[p], status)) push_chunks(list, count, p, cnt[p]);
+    if (p < N && cnt[p] > min_cnt && window_ok(lo[p], cnt[p], G, off[p + 1] - off[p], status))
+        push_chunks(list, count, p, cnt[p]);
 }
 
 int r128(int x) { return (x + 127) & ~127; }
@@ -499,8 +500,8 @@ cudaError_t launch_fine_cost_rows(cudaStream_t s, const RowPlanHost *ph, const f
 }
 
 cudaError_t launch_list_all(cudaStream_t s, const int *lo, const int *cnt, const long long *off, int G, int2 *list,
-                            int *count, int N, int *status) {
-    list_all_kernel<<<(N + 255) / 256, 256, 0, s>>>(lo, cnt, off, G, list, count, N, status);
+                            int *count, int N, int *status, int min_cnt) {
+    list_all_kernel<<<(N + 255) / 256, 256, 0, s>>>(lo, cnt, off, G, list, count, N, status, min_cnt);
     return cudaGetLastError();
 }
 

@@ -5,7 +5,7 @@
 // neighbours, delta = (C(g-1) - C(g+1)) / (2 (C(g-1) - 2 C(g) + C(g+1))), when the winner
 // lies in [lo+1, lo+cnt-2] and that interval holds at least 3 labels (cnt >= 5); Eq. 13
 // prints the denominator with the opposite sign, which would move away from the lower
-// neighbour.  Mode 2 is the soft-argmin sum_g softmax(-C/tau)_g d_g.
+// neighbour.  Mode 2 is the soft-argmin sum_g softmax(-C/tau)_g d_g (FP32 weights).
 #include "lfsgm_internal.cuh"
 
 namespace lfsgm {
@@ -33,13 +33,16 @@ __global__ void wta_kernel(const float *__restrict__ agg, const int *__restrict_
     if (label) label[p] = l + b;
     if (!disp) return;
     if (mode == 2) {
-        double num = 0.0, den = 0.0;
+        // FP32 weights after subtracting the minimum (every exponent <= 0); the mean slot is
+        // mapped to a disparity in double
+        const float it = 1.f / tau;
+        float num = 0.f, den = 0.f;
         for (int j = 0; j < n; j++) {
-            const double w = exp(-((double)s[j] - (double)bv) / (double)tau);
-            num += w * (dmin + (double)(l + j) * step);
+            const float w = expf((bv - s[j]) * it);
+            num = fmaf(w, (float)j, num);
             den += w;
         }
-        disp[p] = (float)(num / den);
+        disp[p] = (float)(dmin + ((double)l + (double)(num / den)) * step);
         return;
     }
     double delta = 0.0;

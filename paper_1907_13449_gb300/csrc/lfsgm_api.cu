@@ -594,9 +594,15 @@ lfsgm_status lfsgm_backward(lfsgm_handle h, const float *views, const float *cos
                                    h->b_amin, (size_t)cap, grad_cost, h->b_gp, h->status);
     }));
     if (grad_views) {
+        // the (pixel, 32-label chunk) items of windows wider than 32 labels; narrower ones by tiles
+        e = cudaMemsetAsync(h->wide_count, 0, 4, s);
+        if (e != cudaSuccess) return cuda_fail(h, e, "memset");
+        LFSGM_TRY(run(h, "list_all", [&] {
+            return launch_list_all(s, lo, cnt, o, c.fine_labels, h->wide_list, h->wide_count, h->N, h->status, 32);
+        }));
         LFSGM_TRY(run(h, "views_backward", [&] {
             return launch_views_backward(s, views, h->d_fine, c.fine_labels, h->nviews, c.H, c.W, h->ref, lo, cnt, o,
-                                         c.w_l2, grad_cost, grad_views);
+                                         c.w_l2, grad_cost, grad_views, h->wide_list, h->wide_count);
         }));
     }
     e = cudaMemcpyAsync(grad_P1, h->b_gp, 4, cudaMemcpyDeviceToDevice, s);

@@ -153,7 +153,7 @@ cudaError_t launch_fine_cost_rows(cudaStream_t s, const RowPlanHost *ph, const f
                                   float wl2, float wc, float dmin, float fstep, float *cost, int *status,
                                   int2 *list, int *list_count);
 cudaError_t launch_list_all(cudaStream_t s, const int *lo, const int *cnt, const long long *off, int G,
-                            int2 *list, int *count, int N, int *status);
+                            int2 *list, int *count, int N, int *status, int min_cnt = 0);
 cudaError_t launch_fine_cost_list(cudaStream_t s, const float *views_pad, const uint64_t *cen_pad, int P, int Wp,
                                   int Hp, const FineTap *tab, int G, int nviews, int H, int W, int ref,
                                   const int *lo, const int *cnt, const long long *off, float wl2,
@@ -182,7 +182,7 @@ cudaError_t launch_sgm_backward(cudaStream_t s, const float *cost, const int *lo
                                 int *status);
 cudaError_t launch_views_backward(cudaStream_t s, const float *views, const FineTap *tab, int G, int nviews,
                                   int H, int W, int ref, const int *lo, const int *cnt, const long long *off,
-                                  float wl2, const float *gcost, float *gviews);
+                                  float wl2, const float *gcost, float *gviews, const int2 *list, const int *count);
 
 constexpr int kPartialBlocks = 1024;
 

@@ -69,6 +69,58 @@ def test_backward_matches_oracle_adjoint(gpu_lib):
     L.close()
 
 
+def _ragged_case(kind, seed=77):
+    """Windows of 5-40 labels at random positions (narrow windows go through the tile kernel,
+    wider ones through the per-chunk kernel); 'wide_range' spreads them over a +-12 px range so
+    that a tile's tap footprint no longer fits its shared-memory box."""
+    if kind == "mixed":
+        p = lfsynth.LFParams(U=7, V=7, H=32, W=40, census_w=5, dmin=-1.0, dmax=1.0, coarse_labels=9,
+                             fine_labels=41, fine_radius=8, w_l2=1.0, w_census=1.0 / 24, subpixel=2,
+                             softmin_tau=TAU)
+    else:
+        p = lfsynth.LFParams(U=7, V=7, H=32, W=40, census_w=5, dmin=-12.0, dmax=12.0, coarse_labels=9,
+                             fine_labels=97, fine_radius=8, w_l2=1.0, w_census=1.0 / 24, subpixel=2,
+                             softmin_tau=TAU)
+    rng = np.random.default_rng(seed)
+    views = rng.uniform(0.0, 1.0, (p.V, p.U, p.H, p.W)).astype(np.float32)
+    cnt = rng.choice(np.array([5, 16, 31, 33, 40], np.int32), size=p.N).astype(np.int32)
+    lo = (rng.random(p.N) * (p.fine_labels - cnt + 1)).astype(np.int32)
+    gd = rng.normal(size=p.N).astype(np.float32)
+    return p, views, lo, cnt, gd
+
+
+@pytest.mark.parametrize("kind", ["mixed", "wide_range"])
+def test_backward_ragged_windows_match_oracle(gpu_lib, kind):
+    import torch
+    p, views, lo, cnt, gd = _ragged_case(kind)
+    cfg = oracle.make_cfg(p)
+    off_o, cost_o = oracle.cost_volume(cfg, views, lo, cnt)
+    P1, P2 = np.float32(0.05 * cost_o.mean()), np.float32(0.5 * cost_o.mean())
+    gC_o, g1_o, g2_o, gV_o = oracle.backward(cfg, views, lo, cnt, cost_o, float(P1), float(P2), gd, TAU)
+    L = _gpu_holder(gpu_lib, p, lo, cnt)
+    vd = torch.from_numpy(views).cuda()
+    L.cost_volume(vd)
+    gcost = torch.empty_like(L.cost)
+    gviews = torch.empty_like(vd)
+    g1 = torch.zeros(1, device="cuda")
+    g2 = torch.zeros(1, device="cuda")
+    gpu_lib.lfsgm_backward(L.h, vd, L.cost, L.lo, L.cnt, L.off, float(P1), float(P2), torch.from_numpy(gd).cuda(),
+                           gcost, g1, g2, gviews)
+    gpu_lib.lfsgm_sync(L.h)
+    gC = gather(gcost.cpu().numpy(), pad4_offsets(cnt), cnt)
+    assert np.abs(gC - gC_o).max() <= GRAD_TOL * np.abs(gC_o).max()
+    # dLoss/dP1, dLoss/dP2 are signed sums over every cell and direction; FP32 errors of relative
+    # size ~1e-4 in the summed adjoints add up in proportion to their total magnitude (scale:
+    # sum |dLoss/dC|), which dominates where the sum cancels (here |dLoss/dP1| ~ 1e-3 sum |dLoss/dC|)
+    mass = 2e-3 * np.abs(gC_o).sum()
+    assert abs(g1.item() - g1_o) <= GRAD_TOL * (abs(g1_o) + mass), (g1.item(), g1_o, mass)
+    assert abs(g2.item() - g2_o) <= GRAD_TOL * (abs(g2_o) + mass), (g2.item(), g2_o, mass)
+    gV = gviews.cpu().numpy()
+    vs = np.abs(gV_o).max()
+    assert np.abs(gV - gV_o).max() <= GRAD_TOL * vs, (kind, np.abs(gV - gV_o).max(), vs)
+    L.close()
+
+
 def test_autograd_functions_match_direct_call(gpu_lib):
     import torch
     p, views, lo, cnt, gd = _setup(seed=5)
