@@ -17,6 +17,9 @@
 
 #include "lfsgm_internal.cuh"
 
+#include <algorithm>
+#include <vector>
+
 namespace lfsgm {
 namespace {
 
@@ -96,10 +99,20 @@ __global__ void __launch_bounds__(256) fine_cost_generic(const float *__restrict
 struct RowPlan {
     int P, Wp, Hp;                    // padding and padded sizes
     int bwf, bhf, bwc, bhc;           // TMA boxes (elements): view values, census words
-    int seg_cap;
-    int o_rf, o_rc, o_ts, stage;      // byte offsets of stage 0's buffers in a warp's slice; stage 1 at +stage
-    int o_segoff, o_coef, o_cdiff, o_mbar, warp_bytes;
+    int seg_cap;                      // most segments (and census breakpoints) in one label range
+    int ds_stride;                    // bytes of one (view, g0) descriptor
+    int o_rf, o_rc, o_ds, stage;      // byte offsets of stage 0's buffers in a warp's slice; stage 1 at +stage
+    int o_coef, o_cdiff, o_mbar, warp_bytes;
 };
+
+// Descriptor of the label range [g0, g0+KW) of one view (built on the host, see
+// build_fine_rows_desc): everything about the range that does not depend on the row segment.
+//   bytes  0..15  int16 xf, yf, xc, yc: tile origins relative to (x0, y); uint8 nseg, ncen
+//   bytes 16..87  uint16 segoff[KW]: byte offset (segment * 512) of label i's coefficients
+//   bytes 96..    int4 seg[seg_cap]: tile offset of the segment's (0,0) tap for lane 0, first
+//                 label, fx, fy (float bits)
+//   then          uint32 cen[seg_cap]: census breakpoint label | tile offset of its word << 8
+constexpr int kDsSegoff = 16, kDsSegs = 96;
 
 __device__ __forceinline__ unsigned smem_u32(const void *p) { return (unsigned)__cvta_generic_to_shared(p); }
 
@@ -124,23 +137,20 @@ __device__ __forceinline__ void push_chunks(int2 *list, int *count, int p, int n
 template <int KW>
 __global__ void __launch_bounds__(128, 4) fine_cost_rows(const __grid_constant__ CUtensorMap tm_v,
                                                          const __grid_constant__ CUtensorMap tm_c,
-                                                         const FineTap *__restrict__ tab, int G, int U, int V,
+                                                         const unsigned char *__restrict__ desc, int G, int U, int V,
                                                          int H, int W, int ref, const int *__restrict__ lo,
                                                          const int *__restrict__ cnt,
                                                          const long long *__restrict__ off,
                                                          const float *__restrict__ views_pad,
                                                          const uint64_t *__restrict__ cen_pad, float wl2, float wc,
-                                                         float dmin, float fstep, float *__restrict__ cost,
+                                                         float fstep, float *__restrict__ cost,
                                                          int *__restrict__ status, int2 *__restrict__ list,
                                                          int *__restrict__ list_count, RowPlan pl) {
     static_assert(KW > 32 && KW <= 64, "two 32-bit masks cover the label range");
     extern __shared__ __align__(128) unsigned char smem[];
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5, wpb = blockDim.x >> 5;
     unsigned char *wb = smem + (size_t)wib * pl.warp_bytes;
-    int *segoff = (int *)(wb + pl.o_segoff);
-    float *cA = (float *)(wb + pl.o_coef);                  // [seg_cap][32] polynomial coefficients
-    float *cB = cA + pl.seg_cap * 32;
-    float *cC = cB + pl.seg_cap * 32;
+    unsigned char *coef = wb + pl.o_coef;                   // float4 (A, B, C, -) [seg_cap][32]
     short *cdiff = (short *)(wb + pl.o_cdiff);              // [KW][32] census steps (|sum| <= views x 48)
     const unsigned mbar0 = smem_u32(wb + pl.o_mbar);
     const int nviews = U * V, uc = ref % U, vc = ref / U;
@@ -186,28 +196,20 @@ __global__ void __launch_bounds__(128, 4) fine_cost_rows(const __grid_constant__
         const int npad = (int)min((long long)((n + 3) & ~3), row);
         for (int j = n; j < npad; j++) cost[o + j] = 0.f;
     }
-    const int nvalid = min(KW, G - g0);
-    const float d0 = fmaf((float)g0, fstep, dmin), d1 = fmaf((float)(g0 + nvalid - 1), fstep, dmin);
     if (lane == 0) {
         asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(mbar0));
         asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(mbar0 + 8));
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     __syncwarp();
-    // uniform tile origins of a view (x rounded down to 16 bytes), with one label of slack
-    auto origins = [&](int view, int &xf, int &yf, int &xc, int &yc) {
-        const float a = (float)(view % U - uc), b = (float)(view / U - vc);
-        const float sx0 = a * d0, sx1 = a * d1, sy0 = b * d0, sy1 = b * d1;
-        xf = (x0 + (int)floorf(fminf(sx0, sx1)) - 1 + pl.P) & ~3;
-        yf = y + (int)floorf(fminf(sy0, sy1)) - 1 + pl.P;
-        xc = (x0 + (int)floorf(fminf(sx0, sx1) + 0.5f) - 1 + pl.P) & ~1;
-        yc = y + (int)floorf(fminf(sy0, sy1) + 0.5f) - 1 + pl.P;
-    };
-    const unsigned tx_bytes = (unsigned)(pl.bwf * pl.bhf * 4 + pl.bwc * pl.bhc * 8 + nvalid * 16);
-    auto issue = [&](int view, int st) {
+    const unsigned tx_bytes = (unsigned)(pl.bwf * pl.bhf * 4 + pl.bwc * pl.bhc * 8 + pl.ds_stride);
+    auto dsc_of = [&](int view) { return desc + ((size_t)view * G + g0) * pl.ds_stride; };
+    // tile origins (relative int16 quads) of the next views, read one view ahead of their issue
+    auto origins = [&](int view) { return __ldg(reinterpret_cast<const int2 *>(dsc_of(view))); };
+    auto issue = [&](int view, int2 org, int st) {
         if (lane != 0) return;
-        int xf, yf, xc, yc;
-        origins(view, xf, yf, xc, yc);
+        const int xf = x0 + (int)(short)(org.x & 0xffff), yf = y + (org.x >> 16);
+        const int xc = x0 + (int)(short)(org.y & 0xffff), yc = y + (org.y >> 16);
         const unsigned mb = mbar0 + 8 * st;
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(mb), "r"(tx_bytes) : "memory");
@@ -218,7 +220,7 @@ __global__ void __launch_bounds__(128, 4) fine_cost_rows(const __grid_constant__
                      ::"r"(smem_u32(wb + pl.o_rc + st * pl.stage)), "l"((unsigned long long)&tm_c), "r"(xc), "r"(yc), "r"(view), "r"(mb)
                      : "memory");
         asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
-                     ::"r"(smem_u32(wb + pl.o_ts + st * pl.stage)), "l"(tab + (size_t)view * G + g0), "r"(nvalid * 16), "r"(mb)
+                     ::"r"(smem_u32(wb + pl.o_ds + st * pl.stage)), "l"(dsc_of(view)), "r"(pl.ds_stride), "r"(mb)
                      : "memory");
     };
     float acc[KW];
@@ -228,12 +230,17 @@ __global__ void __launch_bounds__(128, 4) fine_cost_rows(const __grid_constant__
         cdiff[i * 32 + lane] = 0;
     }
     const int nv = nviews - 1;                      // every view but the reference
-    issue(ref == 0 ? 1 : 0, 0);
+    auto view_of = [&](int vi) { return vi + (vi >= ref); };
+    issue(view_of(0), origins(view_of(0)), 0);
+    int2 org_next = nv > 1 ? origins(view_of(1)) : make_int2(0, 0);
     bool ok = true;
     for (int vi = 0; vi < nv; vi++) {
-        const int view = vi + (vi >= ref);
+        const int view = view_of(vi);
         const int st = vi & 1;
-        if (vi + 1 < nv) issue(vi + 1 + (vi + 1 >= ref), st ^ 1);
+        if (vi + 1 < nv) {
+            issue(view_of(vi + 1), org_next, st ^ 1);
+            if (vi + 2 < nv) org_next = origins(view_of(vi + 2));
+        }
         if (!mbar_wait(mbar0 + 8 * st, (unsigned)(vi >> 1) & 1u)) {
             if (lane == 0) atomicExch(status, 6);
             // let the copies still in flight land (bounded) before the warp's shared memory is released
@@ -243,87 +250,56 @@ __global__ void __launch_bounds__(128, 4) fine_cost_rows(const __grid_constant__
         }
         const float *rf = (const float *)(wb + pl.o_rf + st * pl.stage);
         const uint64_t *rc = (const uint64_t *)(wb + pl.o_rc + st * pl.stage);
-        const int4 *t4 = (const int4 *)(wb + pl.o_ts + st * pl.stage);
-        int xf, yf, xc, yc;
-        origins(view, xf, yf, xc, yc);
-        const FineTap ta = *(const FineTap *)&t4[0], tb = *(const FineTap *)&t4[nvalid - 1];
-        const int oxlo = min(ta.ox, tb.ox), oxhi = max(ta.ox, tb.ox);
-        const int oylo = min(ta.oy, tb.oy), oyhi = max(ta.oy, tb.oy);
-        const int nxlo = min(ta.nx, tb.nx), nxhi = max(ta.nx, tb.nx);
-        const int nylo = min(ta.ny, tb.ny), nyhi = max(ta.ny, tb.ny);
-        // tile coordinates of the taps / census words of lane 0 at shift (0, 0)
-        const int bxf = x0 + pl.P - xf, byf = y + pl.P - yf, bxc = x0 + pl.P - xc, byc = y + pl.P - yc;
-        const int i1 = min(lane + 32, nvalid - 1);
-        const int4 e0 = t4[min(lane, nvalid - 1)], p0 = t4[min(max(lane - 1, 0), nvalid - 1)];
-        const int4 e1 = t4[i1], p1 = t4[max(i1 - 1, 0)];
-        const unsigned sm0 = __ballot_sync(0xffffffffu, lane == 0 || e0.x != p0.x);
-        const unsigned sm1 = __ballot_sync(0xffffffffu, lane + 32 < nvalid && e1.x != p1.x);
-        const unsigned cm0 = __ballot_sync(0xffffffffu, lane == 0 || e0.y != p0.y);
-        const unsigned cm1 = __ballot_sync(0xffffffffu, lane + 32 < nvalid && e1.y != p1.y);
-        const int nseg = __popc(sm0) + __popc(sm1);
-        if (bxf + oxlo < 0 || bxf + 32 + oxhi >= pl.bwf || byf + oylo < 0 || byf + oyhi + 1 >= pl.bhf ||
-            bxc + nxlo < 0 || bxc + 31 + nxhi >= pl.bwc || byc + nylo < 0 || byc + nyhi >= pl.bhc || nseg > pl.seg_cap) {
-            if (lane == 0) atomicExch(status, 7);      // cannot happen with host-sized boxes
+        const unsigned char *ds = wb + pl.o_ds + st * pl.stage;
+        const int4 hdr = *(const int4 *)ds;
+        const int nseg = hdr.z & 0xff, ncen = (hdr.z >> 8) & 0xff;
+        if (nseg < 1 || nseg > pl.seg_cap || ncen > pl.seg_cap) {
+            if (lane == 0) atomicExch(status, 7);      // cannot happen: the host checked every descriptor
             __syncwarp();
             continue;
         }
-        segoff[lane] = (__popc(sm0 & (0xffffffffu >> (31 - lane))) - 1) * 32;
-        if (lane + 32 < KW) segoff[lane + 32] = (__popc(sm0) + __popc(sm1 & (0xffffffffu >> (31 - lane))) - 1) * 32;
+        const int4 *segs = (const int4 *)(ds + kDsSegs);
+        const unsigned *cens = (const unsigned *)(ds + kDsSegs + pl.seg_cap * 16);
+        const unsigned short *segoff = (const unsigned short *)(ds + kDsSegoff);
         // census: integer steps at the census breakpoints
         {
-            unsigned m0 = cm0, m1 = cm1;
             int prev = 0;
-            while (m0 | m1) {
-                int i;
-                if (m0) {
-                    i = __ffs(m0) - 1;
-                    m0 &= m0 - 1;
-                } else {
-                    i = 32 + __ffs(m1) - 1;
-                    m1 &= m1 - 1;
-                }
-                const int wy = t4[i].y;
-                const int tnx = (int16_t)(wy & 0xffff), tny = wy >> 16;
-                const int h = __popcll(cr ^ rc[(byc + tny) * pl.bwc + (bxc + lane + tnx)]);
-                cdiff[i * 32 + lane] += (short)(h - prev);
+            for (int b = 0; b < ncen; b++) {
+                const unsigned e = cens[b];
+                const int h = __popcll(cr ^ rc[(e >> 8) + lane]);
+                cdiff[(e & 0xff) * 32 + lane] += (short)(h - prev);
                 prev = h;
             }
         }
         // l2 term: per cell segment this lane's sample polynomial in the absolute label index
         const float ax = (float)(view % U - uc) * fstep, ay = (float)(view / U - vc) * fstep;
-        {
-            unsigned m0 = sm0, m1 = sm1;
-            for (int sgi = 0; sgi < nseg; sgi++) {
-                int i;
-                if (m0) {
-                    i = __ffs(m0) - 1;
-                    m0 &= m0 - 1;
-                } else {
-                    i = 32 + __ffs(m1) - 1;
-                    m1 &= m1 - 1;
-                }
-                const int4 w = t4[i];
-                const int tox = (int16_t)(w.x & 0xffff), toy = w.x >> 16;
-                const float tfx = __int_as_float(w.z), tfy = __int_as_float(w.w);
-                const float *q = rf + (byf + toy) * pl.bwf + (bxf + lane + tox);
-                const float i00 = q[0], i10 = q[1], i01 = q[pl.bwf], i11 = q[pl.bwf + 1];
-                const float c1 = i10 - i00, c2 = i01 - i00, c3 = (i11 - i01) - c1;
-                // s(t) = c0 + c1 fx + c2 fy + c3 fx fy, fx = fx0 + ax t, fy = fy0 + ay t, t = i' - i
-                const float a0 = fmaf(c3 * tfx, tfy, fmaf(c2, tfy, fmaf(c1, tfx, i00)));
-                const float b0 = fmaf(c3, fmaf(tfx, ay, tfy * ax), fmaf(c2, ay, c1 * ax));
-                const float Cq = c3 * ax * ay;
-                const float fi = (float)i;
-                cA[sgi * 32 + lane] = fmaf(fi, fmaf(fi, Cq, -b0), a0);
-                cB[sgi * 32 + lane] = fmaf(-2.f * fi, Cq, b0);
-                cC[sgi * 32 + lane] = Cq;
-            }
+        for (int sgi = 0; sgi < nseg; sgi++) {
+            const int4 sd = segs[sgi];
+            const float tfx = __int_as_float(sd.z), tfy = __int_as_float(sd.w);
+            const float *q = rf + sd.x + lane;
+            const float i00 = q[0], i10 = q[1], i01 = q[pl.bwf], i11 = q[pl.bwf + 1];
+            const float c1 = i10 - i00, c2 = i01 - i00, c3 = (i11 - i01) - c1;
+            // s(t) = c0 + c1 fx + c2 fy + c3 fx fy, fx = fx0 + ax t, fy = fy0 + ay t, t = i' - i
+            const float a0 = fmaf(c3 * tfx, tfy, fmaf(c2, tfy, fmaf(c1, tfx, i00)));
+            const float b0 = fmaf(c3, fmaf(tfx, ay, tfy * ax), fmaf(c2, ay, c1 * ax));
+            const float Cq = c3 * ax * ay;
+            const float fi = (float)sd.y;
+            *(float4 *)(coef + sgi * 512 + lane * 16) =
+                make_float4(fmaf(fi, fmaf(fi, Cq, -b0), a0), fmaf(-2.f * fi, Cq, b0), Cq, 0.f);
         }
         __syncwarp();
+        const unsigned char *cl = coef + lane * 16;
+        // the labels' segment offsets: 16-bit fields read eight at a time (uniform 16-byte loads)
+        uint4 so[(KW + 7) / 8];
+#pragma unroll
+        for (int k = 0; k < (KW + 7) / 8; k++) so[k] = ((const uint4 *)segoff)[k];
 #pragma unroll
         for (int i = 0; i < KW; i++) {
-            const int so = segoff[i] + lane;
+            const unsigned wsel = (i & 7) < 2 ? so[i >> 3].x : (i & 7) < 4 ? so[i >> 3].y : (i & 7) < 6 ? so[i >> 3].z : so[i >> 3].w;
+            const unsigned sof = (i & 1) ? (wsel >> 16) : (wsel & 0xffffu);
+            const float4 cf = *(const float4 *)(cl + sof);
             const float fi = (float)i;
-            const float smp = fmaf(fi, fmaf(fi, cC[so], cB[so]), cA[so]);
+            const float smp = fmaf(fi, fmaf(fi, cf.z, cf.y), cf.x);
             acc[i] = fmaf(wl2, fabsf(Iref - smp), acc[i]);
         }
         __syncwarp();
@@ -422,18 +398,17 @@ bool plan_fine_rows(int U, int V, int uc, int vc, int H, int W, int G, double dm
     pl.bwc = (spx + 35 + 1) & ~1;
     pl.bhc = spy + 3;
     pl.seg_cap = min(kRowKW, spx + spy + 3);
+    pl.ds_stride = (kDsSegs + pl.seg_cap * 20 + 15) & ~15;
     int o = 0;
     pl.o_mbar = o;
     o += 128;
     pl.o_rf = o;
     pl.o_rc = pl.o_rf + r128(pl.bwf * pl.bhf * 4);
-    pl.o_ts = pl.o_rc + r128(pl.bwc * pl.bhc * 8);
-    pl.stage = pl.o_ts + r128(kRowKW * 16) - pl.o_rf;
+    pl.o_ds = pl.o_rc + r128(pl.bwc * pl.bhc * 8);
+    pl.stage = pl.o_ds + r128(pl.ds_stride) - pl.o_rf;
     o = pl.o_rf + 2 * pl.stage;
-    pl.o_segoff = o;
-    o += r128(kRowKW * 4);
     pl.o_coef = o;
-    o += r128(pl.seg_cap * 3 * 128);
+    o += r128(pl.seg_cap * 512);
     pl.o_cdiff = o;
     o += r128(kRowKW * 64);
     pl.warp_bytes = o;
@@ -444,6 +419,80 @@ bool plan_fine_rows(int U, int V, int uc, int vc, int H, int W, int G, double dm
     out->Wp = pl.Wp;
     out->Hp = pl.Hp;
     return out->ok;
+}
+
+// Descriptors of every (view, g0) label range for the row kernel, from the host copy of the
+// tap table.  The tile origins repeat the kernel's former FP32 estimate (one label of slack around
+// the range's shifts, x rounded down to 16 bytes); every tap and census word of the range is
+// checked to lie inside the tile boxes here, so the kernel needs no bounds test.  Returns false
+// (the caller then sends every window to the list kernel) if any range does not fit.
+bool build_fine_rows_desc(const RowPlanHost *ph, const FineTap *tab, int U, int V, int uc, int vc, int G, float dmin,
+                          float fstep, std::vector<unsigned char> &out) {
+    RowPlan pl;
+    memcpy(&pl, ph->raw, sizeof(pl));
+    const int nviews = U * V;
+    const size_t bytes = (size_t)nviews * G * pl.ds_stride;
+    if (bytes > ((size_t)512 << 20)) return false;
+    out.assign(bytes, 0);
+    std::vector<int> segstart, censtart;
+    for (int view = 0; view < nviews; view++) {
+        const float a = (float)(view % U - uc), b = (float)(view / U - vc);
+        for (int g0 = 0; g0 < G; g0++) {
+            unsigned char *d = out.data() + ((size_t)view * G + g0) * pl.ds_stride;
+            const int nvalid = std::min(kRowKW, G - g0);
+            const float d0 = std::fmaf((float)g0, fstep, dmin), d1 = std::fmaf((float)(g0 + nvalid - 1), fstep, dmin);
+            const float sx0 = a * d0, sx1 = a * d1, sy0 = b * d0, sy1 = b * d1;
+            const int xf = ((int)std::floor(std::fmin(sx0, sx1)) - 1 + pl.P) & ~3;
+            const int yf = (int)std::floor(std::fmin(sy0, sy1)) - 1 + pl.P;
+            const int xc = ((int)std::floor(std::fmin(sx0, sx1) + 0.5f) - 1 + pl.P) & ~1;
+            const int yc = (int)std::floor(std::fmin(sy0, sy1) + 0.5f) - 1 + pl.P;
+            const int bxf = pl.P - xf, byf = pl.P - yf, bxc = pl.P - xc, byc = pl.P - yc;
+            const FineTap *t = tab + (size_t)view * G + g0;
+            segstart.clear();
+            censtart.clear();
+            int oxlo = 1 << 30, oxhi = -(1 << 30), oylo = 1 << 30, oyhi = -(1 << 30);
+            int nxlo = 1 << 30, nxhi = -(1 << 30), nylo = 1 << 30, nyhi = -(1 << 30);
+            for (int i = 0; i < nvalid; i++) {
+                if (i == 0 || t[i].ox != t[i - 1].ox || t[i].oy != t[i - 1].oy) segstart.push_back(i);
+                if (i == 0 || t[i].nx != t[i - 1].nx || t[i].ny != t[i - 1].ny) censtart.push_back(i);
+                oxlo = std::min(oxlo, (int)t[i].ox);
+                oxhi = std::max(oxhi, (int)t[i].ox);
+                oylo = std::min(oylo, (int)t[i].oy);
+                oyhi = std::max(oyhi, (int)t[i].oy);
+                nxlo = std::min(nxlo, (int)t[i].nx);
+                nxhi = std::max(nxhi, (int)t[i].nx);
+                nylo = std::min(nylo, (int)t[i].ny);
+                nyhi = std::max(nyhi, (int)t[i].ny);
+            }
+            if (bxf + oxlo < 0 || bxf + 32 + oxhi >= pl.bwf || byf + oylo < 0 || byf + oyhi + 1 >= pl.bhf ||
+                bxc + nxlo < 0 || bxc + 31 + nxhi >= pl.bwc || byc + nylo < 0 || byc + nyhi >= pl.bhc ||
+                (int)segstart.size() > pl.seg_cap || (int)censtart.size() > pl.seg_cap)
+                return false;
+            const int16_t org[4] = {(int16_t)xf, (int16_t)(yf), (int16_t)xc, (int16_t)yc};
+            memcpy(d, org, 8);
+            d[8] = (unsigned char)segstart.size();
+            d[9] = (unsigned char)censtart.size();
+            uint16_t *segoff = (uint16_t *)(d + kDsSegoff);
+            for (int i = 0, sg = -1; i < kRowKW; i++) {
+                if (sg + 1 < (int)segstart.size() && segstart[sg + 1] == i) sg++;
+                segoff[i] = (uint16_t)(sg * 512);
+            }
+            int32_t *seg = (int32_t *)(d + kDsSegs);
+            for (size_t k = 0; k < segstart.size(); k++) {
+                const FineTap &w = t[segstart[k]];
+                seg[4 * k] = (byf + w.oy) * pl.bwf + (bxf + w.ox);
+                seg[4 * k + 1] = segstart[k];
+                memcpy(&seg[4 * k + 2], &w.fx, 4);
+                memcpy(&seg[4 * k + 3], &w.fy, 4);
+            }
+            uint32_t *cen = (uint32_t *)(d + kDsSegs + pl.seg_cap * 16);
+            for (size_t k = 0; k < censtart.size(); k++) {
+                const FineTap &w = t[censtart[k]];
+                cen[k] = (uint32_t)censtart[k] | ((uint32_t)((byc + w.ny) * pl.bwc + (bxc + w.nx)) << 8);
+            }
+        }
+    }
+    return true;
 }
 
 // Tensor maps of the padded views (float) and census words (uint64), 3-D [view][Hp][Wp].
@@ -482,8 +531,8 @@ bool encode_fine_rows_maps(RowPlanHost *ph, const float *views_pad, const uint64
 }
 
 cudaError_t launch_fine_cost_rows(cudaStream_t s, const RowPlanHost *ph, const float *views_pad,
-                                  const uint64_t *cen_pad, const FineTap *tab, int G, int U, int V, int H, int W, int ref,
-                                  const int *lo, const int *cnt, const long long *off, float wl2, float wc, float dmin,
+                                  const uint64_t *cen_pad, const unsigned char *desc, int G, int U, int V, int H, int W,
+                                  int ref, const int *lo, const int *cnt, const long long *off, float wl2, float wc,
                                   float fstep, float *cost, int *status, int2 *list, int *list_count) {
     RowPlan pl;
     memcpy(&pl, ph->raw, sizeof(pl));
@@ -494,8 +543,8 @@ cudaError_t launch_fine_cost_rows(cudaStream_t s, const RowPlanHost *ph, const f
     const long long tasks = (long long)((W + 31) / 32) * H;
     const unsigned grid = (unsigned)((tasks + wpb - 1) / wpb);
     fine_cost_rows<kRowKW><<<grid, 32 * wpb, smem, s>>>(*(const CUtensorMap *)ph->tm_v, *(const CUtensorMap *)ph->tm_c,
-                                                        tab, G, U, V, H, W, ref, lo, cnt, off, views_pad, cen_pad, wl2,
-                                                        wc, dmin, fstep, cost, status, list, list_count, pl);
+                                                        desc, G, U, V, H, W, ref, lo, cnt, off, views_pad, cen_pad, wl2,
+                                                        wc, fstep, cost, status, list, list_count, pl);
     return cudaGetLastError();
 }
 

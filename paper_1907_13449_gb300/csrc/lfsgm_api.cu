@@ -55,6 +55,7 @@ struct lfsgm_ctx {
     ArmList arms{};
     // device tables
     FineTap *d_fine = nullptr;
+    unsigned char *d_rowdesc = nullptr;   // row-kernel descriptors per (view, g0)
     int *d_otab = nullptr;       // coarse census offsets per (arm view, label), see CoarseArms
     CoarseArms ca{};
     int *d_armviews = nullptr;   // [4][kMaxArmViews]
@@ -346,6 +347,16 @@ lfsgm_status lfsgm_create(const lfsgm_config *cfg, void *stream, lfsgm_handle *o
     if (e == cudaSuccess) e = cudaMemcpy(dst, vec.data(), vec.size() * sizeof(vec[0]), cudaMemcpyHostToDevice); \
     if (e != cudaSuccess) { g_create_err = cudaGetErrorString(e); lfsgm_destroy(h); return LFSGM_ERR_CUDA; }
     ALLOC_COPY(h->d_fine, fine);
+    if (h->rows.ok) {
+        std::vector<unsigned char> desc;
+        const float fstep = (float)((c.dmax - c.dmin) / (double)(c.fine_labels - 1));
+        if (build_fine_rows_desc(&h->rows, fine.data(), c.U, c.V, c.uc, c.vc, c.fine_labels, (float)c.dmin, fstep,
+                                 desc)) {
+            ALLOC_COPY(h->d_rowdesc, desc);
+        } else {
+            h->rows.ok = false;      // every window then goes through the list kernel
+        }
+    }
     ALLOC_COPY(h->d_otab, otab);
     ALLOC_COPY(h->d_armviews, armviews);
     ALLOC_COPY(h->d_sel_cross, sel_cross);
@@ -359,6 +370,7 @@ lfsgm_status lfsgm_destroy(lfsgm_handle h) {
     if (!h) return LFSGM_ERR_INVALID_ARG;
     cudaDeviceSynchronize();
     cudaFree(h->d_fine);
+    cudaFree(h->d_rowdesc);
     cudaFree(h->d_otab);
     cudaFree(h->d_armviews);
     cudaFree(h->d_sel_cross);
@@ -473,9 +485,9 @@ lfsgm_status lfsgm_cost_volume(lfsgm_handle h, const float *views, const int32_t
     const float fstep = (float)((c.dmax - c.dmin) / (double)(c.fine_labels - 1));
     if (h->rows_maps) {
         LFSGM_TRY(run(h, "fine_cost", [&] {
-            return launch_fine_cost_rows(s, &h->rows, h->views_pad, h->cen_pad, h->d_fine, c.fine_labels, c.U, c.V,
-                                         c.H, c.W, h->ref, lo, cnt, (const long long *)off, c.w_l2, c.w_census,
-                                         (float)c.dmin, fstep, cost, h->status, h->wide_list, h->wide_count);
+            return launch_fine_cost_rows(s, &h->rows, h->views_pad, h->cen_pad, h->d_rowdesc, c.fine_labels, c.U,
+                                         c.V, c.H, c.W, h->ref, lo, cnt, (const long long *)off, c.w_l2, c.w_census,
+                                         fstep, cost, h->status, h->wide_list, h->wide_count);
         }));
     } else {
         // shapes whose row tiles do not fit the TMA boxes: every pixel through the list kernel

@@ -4,6 +4,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <vector>
+
 namespace lfsgm {
 
 // Per (view, fine label) shift split of (u-uc, v-vc) * d_g, built on the host in
@@ -147,11 +149,12 @@ bool plan_fine_rows(int U, int V, int uc, int vc, int H, int W, int G, double dm
 bool encode_fine_rows_maps(RowPlanHost *ph, const float *views_pad, const uint64_t *cen_pad, int nviews);
 cudaError_t launch_census_pad(cudaStream_t s, const float *views, int H, int W, int census_w, int P, int Wp,
                               int Hp, const int *d_sel, int nsel, uint64_t *cen_pad, float *views_pad);
+bool build_fine_rows_desc(const RowPlanHost *ph, const FineTap *tab, int U, int V, int uc, int vc, int G,
+                          float dmin, float fstep, std::vector<unsigned char> &out);
 cudaError_t launch_fine_cost_rows(cudaStream_t s, const RowPlanHost *ph, const float *views_pad,
-                                  const uint64_t *cen_pad, const FineTap *tab, int G, int U, int V, int H,
-                                  int W, int ref, const int *lo, const int *cnt, const long long *off,
-                                  float wl2, float wc, float dmin, float fstep, float *cost, int *status,
-                                  int2 *list, int *list_count);
+                                  const uint64_t *cen_pad, const unsigned char *desc, int G, int U, int V, int H,
+                                  int W, int ref, const int *lo, const int *cnt, const long long *off, float wl2,
+                                  float wc, float fstep, float *cost, int *status, int2 *list, int *list_count);
 cudaError_t launch_list_all(cudaStream_t s, const int *lo, const int *cnt, const long long *off, int G,
                             int2 *list, int *count, int N, int *status, int min_cnt = 0);
 cudaError_t launch_fine_cost_list(cudaStream_t s, const float *views_pad, const uint64_t *cen_pad, int P, int Wp,
