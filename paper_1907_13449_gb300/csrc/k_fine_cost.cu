@@ -108,11 +108,11 @@ struct RowPlan {
 // Descriptor of the label range [g0, g0+KW) of one view (built on the host, see
 // build_fine_rows_desc): everything about the range that does not depend on the row segment.
 //   bytes  0..15  int16 xf, yf, xc, yc: tile origins relative to (x0, y); uint8 nseg, ncen
-//   bytes 16..87  uint16 segoff[KW]: byte offset (segment * 512) of label i's coefficients
-//   bytes 96..    int4 seg[seg_cap]: tile offset of the segment's (0,0) tap for lane 0, first
+//   bytes 16..23  uint64 smask: bit i set where label i starts a segment (bit 0 always)
+//   bytes 32..    int4 seg[seg_cap]: tile offset of the segment's (0,0) tap for lane 0, first
 //                 label, fx, fy (float bits)
 //   then          uint32 cen[seg_cap]: census breakpoint label | tile offset of its word << 8
-constexpr int kDsSegoff = 16, kDsSegs = 96;
+constexpr int kDsMask = 16, kDsSegs = 32;
 
 __device__ __forceinline__ unsigned smem_u32(const void *p) { return (unsigned)__cvta_generic_to_shared(p); }
 
@@ -260,7 +260,6 @@ __global__ void __launch_bounds__(128, 4) fine_cost_rows(const __grid_constant__
         }
         const int4 *segs = (const int4 *)(ds + kDsSegs);
         const unsigned *cens = (const unsigned *)(ds + kDsSegs + pl.seg_cap * 16);
-        const unsigned short *segoff = (const unsigned short *)(ds + kDsSegoff);
         // census: integer steps at the census breakpoints
         {
             int prev = 0;
@@ -288,16 +287,19 @@ __global__ void __launch_bounds__(128, 4) fine_cost_rows(const __grid_constant__
                 make_float4(fmaf(fi, fmaf(fi, Cq, -b0), a0), fmaf(-2.f * fi, Cq, b0), Cq, 0.f);
         }
         __syncwarp();
-        const unsigned char *cl = coef + lane * 16;
-        // the labels' segment offsets: 16-bit fields read eight at a time (uniform 16-byte loads)
-        uint4 so[(KW + 7) / 8];
-#pragma unroll
-        for (int k = 0; k < (KW + 7) / 8; k++) so[k] = ((const uint4 *)segoff)[k];
+        // the lane's coefficients of the current segment stay in registers; a new segment's are
+        // loaded where the (warp-uniform) start mask has a bit
+        const uint2 smask = *(const uint2 *)(ds + kDsMask);
+        // (one predicated pointer step and load per label, the mask bit tested against an
+        // immediate: no branch, and the load stays where it is)
+        unsigned cp = smem_u32(coef + lane * 16) - 512u;
+        float4 cf = make_float4(0.f, 0.f, 0.f, 0.f);
 #pragma unroll
         for (int i = 0; i < KW; i++) {
-            const unsigned wsel = (i & 7) < 2 ? so[i >> 3].x : (i & 7) < 4 ? so[i >> 3].y : (i & 7) < 6 ? so[i >> 3].z : so[i >> 3].w;
-            const unsigned sof = (i & 1) ? (wsel >> 16) : (wsel & 0xffffu);
-            const float4 cf = *(const float4 *)(cl + sof);
+            asm volatile("{\n .reg .pred p;\n .reg .b32 t;\n and.b32 t, %5, %6;\n setp.ne.u32 p, t, 0;\n"
+                         " @p add.u32 %4, %4, 512;\n @p ld.shared.v4.f32 {%0, %1, %2, %3}, [%4];\n}"
+                         : "+f"(cf.x), "+f"(cf.y), "+f"(cf.z), "+f"(cf.w), "+r"(cp)
+                         : "r"(i < 32 ? smask.x : smask.y), "r"(1u << (i & 31)));
             const float fi = (float)i;
             const float smp = fmaf(fi, fmaf(fi, cf.z, cf.y), cf.x);
             acc[i] = fmaf(wl2, fabsf(Iref - smp), acc[i]);
@@ -472,11 +474,9 @@ bool build_fine_rows_desc(const RowPlanHost *ph, const FineTap *tab, int U, int 
             memcpy(d, org, 8);
             d[8] = (unsigned char)segstart.size();
             d[9] = (unsigned char)censtart.size();
-            uint16_t *segoff = (uint16_t *)(d + kDsSegoff);
-            for (int i = 0, sg = -1; i < kRowKW; i++) {
-                if (sg + 1 < (int)segstart.size() && segstart[sg + 1] == i) sg++;
-                segoff[i] = (uint16_t)(sg * 512);
-            }
+            uint64_t smask = 0;
+            for (int i : segstart) smask |= 1ull << i;
+            memcpy(d + kDsMask, &smask, 8);
             int32_t *seg = (int32_t *)(d + kDsSegs);
             for (size_t k = 0; k < segstart.size(); k++) {
                 const FineTap &w = t[segstart[k]];
