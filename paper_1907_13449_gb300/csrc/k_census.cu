@@ -13,6 +13,26 @@ namespace {
 
 constexpr int TX = 32, TY = 8;
 
+// Census word of the pixel whose (2 HALF + 1)^2 window starts at t (row stride ld, centre value c):
+// bit k = [c > neighbour k], neighbours row-major without the centre, bit 0 first.  c > nb holds
+// exactly when nb - c is negative (the difference of two distinct finite floats never rounds to
+// zero, x - x = +0, and the tile holds no -0: values are staged as x + 0, which maps -0 to +0),
+// so each bit is the sign of one FP32 subtraction, shifted into the word
+// by a funnel shift; neighbours are visited last to first so that neighbour 0 ends in bit 0.
+template <int HALF>
+__device__ __forceinline__ uint64_t census_word(const float *t, int ld, float c) {
+    constexpr int WN = 2 * HALF + 1, NB = WN * WN - 1, CEN = HALF * WN + HALF;
+    uint32_t lo = 0, hi = 0;
+#pragma unroll
+    for (int k = NB - 1; k >= 0; k--) {
+        const int q = k < CEN ? k : k + 1;                 // window position of neighbour k
+        const float d = t[(q / WN) * ld + (q % WN)] - c;
+        if (k >= 32) hi = __funnelshift_l(__float_as_uint(d), hi, 1);
+        else lo = __funnelshift_l(__float_as_uint(d), lo, 1);
+    }
+    return ((uint64_t)hi << 32) | lo;
+}
+
 template <int HALF>
 __global__ void __launch_bounds__(TX *TY) census_kernel(const float *__restrict__ views, int H, int W,
                                                         const int *__restrict__ sel,
@@ -28,27 +48,13 @@ __global__ void __launch_bounds__(TX *TY) census_kernel(const float *__restrict_
         int ty = i / SW, tx = i - ty * SW;
         int gy = min(max(y0 + ty - HALF, 0), H - 1);
         int gx = min(max(x0 + tx - HALF, 0), W - 1);
-        tile[ty][tx] = __ldg(img + (size_t)gy * W + gx);
+        tile[ty][tx] = __ldg(img + (size_t)gy * W + gx) + 0.0f;   // -0 becomes +0 (see census_word)
     }
     __syncthreads();
     const int x = x0 + threadIdx.x, y = y0 + threadIdx.y;
     if (x >= W || y >= H) return;
     const float c = tile[threadIdx.y + HALF][threadIdx.x + HALF];
-    uint32_t lo = 0, hi = 0;
-    int bit = 0;
-#pragma unroll
-    for (int dy = -HALF; dy <= HALF; dy++) {
-#pragma unroll
-        for (int dx = -HALF; dx <= HALF; dx++) {
-            if (dx == 0 && dy == 0) continue;
-            const float nb = tile[threadIdx.y + HALF + dy][threadIdx.x + HALF + dx];
-            const uint32_t b = c > nb ? 1u : 0u;
-            if (bit < 32) lo |= b << bit;
-            else hi |= b << (bit - 32);
-            bit++;
-        }
-    }
-    cen[(size_t)view * HW + (size_t)y * W + x] = ((uint64_t)hi << 32) | lo;
+    cen[(size_t)view * HW + (size_t)y * W + x] = census_word<HALF>(&tile[threadIdx.y][threadIdx.x], SW + 1, c);
 }
 
 // Same transform, written into edge-replicated padded images: word and value of pixel (x,y) go to
@@ -71,27 +77,13 @@ __global__ void __launch_bounds__(TX *TY) census_pad_kernel(const float *__restr
         int ty = i / SW, tx = i - ty * SW;
         int gy = min(max(y0 + ty - HALF, 0), H - 1);
         int gx = min(max(x0 + tx - HALF, 0), W - 1);
-        tile[ty][tx] = __ldg(img + (size_t)gy * W + gx);
+        tile[ty][tx] = __ldg(img + (size_t)gy * W + gx) + 0.0f;   // -0 becomes +0 (see census_word)
     }
     __syncthreads();
     const int x = x0 + threadIdx.x, y = y0 + threadIdx.y;
     if (x >= W || y >= H) return;
     const float c = tile[threadIdx.y + HALF][threadIdx.x + HALF];
-    uint32_t lo = 0, hi = 0;
-    int bit = 0;
-#pragma unroll
-    for (int dy = -HALF; dy <= HALF; dy++) {
-#pragma unroll
-        for (int dx = -HALF; dx <= HALF; dx++) {
-            if (dx == 0 && dy == 0) continue;
-            const float nb = tile[threadIdx.y + HALF + dy][threadIdx.x + HALF + dx];
-            const uint32_t b = c > nb ? 1u : 0u;
-            if (bit < 32) lo |= b << bit;
-            else hi |= b << (bit - 32);
-            bit++;
-        }
-    }
-    const uint64_t w = ((uint64_t)hi << 32) | lo;
+    const uint64_t w = census_word<HALF>(&tile[threadIdx.y][threadIdx.x], SW + 1, c);
     const int xa = x == 0 ? 0 : x + P, xb = x == W - 1 ? Wp - 1 : x + P;
     const int ya = y == 0 ? 0 : y + P, yb = y == H - 1 ? Hp - 1 : y + P;
     uint64_t *cp = cen_pad + (size_t)view * HWp;

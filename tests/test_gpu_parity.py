@@ -130,6 +130,27 @@ def test_cost_census_only_is_exact(gpu_lib):
     assert np.array_equal(gather(c, off, cnt).astype(np.float64), o_cost)
 
 
+@pytest.mark.parametrize("census_w", [5, 7])
+def test_census_with_ties_and_signed_zeros_is_exact(gpu_lib, census_w):
+    """Views quantised to 4 levels (many equal neighbours) with a quarter of the zeros stored as
+    -0.0: xi = [centre > neighbour] is false for equal values, +0 and -0 included (Eq. 3)."""
+    p = lfsynth.tiny_params(U=5, V=5, H=40, W=56, w_l2=0.0, w_census=1.0, census_w=census_w)
+    rng = np.random.default_rng(3)
+    views = (rng.integers(0, 4, (p.V, p.U, p.H, p.W)) / 3.0).astype(np.float32)
+    neg = (views == 0.0) & (rng.random(views.shape) < 0.25)
+    views[neg] = -0.0
+    assert np.signbit(views).any()
+    cfg = oracle.make_cfg(p)
+    lo = rng.integers(0, 60, p.N).astype(np.int32)
+    cnt = rng.integers(1, 22, p.N).astype(np.int32)
+    o_off, o_cost = oracle.cost_volume(cfg, views, lo, cnt)
+    off, c = _gpu_cost(gpu_lib, p, views, lo, cnt)
+    assert np.array_equal(gather(c, off, cnt).astype(np.float64), o_cost)
+    g = _run_initial(gpu_lib, p, views)
+    ref = oracle.initial_disparity(cfg, views, None, p.p1_frac, p.p2_frac)
+    assert np.array_equal(g["maps"][:len(ref["arms"])], ref["maps"])
+
+
 @pytest.mark.parametrize("shape", [(5, 5, 33, 47), (3, 3, 1, 40), (9, 9, 20, 1), (4, 4, 17, 29)])
 def test_cost_volume_ragged_windows(gpu_lib, shape):
     U, V, H, W = shape
