@@ -233,38 +233,57 @@ __global__ void __launch_bounds__(128) coarse_sgm_kernel(const uint16_t *__restr
 #pragma unroll
     for (int j = 0; j < NP; j++)
         pm[j] = (k0 + 2 * j < Lc ? 0x0000ffffu : 0u) | (k0 + 2 * j + 1 < Lc ? 0xffff0000u : 0u);
-    const long long dp = (long long)dy * W + dx;
-    long long p = (long long)y * W + x;
-    auto ld = [&](long long q) {
+    // cost and sum pointers step along the scanline; the cost rows of the next four steps are in
+    // flight (a ring of four registers, indexed statically by unrolling the steps by four)
+    const long long dstep = ((long long)dy * W + dx) * Lcd;
+    const uint16_t *pc = C + ((long long)y * W + x) * Lcd;
+    uint16_t *ps = S + ((long long)y * W + x) * Lcd;
+    auto ld = [&](int t) {
         T v{};
-        if (act) v = __ldg(reinterpret_cast<const T *>(C + q * Lcd));
+        if (act && t < steps) v = __ldg(reinterpret_cast<const T *>(pc + (long long)t * dstep));
         return v;
     };
-    // the next four cost rows are in flight while a step is computed
-    T r0 = ld(p), r1{}, r2{}, r3{};
-    if (steps > 1) r1 = ld(p + dp);
-    if (steps > 2) r2 = ld(p + 2 * dp);
-    if (steps > 3) r3 = ld(p + 3 * dp);
+    T ring[4] = {ld(0), ld(1), ld(2), ld(3)};
     uint32_t L[NP];
-    uint32_t m = 0;
-    for (int t = 0; t < steps; t++, p += dp) {
-        const T cur = r0;
-        r0 = r1;
-        r1 = r2;
-        r2 = r3;
-        if (t + 4 < steps) r3 = ld(p + 4 * dp);
-        uint32_t c[NP];
-        words_of<LPT>(cur, c);
-        uint32_t Ln[NP];
-        if (t == 0) {
+    uint32_t m;
+    auto finish = [&](const uint32_t *Ln) {       // warp minimum, packed reduction, carry the row
+        uint32_t q = Ln[0];
 #pragma unroll
-            for (int j = 0; j < NP; j++) Ln[j] = (c[j] & pm[j]) | (SENT & ~pm[j]);
-        } else {
+        for (int j = 1; j < NP; j++) q = __vminu2(q, Ln[j]);
+        m = __reduce_min_sync(0xffffffffu, min(q & 0xffffu, q >> 16));
+        if (act) {
+            uint32_t v[NP];
+#pragma unroll
+            for (int j = 0; j < NP; j++) v[j] = Ln[j] & pm[j];
+            red_words<LPT>(ps, v);
+        }
+        ps += dstep;
+#pragma unroll
+        for (int j = 0; j < NP; j++) L[j] = Ln[j];
+    };
+    {   // path start: L = C
+        uint32_t c[NP], Ln[NP];
+        words_of<LPT>(ring[0], c);
+        ring[0] = ld(4);
+#pragma unroll
+        for (int j = 0; j < NP; j++) Ln[j] = (c[j] & pm[j]) | (SENT & ~pm[j]);
+        finish(Ln);
+    }
+    for (int t0 = 1; t0 < steps; t0 += 4) {
+#pragma unroll
+        for (int k = 0; k < 4; k++) {
+            const int t = t0 + k;
+            if (t >= steps) break;
+            const int slot = (1 + k) & 3;          // step t's row sits in ring[t % 4]
+            uint32_t c[NP];
+            words_of<LPT>(ring[slot], c);
+            ring[slot] = ld(t + 4);
             uint32_t left = __shfl_up_sync(0xffffffffu, L[NP - 1], 1);
             uint32_t right = __shfl_down_sync(0xffffffffu, L[0], 1);
             if (lane == 0) left = SENT;
             if (lane == 31) right = SENT;
-            const uint32_t mm = m * 0x10001u, mp2 = (m + P2) * 0x10001u;
+            const uint32_t mm = __byte_perm(m, 0, 0x1010), mp2 = __byte_perm(m + P2, 0, 0x1010);
+            uint32_t Ln[NP];
 #pragma unroll
             for (int j = 0; j < NP; j++) {
                 const uint32_t pw = (j == 0) ? left : L[j - 1];
@@ -275,19 +294,8 @@ __global__ void __launch_bounds__(128) coarse_sgm_kernel(const uint16_t *__restr
                 u = __vminu2(u, mp2);
                 Ln[j] = ((c[j] + (u - mm)) & pm[j]) | (SENT & ~pm[j]);
             }
+            finish(Ln);
         }
-        uint32_t q = Ln[0];
-#pragma unroll
-        for (int j = 1; j < NP; j++) q = __vminu2(q, Ln[j]);
-        m = __reduce_min_sync(0xffffffffu, min(q & 0xffffu, q >> 16));
-        if (act) {
-            uint32_t v[NP];
-#pragma unroll
-            for (int j = 0; j < NP; j++) v[j] = Ln[j] & pm[j];
-            red_words<LPT>(S + p * Lcd, v);
-        }
-#pragma unroll
-        for (int j = 0; j < NP; j++) L[j] = Ln[j];
     }
 }
 
