@@ -64,14 +64,14 @@ __global__ void __launch_bounds__(32 * kBwdWarps) sgm_backward_kernel(
     const float *__restrict__ cost, const int *__restrict__ lo, const int *__restrict__ cnt,
     const long long *__restrict__ off, int H, int W, int G, int Gs, float P1, float P2, ScanTable st,
     const float *__restrict__ gCs, unsigned char *__restrict__ codes, int *__restrict__ amin, size_t nnz_cap,
-    float *__restrict__ gcost, float *__restrict__ gP, int *__restrict__ status) {
+    float *__restrict__ gcost, float *__restrict__ gP, int *__restrict__ status,
+    const int *__restrict__ order) {
     extern __shared__ float sm[];
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
     const int gw = blockIdx.x * kBwdWarps + wib;
     if (gw >= st.cum[8]) return;
-    int r = 0;
-    while (gw >= st.cum[r + 1]) r++;
-    const int s = gw - st.cum[r];
+    const int rs = __ldg(order + gw);            // longest scanlines first
+    const int r = rs & 7, s = rs >> 3;
     const int dx = dir_dx(r), dy = dir_dy(r);
     int x0, y0;
     scan_start(r, s, H, W, x0, y0);
@@ -422,7 +422,7 @@ cudaError_t launch_softargmin_backward(cudaStream_t s, const float *agg, const i
 
 cudaError_t launch_sgm_backward(cudaStream_t s, const float *cost, const int *lo, const int *cnt, const long long *off,
                                 int H, int W, int G, float P1, float P2, const float *gCs, unsigned char *codes,
-                                int *amin, size_t nnz_cap, float *gcost, float *gP, int *status) {
+                                int *amin, size_t nnz_cap, float *gcost, float *gP, int *status, const int *order) {
     const ScanTable st = make_scan_table(H, W);
     const int Gs = (G + 31) & ~31;
     const size_t smem = (size_t)kBwdWarps * 4 * Gs * sizeof(float);   // bufA, bufB, lambda, codes per warp
@@ -433,7 +433,7 @@ cudaError_t launch_sgm_backward(cudaStream_t s, const float *cost, const int *lo
         if (e != cudaSuccess) return e;
     }
     sgm_backward_kernel<<<grid, 32 * kBwdWarps, smem, s>>>(cost, lo, cnt, off, H, W, G, Gs, P1, P2, st, gCs, codes,
-                                                           amin, nnz_cap, gcost, gP, status);
+                                                           amin, nnz_cap, gcost, gP, status, order);
     return cudaGetLastError();
 }
 

@@ -201,7 +201,8 @@ __device__ __forceinline__ void red_words(uint16_t *dst, const uint32_t *v) {
 template <int LPT>
 __global__ void __launch_bounds__(128) coarse_sgm_kernel(const uint16_t *__restrict__ cost, int H, int W, int Lc,
                                                          int Lcd, const int *__restrict__ pen, ScanTable st,
-                                                         int narms, uint16_t *__restrict__ sum) {
+                                                         int narms, uint16_t *__restrict__ sum,
+    const int *__restrict__ order) {
     using T = typename CVec<LPT>::T;
     constexpr int NP = LPT / 2;
     constexpr uint32_t SENT = 0x7fff7fffu;
@@ -211,9 +212,8 @@ __global__ void __launch_bounds__(128) coarse_sgm_kernel(const uint16_t *__restr
     if (gw >= per_arm * narms) return;
     const int arm = gw / per_arm;
     const int w = gw - arm * per_arm;
-    int r = 0;
-    while (w >= st.cum[r + 1]) r++;
-    const int s = w - st.cum[r];
+    const int rs = __ldg(order + w);             // longest scanlines first (within the arm)
+    const int r = rs & 7, s = rs >> 3;
     const int dx = dir_dx(r), dy = dir_dy(r);
     int x, y;
     scan_start(r, s, H, W, x, y);
@@ -354,16 +354,16 @@ cudaError_t launch_coarse_penalties(cudaStream_t s, const unsigned long long *su
 }
 
 cudaError_t launch_coarse_sgm(cudaStream_t s, const uint16_t *cost, int narms, int H, int W, int Lc,
-                              const int *pen, uint16_t *sum) {
+                              const int *pen, uint16_t *sum, const int *order) {
     const ScanTable st = make_scan_table(H, W);
     const int Lcd = coarse_stride(Lc);
     const long long warps = (long long)st.cum[8] * narms;
     const int block = 128;
     const unsigned grid = (unsigned)((warps * 32 + block - 1) / block);
     switch (coarse_lpt(Lc)) {
-    case 2: coarse_sgm_kernel<2><<<grid, block, 0, s>>>(cost, H, W, Lc, Lcd, pen, st, narms, sum); break;
-    case 4: coarse_sgm_kernel<4><<<grid, block, 0, s>>>(cost, H, W, Lc, Lcd, pen, st, narms, sum); break;
-    default: coarse_sgm_kernel<8><<<grid, block, 0, s>>>(cost, H, W, Lc, Lcd, pen, st, narms, sum); break;
+    case 2: coarse_sgm_kernel<2><<<grid, block, 0, s>>>(cost, H, W, Lc, Lcd, pen, st, narms, sum, order); break;
+    case 4: coarse_sgm_kernel<4><<<grid, block, 0, s>>>(cost, H, W, Lc, Lcd, pen, st, narms, sum, order); break;
+    default: coarse_sgm_kernel<8><<<grid, block, 0, s>>>(cost, H, W, Lc, Lcd, pen, st, narms, sum, order); break;
     }
     return cudaGetLastError();
 }

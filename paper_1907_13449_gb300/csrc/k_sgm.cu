@@ -6,7 +6,9 @@
 // alignment (slot i = lo(p) + j - lo(p-r)) is three shuffles with bounds checks: labels outside
 // the predecessor's window are absent from the minimum (Sec. III-E).  Wider windows take the
 // general form with L' in a per-warp shared-memory row (chunks of 32 slots).  Window metadata
-// is fetched 32 pixels at a time (one per lane) and the next cost row one step ahead.  The step is the
+// is fetched 32 pixels at a time (one per lane, the next block one block ahead); a ballot over a
+// block finds the steps that need the general form, and the narrow steps between them run in a
+// tight loop with the next cost row one step ahead.  The step is the
 // normalised recurrence
 //   L(p,g) = C(p,g) + (min(L'(g), L'(g-1)+P1, L'(g+1)+P1, m+P2) - m),   m = min L',
 // and the predecessor minimum m is one redux.sync.min.f32 per pixel.  The 8 directions run
@@ -15,6 +17,8 @@
 // Derived penalties: per-block partial sums (double) of the active slots, then one block
 // adds the partials in a fixed order, so the mean is deterministic.
 #include "lfsgm_internal.cuh"
+
+#include <algorithm>
 
 namespace lfsgm {
 namespace {
@@ -34,123 +38,147 @@ __global__ void __launch_bounds__(32 * kSgmWarps) fine_sgm_kernel(const float *_
                                                                   int H, int W, int Gs,
                                                                   const float *__restrict__ pen,
                                                                   int G, ScanTable st, float *__restrict__ agg,
-                                                                  int *__restrict__ status) {
+                                                                  int *__restrict__ status,
+    const int *__restrict__ order) {
     extern __shared__ float sm[];
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
     const int gw = blockIdx.x * kSgmWarps + wib;
     if (gw >= st.cum[8]) return;
-    int r = 0;
-    while (gw >= st.cum[r + 1]) r++;
-    const int s = gw - st.cum[r];
+    const int rs = __ldg(order + gw);            // longest scanlines first
+    const int r = rs & 7, s = rs >> 3;
     const int dx = dir_dx(r), dy = dir_dy(r);
     int x0, y0;
     scan_start(r, s, H, W, x0, y0);
     const int lx = dx > 0 ? W - x0 : (dx < 0 ? x0 + 1 : 0x7fffffff);
     const int ly = dy > 0 ? H - y0 : (dy < 0 ? y0 + 1 : 0x7fffffff);
     const int len = min(lx, ly);
-    float *bufA = sm + (size_t)wib * 2 * Gs;   // predecessor's path costs (by slot)
+    float *bufA = sm + (size_t)wib * 2 * Gs;   // predecessor's path costs (by slot), general steps
     float *bufB = bufA + Gs;                   // this pixel's
     const float P1 = __ldg(pen), P2 = __ldg(pen + 1);
     const float INF = __int_as_float(0x7f800000);
-    // window metadata of the 32 pixels starting at step k0, one pixel per lane: (lo | cnt << 16)
-    // with cnt = 0 for an invalid window, and the row offset in units of 4 slots
-    int mwin = 0, mofs = 0;
-    auto prefetch = [&](int k0) {
-        const int k = k0 + lane;
-        mwin = 0;
+    const long long p0 = (long long)y0 * W + x0, dpix = (long long)dy * W + dx;
+    // window metadata of the 32 steps starting at kb, one step per lane: (lo | cnt << 16) with
+    // cnt = 0 for an invalid window, and the row offset in units of 4 slots
+    auto fetch = [&](int kb, int &mw, int &mo) {
+        const int k = kb + lane;
+        mw = 0;
+        mo = 0;
         if (k < len) {
-            const int p = (y0 + k * dy) * W + (x0 + k * dx);
+            const long long p = p0 + (long long)k * dpix;
             const int l_ = __ldg(lo + p), n_ = __ldg(cnt + p);
             const long long o_ = __ldg(off + p);
             if (window_ok(l_, n_, G, __ldg(off + p + 1) - o_, status) && (o_ & 3) == 0 && (o_ >> 2) < 0x7fffffff) {
-                mwin = l_ | (n_ << 16);
-                mofs = (int)(o_ >> 2);
+                mw = l_ | (n_ << 16);
+                mo = (int)(o_ >> 2);
             } else if ((o_ & 3) != 0 && status) {
                 atomicExch(status, 7);
             }
         }
     };
-    prefetch(0);
-    int win = __shfl_sync(0xffffffffu, mwin, 0), ofs = __shfl_sync(0xffffffffu, mofs, 0);
-    int l = win & 0xffff, n = win >> 16;
-    float c = (n <= 32 && lane < n) ? __ldg(cost + 4ll * ofs + lane) : 0.f;
-    int plo = 0, pn = 0;
-    float prev = INF, m = 0.f;
-    bool first = true;
-    for (int k = 0; k < len; k++) {
-        // metadata and (narrow) cost row of the next pixel, fetched before this step's work
-        int win1 = 0, ofs1 = 0;
-        float c1 = 0.f;
-        if (k + 1 < len) {
-            if (((k + 1) & 31) == 0) prefetch(k + 1);
-            win1 = __shfl_sync(0xffffffffu, mwin, (k + 1) & 31);
-            ofs1 = __shfl_sync(0xffffffffu, mofs, (k + 1) & 31);
-            const int n1 = win1 >> 16;
-            if (n1 <= 32 && lane < n1) c1 = __ldg(cost + 4ll * ofs1 + lane);
-        }
-        const long long o = 4ll * ofs;
-        if (n == 0) {
-            first = true;      // an invalid window takes no part: the path restarts after it
-        } else if (n <= 32 && (first || pn <= 32)) {
-            // narrow step: the predecessor's costs are in registers, one slot per lane
-            float Lv = c;
-            if (!first) {
-                const int s0 = lane + (l - plo);                 // slot of this label in the predecessor
-                const float v0 = __shfl_sync(0xffffffffu, prev, s0 & 31);
-                const float vm = __shfl_sync(0xffffffffu, prev, (s0 - 1) & 31);
-                const float vp = __shfl_sync(0xffffffffu, prev, (s0 + 1) & 31);
-                float t = m + P2;
-                if ((unsigned)s0 < (unsigned)pn) t = fminf(t, v0);
-                if ((unsigned)(s0 - 1) < (unsigned)pn) t = fminf(t, vm + P1);
-                if ((unsigned)(s0 + 1) < (unsigned)pn) t = fminf(t, vp + P1);
-                Lv = c + (t - m);
-            }
-            const bool act = lane < n;
-            if (act) {
-                atomicAdd(agg + o + lane, Lv);
-                bufB[lane] = Lv;
-            }
-            prev = act ? Lv : INF;
-            m = warp_min(prev);
-            first = false;
-        } else {
-            // general step (a window wider than 32 labels on either side): costs by slot in shared memory
-            float lmin = INF;
-            for (int j = lane; j < n; j += 32) {
-                const float cc = __ldg(cost + o + j);
-                float Lv;
-                if (first) {
-                    Lv = cc;
-                } else {
-                    const int i = l + j - plo;
-                    float t = m + P2;
-                    if ((unsigned)i < (unsigned)pn) t = fminf(t, bufA[i]);
-                    if ((unsigned)(i - 1) < (unsigned)pn) t = fminf(t, bufA[i - 1] + P1);
-                    if ((unsigned)(i + 1) < (unsigned)pn) t = fminf(t, bufA[i + 1] + P1);
-                    Lv = cc + (t - m);
+    int cw, co, nw = 0, no = 0;                // this block's and the next block's metadata
+    fetch(0, cw, co);
+    if (len > 32) fetch(32, nw, no);
+    int plo = 0, pn = 0;                       // predecessor window; pn = 0: the path (re)starts
+    float prev = INF, m = 0.f;                 // predecessor row (one slot per lane) and its minimum
+    bool in_smem = false;                      // the predecessor row is in bufA (after a general step)
+    int k = 0;
+    while (k < len) {
+        const int kb = k & ~31;
+        const int kbend = min(kb + 32, len);
+        // steps of this block that need the general form: invalid or wider than 32 labels
+        const int wn = cw >> 16;
+        const unsigned bad = __ballot_sync(0xffffffffu, kb + lane < len && (wn == 0 || wn > 32));
+        const unsigned ahead = bad & (0xffffffffu << (k - kb));
+        int kend = ahead ? kb + __ffs(ahead) - 1 : kbend;
+        if (pn > 32) kend = k;                 // a wide predecessor: the general form takes this step
+        if (k < kend) {
+            // narrow steps: the predecessor row in registers, the next cost row one step ahead
+            int ofs = __shfl_sync(0xffffffffu, co, k - kb);
+            const int win = __shfl_sync(0xffffffffu, cw, k - kb);
+            int l = win & 0xffff, n = win >> 16;
+            float c = lane < n ? __ldg(cost + 4ll * ofs + lane) : 0.f;
+            for (; k < kend; k++) {
+                const int src = k + 1 - kb;     // 1 .. 32: the next step's lane in this or the next block
+                int win1 = 0, ofs1 = 0;
+                if (k + 1 < len) {
+                    win1 = __shfl_sync(0xffffffffu, src < 32 ? cw : nw, src & 31);
+                    ofs1 = __shfl_sync(0xffffffffu, src < 32 ? co : no, src & 31);
                 }
-                bufB[j] = Lv;
-                lmin = fminf(lmin, Lv);
-                atomicAdd(agg + o + j, Lv);
+                const int n1 = win1 >> 16;
+                float c1 = 0.f;
+                if (n1 <= 32 && lane < n1) c1 = __ldg(cost + 4ll * ofs1 + lane);
+                float Lv = c;
+                if (pn != 0) {
+                    const int s0 = lane + (l - plo);     // slot of this label in the predecessor
+                    const float v0 = __shfl_sync(0xffffffffu, prev, s0 & 31);
+                    const float vm = __shfl_sync(0xffffffffu, prev, (s0 - 1) & 31);
+                    const float vp = __shfl_sync(0xffffffffu, prev, (s0 + 1) & 31);
+                    float t = m + P2;
+                    if ((unsigned)s0 < (unsigned)pn) t = fminf(t, v0);
+                    if ((unsigned)(s0 - 1) < (unsigned)pn) t = fminf(t, vm + P1);
+                    if ((unsigned)(s0 + 1) < (unsigned)pn) t = fminf(t, vp + P1);
+                    Lv = c + (t - m);
+                }
+                const bool act = lane < n;
+                if (act) atomicAdd(agg + 4ll * ofs + lane, Lv);
+                prev = act ? Lv : INF;
+                m = warp_min(prev);
+                plo = l;
+                pn = n;
+                l = win1 & 0xffff;
+                n = n1;
+                ofs = ofs1;
+                c = c1;
             }
-            m = warp_min(lmin);
-            __syncwarp();
-            prev = (lane < n) ? bufB[lane] : INF;     // for a following narrow step
-            first = false;
+            in_smem = false;
         }
-        __syncwarp();
-        if (n != 0) {
-            float *tmp = bufA;
-            bufA = bufB;
-            bufB = tmp;
-            plo = l;
-            pn = n;
+        if (k < kbend) {
+            // one general step: an invalid window restarts the path; a window wider than 32 labels
+            // (this one or the predecessor's) works on rows by slot in shared memory
+            const int win = __shfl_sync(0xffffffffu, cw, k - kb), ofs = __shfl_sync(0xffffffffu, co, k - kb);
+            const int l = win & 0xffff, n = win >> 16;
+            if (n == 0) {
+                pn = 0;
+            } else {
+                if (pn != 0 && !in_smem) {
+                    if (lane < pn) bufA[lane] = prev;
+                    __syncwarp();
+                }
+                const long long o = 4ll * ofs;
+                float lmin = INF;
+                for (int j = lane; j < n; j += 32) {
+                    const float cc = __ldg(cost + o + j);
+                    float Lv = cc;
+                    if (pn != 0) {
+                        const int i = l + j - plo;
+                        float t = m + P2;
+                        if ((unsigned)i < (unsigned)pn) t = fminf(t, bufA[i]);
+                        if ((unsigned)(i - 1) < (unsigned)pn) t = fminf(t, bufA[i - 1] + P1);
+                        if ((unsigned)(i + 1) < (unsigned)pn) t = fminf(t, bufA[i + 1] + P1);
+                        Lv = cc + (t - m);
+                    }
+                    bufB[j] = Lv;
+                    lmin = fminf(lmin, Lv);
+                    atomicAdd(agg + o + j, Lv);
+                }
+                m = warp_min(lmin);
+                __syncwarp();
+                float *tmp = bufA;
+                bufA = bufB;
+                bufB = tmp;
+                prev = lane < n ? bufA[lane] : INF;   // for a following narrow step
+                in_smem = true;
+                plo = l;
+                pn = n;
+                __syncwarp();
+            }
+            k++;
         }
-        win = win1;
-        ofs = ofs1;
-        l = win & 0xffff;
-        n = win >> 16;
-        c = c1;
+        if ((k & 31) == 0 && k < len) {       // next block of metadata
+            cw = nw;
+            co = no;
+            if (k + 32 < len) fetch(k + 32, nw, no);
+        }
     }
 }
 
@@ -230,9 +258,18 @@ cudaError_t launch_fine_penalties(cudaStream_t s, const double *partial, int nbl
     return cudaGetLastError();
 }
 
+void build_scan_order(int H, int W, std::vector<int> &order) {
+    order.clear();
+    for (int r = 0; r < 8; r++)
+        for (int s = 0; s < n_scanlines(r, H, W); s++) order.push_back((s << 3) | r);
+    std::stable_sort(order.begin(), order.end(), [&](int a, int b) {
+        return scan_len(a & 7, a >> 3, H, W) > scan_len(b & 7, b >> 3, H, W);
+    });
+}
+
 cudaError_t launch_fine_sgm(cudaStream_t s, const float *cost, const int *lo, const int *cnt,
                             const long long *off, int H, int W, int G, const float *pen, float *agg,
-                            int *status) {
+                            int *status, const int *order) {
     const ScanTable st = make_scan_table(H, W);
     const int Gs = (G + 31) & ~31;
     const size_t smem = (size_t)kSgmWarps * 2 * Gs * sizeof(float);
@@ -242,7 +279,7 @@ cudaError_t launch_fine_sgm(cudaStream_t s, const float *cost, const int *lo, co
                                              (int)smem);
         if (e != cudaSuccess) return e;
     }
-    fine_sgm_kernel<<<grid, 32 * kSgmWarps, smem, s>>>(cost, lo, cnt, off, H, W, Gs, pen, G, st, agg, status);
+    fine_sgm_kernel<<<grid, 32 * kSgmWarps, smem, s>>>(cost, lo, cnt, off, H, W, Gs, pen, G, st, agg, status, order);
     return cudaGetLastError();
 }
 

@@ -56,6 +56,7 @@ struct lfsgm_ctx {
     // device tables
     FineTap *d_fine = nullptr;
     unsigned char *d_rowdesc = nullptr;   // row-kernel descriptors per (view, g0)
+    int *d_order = nullptr;               // SGM scanlines, longest first
     int *d_otab = nullptr;       // coarse census offsets per (arm view, label), see CoarseArms
     CoarseArms ca{};
     int *d_armviews = nullptr;   // [4][kMaxArmViews]
@@ -347,6 +348,11 @@ lfsgm_status lfsgm_create(const lfsgm_config *cfg, void *stream, lfsgm_handle *o
     if (e == cudaSuccess) e = cudaMemcpy(dst, vec.data(), vec.size() * sizeof(vec[0]), cudaMemcpyHostToDevice); \
     if (e != cudaSuccess) { g_create_err = cudaGetErrorString(e); lfsgm_destroy(h); return LFSGM_ERR_CUDA; }
     ALLOC_COPY(h->d_fine, fine);
+    {
+        std::vector<int> order;
+        build_scan_order(c.H, c.W, order);
+        ALLOC_COPY(h->d_order, order);
+    }
     if (h->rows.ok) {
         std::vector<unsigned char> desc;
         const float fstep = (float)((c.dmax - c.dmin) / (double)(c.fine_labels - 1));
@@ -371,6 +377,7 @@ lfsgm_status lfsgm_destroy(lfsgm_handle h) {
     cudaDeviceSynchronize();
     cudaFree(h->d_fine);
     cudaFree(h->d_rowdesc);
+    cudaFree(h->d_order);
     cudaFree(h->d_otab);
     cudaFree(h->d_armviews);
     cudaFree(h->d_sel_cross);
@@ -444,7 +451,7 @@ lfsgm_status lfsgm_initial_disparity(lfsgm_handle h, const float *views, int32_t
                                        Pc1, Pc2, h->cpen);
     }));
     LFSGM_TRY(run(h, "coarse_sgm", [&] {
-        return launch_coarse_sgm(s, h->ccost, A, c.H, c.W, c.coarse_labels, h->cpen, h->csum);
+        return launch_coarse_sgm(s, h->ccost, A, c.H, c.W, c.coarse_labels, h->cpen, h->csum, h->d_order);
     }));
     LFSGM_TRY(run(h, "coarse_wta", [&] {
         return launch_coarse_wta(s, h->csum, A, N, c.coarse_labels, h->maps, maps);
@@ -550,7 +557,7 @@ lfsgm_status lfsgm_sgm_aggregate(lfsgm_handle h, const float *cost, const int32_
         return cudaGetLastError();
     }));
     LFSGM_TRY(run(h, "fine_sgm", [&] {
-        return launch_fine_sgm(s, cost, lo, cnt, o, c.H, c.W, c.fine_labels, h->fpen, agg, h->status);
+        return launch_fine_sgm(s, cost, lo, cnt, o, c.H, c.W, c.fine_labels, h->fpen, agg, h->status, h->d_order);
     }));
     return LFSGM_OK;
 }
@@ -603,7 +610,7 @@ lfsgm_status lfsgm_backward(lfsgm_handle h, const float *views, const float *cos
     if (e != cudaSuccess) return cuda_fail(h, e, "memset");
     LFSGM_TRY(run(h, "sgm_backward", [&] {
         return launch_sgm_backward(s, cost, lo, cnt, o, c.H, c.W, c.fine_labels, P1, P2, h->b_gcs, h->b_codes,
-                                   h->b_amin, (size_t)cap, grad_cost, h->b_gp, h->status);
+                                   h->b_amin, (size_t)cap, grad_cost, h->b_gp, h->status, h->d_order);
     }));
     if (grad_views) {
         // the (pixel, 32-label chunk) items of windows wider than 32 labels; narrower ones by tiles

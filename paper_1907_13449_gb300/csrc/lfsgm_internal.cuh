@@ -88,6 +88,20 @@ inline ScanTable make_scan_table(int H, int W) {
     return t;
 }
 
+// Length of scanline s of direction r.
+__host__ __device__ inline int scan_len(int r, int s, int H, int W) {
+    int x, y;
+    scan_start(r, s, H, W, x, y);
+    const int dx = dir_dx(r), dy = dir_dy(r);
+    const int lx = dx > 0 ? W - x : (dx < 0 ? x + 1 : 0x7fffffff);
+    const int ly = dy > 0 ? H - y : (dy < 0 ? y + 1 : 0x7fffffff);
+    return lx < ly ? lx : ly;
+}
+// Every (direction r, scanline s) as (s << 3 | r), longest scanline first (ties: r, then s): the
+// SGM kernels take warps in this order, so the short diagonals fill in behind the long lines
+// instead of forming a tail.
+void build_scan_order(int H, int W, std::vector<int> &order);
+
 constexpr int kMaxArmViews = 64;
 
 struct ArmList {
@@ -118,7 +132,7 @@ cudaError_t launch_coarse_penalties(cudaStream_t s, const unsigned long long *su
                                     long long count, double p1f, double p2f, int P1, int P2,
                                     int *pen);
 cudaError_t launch_coarse_sgm(cudaStream_t s, const uint16_t *cost, int narms, int H, int W, int Lc,
-                              const int *pen, uint16_t *sum);
+                              const int *pen, uint16_t *sum, const int *order);
 cudaError_t launch_coarse_wta(cudaStream_t s, const uint16_t *sum, int narms, int N, int Lc, int *maps,
                               int *maps_out);
 
@@ -170,7 +184,7 @@ cudaError_t launch_fine_penalties(cudaStream_t s, const double *partial, int nbl
                                   double p1f, double p2f, float *pen);
 cudaError_t launch_fine_sgm(cudaStream_t s, const float *cost, const int *lo, const int *cnt,
                             const long long *off, int H, int W, int G, const float *pen, float *agg,
-                            int *status);
+                            int *status, const int *order);
 
 cudaError_t launch_wta(cudaStream_t s, const float *agg, const int *lo, const int *cnt,
                        const long long *off, int N, int G, double dmin, double step, int mode,
@@ -182,7 +196,7 @@ cudaError_t launch_softargmin_backward(cudaStream_t s, const float *agg, const i
 cudaError_t launch_sgm_backward(cudaStream_t s, const float *cost, const int *lo, const int *cnt,
                                 const long long *off, int H, int W, int G, float P1, float P2, const float *gCs,
                                 unsigned char *codes, int *amin, size_t nnz_cap, float *gcost, float *gP,
-                                int *status);
+                                int *status, const int *order);
 cudaError_t launch_views_backward(cudaStream_t s, const float *views, const FineTap *tab, int G, int nviews,
                                   int H, int W, int ref, const int *lo, const int *cnt, const long long *off,
                                   float wl2, const float *gcost, float *gviews, const int2 *list, const int *count);
