@@ -320,7 +320,7 @@ __global__ void __launch_bounds__(128, 4) fine_cost_rows(const __grid_constant__
 
 // The per-pixel form over a list of (pixel, chunk) items (the windows left by fine_cost_rows):
 // one warp per item, lane = label of the chunk, taps read from the padded views and census words
-// (no clamping needed).  The chunk's table entries arrive by bulk copies on a per-warp mbarrier,
+// (no clamping needed) at linear offsets (oy Wp + ox, ny Wp + nx) from a table of the handle.  The chunk's table entries arrive by bulk copies on a per-warp mbarrier,
 // kListVB views (up to 32 x 16 bytes each) per stage and two stages, so the taps of the next
 // views are in flight while the current ones are sampled; waits are bounded (on expiry
 // LFSGM_ERR_TIMEOUT is latched).
@@ -328,7 +328,7 @@ constexpr int kListWarps = 4, kListVB = 8;
 
 __global__ void __launch_bounds__(32 * kListWarps) fine_cost_list(const float *__restrict__ views_pad,
                                                       const uint64_t *__restrict__ cen_pad, int P, int Wp, int Hp,
-                                                      const FineTap *__restrict__ tab, int G, int nviews,
+                                                      const int4 *__restrict__ ltab, int G, int nviews,
                                                       int H, int W, int ref, const int *__restrict__ lo,
                                                       const int *__restrict__ cnt,
                                                       const long long *__restrict__ off, float wl2, float wc,
@@ -359,7 +359,7 @@ __global__ void __launch_bounds__(32 * kListWarps) fine_cost_list(const float *_
         const int npad = (int)min((long long)((n + 3) & ~3), row);
         const int j = chunk * 32 + lane;
         const int cn = min(32, n - chunk * 32);                // labels of this chunk (>= 1)
-        const FineTap *tg = tab + (l0 + chunk * 32);
+        const int4 *tg = ltab + (l0 + chunk * 32);
         // stage st receives the taps of views kListVB*b .. kListVB*b + kListVB - 1 (as present)
         auto issue = [&](int b, int st) {
             if (lane != 0) return;
@@ -397,18 +397,17 @@ __global__ void __launch_bounds__(32 * kListWarps) fine_cost_list(const float *_
             if (j < n) {
 #pragma unroll 4
                 for (int k = 0; k < vn; k++) {
-                    const int vi = b * kListVB + k, view = vi + (vi >= ref);
-                    const int4 tw = taps[w][st][k][lane];
-                    const int tox = (int16_t)(tw.x & 0xffff), toy = tw.x >> 16;
-                    const int tnx = (int16_t)(tw.y & 0xffff), tny = tw.y >> 16;
+                    const int vi = b * kListVB + k;
+                    const size_t vb = (size_t)(vi + (vi >= ref)) * HWp + base;
+                    const int4 tw = taps[w][st][k][lane];     // linear tap offsets (x + Wp y), fx, fy
                     const float tfx = __int_as_float(tw.z), tfy = __int_as_float(tw.w);
-                    const float *q = views_pad + (size_t)view * HWp + base + (ptrdiff_t)toy * Wp + tox;
+                    const float *q = views_pad + vb + tw.x;
                     const float i00 = __ldg(q), i10 = __ldg(q + 1), i01 = __ldg(q + Wp), i11 = __ldg(q + Wp + 1);
                     const float top = (1.f - tfx) * i00 + tfx * i10;
                     const float bot = (1.f - tfx) * i01 + tfx * i11;
                     const float smp = (1.f - tfy) * top + tfy * bot;
                     sl2 += fabsf(Iref - smp);
-                    sc += __popcll(cr ^ __ldg(cen_pad + (size_t)view * HWp + base + (ptrdiff_t)tny * Wp + tnx));
+                    sc += __popcll(cr ^ __ldg(cen_pad + vb + tw.y));
                 }
             }
             __syncwarp();          // the stage is refilled two batches later
@@ -604,13 +603,13 @@ cudaError_t launch_list_all(cudaStream_t s, const int *lo, const int *cnt, const
 }
 
 cudaError_t launch_fine_cost_list(cudaStream_t s, const float *views_pad, const uint64_t *cen_pad, int P, int Wp,
-                                  int Hp, const FineTap *tab, int G, int nviews, int H, int W, int ref, const int *lo,
+                                  int Hp, const int4 *ltab, int G, int nviews, int H, int W, int ref, const int *lo,
                                   const int *cnt, const long long *off, float wl2, float wc, float *cost,
                                   const int2 *list, const int *count, int *status) {
     int dev = 0, sms = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    fine_cost_list<<<sms * 12, 32 * kListWarps, 0, s>>>(views_pad, cen_pad, P, Wp, Hp, tab, G, nviews, H, W, ref, lo,
+    fine_cost_list<<<sms * 12, 32 * kListWarps, 0, s>>>(views_pad, cen_pad, P, Wp, Hp, ltab, G, nviews, H, W, ref, lo,
                                                        cnt, off, wl2, wc, cost, list, count, status);
     return cudaGetLastError();
 }

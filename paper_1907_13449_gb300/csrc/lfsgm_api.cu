@@ -57,6 +57,7 @@ struct lfsgm_ctx {
     FineTap *d_fine = nullptr;
     unsigned char *d_rowdesc = nullptr;   // row-kernel descriptors per (view, g0)
     int *d_order = nullptr;               // SGM scanlines, longest first
+    int4 *d_ltab = nullptr;               // taps as linear offsets in the padded images (list kernel)
     int *d_otab = nullptr;       // coarse census offsets per (arm view, label), see CoarseArms
     CoarseArms ca{};
     int *d_armviews = nullptr;   // [4][kMaxArmViews]
@@ -353,6 +354,20 @@ lfsgm_status lfsgm_create(const lfsgm_config *cfg, void *stream, lfsgm_handle *o
         build_scan_order(c.H, c.W, order);
         ALLOC_COPY(h->d_order, order);
     }
+    {
+        // (oy Wp + ox, ny Wp + nx, fx, fy) per (view, fine label), for the padded row stride Wp
+        std::vector<int4> ltab(fine.size());
+        for (size_t i = 0; i < fine.size(); i++) {
+            const FineTap &t = fine[i];
+            int4 e;
+            e.x = (int)t.oy * h->rows.Wp + (int)t.ox;
+            e.y = (int)t.ny * h->rows.Wp + (int)t.nx;
+            memcpy(&e.z, &t.fx, 4);
+            memcpy(&e.w, &t.fy, 4);
+            ltab[i] = e;
+        }
+        ALLOC_COPY(h->d_ltab, ltab);
+    }
     if (h->rows.ok) {
         std::vector<unsigned char> desc;
         const float fstep = (float)((c.dmax - c.dmin) / (double)(c.fine_labels - 1));
@@ -378,6 +393,7 @@ lfsgm_status lfsgm_destroy(lfsgm_handle h) {
     cudaFree(h->d_fine);
     cudaFree(h->d_rowdesc);
     cudaFree(h->d_order);
+    cudaFree(h->d_ltab);
     cudaFree(h->d_otab);
     cudaFree(h->d_armviews);
     cudaFree(h->d_sel_cross);
@@ -504,7 +520,7 @@ lfsgm_status lfsgm_cost_volume(lfsgm_handle h, const float *views, const int32_t
         }));
     }
     LFSGM_TRY(run(h, "fine_cost_wide", [&] {
-        return launch_fine_cost_list(s, h->views_pad, h->cen_pad, h->rows.P, h->rows.Wp, h->rows.Hp, h->d_fine, c.fine_labels,
+        return launch_fine_cost_list(s, h->views_pad, h->cen_pad, h->rows.P, h->rows.Wp, h->rows.Hp, h->d_ltab, c.fine_labels,
                                      h->nviews, c.H, c.W, h->ref, lo, cnt, (const long long *)off, c.w_l2, c.w_census,
                                      cost, h->wide_list, h->wide_count, h->status);
     }));
