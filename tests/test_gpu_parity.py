@@ -72,7 +72,7 @@ def test_initial_disparity_tiny_bitexact(gpu_lib, tiny_case):
 
 
 @pytest.mark.parametrize("variant", ["explicit_pen", "paper_4_views", "census7_odd_shape", "one_pass",
-                                     "row_lf"])
+                                     "row_lf", "max_coarse_labels", "two_coarse_labels"])
 def test_initial_disparity_variants(gpu_lib, variant):
     Pc = (0, 0)
     if variant == "explicit_pen":
@@ -85,6 +85,10 @@ def test_initial_disparity_variants(gpu_lib, variant):
         views, _, p = lfsynth.tiny(params=p)
     elif variant == "one_pass":
         views, _, p = lfsynth.tiny(params=lfsynth.tiny_params(fill_passes=1, phi=1.0))
+    elif variant == "max_coarse_labels":   # Lc = 256: eight labels per lane, 16-byte rows
+        views, _, p = lfsynth.tiny(params=lfsynth.tiny_params(coarse_labels=256))
+    elif variant == "two_coarse_labels":   # the smallest grid: the label step is the whole range
+        views, _, p = lfsynth.tiny(params=lfsynth.tiny_params(coarse_labels=2))
     else:  # a 3-D light field: one row of 7 views (Middlebury-like)
         p = lfsynth.tiny_params(U=7, V=1, H=30, W=70, coarse_labels=130)
         views, _, p = lfsynth.tiny(params=p)
@@ -164,6 +168,26 @@ def test_cost_volume_ragged_windows(gpu_lib, shape):
     lo[::7] = 0                      # whole-range pixels
     lo[1::11] = 80
     cnt[1::11] = 1                   # one-label windows at the top of the range
+    cfg = oracle.make_cfg(p)
+    _, o_cost = oracle.cost_volume(cfg, views, lo, cnt)
+    off, c = _gpu_cost(gpu_lib, p, views, lo, cnt)
+    err = csr_rel_err(gather(c, off, cnt), o_cost, cnt)
+    assert err < RTOL, err
+
+
+def test_cost_volume_max_fine_labels(gpu_lib):
+    """G = 4096 fine labels (the largest grid): ragged windows anywhere in the range, including
+    whole-range pixels (4096 labels, 128 list chunks each) and windows at both ends."""
+    p = lfsynth.LFParams(U=5, V=5, H=24, W=40, census_w=5, dmin=-2.0, dmax=2.0, coarse_labels=32,
+                         fine_labels=4096, fine_radius=15)
+    views = lfsynth.random_views(5, 5, 24, 40, seed=11)
+    rng = np.random.default_rng(12)
+    lo = rng.integers(0, 4096, p.N).astype(np.int32)
+    cnt = np.minimum(rng.integers(1, 40, p.N), 4096 - lo).astype(np.int32)
+    cnt[::53] = 4096
+    lo[::53] = 0
+    lo[5::17] = 0
+    lo[9::19] = 4096 - cnt[9::19]
     cfg = oracle.make_cfg(p)
     _, o_cost = oracle.cost_volume(cfg, views, lo, cnt)
     off, c = _gpu_cost(gpu_lib, p, views, lo, cnt)
