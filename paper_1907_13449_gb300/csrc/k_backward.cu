@@ -86,15 +86,43 @@ __global__ void __launch_bounds__(32 * kBwdWarps) sgm_backward_kernel(
     unsigned char *cds = (unsigned char *)(lam + Gs);
     const float INF = __int_as_float(0x7f800000);
 
+    // window metadata of 32 steps per lane: (lo | cnt << 16), 0 for an invalid window, and the
+    // row offset in units of 4 slots; the next block is fetched one block ahead
+    const long long p0 = (long long)y0 * W + x0, dpix = (long long)dy * W + dx;
+    auto fetch = [&](int kb, int &mw, int &mo, int *st_) {
+        const int k = kb + lane;
+        mw = 0;
+        mo = 0;
+        if (k >= 0 && k < len) {
+            const long long p = p0 + (long long)k * dpix;
+            const int l_ = __ldg(lo + p), n_ = __ldg(cnt + p);
+            const long long o_ = __ldg(off + p);
+            if (window_ok(l_, n_, G, __ldg(off + p + 1) - o_, st_) && (o_ & 3) == 0 && (o_ >> 2) < 0x7fffffff) {
+                mw = l_ | (n_ << 16);
+                mo = (int)(o_ >> 2);
+            }
+        }
+    };
+
     // forward recompute: branch codes and argmin slots
     int plo = 0, pn = 0;
     float m = 0.f;
     bool first = true;
+    int cw, co, nw = 0, no = 0;
+    fetch(0, cw, co, status);
+    if (len > 32) fetch(32, nw, no, status);
     for (int k = 0; k < len; k++) {
-        const int p = (y0 + k * dy) * W + (x0 + k * dx);
-        const int l = lo[p], n = cnt[p];
-        const long long o = off[p];
-        if (!window_ok(l, n, G, off[p + 1] - o, status)) {
+        const int kk = k & 31;
+        if (kk == 0 && k > 0) {
+            cw = nw;
+            co = no;
+            if (k + 32 < len) fetch(k + 32, nw, no, status);
+        }
+        const int win = __shfl_sync(0xffffffffu, cw, kk), ofs = __shfl_sync(0xffffffffu, co, kk);
+        const int p = (int)(p0 + (long long)k * dpix);
+        const int l = win & 0xffff, n = win >> 16;
+        const long long o = 4ll * ofs;
+        if (n == 0) {
             first = true;
             continue;
         }
@@ -136,27 +164,35 @@ __global__ void __launch_bounds__(32 * kBwdWarps) sgm_backward_kernel(
     }
     __syncwarp();
 
-    // reverse sweep
+    // reverse sweep (blocks of metadata in descending order; step k-1 is in this block or the one below)
     float gp1 = 0.f, gp2 = 0.f;
     bool have_inc = false;       // bufA holds the incoming adjoint of the current pixel
+    {
+        const int kb0 = (len - 1) & ~31;
+        fetch(kb0, cw, co, nullptr);
+        if (kb0 >= 32) fetch(kb0 - 32, nw, no, nullptr);
+    }
     for (int k = len - 1; k >= 0; k--) {
-        const int p = (y0 + k * dy) * W + (x0 + k * dx);
-        const int l = lo[p], n = cnt[p];
-        const long long o = off[p];
-        if (!window_ok(l, n, G, off[p + 1] - o, nullptr)) {
+        const int kb = k & ~31, kk = k & 31;
+        if (kk == 31 && k < len - 1) {       // entered a lower block
+            cw = nw;
+            co = no;
+            if (kb >= 32) fetch(kb - 32, nw, no, nullptr);
+        }
+        const int win = __shfl_sync(0xffffffffu, cw, kk), ofs = __shfl_sync(0xffffffffu, co, kk);
+        // predecessor on the path: step k - 1 (this block, or lane 31 of the block below)
+        const int wq = __shfl_sync(0xffffffffu, kk > 0 ? cw : nw, (kk + 31) & 31);
+        const int l = win & 0xffff, n = win >> 16;
+        const long long o = 4ll * ofs;
+        if (n == 0) {
             have_inc = false;
             continue;
         }
-        // predecessor on the path (valid window, inside the image)
         int q = -1, ql = 0, qn = 0;
-        if (k > 0) {
-            const int qq = (y0 + (k - 1) * dy) * W + (x0 + (k - 1) * dx);
-            const int l2 = lo[qq], n2 = cnt[qq];
-            if (window_ok(l2, n2, G, off[qq + 1] - off[qq], nullptr)) {
-                q = qq;
-                ql = l2;
-                qn = n2;
-            }
+        if (k > 0 && (wq >> 16) != 0) {
+            q = (int)(p0 + (long long)(k - 1) * dpix);
+            ql = wq & 0xffff;
+            qn = wq >> 16;
         }
         float dm = 0.f;
         for (int j = lane; j < n; j += 32) {

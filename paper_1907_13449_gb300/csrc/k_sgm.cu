@@ -146,20 +146,28 @@ __global__ void __launch_bounds__(32 * kSgmWarps) fine_sgm_kernel(const float *_
                 }
                 const long long o = 4ll * ofs;
                 float lmin = INF;
-                for (int j = lane; j < n; j += 32) {
-                    const float cc = __ldg(cost + o + j);
-                    float Lv = cc;
-                    if (pn != 0) {
-                        const int i = l + j - plo;
-                        float t = m + P2;
-                        if ((unsigned)i < (unsigned)pn) t = fminf(t, bufA[i]);
-                        if ((unsigned)(i - 1) < (unsigned)pn) t = fminf(t, bufA[i - 1] + P1);
-                        if ((unsigned)(i + 1) < (unsigned)pn) t = fminf(t, bufA[i + 1] + P1);
-                        Lv = cc + (t - m);
+                // eight 32-label chunks per round: their cost loads are in flight together
+                for (int j0 = lane; j0 < n; j0 += 256) {
+                    float cc[8];
+#pragma unroll
+                    for (int u = 0; u < 8; u++) cc[u] = j0 + 32 * u < n ? __ldg(cost + o + j0 + 32 * u) : 0.f;
+#pragma unroll
+                    for (int u = 0; u < 8; u++) {
+                        const int j = j0 + 32 * u;
+                        if (j >= n) break;
+                        float Lv = cc[u];
+                        if (pn != 0) {
+                            const int i = l + j - plo;
+                            float t = m + P2;
+                            if ((unsigned)i < (unsigned)pn) t = fminf(t, bufA[i]);
+                            if ((unsigned)(i - 1) < (unsigned)pn) t = fminf(t, bufA[i - 1] + P1);
+                            if ((unsigned)(i + 1) < (unsigned)pn) t = fminf(t, bufA[i + 1] + P1);
+                            Lv = cc[u] + (t - m);
+                        }
+                        bufB[j] = Lv;
+                        lmin = fminf(lmin, Lv);
+                        atomicAdd(agg + o + j, Lv);
                     }
-                    bufB[j] = Lv;
-                    lmin = fminf(lmin, Lv);
-                    atomicAdd(agg + o + j, Lv);
                 }
                 m = warp_min(lmin);
                 __syncwarp();
