@@ -128,8 +128,16 @@ __global__ void __launch_bounds__(32 * kBwdWarps) sgm_backward_kernel(
         }
         float bv = INF;
         int bj = 0x7fffffff;
-        for (int j = lane; j < n; j += 32) {
-            const float c = cost[o + j];
+        // eight 32-label chunks per round: their cost loads are in flight together
+        for (int j0 = lane; j0 < n; j0 += 256) {
+        float cv[8];
+#pragma unroll
+        for (int u = 0; u < 8; u++) cv[u] = j0 + 32 * u < n ? __ldg(cost + o + j0 + 32 * u) : 0.f;
+#pragma unroll
+        for (int u = 0; u < 8; u++) {
+            const int j = j0 + 32 * u;
+            if (j >= n) break;
+            const float c = cv[u];
             float Lv;
             unsigned char cd = 4;
             if (first) {
@@ -146,6 +154,7 @@ __global__ void __launch_bounds__(32 * kBwdWarps) sgm_backward_kernel(
             bufB[j] = Lv;
             code[o + j] = cd;
             if (Lv < bv) { bv = Lv; bj = j; }
+        }
         }
         // minimum and its lowest slot
         float mv;
@@ -195,10 +204,22 @@ __global__ void __launch_bounds__(32 * kBwdWarps) sgm_backward_kernel(
             qn = wq >> 16;
         }
         float dm = 0.f;
-        for (int j = lane; j < n; j += 32) {
-            const float lv = gCs[o + j] + (have_inc ? bufA[j] : 0.f);
+        for (int j0 = lane; j0 < n; j0 += 256) {
+        float gv[8];
+        unsigned char cv[8];
+#pragma unroll
+        for (int u = 0; u < 8; u++) {
+            const bool in = j0 + 32 * u < n;
+            gv[u] = in ? __ldg(gCs + o + j0 + 32 * u) : 0.f;
+            cv[u] = in ? code[o + j0 + 32 * u] : 0;
+        }
+#pragma unroll
+        for (int u = 0; u < 8; u++) {
+            const int j = j0 + 32 * u;
+            if (j >= n) break;
+            const float lv = gv[u] + (have_inc ? bufA[j] : 0.f);
             atomicAdd(gcost + o + j, lv);
-            const unsigned char cd = code[o + j];
+            const unsigned char cd = cv[u];
             lam[j] = lv;
             cds[j] = cd;
             if (cd == 1 || cd == 2) gp1 += lv;
@@ -207,6 +228,7 @@ __global__ void __launch_bounds__(32 * kBwdWarps) sgm_backward_kernel(
                 dm += lv;
             }
             dm -= lv;
+        }
         }
         dm = warp_sum(dm);
         __syncwarp();
