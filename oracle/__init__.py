@@ -68,6 +68,8 @@ def lib():
             L = _lib
             P = C.POINTER
             L.or_label_disp.restype = C.c_double
+            L.or_set_threads.argtypes = [C.c_int]
+            L.or_set_threads.restype = C.c_int
             L.or_label_disp.argtypes = [C.c_double, C.c_double, C.c_int, C.c_int]
             L.or_shift.argtypes = [C.c_int, C.c_double, P(C.c_int), P(C.c_double), P(C.c_int)]
             L.or_census.argtypes = [P(C.c_double), C.c_int, C.c_int, C.c_int, P(C.c_uint64)]
@@ -240,7 +242,12 @@ def sgm_bounded_path(H, W, lo, cnt, off, cost, P1, P2, direction, normalised=Tru
 
 def threads() -> int:
     """Threads the oracle's parallel loops use (OpenMP default: all cores)."""
-    return int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    return int(lib().or_set_threads(0))
+
+
+def set_threads(n: int) -> int:
+    """Set the threads of the oracle's parallel loops (results do not depend on it)."""
+    return int(lib().or_set_threads(int(n)))
 
 
 def sgm_bounded(H, W, lo, cnt, off, cost, P1, P2):

@@ -33,6 +33,9 @@
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
 
 typedef struct {
     int32_t U, V, H, W;   /* angular and spatial sizes                                */
@@ -647,4 +650,15 @@ void or_cost_backward_views(const or_cfg *c, const double *views, const int32_t 
                     }
             }
         }
+}
+
+/* Threads of the parallel row loops (the results do not depend on it); returns the count in use. */
+int or_set_threads(int n) {
+#ifdef _OPENMP
+    if (n > 0) omp_set_num_threads(n);
+    return omp_get_max_threads();
+#else
+    (void)n;
+    return 1;
+#endif
 }

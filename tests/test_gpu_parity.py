@@ -363,11 +363,7 @@ def bench_case():
     return views, gt, p, cfg, ref
 
 
-def test_bench_shape_full_parity(gpu_lib, bench_case):
-    """9x9 x 512x512, census 7x7, 100 coarse labels, 31-label windows: the same stage chain
-    as the benchmark, compared with the oracle on every pixel."""
-    import torch
-    views, gt, p, cfg, ref = bench_case
+def _full_parity(gpu_lib, views, p, ref):
     lf = gpu_lib.LightFieldDepth(p)
     vd = _dev(views)
     nnz = lf.initial(vd, want_nnz=True)
@@ -384,3 +380,19 @@ def test_bench_shape_full_parity(gpu_lib, bench_case):
     lf.wta()
     _check_end_to_end(_np(lf.label), _np(lf.disp), ref, p)
     lf.close()
+
+
+def test_bench_shape_full_parity(gpu_lib, bench_case):
+    """9x9 x 512x512, census 7x7, 100 coarse labels, 31-label windows: the same stage chain
+    as the benchmark, compared with the oracle on every pixel."""
+    views, gt, p, cfg, ref = bench_case
+    _full_parity(gpu_lib, views, p, ref)
+
+
+def test_plenoptic_shape_full_parity(gpu_lib):
+    """15x15 x 434x625 (225 views, vignetting, noise 0.02), census 7x7, 64 coarse labels over 29
+    views, 31-label windows on a 301-label grid: every pixel against the oracle."""
+    views, gt, p = lfsynth.plenoptic()
+    cfg = oracle.make_cfg(p)
+    ref = oracle.depth(cfg, views, p1f=p.p1_frac, p2f=p.p2_frac)
+    _full_parity(gpu_lib, views, p, ref)
