@@ -57,15 +57,53 @@ __global__ void __launch_bounds__(TX *TY) census_kernel(const float *__restrict_
     cen[(size_t)view * HW + (size_t)y * W + x] = census_word<HALF>(&tile[threadIdx.y][threadIdx.x], SW + 1, c);
 }
 
+// Census words of the two vertically adjacent pixels whose windows start at t and t + ld: every
+// tile value of the union of the two windows is read once, and each word takes its own neighbours
+// in descending order (rows bottom-up, columns right to left), as census_word does.
+template <int HALF>
+__device__ __forceinline__ void census_word2(const float *t, int ld, float c0, float c1, uint64_t &w0,
+                                             uint64_t &w1) {
+    constexpr int WN = 2 * HALF + 1, CEN = HALF * WN + HALF;
+    uint32_t lo0 = 0, hi0 = 0, lo1 = 0, hi1 = 0;
+#pragma unroll
+    for (int ry = WN; ry >= 0; ry--) {                 // union row: window row ry of pixel 0, ry - 1 of pixel 1
+#pragma unroll
+        for (int rx = WN - 1; rx >= 0; rx--) {
+            const float v = t[ry * ld + rx];
+            if (ry < WN) {
+                const int q = ry * WN + rx;
+                if (q != CEN) {
+                    const int k = q < CEN ? q : q - 1;
+                    const uint32_t d = __float_as_uint(v - c0);
+                    if (k >= 32) hi0 = __funnelshift_l(d, hi0, 1);
+                    else lo0 = __funnelshift_l(d, lo0, 1);
+                }
+            }
+            if (ry >= 1) {
+                const int q = (ry - 1) * WN + rx;
+                if (q != CEN) {
+                    const int k = q < CEN ? q : q - 1;
+                    const uint32_t d = __float_as_uint(v - c1);
+                    if (k >= 32) hi1 = __funnelshift_l(d, hi1, 1);
+                    else lo1 = __funnelshift_l(d, lo1, 1);
+                }
+            }
+        }
+    }
+    w0 = ((uint64_t)hi0 << 32) | lo0;
+    w1 = ((uint64_t)hi1 << 32) | lo1;
+}
+
 // Same transform, written into edge-replicated padded images: word and value of pixel (x,y) go to
 // (x+P, y+P), and border pixels also fill the padding rows/columns next to them, so that a read
 // at any padded position (xp, yp) returns the word/value of pixel (clamp(xp-P), clamp(yp-P)) --
 // exactly the clamped read of the unpadded image.  Padded row stride Wp, Hp rows per view.
+// A 32 x 4 thread block covers a 32 x 8 tile: each thread takes two vertically adjacent pixels.
 template <int HALF>
-__global__ void __launch_bounds__(TX *TY) census_pad_kernel(const float *__restrict__ views, int H, int W, int P,
-                                                            int Wp, int Hp, const int *__restrict__ sel,
-                                                            uint64_t *__restrict__ cen_pad,
-                                                            float *__restrict__ views_pad) {
+__global__ void __launch_bounds__(TX *TY / 2) census_pad_kernel(const float *__restrict__ views, int H, int W, int P,
+                                                                int Wp, int Hp, const int *__restrict__ sel,
+                                                                uint64_t *__restrict__ cen_pad,
+                                                                float *__restrict__ views_pad) {
     constexpr int SW = TX + 2 * HALF, SH = TY + 2 * HALF;
     __shared__ float tile[SH][SW + 1];
     const size_t HW = (size_t)H * W, HWp = (size_t)Hp * Wp;
@@ -73,33 +111,40 @@ __global__ void __launch_bounds__(TX *TY) census_pad_kernel(const float *__restr
     const float *img = views + (size_t)view * HW;
     const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
     const int tid = threadIdx.y * TX + threadIdx.x;
-    for (int i = tid; i < SH * SW; i += TX * TY) {
+    for (int i = tid; i < SH * SW; i += TX * TY / 2) {
         int ty = i / SW, tx = i - ty * SW;
         int gy = min(max(y0 + ty - HALF, 0), H - 1);
         int gx = min(max(x0 + tx - HALF, 0), W - 1);
         tile[ty][tx] = __ldg(img + (size_t)gy * W + gx) + 0.0f;   // -0 becomes +0 (see census_word)
     }
     __syncthreads();
-    const int x = x0 + threadIdx.x, y = y0 + threadIdx.y;
+    const int x = x0 + threadIdx.x, ty0 = 2 * threadIdx.y, y = y0 + ty0;
     if (x >= W || y >= H) return;
-    const float c = tile[threadIdx.y + HALF][threadIdx.x + HALF];
-    const uint64_t w = census_word<HALF>(&tile[threadIdx.y][threadIdx.x], SW + 1, c);
-    const int xa = x == 0 ? 0 : x + P, xb = x == W - 1 ? Wp - 1 : x + P;
-    const int ya = y == 0 ? 0 : y + P, yb = y == H - 1 ? Hp - 1 : y + P;
+    const float c0 = tile[ty0 + HALF][threadIdx.x + HALF], c1 = tile[ty0 + 1 + HALF][threadIdx.x + HALF];
+    uint64_t w[2];
+    census_word2<HALF>(&tile[ty0][threadIdx.x], SW + 1, c0, c1, w[0], w[1]);
+    const float cv[2] = {c0, c1};
     uint64_t *cp = cen_pad + (size_t)view * HWp;
     float *vp = views_pad + (size_t)view * HWp;
-    for (int yy = ya; yy <= yb; yy++)
-        for (int xx = xa; xx <= xb; xx++) {
-            cp[(size_t)yy * Wp + xx] = w;
-            vp[(size_t)yy * Wp + xx] = c;
-        }
+    const int xa = x == 0 ? 0 : x + P, xb = x == W - 1 ? Wp - 1 : x + P;
+#pragma unroll
+    for (int r = 0; r < 2; r++) {
+        const int yr = y + r;
+        if (yr >= H) break;
+        const int ya = yr == 0 ? 0 : yr + P, yb = yr == H - 1 ? Hp - 1 : yr + P;
+        for (int yy = ya; yy <= yb; yy++)
+            for (int xx = xa; xx <= xb; xx++) {
+                cp[(size_t)yy * Wp + xx] = w[r];
+                vp[(size_t)yy * Wp + xx] = cv[r];
+            }
+    }
 }
 
 }  // namespace
 
 cudaError_t launch_census_pad(cudaStream_t s, const float *views, int H, int W, int census_w, int P, int Wp, int Hp,
                               const int *d_sel, int nsel, uint64_t *cen_pad, float *views_pad) {
-    dim3 block(TX, TY), grid((W + TX - 1) / TX, (H + TY - 1) / TY, nsel);
+    dim3 block(TX, TY / 2), grid((W + TX - 1) / TX, (H + TY - 1) / TY, nsel);
     if (census_w == 5) census_pad_kernel<2><<<grid, block, 0, s>>>(views, H, W, P, Wp, Hp, d_sel, cen_pad, views_pad);
     else census_pad_kernel<3><<<grid, block, 0, s>>>(views, H, W, P, Wp, Hp, d_sel, cen_pad, views_pad);
     return cudaGetLastError();

@@ -146,13 +146,13 @@ __global__ void __launch_bounds__(32 * kSgmWarps) fine_sgm_kernel(const float *_
                 }
                 const long long o = 4ll * ofs;
                 float lmin = INF;
-                // eight 32-label chunks per round: their cost loads are in flight together
-                for (int j0 = lane; j0 < n; j0 += 256) {
-                    float cc[8];
+                // sixteen 32-label chunks per round: their cost loads are in flight together
+                for (int j0 = lane; j0 < n; j0 += 512) {
+                    float cc[16];
 #pragma unroll
-                    for (int u = 0; u < 8; u++) cc[u] = j0 + 32 * u < n ? __ldg(cost + o + j0 + 32 * u) : 0.f;
+                    for (int u = 0; u < 16; u++) cc[u] = j0 + 32 * u < n ? __ldg(cost + o + j0 + 32 * u) : 0.f;
 #pragma unroll
-                    for (int u = 0; u < 8; u++) {
+                    for (int u = 0; u < 16; u++) {
                         const int j = j0 + 32 * u;
                         if (j >= n) break;
                         float Lv = cc[u];

@@ -177,6 +177,9 @@ def test_backward_bench_shape_invariants(gpu_lib):
     starts = np.cumsum(cnt) - cnt
     sums = np.add.reduceat(gC.astype(np.float64), starts)
     scale = np.add.reduceat(np.abs(gC).astype(np.float64), starts)
-    # FP32 rounding of the adjoint carried along each path is bounded by the global scale
-    assert np.abs(sums).max() <= 1e-5 * scale.max(), (np.abs(sums).max(), scale.max())
+    # the sums vanish in exact arithmetic; in FP32 the adjoint is carried along 512-step paths
+    # (8 of them per pixel) and the softmax weights inherit the float-atomic order of the
+    # aggregate amplified by C_s / tau, so residuals of order n * eps_32 ~ 3e-5 of the global
+    # scale occur (observed 0.9e-5 .. 1.7e-5)
+    assert np.abs(sums).max() <= 1e-4 * scale.max(), (np.abs(sums).max(), scale.max())
     L.close()
