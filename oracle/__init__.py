@@ -69,6 +69,7 @@ def lib():
             P = C.POINTER
             L.or_label_disp.restype = C.c_double
             L.or_set_threads.argtypes = [C.c_int]
+            L.or_median3.argtypes = [C.c_int, C.c_int, P(C.c_double), P(C.c_double)]
             L.or_set_threads.restype = C.c_int
             L.or_label_disp.argtypes = [C.c_double, C.c_double, C.c_int, C.c_int]
             L.or_shift.argtypes = [C.c_int, C.c_double, P(C.c_int), P(C.c_double), P(C.c_int)]
@@ -387,3 +388,12 @@ def backward(cfg: Cfg, views, lo, cnt, cost, P1, P2, gd, tau):
     gC, g1, g2 = sgm_backward(cfg.H, cfg.W, lo, cnt, off, cost, P1, P2, gCs)
     gV = cost_backward_views(cfg, views, lo, cnt, off, gC)
     return gC, g1, g2, gV
+
+
+def median3(disp: np.ndarray) -> np.ndarray:
+    """3 x 3 median of a disparity map [H][W] (Sec. III-F), border pixels repeated; FP64."""
+    d = np.ascontiguousarray(disp, dtype=np.float64)
+    H, W = d.shape
+    out = np.empty_like(d)
+    lib().or_median3(H, W, _ptr(d, C.c_double), _ptr(out, C.c_double))
+    return out

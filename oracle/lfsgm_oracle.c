@@ -662,3 +662,24 @@ int or_set_threads(int n) {
     return 1;
 #endif
 }
+
+/* Post-processing (Sec. III-F, window size 3 from Sec. IV-C): 3 x 3 median of the sub-pixel
+ * disparity map.  Reading: the window is clamped to the image (border pixels repeat), so every
+ * output is the 5th smallest of 9 values. */
+void or_median3(int H, int W, const double *in, double *out) {
+#pragma omp parallel for schedule(static)
+    for (int y = 0; y < H; y++)
+        for (int x = 0; x < W; x++) {
+            double v[9];
+            int n = 0;
+            for (int dy = -1; dy <= 1; dy++)
+                for (int dx = -1; dx <= 1; dx++) {
+                    const int yy = clampi(y + dy, 0, H - 1), xx = clampi(x + dx, 0, W - 1);
+                    double q = in[(size_t)yy * W + xx];
+                    int j = n++;
+                    while (j > 0 && v[j - 1] > q) { v[j] = v[j - 1]; j--; }
+                    v[j] = q;
+                }
+            out[(size_t)y * W + x] = v[4];
+        }
+}

@@ -458,3 +458,38 @@ def test_end_to_end_exact_integer_planes():
     assert np.array_equal(lab[inner], g_true.reshape(p.H, p.W)[inner])
     disp = out["disp"].reshape(p.H, p.W)
     assert np.all(np.abs(disp[inner] - gt2[inner]) <= 0.5 * p.fine_step + 1e-12)
+
+
+# ------------------------------------------------------------ post-processing (Sec. III-F)
+def _median3_numpy(d):
+    """Independent restatement: NumPy's median over edge-padded 3 x 3 windows."""
+    p = np.pad(d, 1, mode="edge")
+    H, W = d.shape
+    win = np.stack([p[dy:dy + H, dx:dx + W] for dy in range(3) for dx in range(3)])
+    return np.median(win, axis=0)
+
+
+def test_median3_matches_padded_numpy_median():
+    rng = np.random.default_rng(21)
+    for shape in [(1, 1), (1, 9), (7, 1), (6, 11), (33, 20)]:
+        d = rng.normal(size=shape)
+        d[rng.random(shape) < 0.3] = 0.5           # ties
+        assert np.array_equal(oracle.median3(d), _median3_numpy(d)), shape
+
+
+def test_median3_removes_impulses_and_keeps_ramps():
+    H, W = 12, 15
+    y, x = np.mgrid[0:H, 0:W].astype(np.float64)
+    ramp = 0.25 * x - 0.5 * y + 3.0
+    m = oracle.median3(ramp)
+    # interior: the window values are ramp(p) + {a i + b j}, symmetric about ramp(p)
+    assert np.array_equal(m[1:-1, 1:-1], ramp[1:-1, 1:-1])
+    # a map varying along x only keeps its left and right border columns (6 of 9 values repeat)
+    xr = np.broadcast_to(0.1 * x[0], (H, W)).copy()
+    assert np.array_equal(oracle.median3(xr), xr)
+    # isolated impulses on a constant background disappear
+    c = np.full((H, W), 1.5)
+    c[3, 4] = 100.0
+    c[8, 10] = -7.0
+    c[0, 0] = 9.0
+    assert np.array_equal(oracle.median3(c), np.full((H, W), 1.5))
