@@ -128,6 +128,12 @@ lfsgm_status lfsgm_sgm_aggregate(lfsgm_handle h, const float *cost, const int32_
 lfsgm_status lfsgm_wta_subpixel(lfsgm_handle h, const float *agg, const int32_t *lo,
                                 const int32_t *cnt, const int64_t *off, int32_t *label, float *disp);
 
+/* Post-processing median filter (Sec. III-F; window size 3, Sec. IV-C): out(p) = median of the
+ * 3 x 3 neighbourhood of p in disp, the window clamped to the image (border values repeat), i.e.
+ * the 5th smallest of 9 values.  disp, out: [H*W] float32, device, distinct buffers.  NaN inputs
+ * (invalid windows) give an unspecified selection.  Asynchronous on the handle's stream. */
+lfsgm_status lfsgm_median_filter(lfsgm_handle h, const float *disp, float *out);
+
 /* Adjoint of cost volume -> SGM -> soft-argmin (not in the paper).  Given grad_disp
  * = dLoss/d disp of the soft-argmin output, returns dLoss/d cost (grad_cost, CSR like
  * cost), dLoss/dP1 and dLoss/dP2 (device scalars) and dLoss/d views through the l2 term

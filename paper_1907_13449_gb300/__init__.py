@@ -59,7 +59,7 @@ EXPORTS = ["lfsgm_create", "lfsgm_destroy", "lfsgm_workspace_size", "lfsgm_set_w
            "lfsgm_launch_count", "lfsgm_set_profiling", "lfsgm_kernel_times", "lfsgm_depth_host",
            "lfsgm_depth", "lfsgm_cost_volume_noalloc", "lfsgm_batch_create", "lfsgm_batch_run",
            "lfsgm_batch_times", "lfsgm_batch_kernel_nodes", "lfsgm_batch_last_error",
-           "lfsgm_batch_destroy"]
+           "lfsgm_batch_destroy", "lfsgm_median_filter"]
 
 
 def load(build_if_missing: bool = False):
@@ -105,6 +105,7 @@ def load(build_if_missing: bool = False):
         L.lfsgm_batch_last_error.argtypes = [vp]
         L.lfsgm_batch_last_error.restype = C.c_char_p
         L.lfsgm_batch_destroy.argtypes = [vp]
+        L.lfsgm_median_filter.argtypes = [vp, vp, vp]
         for name in EXPORTS:
             if name not in ("lfsgm_last_error", "lfsgm_launch_count", "lfsgm_batch_kernel_nodes",
                             "lfsgm_batch_last_error"):
@@ -227,6 +228,12 @@ def lfsgm_backward(h, views, cost, lo, cnt, off, P1, P2, grad_disp, grad_cost, g
                                  _ptr(grad_disp, f, "grad_disp"), _ptr(grad_cost, f, "grad_cost"),
                                  _ptr(grad_P1, f, "grad_P1"), _ptr(grad_P2, f, "grad_P2"),
                                  _ptr(grad_views, f, "grad_views")), h)
+
+
+def lfsgm_median_filter(h, disp, out):
+    """3 x 3 median of the disparity map (Sec. III-F), border values repeated."""
+    import torch
+    _check(load().lfsgm_median_filter(h, _ptr(disp, torch.float32, "disp"), _ptr(out, torch.float32, "out")), h)
 
 
 def lfsgm_sync(h):

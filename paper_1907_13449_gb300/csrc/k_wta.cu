@@ -54,7 +54,41 @@ __global__ void wta_kernel(const float *__restrict__ agg, const int *__restrict_
     disp[p] = (float)(dmin + ((double)(l + b) + delta) * step);
 }
 
+// 3 x 3 median (Sec. III-F): thread per pixel, the window clamped to the image; the median of
+// the 9 values by a fixed min/max exchange network (19 exchanges), exact: it selects one input.
+__device__ __forceinline__ void cswap(float &a, float &b) {
+    const float lo = fminf(a, b), hi = fmaxf(a, b);
+    a = lo;
+    b = hi;
+}
+
+__global__ void median3_kernel(const float *__restrict__ in, float *__restrict__ out, int H, int W) {
+    const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y;
+    if (x >= W) return;
+    const int xm = max(x - 1, 0), xp = min(x + 1, W - 1);
+    const int ym = max(y - 1, 0), yp = min(y + 1, H - 1);
+    const float *r0 = in + (size_t)ym * W, *r1 = in + (size_t)y * W, *r2 = in + (size_t)yp * W;
+    float p0 = __ldg(r0 + xm), p1 = __ldg(r0 + x), p2 = __ldg(r0 + xp);
+    float p3 = __ldg(r1 + xm), p4 = __ldg(r1 + x), p5 = __ldg(r1 + xp);
+    float p6 = __ldg(r2 + xm), p7 = __ldg(r2 + x), p8 = __ldg(r2 + xp);
+    // the classic 19-exchange median-of-9 selection network
+    cswap(p1, p2); cswap(p4, p5); cswap(p7, p8);
+    cswap(p0, p1); cswap(p3, p4); cswap(p6, p7);
+    cswap(p1, p2); cswap(p4, p5); cswap(p7, p8);
+    cswap(p0, p3); cswap(p5, p8); cswap(p4, p7);
+    cswap(p3, p6); cswap(p1, p4); cswap(p2, p5);
+    cswap(p4, p7); cswap(p4, p2); cswap(p6, p4);
+    cswap(p4, p2);
+    out[(size_t)y * W + x] = p4;
+}
+
 }  // namespace
+
+cudaError_t launch_median3(cudaStream_t s, const float *in, float *out, int H, int W) {
+    dim3 block(128), grid((W + 127) / 128, H);
+    median3_kernel<<<grid, block, 0, s>>>(in, out, H, W);
+    return cudaGetLastError();
+}
 
 cudaError_t launch_wta(cudaStream_t s, const float *agg, const int *lo, const int *cnt, const long long *off,
                        int N, int G, double dmin, double step, int mode, float tau, int *label, float *disp,

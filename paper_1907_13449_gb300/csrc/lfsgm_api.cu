@@ -591,6 +591,13 @@ lfsgm_status lfsgm_wta_subpixel(lfsgm_handle h, const float *agg, const int32_t 
     });
 }
 
+lfsgm_status lfsgm_median_filter(lfsgm_handle h, const float *disp, float *out) {
+    if (!h) return LFSGM_ERR_INVALID_ARG;
+    if (!disp || !out) return fail(h, LFSGM_ERR_INVALID_ARG, "null buffer");
+    if (disp == out) return fail(h, LFSGM_ERR_INVALID_ARG, "the median filter needs distinct input and output");
+    return run(h, "median_filter", [&] { return launch_median3(h->stream, disp, out, h->cfg.H, h->cfg.W); });
+}
+
 lfsgm_status lfsgm_backward(lfsgm_handle h, const float *views, const float *cost, const int32_t *lo,
                             const int32_t *cnt, const int64_t *off, float P1, float P2, const float *grad_disp,
                             float *grad_cost, float *grad_P1, float *grad_P2, float *grad_views) {

@@ -186,6 +186,7 @@ cudaError_t launch_fine_sgm(cudaStream_t s, const float *cost, const int *lo, co
                             const long long *off, int H, int W, int G, const float *pen, float *agg,
                             int *status, const int *order);
 
+cudaError_t launch_median3(cudaStream_t s, const float *in, float *out, int H, int W);
 cudaError_t launch_wta(cudaStream_t s, const float *agg, const int *lo, const int *cnt,
                        const long long *off, int N, int G, double dmin, double step, int mode,
                        float tau, int *label, float *disp, int *status);

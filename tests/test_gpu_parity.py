@@ -8,7 +8,7 @@ import pytest
 
 import lfsynth
 import oracle
-from lf_helpers import (DISP_TOL, RTOL, best_of, csr_rel_err, gather, label_mismatch,
+from lf_helpers import (DISP_TOL, RTOL, TIE_REL, best_of, csr_rel_err, gather, label_mismatch,
                         pad4_offsets)
 
 pytestmark = pytest.mark.gpu
@@ -319,6 +319,47 @@ def test_depth_end_to_end_integer_planes_exact(gpu_lib):
     ref = oracle.depth(cfg, views)
     g_label, g_disp, _ = _gpu_depth(gpu_lib, p, views)
     _check_end_to_end(g_label, g_disp, ref, p)
+
+
+@pytest.mark.parametrize("shape", [(1, 1), (1, 70), (45, 1), (37, 129), (512, 512)])
+def test_median_filter_bit_exact(gpu_lib, shape):
+    """3 x 3 median (Sec. III-F) of an FP32 map with many ties: the selection is exact."""
+    import torch
+    H, W = shape
+    p = lfsynth.tiny_params(H=H, W=W)
+    rng = np.random.default_rng(H * 1000 + W)
+    d = rng.normal(size=(H, W)).astype(np.float32)
+    d[rng.random((H, W)) < 0.3] = 0.25
+    h = gpu_lib.lfsgm_create(p)
+    out = torch.full((H * W,), float("nan"), dtype=torch.float32, device="cuda")
+    gpu_lib.lfsgm_median_filter(h, _dev(d.reshape(-1)), out)
+    gpu_lib.lfsgm_sync(h)
+    gpu_lib.lfsgm_destroy(h)
+    ref = oracle.median3(d.astype(np.float64)).astype(np.float32)
+    assert np.array_equal(_np(out).reshape(H, W), ref)
+
+
+def test_median_filter_after_depth_matches_oracle(gpu_lib, tiny_case):
+    """The paper's chain ends with the median: compare where the oracle's WTA decisions of the
+    whole 3 x 3 neighbourhood are not near-ties."""
+    import torch
+    views, gt, p, cfg, ref = tiny_case
+    g_label, g_disp, _ = _gpu_depth(gpu_lib, p, views)
+    h = gpu_lib.lfsgm_create(p)
+    out = torch.empty(p.N, dtype=torch.float32, device="cuda")
+    gpu_lib.lfsgm_median_filter(h, _dev(g_disp), out)
+    gpu_lib.lfsgm_sync(h)
+    gpu_lib.lfsgm_destroy(h)
+    o = oracle.median3(ref["disp"].reshape(p.H, p.W))
+    best = best_of(ref["Cs"], ref["off"], ref["cnt"], ref["label"], ref["lo"])
+    bad = (ref["gap"] <= TIE_REL * np.maximum(1.0, np.abs(best))).reshape(p.H, p.W)
+    bad = np.pad(bad, 1, mode="edge")
+    near = np.zeros((p.H, p.W), bool)
+    for dy in range(3):
+        for dx in range(3):
+            near |= bad[dy:dy + p.H, dx:dx + p.W]
+    assert (~near).mean() > 0.9
+    assert np.max(np.abs(_np(out).reshape(p.H, p.W) - o)[~near]) < DISP_TOL
 
 
 def test_depth_host_matches_device(gpu_lib, tiny_case):
