@@ -47,6 +47,7 @@ class LFParams:
     p2_frac: float = 0.5
     subpixel: int = 1
     softmin_tau: float = 0.1
+    paths: int = 8              # SGM directions: 8, or the paper's 16 (Sec. IV-C)
     uc: int = -1
     vc: int = -1
     name: str = ""

@@ -26,7 +26,8 @@ _LIB = os.path.join(_HERE, "_liboracle.so")
 _lock = threading.Lock()
 _lib = None
 
-DIRECTIONS = ((1, 0), (-1, 0), (0, 1), (0, -1), (1, 1), (-1, -1), (1, -1), (-1, 1))
+DIRECTIONS = ((1, 0), (-1, 0), (0, 1), (0, -1), (1, 1), (-1, -1), (1, -1), (-1, 1),
+              (2, 1), (-2, -1), (2, -1), (-2, 1), (1, 2), (-1, -2), (1, -2), (-1, 2))
 
 
 def build(force: bool = False) -> str:
@@ -44,7 +45,8 @@ class Cfg(C.Structure):
                 ("uc", C.c_int32), ("vc", C.c_int32), ("census_w", C.c_int32),
                 ("dmin", C.c_double), ("dmax", C.c_double), ("Lc", C.c_int32),
                 ("init_views", C.c_int32), ("phi", C.c_double), ("fill_passes", C.c_int32),
-                ("G", C.c_int32), ("R", C.c_int32), ("w_l2", C.c_double), ("w_census", C.c_double)]
+                ("G", C.c_int32), ("R", C.c_int32), ("w_l2", C.c_double), ("w_census", C.c_double),
+                ("paths", C.c_int32)]
 
 
 def make_cfg(p) -> Cfg:
@@ -53,7 +55,7 @@ def make_cfg(p) -> Cfg:
     return Cfg(U=p.U, V=p.V, H=p.H, W=p.W, uc=p.uc, vc=p.vc, census_w=p.census_w,
                dmin=p.dmin, dmax=p.dmax, Lc=p.coarse_labels, init_views=p.init_views,
                phi=p.phi, fill_passes=p.fill_passes, G=p.fine_labels, R=p.fine_radius,
-               w_l2=p.w_l2, w_census=p.w_census)
+               w_l2=p.w_l2, w_census=p.w_census, paths=getattr(p, "paths", 8))
 
 
 def _ptr(a, t):
@@ -86,7 +88,7 @@ def lib():
             L.or_sgm_int_path.argtypes = [C.c_int, C.c_int, C.c_int, P(C.c_int64), C.c_int64,
                                           C.c_int64, C.c_int, P(C.c_int64)]
             L.or_sgm_int.argtypes = [C.c_int, C.c_int, C.c_int, P(C.c_int64), C.c_int64, C.c_int64,
-                                     P(C.c_int64)]
+                                     C.c_int, P(C.c_int64)]
             L.or_wta_int.argtypes = [C.c_size_t, C.c_int, P(C.c_int64), P(C.c_int32)]
             L.or_fuse.argtypes = [C.c_size_t, C.c_int, P(C.c_int32), C.c_double, P(C.c_double)]
             L.or_hole_fill.argtypes = [C.c_int, C.c_int, C.c_int, P(C.c_double)]
@@ -105,7 +107,7 @@ def lib():
                                               P(C.c_int64), P(C.c_double), C.c_double, C.c_double,
                                               C.c_int, C.c_int, P(C.c_double)]
             L.or_sgm_bounded.argtypes = [C.c_int, C.c_int, P(C.c_int32), P(C.c_int32), P(C.c_int64),
-                                         P(C.c_double), C.c_double, C.c_double, P(C.c_double)]
+                                         P(C.c_double), C.c_double, C.c_double, C.c_int, P(C.c_double)]
             L.or_wta_subpixel.argtypes = [P(Cfg), C.c_size_t, P(C.c_int32), P(C.c_int32),
                                           P(C.c_int64), P(C.c_double), C.c_int, C.c_double,
                                           P(C.c_int32), P(C.c_double), P(C.c_double)]
@@ -170,10 +172,10 @@ def sgm_int_path(H, W, Cv: np.ndarray, P1: int, P2: int, direction: int) -> np.n
     return out
 
 
-def sgm_int(H, W, Cv: np.ndarray, P1: int, P2: int) -> np.ndarray:
+def sgm_int(H, W, Cv: np.ndarray, P1: int, P2: int, paths: int = 8) -> np.ndarray:
     Cv = np.ascontiguousarray(Cv, dtype=np.int64)
     out = np.zeros_like(Cv)
-    lib().or_sgm_int(H, W, Cv.shape[-1], _ptr(Cv, C.c_int64), P1, P2, _ptr(out, C.c_int64))
+    lib().or_sgm_int(H, W, Cv.shape[-1], _ptr(Cv, C.c_int64), P1, P2, int(paths), _ptr(out, C.c_int64))
     return out
 
 
@@ -251,14 +253,14 @@ def set_threads(n: int) -> int:
     return int(lib().or_set_threads(int(n)))
 
 
-def sgm_bounded(H, W, lo, cnt, off, cost, P1, P2):
+def sgm_bounded(H, W, lo, cnt, off, cost, P1, P2, paths: int = 8):
     lo = np.ascontiguousarray(lo, dtype=np.int32).reshape(-1)
     cnt = np.ascontiguousarray(cnt, dtype=np.int32).reshape(-1)
     off = np.ascontiguousarray(off, dtype=np.int64)
     cost = np.ascontiguousarray(cost, dtype=np.float64)
     out = np.zeros_like(cost)
     lib().or_sgm_bounded(H, W, _ptr(lo, C.c_int32), _ptr(cnt, C.c_int32), _ptr(off, C.c_int64),
-                         _ptr(cost, C.c_double), float(P1), float(P2), _ptr(out, C.c_double))
+                         _ptr(cost, C.c_double), float(P1), float(P2), int(paths), _ptr(out, C.c_double))
     return out
 
 
@@ -296,7 +298,7 @@ def initial_disparity(cfg: Cfg, views: np.ndarray, penalties=None, p1f=0.05, p2f
             P1, P2 = int_penalties(int(ca.sum()), ca.size, p1f, p2f)
         else:
             P1, P2 = penalties[arm]
-        Cs = sgm_int(H, W, ca, P1, P2)
+        Cs = sgm_int(H, W, ca, P1, P2, cfg.paths)
         maps.append(wta_int(Cs))
         pens.append((P1, P2))
         arms.append(arm)
@@ -319,7 +321,7 @@ def depth(cfg: Cfg, views: np.ndarray, fine_penalties=None, p1f=0.05, p2f=0.5, m
         P1, P2 = p1f * mean, p2f * mean
     else:
         P1, P2 = fine_penalties
-    Cs = sgm_bounded(cfg.H, cfg.W, init["lo"], init["cnt"], off, cost, P1, P2)
+    Cs = sgm_bounded(cfg.H, cfg.W, init["lo"], init["cnt"], off, cost, P1, P2, cfg.paths)
     label, disp, gap = wta_subpixel(cfg, init["lo"], init["cnt"], off, Cs, mode, tau)
     out = dict(init)
     out.update(off=off, cost=cost, P1=P1, P2=P2, Cs=Cs, label=label, disp=disp, gap=gap)
@@ -345,7 +347,7 @@ def softargmin_backward(cfg: Cfg, lo, cnt, off, Cs, gd, tau):
     return out
 
 
-def sgm_backward(H, W, lo, cnt, off, cost, P1, P2, gCs):
+def sgm_backward(H, W, lo, cnt, off, cost, P1, P2, gCs, paths: int = 8):
     """(dLoss/dcost, dLoss/dP1, dLoss/dP2) from dLoss/dC_s, one direction at a time."""
     lo = np.ascontiguousarray(lo, dtype=np.int32).reshape(-1)
     cnt = np.ascontiguousarray(cnt, dtype=np.int32).reshape(-1)
@@ -354,7 +356,7 @@ def sgm_backward(H, W, lo, cnt, off, cost, P1, P2, gCs):
     gCs = np.ascontiguousarray(gCs, dtype=np.float64)
     gC = np.zeros_like(cost)
     g1, g2 = C.c_double(0.0), C.c_double(0.0)
-    for r in range(8):
+    for r in range(paths):
         lib().or_sgm_bounded_path_backward(H, W, _ptr(lo, C.c_int32), _ptr(cnt, C.c_int32), _ptr(off, C.c_int64),
                                            _ptr(cost, C.c_double), float(P1), float(P2), r, _ptr(gCs, C.c_double),
                                            _ptr(gC, C.c_double), C.byref(g1), C.byref(g2))
@@ -376,16 +378,16 @@ def cost_backward_views(cfg: Cfg, views, lo, cnt, off, gcost):
 def loss_from_cost(cfg: Cfg, lo, cnt, cost, P1, P2, gd, tau):
     """Loss = sum_p gd(p) dhat(p) with dhat the soft-argmin of the SGM-aggregated cost."""
     off = offsets(cnt)
-    Cs = sgm_bounded(cfg.H, cfg.W, lo, cnt, off, cost, P1, P2)
+    Cs = sgm_bounded(cfg.H, cfg.W, lo, cnt, off, cost, P1, P2, cfg.paths)
     return float(np.dot(np.asarray(gd, np.float64).reshape(-1), softargmin(cfg, lo, cnt, off, Cs, tau)))
 
 
 def backward(cfg: Cfg, views, lo, cnt, cost, P1, P2, gd, tau):
     """All gradients of Loss = sum_p gd(p) dhat(p): (dcost, dP1, dP2, dviews)."""
     off = offsets(cnt)
-    Cs = sgm_bounded(cfg.H, cfg.W, lo, cnt, off, cost, P1, P2)
+    Cs = sgm_bounded(cfg.H, cfg.W, lo, cnt, off, cost, P1, P2, cfg.paths)
     gCs = softargmin_backward(cfg, lo, cnt, off, Cs, gd, tau)
-    gC, g1, g2 = sgm_backward(cfg.H, cfg.W, lo, cnt, off, cost, P1, P2, gCs)
+    gC, g1, g2 = sgm_backward(cfg.H, cfg.W, lo, cnt, off, cost, P1, P2, gCs, cfg.paths)
     gV = cost_backward_views(cfg, views, lo, cnt, off, gC)
     return gC, g1, g2, gV
 

@@ -49,6 +49,7 @@ typedef struct {
     int32_t G;            /* fine labels on [dmin,dmax], inclusive                    */
     int32_t R;            /* border threshold lambda in fine labels (Eq. 11)           */
     double w_l2, w_census;/* weights of Eq. 12 (l2) and Eq. 15 (census) terms          */
+    int32_t paths;        /* SGM directions: 8, or the paper's 16 (Sec. IV-C)           */
 } or_cfg;
 
 static int clampi(int v, int lo, int hi) { return v < lo ? lo : (v > hi ? hi : v); }
@@ -188,8 +189,10 @@ void or_int_penalties(int64_t sum, int64_t count, double p1f, double p2f, int64_
 }
 
 /* --------------------------------------------------------------- SGM (Eq. 8-9)
- * The 8 directions r = (dx,dy); the predecessor of p is p - r. */
-static const int DIRS[8][2] = {{1, 0}, {-1, 0}, {0, 1}, {0, -1}, {1, 1}, {-1, -1}, {1, -1}, {-1, 1}};
+ * The directions r = (dx,dy); the predecessor of p is p - r.  The first 8 are the horizontal,
+ * vertical and diagonal ones; the paper's 16 (Sec. IV-C) add the eight of slopes 1/2 and 2. */
+static const int DIRS[16][2] = {{1, 0}, {-1, 0}, {0, 1}, {0, -1}, {1, 1}, {-1, -1}, {1, -1}, {-1, 1},
+                                {2, 1}, {-2, -1}, {2, -1}, {-2, 1}, {1, 2}, {-1, -2}, {1, -2}, {-1, 2}};
 
 /* Visit order for direction r: rows and columns are walked so that p - r is always
  * visited before p. */
@@ -229,7 +232,8 @@ static void sgm_int_step(int H, int W, int L, const int64_t *C, int64_t P1, int6
  *   L(p,d) = C(p,d) + (min(L'(d), L'(d-1)+P1, L'(d+1)+P1, m+P2) - m)
  * with L'(.) = L(p-r,.) and L(p,.) = C(p,.) where p-r is outside the image.
  * Pixels whose predecessors are already final are processed in parallel: whole rows
- * for horizontal paths, the pixels of one row otherwise. */
+ * for horizontal paths, the pixels of one row otherwise (every other direction has
+ * dy != 0, so p - r lies in an earlier row). */
 void or_sgm_int_path(int H, int W, int L, const int64_t *C, int64_t P1, int64_t P2, int dir, int64_t *Lr)
 {
     int dx = DIRS[dir][0], dy = DIRS[dir][1];
@@ -247,13 +251,13 @@ void or_sgm_int_path(int H, int W, int L, const int64_t *C, int64_t P1, int64_t 
     }
 }
 
-/* Sum over the 8 directions (Eq. 9). */
-void or_sgm_int(int H, int W, int L, const int64_t *C, int64_t P1, int64_t P2, int64_t *Cs)
+/* Sum over the 8 or 16 directions (Eq. 9). */
+void or_sgm_int(int H, int W, int L, const int64_t *C, int64_t P1, int64_t P2, int paths, int64_t *Cs)
 {
     size_t n = (size_t)H * W * L;
     int64_t *Lr = (int64_t *)malloc(n * sizeof(int64_t));
     memset(Cs, 0, n * sizeof(int64_t));
-    for (int r = 0; r < 8; r++) {
+    for (int r = 0; r < paths; r++) {
         or_sgm_int_path(H, W, L, C, P1, P2, r, Lr);
 #pragma omp parallel for schedule(static)
         for (size_t i = 0; i < n; i++) Cs[i] += Lr[i];
@@ -443,21 +447,25 @@ void or_sgm_bounded_path(int H, int W, const int32_t *lo, const int32_t *cnt, co
     }
 }
 
-/* C_s = sum over the 8 directions (Eq. 9), added as a balanced tree
- * ((L0+L1)+(L2+L3)) + ((L4+L5)+(L6+L7)). */
+/* C_s = sum over the 8 or 16 directions (Eq. 9), added as a balanced tree
+ * ((L0+L1)+(L2+L3)) + ((L4+L5)+(L6+L7)) per group of 8, and the two groups' sums added. */
 void or_sgm_bounded(int H, int W, const int32_t *lo, const int32_t *cnt, const int64_t *off,
-                    const double *C, double P1, double P2, double *Cs)
+                    const double *C, double P1, double P2, int paths, double *Cs)
 {
     size_t N = (size_t)H * W;
     size_t nnz = (size_t)off[N];
-    double *Lr[8];
-    for (int r = 0; r < 8; r++) {
+    double *Lr[16];
+    for (int r = 0; r < paths; r++) {
         Lr[r] = (double *)malloc(nnz * sizeof(double));
         or_sgm_bounded_path(H, W, lo, cnt, off, C, P1, P2, r, 1, Lr[r]);
     }
-    for (size_t i = 0; i < nnz; i++)
-        Cs[i] = ((Lr[0][i] + Lr[1][i]) + (Lr[2][i] + Lr[3][i])) + ((Lr[4][i] + Lr[5][i]) + (Lr[6][i] + Lr[7][i]));
-    for (int r = 0; r < 8; r++) free(Lr[r]);
+    for (size_t i = 0; i < nnz; i++) {
+        double t = ((Lr[0][i] + Lr[1][i]) + (Lr[2][i] + Lr[3][i])) + ((Lr[4][i] + Lr[5][i]) + (Lr[6][i] + Lr[7][i]));
+        if (paths == 16)
+            t += ((Lr[8][i] + Lr[9][i]) + (Lr[10][i] + Lr[11][i])) + ((Lr[12][i] + Lr[13][i]) + (Lr[14][i] + Lr[15][i]));
+        Cs[i] = t;
+    }
+    for (int r = 0; r < paths; r++) free(Lr[r]);
 }
 
 /* ----------------------------------- WTA (Eq. 10) and sub-pixel refinement (Eq. 13)

@@ -14,10 +14,10 @@ import oracle
 TAU = 0.1
 
 
-@pytest.fixture(scope="module")
-def case():
+@pytest.fixture(scope="module", params=[8, 16], ids=["8paths", "16paths"])
+def case(request):
     p = lfsynth.LFParams(U=7, V=7, H=32, W=32, census_w=5, dmin=-1.0, dmax=1.0, coarse_labels=9,
-                         fine_labels=41, fine_radius=8, w_l2=1.0, w_census=1.0 / 24)
+                         fine_labels=41, fine_radius=8, w_l2=1.0, w_census=1.0 / 24, paths=request.param)
     cfg = oracle.make_cfg(p)
     rng = np.random.default_rng(2024)
     views = rng.uniform(0.0, 1.0, (7, 7, 32, 32))
@@ -93,14 +93,14 @@ def test_grad_views_match_finite_differences(case):
 def test_softargmin_gradient_sums_to_zero_per_pixel(case):
     """Adding a constant to a pixel's aggregated costs leaves its softmax unchanged."""
     p, cfg, views, lo, cnt, off, cost, P1, P2, gd, _ = case
-    Cs = oracle.sgm_bounded(p.H, p.W, lo, cnt, off, cost, P1, P2)
+    Cs = oracle.sgm_bounded(p.H, p.W, lo, cnt, off, cost, P1, P2, p.paths)
     gCs = oracle.softargmin_backward(cfg, lo, cnt, off, Cs, gd, TAU)
     assert np.allclose(gCs.reshape(p.N, 16).sum(1), 0.0, atol=1e-12)
 
 
 def test_sgm_cost_gradient_sums_to_zero_per_pixel(case):
     """A constant added to all of a pixel's costs shifts L_r at that pixel only (the
-    normalised recurrence removes it downstream), so C_s(p) shifts by 8 times the constant
+    normalised recurrence removes it downstream), so C_s(p) shifts by (paths) times the constant
     and every soft-argmin is unchanged: the per-pixel sums of dLoss/dcost vanish."""
     p, cfg, views, lo, cnt, off, cost, P1, P2, gd, (gC, g1, g2, gV) = case
     assert np.allclose(gC.reshape(p.N, 16).sum(1), 0.0, atol=1e-10)

@@ -176,7 +176,7 @@ def _path_pixels(H, W, x, y, dx, dy):
     return seq[::-1]
 
 
-@pytest.mark.parametrize("direction", range(8))
+@pytest.mark.parametrize("direction", range(16))
 def test_sgm_bounded_brute_force_path_energy(direction):
     """min over labels of the printed (unnormalised) Eq. 8 at the end of a path equals
     the minimum over all label sequences along the path of sum C + sum V, V = 0/P1/P2
@@ -206,7 +206,7 @@ def test_sgm_bounded_brute_force_path_energy(direction):
                 assert abs(L[off[p] + g - lo[p]] - e) < 1e-12
 
 
-@pytest.mark.parametrize("direction", [0, 3, 4, 7])
+@pytest.mark.parametrize("direction", [0, 3, 4, 7, 8, 11, 12, 15])
 def test_sgm_int_brute_force_path_energy(direction):
     rng = np.random.default_rng(30 + direction)
     H, W, Lb = 3, 4, 3
@@ -237,7 +237,7 @@ def test_sgm_normalised_is_shifted_unnormalised():
     cnt = rng.integers(1, 6, H * W).astype(np.int32)
     off = oracle.offsets(cnt)
     cost = rng.uniform(0, 5, int(off[-1]))
-    for r in range(8):
+    for r in range(16):
         a = oracle.sgm_bounded_path(H, W, lo, cnt, off, cost, 0.5, 2.0, r, True)
         b = oracle.sgm_bounded_path(H, W, lo, cnt, off, cost, 0.5, 2.0, r, False)
         for p in range(H * W):
@@ -258,8 +258,10 @@ def test_sgm_zero_penalties_gives_eight_times_cost_exactly():
     cost = rng.uniform(0, 40, int(off[-1]))
     Cs = oracle.sgm_bounded(H, W, lo, cnt, off, cost, 0.0, 0.0)
     assert np.array_equal(Cs, 8.0 * cost)
+    assert np.array_equal(oracle.sgm_bounded(H, W, lo, cnt, off, cost, 0.0, 0.0, paths=16), 16.0 * cost)
     Ci = rng.integers(0, 200, (H * W, 11)).astype(np.int64)
     assert np.array_equal(oracle.sgm_int(H, W, Ci, 0, 0), 8 * Ci)
+    assert np.array_equal(oracle.sgm_int(H, W, Ci, 0, 0, paths=16), 16 * Ci)
 
 
 def test_sgm_full_window_matches_int_version():
@@ -271,9 +273,10 @@ def test_sgm_full_window_matches_int_version():
     lo = np.zeros(H * W, np.int32)
     cnt = np.full(H * W, Lb, np.int32)
     off = oracle.offsets(cnt)
-    a = oracle.sgm_int(H, W, Ci, 3, 11)
-    b = oracle.sgm_bounded(H, W, lo, cnt, off, Ci.reshape(-1).astype(np.float64), 3.0, 11.0)
-    assert np.array_equal(a.reshape(-1).astype(np.float64), b)
+    for paths in (8, 16):
+        a = oracle.sgm_int(H, W, Ci, 3, 11, paths)
+        b = oracle.sgm_bounded(H, W, lo, cnt, off, Ci.reshape(-1).astype(np.float64), 3.0, 11.0, paths)
+        assert np.array_equal(a.reshape(-1).astype(np.float64), b)
 
 
 # ------------------------------------------------------------- WTA + subpixel
