@@ -67,6 +67,8 @@ typedef struct {
     double  p1_frac, p2_frac;  /* derived penalties: P = frac * mean cost                   */
     int32_t subpixel;          /* 0 none, 1 parabola (Eq. 13), 2 soft-argmin                */
     float   softmin_tau;       /* soft-argmin temperature                                   */
+    int32_t paths;             /* SGM directions: 8, or the paper's 16 (Sec. IV-C) adding the
+                                  slopes 1/2 and 2; 0 is read as 8                            */
 } lfsgm_config;
 
 /* Create a handle for one light-field shape.  `stream` is a cudaStream_t (NULL = the

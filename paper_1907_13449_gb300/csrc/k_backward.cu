@@ -69,15 +69,13 @@ __global__ void __launch_bounds__(32 * kBwdWarps) sgm_backward_kernel(
     extern __shared__ float sm[];
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
     const int gw = blockIdx.x * kBwdWarps + wib;
-    if (gw >= st.cum[8]) return;
+    if (gw >= st.cum[st.paths]) return;
     const int rs = __ldg(order + gw);            // longest scanlines first
-    const int r = rs & 7, s = rs >> 3;
+    const int r = rs & 15, s = rs >> 4;
     const int dx = dir_dx(r), dy = dir_dy(r);
     int x0, y0;
     scan_start(r, s, H, W, x0, y0);
-    const int lx = dx > 0 ? W - x0 : (dx < 0 ? x0 + 1 : 0x7fffffff);
-    const int ly = dy > 0 ? H - y0 : (dy < 0 ? y0 + 1 : 0x7fffffff);
-    const int len = min(lx, ly);
+    const int len = scan_steps(x0, y0, dx, dy, H, W);
     unsigned char *code = codes + (size_t)r * nnz_cap;
     int *am = amin + (size_t)r * H * W;
     float *bufA = sm + (size_t)wib * 4 * Gs;   // forward: predecessor's L;  reverse: incoming adjoint of p
@@ -480,11 +478,11 @@ cudaError_t launch_softargmin_backward(cudaStream_t s, const float *agg, const i
 
 cudaError_t launch_sgm_backward(cudaStream_t s, const float *cost, const int *lo, const int *cnt, const long long *off,
                                 int H, int W, int G, float P1, float P2, const float *gCs, unsigned char *codes,
-                                int *amin, size_t nnz_cap, float *gcost, float *gP, int *status, const int *order) {
-    const ScanTable st = make_scan_table(H, W);
+                                int *amin, size_t nnz_cap, float *gcost, float *gP, int *status, const int *order, int paths) {
+    const ScanTable st = make_scan_table(H, W, paths);
     const int Gs = (G + 31) & ~31;
     const size_t smem = (size_t)kBwdWarps * 4 * Gs * sizeof(float);   // bufA, bufB, lambda, codes per warp
-    const unsigned grid = (unsigned)((st.cum[8] + kBwdWarps - 1) / kBwdWarps);
+    const unsigned grid = (unsigned)((st.cum[paths] + kBwdWarps - 1) / kBwdWarps);
     if (smem > 48 * 1024) {
         const cudaError_t e = cudaFuncSetAttribute(sgm_backward_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                                    (int)smem);

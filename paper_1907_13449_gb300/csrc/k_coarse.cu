@@ -208,20 +208,16 @@ __global__ void __launch_bounds__(128) coarse_sgm_kernel(const uint16_t *__restr
     constexpr uint32_t SENT = 0x7fff7fffu;
     const int lane = threadIdx.x & 31;
     const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int per_arm = st.cum[8];
+    const int per_arm = st.cum[st.paths];
     if (gw >= per_arm * narms) return;
     const int arm = gw / per_arm;
     const int w = gw - arm * per_arm;
     const int rs = __ldg(order + w);             // longest scanlines first (within the arm)
-    const int r = rs & 7, s = rs >> 3;
+    const int r = rs & 15, s = rs >> 4;
     const int dx = dir_dx(r), dy = dir_dy(r);
     int x, y;
     scan_start(r, s, H, W, x, y);
-    int steps = 1 << 30;
-    if (dx > 0) steps = min(steps, W - x);
-    if (dx < 0) steps = min(steps, x + 1);
-    if (dy > 0) steps = min(steps, H - y);
-    if (dy < 0) steps = min(steps, y + 1);
+    const int steps = scan_steps(x, y, dx, dy, H, W);
     const size_t N = (size_t)H * W;
     const int k0 = lane * LPT;
     const bool act = k0 < Lcd;
@@ -354,10 +350,10 @@ cudaError_t launch_coarse_penalties(cudaStream_t s, const unsigned long long *su
 }
 
 cudaError_t launch_coarse_sgm(cudaStream_t s, const uint16_t *cost, int narms, int H, int W, int Lc,
-                              const int *pen, uint16_t *sum, const int *order) {
-    const ScanTable st = make_scan_table(H, W);
+                              const int *pen, uint16_t *sum, const int *order, int paths) {
+    const ScanTable st = make_scan_table(H, W, paths);
     const int Lcd = coarse_stride(Lc);
-    const long long warps = (long long)st.cum[8] * narms;
+    const long long warps = (long long)st.cum[paths] * narms;
     const int block = 128;
     const unsigned grid = (unsigned)((warps * 32 + block - 1) / block);
     switch (coarse_lpt(Lc)) {

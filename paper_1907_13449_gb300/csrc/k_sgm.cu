@@ -43,15 +43,13 @@ __global__ void __launch_bounds__(32 * kSgmWarps) fine_sgm_kernel(const float *_
     extern __shared__ float sm[];
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
     const int gw = blockIdx.x * kSgmWarps + wib;
-    if (gw >= st.cum[8]) return;
+    if (gw >= st.cum[st.paths]) return;
     const int rs = __ldg(order + gw);            // longest scanlines first
-    const int r = rs & 7, s = rs >> 3;
+    const int r = rs & 15, s = rs >> 4;
     const int dx = dir_dx(r), dy = dir_dy(r);
     int x0, y0;
     scan_start(r, s, H, W, x0, y0);
-    const int lx = dx > 0 ? W - x0 : (dx < 0 ? x0 + 1 : 0x7fffffff);
-    const int ly = dy > 0 ? H - y0 : (dy < 0 ? y0 + 1 : 0x7fffffff);
-    const int len = min(lx, ly);
+    const int len = scan_steps(x0, y0, dx, dy, H, W);
     float *bufA = sm + (size_t)wib * 2 * Gs;   // predecessor's path costs (by slot), general steps
     float *bufB = bufA + Gs;                   // this pixel's
     const float P1 = __ldg(pen), P2 = __ldg(pen + 1);
@@ -266,22 +264,22 @@ cudaError_t launch_fine_penalties(cudaStream_t s, const double *partial, int nbl
     return cudaGetLastError();
 }
 
-void build_scan_order(int H, int W, std::vector<int> &order) {
+void build_scan_order(int H, int W, int paths, std::vector<int> &order) {
     order.clear();
-    for (int r = 0; r < 8; r++)
-        for (int s = 0; s < n_scanlines(r, H, W); s++) order.push_back((s << 3) | r);
+    for (int r = 0; r < paths; r++)
+        for (int s = 0; s < n_scanlines(r, H, W); s++) order.push_back((s << 4) | r);
     std::stable_sort(order.begin(), order.end(), [&](int a, int b) {
-        return scan_len(a & 7, a >> 3, H, W) > scan_len(b & 7, b >> 3, H, W);
+        return scan_len(a & 15, a >> 4, H, W) > scan_len(b & 15, b >> 4, H, W);
     });
 }
 
 cudaError_t launch_fine_sgm(cudaStream_t s, const float *cost, const int *lo, const int *cnt,
                             const long long *off, int H, int W, int G, const float *pen, float *agg,
-                            int *status, const int *order) {
-    const ScanTable st = make_scan_table(H, W);
+                            int *status, const int *order, int paths) {
+    const ScanTable st = make_scan_table(H, W, paths);
     const int Gs = (G + 31) & ~31;
     const size_t smem = (size_t)kSgmWarps * 2 * Gs * sizeof(float);
-    const unsigned grid = (unsigned)((st.cum[8] + kSgmWarps - 1) / kSgmWarps);
+    const unsigned grid = (unsigned)((st.cum[paths] + kSgmWarps - 1) / kSgmWarps);
     if (smem > 48 * 1024) {
         cudaError_t e = cudaFuncSetAttribute(fine_sgm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              (int)smem);

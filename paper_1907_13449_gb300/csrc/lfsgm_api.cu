@@ -172,6 +172,7 @@ lfsgm_status validate(const lfsgm_config &c, char *why, size_t n) {
     if (!(c.p1_frac >= 0.0) || !(c.p2_frac >= c.p1_frac)) BAD("need 0 <= p1_frac <= p2_frac");
     if (c.subpixel < 0 || c.subpixel > 2) BAD("subpixel must be 0, 1 or 2");
     if (!(c.softmin_tau > 0.f)) BAD("softmin_tau must be > 0");
+    if (c.paths != 0 && c.paths != 8 && c.paths != 16) BAD("paths must be 8 or 16");
     const double md = std::fmax(std::fabs(c.dmin), std::fabs(c.dmax));
     if (md * (std::max(c.U, c.V)) > 30000.0) BAD("shifts exceed the 16-bit table range");
     return LFSGM_OK;
@@ -268,6 +269,7 @@ lfsgm_status lfsgm_create(const lfsgm_config *cfg, void *stream, lfsgm_handle *o
     if (!cfg || !out) return LFSGM_ERR_INVALID_ARG;
     *out = nullptr;
     lfsgm_config c = *cfg;
+    if (c.paths == 0) c.paths = 8;
     if (c.uc < 0) c.uc = (c.U - 1) / 2;
     if (c.vc < 0) c.vc = (c.V - 1) / 2;
     char why[256];
@@ -288,7 +290,7 @@ lfsgm_status lfsgm_create(const lfsgm_config *cfg, void *stream, lfsgm_handle *o
     // the packed coarse sums hold 8 paths x (C + P2) per 16-bit half
     const long long cmax = (long long)max_arm_views(h) * h->nbits;
     const long long p2max = (long long)std::floor(c.p2_frac * (double)cmax + 0.5);
-    if (8 * (cmax + std::max(p2max, 1LL)) >= 65536) {
+    if ((long long)c.paths * (cmax + std::max(p2max, 1LL)) >= 65536) {
         g_create_err = "coarse path sums would overflow 16 bits (too many arm views x census bits)";
         delete h;
         return LFSGM_ERR_UNSUPPORTED;
@@ -351,7 +353,7 @@ lfsgm_status lfsgm_create(const lfsgm_config *cfg, void *stream, lfsgm_handle *o
     ALLOC_COPY(h->d_fine, fine);
     {
         std::vector<int> order;
-        build_scan_order(c.H, c.W, order);
+        build_scan_order(c.H, c.W, c.paths, order);
         ALLOC_COPY(h->d_order, order);
     }
     {
@@ -467,7 +469,7 @@ lfsgm_status lfsgm_initial_disparity(lfsgm_handle h, const float *views, int32_t
                                        Pc1, Pc2, h->cpen);
     }));
     LFSGM_TRY(run(h, "coarse_sgm", [&] {
-        return launch_coarse_sgm(s, h->ccost, A, c.H, c.W, c.coarse_labels, h->cpen, h->csum, h->d_order);
+        return launch_coarse_sgm(s, h->ccost, A, c.H, c.W, c.coarse_labels, h->cpen, h->csum, h->d_order, c.paths);
     }));
     LFSGM_TRY(run(h, "coarse_wta", [&] {
         return launch_coarse_wta(s, h->csum, A, N, c.coarse_labels, h->maps, maps);
@@ -573,7 +575,8 @@ lfsgm_status lfsgm_sgm_aggregate(lfsgm_handle h, const float *cost, const int32_
         return cudaGetLastError();
     }));
     LFSGM_TRY(run(h, "fine_sgm", [&] {
-        return launch_fine_sgm(s, cost, lo, cnt, o, c.H, c.W, c.fine_labels, h->fpen, agg, h->status, h->d_order);
+        return launch_fine_sgm(s, cost, lo, cnt, o, c.H, c.W, c.fine_labels, h->fpen, agg, h->status, h->d_order,
+                               c.paths);
     }));
     return LFSGM_OK;
 }
@@ -615,8 +618,8 @@ lfsgm_status lfsgm_backward(lfsgm_handle h, const float *views, const float *cos
     if (!h->b_agg) {
         cudaError_t e = cudaMalloc((void **)&h->b_agg, (size_t)cap * 4);
         if (e == cudaSuccess) e = cudaMalloc((void **)&h->b_gcs, (size_t)cap * 4);
-        if (e == cudaSuccess) e = cudaMalloc((void **)&h->b_codes, (size_t)cap * 8);
-        if (e == cudaSuccess) e = cudaMalloc((void **)&h->b_amin, N * 8 * 4);
+        if (e == cudaSuccess) e = cudaMalloc((void **)&h->b_codes, (size_t)cap * c.paths);
+        if (e == cudaSuccess) e = cudaMalloc((void **)&h->b_amin, N * (size_t)c.paths * 4);
         if (e == cudaSuccess) e = cudaMalloc((void **)&h->b_gp, 2 * 4);
         if (e != cudaSuccess) return fail(h, LFSGM_ERR_NO_MEMORY, "backward scratch: %s", cudaGetErrorString(e));
     }
@@ -633,7 +636,7 @@ lfsgm_status lfsgm_backward(lfsgm_handle h, const float *views, const float *cos
     if (e != cudaSuccess) return cuda_fail(h, e, "memset");
     LFSGM_TRY(run(h, "sgm_backward", [&] {
         return launch_sgm_backward(s, cost, lo, cnt, o, c.H, c.W, c.fine_labels, P1, P2, h->b_gcs, h->b_codes,
-                                   h->b_amin, (size_t)cap, grad_cost, h->b_gp, h->status, h->d_order);
+                                   h->b_amin, (size_t)cap, grad_cost, h->b_gp, h->status, h->d_order, c.paths);
     }));
     if (grad_views) {
         // the (pixel, 32-label chunk) items of windows wider than 32 labels; narrower ones by tiles

@@ -41,66 +41,74 @@ __device__ __forceinline__ FineTap load_tap(const FineTap *t) {
 }
 #endif
 
-// The 8 SGM directions r = (dx, dy); the predecessor of p is p - r.  Same order as the
-// paper-side description: (1,0) (-1,0) (0,1) (0,-1) (1,1) (-1,-1) (1,-1) (-1,1).
+// The SGM directions r = (dx, dy); the predecessor of p is p - r.  Same order as the oracle:
+// (1,0) (-1,0) (0,1) (0,-1) (1,1) (-1,-1) (1,-1) (-1,1), then the paper's other eight of its 16
+// (Sec. IV-C), of slopes 1/2 and 2: (2,1) (-2,-1) (2,-1) (-2,1) (1,2) (-1,-2) (1,-2) (-1,2).
+constexpr int kMaxPaths = 16;
 __host__ __device__ inline int dir_dx(int r) {
-    const int t[8] = {1, -1, 0, 0, 1, -1, 1, -1};
+    const int t[16] = {1, -1, 0, 0, 1, -1, 1, -1, 2, -2, 2, -2, 1, -1, 1, -1};
     return t[r];
 }
 __host__ __device__ inline int dir_dy(int r) {
-    const int t[8] = {0, 0, 1, -1, 1, -1, -1, 1};
+    const int t[16] = {0, 0, 1, -1, 1, -1, -1, 1, 1, -1, -1, 1, 2, -2, -2, 2};
     return t[r];
 }
-// Number of scanlines of direction r (paths start where p - r leaves the image).
+// Scanlines of direction r start at the pixels p whose p - r leaves the image: the first
+// by = min(|dy|, H) rows on the side p - r leaves through (all W columns), then the first
+// bx = min(|dx|, W) columns on the other side, without those rows.  Every pixel lies on
+// exactly one scanline (walk back from it until p - r leaves the image).
 __host__ __device__ inline int n_scanlines(int r, int H, int W) {
-    int dx = dir_dx(r), dy = dir_dy(r);
-    if (dy == 0) return H;
-    if (dx == 0) return W;
-    return W + H - 1;
+    const int ax = abs(dir_dx(r)), ay = abs(dir_dy(r));
+    const int bx = ax < W ? ax : W, by = ay < H ? ay : H;
+    return by * W + bx * (H - by);
 }
 // Start pixel of scanline s of direction r.
 __host__ __device__ inline void scan_start(int r, int s, int H, int W, int &x, int &y) {
-    int dx = dir_dx(r), dy = dir_dy(r);
-    if (dy == 0) {
-        y = s;
-        x = dx > 0 ? 0 : W - 1;
-    } else if (dx == 0) {
-        x = s;
-        y = dy > 0 ? 0 : H - 1;
-    } else if (s < W) {
-        x = s;
-        y = dy > 0 ? 0 : H - 1;
-    } else {
-        int i = s - W + 1;
+    const int dx = dir_dx(r), dy = dir_dy(r), ax = abs(dx), ay = abs(dy);
+    const int by = ay < H ? ay : H;
+    if (s < by * W) {
+        const int i = s / W;
+        x = s - i * W;
         y = dy > 0 ? i : H - 1 - i;
-        x = dx > 0 ? 0 : W - 1;
+    } else {
+        const int t = s - by * W, rows = H - by;
+        const int j = t / rows;
+        const int k = t - j * rows;
+        x = dx > 0 ? j : W - 1 - j;
+        y = dy > 0 ? by + k : (dy < 0 ? H - 1 - by - k : k);
     }
+    (void)ax;
 }
 
-// Cumulative scanline counts of the 8 directions (plus total) for one image shape.
+// Cumulative scanline counts of the first `paths` directions (cum[paths] = total).
 struct ScanTable {
-    int cum[9];
+    int cum[kMaxPaths + 1];
+    int paths;
 };
-inline ScanTable make_scan_table(int H, int W) {
+inline ScanTable make_scan_table(int H, int W, int paths) {
     ScanTable t;
+    t.paths = paths;
     t.cum[0] = 0;
-    for (int r = 0; r < 8; r++) t.cum[r + 1] = t.cum[r] + n_scanlines(r, H, W);
+    for (int r = 0; r < kMaxPaths; r++) t.cum[r + 1] = t.cum[r] + (r < paths ? n_scanlines(r, H, W) : 0);
     return t;
 }
 
+// Steps of the scanline starting at (x0, y0) in direction (dx, dy).
+__host__ __device__ inline int scan_steps(int x0, int y0, int dx, int dy, int H, int W) {
+    const int lx = dx > 0 ? (W - 1 - x0) / dx + 1 : (dx < 0 ? x0 / (-dx) + 1 : 0x7fffffff);
+    const int ly = dy > 0 ? (H - 1 - y0) / dy + 1 : (dy < 0 ? y0 / (-dy) + 1 : 0x7fffffff);
+    return lx < ly ? lx : ly;
+}
 // Length of scanline s of direction r.
 __host__ __device__ inline int scan_len(int r, int s, int H, int W) {
     int x, y;
     scan_start(r, s, H, W, x, y);
-    const int dx = dir_dx(r), dy = dir_dy(r);
-    const int lx = dx > 0 ? W - x : (dx < 0 ? x + 1 : 0x7fffffff);
-    const int ly = dy > 0 ? H - y : (dy < 0 ? y + 1 : 0x7fffffff);
-    return lx < ly ? lx : ly;
+    return scan_steps(x, y, dir_dx(r), dir_dy(r), H, W);
 }
-// Every (direction r, scanline s) as (s << 3 | r), longest scanline first (ties: r, then s): the
-// SGM kernels take warps in this order, so the short diagonals fill in behind the long lines
+// Every (direction r < paths, scanline s) as (s << 4 | r), longest scanline first (ties: r, then
+// s): the SGM kernels take warps in this order, so the short lines fill in behind the long ones
 // instead of forming a tail.
-void build_scan_order(int H, int W, std::vector<int> &order);
+void build_scan_order(int H, int W, int paths, std::vector<int> &order);
 
 constexpr int kMaxArmViews = 64;
 
@@ -132,7 +140,7 @@ cudaError_t launch_coarse_penalties(cudaStream_t s, const unsigned long long *su
                                     long long count, double p1f, double p2f, int P1, int P2,
                                     int *pen);
 cudaError_t launch_coarse_sgm(cudaStream_t s, const uint16_t *cost, int narms, int H, int W, int Lc,
-                              const int *pen, uint16_t *sum, const int *order);
+                              const int *pen, uint16_t *sum, const int *order, int paths);
 cudaError_t launch_coarse_wta(cudaStream_t s, const uint16_t *sum, int narms, int N, int Lc, int *maps,
                               int *maps_out);
 
@@ -184,7 +192,7 @@ cudaError_t launch_fine_penalties(cudaStream_t s, const double *partial, int nbl
                                   double p1f, double p2f, float *pen);
 cudaError_t launch_fine_sgm(cudaStream_t s, const float *cost, const int *lo, const int *cnt,
                             const long long *off, int H, int W, int G, const float *pen, float *agg,
-                            int *status, const int *order);
+                            int *status, const int *order, int paths);
 
 cudaError_t launch_median3(cudaStream_t s, const float *in, float *out, int H, int W);
 cudaError_t launch_wta(cudaStream_t s, const float *agg, const int *lo, const int *cnt,
@@ -197,7 +205,7 @@ cudaError_t launch_softargmin_backward(cudaStream_t s, const float *agg, const i
 cudaError_t launch_sgm_backward(cudaStream_t s, const float *cost, const int *lo, const int *cnt,
                                 const long long *off, int H, int W, int G, float P1, float P2, const float *gCs,
                                 unsigned char *codes, int *amin, size_t nnz_cap, float *gcost, float *gP,
-                                int *status, const int *order);
+                                int *status, const int *order, int paths);
 cudaError_t launch_views_backward(cudaStream_t s, const float *views, const FineTap *tab, int G, int nviews,
                                   int H, int W, int ref, const int *lo, const int *cnt, const long long *off,
                                   float wl2, const float *gcost, float *gviews, const int2 *list, const int *count);

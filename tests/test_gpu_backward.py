@@ -89,10 +89,14 @@ def _ragged_case(kind, seed=77):
     return p, views, lo, cnt, gd
 
 
-@pytest.mark.parametrize("kind", ["mixed", "wide_range"])
+@pytest.mark.parametrize("kind", ["mixed", "wide_range", "mixed_16_paths"])
 def test_backward_ragged_windows_match_oracle(gpu_lib, kind):
+    import dataclasses
+
     import torch
-    p, views, lo, cnt, gd = _ragged_case(kind)
+    p, views, lo, cnt, gd = _ragged_case(kind.replace("_16_paths", ""))
+    if kind.endswith("16_paths"):
+        p = dataclasses.replace(p, paths=16)
     cfg = oracle.make_cfg(p)
     off_o, cost_o = oracle.cost_volume(cfg, views, lo, cnt)
     P1, P2 = np.float32(0.05 * cost_o.mean()), np.float32(0.5 * cost_o.mean())

@@ -3,6 +3,8 @@
 Bars: census/Hamming, coarse maps, windows and labels bit-exact (labels: except where the
 oracle's own decision is a near-tie, gap <= 1e-5 * scale); l2 and aggregated costs within
 1e-5 relative to the per-pixel scale; sub-pixel disparity within 1e-3 px."""
+import dataclasses
+
 import numpy as np
 import pytest
 
@@ -72,7 +74,7 @@ def test_initial_disparity_tiny_bitexact(gpu_lib, tiny_case):
 
 
 @pytest.mark.parametrize("variant", ["explicit_pen", "paper_4_views", "census7_odd_shape", "one_pass",
-                                     "row_lf", "max_coarse_labels", "two_coarse_labels"])
+                                     "row_lf", "max_coarse_labels", "two_coarse_labels", "paths16"])
 def test_initial_disparity_variants(gpu_lib, variant):
     Pc = (0, 0)
     if variant == "explicit_pen":
@@ -89,6 +91,8 @@ def test_initial_disparity_variants(gpu_lib, variant):
         views, _, p = lfsynth.tiny(params=lfsynth.tiny_params(coarse_labels=256))
     elif variant == "two_coarse_labels":   # the smallest grid: the label step is the whole range
         views, _, p = lfsynth.tiny(params=lfsynth.tiny_params(coarse_labels=2))
+    elif variant == "paths16":             # the paper's 16 SGM directions (Sec. IV-C)
+        views, _, p = lfsynth.tiny(params=lfsynth.tiny_params(paths=16, H=41, W=53))
     else:  # a 3-D light field: one row of 7 views (Middlebury-like)
         p = lfsynth.tiny_params(U=7, V=1, H=30, W=70, coarse_labels=130)
         views, _, p = lfsynth.tiny(params=p)
@@ -209,31 +213,36 @@ def _gpu_sgm(lf, p, cost32, lo, cnt, P1, P2):
     return off, _np(agg)
 
 
-def test_sgm_tiny(gpu_lib, tiny_case):
+@pytest.mark.parametrize("paths", [8, 16])
+def test_sgm_tiny(gpu_lib, tiny_case, paths):
     views, gt, p, cfg, ref = tiny_case
+    p = dataclasses.replace(p, paths=paths)
     c32 = ref["cost"].astype(np.float32)
     P1, P2 = np.float32(ref["P1"]), np.float32(ref["P2"])
     o_Cs = oracle.sgm_bounded(p.H, p.W, ref["lo"], ref["cnt"], ref["off"], c32.astype(np.float64),
-                              float(P1), float(P2))
+                              float(P1), float(P2), paths)
     off, agg = _gpu_sgm(gpu_lib, p, c32, ref["lo"], ref["cnt"], P1, P2)
     err = csr_rel_err(gather(agg, off, ref["cnt"]), o_Cs, ref["cnt"])
     assert err < RTOL, err
 
 
-def test_sgm_zero_penalties_is_eight_times_cost(gpu_lib, tiny_case):
+@pytest.mark.parametrize("paths", [8, 16])
+def test_sgm_zero_penalties_is_paths_times_cost(gpu_lib, tiny_case, paths):
     views, gt, p, cfg, ref = tiny_case
+    p = dataclasses.replace(p, paths=paths)
     c32 = ref["cost"].astype(np.float32)
     off, agg = _gpu_sgm(gpu_lib, p, c32, ref["lo"], ref["cnt"], 0.0, 0.0)
     g = gather(agg, off, ref["cnt"]).astype(np.float64)
-    assert np.max(np.abs(g - 8.0 * c32) / np.maximum(8.0 * c32, 1e-30)) < 1e-6
+    assert np.max(np.abs(g - paths * c32) / np.maximum(paths * c32, 1e-30)) < 1e-6
 
 
-@pytest.mark.parametrize("shape", [(1, 50), (50, 1), (3, 70), (23, 37), (64, 9)])
-def test_sgm_ragged_and_wide_windows(gpu_lib, shape):
+@pytest.mark.parametrize("paths", [8, 16])
+@pytest.mark.parametrize("shape", [(1, 50), (50, 1), (2, 31), (3, 70), (23, 37), (64, 9)])
+def test_sgm_ragged_and_wide_windows(gpu_lib, shape, paths):
     H, W = shape
     G = 150
     p = lfsynth.LFParams(U=3, V=3, H=H, W=W, census_w=5, dmin=-2.0, dmax=2.0, coarse_labels=32,
-                         fine_labels=G, fine_radius=5)
+                         fine_labels=G, fine_radius=5, paths=paths)
     rng = np.random.default_rng(H * 100 + W)
     lo = rng.integers(0, G, H * W).astype(np.int32)
     cnt = np.minimum(rng.integers(1, 40, H * W), G - lo).astype(np.int32)
@@ -243,7 +252,7 @@ def test_sgm_ragged_and_wide_windows(gpu_lib, shape):
     off_o = oracle.offsets(cnt)
     cost = rng.uniform(0, 30, int(off_o[-1])).astype(np.float32)
     P1, P2 = np.float32(1.7), np.float32(9.5)
-    o_Cs = oracle.sgm_bounded(H, W, lo, cnt, off_o, cost.astype(np.float64), float(P1), float(P2))
+    o_Cs = oracle.sgm_bounded(H, W, lo, cnt, off_o, cost.astype(np.float64), float(P1), float(P2), paths)
     off, agg = _gpu_sgm(gpu_lib, p, cost, lo, cnt, P1, P2)
     err = csr_rel_err(gather(agg, off, cnt), o_Cs, cnt)
     assert err < RTOL, err
@@ -311,6 +320,13 @@ def test_depth_end_to_end_tiny(gpu_lib, tiny_case):
     g_label, g_disp, n = _gpu_depth(gpu_lib, p, views)
     _check_end_to_end(g_label, g_disp, ref, p)
     assert n > 10
+
+
+def test_depth_end_to_end_16_paths(gpu_lib):
+    views, gt, p = lfsynth.tiny(params=lfsynth.tiny_params(paths=16))
+    ref = oracle.depth(oracle.make_cfg(p), views, p1f=p.p1_frac, p2f=p.p2_frac)
+    g_label, g_disp, _ = _gpu_depth(gpu_lib, p, views)
+    _check_end_to_end(g_label, g_disp, ref, p)
 
 
 def test_depth_end_to_end_integer_planes_exact(gpu_lib):
