@@ -89,7 +89,7 @@ def workload(name, lf_index):
 def workload_label(p):
     return (f"{p.name}: {p.U}x{p.V} views of {p.H}x{p.W} f32, census {p.census_w}x{p.census_w}, "
             f"coarse {p.coarse_labels} labels on [{p.dmin:g},{p.dmax:g}], fine window 2x{p.fine_radius}+1 "
-            f"of {p.fine_labels} labels, 8-path SGM, parabolic sub-pixel")
+            f"of {p.fine_labels} labels, {p.paths}-path SGM, parabolic sub-pixel")
 
 
 class ClockSampler:

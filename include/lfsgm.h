@@ -88,7 +88,7 @@ lfsgm_status lfsgm_max_nnz(lfsgm_handle h, int64_t *nnz);
 
 /* Initial disparity map and fine search windows (Sec. III-D, Eq. 7-11):
  * census of the cross views (Eq. 2-3), per-arm census cost over the coarse labels
- * (Eq. 7 summed over the arm's views), integer SGM per arm over 8 paths (Eq. 8-9),
+ * (Eq. 7 summed over the arm's views), integer SGM per arm over cfg.paths paths (Eq. 8-9),
  * WTA per arm (Eq. 10), sequential fusion with threshold phi, median hole filling,
  * borders D_init +- lambda saturated to T (Eq. 11; discarded pixels: whole range).
  *   views  [V][U][H][W] float32
@@ -113,10 +113,10 @@ lfsgm_status lfsgm_initial_disparity(lfsgm_handle h, const float *views, int32_t
 lfsgm_status lfsgm_cost_volume(lfsgm_handle h, const float *views, const int32_t *lo,
                                const int32_t *cnt, const int64_t *off, float *cost);
 
-/* Bounded 8-path SGM (Sec. III-E with Eq. 8-9), normalised recurrence
+/* Bounded SGM over cfg.paths (8 or 16) paths (Sec. III-E with Eq. 8-9), normalised recurrence
  *   L_r(p,g) = C(p,g) + (min(L'(g), L'(g-1)+P1, L'(g+1)+P1, m+P2) - m),
  * L' = L_r(p-r,.) over the predecessor's window, m its minimum, absent labels left out,
- * L_r = C at path starts; agg = sum over the 8 directions.  P1 < 0 -> P1 = p1_frac *
+ * L_r = C at path starts; agg = sum over the directions.  P1 < 0 -> P1 = p1_frac *
  * mean(cost over active slots), P2 = p2_frac * mean (computed on the device).
  * Requires 0 <= P1 <= P2 otherwise.  agg [off[N]] float32 out. */
 lfsgm_status lfsgm_sgm_aggregate(lfsgm_handle h, const float *cost, const int32_t *lo,

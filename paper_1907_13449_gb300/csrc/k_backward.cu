@@ -1,4 +1,4 @@
-// k_backward.cu -- adjoint of cost volume -> bounded 8-path SGM -> soft-argmin (not in the paper).
+// k_backward.cu -- adjoint of cost volume -> bounded SGM (8 or 16 paths) -> soft-argmin (not in the paper).
 //
 // Loss gradients arrive as grad_disp = dLoss/d dhat(p) for the soft-argmin disparity
 // dhat = sum_g softmax(-C_s/tau)_g d_g.  Three kernels:

@@ -1,7 +1,7 @@
 // k_coarse.cu -- the initial (coarse) pass of Sec. III-D: per-arm census cost (Eq. 7),
-// penalties, integer 8-path SGM (Eq. 8-9) and WTA (Eq. 10).
+// penalties, integer SGM over 8 or 16 paths (Eq. 8-9) and WTA (Eq. 10).
 //
-// Layout: the arm cost and the 8-path sums are uint16 [arm][pixel][Lcd], the label dimension
+// Layout: the arm cost and the path sums are uint16 [arm][pixel][Lcd], the label dimension
 // padded only to Lcd = round_up(Lc, max(4, LPT)) (LPT = labels per lane: 2, 4 or 8 for
 // Lc <= 64, 128, 256), so a lane's LPT labels are one aligned 4/8/16-byte word.
 //  - cost: one warp per run of 16 pixels of a row and one arm; lanes hold LPT labels each and
@@ -9,7 +9,7 @@
 //    clamping needed), the shifts coming as linear offsets from a per-arm table.
 //  - SGM: one warp per (arm, direction, scanline); the lane's labels stay in registers, the
 //    d-1 / d+1 neighbours across lanes come by one shuffle each way, the predecessor minimum by
-//    one redux.sync; the next 4 cost rows are prefetched; the 8 directions add into the sums
+//    one redux.sync; the next 4 cost rows are prefetched; the directions add into the sums
 //    with one packed 32/64-bit reduction per lane and step (the host checks that a label's sum
 //    over the 8 paths stays below 2^16, so the 16-bit fields never carry into each other).
 //  - WTA: one warp per (arm, pixel), argmin by one redux.sync over (sum << 8 | label).
@@ -295,7 +295,7 @@ __global__ void __launch_bounds__(128) coarse_sgm_kernel(const uint16_t *__restr
     }
 }
 
-// WTA over the 8-path sums (Eq. 10): lowest label on ties (the key is sum << 8 | label).
+// WTA over the path sums (Eq. 10): lowest label on ties (the key is sum << 8 | label).
 template <int LPT>
 __global__ void __launch_bounds__(128) coarse_wta_kernel(const uint16_t *__restrict__ sum, int narms, int N, int Lc,
                                                          int Lcd, int *__restrict__ maps, int *__restrict__ maps_out) {

@@ -1,4 +1,4 @@
-// k_sgm.cu -- bounded 8-path SGM on the windowed fine cost (Sec. III-E with Eq. 8-9).
+// k_sgm.cu -- bounded SGM over 8 or 16 paths on the windowed fine cost (Sec. III-E with Eq. 8-9).
 //
 // One warp per (direction, scanline).  Lane j owns slot j of the current pixel's window.
 // When this window and the predecessor's are both at most 32 labels wide (the regular case),
@@ -11,7 +11,7 @@
 // tight loop with the next cost row one step ahead.  The step is the
 // normalised recurrence
 //   L(p,g) = C(p,g) + (min(L'(g), L'(g-1)+P1, L'(g+1)+P1, m+P2) - m),   m = min L',
-// and the predecessor minimum m is one redux.sync.min.f32 per pixel.  The 8 directions run
+// and the predecessor minimum m is one redux.sync.min.f32 per pixel.  The 8 or 16 directions run
 // concurrently and add into agg (zeroed by the caller) with float atomics.
 //
 // Derived penalties: per-block partial sums (double) of the active slots, then one block

@@ -88,7 +88,7 @@ struct lfsgm_ctx {
     long long *o_off = nullptr;
     float *o_cost = nullptr, *o_agg = nullptr, *o_disp = nullptr, *o_views = nullptr;
     // backward scratch (allocated on the first lfsgm_backward): aggregate, dLoss/dC_s, branch codes
-    // of the 8 directions, argmin slots, penalty gradients
+    // of the 8 or 16 directions, argmin slots, penalty gradients
     float *b_agg = nullptr, *b_gcs = nullptr, *b_gp = nullptr;
     unsigned char *b_codes = nullptr;
     int *b_amin = nullptr;
@@ -287,7 +287,7 @@ lfsgm_status lfsgm_create(const lfsgm_config *cfg, void *stream, lfsgm_handle *o
     h->Lcd = coarse_stride(c.coarse_labels);
     plan_fine_rows(c.U, c.V, c.uc, c.vc, c.H, c.W, c.fine_labels, c.dmin, c.dmax, &h->rows);
     build_arms(h);
-    // the packed coarse sums hold 8 paths x (C + P2) per 16-bit half
+    // the packed coarse sums hold (paths) x (C + P2) per 16-bit half
     const long long cmax = (long long)max_arm_views(h) * h->nbits;
     const long long p2max = (long long)std::floor(c.p2_frac * (double)cmax + 0.5);
     if ((long long)c.paths * (cmax + std::max(p2max, 1LL)) >= 65536) {
@@ -418,7 +418,7 @@ lfsgm_status lfsgm_workspace_size(lfsgm_handle h, size_t *bytes) {
     b += align256(h->nviews * HWp * 8);            // census words, edge-replicated padding
     b += align256(h->nviews * HWp * 4);            // views, edge-replicated padding
     b += align256(A * N * h->Lcd * 2);              // coarse cost
-    b += align256(A * N * h->Lcd * 2);              // coarse 8-path sums
+    b += align256(A * N * h->Lcd * 2);              // coarse path sums
     b += align256(4 * N * 4);                       // maps
     b += 3 * align256(N * 4);                       // F0, F1, padded counts
     b += align256(N * (size_t)((h->cfg.fine_labels + 31) / 32) * 8);   // (pixel, chunk) list

@@ -1,4 +1,4 @@
-"""Pins of the oracle's FP64 adjoint (soft-argmin -> 8-path bounded SGM -> l2/census cost
+"""Pins of the oracle's FP64 adjoint (soft-argmin -> bounded SGM over 8 or 16 paths -> l2/census cost
 -> views) against central finite differences in FP64 and exact invariants.
 
 Workload: 7x7 views of 32x32, every pixel searching one dense 16-label window (the initial
