@@ -295,6 +295,15 @@ def run_ours(args, ws, rank, local):
         lf.lfsgm_depth_host(L.h, vh, dh, lh)
         e2e.append((time.perf_counter() - t0) * 1e3)
     e2e_ms = statistics.mean(e2e)
+    # accuracy of the disparity map against the scene's ground truth (Sec. IV-B measures)
+    from paper_1907_13449_gb300 import quality
+    margin = int(np.ceil(max(p.U - 1 - p.uc, p.uc, p.V - 1 - p.vc, p.vc) * max(abs(p.dmin), abs(p.dmax)))) \
+        + p.census_w // 2
+    qual = {"all_pixels": quality.report(dh.numpy(), gt, e2e_ms * 1e-3),
+            "interior": quality.report(dh.numpy(), gt, e2e_ms * 1e-3, margin=margin),
+            "note": "BadPix(0.07) in %, MSE x 100, M = (100 - BadPix) / e2e runtime (Eq. 14); synthetic "
+                    "ground truth of the rendered scene; interior = pixels farther than max shift + census "
+                    "half-width from the border"}
 
     if rank != 0:
         if ws > 1:
@@ -341,6 +350,7 @@ def run_ours(args, ws, rank, local):
                         "unit": "ms, cost+SGM per step on this rank"},
         "active_cells": active, "nnz_padded": nnz,
         "full_forward_ms_per_lf": round(step_ms / (K * ws), 4),
+        "quality": qual,
         "paths16": {"cost_sgm_ms": round(paths16_ms, 4), "note": "the same light field with the paper's 16 SGM "
                     "directions (Sec. IV-C); the workload's configs use 8"},
         "post_filter": {"median3_ms": round(median_ms, 4), "note": "3x3 median of the disparity map, "

@@ -48,6 +48,7 @@ class LFParams:
     subpixel: int = 1
     softmin_tau: float = 0.1
     paths: int = 8              # SGM directions: 8, or the paper's 16 (Sec. IV-C)
+    edge_threshold: float = 0.0 # Sobel edge exclusion from the borders (Sec. III-D); 0 = off
     uc: int = -1
     vc: int = -1
     name: str = ""

@@ -46,7 +46,7 @@ class Cfg(C.Structure):
                 ("dmin", C.c_double), ("dmax", C.c_double), ("Lc", C.c_int32),
                 ("init_views", C.c_int32), ("phi", C.c_double), ("fill_passes", C.c_int32),
                 ("G", C.c_int32), ("R", C.c_int32), ("w_l2", C.c_double), ("w_census", C.c_double),
-                ("paths", C.c_int32)]
+                ("paths", C.c_int32), ("edge_threshold", C.c_float)]
 
 
 def make_cfg(p) -> Cfg:
@@ -55,7 +55,8 @@ def make_cfg(p) -> Cfg:
     return Cfg(U=p.U, V=p.V, H=p.H, W=p.W, uc=p.uc, vc=p.vc, census_w=p.census_w,
                dmin=p.dmin, dmax=p.dmax, Lc=p.coarse_labels, init_views=p.init_views,
                phi=p.phi, fill_passes=p.fill_passes, G=p.fine_labels, R=p.fine_radius,
-               w_l2=p.w_l2, w_census=p.w_census, paths=getattr(p, "paths", 8))
+               w_l2=p.w_l2, w_census=p.w_census, paths=getattr(p, "paths", 8),
+               edge_threshold=getattr(p, "edge_threshold", 0.0))
 
 
 def _ptr(a, t):
@@ -92,7 +93,8 @@ def lib():
             L.or_wta_int.argtypes = [C.c_size_t, C.c_int, P(C.c_int64), P(C.c_int32)]
             L.or_fuse.argtypes = [C.c_size_t, C.c_int, P(C.c_int32), C.c_double, P(C.c_double)]
             L.or_hole_fill.argtypes = [C.c_int, C.c_int, C.c_int, P(C.c_double)]
-            L.or_windows.argtypes = [P(Cfg), C.c_size_t, P(C.c_double), P(C.c_int32), P(C.c_int32)]
+            L.or_windows.argtypes = [P(Cfg), C.c_size_t, P(C.c_double), P(C.c_uint8), P(C.c_int32), P(C.c_int32)]
+            L.or_sobel_edges.argtypes = [C.c_int, C.c_int, P(C.c_float), C.c_float, P(C.c_uint8)]
             L.or_cost_volume.argtypes = [P(Cfg), P(C.c_double), P(C.c_uint64), P(C.c_int32),
                                          P(C.c_int32), P(C.c_int64), P(C.c_double)]
             L.or_softargmin_backward.argtypes = [P(Cfg), C.c_size_t, P(C.c_int32), P(C.c_int32), P(C.c_int64),
@@ -200,12 +202,22 @@ def hole_fill(dinit: np.ndarray, H: int, W: int, passes: int) -> np.ndarray:
     return d
 
 
-def windows(cfg: Cfg, dinit: np.ndarray):
+def sobel_edges(I: np.ndarray, threshold: float) -> np.ndarray:
+    """Edge mask of the reference view for the border exclusion (Sec. III-D), FP32 Sobel."""
+    I = np.ascontiguousarray(I, dtype=np.float32)
+    H, W = I.shape
+    out = np.zeros((H, W), np.uint8)
+    lib().or_sobel_edges(H, W, _ptr(I, C.c_float), float(threshold), _ptr(out, C.c_uint8))
+    return out.astype(bool)
+
+
+def windows(cfg: Cfg, dinit: np.ndarray, edge=None):
     d = np.ascontiguousarray(dinit, dtype=np.float64).reshape(-1)
     lo = np.zeros(d.size, np.int32)
     cnt = np.zeros(d.size, np.int32)
-    lib().or_windows(C.byref(cfg), d.size, _ptr(d, C.c_double), _ptr(lo, C.c_int32),
-                     _ptr(cnt, C.c_int32))
+    e = None if edge is None else np.ascontiguousarray(edge, dtype=np.uint8).reshape(-1)
+    lib().or_windows(C.byref(cfg), d.size, _ptr(d, C.c_double), None if e is None else _ptr(e, C.c_uint8),
+                     _ptr(lo, C.c_int32), _ptr(cnt, C.c_int32))
     return lo, cnt
 
 
@@ -305,7 +317,10 @@ def initial_disparity(cfg: Cfg, views: np.ndarray, penalties=None, p1f=0.05, p2f
     maps = np.stack(maps)
     fused = fuse(maps, cfg.phi)
     filled = hole_fill(fused, H, W, cfg.fill_passes)
-    lo, cnt = windows(cfg, filled)
+    edge = None
+    if cfg.edge_threshold > 0:
+        edge = sobel_edges(views[cfg.vc, cfg.uc], cfg.edge_threshold)
+    lo, cnt = windows(cfg, filled, edge)
     return {"maps": maps, "arms": arms, "penalties": pens, "fused": fused,
             "dinit": filled, "lo": lo, "cnt": cnt, "census": cen}
 

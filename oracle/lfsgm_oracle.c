@@ -50,6 +50,7 @@ typedef struct {
     int32_t R;            /* border threshold lambda in fine labels (Eq. 11)           */
     double w_l2, w_census;/* weights of Eq. 12 (l2) and Eq. 15 (census) terms          */
     int32_t paths;        /* SGM directions: 8, or the paper's 16 (Sec. IV-C)           */
+    float edge_threshold; /* Sobel edge exclusion (Sec. III-D): 0 = off                 */
 } or_cfg;
 
 static int clampi(int v, int lo, int hi) { return v < lo ? lo : (v > hi ? hi : v); }
@@ -336,10 +337,40 @@ void or_hole_fill(int H, int W, int passes, double *dinit)
  * moved to the nearest fine label gc (exact rational arithmetic, ties upward), the
  * window is [gc - R, gc + R] saturated to [0, G-1]; a discarded pixel searches the
  * whole range T.  (lo, cnt) give the window as first fine label and label count. */
-void or_windows(const or_cfg *c, size_t N, const double *dinit, int32_t *lo, int32_t *cnt)
+/* Edges of the reference view for the border exclusion (Sec. III-D): the 3 x 3 Sobel gradient
+ * with the neighbours clamped to the image,
+ *   gx = ((p2 + 2 p5) + p8) - ((p0 + 2 p3) + p6),  gy = ((p6 + 2 p7) + p8) - ((p0 + 2 p1) + p2)
+ * (p0..p8 the window row-major), and a pixel is an edge iff gx^2 + gy^2 > t^2.  The paper gives
+ * no threshold.  The sums, squares and the comparison are IEEE FP32 in exactly this order, so the
+ * integer decision is the same in any implementation that follows it. */
+void or_sobel_edges(int H, int W, const float *I, float t, uint8_t *edge)
+{
+    const float t2 = t * t;
+    for (int y = 0; y < H; y++)
+        for (int x = 0; x < W; x++) {
+            float q[9];
+            for (int dy = -1; dy <= 1; dy++)
+                for (int dx = -1; dx <= 1; dx++)
+                    q[(dy + 1) * 3 + dx + 1] = I[(size_t)clampi(y + dy, 0, H - 1) * W + clampi(x + dx, 0, W - 1)];
+            volatile float a, b, gx, gy, m;
+            a = q[2] + 2.0f * q[5]; a = a + q[8];
+            b = q[0] + 2.0f * q[3]; b = b + q[6];
+            gx = a - b;
+            a = q[6] + 2.0f * q[7]; a = a + q[8];
+            b = q[0] + 2.0f * q[1]; b = b + q[2];
+            gy = a - b;
+            a = gx * gx;
+            b = gy * gy;
+            m = a + b;
+            edge[(size_t)y * W + x] = m > t2;
+        }
+}
+
+/* Borders (Eq. 11); `edge` (nullable): pixels excluded from the borders search the whole range. */
+void or_windows(const or_cfg *c, size_t N, const double *dinit, const uint8_t *edge, int32_t *lo, int32_t *cnt)
 {
     for (size_t p = 0; p < N; p++) {
-        if (isnan(dinit[p])) { lo[p] = 0; cnt[p] = c->G; continue; }
+        if (isnan(dinit[p]) || (edge && edge[p])) { lo[p] = 0; cnt[p] = c->G; continue; }
         int64_t m = (int64_t)(dinit[p] * 8.0);           /* exact: dinit is k/8 */
         int64_t num = m * (int64_t)(c->G - 1);
         int64_t den = 8 * (int64_t)(c->Lc - 1);

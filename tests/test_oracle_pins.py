@@ -496,3 +496,34 @@ def test_median3_removes_impulses_and_keeps_ramps():
     c[8, 10] = -7.0
     c[0, 0] = 9.0
     assert np.array_equal(oracle.median3(c), np.full((H, W), 1.5))
+
+
+# -------------------------------------------------- edge exclusion from the borders (Sec. III-D)
+def test_sobel_edges_on_constant_ramp_and_step():
+    H, W = 9, 12
+    assert not oracle.sobel_edges(np.full((H, W), 0.3), 1e-6).any()
+    # linear ramp a x: gx = 8 a in the interior (the weights 1, 2, 1 over a central difference of 2a)
+    a = 0.125
+    ramp = np.broadcast_to(a * np.arange(W, dtype=np.float64), (H, W))
+    e_lo = oracle.sobel_edges(ramp, 8 * a - 0.01)
+    e_hi = oracle.sobel_edges(ramp, 8 * a + 0.01)
+    assert e_lo[:, 1:-1].all() and not e_hi.any()
+    # border columns see a one-sided difference a: gx = 4 a
+    assert not e_lo[:, 0].any() and not e_lo[:, -1].any()
+    # a vertical step of height 1 between columns 5 and 6: gx = 4 on both columns next to it
+    step = np.zeros((H, W))
+    step[:, 6:] = 1.0
+    e = oracle.sobel_edges(step, 3.9)
+    assert e[:, 5].all() and e[:, 6].all() and e.sum() == 2 * H
+
+
+def test_edges_search_the_whole_range():
+    p = lfsynth.tiny_params(H=8, W=8, edge_threshold=0.5)
+    cfg = oracle.make_cfg(p)
+    dinit = np.full(p.N, 3.0)
+    edge = np.zeros(p.N, bool)
+    edge[[5, 17, 60]] = True
+    lo0, cnt0 = oracle.windows(cfg, dinit)
+    lo, cnt = oracle.windows(cfg, dinit, edge)
+    assert np.array_equal(lo[~edge], lo0[~edge]) and np.array_equal(cnt[~edge], cnt0[~edge])
+    assert np.all(lo[edge] == 0) and np.all(cnt[edge] == p.fine_labels)
