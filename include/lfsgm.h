@@ -69,6 +69,9 @@ typedef struct {
     float   softmin_tau;       /* soft-argmin temperature                                   */
     int32_t paths;             /* SGM directions: 8, or the paper's 16 (Sec. IV-C) adding the
                                   slopes 1/2 and 2; 0 is read as 8                            */
+    float   edge_threshold;    /* Sobel edge exclusion from the borders (Sec. III-D): pixels of
+                                  the reference view with gx^2 + gy^2 > t^2 (FP32, 3 x 3 Sobel,
+                                  clamped) search the whole range; 0 = off                    */
 } lfsgm_config;
 
 /* Create a handle for one light-field shape.  `stream` is a cudaStream_t (NULL = the

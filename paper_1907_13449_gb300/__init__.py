@@ -40,7 +40,8 @@ class Config(C.Structure):
                 ("init_views", C.c_int32), ("phi", C.c_double), ("fill_passes", C.c_int32),
                 ("fine_labels", C.c_int32), ("fine_radius", C.c_int32), ("w_l2", C.c_float),
                 ("w_census", C.c_float), ("p1_frac", C.c_double), ("p2_frac", C.c_double),
-                ("subpixel", C.c_int32), ("softmin_tau", C.c_float), ("paths", C.c_int32)]
+                ("subpixel", C.c_int32), ("softmin_tau", C.c_float), ("paths", C.c_int32),
+                ("edge_threshold", C.c_float)]
 
 
 def make_config(p) -> Config:
@@ -50,7 +51,8 @@ def make_config(p) -> Config:
                   init_views=p.init_views, phi=p.phi, fill_passes=p.fill_passes,
                   fine_labels=p.fine_labels, fine_radius=p.fine_radius, w_l2=p.w_l2,
                   w_census=p.w_census, p1_frac=p.p1_frac, p2_frac=p.p2_frac, subpixel=p.subpixel,
-                  softmin_tau=p.softmin_tau, paths=getattr(p, "paths", 8))
+                  softmin_tau=p.softmin_tau, paths=getattr(p, "paths", 8),
+                  edge_threshold=getattr(p, "edge_threshold", 0.0))
 
 
 EXPORTS = ["lfsgm_create", "lfsgm_destroy", "lfsgm_workspace_size", "lfsgm_set_workspace",

@@ -50,16 +50,32 @@ __global__ void fill_kernel(const int *__restrict__ Fin, int *__restrict__ Fout,
 
 // Borders (Eq. 11): nearest fine label gc = round_half_up(m (G-1) / (8 (Lc-1))), window
 // [gc - R, gc + R] saturated to [0, G-1]; a discarded pixel gets the whole range.
+// Edge test of the border exclusion (Sec. III-D) on the edge-padded reference view (a padded read
+// is the clamped read): the 3 x 3 Sobel sums, their squares and the comparison in FP32 with
+// explicit rounding, in the order the oracle uses, so both take the same decision.
+__device__ __forceinline__ bool sobel_edge(const float *I, int Wp, float t) {
+    const float q0 = I[-Wp - 1], q1 = I[-Wp], q2 = I[-Wp + 1];
+    const float q3 = I[-1], q5 = I[1];
+    const float q6 = I[Wp - 1], q7 = I[Wp], q8 = I[Wp + 1];
+    const float gx = __fsub_rn(__fadd_rn(__fadd_rn(q2, __fmul_rn(2.0f, q5)), q8),
+                               __fadd_rn(__fadd_rn(q0, __fmul_rn(2.0f, q3)), q6));
+    const float gy = __fsub_rn(__fadd_rn(__fadd_rn(q6, __fmul_rn(2.0f, q7)), q8),
+                               __fadd_rn(__fadd_rn(q0, __fmul_rn(2.0f, q1)), q2));
+    return __fadd_rn(__fmul_rn(gx, gx), __fmul_rn(gy, gy)) > __fmul_rn(t, t);
+}
+
 __global__ void windows_kernel(const int *__restrict__ F, int N, int G, int Lc, int R, int *__restrict__ lo,
-                               int *__restrict__ cnt, float *__restrict__ dinit, int *__restrict__ cntpad) {
+                               int *__restrict__ cnt, float *__restrict__ dinit, int *__restrict__ cntpad,
+                               const float *__restrict__ ref_pad, int P, int Wp, int W, float edge_t) {
     const int p = blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= N) return;
     const int v = F[p];
+    const bool edge = edge_t > 0.f && sobel_edge(ref_pad + (size_t)(p / W + P) * Wp + (p % W + P), Wp, edge_t);
     int a, n;
-    if (v < 0) {
+    if (v < 0 || edge) {
         a = 0;
         n = G;
-        if (dinit) dinit[p] = __int_as_float(0x7fc00000);
+        if (dinit) dinit[p] = v < 0 ? __int_as_float(0x7fc00000) : 0.125f * (float)v;
     } else {
         const long long num = (long long)v * (G - 1);
         const long long den = 8LL * (Lc - 1);
@@ -153,8 +169,9 @@ cudaError_t launch_fill(cudaStream_t s, const int *Fin, int *Fout, int H, int W)
     return cudaGetLastError();
 }
 cudaError_t launch_windows(cudaStream_t s, const int *F, int N, int G, int Lc, int R, int *lo, int *cnt,
-                           float *dinit, int *cntpad) {
-    windows_kernel<<<(N + 255) / 256, 256, 0, s>>>(F, N, G, Lc, R, lo, cnt, dinit, cntpad);
+                           float *dinit, int *cntpad, const float *ref_pad, int P, int Wp, int W, float edge_t) {
+    windows_kernel<<<(N + 255) / 256, 256, 0, s>>>(F, N, G, Lc, R, lo, cnt, dinit, cntpad, ref_pad, P, Wp, W,
+                                                   edge_t);
     return cudaGetLastError();
 }
 int scan_tiles(int N) { return (N + kScanTile - 1) / kScanTile; }

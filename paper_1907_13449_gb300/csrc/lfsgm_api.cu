@@ -173,6 +173,7 @@ lfsgm_status validate(const lfsgm_config &c, char *why, size_t n) {
     if (c.subpixel < 0 || c.subpixel > 2) BAD("subpixel must be 0, 1 or 2");
     if (!(c.softmin_tau > 0.f)) BAD("softmin_tau must be > 0");
     if (c.paths != 0 && c.paths != 8 && c.paths != 16) BAD("paths must be 8 or 16");
+    if (!(c.edge_threshold >= 0.f) || !std::isfinite(c.edge_threshold)) BAD("edge_threshold must be finite and >= 0");
     const double md = std::fmax(std::fabs(c.dmin), std::fabs(c.dmax));
     if (md * (std::max(c.U, c.V)) > 30000.0) BAD("shifts exceed the 16-bit table range");
     return LFSGM_OK;
@@ -481,7 +482,9 @@ lfsgm_status lfsgm_initial_disparity(lfsgm_handle h, const float *views, int32_t
         std::swap(fin, fout);
     }
     LFSGM_TRY(run(h, "windows", [&] {
-        return launch_windows(s, fin, N, c.fine_labels, c.coarse_labels, c.fine_radius, lo, cnt, dinit, h->cntpad);
+        return launch_windows(s, fin, N, c.fine_labels, c.coarse_labels, c.fine_radius, lo, cnt, dinit, h->cntpad,
+                              h->views_pad + (size_t)h->ref * h->rows.Hp * h->rows.Wp, h->rows.P, h->rows.Wp,
+                              c.W, c.edge_threshold);
     }));
     LFSGM_TRY(run(h, "scan_sums", [&] { return launch_scan_sums(s, h->cntpad, N, h->tsum); }));
     LFSGM_TRY(run(h, "scan_top", [&] { return launch_scan_top(s, h->tsum, N); }));

@@ -147,7 +147,8 @@ cudaError_t launch_coarse_wta(cudaStream_t s, const uint16_t *sum, int narms, in
 cudaError_t launch_fuse(cudaStream_t s, const int *maps, int narms, int N, double phi, int *F);
 cudaError_t launch_fill(cudaStream_t s, const int *Fin, int *Fout, int H, int W);
 cudaError_t launch_windows(cudaStream_t s, const int *F, int N, int G, int Lc, int R, int *lo,
-                           int *cnt, float *dinit, int *cntpad);
+                           int *cnt, float *dinit, int *cntpad, const float *ref_pad, int P, int Wp, int W,
+                           float edge_t);
 int scan_tiles(int N);   // tiles of the offset scan (tile sums buffer length)
 cudaError_t launch_scan_sums(cudaStream_t s, const int *cntpad, int N, long long *tsum);
 cudaError_t launch_scan_top(cudaStream_t s, long long *tsum, int N);

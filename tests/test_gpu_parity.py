@@ -74,7 +74,8 @@ def test_initial_disparity_tiny_bitexact(gpu_lib, tiny_case):
 
 
 @pytest.mark.parametrize("variant", ["explicit_pen", "paper_4_views", "census7_odd_shape", "one_pass",
-                                     "row_lf", "max_coarse_labels", "two_coarse_labels", "paths16"])
+                                     "row_lf", "max_coarse_labels", "two_coarse_labels", "paths16",
+                                     "sobel_edges"])
 def test_initial_disparity_variants(gpu_lib, variant):
     Pc = (0, 0)
     if variant == "explicit_pen":
@@ -93,6 +94,9 @@ def test_initial_disparity_variants(gpu_lib, variant):
         views, _, p = lfsynth.tiny(params=lfsynth.tiny_params(coarse_labels=2))
     elif variant == "paths16":             # the paper's 16 SGM directions (Sec. IV-C)
         views, _, p = lfsynth.tiny(params=lfsynth.tiny_params(paths=16, H=41, W=53))
+    elif variant == "sobel_edges":         # edge exclusion from the borders (Sec. III-D)
+        views, _, p = lfsynth.tiny(params=lfsynth.tiny_params(edge_threshold=1.5))
+        assert 0.05 < oracle.sobel_edges(views[p.vc, p.uc], 1.5).mean() < 0.95
     else:  # a 3-D light field: one row of 7 views (Middlebury-like)
         p = lfsynth.tiny_params(U=7, V=1, H=30, W=70, coarse_labels=130)
         views, _, p = lfsynth.tiny(params=p)
