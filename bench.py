@@ -79,11 +79,7 @@ def dist_env():
 
 def workload(name, lf_index):
     import lfsynth
-    if name == "bench":
-        return lfsynth.bench(lf_index)
-    if name == "plenoptic":
-        return lfsynth.plenoptic(lf_index)
-    return lfsynth.tiny(lf_index)
+    return lfsynth.WORKLOADS[name](lf_index)
 
 
 def workload_label(p):
@@ -616,7 +612,7 @@ def main():
     ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="bench", choices=["bench", "plenoptic", "tiny"])
+    ap.add_argument("--workload", default="bench", choices=["bench", "plenoptic", "tiny", "epfl", "middlebury"])
     ap.add_argument("--cpu-rows", type=int, default=512, help="image rows of the oracle sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--batch-lfs", type=int, default=64, help="light fields in the mixed batch (0: skip)")

@@ -187,6 +187,28 @@ def plenoptic_params(**kw) -> LFParams:
     return LFParams(**d)
 
 
+def epfl_params(**kw) -> LFParams:
+    """EPFL-shaped (Sec. IV-E): 3x3 x 541x376, narrow baseline (disparity in [-1, 1] px), 32 coarse
+    labels over 5 cross views, fine +-0.3 px by 0.02 (101 labels).  The fine cost is l2 + census:
+    with |u - uc| <= 1 the census term, sampled at the nearest integer shift, is the same for
+    every label within half a pixel, so census alone cannot place these disparities."""
+    d = dict(U=3, V=3, H=376, W=541, census_w=7, dmin=-1.0, dmax=1.0, coarse_labels=32,
+             fine_labels=101, fine_radius=15, name="epfl 3x3x376x541")
+    d.update(kw)
+    return LFParams(**d)
+
+
+def middlebury_params(**kw) -> LFParams:
+    """Middlebury-shaped (Sec. IV-E): 7 views in a row (U=7, V=1) of a half-size 555x650 image,
+    wide baseline (disparity in [0, 12] px per view step), census cost, boundary-less search
+    (every window is the whole range: the radius covers the grid), 64 coarse labels, 121 fine
+    labels by 0.1 px."""
+    d = dict(U=7, V=1, H=555, W=650, census_w=7, dmin=0.0, dmax=12.0, coarse_labels=64,
+             fine_labels=121, fine_radius=121, w_l2=0.0, w_census=1.0, name="middlebury 7x1x555x650")
+    d.update(kw)
+    return LFParams(**d)
+
+
 def tiny(lf_index: int = 0, params: LFParams | None = None):
     """Uniform-noise texture on 3 fronto-parallel planes (-1.5 background, 0.25 centre
     rectangle, 1.75 inner rectangle), noise sigma 0.01."""
@@ -257,6 +279,20 @@ def plenoptic(lf_index: int = 0, params: LFParams | None = None):
     return views, gt, p
 
 
+def epfl(lf_index: int = 0, params: LFParams | None = None):
+    """8 slanted planes with disparity in [-0.9, 0.9] px, noise sigma 0.01."""
+    p = params or epfl_params()
+    views, gt = voronoi_scene(p, 1000 * 5 + lf_index, 8, (-0.8, 0.8), 0.2, 0.9, 0.01)
+    return views, gt, p
+
+
+def middlebury(lf_index: int = 0, params: LFParams | None = None):
+    """8 slanted planes with disparity in [0.5, 11.5] px per view step, noise sigma 0.01."""
+    p = params or middlebury_params()
+    views, gt = voronoi_scene(p, 1000 * 6 + lf_index, 8, (1.5, 10.5), 1.0, 11.5, 0.01)
+    return views, gt, p
+
+
 def integer_planes(U=5, V=5, H=48, W=48, disps=(-1.0, 0.0, 1.0), seed=7, **kw):
     """Noise-free fronto-parallel planes with integer disparity: every view is an exact
     integer shift of a seeded uniform texture (nested rectangles, one per plane)."""
@@ -288,7 +324,7 @@ def random_views(U, V, H, W, seed=0, lo=0.0, hi=1.0):
     return rng.uniform(lo, hi, size=(V, U, H, W)).astype(np.float32)
 
 
-WORKLOADS = {"tiny": tiny, "bench": bench, "plenoptic": plenoptic}
+WORKLOADS = {"tiny": tiny, "bench": bench, "plenoptic": plenoptic, "epfl": epfl, "middlebury": middlebury}
 
 
 # ------------------------------------------------------------------ device-side rendering

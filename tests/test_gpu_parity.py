@@ -326,6 +326,19 @@ def test_depth_end_to_end_tiny(gpu_lib, tiny_case):
     assert n > 10
 
 
+@pytest.mark.parametrize("kind", ["epfl", "middlebury"])
+def test_depth_end_to_end_real_world_shapes(gpu_lib, kind):
+    """EPFL-shaped (3x3 views) and Middlebury-shaped (a row of 7 views, boundary-less search)
+    light fields, census cost only (Eq. 15), at reduced image size."""
+    if kind == "epfl":
+        views, gt, p = lfsynth.epfl(params=lfsynth.epfl_params(H=94, W=135))
+    else:
+        views, gt, p = lfsynth.middlebury(params=lfsynth.middlebury_params(H=70, W=81))
+    ref = oracle.depth(oracle.make_cfg(p), views, p1f=p.p1_frac, p2f=p.p2_frac)
+    g_label, g_disp, _ = _gpu_depth(gpu_lib, p, views)
+    _check_end_to_end(g_label, g_disp, ref, p)
+
+
 def test_depth_end_to_end_16_paths(gpu_lib):
     views, gt, p = lfsynth.tiny(params=lfsynth.tiny_params(paths=16))
     ref = oracle.depth(oracle.make_cfg(p), views, p1f=p.p1_frac, p2f=p.p2_frac)

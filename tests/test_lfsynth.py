@@ -30,3 +30,13 @@ def test_batch_mix_covers_shapes_labels_and_census():
     assert {p.census_w for p in ps} == {5, 7}
     combos = {(p.U, p.census_w, p.coarse_labels) for p in ps}
     assert len(combos) == 32                      # every class meets every census and label count
+
+
+def test_real_world_shaped_workloads():
+    for f, shape in [(lfsynth.epfl, (3, 3, 60, 80)), (lfsynth.middlebury, (1, 7, 50, 70))]:
+        V, U, H, W = shape
+        p0 = f.__name__ == "epfl" and lfsynth.epfl_params(H=H, W=W) or lfsynth.middlebury_params(H=H, W=W)
+        views, gt, p = f(params=p0)
+        assert views.shape == shape and views.dtype == np.float32
+        assert gt.shape == (H, W) and p.dmin <= gt.min() and gt.max() <= p.dmax
+    assert lfsynth.middlebury_params().fine_radius >= lfsynth.middlebury_params().fine_labels   # boundary-less
