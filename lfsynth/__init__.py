@@ -49,6 +49,7 @@ class LFParams:
     softmin_tau: float = 0.1
     paths: int = 8              # SGM directions: 8, or the paper's 16 (Sec. IV-C)
     edge_threshold: float = 0.0 # Sobel edge exclusion from the borders (Sec. III-D); 0 = off
+    channels: int = 1           # 1 (grey) or 3 (RGB: views[v][u][c][y][x])
     uc: int = -1
     vc: int = -1
     name: str = ""
@@ -104,14 +105,18 @@ def _sample(tex: np.ndarray, margin: int, idx: np.ndarray, x: np.ndarray, y: np.
 
 
 def render(p: LFParams, planes, region, textures, margin, noise_rng, sigma, vignette=False):
-    """Render views[v][u][y][x] (float32) and the reference-view disparity (float64).
+    """Render views[v][u][y][x] (float32; views[v][u][c][y][x] for colour textures) and the
+    reference-view disparity (float64).
 
     ``region(i, x, y)`` -> bool array: is reference point (x, y) on plane i.
-    ``textures[i]``: texture of plane i on the reference grid plus ``margin``."""
+    ``textures[i]``: texture of plane i on the reference grid plus ``margin`` ([th][tw], or
+    [C][th][tw] for C colour channels, each sampled at the same points)."""
     U, V, H, W = p.U, p.V, p.H, p.W
     Y, X = np.mgrid[0:H, 0:W].astype(np.float64)
     tex = np.stack(textures)
-    views = np.zeros((V, U, H, W), np.float32)
+    colour = tex.ndim == 4
+    C = tex.shape[1] if colour else 1
+    views = np.zeros((V, U, C, H, W) if colour else (V, U, H, W), np.float32)
     gt = None
     for v in range(V):
         for u in range(U):
@@ -141,7 +146,10 @@ def render(p: LFParams, planes, region, textures, margin, noise_rng, sigma, vign
                     arr[fall] = val if np.isscalar(val) else val[fall]
             hole = ~np.isfinite(best_d)
             idx, xs, ys = (np.where(hole, f, bb) for f, bb in zip(far, best))
-            img = _sample(tex, margin, idx, xs, ys)
+            if colour:
+                img = np.stack([_sample(tex[:, ch], margin, idx, xs, ys) for ch in range(C)])
+            else:
+                img = _sample(tex, margin, idx, xs, ys)
             if a == 0 and b == 0:
                 gt = np.where(hole, far_d, best_d)
             if sigma > 0:
@@ -217,6 +225,9 @@ def tiny(lf_index: int = 0, params: LFParams | None = None):
     margin = int(math.ceil(max(abs(p.dmin), abs(p.dmax)) * max(p.U, p.V))) + 2
     th, tw = p.H + 2 * margin, p.W + 2 * margin
     textures = [tex_rng.uniform(0.05, 0.95, size=(th, tw)) for _ in range(3)]
+    if p.channels > 1:       # further channels drawn after the grey ones (grey scenes unchanged)
+        extra = [[tex_rng.uniform(0.05, 0.95, size=(th, tw)) for _ in range(p.channels - 1)] for _ in range(3)]
+        textures = [np.stack([t] + e) for t, e in zip(textures, extra)]
     planes = [Plane(-1.5), Plane(0.25), Plane(1.75)]
     H, W = p.H, p.W
     rects = [None, (W * 0.25, H * 0.25, W * 0.75, H * 0.75), (W * 0.40, H * 0.375, W * 0.60, H * 0.625)]
@@ -237,6 +248,10 @@ def voronoi_scene(p: LFParams, seed: int, n_planes: int, a_range, slope, clamp, 
     margin = int(math.ceil(max(abs(p.dmin), abs(p.dmax)) * max(p.U, p.V))) + 2
     th, tw = p.H + 2 * margin, p.W + 2 * margin
     textures = [_blur121(tex_rng.uniform(0.0, 1.0, size=(th, tw))) for _ in range(n_planes)]
+    if p.channels > 1:       # further channels drawn after the grey ones (grey scenes unchanged)
+        extra = [[_blur121(tex_rng.uniform(0.0, 1.0, size=(th, tw))) for _ in range(p.channels - 1)]
+                 for _ in range(n_planes)]
+        textures = [np.stack([t] + e) for t, e in zip(textures, extra)]
     sites = np.stack([geo_rng.uniform(0, p.W, n_planes), geo_rng.uniform(0, p.H, n_planes)], 1)
     planes = []
     for _ in range(n_planes):
@@ -304,6 +319,9 @@ def integer_planes(U=5, V=5, H=48, W=48, disps=(-1.0, 0.0, 1.0), seed=7, **kw):
     margin = int(math.ceil(max(abs(p.dmin), abs(p.dmax)) * max(p.U, p.V))) + 2
     th, tw = p.H + 2 * margin, p.W + 2 * margin
     textures = [tex_rng.uniform(0.05, 0.95, size=(th, tw)) for _ in disps]
+    if p.channels > 1:       # further channels drawn after the grey ones (grey scenes unchanged)
+        extra = [[tex_rng.uniform(0.05, 0.95, size=(th, tw)) for _ in range(p.channels - 1)] for _ in disps]
+        textures = [np.stack([t] + e) for t, e in zip(textures, extra)]
     order = np.argsort(disps)
     planes = [Plane(float(disps[i])) for i in order]
     n = len(planes)
@@ -318,10 +336,12 @@ def integer_planes(U=5, V=5, H=48, W=48, disps=(-1.0, 0.0, 1.0), seed=7, **kw):
     return views, gt, p
 
 
-def random_views(U, V, H, W, seed=0, lo=0.0, hi=1.0):
-    """Plain i.i.d. uniform views (for stage-level tests that need no scene)."""
+def random_views(U, V, H, W, seed=0, lo=0.0, hi=1.0, channels=1):
+    """Plain i.i.d. uniform views (for stage-level tests that need no scene);
+    [V][U][C][H][W] when ``channels`` > 1."""
     rng = np.random.default_rng(seed)
-    return rng.uniform(lo, hi, size=(V, U, H, W)).astype(np.float32)
+    shape = (V, U, H, W) if channels == 1 else (V, U, channels, H, W)
+    return rng.uniform(lo, hi, size=shape).astype(np.float32)
 
 
 WORKLOADS = {"tiny": tiny, "bench": bench, "plenoptic": plenoptic, "epfl": epfl, "middlebury": middlebury}

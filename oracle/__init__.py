@@ -46,17 +46,21 @@ class Cfg(C.Structure):
                 ("dmin", C.c_double), ("dmax", C.c_double), ("Lc", C.c_int32),
                 ("init_views", C.c_int32), ("phi", C.c_double), ("fill_passes", C.c_int32),
                 ("G", C.c_int32), ("R", C.c_int32), ("w_l2", C.c_double), ("w_census", C.c_double),
-                ("paths", C.c_int32), ("edge_threshold", C.c_float)]
+                ("paths", C.c_int32), ("edge_threshold", C.c_float), ("channels", C.c_int32)]
 
 
 def make_cfg(p) -> Cfg:
     """Oracle config from any object with the method's parameter names
-    (``lfsynth.LFParams`` or the library's config dataclass)."""
+    (``lfsynth.LFParams`` or the library's config dataclass).  Views are
+    [V][U][H][W] for one channel and [V][U][C][H][W] for C = 3 (RGB)."""
+    channels = int(getattr(p, "channels", 1) or 1)
+    if channels not in (1, 3):
+        raise ValueError(f"channels must be 1 or 3, got {channels}")
     return Cfg(U=p.U, V=p.V, H=p.H, W=p.W, uc=p.uc, vc=p.vc, census_w=p.census_w,
                dmin=p.dmin, dmax=p.dmax, Lc=p.coarse_labels, init_views=p.init_views,
                phi=p.phi, fill_passes=p.fill_passes, G=p.fine_labels, R=p.fine_radius,
                w_l2=p.w_l2, w_census=p.w_census, paths=getattr(p, "paths", 8),
-               edge_threshold=getattr(p, "edge_threshold", 0.0))
+               edge_threshold=getattr(p, "edge_threshold", 0.0), channels=channels)
 
 
 def _ptr(a, t):
@@ -203,8 +207,11 @@ def hole_fill(dinit: np.ndarray, H: int, W: int, passes: int) -> np.ndarray:
 
 
 def sobel_edges(I: np.ndarray, threshold: float) -> np.ndarray:
-    """Edge mask of the reference view for the border exclusion (Sec. III-D), FP32 Sobel."""
+    """Edge mask of the reference view for the border exclusion (Sec. III-D), FP32 Sobel.
+    ``I`` is [H][W], or [C][H][W]: a pixel is an edge iff it is one in any channel."""
     I = np.ascontiguousarray(I, dtype=np.float32)
+    if I.ndim == 3:
+        return np.logical_or.reduce([sobel_edges(I[ch], threshold) for ch in range(I.shape[0])])
     H, W = I.shape
     out = np.zeros((H, W), np.uint8)
     lib().or_sobel_edges(H, W, _ptr(I, C.c_float), float(threshold), _ptr(out, C.c_uint8))

@@ -10,8 +10,9 @@
  * equations in the paper's order, with plain loops, in double precision.
  *
  * Conventions (the paper's symbols in brackets):
- *   views[v][u][y][x]  float32 input, (x,y) spatial [(u,v) in the paper],
- *                      (u,v) angular [(s,t) in the paper]; reference (uc,vc).
+ *   views[v][u][c][y][x]  float32 input, (x,y) spatial [(u,v) in the paper],
+ *                      (u,v) angular [(s,t) in the paper]; reference (uc,vc);
+ *                      c the colour channel (C = 1 grey, C = 3 RGB).
  *   a view (u,v) is sampled for pixel (x,y) and disparity d at
  *        (x + (u-uc)*d, y + (v-vc)*d)                     (Eq. 1, sign flipped:
  *   the paper writes (s^-s)*d; we measure d with the opposite sign so that a
@@ -51,9 +52,11 @@ typedef struct {
     double w_l2, w_census;/* weights of Eq. 12 (l2) and Eq. 15 (census) terms          */
     int32_t paths;        /* SGM directions: 8, or the paper's 16 (Sec. IV-C)           */
     float edge_threshold; /* Sobel edge exclusion (Sec. III-D): 0 = off                 */
+    int32_t channels;     /* colour channels C: 1 or 3 (0 means 1)                      */
 } or_cfg;
 
 static int clampi(int v, int lo, int hi) { return v < lo ? lo : (v > hi ? hi : v); }
+static int nchan(const or_cfg *c) { return c->channels > 1 ? c->channels : 1; }
 
 /* Disparity of label k on an inclusive grid of L labels over [dmin,dmax]. */
 double or_label_disp(double dmin, double dmax, int L, int k)
@@ -110,14 +113,14 @@ int or_hamming(uint64_t a, uint64_t b)
     return n;
 }
 
-/* Census words of every view: out[(v*U+u)*H*W + y*W + x]. */
+/* Census words of every view and channel, each channel on its own (Sec. III-B):
+ * out[((v*U+u)*C + ch)*H*W + y*W + x]. */
 void or_census_all(const or_cfg *c, const double *views, uint64_t *out)
 {
     size_t HW = (size_t)c->H * c->W;
-    for (int v = 0; v < c->V; v++)
-        for (int u = 0; u < c->U; u++)
-            or_census(views + ((size_t)v * c->U + u) * HW, c->H, c->W, c->census_w,
-                      out + ((size_t)v * c->U + u) * HW);
+    size_t planes = (size_t)c->V * c->U * nchan(c);
+    for (size_t q = 0; q < planes; q++)
+        or_census(views + q * HW, c->H, c->W, c->census_w, out + q * HW);
 }
 
 /* ------------------------------------------------------ Initial views (Sec. III-D)
@@ -145,7 +148,8 @@ int or_arm_views(const or_cfg *c, int arm, int *uv)
 }
 
 /* Coarse census cost of one arm (Eq. 7, summed over the arm's views as in Eq. 15):
- *   C_a(p,k) = sum_{(u,v) in arm} HD(cen_ref(p), cen_uv(p + nearest shift at d_k)).
+ *   C_a(p,k) = sum_{(u,v) in arm} sum_ch HD(cen_ref,ch(p), cen_uv,ch(p + nearest shift at d_k)),
+ * the Hamming distances of the channels summed (Sec. III-B).
  * cen: census words of all views (or_census_all).  out: [H*W][Lc] int64.
  * Returns the number of views in the arm (0 = empty arm, out untouched). */
 int or_coarse_cost(const or_cfg *c, const uint64_t *cen, int arm, int64_t *out)
@@ -154,7 +158,8 @@ int or_coarse_cost(const or_cfg *c, const uint64_t *cen, int arm, int64_t *out)
     int nv = or_arm_views(c, arm, uv);
     if (nv == 0) return 0;
     size_t HW = (size_t)c->H * c->W;
-    const uint64_t *cref = cen + ((size_t)c->vc * c->U + c->uc) * HW;
+    const int Ch = nchan(c);
+    const uint64_t *cref = cen + ((size_t)c->vc * c->U + c->uc) * Ch * HW;
 #pragma omp parallel for schedule(static)
     for (int y = 0; y < c->H; y++)
         for (int x = 0; x < c->W; x++)
@@ -168,8 +173,9 @@ int or_coarse_cost(const or_cfg *c, const uint64_t *cen, int arm, int64_t *out)
                     or_shift(u - c->uc, d, &ox, &fx, &nx);
                     or_shift(v - c->vc, d, &oy, &fy, &ny);
                     int xx = clampi(x + nx, 0, c->W - 1), yy = clampi(y + ny, 0, c->H - 1);
-                    const uint64_t *cv = cen + ((size_t)v * c->U + u) * HW;
-                    sum += or_hamming(cref[(size_t)y * c->W + x], cv[(size_t)yy * c->W + xx]);
+                    const uint64_t *cv = cen + ((size_t)v * c->U + u) * Ch * HW;
+                    for (int ch = 0; ch < Ch; ch++)
+                        sum += or_hamming(cref[ch * HW + (size_t)y * c->W + x], cv[ch * HW + (size_t)yy * c->W + xx]);
                 }
                 out[((size_t)y * c->W + x) * c->Lc + k] = sum;
             }
@@ -386,9 +392,11 @@ void or_windows(const or_cfg *c, size_t N, const double *dinit, const uint8_t *e
 /* ----------------------------------------------- Fine cost volume (Eq. 12 + Eq. 15)
  * For every pixel p and fine label g in its window, over every view (u,v) except the
  * reference:
- *   S_l2 += | I_ref(p) - bilinear(I_uv, p + (u-uc, v-vc) * d_g) |   (Eq. 6, Eq. 12;
- *           for one channel the l2 norm of the difference is its absolute value)
- *   S_c  += HD(cen_ref(p), cen_uv(p + nearest shift))                (Eq. 4, Eq. 15)
+ *   S_l2 += || I_ref(p) - bilinear(I_uv, p + (u-uc, v-vc) * d_g) ||  (Eq. 6, Eq. 12:
+ *           the Euclidean norm over the channels, sqrt(sum_ch delta_ch^2); for one
+ *           channel it is written as the absolute value of the difference)
+ *   S_c  += sum_ch HD(cen_ref,ch(p), cen_uv,ch(p + nearest shift))   (Eq. 4, Eq. 15;
+ *           the channels' Hamming distances summed, Sec. III-B)
  *   C(p,g) = w_l2 * S_l2 + w_census * S_c.
  * Bilinear: (1-fy)[(1-fx) I(x0,y0) + fx I(x0+1,y0)] + fy[(1-fx) I(x0,y0+1) + fx I(x0+1,y0+1)]
  * with every tap index clamped.  Output: cost[off[p] + j] for slot j = g - lo[p]. */
@@ -396,8 +404,9 @@ void or_cost_volume(const or_cfg *c, const double *views, const uint64_t *cen,
                     const int32_t *lo, const int32_t *cnt, const int64_t *off, double *cost)
 {
     size_t HW = (size_t)c->H * c->W;
-    const double *Iref = views + ((size_t)c->vc * c->U + c->uc) * HW;
-    const uint64_t *cref = cen + ((size_t)c->vc * c->U + c->uc) * HW;
+    const int Ch = nchan(c);
+    const double *Iref = views + ((size_t)c->vc * c->U + c->uc) * Ch * HW;
+    const uint64_t *cref = cen + ((size_t)c->vc * c->U + c->uc) * Ch * HW;
 #pragma omp parallel for schedule(dynamic, 1)
     for (int y = 0; y < c->H; y++)
         for (int x = 0; x < c->W; x++) {
@@ -409,20 +418,27 @@ void or_cost_volume(const or_cfg *c, const double *views, const uint64_t *cen,
                 for (int v = 0; v < c->V; v++)
                     for (int u = 0; u < c->U; u++) {
                         if (u == c->uc && v == c->vc) continue;
-                        const double *I = views + ((size_t)v * c->U + u) * HW;
                         int ox, oy, nx, ny;
                         double fx, fy;
                         or_shift(u - c->uc, d, &ox, &fx, &nx);
                         or_shift(v - c->vc, d, &oy, &fy, &ny);
                         int x0 = clampi(x + ox, 0, c->W - 1), x1 = clampi(x + ox + 1, 0, c->W - 1);
                         int y0 = clampi(y + oy, 0, c->H - 1), y1 = clampi(y + oy + 1, 0, c->H - 1);
-                        double i00 = I[(size_t)y0 * c->W + x0], i10 = I[(size_t)y0 * c->W + x1];
-                        double i01 = I[(size_t)y1 * c->W + x0], i11 = I[(size_t)y1 * c->W + x1];
-                        double smp = (1.0 - fy) * ((1.0 - fx) * i00 + fx * i10)
-                                   + fy * ((1.0 - fx) * i01 + fx * i11);
-                        sl2 += fabs((double)Iref[p] - smp);
                         int xn = clampi(x + nx, 0, c->W - 1), yn = clampi(y + ny, 0, c->H - 1);
-                        sc += (double)or_hamming(cref[p], cen[((size_t)v * c->U + u) * HW + (size_t)yn * c->W + xn]);
+                        double sq = 0.0;
+                        for (int ch = 0; ch < Ch; ch++) {
+                            const double *I = views + (((size_t)v * c->U + u) * Ch + ch) * HW;
+                            double i00 = I[(size_t)y0 * c->W + x0], i10 = I[(size_t)y0 * c->W + x1];
+                            double i01 = I[(size_t)y1 * c->W + x0], i11 = I[(size_t)y1 * c->W + x1];
+                            double smp = (1.0 - fy) * ((1.0 - fx) * i00 + fx * i10)
+                                       + fy * ((1.0 - fx) * i01 + fx * i11);
+                            double delta = Iref[ch * HW + p] - smp;
+                            if (Ch == 1) sl2 += fabs(delta);
+                            else sq += delta * delta;
+                            sc += (double)or_hamming(cref[ch * HW + p],
+                                                     cen[(((size_t)v * c->U + u) * Ch + ch) * HW + (size_t)yn * c->W + xn]);
+                        }
+                        if (Ch > 1) sl2 += sqrt(sq);
                     }
                 cost[off[p] + j] = c->w_l2 * sl2 + c->w_census * sc;
             }
@@ -650,14 +666,17 @@ void or_sgm_bounded_path_backward(int H, int W, const int32_t *lo, const int32_t
 }
 
 /* Adjoint of the cost volume w.r.t. the views through the l2 term (Eq. 6, Eq. 12):
- *   d C / d I_ref(p) = w_l2 sum_v sign(I_ref(p) - B_v),  d C / d I_v(tap) = -w_l2 sign(.) w_tap,
- * sign(0) = 0, taps clamped as in the forward; the census term is piecewise constant (no gradient). */
+ *   d C / d I_ref,ch(p) = w_l2 sum_v e_ch,  d C / d I_v,ch(tap) = -w_l2 e_ch w_tap,
+ * with e = delta / ||delta|| the unit colour difference (delta = I_ref(p) - B_v over the
+ * channels; e = 0 where delta = 0), which for one channel is sign(delta); taps clamped as in
+ * the forward; the census term is piecewise constant (no gradient). */
 void or_cost_backward_views(const or_cfg *c, const double *views, const int32_t *lo, const int32_t *cnt,
                             const int64_t *off, const double *gcost, double *gviews)
 {
     size_t HW = (size_t)c->H * c->W;
-    const double *Iref = views + ((size_t)c->vc * c->U + c->uc) * HW;
-    double *gref = gviews + ((size_t)c->vc * c->U + c->uc) * HW;
+    const int Ch = nchan(c);
+    const double *Iref = views + ((size_t)c->vc * c->U + c->uc) * Ch * HW;
+    double *gref = gviews + ((size_t)c->vc * c->U + c->uc) * Ch * HW;
     for (int y = 0; y < c->H; y++)
         for (int x = 0; x < c->W; x++) {
             size_t p = (size_t)y * c->W + x;
@@ -668,24 +687,33 @@ void or_cost_backward_views(const or_cfg *c, const double *views, const int32_t 
                 for (int v = 0; v < c->V; v++)
                     for (int u = 0; u < c->U; u++) {
                         if (u == c->uc && v == c->vc) continue;
-                        const double *I = views + ((size_t)v * c->U + u) * HW;
-                        double *gI = gviews + ((size_t)v * c->U + u) * HW;
                         int ox, oy, nx, ny;
                         double fx, fy;
                         or_shift(u - c->uc, d, &ox, &fx, &nx);
                         or_shift(v - c->vc, d, &oy, &fy, &ny);
                         int x0 = clampi(x + ox, 0, c->W - 1), x1 = clampi(x + ox + 1, 0, c->W - 1);
                         int y0 = clampi(y + oy, 0, c->H - 1), y1 = clampi(y + oy + 1, 0, c->H - 1);
-                        double smp = (1.0 - fy) * ((1.0 - fx) * I[(size_t)y0 * c->W + x0] + fx * I[(size_t)y0 * c->W + x1])
-                                   + fy * ((1.0 - fx) * I[(size_t)y1 * c->W + x0] + fx * I[(size_t)y1 * c->W + x1]);
-                        double delta = Iref[p] - smp;
-                        double sg = delta > 0.0 ? 1.0 : (delta < 0.0 ? -1.0 : 0.0);
-                        double g = gcv * c->w_l2 * sg;
-                        gref[p] += g;
-                        gI[(size_t)y0 * c->W + x0] -= g * (1.0 - fy) * (1.0 - fx);
-                        gI[(size_t)y0 * c->W + x1] -= g * (1.0 - fy) * fx;
-                        gI[(size_t)y1 * c->W + x0] -= g * fy * (1.0 - fx);
-                        gI[(size_t)y1 * c->W + x1] -= g * fy * fx;
+                        double delta[4] = {0.0, 0.0, 0.0, 0.0}, sq = 0.0;
+                        for (int ch = 0; ch < Ch; ch++) {
+                            const double *I = views + (((size_t)v * c->U + u) * Ch + ch) * HW;
+                            double smp = (1.0 - fy) * ((1.0 - fx) * I[(size_t)y0 * c->W + x0] + fx * I[(size_t)y0 * c->W + x1])
+                                       + fy * ((1.0 - fx) * I[(size_t)y1 * c->W + x0] + fx * I[(size_t)y1 * c->W + x1]);
+                            delta[ch] = Iref[ch * HW + p] - smp;
+                            sq += delta[ch] * delta[ch];
+                        }
+                        double norm = sqrt(sq);
+                        for (int ch = 0; ch < Ch; ch++) {
+                            double e;
+                            if (Ch == 1) e = delta[0] > 0.0 ? 1.0 : (delta[0] < 0.0 ? -1.0 : 0.0);
+                            else e = norm > 0.0 ? delta[ch] / norm : 0.0;
+                            double g = gcv * c->w_l2 * e;
+                            double *gI = gviews + (((size_t)v * c->U + u) * Ch + ch) * HW;
+                            gref[ch * HW + p] += g;
+                            gI[(size_t)y0 * c->W + x0] -= g * (1.0 - fy) * (1.0 - fx);
+                            gI[(size_t)y0 * c->W + x1] -= g * (1.0 - fy) * fx;
+                            gI[(size_t)y1 * c->W + x0] -= g * fy * (1.0 - fx);
+                            gI[(size_t)y1 * c->W + x1] -= g * fy * fx;
+                        }
                     }
             }
         }
