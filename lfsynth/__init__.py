@@ -50,6 +50,8 @@ class LFParams:
     paths: int = 8              # SGM directions: 8, or the paper's 16 (Sec. IV-C)
     edge_threshold: float = 0.0 # Sobel edge exclusion from the borders (Sec. III-D); 0 = off
     channels: int = 1           # 1 (grey) or 3 (RGB: views[v][u][c][y][x])
+    boundless: int = 0          # 1: no initial map, every window is the whole range (Sec. IV-E)
+    fine_radius_far: int = 0    # > 0: lambda at d = dmin, moving linearly to fine_radius at dmax
     uc: int = -1
     vc: int = -1
     name: str = ""
@@ -209,10 +211,11 @@ def epfl_params(**kw) -> LFParams:
 def middlebury_params(**kw) -> LFParams:
     """Middlebury-shaped (Sec. IV-E): 7 views in a row (U=7, V=1) of a half-size 555x650 image,
     wide baseline (disparity in [0, 12] px per view step), census cost, boundary-less search
-    (every window is the whole range: the radius covers the grid), 64 coarse labels, 121 fine
-    labels by 0.1 px."""
+    (no initial map: every window is the whole range), 121 fine labels by 0.1 px (64 coarse
+    labels, unused)."""
     d = dict(U=7, V=1, H=555, W=650, census_w=7, dmin=0.0, dmax=12.0, coarse_labels=64,
-             fine_labels=121, fine_radius=121, w_l2=0.0, w_census=1.0, name="middlebury 7x1x555x650")
+             fine_labels=121, fine_radius=5, boundless=1, w_l2=0.0, w_census=1.0,
+             name="middlebury 7x1x555x650")
     d.update(kw)
     return LFParams(**d)
 
@@ -345,6 +348,8 @@ def random_views(U, V, H, W, seed=0, lo=0.0, hi=1.0, channels=1):
 
 
 WORKLOADS = {"tiny": tiny, "bench": bench, "plenoptic": plenoptic, "epfl": epfl, "middlebury": middlebury}
+PARAMS = {"tiny": tiny_params, "bench": bench_params, "plenoptic": plenoptic_params, "epfl": epfl_params,
+          "middlebury": middlebury_params}
 
 
 # ------------------------------------------------------------------ device-side rendering

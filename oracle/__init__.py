@@ -46,7 +46,8 @@ class Cfg(C.Structure):
                 ("dmin", C.c_double), ("dmax", C.c_double), ("Lc", C.c_int32),
                 ("init_views", C.c_int32), ("phi", C.c_double), ("fill_passes", C.c_int32),
                 ("G", C.c_int32), ("R", C.c_int32), ("w_l2", C.c_double), ("w_census", C.c_double),
-                ("paths", C.c_int32), ("edge_threshold", C.c_float), ("channels", C.c_int32)]
+                ("paths", C.c_int32), ("edge_threshold", C.c_float), ("channels", C.c_int32),
+                ("boundless", C.c_int32), ("R_far", C.c_int32)]
 
 
 def make_cfg(p) -> Cfg:
@@ -60,7 +61,8 @@ def make_cfg(p) -> Cfg:
                dmin=p.dmin, dmax=p.dmax, Lc=p.coarse_labels, init_views=p.init_views,
                phi=p.phi, fill_passes=p.fill_passes, G=p.fine_labels, R=p.fine_radius,
                w_l2=p.w_l2, w_census=p.w_census, paths=getattr(p, "paths", 8),
-               edge_threshold=getattr(p, "edge_threshold", 0.0), channels=channels)
+               edge_threshold=getattr(p, "edge_threshold", 0.0), channels=channels,
+               boundless=int(getattr(p, "boundless", 0)), R_far=int(getattr(p, "fine_radius_far", 0)))
 
 
 def _ptr(a, t):
@@ -98,6 +100,8 @@ def lib():
             L.or_fuse.argtypes = [C.c_size_t, C.c_int, P(C.c_int32), C.c_double, P(C.c_double)]
             L.or_hole_fill.argtypes = [C.c_int, C.c_int, C.c_int, P(C.c_double)]
             L.or_windows.argtypes = [P(Cfg), C.c_size_t, P(C.c_double), P(C.c_uint8), P(C.c_int32), P(C.c_int32)]
+            L.or_radius.restype = C.c_int
+            L.or_radius.argtypes = [P(Cfg), C.c_int64]
             L.or_sobel_edges.argtypes = [C.c_int, C.c_int, P(C.c_float), C.c_float, P(C.c_uint8)]
             L.or_cost_volume.argtypes = [P(Cfg), P(C.c_double), P(C.c_uint64), P(C.c_int32),
                                          P(C.c_int32), P(C.c_int64), P(C.c_double)]
@@ -218,6 +222,11 @@ def sobel_edges(I: np.ndarray, threshold: float) -> np.ndarray:
     return out.astype(bool)
 
 
+def radius(cfg: Cfg, gc: int) -> int:
+    """Border threshold lambda of a window centred on fine label gc (constant unless R_far > 0)."""
+    return int(lib().or_radius(C.byref(cfg), int(gc)))
+
+
 def windows(cfg: Cfg, dinit: np.ndarray, edge=None):
     d = np.ascontiguousarray(dinit, dtype=np.float64).reshape(-1)
     lo = np.zeros(d.size, np.int32)
@@ -308,6 +317,12 @@ def initial_disparity(cfg: Cfg, views: np.ndarray, penalties=None, p1f=0.05, p2f
     if cen is None:
         cen = census_all(cfg, views)
     H, W, N = cfg.H, cfg.W, cfg.H * cfg.W
+    if cfg.boundless:
+        # boundary-less search (Sec. IV-E): no initial map, every window is the whole range
+        nan = np.full(N, np.nan)
+        lo, cnt = windows(cfg, nan)
+        return {"maps": np.zeros((0, N), np.int32), "arms": [], "penalties": [], "fused": nan,
+                "dinit": nan, "lo": lo, "cnt": cnt, "census": cen}
     maps, pens, arms = [], [], []
     for arm in range(4):
         ca = coarse_cost(cfg, cen, arm)

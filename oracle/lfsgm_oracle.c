@@ -53,6 +53,8 @@ typedef struct {
     int32_t paths;        /* SGM directions: 8, or the paper's 16 (Sec. IV-C)           */
     float edge_threshold; /* Sobel edge exclusion (Sec. III-D): 0 = off                 */
     int32_t channels;     /* colour channels C: 1 or 3 (0 means 1)                      */
+    int32_t boundless;    /* 1: every window is the whole range, no initial map (Sec. IV-E) */
+    int32_t R_far;        /* > 0: border threshold at d = dmin (depth-dependent lambda)     */
 } or_cfg;
 
 static int clampi(int v, int lo, int hi) { return v < lo ? lo : (v > hi ? hi : v); }
@@ -372,16 +374,38 @@ void or_sobel_edges(int H, int W, const float *I, float t, uint8_t *edge)
         }
 }
 
-/* Borders (Eq. 11); `edge` (nullable): pixels excluded from the borders search the whole range. */
+/* floor(a / b) for b > 0 */
+static int64_t floordiv(int64_t a, int64_t b)
+{
+    int64_t q = a / b;
+    return (a % b != 0 && a < 0) ? q - 1 : q;
+}
+
+/* Border threshold lambda for a window centred on fine label gc.  Constant R (Eq. 11) unless
+ * R_far > 0: then lambda moves linearly from R_far at the far end of the range (gc = 0, d = dmin)
+ * to R at the near end (gc = G-1), rounded half up in exact integer arithmetic:
+ *   lambda(gc) = R + floor((2 (R_far - R)(G-1-gc) + (G-1)) / (2 (G-1))).
+ * The paper proposes a larger threshold for small disparities (Sec. IV-F) without a formula. */
+int or_radius(const or_cfg *c, int64_t gc)
+{
+    if (c->R_far <= 0) return c->R;
+    int64_t den = (int64_t)c->G - 1;
+    int64_t num = ((int64_t)c->R_far - c->R) * (den - gc);
+    return c->R + (int)floordiv(2 * num + den, 2 * den);
+}
+
+/* Borders (Eq. 11); `edge` (nullable): pixels excluded from the borders search the whole range;
+ * in the boundary-less mode (Sec. IV-E) every pixel does. */
 void or_windows(const or_cfg *c, size_t N, const double *dinit, const uint8_t *edge, int32_t *lo, int32_t *cnt)
 {
     for (size_t p = 0; p < N; p++) {
-        if (isnan(dinit[p]) || (edge && edge[p])) { lo[p] = 0; cnt[p] = c->G; continue; }
+        if (c->boundless || isnan(dinit[p]) || (edge && edge[p])) { lo[p] = 0; cnt[p] = c->G; continue; }
         int64_t m = (int64_t)(dinit[p] * 8.0);           /* exact: dinit is k/8 */
         int64_t num = m * (int64_t)(c->G - 1);
         int64_t den = 8 * (int64_t)(c->Lc - 1);
         int64_t gc = (2 * num + den) / (2 * den);
-        int64_t a = gc - c->R, b = gc + c->R;
+        int64_t R = or_radius(c, gc);
+        int64_t a = gc - R, b = gc + R;
         if (a < 0) a = 0;
         if (b > c->G - 1) b = c->G - 1;
         lo[p] = (int32_t)a;
