@@ -7,7 +7,7 @@ metric is the time of the cost volume + SGM stages per light field (the paper's 
 map stage, Sec. III-E); the full-step time is reported beside it.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                  [--workload bench|plenoptic|tiny]
+                  [--workload bench|plenoptic|tiny|epfl|middlebury] [--channels 1|3]
 
 Beside it: the training pattern (forward + hand-written backward, soft-argmin) and the
 serving pattern (64 mixed light fields as one CUDA-graph launch against sequential launches).
@@ -40,15 +40,15 @@ FP32_LANES_PER_SM = 128
 # DRAM bytes (read + write) per launch from one ncu capture of the bench workload, with the
 # SHA-256 prefix of the kernel's source at capture time; a changed source reports null.
 NCU_TRAFFIC = {
-    "fine_cost": {"bytes": 315813376, "source": "paper_1907_13449_gb300/csrc/k_fine_cost.cu",
+    "fine_cost": {"bytes": 315813376, "workload": "bench", "channels": 1, "source": "paper_1907_13449_gb300/csrc/k_fine_cost.cu",
                   "sha256_16": "fca9a7c0741d2296", "capture": "profiles/fine_cost_rows_bench_9x9x512x512.md"},
 }
 
 
-def ncu_traffic(kernel):
+def ncu_traffic(kernel, workload_name="bench", channels=1):
     import hashlib
     e = NCU_TRAFFIC.get(kernel)
-    if not e:
+    if not e or e["workload"] != workload_name or e["channels"] != channels:
         return None
     try:
         with open(os.path.join(ROOT, e["source"]), "rb") as f:
@@ -77,13 +77,16 @@ def dist_env():
     return ws, rank, local
 
 
-def workload(name, lf_index):
+def workload(name, lf_index, channels=1):
     import lfsynth
-    return lfsynth.WORKLOADS[name](lf_index)
+    if channels == 1:
+        return lfsynth.WORKLOADS[name](lf_index)
+    return lfsynth.WORKLOADS[name](lf_index, params=lfsynth.PARAMS[name](channels=channels))
 
 
 def workload_label(p):
-    return (f"{p.name}: {p.U}x{p.V} views of {p.H}x{p.W} f32, census {p.census_w}x{p.census_w}, "
+    colour = " RGB" if p.channels == 3 else ""
+    return (f"{p.name}: {p.U}x{p.V} views of {p.H}x{p.W}{colour} f32, census {p.census_w}x{p.census_w}, "
             f"coarse {p.coarse_labels} labels on [{p.dmin:g},{p.dmax:g}], fine window 2x{p.fine_radius}+1 "
             f"of {p.fine_labels} labels, {p.paths}-path SGM, parabolic sub-pixel")
 
@@ -148,16 +151,18 @@ def hbm_bytes_cost_sgm(p, nnz_active):
     writes its outputs once (views; window map lo/cnt/off 16 B per pixel per stage;
     cost written and read once; aggregated cost written once)."""
     N = p.H * p.W
-    views = p.U * p.V * N * 4
+    views = p.U * p.V * p.channels * N * 4
     cost = 4 * nnz_active
     return {"cost_volume": views + 16 * N + cost, "sgm_aggregate": 16 * N + cost + cost}
 
 
 def alu_ops_cost(p, nnz_active):
     """Algorithmic FP32 lane operations of the cost volume: per (active cell, non-reference
-    view) a bilinear sample (3 lerps, 2 ops each), the difference and its absolute-value
-    accumulation (2 ops)."""
-    return nnz_active * (p.U * p.V - 1) * 8
+    view, channel) a bilinear sample (3 lerps, 2 ops each), the difference and its absolute-value
+    accumulation, or for colour its squared accumulation (2 ops); colour adds one square root
+    per (cell, view)."""
+    per_view = 8 * p.channels + (1 if p.channels > 1 else 0)
+    return nnz_active * (p.U * p.V - 1) * per_view
 
 
 def max_over_ranks(vals, ws, device):
@@ -184,7 +189,7 @@ def run_ours(args, ws, rank, local):
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     lib = lf.load()
-    views_np, gt, p = workload(args.workload, rank)
+    views_np, gt, p = workload(args.workload, rank, args.channels)
     views = torch.from_numpy(views_np).to(dev)
     stream = torch.cuda.current_stream(dev)
     L = lf.LightFieldDepth(p, stream=stream, device=dev)
@@ -312,23 +317,25 @@ def run_ours(args, ws, rank, local):
     value = ms_per_lf(stage_ms, K, ws)          # whole-job ms per light field (cost+SGM)
     # dominant kernel of the cost+SGM stages and its roofline
     hot = ["fine_cost", "fine_sgm", "census_all", "cost_partial_sums", "zero_agg"]
+    if p.channels > 1:
+        hot.append("fine_cost_wide")      # colour: every window goes through the list kernel
     dom = max((k for k in kernels if k in hot), key=lambda k: kernels[k]["ms_total"])
     mhz = (clocks or {}).get("sm_mhz") or peaks.get("sm_max_mhz", 2070.0)
     by = hbm_bytes_cost_sgm(p, active)
-    if dom == "fine_cost":
+    if dom in ("fine_cost", "fine_cost_wide"):
         ops = alu_ops_cost(p, active)
         peak_ops = N_SM * FP32_LANES_PER_SM * mhz * 1e6
         ach = ops / (kernels[dom]["ms_avg"] * 1e-3)
         roof = {"kernel": dom, "bound": "alu", "achieved": round(ach / 1e12, 3),
                 "peak": round(peak_ops / 1e12, 3), "unit": "T FP32 lane-ops/s",
-                "frac": round(ach / peak_ops, 4), "traffic": ncu_traffic(dom),
+                "frac": round(ach / peak_ops, 4), "traffic": ncu_traffic(dom, args.workload, p.channels),
                 "algorithmic_bytes": by["cost_volume"],
                 "peak_basis": f"{N_SM} SMs x {FP32_LANES_PER_SM} FP32 lanes x {mhz:.0f} MHz (median SM clock under load)"}
     else:
         b = by["sgm_aggregate"] if dom == "fine_sgm" else by["cost_volume"]
         ach = b / (kernels[dom]["ms_avg"] * 1e-3) / 1e9
         roof = {"kernel": dom, "bound": "hbm", "achieved": round(ach, 1), "peak": peaks["hbm_gbs"],
-                "unit": "GB/s", "frac": round(ach / peaks["hbm_gbs"], 4), "traffic": ncu_traffic(dom)}
+                "unit": "GB/s", "frac": round(ach / peaks["hbm_gbs"], 4), "traffic": ncu_traffic(dom, args.workload, p.channels)}
     hbm_total = by["cost_volume"] + by["sgm_aggregate"]
     hbm_model = {"bytes_per_lf": hbm_total, "roofline_ms": round(hbm_total / (peaks["hbm_gbs"] * 1e9) * 1e3, 4),
                  "frac": round(hbm_total / (peaks["hbm_gbs"] * 1e9) * 1e3 / value, 4),
@@ -532,7 +539,7 @@ class OracleBand:
         import oracle
         if rows not in self.cache:
             p = self.p
-            band = np.ascontiguousarray(self.views_np[:, :, :rows, :])
+            band = np.ascontiguousarray(self.views_np[..., :rows, :])     # [V][U]([C])[rows][W]
             q = type(p)(**{**p.__dict__, "H": rows})
             cfg = oracle.make_cfg(q)
             init = oracle.initial_disparity(cfg, band, None, q.p1_frac, q.p2_frac)
@@ -583,7 +590,7 @@ def run_reference(args, ws, rank):
     if rank != 0:
         return None
     import oracle
-    views_np, gt, p = workload(args.workload, 0)
+    views_np, gt, p = workload(args.workload, 0, args.channels)
     ob = OracleBand(views_np, p)
     cal_rows = min(32, p.H)
     t_cal = ob.run(cal_rows)
@@ -618,6 +625,8 @@ def main():
     ap.add_argument("--batch-lfs", type=int, default=64, help="light fields in the mixed batch (0: skip)")
     ap.add_argument("--batch-branches", type=int, default=0, help="concurrent branches (0: autotune)")
     ap.add_argument("--no-backward", dest="backward", action="store_false")
+    ap.add_argument("--channels", type=int, default=1, choices=[1, 3],
+                    help="colour channels of the rendered light field (3: RGB, Sec. III-B/C)")
     args = ap.parse_args()
     ws, rank, local = dist_env()
     if args.impl == "reference":

@@ -9,9 +9,10 @@
  * Argument errors are returned at once; errors detected inside kernels are latched
  * in a device status word and returned by lfsgm_sync.  Nothing traps or aborts.
  *
- * Notation.  views[v][u][y][x] float32, contiguous: (x,y) spatial position in a view
- * (the paper's (u,v)), (u,v) angular position of the view (the paper's (s,t)),
- * reference view (uc,vc).  A view (u,v) is sampled for pixel (x,y) and disparity d at
+ * Notation.  views[v][u][c][y][x] float32, contiguous: (x,y) spatial position in a view
+ * (the paper's (u,v)), (u,v) angular position of the view (the paper's (s,t)), c the colour
+ * channel (cfg.channels = C: 1 grey, then views[v][u][y][x]; or 3 RGB), reference view
+ * (uc,vc).  A view (u,v) is sampled for pixel (x,y) and disparity d at
  *     (x + (u-uc) d, y + (v-vc) d)                      (Sec. III-A, Eq. 1)
  * (the paper writes (s^-s) d: our d has the opposite sign, larger d = nearer).
  * Labels: coarse k in [0,Lc) and fine g in [0,G) on inclusive grids over [dmin,dmax]:
@@ -71,7 +72,18 @@ typedef struct {
                                   slopes 1/2 and 2; 0 is read as 8                            */
     float   edge_threshold;    /* Sobel edge exclusion from the borders (Sec. III-D): pixels of
                                   the reference view with gx^2 + gy^2 > t^2 (FP32, 3 x 3 Sobel,
-                                  clamped) search the whole range; 0 = off                    */
+                                  clamped) search the whole range; 0 = off.  Colour: a pixel is
+                                  an edge when it is one in any channel                       */
+    int32_t channels;          /* colour channels C: 1 (grey) or 3 (RGB, Sec. III-B/C: census per
+                                  channel with the Hamming distances summed, l2 the Euclidean
+                                  norm of the colour difference); 0 is read as 1              */
+    int32_t boundless;         /* 1: boundary-less search (Sec. IV-E): no initial map, every
+                                  window is the whole range T; 0: bounded (Eq. 11)            */
+    int32_t fine_radius_far;   /* > 0: depth-dependent border threshold (Sec. IV-F proposes a
+                                  larger one for small disparities): lambda moves linearly from
+                                  fine_radius_far at d = dmin to fine_radius at d = dmax,
+                                  lambda(gc) = R + floor((2 (Rfar-R)(G-1-gc) + G-1) / (2 (G-1)))
+                                  for the window centre gc; <= 0: constant fine_radius         */
 } lfsgm_config;
 
 /* Create a handle for one light-field shape.  `stream` is a cudaStream_t (NULL = the
@@ -94,7 +106,9 @@ lfsgm_status lfsgm_max_nnz(lfsgm_handle h, int64_t *nnz);
  * (Eq. 7 summed over the arm's views), integer SGM per arm over cfg.paths paths (Eq. 8-9),
  * WTA per arm (Eq. 10), sequential fusion with threshold phi, median hole filling,
  * borders D_init +- lambda saturated to T (Eq. 11; discarded pixels: whole range).
- *   views  [V][U][H][W] float32
+ * Boundary-less mode (cfg.boundless): only the windows are written (lo = 0, cnt = G), dinit is
+ * NaN everywhere and maps is left untouched; no census or coarse work is done.
+ *   views  [V][U][C][H][W] float32
  *   Pc1, Pc2  integer coarse penalties; Pc1 <= 0 -> per arm round(p*_frac * mean arm
  *             cost) with P1 >= 1, P2 >= P1.
  *   lo, cnt   [H*W] int32 out: window first fine label and label count
@@ -110,9 +124,10 @@ lfsgm_status lfsgm_initial_disparity(lfsgm_handle h, const float *views, int32_t
 
 /* Bounded fine cost volume (Sec. III-E, Eq. 12 and Eq. 15) over every view but the
  * reference, for the labels of each pixel's window:
- *   C(p,g) = w_l2 * sum |I_ref(p) - bilinear(I_uv, p + (u-uc, v-vc) d_g)|
- *          + w_census * sum HD(census_ref(p), census_uv(p + nearest shift)).
- *   views [V][U][H][W] float32; lo, cnt, off as produced above; cost [off[N]] float32 out. */
+ *   C(p,g) = w_l2 * sum || I_ref(p) - bilinear(I_uv, p + (u-uc, v-vc) d_g) ||
+ *          + w_census * sum sum_c HD(census_ref,c(p), census_uv,c(p + nearest shift)),
+ * the norm over the C channels (for C = 1 the absolute difference).
+ *   views [V][U][C][H][W] float32; lo, cnt, off as produced above; cost [off[N]] float32 out. */
 lfsgm_status lfsgm_cost_volume(lfsgm_handle h, const float *views, const int32_t *lo,
                                const int32_t *cnt, const int64_t *off, float *cost);
 
@@ -142,7 +157,8 @@ lfsgm_status lfsgm_median_filter(lfsgm_handle h, const float *disp, float *out);
 /* Adjoint of cost volume -> SGM -> soft-argmin (not in the paper).  Given grad_disp
  * = dLoss/d disp of the soft-argmin output, returns dLoss/d cost (grad_cost, CSR like
  * cost), dLoss/dP1 and dLoss/dP2 (device scalars) and dLoss/d views through the l2 term
- * and its bilinear weights (grad_views [V][U][H][W]; the census term has no gradient).
+ * and its bilinear weights (grad_views [V][U][C][H][W]; the census term has no gradient; for C > 1
+ * the l2 term's gradient is w_l2 times the unit colour difference, 0 where the colours agree).
  * Path costs are recomputed per direction; subgradients follow the recorded argmin.
  * grad_views may be NULL (then only grad_cost and the penalty gradients are formed). */
 lfsgm_status lfsgm_backward(lfsgm_handle h, const float *views, const float *cost,
@@ -170,7 +186,7 @@ lfsgm_status lfsgm_kernel_times(lfsgm_handle h, const char **names, float *ms, i
  * runs initial disparity, cost volume, SGM (derived penalties) and WTA/sub-pixel,
  * copies disp (and label when non-NULL) device->host, and synchronises.  Device
  * buffers are owned by the handle and allocated on first use.
- *   views_host [V][U][H][W] float32 (pinned memory gives full copy speed)
+ *   views_host [V][U][C][H][W] float32 (pinned memory gives full copy speed)
  *   disp_host [H*W] float32, label_host [H*W] int32 (nullable). */
 lfsgm_status lfsgm_depth_host(lfsgm_handle h, const float *views_host, float *disp_host,
                               int32_t *label_host);
@@ -180,7 +196,7 @@ lfsgm_status lfsgm_depth_host(lfsgm_handle h, const float *views_host, float *di
 lfsgm_status lfsgm_depth(lfsgm_handle h, const float *views, float *disp, int32_t *label);
 
 /* Batches (not in the paper): n light fields of mixed shape run as ONE CUDA-graph launch.
- * Each light field i has its own configuration cfgs[i], views[i] ([V][U][H][W] float32, device)
+ * Each light field i has its own configuration cfgs[i], views[i] ([V][U][C][H][W] float32, device)
  * and output disp[i] ([H*W] float32, device); the pointers are baked into the graph at creation.
  * The pipeline of lfsgm_depth (derived penalties) runs for every light field; light fields are
  * spread over `branches` concurrent streams forked from `stream` (longest work first), branches
@@ -210,7 +226,8 @@ lfsgm_status lfsgm_batch_destroy(lfsgm_batch b);
  * is one static device array of 32 MiB that every GPU loading this library holds until
  * the process exits.  It serves light fields with
  *     256 + round256(4 U V) + round256(16 U V G) + 8 U V H W <= 32 MiB
- * (e.g. 5x5 views of 64x64 .. 256x256) and returns LFSGM_ERR_UNSUPPORTED beyond that.
+ * (e.g. 5x5 views of 64x64 .. 256x256) and returns LFSGM_ERR_UNSUPPORTED beyond that and
+ * for colour light fields (channels > 1).
  * The first call on each device resolves the array's device address (cudaGetSymbolAddress,
  * with that device current): make that first call before any stream capture.  All calls
  * share the array, so calls that overlap on the GPU (two streams, or two host threads at

@@ -41,18 +41,21 @@ class Config(C.Structure):
                 ("fine_labels", C.c_int32), ("fine_radius", C.c_int32), ("w_l2", C.c_float),
                 ("w_census", C.c_float), ("p1_frac", C.c_double), ("p2_frac", C.c_double),
                 ("subpixel", C.c_int32), ("softmin_tau", C.c_float), ("paths", C.c_int32),
-                ("edge_threshold", C.c_float)]
+                ("edge_threshold", C.c_float), ("channels", C.c_int32), ("boundless", C.c_int32),
+                ("fine_radius_far", C.c_int32)]
 
 
 def make_config(p) -> Config:
-    """``Config`` from any object carrying the method's parameter names."""
+    """``Config`` from any object carrying the method's parameter names (views are
+    [V][U][H][W] for one channel, [V][U][C][H][W] for ``channels`` = 3)."""
     return Config(U=p.U, V=p.V, H=p.H, W=p.W, uc=getattr(p, "uc", -1), vc=getattr(p, "vc", -1),
                   census_w=p.census_w, dmin=p.dmin, dmax=p.dmax, coarse_labels=p.coarse_labels,
                   init_views=p.init_views, phi=p.phi, fill_passes=p.fill_passes,
                   fine_labels=p.fine_labels, fine_radius=p.fine_radius, w_l2=p.w_l2,
                   w_census=p.w_census, p1_frac=p.p1_frac, p2_frac=p.p2_frac, subpixel=p.subpixel,
                   softmin_tau=p.softmin_tau, paths=getattr(p, "paths", 8),
-                  edge_threshold=getattr(p, "edge_threshold", 0.0))
+                  edge_threshold=getattr(p, "edge_threshold", 0.0), channels=getattr(p, "channels", 1),
+                  boundless=getattr(p, "boundless", 0), fine_radius_far=getattr(p, "fine_radius_far", 0))
 
 
 EXPORTS = ["lfsgm_create", "lfsgm_destroy", "lfsgm_workspace_size", "lfsgm_set_workspace",
@@ -288,7 +291,8 @@ def lfsgm_cost_volume_noalloc(cfg, views, lo, cnt, off, cost, stream=None):
         _ptr(cost, torch.float32, "cost"))
     if st != OK:
         raise LfsgmError(st, "lfsgm_cost_volume_noalloc: " + {1: "invalid config or null buffer",
-                                                              5: "light field too large for the static scratch",
+                                                              5: "light field too large for the static scratch"
+                                                                 " (or in colour)",
                                                               4: "CUDA error"}.get(st, ""))
 
 

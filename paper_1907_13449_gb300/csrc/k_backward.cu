@@ -266,6 +266,10 @@ __global__ void __launch_bounds__(32 * kBwdWarps) sgm_backward_kernel(
 // reference pixel and -g * (bilinear weight) to the four taps.  Lanes whose labels share a
 // bilinear cell form contiguous runs (the integer shift is monotone in the label), so a segmented
 // shuffle sum leaves each run's total in its first lane, which issues the four atomics.
+// Colour (C > 1; images are planes view * C + c): the l2 term is the Euclidean norm of the colour
+// difference delta, so channel c takes g_c = dLoss/dC * w_l2 * delta_c / ||delta|| (0 where
+// delta = 0), and each channel's four taps are summed over the run the same way.
+template <int C>
 __global__ void __launch_bounds__(256) views_backward_kernel(const float *__restrict__ views,
                                                              const FineTap *__restrict__ tab, int G, int nviews,
                                                              int H, int W, int ref, const int *__restrict__ lo,
@@ -287,28 +291,42 @@ __global__ void __launch_bounds__(256) views_backward_kernel(const float *__rest
         const int j = chunk * 32 + lane;
         const bool act = j < n;
         const int x = p % W, y = p / W;
-        const float Iref = __ldg(views + (size_t)ref * N + p);
+        float Iref[C], gref[C];
+#pragma unroll
+        for (int ch = 0; ch < C; ch++) {
+            Iref[ch] = __ldg(views + ((size_t)ref * C + ch) * N + p);
+            gref[ch] = 0.f;
+        }
         const float gc = act ? wl2 * __ldg(gcost + o + j) : 0.f;
-        float gref = 0.f;
         for (int vi = 0; vi < nviews - 1; vi++) {
             const int view = vi + (vi >= ref);
             FineTap t;
             t.ox = t.oy = 0;
             t.fx = t.fy = 0.f;
             if (act) t = load_tap(tab + (size_t)view * G + l0 + j);
-            const float *I = views + (size_t)view * N;
             const int x0 = min(max(x + t.ox, 0), W - 1), x1 = min(max(x + t.ox + 1, 0), W - 1);
             const int y0 = min(max(y + t.oy, 0), H - 1), y1 = min(max(y + t.oy + 1, 0), H - 1);
-            float g = 0.f;
+            float g[C];
+#pragma unroll
+            for (int ch = 0; ch < C; ch++) g[ch] = 0.f;
             if (act && gc != 0.f) {
-                const float top = (1.f - t.fx) * __ldg(I + y0 * W + x0) + t.fx * __ldg(I + y0 * W + x1);
-                const float bot = (1.f - t.fx) * __ldg(I + y1 * W + x0) + t.fx * __ldg(I + y1 * W + x1);
-                const float d = Iref - ((1.f - t.fy) * top + t.fy * bot);
-                g = d > 0.f ? gc : (d < 0.f ? -gc : 0.f);
+                float dl[C], sq = 0.f;
+#pragma unroll
+                for (int ch = 0; ch < C; ch++) {
+                    const float *I = views + ((size_t)view * C + ch) * N;
+                    const float top = (1.f - t.fx) * __ldg(I + y0 * W + x0) + t.fx * __ldg(I + y0 * W + x1);
+                    const float bot = (1.f - t.fx) * __ldg(I + y1 * W + x0) + t.fx * __ldg(I + y1 * W + x1);
+                    dl[ch] = Iref[ch] - ((1.f - t.fy) * top + t.fy * bot);
+                    sq = fmaf(dl[ch], dl[ch], sq);
+                }
+                if (C == 1) {
+                    g[0] = dl[0] > 0.f ? gc : (dl[0] < 0.f ? -gc : 0.f);
+                } else if (sq > 0.f) {
+                    const float nrm = sqrtf(sq);
+#pragma unroll
+                    for (int ch = 0; ch < C; ch++) g[ch] = gc * (dl[ch] / nrm);
+                }
             }
-            gref += g;
-            float a00 = -g * (1.f - t.fy) * (1.f - t.fx), a10 = -g * (1.f - t.fy) * t.fx;
-            float a01 = -g * t.fy * (1.f - t.fx), a11 = -g * t.fy * t.fx;
             // runs of equal bilinear cells; inactive lanes (the chunk's tail) form their own run
             const int key = act ? (((int)t.oy << 16) ^ ((int)t.ox & 0xffff)) : 0x7fffffff;
             const int kprev = __shfl_up_sync(0xffffffffu, key, 1);
@@ -317,28 +335,37 @@ __global__ void __launch_bounds__(256) views_backward_kernel(const float *__rest
             const unsigned later = lane == 31 ? 0u : (heads & (0xfffffffeu << lane));
             const int end = later ? __ffs(later) - 2 : 31;
 #pragma unroll
-            for (int d = 1; d < 32; d <<= 1) {
-                const float b00 = __shfl_down_sync(0xffffffffu, a00, d);
-                const float b10 = __shfl_down_sync(0xffffffffu, a10, d);
-                const float b01 = __shfl_down_sync(0xffffffffu, a01, d);
-                const float b11 = __shfl_down_sync(0xffffffffu, a11, d);
-                if (lane + d <= end) {
-                    a00 += b00;
-                    a10 += b10;
-                    a01 += b01;
-                    a11 += b11;
+            for (int ch = 0; ch < C; ch++) {
+                gref[ch] += g[ch];
+                float a00 = -g[ch] * (1.f - t.fy) * (1.f - t.fx), a10 = -g[ch] * (1.f - t.fy) * t.fx;
+                float a01 = -g[ch] * t.fy * (1.f - t.fx), a11 = -g[ch] * t.fy * t.fx;
+#pragma unroll
+                for (int d = 1; d < 32; d <<= 1) {
+                    const float b00 = __shfl_down_sync(0xffffffffu, a00, d);
+                    const float b10 = __shfl_down_sync(0xffffffffu, a10, d);
+                    const float b01 = __shfl_down_sync(0xffffffffu, a01, d);
+                    const float b11 = __shfl_down_sync(0xffffffffu, a11, d);
+                    if (lane + d <= end) {
+                        a00 += b00;
+                        a10 += b10;
+                        a01 += b01;
+                        a11 += b11;
+                    }
+                }
+                if (head && act) {
+                    float *gI = gviews + ((size_t)view * C + ch) * N;
+                    if (a00 != 0.f) atomicAdd(gI + y0 * W + x0, a00);
+                    if (a10 != 0.f) atomicAdd(gI + y0 * W + x1, a10);
+                    if (a01 != 0.f) atomicAdd(gI + y1 * W + x0, a01);
+                    if (a11 != 0.f) atomicAdd(gI + y1 * W + x1, a11);
                 }
             }
-            if (head && act) {
-                float *gI = gviews + (size_t)view * N;
-                if (a00 != 0.f) atomicAdd(gI + y0 * W + x0, a00);
-                if (a10 != 0.f) atomicAdd(gI + y0 * W + x1, a10);
-                if (a01 != 0.f) atomicAdd(gI + y1 * W + x0, a01);
-                if (a11 != 0.f) atomicAdd(gI + y1 * W + x1, a11);
-            }
         }
-        gref = warp_sum(gref);
-        if (lane == 0 && gref != 0.f) atomicAdd(gviews + (size_t)ref * N + p, gref);
+#pragma unroll
+        for (int ch = 0; ch < C; ch++) {
+            const float gr = warp_sum(gref[ch]);
+            if (lane == 0 && gr != 0.f) atomicAdd(gviews + ((size_t)ref * C + ch) * N + p, gr);
+        }
     }
 }
 
@@ -493,20 +520,26 @@ cudaError_t launch_sgm_backward(cudaStream_t s, const float *cost, const int *lo
     return cudaGetLastError();
 }
 
-cudaError_t launch_views_backward(cudaStream_t s, const float *views, const FineTap *tab, int G, int nviews, int H,
-                                  int W, int ref, const int *lo, const int *cnt, const long long *off, float wl2,
-                                  const float *gcost, float *gviews, const int2 *list, const int *count) {
+cudaError_t launch_views_backward(cudaStream_t s, const float *views, const FineTap *tab, int G, int nviews, int C,
+                                  int H, int W, int ref, const int *lo, const int *cnt, const long long *off,
+                                  float wl2, const float *gcost, float *gviews, const int2 *list, const int *count) {
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (C == 3) {
+        // colour: the list holds every window's chunks
+        views_backward_kernel<3><<<sms * 8, 256, 0, s>>>(views, tab, G, nviews, H, W, ref, lo, cnt, off, wl2, gcost,
+                                                         gviews, list, count);
+        return cudaGetLastError();
+    }
     dim3 grid((W + 31) / 32, (H + kVbRows - 1) / kVbRows);
     views_backward_tile_kernel<<<grid, 32 * kVbRows, 0, s>>>(views, tab, G, nviews, H, W, ref, lo, cnt, off, wl2, gcost,
                                                              gviews);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     // windows wider than 32 labels (the list holds their chunks)
-    int dev = 0, sms = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    views_backward_kernel<<<sms * 8, 256, 0, s>>>(views, tab, G, nviews, H, W, ref, lo, cnt, off, wl2, gcost, gviews,
-                                                  list, count);
+    views_backward_kernel<1><<<sms * 8, 256, 0, s>>>(views, tab, G, nviews, H, W, ref, lo, cnt, off, wl2, gcost, gviews,
+                                                     list, count);
     return cudaGetLastError();
 }
 

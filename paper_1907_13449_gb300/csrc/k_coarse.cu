@@ -80,12 +80,13 @@ __device__ __forceinline__ void load_offsets(const int *p, int *o) {
 
 // Eq. 7 per arm: C_a(p, k) = sum over the arm's views of the Hamming distance between the
 // reference census word at p and the view's word at p + n(view, k) (nearest shift, clamped --
-// the padded census repeats the border words, so the linear offset needs no clamping).  A warp
+// the padded census repeats the border words, so the linear offset needs no clamping), summed
+// over the C colour channels (census planes view * C + c; Sec. III-B).  A warp
 // takes a run of RUN = 32 / LPT pixels; views are the outer loop, so a view's label offsets are
 // read once and the RUN x LPT census loads of the view are independent of each other.
 template <int LPT>
 __global__ void __launch_bounds__(128) coarse_cost_kernel(const uint64_t *__restrict__ cen_pad, size_t HWp, int Wp,
-                                                          int P, int H, int W, int ref,
+                                                          int P, int H, int W, int ref, int C,
                                                           const int *__restrict__ armviews,
                                                           const int *__restrict__ otab, CoarseArms ca, int Lc,
                                                           int Lcd, uint16_t *__restrict__ out,
@@ -107,23 +108,25 @@ __global__ void __launch_bounds__(128) coarse_cost_kernel(const uint64_t *__rest
     const size_t rowoff = (size_t)(y + P) * Wp + P + xs;
     unsigned long long total = 0;
     if (act) {
-        uint64_t r[RUN];
-        const uint64_t *refrow = cen_pad + (size_t)ref * HWp + rowoff;
-#pragma unroll
-        for (int i = 0; i < RUN; i++) r[i] = __ldg(refrow + i);     // padded: in bounds past W too
         int c[RUN][LPT];
 #pragma unroll
         for (int i = 0; i < RUN; i++)
 #pragma unroll
             for (int j = 0; j < LPT; j++) c[i][j] = 0;
-        for (int v = 0; v < nv; v++) {
-            const uint64_t *base = cen_pad + (size_t)__ldg(views + v) * HWp + rowoff;
-            int o[LPT];
-            load_offsets<LPT>(ot + v * Lcd, o);
+        for (int ch = 0; ch < C; ch++) {
+            uint64_t r[RUN];
+            const uint64_t *refrow = cen_pad + ((size_t)ref * C + ch) * HWp + rowoff;
 #pragma unroll
-            for (int i = 0; i < RUN; i++)
+            for (int i = 0; i < RUN; i++) r[i] = __ldg(refrow + i);     // padded: in bounds past W too
+            for (int v = 0; v < nv; v++) {
+                const uint64_t *base = cen_pad + ((size_t)__ldg(views + v) * C + ch) * HWp + rowoff;
+                int o[LPT];
+                load_offsets<LPT>(ot + v * Lcd, o);
 #pragma unroll
-                for (int j = 0; j < LPT; j++) c[i][j] += __popcll(r[i] ^ __ldg(base + i + o[j]));
+                for (int i = 0; i < RUN; i++)
+#pragma unroll
+                    for (int j = 0; j < LPT; j++) c[i][j] += __popcll(r[i] ^ __ldg(base + i + o[j]));
+            }
         }
         uint16_t *O = out + ((size_t)a * N + (size_t)y * W + xs) * Lcd + k0;
 #pragma unroll
@@ -327,7 +330,7 @@ int coarse_stride(int Lc) {
     return (Lc + q - 1) / q * q;
 }
 
-cudaError_t launch_coarse_cost(cudaStream_t s, const uint64_t *cen_pad, int P, int Wp, int Hp, int H, int W, int ref,
+cudaError_t launch_coarse_cost(cudaStream_t s, const uint64_t *cen_pad, int P, int Wp, int Hp, int H, int W, int ref, int C,
                                const int *armviews, const int *otab, const CoarseArms &ca, int Lc,
                                uint16_t *out, unsigned long long *armsum) {
     const int Lcd = coarse_stride(Lc);
@@ -336,9 +339,9 @@ cudaError_t launch_coarse_cost(cudaStream_t s, const uint64_t *cen_pad, int P, i
     const long long tasks = (long long)((W + run - 1) / run) * H;
     dim3 grid((unsigned)((tasks + 3) / 4), (unsigned)ca.n_arms);
     switch (coarse_lpt(Lc)) {
-    case 2: coarse_cost_kernel<2><<<grid, 128, 0, s>>>(cen_pad, HWp, Wp, P, H, W, ref, armviews, otab, ca, Lc, Lcd, out, armsum); break;
-    case 4: coarse_cost_kernel<4><<<grid, 128, 0, s>>>(cen_pad, HWp, Wp, P, H, W, ref, armviews, otab, ca, Lc, Lcd, out, armsum); break;
-    default: coarse_cost_kernel<8><<<grid, 128, 0, s>>>(cen_pad, HWp, Wp, P, H, W, ref, armviews, otab, ca, Lc, Lcd, out, armsum); break;
+    case 2: coarse_cost_kernel<2><<<grid, 128, 0, s>>>(cen_pad, HWp, Wp, P, H, W, ref, C, armviews, otab, ca, Lc, Lcd, out, armsum); break;
+    case 4: coarse_cost_kernel<4><<<grid, 128, 0, s>>>(cen_pad, HWp, Wp, P, H, W, ref, C, armviews, otab, ca, Lc, Lcd, out, armsum); break;
+    default: coarse_cost_kernel<8><<<grid, 128, 0, s>>>(cen_pad, HWp, Wp, P, H, W, ref, C, armviews, otab, ca, Lc, Lcd, out, armsum); break;
     }
     return cudaGetLastError();
 }

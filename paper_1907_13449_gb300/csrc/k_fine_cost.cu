@@ -323,9 +323,12 @@ __global__ void __launch_bounds__(128, 4) fine_cost_rows(const __grid_constant__
 // (no clamping needed) at linear offsets (oy Wp + ox, ny Wp + nx) from a table of the handle.  The chunk's table entries arrive by bulk copies on a per-warp mbarrier,
 // kListVB views (up to 32 x 16 bytes each) per stage and two stages, so the taps of the next
 // views are in flight while the current ones are sampled; waits are bounded (on expiry
-// LFSGM_ERR_TIMEOUT is latched).
+// LFSGM_ERR_TIMEOUT is latched).  Colour (C > 1): the images are planes view * C + c; each tap
+// samples every channel, the l2 term is the Euclidean norm of the colour difference and the
+// census term sums the channels' Hamming distances (Sec. III-B/C).
 constexpr int kListWarps = 4, kListVB = 8;
 
+template <int C>
 __global__ void __launch_bounds__(32 * kListWarps) fine_cost_list(const float *__restrict__ views_pad,
                                                       const uint64_t *__restrict__ cen_pad, int P, int Wp, int Hp,
                                                       const int4 *__restrict__ ltab, int G, int nviews,
@@ -376,8 +379,13 @@ __global__ void __launch_bounds__(32 * kListWarps) fine_cost_list(const float *_
         };
         const int x = p % W, y = p / W;
         const size_t base = (size_t)(y + P) * Wp + (x + P);
-        const float Iref = __ldg(views_pad + (size_t)ref * HWp + base);
-        const uint64_t cr = __ldg(cen_pad + (size_t)ref * HWp + base);
+        float Iref[C];
+        uint64_t cr[C];
+#pragma unroll
+        for (int ch = 0; ch < C; ch++) {
+            Iref[ch] = __ldg(views_pad + ((size_t)ref * C + ch) * HWp + base);
+            cr[ch] = __ldg(cen_pad + ((size_t)ref * C + ch) * HWp + base);
+        }
         float sl2 = 0.f;
         int sc = 0;
         issue(0, 0);
@@ -398,16 +406,22 @@ __global__ void __launch_bounds__(32 * kListWarps) fine_cost_list(const float *_
 #pragma unroll 4
                 for (int k = 0; k < vn; k++) {
                     const int vi = b * kListVB + k;
-                    const size_t vb = (size_t)(vi + (vi >= ref)) * HWp + base;
+                    const size_t vb = (size_t)(vi + (vi >= ref)) * C * HWp + base;
                     const int4 tw = taps[w][st][k][lane];     // linear tap offsets (x + Wp y), fx, fy
                     const float tfx = __int_as_float(tw.z), tfy = __int_as_float(tw.w);
-                    const float *q = views_pad + vb + tw.x;
-                    const float i00 = __ldg(q), i10 = __ldg(q + 1), i01 = __ldg(q + Wp), i11 = __ldg(q + Wp + 1);
-                    const float top = (1.f - tfx) * i00 + tfx * i10;
-                    const float bot = (1.f - tfx) * i01 + tfx * i11;
-                    const float smp = (1.f - tfy) * top + tfy * bot;
-                    sl2 += fabsf(Iref - smp);
-                    sc += __popcll(cr ^ __ldg(cen_pad + vb + tw.y));
+                    float sq = 0.f;
+#pragma unroll
+                    for (int ch = 0; ch < C; ch++) {
+                        const float *q = views_pad + vb + ch * HWp + tw.x;
+                        const float i00 = __ldg(q), i10 = __ldg(q + 1), i01 = __ldg(q + Wp), i11 = __ldg(q + Wp + 1);
+                        const float top = (1.f - tfx) * i00 + tfx * i10;
+                        const float bot = (1.f - tfx) * i01 + tfx * i11;
+                        const float dl = Iref[ch] - ((1.f - tfy) * top + tfy * bot);
+                        if (C == 1) sl2 += fabsf(dl);
+                        else sq = fmaf(dl, dl, sq);
+                        sc += __popcll(cr[ch] ^ __ldg(cen_pad + vb + ch * HWp + tw.y));
+                    }
+                    if (C > 1) sl2 += sqrtf(sq);
                 }
             }
             __syncwarp();          // the stage is refilled two batches later
@@ -603,14 +617,18 @@ cudaError_t launch_list_all(cudaStream_t s, const int *lo, const int *cnt, const
 }
 
 cudaError_t launch_fine_cost_list(cudaStream_t s, const float *views_pad, const uint64_t *cen_pad, int P, int Wp,
-                                  int Hp, const int4 *ltab, int G, int nviews, int H, int W, int ref, const int *lo,
-                                  const int *cnt, const long long *off, float wl2, float wc, float *cost,
-                                  const int2 *list, const int *count, int *status) {
+                                  int Hp, const int4 *ltab, int G, int nviews, int C, int H, int W, int ref,
+                                  const int *lo, const int *cnt, const long long *off, float wl2, float wc,
+                                  float *cost, const int2 *list, const int *count, int *status) {
     int dev = 0, sms = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    fine_cost_list<<<sms * 12, 32 * kListWarps, 0, s>>>(views_pad, cen_pad, P, Wp, Hp, ltab, G, nviews, H, W, ref, lo,
-                                                       cnt, off, wl2, wc, cost, list, count, status);
+    if (C == 3)
+        fine_cost_list<3><<<sms * 12, 32 * kListWarps, 0, s>>>(views_pad, cen_pad, P, Wp, Hp, ltab, G, nviews, H, W,
+                                                              ref, lo, cnt, off, wl2, wc, cost, list, count, status);
+    else
+        fine_cost_list<1><<<sms * 12, 32 * kListWarps, 0, s>>>(views_pad, cen_pad, P, Wp, Hp, ltab, G, nviews, H, W,
+                                                              ref, lo, cnt, off, wl2, wc, cost, list, count, status);
     return cudaGetLastError();
 }
 

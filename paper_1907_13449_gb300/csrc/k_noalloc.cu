@@ -105,6 +105,7 @@ extern "C" lfsgm_status lfsgm_cost_volume_noalloc(const lfsgm_config *cfg, void 
         !std::isfinite(c.w_l2) || !std::isfinite(c.w_census) ||
         std::fmax(std::fabs(c.dmin), std::fabs(c.dmax)) * (c.U > c.V ? c.U : c.V) > 30000.0)
         return LFSGM_ERR_INVALID_ARG;
+    if (c.channels != 0 && c.channels != 1) return c.channels == 3 ? LFSGM_ERR_UNSUPPORTED : LFSGM_ERR_INVALID_ARG;
     const size_t nviews = (size_t)c.U * c.V, N = (size_t)c.H * c.W, G = (size_t)c.fine_labels;
     // scratch layout: status word | view list | shift table | census words of every view
     const size_t o_sel = 256, o_tab = o_sel + round256(nviews * 4), o_cen = o_tab + round256(nviews * G * 16);

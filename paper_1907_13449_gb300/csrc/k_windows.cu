@@ -49,7 +49,10 @@ __global__ void fill_kernel(const int *__restrict__ Fin, int *__restrict__ Fout,
 }
 
 // Borders (Eq. 11): nearest fine label gc = round_half_up(m (G-1) / (8 (Lc-1))), window
-// [gc - R, gc + R] saturated to [0, G-1]; a discarded pixel gets the whole range.
+// [gc - R, gc + R] saturated to [0, G-1]; a discarded pixel gets the whole range, and so does
+// every pixel in the boundary-less mode (Sec. IV-E; F is not read).  Rfar > 0 makes the
+// threshold depth-dependent (Sec. IV-F proposes a larger one for small disparities): linear from
+// Rfar at gc = 0 to R at gc = G-1, R(gc) = R + floor((2 (Rfar - R)(G-1-gc) + G-1) / (2 (G-1))).
 // Edge test of the border exclusion (Sec. III-D) on the edge-padded reference view (a padded read
 // is the clamped read): the 3 x 3 Sobel sums, their squares and the comparison in FP32 with
 // explicit rounding, in the order the oracle uses, so both take the same decision.
@@ -66,11 +69,17 @@ __device__ __forceinline__ bool sobel_edge(const float *I, int Wp, float t) {
 
 __global__ void windows_kernel(const int *__restrict__ F, int N, int G, int Lc, int R, int *__restrict__ lo,
                                int *__restrict__ cnt, float *__restrict__ dinit, int *__restrict__ cntpad,
-                               const float *__restrict__ ref_pad, int P, int Wp, int W, float edge_t) {
+                               const float *__restrict__ ref_pad, int C, size_t HWp, int P, int Wp, int W,
+                               float edge_t, int Rfar, int boundless) {
     const int p = blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= N) return;
-    const int v = F[p];
-    const bool edge = edge_t > 0.f && sobel_edge(ref_pad + (size_t)(p / W + P) * Wp + (p % W + P), Wp, edge_t);
+    const int v = boundless ? -1 : F[p];
+    // an edge in any channel of the reference view (its C padded planes, HWp apart)
+    bool edge = false;
+    if (edge_t > 0.f && !boundless) {
+        const float *q = ref_pad + (size_t)(p / W + P) * Wp + (p % W + P);
+        for (int ch = 0; ch < C && !edge; ch++) edge = sobel_edge(q + ch * HWp, Wp, edge_t);
+    }
     int a, n;
     if (v < 0 || edge) {
         a = 0;
@@ -80,7 +89,14 @@ __global__ void windows_kernel(const int *__restrict__ F, int N, int G, int Lc, 
         const long long num = (long long)v * (G - 1);
         const long long den = 8LL * (Lc - 1);
         const long long gc = (2 * num + den) / (2 * den);
-        long long lo_ = gc - R, hi_ = gc + R;
+        long long r = R;
+        if (Rfar > 0) {
+            const long long dg = G - 1, t = 2 * (long long)(Rfar - R) * (dg - gc) + dg;
+            long long q = t / (2 * dg);
+            if (t % (2 * dg) != 0 && t < 0) q--;          // floor division
+            r = R + q;
+        }
+        long long lo_ = gc - r, hi_ = gc + r;
         if (lo_ < 0) lo_ = 0;
         if (hi_ > G - 1) hi_ = G - 1;
         a = (int)lo_;
@@ -169,9 +185,10 @@ cudaError_t launch_fill(cudaStream_t s, const int *Fin, int *Fout, int H, int W)
     return cudaGetLastError();
 }
 cudaError_t launch_windows(cudaStream_t s, const int *F, int N, int G, int Lc, int R, int *lo, int *cnt,
-                           float *dinit, int *cntpad, const float *ref_pad, int P, int Wp, int W, float edge_t) {
-    windows_kernel<<<(N + 255) / 256, 256, 0, s>>>(F, N, G, Lc, R, lo, cnt, dinit, cntpad, ref_pad, P, Wp, W,
-                                                   edge_t);
+                           float *dinit, int *cntpad, const float *ref_pad, int C, size_t HWp, int P, int Wp,
+                           int W, float edge_t, int Rfar, int boundless) {
+    windows_kernel<<<(N + 255) / 256, 256, 0, s>>>(F, N, G, Lc, R, lo, cnt, dinit, cntpad, ref_pad, C, HWp, P, Wp,
+                                                   W, edge_t, Rfar, boundless);
     return cudaGetLastError();
 }
 int scan_tiles(int N) { return (N + kScanTile - 1) / kScanTile; }

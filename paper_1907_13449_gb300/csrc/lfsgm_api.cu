@@ -52,6 +52,7 @@ struct lfsgm_ctx {
     lfsgm_config cfg{};
     cudaStream_t stream = nullptr;
     int N = 0, nviews = 0, ref = 0, nbits = 0, Lcd = 0;
+    int C = 1;                            // colour channels; images are planes view * C + c
     ArmList arms{};
     // device tables
     FineTap *d_fine = nullptr;
@@ -61,9 +62,9 @@ struct lfsgm_ctx {
     int *d_otab = nullptr;       // coarse census offsets per (arm view, label), see CoarseArms
     CoarseArms ca{};
     int *d_armviews = nullptr;   // [4][kMaxArmViews]
-    int *d_sel_cross = nullptr;  // reference + arm views
+    int *d_sel_cross = nullptr;  // planes of the reference and the arm views
     int n_sel_cross = 0;
-    int *d_sel_all = nullptr;    // every view
+    int *d_sel_all = nullptr;    // planes of every view
     // workspace
     void *ws = nullptr;
     size_t ws_bytes = 0;
@@ -173,6 +174,9 @@ lfsgm_status validate(const lfsgm_config &c, char *why, size_t n) {
     if (c.subpixel < 0 || c.subpixel > 2) BAD("subpixel must be 0, 1 or 2");
     if (!(c.softmin_tau > 0.f)) BAD("softmin_tau must be > 0");
     if (c.paths != 0 && c.paths != 8 && c.paths != 16) BAD("paths must be 8 or 16");
+    if (c.channels != 0 && c.channels != 1 && c.channels != 3) BAD("channels must be 1 or 3");
+    if (c.boundless != 0 && c.boundless != 1) BAD("boundless must be 0 or 1");
+    if (c.fine_radius_far > 0 && c.fine_radius < 0) BAD("fine_radius must be >= 0");
     if (!(c.edge_threshold >= 0.f) || !std::isfinite(c.edge_threshold)) BAD("edge_threshold must be finite and >= 0");
     const double md = std::fmax(std::fabs(c.dmin), std::fabs(c.dmax));
     if (md * (std::max(c.U, c.V)) > 30000.0) BAD("shifts exceed the 16-bit table range");
@@ -242,8 +246,8 @@ lfsgm_status bind_workspace(lfsgm_ctx *h, void *dptr, size_t bytes, bool owned) 
     // the status word comes first, so handles that share one workspace (a batch branch) share it
     h->status = (int *)take(4);
     const size_t HWp = (size_t)h->rows.Hp * h->rows.Wp;
-    h->cen_pad = (uint64_t *)take(h->nviews * HWp * 8);
-    h->views_pad = (float *)take(h->nviews * HWp * 4);
+    h->cen_pad = (uint64_t *)take((size_t)h->nviews * h->C * HWp * 8);
+    h->views_pad = (float *)take((size_t)h->nviews * h->C * HWp * 4);
     h->rows_maps = h->rows.ok && encode_fine_rows_maps(&h->rows, h->views_pad, h->cen_pad, h->nviews);
     h->ccost = (uint16_t *)take(A * N * h->Lcd * 2);
     h->csum = (uint16_t *)take(A * N * h->Lcd * 2);
@@ -271,6 +275,7 @@ lfsgm_status lfsgm_create(const lfsgm_config *cfg, void *stream, lfsgm_handle *o
     *out = nullptr;
     lfsgm_config c = *cfg;
     if (c.paths == 0) c.paths = 8;
+    if (c.channels == 0) c.channels = 1;
     if (c.uc < 0) c.uc = (c.U - 1) / 2;
     if (c.vc < 0) c.vc = (c.V - 1) / 2;
     char why[256];
@@ -283,15 +288,16 @@ lfsgm_status lfsgm_create(const lfsgm_config *cfg, void *stream, lfsgm_handle *o
     h->stream = (cudaStream_t)stream;
     h->N = c.H * c.W;
     h->nviews = c.U * c.V;
+    h->C = c.channels;
     h->ref = c.vc * c.U + c.uc;
     h->nbits = c.census_w * c.census_w - 1;
     h->Lcd = coarse_stride(c.coarse_labels);
     plan_fine_rows(c.U, c.V, c.uc, c.vc, c.H, c.W, c.fine_labels, c.dmin, c.dmax, &h->rows);
     build_arms(h);
     // the packed coarse sums hold (paths) x (C + P2) per 16-bit half
-    const long long cmax = (long long)max_arm_views(h) * h->nbits;
+    const long long cmax = (long long)max_arm_views(h) * h->nbits * h->C;
     const long long p2max = (long long)std::floor(c.p2_frac * (double)cmax + 0.5);
-    if ((long long)c.paths * (cmax + std::max(p2max, 1LL)) >= 65536) {
+    if (!c.boundless && (long long)c.paths * (cmax + std::max(p2max, 1LL)) >= 65536) {
         g_create_err = "coarse path sums would overflow 16 bits (too many arm views x census bits)";
         delete h;
         return LFSGM_ERR_UNSUPPORTED;
@@ -323,13 +329,16 @@ lfsgm_status lfsgm_create(const lfsgm_config *cfg, void *stream, lfsgm_handle *o
             }
         }
     std::vector<int> armviews(4 * kMaxArmViews, 0), sel_cross, sel_all;
-    sel_cross.push_back(h->ref);
+    auto planes_of = [&](std::vector<int> &sel, int view) {
+        for (int ch = 0; ch < h->C; ch++) sel.push_back(view * h->C + ch);
+    };
+    planes_of(sel_cross, h->ref);
     for (int a = 0; a < h->arms.n_arms; a++)
         for (int i = 0; i < h->arms.nv[a]; i++) {
             armviews[a * kMaxArmViews + i] = h->arms.views[a][i];
-            sel_cross.push_back(h->arms.views[a][i]);
+            planes_of(sel_cross, h->arms.views[a][i]);
         }
-    for (int i = 0; i < h->nviews; i++) sel_all.push_back(i);
+    for (int i = 0; i < h->nviews; i++) planes_of(sel_all, i);
     // per arm: [nv][Lcd] linear offsets ny * Wp + nx of the nearest coarse shifts (0 = padding)
     std::vector<int> otab;
     h->ca.n_arms = h->arms.n_arms;
@@ -371,6 +380,7 @@ lfsgm_status lfsgm_create(const lfsgm_config *cfg, void *stream, lfsgm_handle *o
         }
         ALLOC_COPY(h->d_ltab, ltab);
     }
+    if (h->C > 1) h->rows.ok = false;   // colour: every window through the list kernel
     if (h->rows.ok) {
         std::vector<unsigned char> desc;
         const float fstep = (float)((c.dmax - c.dmin) / (double)(c.fine_labels - 1));
@@ -416,8 +426,8 @@ lfsgm_status lfsgm_workspace_size(lfsgm_handle h, size_t *bytes) {
     const size_t N = (size_t)h->N, A = (size_t)std::max(h->arms.n_arms, 1);
     size_t b = 0;
     const size_t HWp = (size_t)h->rows.Hp * h->rows.Wp;
-    b += align256(h->nviews * HWp * 8);            // census words, edge-replicated padding
-    b += align256(h->nviews * HWp * 4);            // views, edge-replicated padding
+    b += align256((size_t)h->nviews * h->C * HWp * 8);   // census words per plane, edge-replicated padding
+    b += align256((size_t)h->nviews * h->C * HWp * 4);   // views per plane, edge-replicated padding
     b += align256(A * N * h->Lcd * 2);              // coarse cost
     b += align256(A * N * h->Lcd * 2);              // coarse path sums
     b += align256(4 * N * 4);                       // maps
@@ -448,43 +458,48 @@ lfsgm_status lfsgm_initial_disparity(lfsgm_handle h, const float *views, int32_t
     if (!h) return LFSGM_ERR_INVALID_ARG;
     if (!views || !lo || !cnt || !off) return fail(h, LFSGM_ERR_INVALID_ARG, "null buffer");
     if (Pc1 > 0 && Pc2 < Pc1) return fail(h, LFSGM_ERR_INVALID_ARG, "need P2 >= P1 (Eq. 8)");
-    if (Pc1 > 0 && 8LL * ((long long)max_arm_views(h) * h->nbits + Pc2) >= 65536)
+    if (Pc1 > 0 && (long long)h->cfg.paths * ((long long)max_arm_views(h) * h->nbits * h->C + Pc2) >= 65536)
         return fail(h, LFSGM_ERR_UNSUPPORTED, "coarse P2 too large for 16-bit path sums");
     LFSGM_TRY(ensure_workspace(h));
     const lfsgm_config &c = h->cfg;
     cudaStream_t s = h->stream;
     const int N = h->N, A = h->arms.n_arms;
-    LFSGM_TRY(run(h, "census_cross", [&] {
-        return launch_census_pad(s, views, c.H, c.W, c.census_w, h->rows.P, h->rows.Wp, h->rows.Hp, h->d_sel_cross,
-                                 h->n_sel_cross, h->cen_pad, h->views_pad);
-    }));
-    cudaError_t e = cudaMemsetAsync(h->armsum, 0, 4 * 8, s);
-    if (e == cudaSuccess) e = cudaMemsetAsync(h->csum, 0, (size_t)A * N * h->Lcd * 2, s);
-    if (e != cudaSuccess) return cuda_fail(h, e, "memset");
-    LFSGM_TRY(run(h, "coarse_cost", [&] {
-        return launch_coarse_cost(s, h->cen_pad, h->rows.P, h->rows.Wp, h->rows.Hp, c.H, c.W, h->ref, h->d_armviews,
-                                  h->d_otab, h->ca, c.coarse_labels, h->ccost, h->armsum);
-    }));
-    LFSGM_TRY(run(h, "coarse_penalties", [&] {
-        return launch_coarse_penalties(s, h->armsum, A, (long long)N * c.coarse_labels, c.p1_frac, c.p2_frac,
-                                       Pc1, Pc2, h->cpen);
-    }));
-    LFSGM_TRY(run(h, "coarse_sgm", [&] {
-        return launch_coarse_sgm(s, h->ccost, A, c.H, c.W, c.coarse_labels, h->cpen, h->csum, h->d_order, c.paths);
-    }));
-    LFSGM_TRY(run(h, "coarse_wta", [&] {
-        return launch_coarse_wta(s, h->csum, A, N, c.coarse_labels, h->maps, maps);
-    }));
-    LFSGM_TRY(run(h, "fuse", [&] { return launch_fuse(s, h->maps, A, N, c.phi, h->F0); }));
     int *fin = h->F0, *fout = h->F1;
-    for (int it = 0; it < c.fill_passes; it++) {
-        LFSGM_TRY(run(h, "hole_fill", [&] { return launch_fill(s, fin, fout, c.H, c.W); }));
-        std::swap(fin, fout);
+    cudaError_t e = cudaSuccess;
+    if (!c.boundless) {   // boundary-less: no initial map, the windows kernel writes whole-range windows
+        LFSGM_TRY(run(h, "census_cross", [&] {
+            return launch_census_pad(s, views, c.H, c.W, c.census_w, h->rows.P, h->rows.Wp, h->rows.Hp,
+                                     h->d_sel_cross, h->n_sel_cross, h->cen_pad, h->views_pad);
+        }));
+        e = cudaMemsetAsync(h->armsum, 0, 4 * 8, s);
+        if (e == cudaSuccess) e = cudaMemsetAsync(h->csum, 0, (size_t)A * N * h->Lcd * 2, s);
+        if (e != cudaSuccess) return cuda_fail(h, e, "memset");
+        LFSGM_TRY(run(h, "coarse_cost", [&] {
+            return launch_coarse_cost(s, h->cen_pad, h->rows.P, h->rows.Wp, h->rows.Hp, c.H, c.W, h->ref, h->C,
+                                      h->d_armviews, h->d_otab, h->ca, c.coarse_labels, h->ccost, h->armsum);
+        }));
+        LFSGM_TRY(run(h, "coarse_penalties", [&] {
+            return launch_coarse_penalties(s, h->armsum, A, (long long)N * c.coarse_labels, c.p1_frac, c.p2_frac,
+                                           Pc1, Pc2, h->cpen);
+        }));
+        LFSGM_TRY(run(h, "coarse_sgm", [&] {
+            return launch_coarse_sgm(s, h->ccost, A, c.H, c.W, c.coarse_labels, h->cpen, h->csum, h->d_order,
+                                     c.paths);
+        }));
+        LFSGM_TRY(run(h, "coarse_wta", [&] {
+            return launch_coarse_wta(s, h->csum, A, N, c.coarse_labels, h->maps, maps);
+        }));
+        LFSGM_TRY(run(h, "fuse", [&] { return launch_fuse(s, h->maps, A, N, c.phi, h->F0); }));
+        for (int it = 0; it < c.fill_passes; it++) {
+            LFSGM_TRY(run(h, "hole_fill", [&] { return launch_fill(s, fin, fout, c.H, c.W); }));
+            std::swap(fin, fout);
+        }
     }
     LFSGM_TRY(run(h, "windows", [&] {
         return launch_windows(s, fin, N, c.fine_labels, c.coarse_labels, c.fine_radius, lo, cnt, dinit, h->cntpad,
-                              h->views_pad + (size_t)h->ref * h->rows.Hp * h->rows.Wp, h->rows.P, h->rows.Wp,
-                              c.W, c.edge_threshold);
+                              h->views_pad + (size_t)h->ref * h->C * h->rows.Hp * h->rows.Wp, h->C,
+                              (size_t)h->rows.Hp * h->rows.Wp, h->rows.P, h->rows.Wp, c.W, c.edge_threshold,
+                              c.fine_radius_far, c.boundless);
     }));
     LFSGM_TRY(run(h, "scan_sums", [&] { return launch_scan_sums(s, h->cntpad, N, h->tsum); }));
     LFSGM_TRY(run(h, "scan_top", [&] { return launch_scan_top(s, h->tsum, N); }));
@@ -506,7 +521,7 @@ lfsgm_status lfsgm_cost_volume(lfsgm_handle h, const float *views, const int32_t
     cudaStream_t s = h->stream;
     LFSGM_TRY(run(h, "census_all", [&] {
         return launch_census_pad(s, views, c.H, c.W, c.census_w, h->rows.P, h->rows.Wp, h->rows.Hp, h->d_sel_all,
-                                 h->nviews, h->cen_pad, h->views_pad);
+                                 h->nviews * h->C, h->cen_pad, h->views_pad);
     }));
     const cudaError_t e = cudaMemsetAsync(h->wide_count, 0, 4, s);
     if (e != cudaSuccess) return cuda_fail(h, e, "memset");
@@ -526,8 +541,8 @@ lfsgm_status lfsgm_cost_volume(lfsgm_handle h, const float *views, const int32_t
     }
     LFSGM_TRY(run(h, "fine_cost_wide", [&] {
         return launch_fine_cost_list(s, h->views_pad, h->cen_pad, h->rows.P, h->rows.Wp, h->rows.Hp, h->d_ltab, c.fine_labels,
-                                     h->nviews, c.H, c.W, h->ref, lo, cnt, (const long long *)off, c.w_l2, c.w_census,
-                                     cost, h->wide_list, h->wide_count, h->status);
+                                     h->nviews, h->C, c.H, c.W, h->ref, lo, cnt, (const long long *)off, c.w_l2,
+                                     c.w_census, cost, h->wide_list, h->wide_count, h->status);
     }));
     return LFSGM_OK;
 }
@@ -635,7 +650,7 @@ lfsgm_status lfsgm_backward(lfsgm_handle h, const float *views, const float *cos
                                           grad_disp, h->b_gcs, grad_cost, h->status);
     }));
     cudaError_t e = cudaMemsetAsync(h->b_gp, 0, 8, s);
-    if (e == cudaSuccess && grad_views) e = cudaMemsetAsync(grad_views, 0, (size_t)h->nviews * N * 4, s);
+    if (e == cudaSuccess && grad_views) e = cudaMemsetAsync(grad_views, 0, (size_t)h->nviews * h->C * N * 4, s);
     if (e != cudaSuccess) return cuda_fail(h, e, "memset");
     LFSGM_TRY(run(h, "sgm_backward", [&] {
         return launch_sgm_backward(s, cost, lo, cnt, o, c.H, c.W, c.fine_labels, P1, P2, h->b_gcs, h->b_codes,
@@ -643,14 +658,16 @@ lfsgm_status lfsgm_backward(lfsgm_handle h, const float *views, const float *cos
     }));
     if (grad_views) {
         // the (pixel, 32-label chunk) items of windows wider than 32 labels; narrower ones by tiles
+        // (grey); colour windows all go through the item list
         e = cudaMemsetAsync(h->wide_count, 0, 4, s);
         if (e != cudaSuccess) return cuda_fail(h, e, "memset");
         LFSGM_TRY(run(h, "list_all", [&] {
-            return launch_list_all(s, lo, cnt, o, c.fine_labels, h->wide_list, h->wide_count, h->N, h->status, 32);
+            return launch_list_all(s, lo, cnt, o, c.fine_labels, h->wide_list, h->wide_count, h->N, h->status,
+                                   h->C > 1 ? 0 : 32);
         }));
         LFSGM_TRY(run(h, "views_backward", [&] {
-            return launch_views_backward(s, views, h->d_fine, c.fine_labels, h->nviews, c.H, c.W, h->ref, lo, cnt, o,
-                                         c.w_l2, grad_cost, grad_views, h->wide_list, h->wide_count);
+            return launch_views_backward(s, views, h->d_fine, c.fine_labels, h->nviews, h->C, c.H, c.W, h->ref, lo,
+                                         cnt, o, c.w_l2, grad_cost, grad_views, h->wide_list, h->wide_count);
         }));
     }
     e = cudaMemcpyAsync(grad_P1, h->b_gp, 4, cudaMemcpyDeviceToDevice, s);
@@ -732,7 +749,7 @@ lfsgm_status lfsgm_depth(lfsgm_handle h, const float *views, float *disp, int32_
 lfsgm_status lfsgm_depth_host(lfsgm_handle h, const float *views_host, float *disp_host, int32_t *label_host) {
     if (!h) return LFSGM_ERR_INVALID_ARG;
     if (!views_host || !disp_host) return fail(h, LFSGM_ERR_INVALID_ARG, "null host buffer");
-    const size_t N = (size_t)h->N, vbytes = (size_t)h->nviews * N * 4;
+    const size_t N = (size_t)h->N, vbytes = (size_t)h->nviews * h->C * N * 4;
     if (!h->o_views) {
         const cudaError_t e = cudaMalloc((void **)&h->o_views, vbytes);
         if (e != cudaSuccess) return fail(h, LFSGM_ERR_NO_MEMORY, "views buffer: %s", cudaGetErrorString(e));
@@ -975,7 +992,7 @@ lfsgm_status lfsgm_batch_create(int32_t n, const lfsgm_config *cfgs, const float
         b->views.push_back(views[i]);
         b->disp.push_back(disp[i]);
         const lfsgm_config &c = h->cfg;
-        b->work.push_back((double)h->N * ((double)h->nviews * (2 * c.fine_radius + 1) + 4.0 * c.coarse_labels));
+        b->work.push_back((double)h->N * ((double)h->nviews * h->C * (2 * c.fine_radius + 1) + 4.0 * c.coarse_labels));
     }
     cudaError_t e = cudaMalloc((void **)&b->stamps, (1 + 2 * (size_t)n) * 8);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming);

@@ -133,8 +133,9 @@ struct CoarseArms {
 };
 int coarse_lpt(int Lc);       // labels per lane: 2, 4, 8 for Lc <= 64, 128, 256
 int coarse_stride(int Lc);    // Lcd: label stride of the coarse cost and sums
+// Images are planes view * C + c of H x W (padded: Hp x Wp); `ref` and `armviews` count views.
 cudaError_t launch_coarse_cost(cudaStream_t s, const uint64_t *cen_pad, int P, int Wp, int Hp, int H, int W, int ref,
-                               const int *armviews, const int *otab, const CoarseArms &ca, int Lc,
+                               int C, const int *armviews, const int *otab, const CoarseArms &ca, int Lc,
                                uint16_t *out, unsigned long long *armsum);
 cudaError_t launch_coarse_penalties(cudaStream_t s, const unsigned long long *sums, int narms,
                                     long long count, double p1f, double p2f, int P1, int P2,
@@ -147,8 +148,8 @@ cudaError_t launch_coarse_wta(cudaStream_t s, const uint16_t *sum, int narms, in
 cudaError_t launch_fuse(cudaStream_t s, const int *maps, int narms, int N, double phi, int *F);
 cudaError_t launch_fill(cudaStream_t s, const int *Fin, int *Fout, int H, int W);
 cudaError_t launch_windows(cudaStream_t s, const int *F, int N, int G, int Lc, int R, int *lo,
-                           int *cnt, float *dinit, int *cntpad, const float *ref_pad, int P, int Wp, int W,
-                           float edge_t);
+                           int *cnt, float *dinit, int *cntpad, const float *ref_pad, int C, size_t HWp, int P,
+                           int Wp, int W, float edge_t, int Rfar, int boundless);
 int scan_tiles(int N);   // tiles of the offset scan (tile sums buffer length)
 cudaError_t launch_scan_sums(cudaStream_t s, const int *cntpad, int N, long long *tsum);
 cudaError_t launch_scan_top(cudaStream_t s, long long *tsum, int N);
@@ -181,7 +182,7 @@ cudaError_t launch_fine_cost_rows(cudaStream_t s, const RowPlanHost *ph, const f
 cudaError_t launch_list_all(cudaStream_t s, const int *lo, const int *cnt, const long long *off, int G,
                             int2 *list, int *count, int N, int *status, int min_cnt = 0);
 cudaError_t launch_fine_cost_list(cudaStream_t s, const float *views_pad, const uint64_t *cen_pad, int P, int Wp,
-                                  int Hp, const int4 *ltab, int G, int nviews, int H, int W, int ref,
+                                  int Hp, const int4 *ltab, int G, int nviews, int C, int H, int W, int ref,
                                   const int *lo, const int *cnt, const long long *off, float wl2,
                                   float wc, float *cost, const int2 *list, const int *count, int *status);
 
@@ -207,7 +208,7 @@ cudaError_t launch_sgm_backward(cudaStream_t s, const float *cost, const int *lo
                                 const long long *off, int H, int W, int G, float P1, float P2, const float *gCs,
                                 unsigned char *codes, int *amin, size_t nnz_cap, float *gcost, float *gP,
                                 int *status, const int *order, int paths);
-cudaError_t launch_views_backward(cudaStream_t s, const float *views, const FineTap *tab, int G, int nviews,
+cudaError_t launch_views_backward(cudaStream_t s, const float *views, const FineTap *tab, int G, int nviews, int C,
                                   int H, int W, int ref, const int *lo, const int *cnt, const long long *off,
                                   float wl2, const float *gcost, float *gviews, const int2 *list, const int *count);
 

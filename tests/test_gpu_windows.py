@@ -1,0 +1,52 @@
+"""Window variants on the GPU against the oracle, through the C ABI: the depth-dependent border
+threshold (Sec. IV-F; windows bit-exact) and the boundary-less search (Sec. IV-E; no initial map,
+every window the whole range)."""
+import dataclasses
+
+import numpy as np
+import pytest
+
+import lfsynth
+import oracle
+from test_gpu_parity import _check_end_to_end, _check_initial, _gpu_depth, _run_initial
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.mark.parametrize("radii", [(2, 8), (8, 2), (5, 5), (0, 12)])
+def test_depth_dependent_radius_windows_bitexact(gpu_lib, radii):
+    R, R_far = radii
+    views, _, p = lfsynth.tiny(params=lfsynth.tiny_params(fine_radius=R, fine_radius_far=R_far))
+    cfg = oracle.make_cfg(p)
+    ref = oracle.initial_disparity(cfg, views, None, p.p1_frac, p.p2_frac)
+    g = _run_initial(gpu_lib, p, views)
+    _check_initial(g, ref, p)
+    if R != R_far:
+        assert len(np.unique(ref["cnt"][ref["cnt"] < p.fine_labels])) > 2     # the radius varies
+
+
+def test_depth_dependent_radius_end_to_end(gpu_lib):
+    views, _, p = lfsynth.tiny(1, params=lfsynth.tiny_params(fine_radius=3, fine_radius_far=9))
+    ref = oracle.depth(oracle.make_cfg(p), views, p1f=p.p1_frac, p2f=p.p2_frac)
+    g_label, g_disp, _ = _gpu_depth(gpu_lib, p, views)
+    _check_end_to_end(g_label, g_disp, ref, p)
+
+
+def test_boundless_initial_pass_writes_whole_range_windows_only(gpu_lib):
+    views, _, p = lfsynth.tiny(params=lfsynth.tiny_params(boundless=1, edge_threshold=1.5))
+    g = _run_initial(gpu_lib, p, views)
+    assert np.all(g["lo"] == 0) and np.all(g["cnt"] == p.fine_labels)
+    assert np.all(np.isnan(g["dinit"]))
+    assert np.all(g["maps"] == -7)                     # untouched
+    ref = oracle.initial_disparity(oracle.make_cfg(p), views, None, p.p1_frac, p.p2_frac)
+    _check_initial(g, ref, p)
+
+
+def test_boundless_depth_matches_oracle_with_fewer_launches(gpu_lib):
+    views, _, p = lfsynth.tiny(2, params=lfsynth.tiny_params(H=48, W=56))
+    pb = dataclasses.replace(p, boundless=1)
+    ref = oracle.depth(oracle.make_cfg(pb), views, p1f=p.p1_frac, p2f=p.p2_frac)
+    g_label, g_disp, n_free = _gpu_depth(gpu_lib, pb, views)
+    _check_end_to_end(g_label, g_disp, ref, pb)
+    _, _, n_bounded = _gpu_depth(gpu_lib, p, views)
+    assert n_free < n_bounded - 5                      # no census / coarse cost / SGM / WTA / fill
