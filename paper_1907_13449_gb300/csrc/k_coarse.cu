@@ -31,6 +31,7 @@ struct CVec<2> {
         c[1] = w >> 16;
     }
     __device__ static T pack(const int *c) { return (uint32_t)c[0] | ((uint32_t)c[1] << 16); }
+    __device__ static T fill(uint32_t w) { return w; }
 };
 template <>
 struct CVec<4> {
@@ -44,6 +45,7 @@ struct CVec<4> {
     __device__ static T pack(const int *c) {
         return make_uint2((uint32_t)c[0] | ((uint32_t)c[1] << 16), (uint32_t)c[2] | ((uint32_t)c[3] << 16));
     }
+    __device__ static T fill(uint32_t w) { return make_uint2(w, w); }
 };
 template <>
 struct CVec<8> {
@@ -62,83 +64,81 @@ struct CVec<8> {
         return make_uint4((uint32_t)c[0] | ((uint32_t)c[1] << 16), (uint32_t)c[2] | ((uint32_t)c[3] << 16),
                           (uint32_t)c[4] | ((uint32_t)c[5] << 16), (uint32_t)c[6] | ((uint32_t)c[7] << 16));
     }
+    __device__ static T fill(uint32_t w) { return make_uint4(w, w, w, w); }
 };
-
-template <int LPT>
-__device__ __forceinline__ void load_offsets(const int *p, int *o) {
-    if constexpr (LPT == 2) {
-        const int2 v = __ldg(reinterpret_cast<const int2 *>(p));
-        o[0] = v.x; o[1] = v.y;
-    } else {
-#pragma unroll
-        for (int j = 0; j < LPT; j += 4) {
-            const int4 v = __ldg(reinterpret_cast<const int4 *>(p + j));
-            o[j] = v.x; o[j + 1] = v.y; o[j + 2] = v.z; o[j + 3] = v.w;
-        }
-    }
-}
 
 // Eq. 7 per arm: C_a(p, k) = sum over the arm's views of the Hamming distance between the
 // reference census word at p and the view's word at p + n(view, k) (nearest shift, clamped --
 // the padded census repeats the border words, so the linear offset needs no clamping), summed
-// over the C colour channels (census planes view * C + c; Sec. III-B).  A warp
-// takes a run of RUN = 32 / LPT pixels; views are the outer loop, so a view's label offsets are
-// read once and the RUN x LPT census loads of the view are independent of each other.
-template <int LPT>
+// over the C colour channels (census planes view * C + c; Sec. III-B).
+// Cost of an absent (padding) label, k >= Lc.  The host bounds paths x (C + P2) below 2^16, so a
+// present label's path cost (at most C + P2) stays below 2^13 = kAbsent for 8 and 16 paths.
+constexpr int kAbsent = 0x2000;
+
+// One warp per run of 32 pixels of a row and one arm, lane = pixel: a label's shift is the same
+// for every pixel, so for each (label, view) the 32 lanes read 32 consecutive words -- one
+// coalesced 256-byte access.  Labels go 4 at a time (their offsets are one uniform 16-byte load);
+// the 32 pixels' costs collect in a shared-memory tile (row stride rw words, rw = 2 mod 32, so
+// the lanes' 8-byte stores do not conflict) and leave as the contiguous block [32][Lcd] of the
+// output.  Lanes past the end of the row repeat the last pixel and are not stored.
+template <int C>
 __global__ void __launch_bounds__(128) coarse_cost_kernel(const uint64_t *__restrict__ cen_pad, size_t HWp, int Wp,
-                                                          int P, int H, int W, int ref, int C,
+                                                          int P, int H, int W, int ref,
                                                           const int *__restrict__ armviews,
                                                           const int *__restrict__ otab, CoarseArms ca, int Lc,
-                                                          int Lcd, uint16_t *__restrict__ out,
+                                                          int Lcd, int rw, uint16_t *__restrict__ out,
                                                           unsigned long long *__restrict__ armsum) {
-    using V = CVec<LPT>;
-    constexpr int RUN = 32 / LPT;
+    extern __shared__ __align__(16) uint32_t tile[];     // [4 warps][32 pixels][rw words]
     const int a = blockIdx.y;
-    const int lane = threadIdx.x & 31;
-    const int runs_x = (W + RUN - 1) / RUN;
-    const int task = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-    if (task >= runs_x * H) return;
-    const int y = task / runs_x, xs = (task - y * runs_x) * RUN;
-    const int k0 = lane * LPT;
-    const bool act = k0 < Lcd;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int runs_x = (W + 31) >> 5;
+    const int task = blockIdx.x * 4 + w;
+    if (task >= runs_x * H) return;                      // no block-wide barrier below
+    const int y = task / runs_x, x0 = (task - y * runs_x) * 32;
+    const size_t base = (size_t)(y + P) * Wp + P + min(x0 + lane, W - 1);
     const int nv = ca.nv[a];
     const int *views = armviews + a * kMaxArmViews;
-    const int *ot = otab + ca.tab_off[a] + k0;
-    const size_t N = (size_t)H * W;
-    const size_t rowoff = (size_t)(y + P) * Wp + P + xs;
+    const int *ot = otab + ca.tab_off[a];
+    uint64_t r[C];
+#pragma unroll
+    for (int ch = 0; ch < C; ch++) r[ch] = __ldg(cen_pad + ((size_t)ref * C + ch) * HWp + base);
+    uint32_t *T = tile + (size_t)(w * 32 + lane) * rw;
     unsigned long long total = 0;
-    if (act) {
-        int c[RUN][LPT];
-#pragma unroll
-        for (int i = 0; i < RUN; i++)
-#pragma unroll
-            for (int j = 0; j < LPT; j++) c[i][j] = 0;
-        for (int ch = 0; ch < C; ch++) {
-            uint64_t r[RUN];
-            const uint64_t *refrow = cen_pad + ((size_t)ref * C + ch) * HWp + rowoff;
-#pragma unroll
-            for (int i = 0; i < RUN; i++) r[i] = __ldg(refrow + i);     // padded: in bounds past W too
+    for (int k0 = 0; k0 < Lcd; k0 += 4) {
+        int c0 = 0, c1 = 0, c2 = 0, c3 = 0;
+        if (k0 < Lc) {
             for (int v = 0; v < nv; v++) {
-                const uint64_t *base = cen_pad + ((size_t)__ldg(views + v) * C + ch) * HWp + rowoff;
-                int o[LPT];
-                load_offsets<LPT>(ot + v * Lcd, o);
+                const int4 o = __ldg(reinterpret_cast<const int4 *>(ot + v * Lcd + k0));
+                const size_t vb = (size_t)__ldg(views + v) * C;
 #pragma unroll
-                for (int i = 0; i < RUN; i++)
-#pragma unroll
-                    for (int j = 0; j < LPT; j++) c[i][j] += __popcll(r[i] ^ __ldg(base + i + o[j]));
+                for (int ch = 0; ch < C; ch++) {
+                    const uint64_t *q = cen_pad + (vb + ch) * HWp + base;
+                    c0 += __popcll(r[ch] ^ __ldg(q + o.x));
+                    c1 += __popcll(r[ch] ^ __ldg(q + o.y));
+                    c2 += __popcll(r[ch] ^ __ldg(q + o.z));
+                    c3 += __popcll(r[ch] ^ __ldg(q + o.w));
+                }
             }
+            if (k0 + 1 >= Lc) c1 = 0;
+            if (k0 + 2 >= Lc) c2 = 0;
+            if (k0 + 3 >= Lc) c3 = 0;
         }
-        uint16_t *O = out + ((size_t)a * N + (size_t)y * W + xs) * Lcd + k0;
-#pragma unroll
-        for (int i = 0; i < RUN; i++) {
-            if (xs + i >= W) break;
-#pragma unroll
-            for (int j = 0; j < LPT; j++) {
-                if (k0 + j >= Lc) c[i][j] = 0;
-                total += (unsigned)c[i][j];
-            }
-            *reinterpret_cast<typename V::T *>(O + (size_t)i * Lcd) = V::pack(c[i]);
-        }
+        if (x0 + lane < W) total += (unsigned)(c0 + c1 + c2 + c3);
+        // padding labels (k >= Lc) hold kAbsent, above every path cost of a present label
+        if (k0 + 0 >= Lc) c0 = kAbsent;
+        if (k0 + 1 >= Lc) c1 = kAbsent;
+        if (k0 + 2 >= Lc) c2 = kAbsent;
+        if (k0 + 3 >= Lc) c3 = kAbsent;
+        *reinterpret_cast<uint2 *>(T + (k0 >> 1)) = make_uint2((uint32_t)c0 | ((uint32_t)c1 << 16),
+                                                               (uint32_t)c2 | ((uint32_t)c3 << 16));
+    }
+    __syncwarp();
+    const int npx = min(32, W - x0), q4 = Lcd >> 2;      // 8-byte pieces per pixel row
+    uint2 *dst = reinterpret_cast<uint2 *>(out + ((size_t)a * H * W + (size_t)y * W + x0) * Lcd);
+    const uint32_t *Tw = tile + (size_t)w * 32 * rw;
+    for (int e = lane; e < npx * q4; e += 32) {
+        const int i = e / q4, q = e - i * q4;
+        dst[e] = *reinterpret_cast<const uint2 *>(Tw + i * rw + 2 * q);
     }
     for (int o = 16; o > 0; o >>= 1) total += __shfl_down_sync(0xffffffffu, total, o);
     if (lane == 0 && total) atomicAdd(armsum + a, total);
@@ -198,12 +198,16 @@ __device__ __forceinline__ void red_words(uint16_t *dst, const uint32_t *v) {
 // L = C where the predecessor is outside the image; sum over directions (Eq. 9).
 // A lane's labels are held as 16-bit pairs in 32-bit words: the minima are per-halfword
 // (__vminu2) and the additions and the subtraction of m are plain 32-bit operations, exact
-// because every present value stays below 2^13 (the host bounds 8 (C + P2) < 2^16) and is at
-// least m, so no halfword carries or borrows.  An absent label (k >= Lc) holds 0x7fff, above
-// any present value and below 2^16 - P1.
+// because every present value stays below 2^13 (the host bounds paths (C + P2) < 2^16) and is at
+// least m, so no halfword carries or borrows.  Absent labels need no masks: their cost is
+// kAbsent = 2^13 (padding labels, and lanes past Lcd read it too), so their path cost stays in
+// [2^13, 2^13 + P2], above every present value (never a minimum, never a chosen neighbour) and
+// below 2^14; labels below 0 read 0x7fff.  The absent labels' sums overflow their halfwords,
+// but a carry only runs into higher, also absent, labels or out of the reduced word, and the
+// WTA reads labels below Lc only.
 template <int LPT>
 __global__ void __launch_bounds__(128) coarse_sgm_kernel(const uint16_t *__restrict__ cost, int H, int W, int Lc,
-                                                         int Lcd, const int *__restrict__ pen, ScanTable st,
+                                                         int Lcd, const int *__restrict__ pen, int per_arm,
                                                          int narms, uint16_t *__restrict__ sum,
     const int *__restrict__ order) {
     using T = typename CVec<LPT>::T;
@@ -211,7 +215,6 @@ __global__ void __launch_bounds__(128) coarse_sgm_kernel(const uint16_t *__restr
     constexpr uint32_t SENT = 0x7fff7fffu;
     const int lane = threadIdx.x & 31;
     const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int per_arm = st.cum[st.paths];
     if (gw >= per_arm * narms) return;
     const int arm = gw / per_arm;
     const int w = gw - arm * per_arm;
@@ -228,17 +231,14 @@ __global__ void __launch_bounds__(128) coarse_sgm_kernel(const uint16_t *__restr
     uint16_t *S = sum + (size_t)arm * N * Lcd + k0;
     const uint32_t P1 = (uint32_t)__ldg(pen + 2 * arm), P2 = (uint32_t)__ldg(pen + 2 * arm + 1);
     const uint32_t P1P1 = P1 * 0x10001u;
-    uint32_t pm[NP];                     // 0xffff in the halfwords of present labels
-#pragma unroll
-    for (int j = 0; j < NP; j++)
-        pm[j] = (k0 + 2 * j < Lc ? 0x0000ffffu : 0u) | (k0 + 2 * j + 1 < Lc ? 0xffff0000u : 0u);
+    constexpr uint32_t ABS2 = (uint32_t)kAbsent * 0x10001u;
     // cost and sum pointers step along the scanline; the cost rows of the next four steps are in
     // flight (a ring of four registers, indexed statically by unrolling the steps by four)
     const long long dstep = ((long long)dy * W + dx) * Lcd;
     const uint16_t *pc = C + ((long long)y * W + x) * Lcd;
     uint16_t *ps = S + ((long long)y * W + x) * Lcd;
     auto ld = [&](int t) {
-        T v{};
+        T v = CVec<LPT>::fill(ABS2);
         if (act && t < steps) v = __ldg(reinterpret_cast<const T *>(pc + (long long)t * dstep));
         return v;
     };
@@ -250,22 +250,15 @@ __global__ void __launch_bounds__(128) coarse_sgm_kernel(const uint16_t *__restr
 #pragma unroll
         for (int j = 1; j < NP; j++) q = __vminu2(q, Ln[j]);
         m = __reduce_min_sync(0xffffffffu, min(q & 0xffffu, q >> 16));
-        if (act) {
-            uint32_t v[NP];
-#pragma unroll
-            for (int j = 0; j < NP; j++) v[j] = Ln[j] & pm[j];
-            red_words<LPT>(ps, v);
-        }
+        if (act) red_words<LPT>(ps, Ln);
         ps += dstep;
 #pragma unroll
         for (int j = 0; j < NP; j++) L[j] = Ln[j];
     };
     {   // path start: L = C
-        uint32_t c[NP], Ln[NP];
-        words_of<LPT>(ring[0], c);
+        uint32_t Ln[NP];
+        words_of<LPT>(ring[0], Ln);
         ring[0] = ld(4);
-#pragma unroll
-        for (int j = 0; j < NP; j++) Ln[j] = (c[j] & pm[j]) | (SENT & ~pm[j]);
         finish(Ln);
     }
     for (int t0 = 1; t0 < steps; t0 += 4) {
@@ -291,7 +284,7 @@ __global__ void __launch_bounds__(128) coarse_sgm_kernel(const uint16_t *__restr
                 const uint32_t rp = __byte_perm(L[j], nw, 0x5432);    // labels 2j+1, 2j+2
                 uint32_t u = __vminu2(L[j], __vminu2(lm, rp) + P1P1);
                 u = __vminu2(u, mp2);
-                Ln[j] = ((c[j] + (u - mm)) & pm[j]) | (SENT & ~pm[j]);
+                Ln[j] = c[j] + (u - mm);
             }
             finish(Ln);
         }
@@ -299,26 +292,38 @@ __global__ void __launch_bounds__(128) coarse_sgm_kernel(const uint16_t *__restr
 }
 
 // WTA over the path sums (Eq. 10): lowest label on ties (the key is sum << 8 | label).
+// One warp per 8 consecutive (arm, pixel) rows: the 8 rows' loads are issued before the first
+// reduction, so a warp waits for memory once instead of once per pixel.
+constexpr int kWtaRows = 8;
 template <int LPT>
 __global__ void __launch_bounds__(128) coarse_wta_kernel(const uint16_t *__restrict__ sum, int narms, int N, int Lc,
                                                          int Lcd, int *__restrict__ maps, int *__restrict__ maps_out) {
     using V = CVec<LPT>;
     const int lane = threadIdx.x & 31;
-    const long long gw = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    if (gw >= (long long)narms * N) return;
+    const long long g0 = (((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5) * kWtaRows;
+    const long long total = (long long)narms * N;
+    if (g0 >= total) return;
     const int k0 = lane * LPT;
-    unsigned key = 0xffffffffu;
-    if (k0 < Lcd) {
+    typename V::T w[kWtaRows];
+#pragma unroll
+    for (int i = 0; i < kWtaRows; i++) {
+        w[i] = typename V::T{};
+        if (k0 < Lcd && g0 + i < total) w[i] = __ldg(reinterpret_cast<const typename V::T *>(sum + (g0 + i) * Lcd + k0));
+    }
+#pragma unroll
+    for (int i = 0; i < kWtaRows; i++) {
+        if (g0 + i >= total) break;                       // warp-uniform
+        unsigned key = 0xffffffffu;
         int c[LPT];
-        V::unpack(__ldg(reinterpret_cast<const typename V::T *>(sum + gw * Lcd + k0)), c);
+        V::unpack(w[i], c);
 #pragma unroll
         for (int j = 0; j < LPT; j++)
             if (k0 + j < Lc) key = min(key, ((unsigned)c[j] << 8) | (unsigned)(k0 + j));
-    }
-    key = __reduce_min_sync(0xffffffffu, key);
-    if (lane == 0) {
-        maps[gw] = (int)(key & 0xffu);
-        if (maps_out) maps_out[gw] = (int)(key & 0xffu);
+        key = __reduce_min_sync(0xffffffffu, key);
+        if (lane == 0) {
+            maps[g0 + i] = (int)(key & 0xffu);
+            if (maps_out) maps_out[g0 + i] = (int)(key & 0xffu);
+        }
     }
 }
 
@@ -335,14 +340,16 @@ cudaError_t launch_coarse_cost(cudaStream_t s, const uint64_t *cen_pad, int P, i
                                uint16_t *out, unsigned long long *armsum) {
     const int Lcd = coarse_stride(Lc);
     const size_t HWp = (size_t)Hp * Wp;
-    const int run = 32 / coarse_lpt(Lc);
-    const long long tasks = (long long)((W + run - 1) / run) * H;
+    const int rw = Lcd / 2 + (((2 - Lcd / 2) % 32) + 32) % 32;   // row stride in words, = 2 mod 32
+    const size_t smem = (size_t)4 * 32 * rw * 4;
+    const long long tasks = (long long)((W + 31) / 32) * H;
     dim3 grid((unsigned)((tasks + 3) / 4), (unsigned)ca.n_arms);
-    switch (coarse_lpt(Lc)) {
-    case 2: coarse_cost_kernel<2><<<grid, 128, 0, s>>>(cen_pad, HWp, Wp, P, H, W, ref, C, armviews, otab, ca, Lc, Lcd, out, armsum); break;
-    case 4: coarse_cost_kernel<4><<<grid, 128, 0, s>>>(cen_pad, HWp, Wp, P, H, W, ref, C, armviews, otab, ca, Lc, Lcd, out, armsum); break;
-    default: coarse_cost_kernel<8><<<grid, 128, 0, s>>>(cen_pad, HWp, Wp, P, H, W, ref, C, armviews, otab, ca, Lc, Lcd, out, armsum); break;
+    auto kern = C == 3 ? coarse_cost_kernel<3> : coarse_cost_kernel<1>;
+    if (smem > 48 * 1024) {
+        const cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
     }
+    kern<<<grid, 128, smem, s>>>(cen_pad, HWp, Wp, P, H, W, ref, armviews, otab, ca, Lc, Lcd, rw, out, armsum);
     return cudaGetLastError();
 }
 
@@ -360,9 +367,9 @@ cudaError_t launch_coarse_sgm(cudaStream_t s, const uint16_t *cost, int narms, i
     const int block = 128;
     const unsigned grid = (unsigned)((warps * 32 + block - 1) / block);
     switch (coarse_lpt(Lc)) {
-    case 2: coarse_sgm_kernel<2><<<grid, block, 0, s>>>(cost, H, W, Lc, Lcd, pen, st, narms, sum, order); break;
-    case 4: coarse_sgm_kernel<4><<<grid, block, 0, s>>>(cost, H, W, Lc, Lcd, pen, st, narms, sum, order); break;
-    default: coarse_sgm_kernel<8><<<grid, block, 0, s>>>(cost, H, W, Lc, Lcd, pen, st, narms, sum, order); break;
+    case 2: coarse_sgm_kernel<2><<<grid, block, 0, s>>>(cost, H, W, Lc, Lcd, pen, st.cum[paths], narms, sum, order); break;
+    case 4: coarse_sgm_kernel<4><<<grid, block, 0, s>>>(cost, H, W, Lc, Lcd, pen, st.cum[paths], narms, sum, order); break;
+    default: coarse_sgm_kernel<8><<<grid, block, 0, s>>>(cost, H, W, Lc, Lcd, pen, st.cum[paths], narms, sum, order); break;
     }
     return cudaGetLastError();
 }
@@ -370,7 +377,7 @@ cudaError_t launch_coarse_sgm(cudaStream_t s, const uint16_t *cost, int narms, i
 cudaError_t launch_coarse_wta(cudaStream_t s, const uint16_t *sum, int narms, int N, int Lc, int *maps,
                               int *maps_out) {
     const int Lcd = coarse_stride(Lc);
-    const long long warps = (long long)narms * N;
+    const long long warps = ((long long)narms * N + kWtaRows - 1) / kWtaRows;
     const unsigned grid = (unsigned)((warps * 32 + 127) / 128);
     switch (coarse_lpt(Lc)) {
     case 2: coarse_wta_kernel<2><<<grid, 128, 0, s>>>(sum, narms, N, Lc, Lcd, maps, maps_out); break;

@@ -540,9 +540,10 @@ lfsgm_status lfsgm_cost_volume(lfsgm_handle h, const float *views, const int32_t
         }));
     }
     LFSGM_TRY(run(h, "fine_cost_wide", [&] {
-        return launch_fine_cost_list(s, h->views_pad, h->cen_pad, h->rows.P, h->rows.Wp, h->rows.Hp, h->d_ltab, c.fine_labels,
-                                     h->nviews, h->C, c.H, c.W, h->ref, lo, cnt, (const long long *)off, c.w_l2,
-                                     c.w_census, cost, h->wide_list, h->wide_count, h->status);
+        return launch_fine_cost_list(s, h->views_pad, h->cen_pad, h->rows.P, h->rows.Wp, h->rows.Hp, h->d_ltab,
+                                     c.fine_labels, h->nviews, h->C, c.H, c.W, h->ref, lo, cnt,
+                                     (const long long *)off, c.w_l2, c.w_census, cost, h->wide_list, h->wide_count,
+                                     h->status);
     }));
     return LFSGM_OK;
 }
