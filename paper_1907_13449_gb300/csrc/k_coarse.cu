@@ -77,23 +77,22 @@ constexpr int kAbsent = 0x2000;
 
 // One warp per run of 32 pixels of a row and one arm, lane = pixel: a label's shift is the same
 // for every pixel, so for each (label, view) the 32 lanes read 32 consecutive words -- one
-// coalesced 256-byte access.  Labels go 4 at a time (their offsets are one uniform 16-byte load);
-// the 32 pixels' costs collect in a shared-memory tile (row stride rw words, rw = 2 mod 32, so
-// the lanes' 8-byte stores do not conflict) and leave as the contiguous block [32][Lcd] of the
-// output.  Lanes past the end of the row repeat the last pixel and are not stored.
+// coalesced 256-byte access.  Labels go 4 at a time (their offsets are one uniform 16-byte load),
+// and each lane stores its pixel's 4 costs as one 8-byte word (a staging tile in shared memory
+// made the stores coalesced but took the L1 capacity the census gathers live on: 0.42 vs 0.34 ms
+// on 9x9 x 512x512).  Lanes past the end of the row repeat the last pixel and are not stored.
 template <int C>
 __global__ void __launch_bounds__(128) coarse_cost_kernel(const uint64_t *__restrict__ cen_pad, size_t HWp, int Wp,
                                                           int P, int H, int W, int ref,
                                                           const int *__restrict__ armviews,
                                                           const int *__restrict__ otab, CoarseArms ca, int Lc,
-                                                          int Lcd, int rw, uint16_t *__restrict__ out,
+                                                          int Lcd, uint16_t *__restrict__ out,
                                                           unsigned long long *__restrict__ armsum) {
-    extern __shared__ __align__(16) uint32_t tile[];     // [4 warps][32 pixels][rw words]
     const int a = blockIdx.y;
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const int runs_x = (W + 31) >> 5;
     const int task = blockIdx.x * 4 + w;
-    if (task >= runs_x * H) return;                      // no block-wide barrier below
+    if (task >= runs_x * H) return;
     const int y = task / runs_x, x0 = (task - y * runs_x) * 32;
     const size_t base = (size_t)(y + P) * Wp + P + min(x0 + lane, W - 1);
     const int nv = ca.nv[a];
@@ -102,7 +101,8 @@ __global__ void __launch_bounds__(128) coarse_cost_kernel(const uint64_t *__rest
     uint64_t r[C];
 #pragma unroll
     for (int ch = 0; ch < C; ch++) r[ch] = __ldg(cen_pad + ((size_t)ref * C + ch) * HWp + base);
-    uint32_t *T = tile + (size_t)(w * 32 + lane) * rw;
+    uint16_t *O = out + ((size_t)a * H * W + (size_t)y * W + min(x0 + lane, W - 1)) * Lcd;
+    const bool store = x0 + lane < W;
     unsigned long long total = 0;
     for (int k0 = 0; k0 < Lcd; k0 += 4) {
         int c0 = 0, c1 = 0, c2 = 0, c3 = 0;
@@ -123,22 +123,15 @@ __global__ void __launch_bounds__(128) coarse_cost_kernel(const uint64_t *__rest
             if (k0 + 2 >= Lc) c2 = 0;
             if (k0 + 3 >= Lc) c3 = 0;
         }
-        if (x0 + lane < W) total += (unsigned)(c0 + c1 + c2 + c3);
+        if (store) total += (unsigned)(c0 + c1 + c2 + c3);
         // padding labels (k >= Lc) hold kAbsent, above every path cost of a present label
         if (k0 + 0 >= Lc) c0 = kAbsent;
         if (k0 + 1 >= Lc) c1 = kAbsent;
         if (k0 + 2 >= Lc) c2 = kAbsent;
         if (k0 + 3 >= Lc) c3 = kAbsent;
-        *reinterpret_cast<uint2 *>(T + (k0 >> 1)) = make_uint2((uint32_t)c0 | ((uint32_t)c1 << 16),
-                                                               (uint32_t)c2 | ((uint32_t)c3 << 16));
-    }
-    __syncwarp();
-    const int npx = min(32, W - x0), q4 = Lcd >> 2;      // 8-byte pieces per pixel row
-    uint2 *dst = reinterpret_cast<uint2 *>(out + ((size_t)a * H * W + (size_t)y * W + x0) * Lcd);
-    const uint32_t *Tw = tile + (size_t)w * 32 * rw;
-    for (int e = lane; e < npx * q4; e += 32) {
-        const int i = e / q4, q = e - i * q4;
-        dst[e] = *reinterpret_cast<const uint2 *>(Tw + i * rw + 2 * q);
+        if (store)
+            *reinterpret_cast<uint2 *>(O + k0) = make_uint2((uint32_t)c0 | ((uint32_t)c1 << 16),
+                                                            (uint32_t)c2 | ((uint32_t)c3 << 16));
     }
     for (int o = 16; o > 0; o >>= 1) total += __shfl_down_sync(0xffffffffu, total, o);
     if (lane == 0 && total) atomicAdd(armsum + a, total);
@@ -340,16 +333,10 @@ cudaError_t launch_coarse_cost(cudaStream_t s, const uint64_t *cen_pad, int P, i
                                uint16_t *out, unsigned long long *armsum) {
     const int Lcd = coarse_stride(Lc);
     const size_t HWp = (size_t)Hp * Wp;
-    const int rw = Lcd / 2 + (((2 - Lcd / 2) % 32) + 32) % 32;   // row stride in words, = 2 mod 32
-    const size_t smem = (size_t)4 * 32 * rw * 4;
     const long long tasks = (long long)((W + 31) / 32) * H;
     dim3 grid((unsigned)((tasks + 3) / 4), (unsigned)ca.n_arms);
     auto kern = C == 3 ? coarse_cost_kernel<3> : coarse_cost_kernel<1>;
-    if (smem > 48 * 1024) {
-        const cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return e;
-    }
-    kern<<<grid, 128, smem, s>>>(cen_pad, HWp, Wp, P, H, W, ref, armviews, otab, ca, Lc, Lcd, rw, out, armsum);
+    kern<<<grid, 128, 0, s>>>(cen_pad, HWp, Wp, P, H, W, ref, armviews, otab, ca, Lc, Lcd, out, armsum);
     return cudaGetLastError();
 }
 

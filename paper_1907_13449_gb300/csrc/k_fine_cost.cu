@@ -320,39 +320,27 @@ __global__ void __launch_bounds__(128, 4) fine_cost_rows(const __grid_constant__
 
 // The per-pixel form over a list of (pixel, chunk) items (the windows left by fine_cost_rows):
 // one warp per item, lane = label of the chunk, taps read from the padded views and census words
-// (no clamping needed) at linear offsets (oy Wp + ox, ny Wp + nx) from a table of the handle.  The chunk's table entries arrive by bulk copies on a per-warp mbarrier,
-// kListVB views (up to 32 x 16 bytes each) per stage and two stages, so the taps of the next
-// views are in flight while the current ones are sampled; waits are bounded (on expiry
-// LFSGM_ERR_TIMEOUT is latched).  Colour (C > 1): the images are planes view * C + c; each tap
-// samples every channel, the l2 term is the Euclidean norm of the colour difference and the
-// census term sums the channels' Hamming distances (Sec. III-B/C).
-constexpr int kListWarps = 4, kListVB = 8;
+// (no clamping needed) at linear offsets (oy Wp + ox, ny Wp + nx).  Each lane reads its label's
+// table entry of a view with one coalesced 16-byte load (the warp's 32 entries are contiguous);
+// two views per unrolled step keep their loads in flight together.  Colour (C > 1): the images
+// are planes view * C + c; each tap samples every channel, the l2 term is the Euclidean norm of
+// the colour difference and the census term sums the channels' Hamming distances (Sec. III-B/C).
+constexpr int kListWarps = 4;
 
 template <int C>
 __global__ void __launch_bounds__(32 * kListWarps) fine_cost_list(const float *__restrict__ views_pad,
                                                       const uint64_t *__restrict__ cen_pad, int P, int Wp, int Hp,
                                                       const int4 *__restrict__ ltab, int G, int nviews,
-                                                      int H, int W, int ref, const int *__restrict__ lo,
+                                                      int W, int ref, const int *__restrict__ lo,
                                                       const int *__restrict__ cnt,
                                                       const long long *__restrict__ off, float wl2, float wc,
                                                       float *__restrict__ cost, const int2 *__restrict__ list,
-                                                      const int *__restrict__ count, int *__restrict__ status) {
-    __shared__ __align__(128) int4 taps[kListWarps][2][kListVB][32];
-    __shared__ __align__(8) unsigned long long mbar[kListWarps][2];
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+                                                      const int *__restrict__ count) {
+    const int lane = threadIdx.x & 31;
     const int warps = (gridDim.x * blockDim.x) >> 5;
     const size_t HWp = (size_t)Hp * Wp;
     const int total = *count;
-    const unsigned mb0 = smem_u32(&mbar[w][0]);
-    if (lane == 0) {
-        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(mb0));
-        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(mb0 + 8));
-        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-    }
-    __syncwarp();
-    unsigned ph0 = 0, ph1 = 0;                 // phase parity of each stage's barrier
     const int nv1 = nviews - 1;
-    const int nb = (nv1 + kListVB - 1) / kListVB;
     for (int t = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; t < total; t += warps) {
         const int2 item = list[t];
         const int p = item.x, chunk = item.y;
@@ -361,70 +349,39 @@ __global__ void __launch_bounds__(32 * kListWarps) fine_cost_list(const float *_
         if (!window_ok(l0, n, G, row, nullptr)) continue;      // items are pushed for valid windows only
         const int npad = (int)min((long long)((n + 3) & ~3), row);
         const int j = chunk * 32 + lane;
-        const int cn = min(32, n - chunk * 32);                // labels of this chunk (>= 1)
-        const int4 *tg = ltab + (l0 + chunk * 32);
-        // stage st receives the taps of views kListVB*b .. kListVB*b + kListVB - 1 (as present)
-        auto issue = [&](int b, int st) {
-            if (lane != 0) return;
-            const int v0 = b * kListVB, vn = min(kListVB, nv1 - v0);
-            const unsigned mb = mb0 + 8 * st;
-            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-            asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(mb), "r"(vn * cn * 16) : "memory");
-            for (int k = 0; k < vn; k++) {
-                const int vi = v0 + k, view = vi + (vi >= ref);
-                asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
-                             ::"r"(smem_u32(&taps[w][st][k][0])), "l"(tg + (size_t)view * G), "r"(cn * 16), "r"(mb)
-                             : "memory");
-            }
-        };
         const int x = p % W, y = p / W;
         const size_t base = (size_t)(y + P) * Wp + (x + P);
-        float Iref[C];
-        uint64_t cr[C];
-#pragma unroll
-        for (int ch = 0; ch < C; ch++) {
-            Iref[ch] = __ldg(views_pad + ((size_t)ref * C + ch) * HWp + base);
-            cr[ch] = __ldg(cen_pad + ((size_t)ref * C + ch) * HWp + base);
-        }
         float sl2 = 0.f;
         int sc = 0;
-        issue(0, 0);
-        for (int b = 0; b < nb; b++) {
-            const int st = b & 1;
-            if (b + 1 < nb) issue(b + 1, st ^ 1);
-            const unsigned par = st ? ph1 : ph0;
-            if (!mbar_wait(mb0 + 8 * st, par)) {
-                if (lane == 0) atomicExch(status, 6);
-                // let the copies still in flight land (bounded) before the warp leaves
-                if (b + 1 < nb) mbar_wait(mb0 + 8 * (st ^ 1), st ? ph0 : ph1);
-                return;
-            }
-            if (st) ph1 ^= 1u;
-            else ph0 ^= 1u;
-            const int vn = min(kListVB, nv1 - b * kListVB);
-            if (j < n) {
-#pragma unroll 4
-                for (int k = 0; k < vn; k++) {
-                    const int vi = b * kListVB + k;
-                    const size_t vb = (size_t)(vi + (vi >= ref)) * C * HWp + base;
-                    const int4 tw = taps[w][st][k][lane];     // linear tap offsets (x + Wp y), fx, fy
-                    const float tfx = __int_as_float(tw.z), tfy = __int_as_float(tw.w);
-                    float sq = 0.f;
+        if (j < n) {
+            float Iref[C];
+            uint64_t cr[C];
 #pragma unroll
-                    for (int ch = 0; ch < C; ch++) {
-                        const float *q = views_pad + vb + ch * HWp + tw.x;
-                        const float i00 = __ldg(q), i10 = __ldg(q + 1), i01 = __ldg(q + Wp), i11 = __ldg(q + Wp + 1);
-                        const float top = (1.f - tfx) * i00 + tfx * i10;
-                        const float bot = (1.f - tfx) * i01 + tfx * i11;
-                        const float dl = Iref[ch] - ((1.f - tfy) * top + tfy * bot);
-                        if (C == 1) sl2 += fabsf(dl);
-                        else sq = fmaf(dl, dl, sq);
-                        sc += __popcll(cr[ch] ^ __ldg(cen_pad + vb + ch * HWp + tw.y));
-                    }
-                    if (C > 1) sl2 += sqrtf(sq);
-                }
+            for (int ch = 0; ch < C; ch++) {
+                Iref[ch] = __ldg(views_pad + ((size_t)ref * C + ch) * HWp + base);
+                cr[ch] = __ldg(cen_pad + ((size_t)ref * C + ch) * HWp + base);
             }
-            __syncwarp();          // the stage is refilled two batches later
+            const int4 *tg = ltab + l0 + j;
+#pragma unroll 2
+            for (int vi = 0; vi < nv1; vi++) {
+                const int view = vi + (vi >= ref);
+                const int4 tw = __ldg(tg + (size_t)view * G);     // linear tap offsets (x + Wp y), fx, fy
+                const size_t vb = (size_t)view * C * HWp + base;
+                const float tfx = __int_as_float(tw.z), tfy = __int_as_float(tw.w);
+                float sq = 0.f;
+#pragma unroll
+                for (int ch = 0; ch < C; ch++) {
+                    const float *q = views_pad + vb + ch * HWp + tw.x;
+                    const float i00 = __ldg(q), i10 = __ldg(q + 1), i01 = __ldg(q + Wp), i11 = __ldg(q + Wp + 1);
+                    const float top = (1.f - tfx) * i00 + tfx * i10;
+                    const float bot = (1.f - tfx) * i01 + tfx * i11;
+                    const float dl = Iref[ch] - ((1.f - tfy) * top + tfy * bot);
+                    if (C == 1) sl2 += fabsf(dl);
+                    else sq = fmaf(dl, dl, sq);
+                    sc += __popcll(cr[ch] ^ __ldg(cen_pad + vb + ch * HWp + tw.y));
+                }
+                if (C > 1) sl2 += sqrtf(sq);
+            }
         }
         if (j < npad) cost[o + j] = (j < n) ? wl2 * sl2 + wc * (float)sc : 0.f;
     }
@@ -617,18 +574,18 @@ cudaError_t launch_list_all(cudaStream_t s, const int *lo, const int *cnt, const
 }
 
 cudaError_t launch_fine_cost_list(cudaStream_t s, const float *views_pad, const uint64_t *cen_pad, int P, int Wp,
-                                  int Hp, const int4 *ltab, int G, int nviews, int C, int H, int W, int ref,
+                                  int Hp, const int4 *ltab, int G, int nviews, int C, int W, int ref,
                                   const int *lo, const int *cnt, const long long *off, float wl2, float wc,
-                                  float *cost, const int2 *list, const int *count, int *status) {
+                                  float *cost, const int2 *list, const int *count) {
     int dev = 0, sms = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     if (C == 3)
-        fine_cost_list<3><<<sms * 12, 32 * kListWarps, 0, s>>>(views_pad, cen_pad, P, Wp, Hp, ltab, G, nviews, H, W,
-                                                              ref, lo, cnt, off, wl2, wc, cost, list, count, status);
+        fine_cost_list<3><<<sms * 12, 32 * kListWarps, 0, s>>>(views_pad, cen_pad, P, Wp, Hp, ltab, G, nviews, W, ref,
+                                                              lo, cnt, off, wl2, wc, cost, list, count);
     else
-        fine_cost_list<1><<<sms * 12, 32 * kListWarps, 0, s>>>(views_pad, cen_pad, P, Wp, Hp, ltab, G, nviews, H, W,
-                                                              ref, lo, cnt, off, wl2, wc, cost, list, count, status);
+        fine_cost_list<1><<<sms * 12, 32 * kListWarps, 0, s>>>(views_pad, cen_pad, P, Wp, Hp, ltab, G, nviews, W, ref,
+                                                              lo, cnt, off, wl2, wc, cost, list, count);
     return cudaGetLastError();
 }
 

@@ -88,6 +88,8 @@ struct lfsgm_ctx {
     int *o_lo = nullptr, *o_cnt = nullptr, *o_label = nullptr;
     long long *o_off = nullptr;
     float *o_cost = nullptr, *o_agg = nullptr, *o_disp = nullptr, *o_views = nullptr;
+    cudaStream_t up = nullptr;            // upload stream of lfsgm_depth_host (the non-cross views)
+    cudaEvent_t up_done = nullptr;
     // backward scratch (allocated on the first lfsgm_backward): aggregate, dLoss/dC_s, branch codes
     // of the 8 or 16 directions, argmin slots, penalty gradients
     float *b_agg = nullptr, *b_gcs = nullptr, *b_gp = nullptr;
@@ -414,6 +416,8 @@ lfsgm_status lfsgm_destroy(lfsgm_handle h) {
     if (h->ws_owned) cudaFree(h->ws);
     cudaFree(h->o_lo); cudaFree(h->o_cnt); cudaFree(h->o_label); cudaFree(h->o_off);
     cudaFree(h->o_cost); cudaFree(h->o_agg); cudaFree(h->o_disp); cudaFree(h->o_views);
+    if (h->up_done) cudaEventDestroy(h->up_done);
+    if (h->up) cudaStreamDestroy(h->up);
     cudaFree(h->b_agg); cudaFree(h->b_gcs); cudaFree(h->b_gp); cudaFree(h->b_codes); cudaFree(h->b_amin);
     for (auto &r : h->prof) { cudaEventDestroy(r.a); cudaEventDestroy(r.b); }
     for (auto e : h->pool) cudaEventDestroy(e);
@@ -541,9 +545,8 @@ lfsgm_status lfsgm_cost_volume(lfsgm_handle h, const float *views, const int32_t
     }
     LFSGM_TRY(run(h, "fine_cost_wide", [&] {
         return launch_fine_cost_list(s, h->views_pad, h->cen_pad, h->rows.P, h->rows.Wp, h->rows.Hp, h->d_ltab,
-                                     c.fine_labels, h->nviews, h->C, c.H, c.W, h->ref, lo, cnt,
-                                     (const long long *)off, c.w_l2, c.w_census, cost, h->wide_list, h->wide_count,
-                                     h->status);
+                                     c.fine_labels, h->nviews, h->C, c.W, h->ref, lo, cnt, (const long long *)off,
+                                     c.w_l2, c.w_census, cost, h->wide_list, h->wide_count);
     }));
     return LFSGM_OK;
 }
@@ -723,9 +726,12 @@ lfsgm_status lfsgm_kernel_times(lfsgm_handle h, const char **names, float *ms, i
     return LFSGM_OK;
 }
 
-lfsgm_status lfsgm_depth(lfsgm_handle h, const float *views, float *disp, int32_t *label) {
-    if (!h) return LFSGM_ERR_INVALID_ARG;
-    if (!views) return fail(h, LFSGM_ERR_INVALID_ARG, "null views");
+}  // extern "C"
+
+namespace {
+// The whole method on device views; `wait` (nullable) is an event the cost stage waits for (views
+// that only the cost stage reads may still be arriving while the initial pass runs).
+lfsgm_status depth_chain(lfsgm_handle h, const float *views, float *disp, int32_t *label, cudaEvent_t wait) {
     const size_t N = (size_t)h->N;
     int64_t maxnnz = 0;
     lfsgm_max_nnz(h, &maxnnz);
@@ -741,24 +747,70 @@ lfsgm_status lfsgm_depth(lfsgm_handle h, const float *views, float *disp, int32_
     }
     int64_t *off = (int64_t *)h->o_off;
     LFSGM_TRY(lfsgm_initial_disparity(h, views, 0, 0, h->o_lo, h->o_cnt, off, nullptr, nullptr, nullptr));
+    if (wait) {
+        const cudaError_t e = cudaStreamWaitEvent(h->stream, wait, 0);
+        if (e != cudaSuccess) return cuda_fail(h, e, "upload wait");
+    }
     LFSGM_TRY(lfsgm_cost_volume(h, views, h->o_lo, h->o_cnt, off, h->o_cost));
     LFSGM_TRY(lfsgm_sgm_aggregate(h, h->o_cost, h->o_lo, h->o_cnt, off, -1.f, -1.f, h->o_agg));
     return lfsgm_wta_subpixel(h, h->o_agg, h->o_lo, h->o_cnt, off, label ? label : h->o_label,
                               disp ? disp : h->o_disp);
 }
+}  // namespace
+
+extern "C" {
+
+lfsgm_status lfsgm_depth(lfsgm_handle h, const float *views, float *disp, int32_t *label) {
+    if (!h) return LFSGM_ERR_INVALID_ARG;
+    if (!views) return fail(h, LFSGM_ERR_INVALID_ARG, "null views");
+    return depth_chain(h, views, disp, label, nullptr);
+}
 
 lfsgm_status lfsgm_depth_host(lfsgm_handle h, const float *views_host, float *disp_host, int32_t *label_host) {
     if (!h) return LFSGM_ERR_INVALID_ARG;
     if (!views_host || !disp_host) return fail(h, LFSGM_ERR_INVALID_ARG, "null host buffer");
-    const size_t N = (size_t)h->N, vbytes = (size_t)h->nviews * h->C * N * 4;
+    const lfsgm_config &c = h->cfg;
+    const size_t N = (size_t)h->N, vv = (size_t)h->C * N * 4, vbytes = (size_t)h->nviews * vv;
     if (!h->o_views) {
-        const cudaError_t e = cudaMalloc((void **)&h->o_views, vbytes);
+        cudaError_t e = cudaMalloc((void **)&h->o_views, vbytes);
+        if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&h->up, cudaStreamNonBlocking);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->up_done, cudaEventDisableTiming);
         if (e != cudaSuccess) return fail(h, LFSGM_ERR_NO_MEMORY, "views buffer: %s", cudaGetErrorString(e));
     }
     cudaStream_t s = h->stream;
-    cudaError_t e = cudaMemcpyAsync(h->o_views, views_host, vbytes, cudaMemcpyHostToDevice, s);
+    char *dv = (char *)h->o_views;
+    const char *hv = (const char *)views_host;
+    cudaError_t e = cudaSuccess;
+    cudaEvent_t wait = nullptr;
+    if (c.boundless) {
+        e = cudaMemcpyAsync(dv, hv, vbytes, cudaMemcpyHostToDevice, s);
+    } else {
+        // The initial pass reads the cross views only (row vc and column uc): they go first on the
+        // handle's stream; the other views go on the upload stream meanwhile, as four rectangles of
+        // the [V][U] view grid, and the cost stage waits for them.
+        const size_t pitch = (size_t)c.U * vv;
+        e = cudaMemcpyAsync(dv + c.vc * pitch, hv + c.vc * pitch, pitch, cudaMemcpyHostToDevice, s);
+        if (e == cudaSuccess)
+            e = cudaMemcpy2DAsync(dv + c.uc * vv, pitch, hv + c.uc * vv, pitch, vv, c.V, cudaMemcpyHostToDevice, s);
+        // the upload stream starts after the work already queued on the handle's stream, so that a
+        // previous light field's kernels are done with the buffer
+        if (e == cudaSuccess) e = cudaEventRecord(h->up_done, s);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(h->up, h->up_done, 0);
+        const int rows[2][2] = {{0, c.vc}, {c.vc + 1, c.V}};
+        const int cols[2][2] = {{0, c.uc}, {c.uc + 1, c.U}};
+        for (int r = 0; r < 2 && e == cudaSuccess; r++)
+            for (int q = 0; q < 2 && e == cudaSuccess; q++) {
+                const int v0 = rows[r][0], nvr = rows[r][1] - rows[r][0];
+                const int u0 = cols[q][0], nuc = cols[q][1] - cols[q][0];
+                if (nvr <= 0 || nuc <= 0) continue;
+                const size_t o = (size_t)v0 * pitch + (size_t)u0 * vv;
+                e = cudaMemcpy2DAsync(dv + o, pitch, hv + o, pitch, (size_t)nuc * vv, nvr, cudaMemcpyHostToDevice, h->up);
+            }
+        if (e == cudaSuccess) e = cudaEventRecord(h->up_done, h->up);
+        wait = h->up_done;
+    }
     if (e != cudaSuccess) return cuda_fail(h, e, "views upload");
-    LFSGM_TRY(lfsgm_depth(h, h->o_views, nullptr, nullptr));
+    LFSGM_TRY(depth_chain(h, h->o_views, nullptr, nullptr, wait));
     e = cudaMemcpyAsync(disp_host, h->o_disp, N * 4, cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess && label_host) e = cudaMemcpyAsync(label_host, h->o_label, N * 4, cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);

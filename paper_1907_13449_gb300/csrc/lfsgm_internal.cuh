@@ -182,9 +182,9 @@ cudaError_t launch_fine_cost_rows(cudaStream_t s, const RowPlanHost *ph, const f
 cudaError_t launch_list_all(cudaStream_t s, const int *lo, const int *cnt, const long long *off, int G,
                             int2 *list, int *count, int N, int *status, int min_cnt = 0);
 cudaError_t launch_fine_cost_list(cudaStream_t s, const float *views_pad, const uint64_t *cen_pad, int P, int Wp,
-                                  int Hp, const int4 *ltab, int G, int nviews, int C, int H, int W, int ref,
-                                  const int *lo, const int *cnt, const long long *off, float wl2,
-                                  float wc, float *cost, const int2 *list, const int *count, int *status);
+                                  int Hp, const int4 *ltab, int G, int nviews, int C, int W, int ref,
+                                  const int *lo, const int *cnt, const long long *off, float wl2, float wc,
+                                  float *cost, const int2 *list, const int *count);
 
 // partial: nblocks sums of the active costs followed by nblocks counts of active slots
 cudaError_t launch_cost_partial_sums(cudaStream_t s, const float *cost, const int *cnt,

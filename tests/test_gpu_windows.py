@@ -50,3 +50,29 @@ def test_boundless_depth_matches_oracle_with_fewer_launches(gpu_lib):
     _check_end_to_end(g_label, g_disp, ref, pb)
     _, _, n_bounded = _gpu_depth(gpu_lib, p, views)
     assert n_free < n_bounded - 5                      # no census / coarse cost / SGM / WTA / fill
+
+
+@pytest.mark.parametrize("kind", ["corner_reference", "boundless"])
+def test_depth_host_matches_device(gpu_lib, kind):
+    """lfsgm_depth_host uploads the cross views first and the other views on a second stream
+    (four rectangles of the view grid, some empty when the reference view sits in a corner);
+    the result equals the device-buffer entry point."""
+    import torch
+    from test_gpu_parity import _dev, _np
+    if kind == "corner_reference":
+        views, _, p = lfsynth.tiny(params=lfsynth.tiny_params(uc=0, vc=4, H=40, W=48))
+    else:
+        views, _, p = lfsynth.tiny(params=lfsynth.tiny_params(boundless=1, H=40, W=48))
+    h = gpu_lib.lfsgm_create(p)
+    label = torch.empty(p.N, dtype=torch.int32, device="cuda")
+    disp = torch.empty(p.N, dtype=torch.float32, device="cuda")
+    gpu_lib.lfsgm_depth(h, _dev(views), disp, label)
+    vh = torch.from_numpy(np.ascontiguousarray(views)).pin_memory()
+    dh = torch.empty(p.N, dtype=torch.float32).pin_memory()
+    lh = torch.empty(p.N, dtype=torch.int32).pin_memory()
+    for _ in range(2):                                  # twice: the buffer is reused
+        gpu_lib.lfsgm_depth_host(h, vh, dh, lh)
+        assert np.array_equal(lh.numpy(), _np(label))
+        assert np.max(np.abs(dh.numpy() - _np(disp))) < 1e-5
+    gpu_lib.lfsgm_sync(h)
+    gpu_lib.lfsgm_destroy(h)
