@@ -40,8 +40,9 @@ FP32_LANES_PER_SM = 128
 # DRAM bytes (read + write) per launch from one ncu capture of the bench workload, with the
 # SHA-256 prefix of the kernel's source at capture time; a changed source reports null.
 NCU_TRAFFIC = {
-    "fine_cost": {"bytes": 315813376, "workload": "bench", "channels": 1, "source": "paper_1907_13449_gb300/csrc/k_fine_cost.cu",
-                  "sha256_16": "fca9a7c0741d2296", "capture": "profiles/fine_cost_rows_bench_9x9x512x512.md"},
+    "fine_cost": {"bytes": 316136960, "workload": "bench", "channels": 1,
+                  "source": "paper_1907_13449_gb300/csrc/k_fine_cost.cu",
+                  "sha256_16": "b17612dc59d1556d", "capture": "profiles/fine_cost_rows_bench_9x9x512x512.md"},
 }
 
 
@@ -157,12 +158,41 @@ def hbm_bytes_cost_sgm(p, nnz_active):
 
 
 def alu_ops_cost(p, nnz_active):
-    """Algorithmic FP32 lane operations of the cost volume: per (active cell, non-reference
+    """Algorithmic 32-bit lane operations of the cost volume: per (active cell, non-reference
     view, channel) a bilinear sample (3 lerps, 2 ops each), the difference and its absolute-value
-    accumulation, or for colour its squared accumulation (2 ops); colour adds one square root
-    per (cell, view)."""
-    per_view = 8 * p.channels + (1 if p.channels > 1 else 0)
+    accumulation, or for colour its squared accumulation (2 ops), and the census term (xor,
+    popcount and add of the 64-bit words: 3 ops); colour adds one square root per (cell, view)."""
+    per_view = 11 * p.channels + (1 if p.channels > 1 else 0)
     return nnz_active * (p.U * p.V - 1) * per_view
+
+
+ROW_KW = 36      # label span of the row cost kernel (kRowKW in k_fine_cost.cu)
+
+
+def row_kernel_cells(lo, cnt, H, W):
+    """Cells the row cost kernel computes (the rest go to the list kernel): per run of 32 pixels
+    of a row it takes the ROW_KW-label range [g0, g0 + ROW_KW) that holds the most windows of at
+    most 32 labels (ties: the lowest start, candidates in lane order) and computes the windows
+    inside it -- the kernel's own selection, replayed on the host from the window map."""
+    import numpy as np
+    lo = lo.reshape(H, W).astype(np.int64)
+    cnt = cnt.reshape(H, W).astype(np.int64)
+    Wt = (W + 31) // 32 * 32
+    l = np.zeros((H, Wt), np.int64)
+    n = np.zeros((H, Wt), np.int64)
+    l[:, :W], n[:, :W] = lo, cnt
+    l, n = l.reshape(-1, 32), n.reshape(-1, 32)
+    nar = (n >= 1) & (n <= 32)
+    best = np.full(l.shape[0], -1)
+    g0 = np.zeros(l.shape[0], np.int64)
+    for c in range(32):
+        cl = l[:, c]
+        fit = (nar & (l >= cl[:, None]) & (l + n <= cl[:, None] + ROW_KW)).sum(1)
+        take = nar[:, c] & ((fit > best) | ((fit == best) & (cl < g0)))
+        best = np.where(take, fit, best)
+        g0 = np.where(take, cl, g0)
+    fits = nar & (l >= g0[:, None]) & (l + n <= g0[:, None] + ROW_KW) & (best[:, None] > 0)
+    return int((n * fits).sum())
 
 
 def max_over_ranks(vals, ws, device):
@@ -215,6 +245,7 @@ def run_ours(args, ws, rank, local):
     nnz = int(L.off[-1].item())
     cnt = L.cnt.cpu().numpy()
     active = int(cnt.sum())
+    row_cells = row_kernel_cells(L.lo.cpu().numpy(), cnt, p.H, p.W) if p.channels == 1 else 0
 
     lf.lfsgm_set_profiling(L.h, True)
     lf.lfsgm_kernel_times(L.h)          # drop anything recorded so far
@@ -323,11 +354,15 @@ def run_ours(args, ws, rank, local):
     mhz = (clocks or {}).get("sm_mhz") or peaks.get("sm_max_mhz", 2070.0)
     by = hbm_bytes_cost_sgm(p, active)
     if dom in ("fine_cost", "fine_cost_wide"):
-        ops = alu_ops_cost(p, active)
+        # the row kernel computes row_cells of the active cells, the list kernel the rest
+        # (colour: every cell goes through the list kernel)
+        ops = alu_ops_cost(p, row_cells if dom == "fine_cost" else active - row_cells)
         peak_ops = N_SM * FP32_LANES_PER_SM * mhz * 1e6
         ach = ops / (kernels[dom]["ms_avg"] * 1e-3)
         roof = {"kernel": dom, "bound": "alu", "achieved": round(ach / 1e12, 3),
-                "peak": round(peak_ops / 1e12, 3), "unit": "T FP32 lane-ops/s",
+                "peak": round(peak_ops / 1e12, 3), "unit": "T 32-bit lane-ops/s",
+                "cells": row_cells if dom == "fine_cost" else active - row_cells,
+                "lane_ops_per_cell_view": 11 * p.channels + (1 if p.channels > 1 else 0),
                 "frac": round(ach / peak_ops, 4), "traffic": ncu_traffic(dom, args.workload, p.channels),
                 "algorithmic_bytes": by["cost_volume"],
                 "peak_basis": f"{N_SM} SMs x {FP32_LANES_PER_SM} FP32 lanes x {mhz:.0f} MHz (median SM clock under load)"}

@@ -2,17 +2,18 @@
 // penalties, integer SGM over 8 or 16 paths (Eq. 8-9) and WTA (Eq. 10).
 //
 // Layout: the arm cost and the path sums are uint16 [arm][pixel][Lcd], the label dimension
-// padded only to Lcd = round_up(Lc, max(4, LPT)) (LPT = labels per lane: 2, 4 or 8 for
-// Lc <= 64, 128, 256), so a lane's LPT labels are one aligned 4/8/16-byte word.
-//  - cost: one warp per run of 16 pixels of a row and one arm; lanes hold LPT labels each and
-//    read the census words at the labels' nearest shifts from the edge-padded census (no
-//    clamping needed), the shifts coming as linear offsets from a per-arm table.
-//  - SGM: one warp per (arm, direction, scanline); the lane's labels stay in registers, the
-//    d-1 / d+1 neighbours across lanes come by one shuffle each way, the predecessor minimum by
-//    one redux.sync; the next 4 cost rows are prefetched; the directions add into the sums
-//    with one packed 32/64-bit reduction per lane and step (the host checks that a label's sum
-//    over the 8 paths stays below 2^16, so the 16-bit fields never carry into each other).
-//  - WTA: one warp per (arm, pixel), argmin by one redux.sync over (sum << 8 | label).
+// padded to Lcd = round_up(Lc, 8), so a lane's 4 or 8 labels are one aligned 8- or 16-byte word;
+// padding labels hold the absent-label cost (see the SGM).
+//  - cost: one warp per run of 32 pixels of a row and one arm, lanes = pixels; the census words
+//    at the labels' nearest shifts come from the edge-padded census (no clamping needed), the
+//    shifts as linear offsets from a per-arm table.
+//  - SGM: 16 lanes per (arm, direction, scanline), two arms per warp (Lc <= 128), or one warp per
+//    arm (Lc <= 256); a lane's labels stay in registers, the d-1 / d+1 neighbours across lanes
+//    come by one shuffle each way, the predecessor minimum by redux.sync; the next 4 cost rows
+//    are prefetched; the directions add into the sums with packed 64-bit reductions (the host
+//    checks that a label's sum over the paths stays below 2^16, so the 16-bit fields never
+//    carry into each other).
+//  - WTA: one warp per 8 (arm, pixel) rows, argmin by one redux.sync over (sum << 8 | label).
 #include "lfsgm_internal.cuh"
 
 #include <algorithm>
@@ -190,7 +191,7 @@ __device__ __forceinline__ void red_words(uint16_t *dst, const uint32_t *v) {
 //   L(p,k) = C(p,k) + (min(L'(k), L'(k-1)+P1, L'(k+1)+P1, m+P2) - m),  m = min_k L'(k),
 // L = C where the predecessor is outside the image; sum over directions (Eq. 9).
 // A lane's labels are held as 16-bit pairs in 32-bit words: the minima are per-halfword
-// (__vminu2) and the additions and the subtraction of m are plain 32-bit operations, exact
+// (DPX __vimin3_u16x2 / __viaddmin_u16x2) and the additions and the subtraction of m are plain 32-bit operations, exact
 // because every present value stays below 2^13 (the host bounds paths (C + P2) < 2^16) and is at
 // least m, so no halfword carries or borrows.  Absent labels need no masks: their cost is
 // kAbsent = 2^13 (padding labels, and lanes past Lcd read it too), so their path cost stays in
@@ -198,19 +199,27 @@ __device__ __forceinline__ void red_words(uint16_t *dst, const uint32_t *v) {
 // below 2^14; labels below 0 read 0x7fff.  The absent labels' sums overflow their halfwords,
 // but a carry only runs into higher, also absent, labels or out of the reduced word, and the
 // WTA reads labels below Lc only.
-template <int LPT>
+// A group of GW lanes walks one arm's scanline: GW = 32 (one arm per warp, Lc up to 256) or 16
+// (two arms per warp on the same scanline, Lc up to 128).  Two arms per warp halve the warp steps:
+// the loads, shuffles, reductions and loop control of a step serve both arms.  Each half's
+// minimum m comes from a full-warp redux in which the other half contributes 0xffffffff.
+template <int LPT, int GW>
 __global__ void __launch_bounds__(128) coarse_sgm_kernel(const uint16_t *__restrict__ cost, int H, int W, int Lc,
                                                          int Lcd, const int *__restrict__ pen, int per_arm,
                                                          int narms, uint16_t *__restrict__ sum,
     const int *__restrict__ order) {
     using T = typename CVec<LPT>::T;
-    constexpr int NP = LPT / 2;
+    constexpr int NP = LPT / 2, AP = 32 / GW;    // label words per lane, arms per warp
     constexpr uint32_t SENT = 0x7fff7fffu;
-    const int lane = threadIdx.x & 31;
+    const int lane = threadIdx.x & 31, gl = lane % GW, ga = lane / GW;
     const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    if (gw >= per_arm * narms) return;
-    const int arm = gw / per_arm;
-    const int w = gw - arm * per_arm;
+    const int groups = (narms + AP - 1) / AP;
+    if (gw >= per_arm * groups) return;
+    const int ag = gw / per_arm;
+    const int w = gw - ag * per_arm;
+    const int arm_raw = ag * AP + ga;
+    const bool arm_ok = arm_raw < narms;             // a spare half (odd arm count) only idles
+    const int arm = arm_ok ? arm_raw : 0;
     const int rs = __ldg(order + w);             // longest scanlines first (within the arm)
     const int r = rs & 15, s = rs >> 4;
     const int dx = dir_dx(r), dy = dir_dy(r);
@@ -218,8 +227,8 @@ __global__ void __launch_bounds__(128) coarse_sgm_kernel(const uint16_t *__restr
     scan_start(r, s, H, W, x, y);
     const int steps = scan_steps(x, y, dx, dy, H, W);
     const size_t N = (size_t)H * W;
-    const int k0 = lane * LPT;
-    const bool act = k0 < Lcd;
+    const int k0 = gl * LPT;
+    const bool act = arm_ok && k0 < Lcd;
     const uint16_t *C = cost + (size_t)arm * N * Lcd + k0;
     uint16_t *S = sum + (size_t)arm * N * Lcd + k0;
     const uint32_t P1 = (uint32_t)__ldg(pen + 2 * arm), P2 = (uint32_t)__ldg(pen + 2 * arm + 1);
@@ -241,8 +250,15 @@ __global__ void __launch_bounds__(128) coarse_sgm_kernel(const uint16_t *__restr
     auto finish = [&](const uint32_t *Ln) {       // warp minimum, packed reduction, carry the row
         uint32_t q = Ln[0];
 #pragma unroll
-        for (int j = 1; j < NP; j++) q = __vminu2(q, Ln[j]);
-        m = __reduce_min_sync(0xffffffffu, min(q & 0xffffu, q >> 16));
+        for (int j = 1; j < NP; j++) q = __vimin3_u16x2(q, Ln[j], Ln[j]);
+        const uint32_t v = min(q & 0xffffu, q >> 16);
+        if constexpr (GW == 32) {
+            m = __reduce_min_sync(0xffffffffu, v);
+        } else {
+            const uint32_t m0 = __reduce_min_sync(0xffffffffu, ga == 0 ? v : 0xffffffffu);
+            const uint32_t m1 = __reduce_min_sync(0xffffffffu, ga == 1 ? v : 0xffffffffu);
+            m = ga ? m1 : m0;
+        }
         if (act) red_words<LPT>(ps, Ln);
         ps += dstep;
 #pragma unroll
@@ -263,11 +279,13 @@ __global__ void __launch_bounds__(128) coarse_sgm_kernel(const uint16_t *__restr
             uint32_t c[NP];
             words_of<LPT>(ring[slot], c);
             ring[slot] = ld(t + 4);
-            uint32_t left = __shfl_up_sync(0xffffffffu, L[NP - 1], 1);
-            uint32_t right = __shfl_down_sync(0xffffffffu, L[0], 1);
-            if (lane == 0) left = SENT;
-            if (lane == 31) right = SENT;
-            const uint32_t mm = __byte_perm(m, 0, 0x1010), mp2 = __byte_perm(m + P2, 0, 0x1010);
+            uint32_t left = __shfl_up_sync(0xffffffffu, L[NP - 1], 1, GW);
+            uint32_t right = __shfl_down_sync(0xffffffffu, L[0], 1, GW);
+            if (gl == 0) left = SENT;
+            if (gl == GW - 1) right = SENT;
+            // min(L'(k), L'(k-1)+P1, L'(k+1)+P1, m+P2) = min(L'(k), min(L'(k-1), L'(k+1), m+P2-P1) + P1):
+            // one 3-way and one add-then-min per halfword pair (DPX)
+            const uint32_t mm = __byte_perm(m, 0, 0x1010), mq = __byte_perm(m + P2 - P1, 0, 0x1010);
             uint32_t Ln[NP];
 #pragma unroll
             for (int j = 0; j < NP; j++) {
@@ -275,8 +293,7 @@ __global__ void __launch_bounds__(128) coarse_sgm_kernel(const uint16_t *__restr
                 const uint32_t nw = (j == NP - 1) ? right : L[j + 1];
                 const uint32_t lm = __byte_perm(pw, L[j], 0x5432);    // labels 2j-1, 2j
                 const uint32_t rp = __byte_perm(L[j], nw, 0x5432);    // labels 2j+1, 2j+2
-                uint32_t u = __vminu2(L[j], __vminu2(lm, rp) + P1P1);
-                u = __vminu2(u, mp2);
+                const uint32_t u = __viaddmin_u16x2(__vimin3_u16x2(lm, rp, mq), P1P1, L[j]);
                 Ln[j] = c[j] + (u - mm);
             }
             finish(Ln);
@@ -323,10 +340,7 @@ __global__ void __launch_bounds__(128) coarse_wta_kernel(const uint16_t *__restr
 }  // namespace
 
 int coarse_lpt(int Lc) { return Lc <= 64 ? 2 : (Lc <= 128 ? 4 : 8); }
-int coarse_stride(int Lc) {
-    const int q = std::max(4, coarse_lpt(Lc));
-    return (Lc + q - 1) / q * q;
-}
+int coarse_stride(int Lc) { return (Lc + 7) / 8 * 8; }
 
 cudaError_t launch_coarse_cost(cudaStream_t s, const uint64_t *cen_pad, int P, int Wp, int Hp, int H, int W, int ref, int C,
                                const int *armviews, const int *otab, const CoarseArms &ca, int Lc,
@@ -350,14 +364,18 @@ cudaError_t launch_coarse_sgm(cudaStream_t s, const uint16_t *cost, int narms, i
                               const int *pen, uint16_t *sum, const int *order, int paths) {
     const ScanTable st = make_scan_table(H, W, paths);
     const int Lcd = coarse_stride(Lc);
-    const long long warps = (long long)st.cum[paths] * narms;
+    const int per_arm = st.cum[paths];
     const int block = 128;
-    const unsigned grid = (unsigned)((warps * 32 + block - 1) / block);
-    switch (coarse_lpt(Lc)) {
-    case 2: coarse_sgm_kernel<2><<<grid, block, 0, s>>>(cost, H, W, Lc, Lcd, pen, st.cum[paths], narms, sum, order); break;
-    case 4: coarse_sgm_kernel<4><<<grid, block, 0, s>>>(cost, H, W, Lc, Lcd, pen, st.cum[paths], narms, sum, order); break;
-    default: coarse_sgm_kernel<8><<<grid, block, 0, s>>>(cost, H, W, Lc, Lcd, pen, st.cum[paths], narms, sum, order); break;
-    }
+    auto grid = [&](int arms_per_warp) {
+        const long long warps = (long long)per_arm * ((narms + arms_per_warp - 1) / arms_per_warp);
+        return (unsigned)((warps * 32 + block - 1) / block);
+    };
+    if (Lc <= 64)          // 16 lanes x 4 labels per arm, two arms per warp
+        coarse_sgm_kernel<4, 16><<<grid(2), block, 0, s>>>(cost, H, W, Lc, Lcd, pen, per_arm, narms, sum, order);
+    else if (Lc <= 128)    // 16 lanes x 8 labels per arm, two arms per warp
+        coarse_sgm_kernel<8, 16><<<grid(2), block, 0, s>>>(cost, H, W, Lc, Lcd, pen, per_arm, narms, sum, order);
+    else                   // 32 lanes x 8 labels, one arm per warp
+        coarse_sgm_kernel<8, 32><<<grid(1), block, 0, s>>>(cost, H, W, Lc, Lcd, pen, per_arm, narms, sum, order);
     return cudaGetLastError();
 }
 
