@@ -2,21 +2,22 @@
 // penalties, integer SGM over 8 or 16 paths (Eq. 8-9) and WTA (Eq. 10).
 //
 // Layout: the arm cost and the path sums are uint16 [arm][pixel][Lcd], the label dimension
-// padded to Lcd = round_up(Lc, 8), so a lane's 4 or 8 labels are one aligned 8- or 16-byte word;
-// padding labels hold the absent-label cost (see the SGM).
+// padded only to Lcd = round_up(Lc, max(4, LPT)) (LPT = labels per lane: 2, 4 or 8 for
+// Lc <= 64, 128, 256), so a lane's LPT labels are one aligned 4/8/16-byte word; padding labels
+// hold the absent-label cost (see the SGM).
 //  - cost: one warp per run of 32 pixels of a row and one arm, lanes = pixels; the census words
 //    at the labels' nearest shifts come from the edge-padded census (no clamping needed), the
 //    shifts as linear offsets from a per-arm table.
-//  - SGM: 16 lanes per (arm, direction, scanline), two arms per warp (Lc <= 128), or one warp per
-//    arm (Lc <= 256); a lane's labels stay in registers, the d-1 / d+1 neighbours across lanes
-//    come by one shuffle each way, the predecessor minimum by redux.sync; the next 4 cost rows
-//    are prefetched; the directions add into the sums with packed 64-bit reductions (the host
-//    checks that a label's sum over the paths stays below 2^16, so the 16-bit fields never
-//    carry into each other).
+//  - SGM: one warp per (arm, direction, scanline); the lane's labels stay in registers, the
+//    d-1 / d+1 neighbours across lanes come by one shuffle each way, the predecessor minimum by
+//    one redux.sync; the next 4 cost rows are prefetched; the directions add into the sums
+//    with one packed 32/64-bit reduction per lane and step (the host checks that a label's sum
+//    over the paths stays below 2^16, so the 16-bit fields never carry into each other).
 //  - WTA: one warp per 8 (arm, pixel) rows, argmin by one redux.sync over (sum << 8 | label).
 #include "lfsgm_internal.cuh"
 
 #include <algorithm>
+#include <type_traits>
 
 namespace lfsgm {
 namespace {
@@ -82,12 +83,15 @@ constexpr int kAbsent = 0x2000;
 // and each lane stores its pixel's 4 costs as one 8-byte word (a staging tile in shared memory
 // made the stores coalesced but took the L1 capacity the census gathers live on: 0.42 vs 0.34 ms
 // on 9x9 x 512x512).  Lanes past the end of the row repeat the last pixel and are not stored.
-template <int C>
+// OT = uint8_t when every cost fits a byte (arm views x census bits x channels <= 255): half the
+// bytes for the eight sweeps of the SGM to read; padding labels then hold 0 and the SGM marks
+// them absent itself.
+template <int C, typename OT>
 __global__ void __launch_bounds__(128) coarse_cost_kernel(const uint64_t *__restrict__ cen_pad, size_t HWp, int Wp,
                                                           int P, int H, int W, int ref,
                                                           const int *__restrict__ armviews,
                                                           const int *__restrict__ otab, CoarseArms ca, int Lc,
-                                                          int Lcd, uint16_t *__restrict__ out,
+                                                          int Lcd, OT *__restrict__ out,
                                                           unsigned long long *__restrict__ armsum) {
     const int a = blockIdx.y;
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
@@ -102,7 +106,7 @@ __global__ void __launch_bounds__(128) coarse_cost_kernel(const uint64_t *__rest
     uint64_t r[C];
 #pragma unroll
     for (int ch = 0; ch < C; ch++) r[ch] = __ldg(cen_pad + ((size_t)ref * C + ch) * HWp + base);
-    uint16_t *O = out + ((size_t)a * H * W + (size_t)y * W + min(x0 + lane, W - 1)) * Lcd;
+    OT *O = out + ((size_t)a * H * W + (size_t)y * W + min(x0 + lane, W - 1)) * Lcd;
     const bool store = x0 + lane < W;
     unsigned long long total = 0;
     for (int k0 = 0; k0 < Lcd; k0 += 4) {
@@ -125,14 +129,20 @@ __global__ void __launch_bounds__(128) coarse_cost_kernel(const uint64_t *__rest
             if (k0 + 3 >= Lc) c3 = 0;
         }
         if (store) total += (unsigned)(c0 + c1 + c2 + c3);
-        // padding labels (k >= Lc) hold kAbsent, above every path cost of a present label
-        if (k0 + 0 >= Lc) c0 = kAbsent;
-        if (k0 + 1 >= Lc) c1 = kAbsent;
-        if (k0 + 2 >= Lc) c2 = kAbsent;
-        if (k0 + 3 >= Lc) c3 = kAbsent;
-        if (store)
-            *reinterpret_cast<uint2 *>(O + k0) = make_uint2((uint32_t)c0 | ((uint32_t)c1 << 16),
-                                                            (uint32_t)c2 | ((uint32_t)c3 << 16));
+        if constexpr (sizeof(OT) == 1) {
+            if (store)
+                *reinterpret_cast<uint32_t *>(O + k0) =
+                    (uint32_t)c0 | ((uint32_t)c1 << 8) | ((uint32_t)c2 << 16) | ((uint32_t)c3 << 24);
+        } else {
+            // padding labels (k >= Lc) hold kAbsent, above every path cost of a present label
+            if (k0 + 0 >= Lc) c0 = kAbsent;
+            if (k0 + 1 >= Lc) c1 = kAbsent;
+            if (k0 + 2 >= Lc) c2 = kAbsent;
+            if (k0 + 3 >= Lc) c3 = kAbsent;
+            if (store)
+                *reinterpret_cast<uint2 *>(O + k0) = make_uint2((uint32_t)c0 | ((uint32_t)c1 << 16),
+                                                                (uint32_t)c2 | ((uint32_t)c3 << 16));
+        }
     }
     for (int o = 16; o > 0; o >>= 1) total += __shfl_down_sync(0xffffffffu, total, o);
     if (lane == 0 && total) atomicAdd(armsum + a, total);
@@ -199,27 +209,49 @@ __device__ __forceinline__ void red_words(uint16_t *dst, const uint32_t *v) {
 // below 2^14; labels below 0 read 0x7fff.  The absent labels' sums overflow their halfwords,
 // but a carry only runs into higher, also absent, labels or out of the reduced word, and the
 // WTA reads labels below Lc only.
-// A group of GW lanes walks one arm's scanline: GW = 32 (one arm per warp, Lc up to 256) or 16
-// (two arms per warp on the same scanline, Lc up to 128).  Two arms per warp halve the warp steps:
-// the loads, shuffles, reductions and loop control of a step serve both arms.  Each half's
-// minimum m comes from a full-warp redux in which the other half contributes 0xffffffff.
-template <int LPT, int GW>
-__global__ void __launch_bounds__(128) coarse_sgm_kernel(const uint16_t *__restrict__ cost, int H, int W, int Lc,
+// Byte costs (C8): a lane's LPT bytes are one 2/4/8-byte load, widened to halfword pairs by byte
+// permutes, with kAbsent or-ed into the absent labels' halves (their bytes are 0).
+template <int LPT>
+struct BVec;
+template <>
+struct BVec<2> {
+    using T = uint16_t;
+    __device__ static void widen(T v, uint32_t *c) { c[0] = __byte_perm((uint32_t)v, 0, 0x4140); }
+};
+template <>
+struct BVec<4> {
+    using T = uint32_t;
+    __device__ static void widen(T v, uint32_t *c) {
+        c[0] = __byte_perm(v, 0, 0x4140);
+        c[1] = __byte_perm(v, 0, 0x4342);
+    }
+};
+template <>
+struct BVec<8> {
+    using T = uint2;
+    __device__ static void widen(T v, uint32_t *c) {
+        c[0] = __byte_perm(v.x, 0, 0x4140);
+        c[1] = __byte_perm(v.x, 0, 0x4342);
+        c[2] = __byte_perm(v.y, 0, 0x4140);
+        c[3] = __byte_perm(v.y, 0, 0x4342);
+    }
+};
+
+template <int LPT, bool C8>
+__global__ void __launch_bounds__(128) coarse_sgm_kernel(const void *__restrict__ cost_v, int H, int W, int Lc,
                                                          int Lcd, const int *__restrict__ pen, int per_arm,
                                                          int narms, uint16_t *__restrict__ sum,
     const int *__restrict__ order) {
-    using T = typename CVec<LPT>::T;
-    constexpr int NP = LPT / 2, AP = 32 / GW;    // label words per lane, arms per warp
+    using CT = typename std::conditional<C8, uint8_t, uint16_t>::type;
+    using T = typename std::conditional<C8, typename BVec<LPT>::T, typename CVec<LPT>::T>::type;
+    const CT *cost = reinterpret_cast<const CT *>(cost_v);
+    constexpr int NP = LPT / 2;
     constexpr uint32_t SENT = 0x7fff7fffu;
-    const int lane = threadIdx.x & 31, gl = lane % GW, ga = lane / GW;
+    const int lane = threadIdx.x & 31;
     const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int groups = (narms + AP - 1) / AP;
-    if (gw >= per_arm * groups) return;
-    const int ag = gw / per_arm;
-    const int w = gw - ag * per_arm;
-    const int arm_raw = ag * AP + ga;
-    const bool arm_ok = arm_raw < narms;             // a spare half (odd arm count) only idles
-    const int arm = arm_ok ? arm_raw : 0;
+    if (gw >= per_arm * narms) return;
+    const int arm = gw / per_arm;
+    const int w = gw - arm * per_arm;
     const int rs = __ldg(order + w);             // longest scanlines first (within the arm)
     const int r = rs & 15, s = rs >> 4;
     const int dx = dir_dx(r), dy = dir_dy(r);
@@ -227,22 +259,38 @@ __global__ void __launch_bounds__(128) coarse_sgm_kernel(const uint16_t *__restr
     scan_start(r, s, H, W, x, y);
     const int steps = scan_steps(x, y, dx, dy, H, W);
     const size_t N = (size_t)H * W;
-    const int k0 = gl * LPT;
-    const bool act = arm_ok && k0 < Lcd;
-    const uint16_t *C = cost + (size_t)arm * N * Lcd + k0;
+    const int k0 = lane * LPT;
+    const bool act = k0 < Lcd;
+    const CT *C = cost + (size_t)arm * N * Lcd + k0;
     uint16_t *S = sum + (size_t)arm * N * Lcd + k0;
     const uint32_t P1 = (uint32_t)__ldg(pen + 2 * arm), P2 = (uint32_t)__ldg(pen + 2 * arm + 1);
     const uint32_t P1P1 = P1 * 0x10001u;
     constexpr uint32_t ABS2 = (uint32_t)kAbsent * 0x10001u;
+    // byte costs: kAbsent in the halves of labels >= Lc (all of them on lanes past Lcd)
+    uint32_t am[NP];
+#pragma unroll
+    for (int j = 0; j < NP; j++)
+        am[j] = (k0 + 2 * j < Lc && act ? 0u : (uint32_t)kAbsent) | (k0 + 2 * j + 1 < Lc && act ? 0u : (uint32_t)kAbsent << 16);
     // cost and sum pointers step along the scanline; the cost rows of the next four steps are in
     // flight (a ring of four registers, indexed statically by unrolling the steps by four)
     const long long dstep = ((long long)dy * W + dx) * Lcd;
-    const uint16_t *pc = C + ((long long)y * W + x) * Lcd;
+    const CT *pc = C + ((long long)y * W + x) * Lcd;
     uint16_t *ps = S + ((long long)y * W + x) * Lcd;
     auto ld = [&](int t) {
-        T v = CVec<LPT>::fill(ABS2);
+        T v;
+        if constexpr (C8) v = T{};
+        else v = CVec<LPT>::fill(ABS2);
         if (act && t < steps) v = __ldg(reinterpret_cast<const T *>(pc + (long long)t * dstep));
         return v;
+    };
+    auto words = [&](const T &v, uint32_t *c) {
+        if constexpr (C8) {
+            BVec<LPT>::widen(v, c);
+#pragma unroll
+            for (int j = 0; j < NP; j++) c[j] |= am[j];
+        } else {
+            words_of<LPT>(v, c);
+        }
     };
     T ring[4] = {ld(0), ld(1), ld(2), ld(3)};
     uint32_t L[NP];
@@ -251,14 +299,7 @@ __global__ void __launch_bounds__(128) coarse_sgm_kernel(const uint16_t *__restr
         uint32_t q = Ln[0];
 #pragma unroll
         for (int j = 1; j < NP; j++) q = __vimin3_u16x2(q, Ln[j], Ln[j]);
-        const uint32_t v = min(q & 0xffffu, q >> 16);
-        if constexpr (GW == 32) {
-            m = __reduce_min_sync(0xffffffffu, v);
-        } else {
-            const uint32_t m0 = __reduce_min_sync(0xffffffffu, ga == 0 ? v : 0xffffffffu);
-            const uint32_t m1 = __reduce_min_sync(0xffffffffu, ga == 1 ? v : 0xffffffffu);
-            m = ga ? m1 : m0;
-        }
+        m = __reduce_min_sync(0xffffffffu, min(q & 0xffffu, q >> 16));
         if (act) red_words<LPT>(ps, Ln);
         ps += dstep;
 #pragma unroll
@@ -266,7 +307,7 @@ __global__ void __launch_bounds__(128) coarse_sgm_kernel(const uint16_t *__restr
     };
     {   // path start: L = C
         uint32_t Ln[NP];
-        words_of<LPT>(ring[0], Ln);
+        words(ring[0], Ln);
         ring[0] = ld(4);
         finish(Ln);
     }
@@ -277,12 +318,12 @@ __global__ void __launch_bounds__(128) coarse_sgm_kernel(const uint16_t *__restr
             if (t >= steps) break;
             const int slot = (1 + k) & 3;          // step t's row sits in ring[t % 4]
             uint32_t c[NP];
-            words_of<LPT>(ring[slot], c);
+            words(ring[slot], c);
             ring[slot] = ld(t + 4);
-            uint32_t left = __shfl_up_sync(0xffffffffu, L[NP - 1], 1, GW);
-            uint32_t right = __shfl_down_sync(0xffffffffu, L[0], 1, GW);
-            if (gl == 0) left = SENT;
-            if (gl == GW - 1) right = SENT;
+            uint32_t left = __shfl_up_sync(0xffffffffu, L[NP - 1], 1);
+            uint32_t right = __shfl_down_sync(0xffffffffu, L[0], 1);
+            if (lane == 0) left = SENT;
+            if (lane == 31) right = SENT;
             // min(L'(k), L'(k-1)+P1, L'(k+1)+P1, m+P2) = min(L'(k), min(L'(k-1), L'(k+1), m+P2-P1) + P1):
             // one 3-way and one add-then-min per halfword pair (DPX)
             const uint32_t mm = __byte_perm(m, 0, 0x1010), mq = __byte_perm(m + P2 - P1, 0, 0x1010);
@@ -340,17 +381,25 @@ __global__ void __launch_bounds__(128) coarse_wta_kernel(const uint16_t *__restr
 }  // namespace
 
 int coarse_lpt(int Lc) { return Lc <= 64 ? 2 : (Lc <= 128 ? 4 : 8); }
-int coarse_stride(int Lc) { return (Lc + 7) / 8 * 8; }
+int coarse_stride(int Lc) {
+    const int q = std::max(4, coarse_lpt(Lc));
+    return (Lc + q - 1) / q * q;
+}
 
 cudaError_t launch_coarse_cost(cudaStream_t s, const uint64_t *cen_pad, int P, int Wp, int Hp, int H, int W, int ref, int C,
                                const int *armviews, const int *otab, const CoarseArms &ca, int Lc,
-                               uint16_t *out, unsigned long long *armsum) {
+                               void *out, bool out8, unsigned long long *armsum) {
     const int Lcd = coarse_stride(Lc);
     const size_t HWp = (size_t)Hp * Wp;
     const long long tasks = (long long)((W + 31) / 32) * H;
     dim3 grid((unsigned)((tasks + 3) / 4), (unsigned)ca.n_arms);
-    auto kern = C == 3 ? coarse_cost_kernel<3> : coarse_cost_kernel<1>;
-    kern<<<grid, 128, 0, s>>>(cen_pad, HWp, Wp, P, H, W, ref, armviews, otab, ca, Lc, Lcd, out, armsum);
+    if (out8) {
+        auto kern = C == 3 ? coarse_cost_kernel<3, uint8_t> : coarse_cost_kernel<1, uint8_t>;
+        kern<<<grid, 128, 0, s>>>(cen_pad, HWp, Wp, P, H, W, ref, armviews, otab, ca, Lc, Lcd, (uint8_t *)out, armsum);
+    } else {
+        auto kern = C == 3 ? coarse_cost_kernel<3, uint16_t> : coarse_cost_kernel<1, uint16_t>;
+        kern<<<grid, 128, 0, s>>>(cen_pad, HWp, Wp, P, H, W, ref, armviews, otab, ca, Lc, Lcd, (uint16_t *)out, armsum);
+    }
     return cudaGetLastError();
 }
 
@@ -360,22 +409,20 @@ cudaError_t launch_coarse_penalties(cudaStream_t s, const unsigned long long *su
     return cudaGetLastError();
 }
 
-cudaError_t launch_coarse_sgm(cudaStream_t s, const uint16_t *cost, int narms, int H, int W, int Lc,
+cudaError_t launch_coarse_sgm(cudaStream_t s, const void *cost, bool cost8, int narms, int H, int W, int Lc,
                               const int *pen, uint16_t *sum, const int *order, int paths) {
     const ScanTable st = make_scan_table(H, W, paths);
     const int Lcd = coarse_stride(Lc);
-    const int per_arm = st.cum[paths];
+    const long long warps = (long long)st.cum[paths] * narms;
     const int block = 128;
-    auto grid = [&](int arms_per_warp) {
-        const long long warps = (long long)per_arm * ((narms + arms_per_warp - 1) / arms_per_warp);
-        return (unsigned)((warps * 32 + block - 1) / block);
-    };
-    if (Lc <= 64)          // 16 lanes x 4 labels per arm, two arms per warp
-        coarse_sgm_kernel<4, 16><<<grid(2), block, 0, s>>>(cost, H, W, Lc, Lcd, pen, per_arm, narms, sum, order);
-    else if (Lc <= 128)    // 16 lanes x 8 labels per arm, two arms per warp
-        coarse_sgm_kernel<8, 16><<<grid(2), block, 0, s>>>(cost, H, W, Lc, Lcd, pen, per_arm, narms, sum, order);
-    else                   // 32 lanes x 8 labels, one arm per warp
-        coarse_sgm_kernel<8, 32><<<grid(1), block, 0, s>>>(cost, H, W, Lc, Lcd, pen, per_arm, narms, sum, order);
+    const unsigned grid = (unsigned)((warps * 32 + block - 1) / block);
+#define LFSGM_SGM(LPT, B) coarse_sgm_kernel<LPT, B><<<grid, block, 0, s>>>(cost, H, W, Lc, Lcd, pen, st.cum[paths], narms, sum, order)
+    switch (coarse_lpt(Lc)) {
+    case 2: if (cost8) LFSGM_SGM(2, true); else LFSGM_SGM(2, false); break;
+    case 4: if (cost8) LFSGM_SGM(4, true); else LFSGM_SGM(4, false); break;
+    default: if (cost8) LFSGM_SGM(8, true); else LFSGM_SGM(8, false); break;
+    }
+#undef LFSGM_SGM
     return cudaGetLastError();
 }
 

@@ -580,8 +580,10 @@ cudaError_t launch_fine_cost_list(cudaStream_t s, const float *views_pad, const 
     int dev = 0, sms = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    // grid-stride over the items: 12 CTAs per SM for the grey residue (a few ten thousand items),
+    // 24 for colour, where every window is an item (measured best of 12 / 16 / 24)
     if (C == 3)
-        fine_cost_list<3><<<sms * 12, 32 * kListWarps, 0, s>>>(views_pad, cen_pad, P, Wp, Hp, ltab, G, nviews, W, ref,
+        fine_cost_list<3><<<sms * 24, 32 * kListWarps, 0, s>>>(views_pad, cen_pad, P, Wp, Hp, ltab, G, nviews, W, ref,
                                                               lo, cnt, off, wl2, wc, cost, list, count);
     else
         fine_cost_list<1><<<sms * 12, 32 * kListWarps, 0, s>>>(views_pad, cen_pad, P, Wp, Hp, ltab, G, nviews, W, ref,

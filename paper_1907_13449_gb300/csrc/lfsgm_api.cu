@@ -69,7 +69,8 @@ struct lfsgm_ctx {
     void *ws = nullptr;
     size_t ws_bytes = 0;
     bool ws_owned = false;
-    uint16_t *ccost = nullptr;
+    void *ccost = nullptr;                // coarse arm costs, uint8 when they fit a byte (cost8), else uint16
+    bool cost8 = false;
     uint16_t *csum = nullptr;
     int *maps = nullptr, *F0 = nullptr, *F1 = nullptr, *cntpad = nullptr;
     int2 *wide_list = nullptr;         // (pixel, 32-label chunk) items for the list kernel
@@ -251,7 +252,7 @@ lfsgm_status bind_workspace(lfsgm_ctx *h, void *dptr, size_t bytes, bool owned) 
     h->cen_pad = (uint64_t *)take((size_t)h->nviews * h->C * HWp * 8);
     h->views_pad = (float *)take((size_t)h->nviews * h->C * HWp * 4);
     h->rows_maps = h->rows.ok && encode_fine_rows_maps(&h->rows, h->views_pad, h->cen_pad, h->nviews);
-    h->ccost = (uint16_t *)take(A * N * h->Lcd * 2);
+    h->ccost = take(A * N * h->Lcd * (h->cost8 ? 1 : 2));
     h->csum = (uint16_t *)take(A * N * h->Lcd * 2);
     h->maps = (int *)take(4 * N * 4);
     h->F0 = (int *)take(N * 4);
@@ -298,6 +299,7 @@ lfsgm_status lfsgm_create(const lfsgm_config *cfg, void *stream, lfsgm_handle *o
     build_arms(h);
     // the packed coarse sums hold (paths) x (C + P2) per 16-bit half
     const long long cmax = (long long)max_arm_views(h) * h->nbits * h->C;
+    h->cost8 = cmax <= 255;
     const long long p2max = (long long)std::floor(c.p2_frac * (double)cmax + 0.5);
     if (!c.boundless && (long long)c.paths * (cmax + std::max(p2max, 1LL)) >= 65536) {
         g_create_err = "coarse path sums would overflow 16 bits (too many arm views x census bits)";
@@ -432,7 +434,7 @@ lfsgm_status lfsgm_workspace_size(lfsgm_handle h, size_t *bytes) {
     const size_t HWp = (size_t)h->rows.Hp * h->rows.Wp;
     b += align256((size_t)h->nviews * h->C * HWp * 8);   // census words per plane, edge-replicated padding
     b += align256((size_t)h->nviews * h->C * HWp * 4);   // views per plane, edge-replicated padding
-    b += align256(A * N * h->Lcd * 2);              // coarse cost
+    b += align256(A * N * h->Lcd * (h->cost8 ? 1 : 2));   // coarse cost (bytes when they fit)
     b += align256(A * N * h->Lcd * 2);              // coarse path sums
     b += align256(4 * N * 4);                       // maps
     b += 3 * align256(N * 4);                       // F0, F1, padded counts
@@ -480,14 +482,15 @@ lfsgm_status lfsgm_initial_disparity(lfsgm_handle h, const float *views, int32_t
         if (e != cudaSuccess) return cuda_fail(h, e, "memset");
         LFSGM_TRY(run(h, "coarse_cost", [&] {
             return launch_coarse_cost(s, h->cen_pad, h->rows.P, h->rows.Wp, h->rows.Hp, c.H, c.W, h->ref, h->C,
-                                      h->d_armviews, h->d_otab, h->ca, c.coarse_labels, h->ccost, h->armsum);
+                                      h->d_armviews, h->d_otab, h->ca, c.coarse_labels, h->ccost, h->cost8,
+                                      h->armsum);
         }));
         LFSGM_TRY(run(h, "coarse_penalties", [&] {
             return launch_coarse_penalties(s, h->armsum, A, (long long)N * c.coarse_labels, c.p1_frac, c.p2_frac,
                                            Pc1, Pc2, h->cpen);
         }));
         LFSGM_TRY(run(h, "coarse_sgm", [&] {
-            return launch_coarse_sgm(s, h->ccost, A, c.H, c.W, c.coarse_labels, h->cpen, h->csum, h->d_order,
+            return launch_coarse_sgm(s, h->ccost, h->cost8, A, c.H, c.W, c.coarse_labels, h->cpen, h->csum, h->d_order,
                                      c.paths);
         }));
         LFSGM_TRY(run(h, "coarse_wta", [&] {

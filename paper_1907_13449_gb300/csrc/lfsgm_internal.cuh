@@ -136,11 +136,11 @@ int coarse_stride(int Lc);    // Lcd: label stride of the coarse cost and sums
 // Images are planes view * C + c of H x W (padded: Hp x Wp); `ref` and `armviews` count views.
 cudaError_t launch_coarse_cost(cudaStream_t s, const uint64_t *cen_pad, int P, int Wp, int Hp, int H, int W, int ref,
                                int C, const int *armviews, const int *otab, const CoarseArms &ca, int Lc,
-                               uint16_t *out, unsigned long long *armsum);
+                               void *out, bool out8, unsigned long long *armsum);
 cudaError_t launch_coarse_penalties(cudaStream_t s, const unsigned long long *sums, int narms,
                                     long long count, double p1f, double p2f, int P1, int P2,
                                     int *pen);
-cudaError_t launch_coarse_sgm(cudaStream_t s, const uint16_t *cost, int narms, int H, int W, int Lc,
+cudaError_t launch_coarse_sgm(cudaStream_t s, const void *cost, bool cost8, int narms, int H, int W, int Lc,
                               const int *pen, uint16_t *sum, const int *order, int paths);
 cudaError_t launch_coarse_wta(cudaStream_t s, const uint16_t *sum, int narms, int N, int Lc, int *maps,
                               int *maps_out);
