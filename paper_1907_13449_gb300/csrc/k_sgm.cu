@@ -189,11 +189,16 @@ __global__ void __launch_bounds__(32 * kSgmWarps) fine_sgm_kernel(const float *_
 }
 
 // Per-block sums of the active costs and slot counts (rows are 16-byte aligned, read as float4;
-// slots past cnt are masked).  Each thread adds its pixels in a fixed order, the block adds its
-// warps in a fixed order: the partials, and hence the mean, are deterministic.
-__global__ void cost_partial_kernel(const float *__restrict__ cost, const int *__restrict__ cnt,
-                                    const long long *__restrict__ off, int N, int G,
-                                    double *__restrict__ partial, int *__restrict__ status) {
+// slots past cnt are masked, so padding is never read into the sum).  Each thread adds its pixels
+// in a fixed order (windows of up to 32 slots with all their loads issued together), the block
+// adds its warps in a fixed order, and the last block to finish (ticket counter) adds the block
+// partials in block order and writes the penalties: the mean is deterministic.
+__global__ void __launch_bounds__(256) cost_partial_kernel(const float *__restrict__ cost,
+                                                           const int *__restrict__ cnt,
+                                                           const long long *__restrict__ off, int N, int G,
+                                                           double *__restrict__ partial, double p1f, double p2f,
+                                                           float *__restrict__ pen, unsigned *__restrict__ ticket,
+                                                           int *__restrict__ status) {
     double s = 0.0, c = 0.0;
     for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < N; p += gridDim.x * blockDim.x) {
         const long long o = off[p];
@@ -201,9 +206,21 @@ __global__ void cost_partial_kernel(const float *__restrict__ cost, const int *_
         if (!window_ok(0, n, G, off[p + 1] - o, status)) continue;
         const float4 *r = reinterpret_cast<const float4 *>(cost + o);
         float ps = 0.f;
-        for (int j = 0; j < n; j += 4) {
-            const float4 v = __ldg(r + (j >> 2));
-            ps += v.x + (j + 1 < n ? v.y : 0.f) + (j + 2 < n ? v.z : 0.f) + (j + 3 < n ? v.w : 0.f);
+        if (n <= 32) {
+            float4 v[8];
+#pragma unroll
+            for (int q = 0; q < 8; q++) v[q] = 4 * q < n ? __ldg(r + q) : make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+            for (int q = 0; q < 8; q++) {
+                const int j = 4 * q;
+                ps += (j < n ? v[q].x : 0.f) + (j + 1 < n ? v[q].y : 0.f) + (j + 2 < n ? v[q].z : 0.f) +
+                      (j + 3 < n ? v[q].w : 0.f);
+            }
+        } else {
+            for (int j = 0; j < n; j += 4) {
+                const float4 v = __ldg(r + (j >> 2));
+                ps += v.x + (j + 1 < n ? v.y : 0.f) + (j + 2 < n ? v.z : 0.f) + (j + 3 < n ? v.w : 0.f);
+            }
         }
         s += (double)ps;
         c += n;
@@ -213,6 +230,7 @@ __global__ void cost_partial_kernel(const float *__restrict__ cost, const int *_
         c += __shfl_down_sync(0xffffffffu, c, k);
     }
     __shared__ double ws[32], wc[32];
+    __shared__ bool last;
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     if (lane == 0) {
         ws[wid] = s;
@@ -227,40 +245,37 @@ __global__ void cost_partial_kernel(const float *__restrict__ cost, const int *_
         }
         partial[blockIdx.x] = b;
         partial[gridDim.x + blockIdx.x] = bc;
+        __threadfence();                                   // partials visible before the ticket
+        last = atomicAdd(ticket, 1u) == gridDim.x - 1;
     }
-}
-
-// Mean over the active slots: one warp adds the partials (lane-strided, then a fixed
-// shuffle tree), so the result does not depend on timing.
-__global__ void fine_penalty_kernel(const double *__restrict__ partial, int nblocks, double p1f, double p2f,
-                                    float *__restrict__ pen) {
-    double s = 0.0, c = 0.0;
-    for (int i = threadIdx.x; i < nblocks; i += 32) {
-        s += partial[i];
-        c += partial[nblocks + i];
+    __syncthreads();
+    if (!last || wid != 0) return;
+    // the last block: all partials are written; add them in block order
+    const int nb = gridDim.x;
+    s = 0.0;
+    c = 0.0;
+    for (int i = lane; i < nb; i += 32) {
+        s += __ldcg(partial + i);
+        c += __ldcg(partial + nb + i);
     }
     for (int k = 16; k > 0; k >>= 1) {
         s += __shfl_down_sync(0xffffffffu, s, k);
         c += __shfl_down_sync(0xffffffffu, c, k);
     }
-    if (threadIdx.x == 0) {
+    if (lane == 0) {
         const double mean = c > 0.0 ? s / c : 0.0;
         pen[0] = (float)(p1f * mean);
         pen[1] = (float)(p2f * mean);
+        *ticket = 0u;                                      // ready for the next launch
     }
 }
 
 }  // namespace
 
 cudaError_t launch_cost_partial_sums(cudaStream_t s, const float *cost, const int *cnt, const long long *off,
-                                     int N, int G, double *partial, int nblocks, int *status) {
-    cost_partial_kernel<<<nblocks, 256, 0, s>>>(cost, cnt, off, N, G, partial, status);
-    return cudaGetLastError();
-}
-
-cudaError_t launch_fine_penalties(cudaStream_t s, const double *partial, int nblocks, double p1f, double p2f,
-                                  float *pen) {
-    fine_penalty_kernel<<<1, 32, 0, s>>>(partial, nblocks, p1f, p2f, pen);
+                                     int N, int G, double *partial, int nblocks, double p1f, double p2f,
+                                     float *pen, unsigned *ticket, int *status) {
+    cost_partial_kernel<<<nblocks, 256, 0, s>>>(cost, cnt, off, N, G, partial, p1f, p2f, pen, ticket, status);
     return cudaGetLastError();
 }
 

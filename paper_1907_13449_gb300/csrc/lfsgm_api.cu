@@ -65,6 +65,8 @@ struct lfsgm_ctx {
     int *d_sel_cross = nullptr;  // planes of the reference and the arm views
     int n_sel_cross = 0;
     int *d_sel_all = nullptr;    // planes of every view
+    int *d_sel_rest = nullptr;   // planes of the views that are not cross views
+    int n_sel_rest = 0;
     // workspace
     void *ws = nullptr;
     size_t ws_bytes = 0;
@@ -83,6 +85,7 @@ struct lfsgm_ctx {
     int *cpen = nullptr;
     float *fpen = nullptr;
     double *partial = nullptr;
+    unsigned *ticket = nullptr;           // last-block counter of the penalty mean (zero between launches)
     long long *tsum = nullptr;
     int *status = nullptr;
     // buffers of the whole-method entry points (owned, allocated on first use)
@@ -246,8 +249,11 @@ lfsgm_status bind_workspace(lfsgm_ctx *h, void *dptr, size_t bytes, bool owned) 
     const size_t N = (size_t)h->N, A = (size_t)std::max(h->arms.n_arms, 1);
     char *p = (char *)dptr;
     auto take = [&](size_t n) { char *q = p; p += align256(n); return (void *)q; };
-    // the status word comes first, so handles that share one workspace (a batch branch) share it
+    // the status word and the penalty-mean ticket come first, so handles that share one workspace (a
+    // batch branch) share them: every layout agrees on these two words (the ticket is zero between
+    // launches, and another handle's layout may overlay anything after them)
     h->status = (int *)take(4);
+    h->ticket = (unsigned *)take(4);
     const size_t HWp = (size_t)h->rows.Hp * h->rows.Wp;
     h->cen_pad = (uint64_t *)take((size_t)h->nviews * h->C * HWp * 8);
     h->views_pad = (float *)take((size_t)h->nviews * h->C * HWp * 4);
@@ -265,7 +271,8 @@ lfsgm_status bind_workspace(lfsgm_ctx *h, void *dptr, size_t bytes, bool owned) 
     h->fpen = (float *)take(2 * 4);
     h->partial = (double *)take(2 * kPartialBlocks * 8);
     h->tsum = (long long *)take((size_t)scan_tiles(h->N) * 8);
-    const cudaError_t e = cudaMemsetAsync(h->status, 0, 4, h->stream);
+    cudaError_t e = cudaMemsetAsync(h->status, 0, 4, h->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(h->ticket, 0, 4, h->stream);
     if (e != cudaSuccess) return cuda_fail(h, e, "status clear");
     return LFSGM_OK;
 }
@@ -343,6 +350,17 @@ lfsgm_status lfsgm_create(const lfsgm_config *cfg, void *stream, lfsgm_handle *o
             planes_of(sel_cross, h->arms.views[a][i]);
         }
     for (int i = 0; i < h->nviews; i++) planes_of(sel_all, i);
+    // the complement of the initial pass's planes (reference and arm views; with the paper's four
+    // extreme views the inner cross views are not among them)
+    std::vector<char> in_cross(h->nviews, 0);
+    in_cross[h->ref] = 1;
+    for (int a = 0; a < h->arms.n_arms; a++)
+        for (int i = 0; i < h->arms.nv[a]; i++) in_cross[h->arms.views[a][i]] = 1;
+    std::vector<int> sel_rest;
+    for (int i = 0; i < h->nviews; i++)
+        if (!in_cross[i]) planes_of(sel_rest, i);
+    h->n_sel_rest = (int)sel_rest.size();
+    if (sel_rest.empty()) sel_rest.push_back(0);          // (never launched: n_sel_rest = 0)
     // per arm: [nv][Lcd] linear offsets ny * Wp + nx of the nearest coarse shifts (0 = padding)
     std::vector<int> otab;
     h->ca.n_arms = h->arms.n_arms;
@@ -399,6 +417,7 @@ lfsgm_status lfsgm_create(const lfsgm_config *cfg, void *stream, lfsgm_handle *o
     ALLOC_COPY(h->d_armviews, armviews);
     ALLOC_COPY(h->d_sel_cross, sel_cross);
     ALLOC_COPY(h->d_sel_all, sel_all);
+    ALLOC_COPY(h->d_sel_rest, sel_rest);
 #undef ALLOC_COPY
     *out = h;
     return LFSGM_OK;
@@ -415,6 +434,7 @@ lfsgm_status lfsgm_destroy(lfsgm_handle h) {
     cudaFree(h->d_armviews);
     cudaFree(h->d_sel_cross);
     cudaFree(h->d_sel_all);
+    cudaFree(h->d_sel_rest);
     if (h->ws_owned) cudaFree(h->ws);
     cudaFree(h->o_lo); cudaFree(h->o_cnt); cudaFree(h->o_label); cudaFree(h->o_off);
     cudaFree(h->o_cost); cudaFree(h->o_agg); cudaFree(h->o_disp); cudaFree(h->o_views);
@@ -441,7 +461,7 @@ lfsgm_status lfsgm_workspace_size(lfsgm_handle h, size_t *bytes) {
     b += align256(N * (size_t)((h->cfg.fine_labels + 31) / 32) * 8);   // (pixel, chunk) list
     b += align256(4);                               // wide-pixel count
     b += align256(4 * 8) + align256(8 * 4) + align256(2 * 4);
-    b += align256(2 * kPartialBlocks * 8) + align256(4);
+    b += align256(2 * kPartialBlocks * 8) + 2 * align256(4);   // partials; status word and ticket
     b += align256((size_t)scan_tiles(h->N) * 8);    // offset-scan tile sums
     *bytes = b;
     return LFSGM_OK;
@@ -519,17 +539,29 @@ lfsgm_status lfsgm_initial_disparity(lfsgm_handle h, const float *views, int32_t
     return LFSGM_OK;
 }
 
-lfsgm_status lfsgm_cost_volume(lfsgm_handle h, const float *views, const int32_t *lo, const int32_t *cnt,
-                               const int64_t *off, float *cost) {
+}  // extern "C"
+
+namespace {
+// The cost stage; `cross_done`: the padded census and views of the cross views already hold these
+// views (the whole-method chain, right after its initial pass), so only the others are transformed.
+lfsgm_status cost_volume_impl(lfsgm_handle h, const float *views, const int32_t *lo, const int32_t *cnt,
+                              const int64_t *off, float *cost, bool cross_done) {
     if (!h) return LFSGM_ERR_INVALID_ARG;
     if (!views || !lo || !cnt || !off || !cost) return fail(h, LFSGM_ERR_INVALID_ARG, "null buffer");
     LFSGM_TRY(ensure_workspace(h));
     const lfsgm_config &c = h->cfg;
     cudaStream_t s = h->stream;
-    LFSGM_TRY(run(h, "census_all", [&] {
-        return launch_census_pad(s, views, c.H, c.W, c.census_w, h->rows.P, h->rows.Wp, h->rows.Hp, h->d_sel_all,
-                                 h->nviews * h->C, h->cen_pad, h->views_pad);
-    }));
+    if (!cross_done) {
+        LFSGM_TRY(run(h, "census_all", [&] {
+            return launch_census_pad(s, views, c.H, c.W, c.census_w, h->rows.P, h->rows.Wp, h->rows.Hp,
+                                     h->d_sel_all, h->nviews * h->C, h->cen_pad, h->views_pad);
+        }));
+    } else if (h->n_sel_rest > 0) {
+        LFSGM_TRY(run(h, "census_rest", [&] {
+            return launch_census_pad(s, views, c.H, c.W, c.census_w, h->rows.P, h->rows.Wp, h->rows.Hp,
+                                     h->d_sel_rest, h->n_sel_rest, h->cen_pad, h->views_pad);
+        }));
+    }
     const cudaError_t e = cudaMemsetAsync(h->wide_count, 0, 4, s);
     if (e != cudaSuccess) return cuda_fail(h, e, "memset");
     const float fstep = (float)((c.dmax - c.dmin) / (double)(c.fine_labels - 1));
@@ -552,6 +584,14 @@ lfsgm_status lfsgm_cost_volume(lfsgm_handle h, const float *views, const int32_t
                                      c.w_l2, c.w_census, cost, h->wide_list, h->wide_count);
     }));
     return LFSGM_OK;
+}
+}  // namespace
+
+extern "C" {
+
+lfsgm_status lfsgm_cost_volume(lfsgm_handle h, const float *views, const int32_t *lo, const int32_t *cnt,
+                               const int64_t *off, float *cost) {
+    return cost_volume_impl(h, views, lo, cnt, off, cost, false);
 }
 
 }  // extern "C"
@@ -584,10 +624,7 @@ lfsgm_status lfsgm_sgm_aggregate(lfsgm_handle h, const float *cost, const int32_
     if (derived) {
         LFSGM_TRY(run(h, "cost_partial_sums", [&] {
             return launch_cost_partial_sums(s, cost, cnt, o, h->N, c.fine_labels, h->partial, kPartialBlocks,
-                                            h->status);
-        }));
-        LFSGM_TRY(run(h, "fine_penalties", [&] {
-            return launch_fine_penalties(s, h->partial, kPartialBlocks, c.p1_frac, c.p2_frac, h->fpen);
+                                            c.p1_frac, c.p2_frac, h->fpen, h->ticket, h->status);
         }));
     } else {
         LFSGM_TRY(run(h, "set_penalties", [&] {
@@ -754,7 +791,7 @@ lfsgm_status depth_chain(lfsgm_handle h, const float *views, float *disp, int32_
         const cudaError_t e = cudaStreamWaitEvent(h->stream, wait, 0);
         if (e != cudaSuccess) return cuda_fail(h, e, "upload wait");
     }
-    LFSGM_TRY(lfsgm_cost_volume(h, views, h->o_lo, h->o_cnt, off, h->o_cost));
+    LFSGM_TRY(cost_volume_impl(h, views, h->o_lo, h->o_cnt, off, h->o_cost, !h->cfg.boundless));
     LFSGM_TRY(lfsgm_sgm_aggregate(h, h->o_cost, h->o_lo, h->o_cnt, off, -1.f, -1.f, h->o_agg));
     return lfsgm_wta_subpixel(h, h->o_agg, h->o_lo, h->o_cnt, off, label ? label : h->o_label,
                               disp ? disp : h->o_disp);
@@ -966,7 +1003,7 @@ lfsgm_status batch_build(lfsgm_batch_ctx *b, int K) {
             stamp_kernel<<<1, 1, 0, b->bs[k]>>>(b->stamps + 1 + 2 * i);
             int64_t *off = (int64_t *)x.off;
             st = lfsgm_initial_disparity(h, b->views[i], 0, 0, x.lo, x.cnt, off, nullptr, nullptr, nullptr);
-            if (st == LFSGM_OK) st = lfsgm_cost_volume(h, b->views[i], x.lo, x.cnt, off, x.cost);
+            if (st == LFSGM_OK) st = cost_volume_impl(h, b->views[i], x.lo, x.cnt, off, x.cost, !h->cfg.boundless);
             if (st == LFSGM_OK) st = lfsgm_sgm_aggregate(h, x.cost, x.lo, x.cnt, off, -1.f, -1.f, x.agg);
             if (st == LFSGM_OK) st = lfsgm_wta_subpixel(h, x.agg, x.lo, x.cnt, off, x.label, b->disp[i]);
             if (st != LFSGM_OK) {

@@ -186,12 +186,12 @@ cudaError_t launch_fine_cost_list(cudaStream_t s, const float *views_pad, const 
                                   const int *lo, const int *cnt, const long long *off, float wl2, float wc,
                                   float *cost, const int2 *list, const int *count);
 
-// partial: nblocks sums of the active costs followed by nblocks counts of active slots
+// Mean cost over the active slots and the derived penalties pen = (p1f, p2f) x mean, in one launch:
+// partial holds nblocks sums followed by nblocks counts; ticket (zero between launches) picks the
+// block that adds them up.
 cudaError_t launch_cost_partial_sums(cudaStream_t s, const float *cost, const int *cnt,
                                      const long long *off, int N, int G, double *partial, int nblocks,
-                                     int *status);
-cudaError_t launch_fine_penalties(cudaStream_t s, const double *partial, int nblocks,
-                                  double p1f, double p2f, float *pen);
+                                     double p1f, double p2f, float *pen, unsigned *ticket, int *status);
 cudaError_t launch_fine_sgm(cudaStream_t s, const float *cost, const int *lo, const int *cnt,
                             const long long *off, int H, int W, int G, const float *pen, float *agg,
                             int *status, const int *order, int paths);

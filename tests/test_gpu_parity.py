@@ -346,6 +346,15 @@ def test_depth_end_to_end_16_paths(gpu_lib):
     _check_end_to_end(g_label, g_disp, ref, p)
 
 
+def test_depth_end_to_end_paper_4_views(gpu_lib):
+    """The paper's initial views (the four extreme views only): the whole-method chain transforms
+    the inner cross views in its cost stage (the initial pass never touched them)."""
+    views, gt, p = lfsynth.tiny(params=lfsynth.tiny_params(init_views=0))
+    ref = oracle.depth(oracle.make_cfg(p), views, p1f=p.p1_frac, p2f=p.p2_frac)
+    g_label, g_disp, _ = _gpu_depth(gpu_lib, p, views)
+    _check_end_to_end(g_label, g_disp, ref, p)
+
+
 def test_depth_end_to_end_integer_planes_exact(gpu_lib):
     views, gt, p = lfsynth.integer_planes(H=96, W=96)
     cfg = oracle.make_cfg(p)
