@@ -50,10 +50,15 @@ __global__ void __launch_bounds__(32 * kSgmWarps) fine_sgm_kernel(const float *_
     int x0, y0;
     scan_start(r, s, H, W, x0, y0);
     const int len = scan_steps(x0, y0, dx, dy, H, W);
-    float *bufA = sm + (size_t)wib * 2 * Gs;   // predecessor's path costs (by slot), general steps
-    float *bufB = bufA + Gs;                   // this pixel's
+    // rows by slot with one sentinel slot on each side (slot -1 and slot n hold +inf), Gs + 2 floats
+    float *bufA = sm + (size_t)wib * 2 * (Gs + 2) + 1;   // predecessor's path costs, general steps
+    float *bufB = bufA + (Gs + 2);                       // this pixel's
     const float P1 = __ldg(pen), P2 = __ldg(pen + 1);
     const float INF = __int_as_float(0x7f800000);
+    if (lane == 0) {
+        bufA[-1] = INF;
+        bufB[-1] = INF;
+    }
     const long long p0 = (long long)y0 * W + x0, dpix = (long long)dy * W + dx;
     // window metadata of the 32 steps starting at kb, one step per lane: (lo | cnt << 16) with
     // cnt = 0 for an invalid window, and the row offset in units of 4 slots
@@ -111,10 +116,12 @@ __global__ void __launch_bounds__(32 * kSgmWarps) fine_sgm_kernel(const float *_
                     const float v0 = __shfl_sync(0xffffffffu, prev, s0 & 31);
                     const float vm = __shfl_sync(0xffffffffu, prev, (s0 - 1) & 31);
                     const float vp = __shfl_sync(0xffffffffu, prev, (s0 + 1) & 31);
-                    float t = m + P2;
+                    // min(L'(g-1) + P1, L'(g+1) + P1) = min(L'(g-1), L'(g+1)) + P1 exactly (rounding
+                    // is monotone); an absent neighbour is +inf
+                    const float a = (unsigned)(s0 - 1) < (unsigned)pn ? vm : INF;
+                    const float b = (unsigned)(s0 + 1) < (unsigned)pn ? vp : INF;
+                    float t = fminf(m + P2, fminf(a, b) + P1);
                     if ((unsigned)s0 < (unsigned)pn) t = fminf(t, v0);
-                    if ((unsigned)(s0 - 1) < (unsigned)pn) t = fminf(t, vm + P1);
-                    if ((unsigned)(s0 + 1) < (unsigned)pn) t = fminf(t, vp + P1);
                     Lv = c + (t - m);
                 }
                 const bool act = lane < n;
@@ -140,6 +147,7 @@ __global__ void __launch_bounds__(32 * kSgmWarps) fine_sgm_kernel(const float *_
             } else {
                 if (pn != 0 && !in_smem) {
                     if (lane < pn) bufA[lane] = prev;
+                    if (lane == 0) bufA[pn] = INF;
                     __syncwarp();
                 }
                 const long long o = 4ll * ofs;
@@ -155,11 +163,13 @@ __global__ void __launch_bounds__(32 * kSgmWarps) fine_sgm_kernel(const float *_
                         if (j >= n) break;
                         float Lv = cc[u];
                         if (pn != 0) {
+                            // slots of the predecessor, clamped to [-1, pn]: out of range reads a
+                            // sentinel (+inf), so an absent label drops out of the minimum
                             const int i = l + j - plo;
-                            float t = m + P2;
-                            if ((unsigned)i < (unsigned)pn) t = fminf(t, bufA[i]);
-                            if ((unsigned)(i - 1) < (unsigned)pn) t = fminf(t, bufA[i - 1] + P1);
-                            if ((unsigned)(i + 1) < (unsigned)pn) t = fminf(t, bufA[i + 1] + P1);
+                            const float v0 = bufA[min(max(i, -1), pn)];
+                            const float vm = bufA[min(max(i - 1, -1), pn)];
+                            const float vp = bufA[min(max(i + 1, -1), pn)];
+                            const float t = fminf(fminf(m + P2, v0), fminf(vm, vp) + P1);
                             Lv = cc[u] + (t - m);
                         }
                         bufB[j] = Lv;
@@ -168,6 +178,7 @@ __global__ void __launch_bounds__(32 * kSgmWarps) fine_sgm_kernel(const float *_
                     }
                 }
                 m = warp_min(lmin);
+                if (lane == 0) bufB[n] = INF;
                 __syncwarp();
                 float *tmp = bufA;
                 bufA = bufB;
@@ -293,7 +304,7 @@ cudaError_t launch_fine_sgm(cudaStream_t s, const float *cost, const int *lo, co
                             int *status, const int *order, int paths) {
     const ScanTable st = make_scan_table(H, W, paths);
     const int Gs = (G + 31) & ~31;
-    const size_t smem = (size_t)kSgmWarps * 2 * Gs * sizeof(float);
+    const size_t smem = (size_t)kSgmWarps * 2 * (Gs + 2) * sizeof(float);
     const unsigned grid = (unsigned)((st.cum[paths] + kSgmWarps - 1) / kSgmWarps);
     if (smem > 48 * 1024) {
         cudaError_t e = cudaFuncSetAttribute(fine_sgm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
