@@ -26,22 +26,51 @@ __global__ void wta_kernel(const float *__restrict__ agg, const int *__restrict_
     }
     int b = 0;
     float bv = s[0];
-    for (int j = 1; j < n; j++) {
-        const float v = s[j];
-        if (v < bv) { bv = v; b = j; }
+    const float it = 1.f / tau;
+    float num = 0.f, den = 0.f;
+    if (n <= 32) {
+        // the whole window in registers: its (16-byte aligned) row as 8 vector loads issued together
+        float v[32];
+        const float4 *r = reinterpret_cast<const float4 *>(s);
+#pragma unroll
+        for (int q = 0; q < 8; q++) {
+            const float4 w = 4 * q < n ? __ldg(r + q) : make_float4(0.f, 0.f, 0.f, 0.f);
+            v[4 * q] = w.x;
+            v[4 * q + 1] = w.y;
+            v[4 * q + 2] = w.z;
+            v[4 * q + 3] = w.w;
+        }
+        bv = v[0];
+#pragma unroll
+        for (int j = 1; j < 32; j++)
+            if (j < n && v[j] < bv) { bv = v[j]; b = j; }
+        if (mode == 2 && disp) {
+#pragma unroll
+            for (int j = 0; j < 32; j++)
+                if (j < n) {
+                    const float w = expf((bv - v[j]) * it);
+                    num = fmaf(w, (float)j, num);
+                    den += w;
+                }
+        }
+    } else {
+        for (int j = 1; j < n; j++) {
+            const float v = s[j];
+            if (v < bv) { bv = v; b = j; }
+        }
+        if (mode == 2 && disp) {
+            for (int j = 0; j < n; j++) {
+                const float w = expf((bv - s[j]) * it);
+                num = fmaf(w, (float)j, num);
+                den += w;
+            }
+        }
     }
     if (label) label[p] = l + b;
     if (!disp) return;
     if (mode == 2) {
-        // FP32 weights after subtracting the minimum (every exponent <= 0); the mean slot is
-        // mapped to a disparity in double
-        const float it = 1.f / tau;
-        float num = 0.f, den = 0.f;
-        for (int j = 0; j < n; j++) {
-            const float w = expf((bv - s[j]) * it);
-            num = fmaf(w, (float)j, num);
-            den += w;
-        }
+        // FP32 weights after subtracting the minimum (every exponent <= 0), summed in slot order;
+        // the mean slot is mapped to a disparity in double
         disp[p] = (float)(dmin + ((double)l + (double)(num / den)) * step);
         return;
     }
