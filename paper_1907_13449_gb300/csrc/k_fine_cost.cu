@@ -109,10 +109,11 @@ struct RowPlan {
 // build_fine_rows_desc): everything about the range that does not depend on the row segment.
 //   bytes  0..15  int16 xf, yf, xc, yc: tile origins relative to (x0, y); uint8 nseg, ncen
 //   bytes 16..23  uint64 smask: bit i set where label i starts a segment (bit 0 always)
+//   bytes 24..31  float ax, ay: the view's (u-uc) * step and (v-vc) * step
 //   bytes 32..    int4 seg[seg_cap]: tile offset of the segment's (0,0) tap for lane 0, first
 //                 label, fx, fy (float bits)
 //   then          uint32 cen[seg_cap]: census breakpoint label | tile offset of its word << 8
-constexpr int kDsMask = 16, kDsSegs = 32;
+constexpr int kDsMask = 16, kDsAxy = 24, kDsSegs = 32;
 
 __device__ __forceinline__ unsigned smem_u32(const void *p) { return (unsigned)__cvta_generic_to_shared(p); }
 
@@ -153,7 +154,7 @@ __global__ void __launch_bounds__(128, 4) fine_cost_rows(const __grid_constant__
     unsigned char *coef = wb + pl.o_coef;                   // float4 (A, B, C, -) [seg_cap][32]
     short *cdiff = (short *)(wb + pl.o_cdiff);              // [KW][32] census steps (|sum| <= views x 48)
     const unsigned mbar0 = smem_u32(wb + pl.o_mbar);
-    const int nviews = U * V, uc = ref % U, vc = ref / U;
+    const int nviews = U * V;
     const size_t HWp = (size_t)pl.Hp * pl.Wp;
     const int tiles_x = (W + 31) >> 5;
     const int task = blockIdx.x * wpb + wib;
@@ -271,7 +272,8 @@ __global__ void __launch_bounds__(128, 4) fine_cost_rows(const __grid_constant__
             }
         }
         // l2 term: per cell segment this lane's sample polynomial in the absolute label index
-        const float ax = (float)(view % U - uc) * fstep, ay = (float)(view / U - vc) * fstep;
+        const float2 axy = *(const float2 *)(ds + kDsAxy);
+        const float ax = axy.x, ay = axy.y;
         for (int sgi = 0; sgi < nseg; sgi++) {
             const int4 sd = segs[sgi];
             const float tfx = __int_as_float(sd.z), tfy = __int_as_float(sd.w);
@@ -496,6 +498,9 @@ bool build_fine_rows_desc(const RowPlanHost *ph, const FineTap *tab, int U, int 
             uint64_t smask = 0;
             for (int i : segstart) smask |= 1ull << i;
             memcpy(d + kDsMask, &smask, 8);
+            // the view's disparity-to-shift factors (u-uc) * step, (v-vc) * step, as the kernel's FP32
+            const float axy[2] = {a * fstep, b * fstep};
+            memcpy(d + kDsAxy, axy, 8);
             int32_t *seg = (int32_t *)(d + kDsSegs);
             for (size_t k = 0; k < segstart.size(); k++) {
                 const FineTap &w = t[segstart[k]];
