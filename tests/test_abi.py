@@ -89,6 +89,10 @@ def _raw_create(lib, **kw):
     ("p2_frac", 0.01, "p1_frac"),
     ("subpixel", 3, "subpixel"),
     ("softmin_tau", 0.0, "softmin_tau"),
+    ("paths", 12, "paths"),
+    ("edge_threshold", -1.0, "edge_threshold"),
+    ("channels", 2, "channels"),
+    ("boundless", 2, "boundless"),
     ("U", 1, None),
 ])
 def test_invalid_config_rejected_before_any_cuda_call(lib, field, value, needle):
