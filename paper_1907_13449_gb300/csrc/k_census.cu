@@ -99,7 +99,10 @@ __device__ __forceinline__ void census_word2(const float *t, int ld, float c0, f
 // at any padded position (xp, yp) returns the word/value of pixel (clamp(xp-P), clamp(yp-P)) --
 // exactly the clamped read of the unpadded image.  Padded row stride Wp, Hp rows per view.
 // A 32 x 4 thread block covers a 32 x 8 tile: each thread takes two vertically adjacent pixels.
-template <int HALF>
+// Colour (C = 3): one block per view transforms the C channel planes in turn (census words go to
+// the planes view * C + c), and the padded view is written interleaved, one float4 (the C
+// channels and a zero) per pixel, so that a bilinear tap of all channels is one 16-byte load.
+template <int HALF, int C>
 __global__ void __launch_bounds__(TX *TY / 2) census_pad_kernel(const float *__restrict__ views, int H, int W, int P,
                                                                 int Wp, int Hp, const int *__restrict__ sel,
                                                                 uint64_t *__restrict__ cen_pad,
@@ -108,45 +111,65 @@ __global__ void __launch_bounds__(TX *TY / 2) census_pad_kernel(const float *__r
     __shared__ float tile[SH][SW + 1];
     const size_t HW = (size_t)H * W, HWp = (size_t)Hp * Wp;
     const int view = sel[blockIdx.z];
-    const float *img = views + (size_t)view * HW;
     const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
     const int tid = threadIdx.y * TX + threadIdx.x;
-    for (int i = tid; i < SH * SW; i += TX * TY / 2) {
-        int ty = i / SW, tx = i - ty * SW;
-        int gy = min(max(y0 + ty - HALF, 0), H - 1);
-        int gx = min(max(x0 + tx - HALF, 0), W - 1);
-        tile[ty][tx] = __ldg(img + (size_t)gy * W + gx) + 0.0f;   // -0 becomes +0 (see census_word)
-    }
-    __syncthreads();
     const int x = x0 + threadIdx.x, ty0 = 2 * threadIdx.y, y = y0 + ty0;
-    if (x >= W || y >= H) return;
-    const float c0 = tile[ty0 + HALF][threadIdx.x + HALF], c1 = tile[ty0 + 1 + HALF][threadIdx.x + HALF];
-    uint64_t w[2];
-    census_word2<HALF>(&tile[ty0][threadIdx.x], SW + 1, c0, c1, w[0], w[1]);
-    const float cv[2] = {c0, c1};
-    uint64_t *cp = cen_pad + (size_t)view * HWp;
-    float *vp = views_pad + (size_t)view * HWp;
+    const bool inb = x < W && y < H;
     const int xa = x == 0 ? 0 : x + P, xb = x == W - 1 ? Wp - 1 : x + P;
+    float cv[2][C];
 #pragma unroll
-    for (int r = 0; r < 2; r++) {
-        const int yr = y + r;
-        if (yr >= H) break;
-        const int ya = yr == 0 ? 0 : yr + P, yb = yr == H - 1 ? Hp - 1 : yr + P;
-        for (int yy = ya; yy <= yb; yy++)
-            for (int xx = xa; xx <= xb; xx++) {
-                cp[(size_t)yy * Wp + xx] = w[r];
-                vp[(size_t)yy * Wp + xx] = cv[r];
+    for (int ch = 0; ch < C; ch++) {
+        const float *img = views + ((size_t)view * C + ch) * HW;
+        if (ch) __syncthreads();                                   // the previous channel's tile is used up
+        for (int i = tid; i < SH * SW; i += TX * TY / 2) {
+            int ty = i / SW, tx = i - ty * SW;
+            int gy = min(max(y0 + ty - HALF, 0), H - 1);
+            int gx = min(max(x0 + tx - HALF, 0), W - 1);
+            tile[ty][tx] = __ldg(img + (size_t)gy * W + gx) + 0.0f;   // -0 becomes +0 (see census_word)
+        }
+        __syncthreads();
+        if (inb) {
+            const float c0 = tile[ty0 + HALF][threadIdx.x + HALF], c1 = tile[ty0 + 1 + HALF][threadIdx.x + HALF];
+            uint64_t w[2];
+            census_word2<HALF>(&tile[ty0][threadIdx.x], SW + 1, c0, c1, w[0], w[1]);
+            cv[0][ch] = c0;
+            cv[1][ch] = c1;
+            uint64_t *cp = cen_pad + ((size_t)view * C + ch) * HWp;
+            // the census words of this channel, and with the last channel the padded view
+#pragma unroll
+            for (int r = 0; r < 2; r++) {
+                const int yr = y + r;
+                if (yr >= H) break;
+                const int ya = yr == 0 ? 0 : yr + P, yb = yr == H - 1 ? Hp - 1 : yr + P;
+                for (int yy = ya; yy <= yb; yy++)
+                    for (int xx = xa; xx <= xb; xx++) {
+                        const size_t q = (size_t)yy * Wp + xx;
+                        cp[q] = w[r];
+                        if (ch == C - 1) {
+                            if constexpr (C == 1)
+                                views_pad[(size_t)view * HWp + q] = cv[r][0];
+                            else
+                                reinterpret_cast<float4 *>(views_pad)[(size_t)view * HWp + q] =
+                                    make_float4(cv[r][0], cv[r][1], cv[r][2], 0.f);
+                        }
+                    }
             }
+        }
     }
 }
 
 }  // namespace
 
 cudaError_t launch_census_pad(cudaStream_t s, const float *views, int H, int W, int census_w, int P, int Wp, int Hp,
-                              const int *d_sel, int nsel, uint64_t *cen_pad, float *views_pad) {
+                              int C, const int *d_sel, int nsel, uint64_t *cen_pad, float *views_pad) {
     dim3 block(TX, TY / 2), grid((W + TX - 1) / TX, (H + TY - 1) / TY, nsel);
-    if (census_w == 5) census_pad_kernel<2><<<grid, block, 0, s>>>(views, H, W, P, Wp, Hp, d_sel, cen_pad, views_pad);
-    else census_pad_kernel<3><<<grid, block, 0, s>>>(views, H, W, P, Wp, Hp, d_sel, cen_pad, views_pad);
+    if (C == 3) {
+        if (census_w == 5) census_pad_kernel<2, 3><<<grid, block, 0, s>>>(views, H, W, P, Wp, Hp, d_sel, cen_pad, views_pad);
+        else census_pad_kernel<3, 3><<<grid, block, 0, s>>>(views, H, W, P, Wp, Hp, d_sel, cen_pad, views_pad);
+    } else {
+        if (census_w == 5) census_pad_kernel<2, 1><<<grid, block, 0, s>>>(views, H, W, P, Wp, Hp, d_sel, cen_pad, views_pad);
+        else census_pad_kernel<3, 1><<<grid, block, 0, s>>>(views, H, W, P, Wp, Hp, d_sel, cen_pad, views_pad);
+    }
     return cudaGetLastError();
 }
 

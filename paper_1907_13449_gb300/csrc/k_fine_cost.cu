@@ -324,9 +324,11 @@ __global__ void __launch_bounds__(128, 4) fine_cost_rows(const __grid_constant__
 // one warp per item, lane = label of the chunk, taps read from the padded views and census words
 // (no clamping needed) at linear offsets (oy Wp + ox, ny Wp + nx).  Each lane reads its label's
 // table entry of a view with one coalesced 16-byte load (the warp's 32 entries are contiguous);
-// two views per unrolled step keep their loads in flight together.  Colour (C > 1): the images
-// are planes view * C + c; each tap samples every channel, the l2 term is the Euclidean norm of
-// the colour difference and the census term sums the channels' Hamming distances (Sec. III-B/C).
+// two views per unrolled step keep their loads in flight together.  Colour (C > 1): the padded
+// views hold one float4 per pixel (channels interleaved), so a bilinear tap of all channels is
+// four 16-byte loads, and the census words are planes view * C + c; the l2 term is the Euclidean
+// norm of the colour difference and the census term sums the channels' Hamming distances
+// (Sec. III-B/C).
 constexpr int kListWarps = 4;
 
 template <int C>
@@ -356,33 +358,49 @@ __global__ void __launch_bounds__(32 * kListWarps) fine_cost_list(const float *_
         float sl2 = 0.f;
         int sc = 0;
         if (j < n) {
-            float Iref[C];
             uint64_t cr[C];
 #pragma unroll
-            for (int ch = 0; ch < C; ch++) {
-                Iref[ch] = __ldg(views_pad + ((size_t)ref * C + ch) * HWp + base);
-                cr[ch] = __ldg(cen_pad + ((size_t)ref * C + ch) * HWp + base);
-            }
+            for (int ch = 0; ch < C; ch++) cr[ch] = __ldg(cen_pad + ((size_t)ref * C + ch) * HWp + base);
             const int4 *tg = ltab + l0 + j;
+            if constexpr (C == 1) {
+                const float Iref = __ldg(views_pad + (size_t)ref * HWp + base);
 #pragma unroll 2
-            for (int vi = 0; vi < nv1; vi++) {
-                const int view = vi + (vi >= ref);
-                const int4 tw = __ldg(tg + (size_t)view * G);     // linear tap offsets (x + Wp y), fx, fy
-                const size_t vb = (size_t)view * C * HWp + base;
-                const float tfx = __int_as_float(tw.z), tfy = __int_as_float(tw.w);
-                float sq = 0.f;
-#pragma unroll
-                for (int ch = 0; ch < C; ch++) {
-                    const float *q = views_pad + vb + ch * HWp + tw.x;
+                for (int vi = 0; vi < nv1; vi++) {
+                    const int view = vi + (vi >= ref);
+                    const int4 tw = __ldg(tg + (size_t)view * G);     // linear tap offsets (x + Wp y), fx, fy
+                    const size_t vb = (size_t)view * HWp + base;
+                    const float tfx = __int_as_float(tw.z), tfy = __int_as_float(tw.w);
+                    const float *q = views_pad + vb + tw.x;
                     const float i00 = __ldg(q), i10 = __ldg(q + 1), i01 = __ldg(q + Wp), i11 = __ldg(q + Wp + 1);
                     const float top = (1.f - tfx) * i00 + tfx * i10;
                     const float bot = (1.f - tfx) * i01 + tfx * i11;
-                    const float dl = Iref[ch] - ((1.f - tfy) * top + tfy * bot);
-                    if (C == 1) sl2 += fabsf(dl);
-                    else sq = fmaf(dl, dl, sq);
-                    sc += __popcll(cr[ch] ^ __ldg(cen_pad + vb + ch * HWp + tw.y));
+                    sl2 += fabsf(Iref - ((1.f - tfy) * top + tfy * bot));
+                    sc += __popcll(cr[0] ^ __ldg(cen_pad + vb + tw.y));
                 }
-                if (C > 1) sl2 += sqrtf(sq);
+            } else {
+                const float4 *v4 = reinterpret_cast<const float4 *>(views_pad);
+                const float4 Iref = __ldg(v4 + (size_t)ref * HWp + base);
+#pragma unroll 2
+                for (int vi = 0; vi < nv1; vi++) {
+                    const int view = vi + (vi >= ref);
+                    const int4 tw = __ldg(tg + (size_t)view * G);
+                    const size_t pb = (size_t)view * HWp + base;
+                    const float tfx = __int_as_float(tw.z), tfy = __int_as_float(tw.w);
+                    const float4 *q = v4 + pb + tw.x;
+                    const float4 a = __ldg(q), b = __ldg(q + 1), c = __ldg(q + Wp), d = __ldg(q + Wp + 1);
+                    auto sample = [&](float i00, float i10, float i01, float i11) {
+                        const float top = (1.f - tfx) * i00 + tfx * i10;
+                        const float bot = (1.f - tfx) * i01 + tfx * i11;
+                        return (1.f - tfy) * top + tfy * bot;
+                    };
+                    const float d0 = Iref.x - sample(a.x, b.x, c.x, d.x);
+                    const float d1 = Iref.y - sample(a.y, b.y, c.y, d.y);
+                    const float d2 = Iref.z - sample(a.z, b.z, c.z, d.z);
+                    sl2 += sqrtf(fmaf(d2, d2, fmaf(d1, d1, d0 * d0)));
+#pragma unroll
+                    for (int ch = 0; ch < C; ch++)
+                        sc += __popcll(cr[ch] ^ __ldg(cen_pad + ((size_t)view * C + ch) * HWp + base + tw.y));
+                }
             }
         }
         if (j < npad) cost[o + j] = (j < n) ? wl2 * sl2 + wc * (float)sc : 0.f;

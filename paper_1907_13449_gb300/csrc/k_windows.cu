@@ -56,10 +56,10 @@ __global__ void fill_kernel(const int *__restrict__ Fin, int *__restrict__ Fout,
 // Edge test of the border exclusion (Sec. III-D) on the edge-padded reference view (a padded read
 // is the clamped read): the 3 x 3 Sobel sums, their squares and the comparison in FP32 with
 // explicit rounding, in the order the oracle uses, so both take the same decision.
-__device__ __forceinline__ bool sobel_edge(const float *I, int Wp, float t) {
-    const float q0 = I[-Wp - 1], q1 = I[-Wp], q2 = I[-Wp + 1];
-    const float q3 = I[-1], q5 = I[1];
-    const float q6 = I[Wp - 1], q7 = I[Wp], q8 = I[Wp + 1];
+__device__ __forceinline__ bool sobel_edge(const float *I, int sx, int sy, float t) {
+    const float q0 = I[-sy - sx], q1 = I[-sy], q2 = I[-sy + sx];
+    const float q3 = I[-sx], q5 = I[sx];
+    const float q6 = I[sy - sx], q7 = I[sy], q8 = I[sy + sx];
     const float gx = __fsub_rn(__fadd_rn(__fadd_rn(q2, __fmul_rn(2.0f, q5)), q8),
                                __fadd_rn(__fadd_rn(q0, __fmul_rn(2.0f, q3)), q6));
     const float gy = __fsub_rn(__fadd_rn(__fadd_rn(q6, __fmul_rn(2.0f, q7)), q8),
@@ -69,16 +69,18 @@ __device__ __forceinline__ bool sobel_edge(const float *I, int Wp, float t) {
 
 __global__ void windows_kernel(const int *__restrict__ F, int N, int G, int Lc, int R, int *__restrict__ lo,
                                int *__restrict__ cnt, float *__restrict__ dinit, int *__restrict__ cntpad,
-                               const float *__restrict__ ref_pad, int C, size_t HWp, int P, int Wp, int W,
+                               const float *__restrict__ ref_pad, int C, int P, int Wp, int W,
                                float edge_t, int Rfar, int boundless) {
     const int p = blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= N) return;
     const int v = boundless ? -1 : F[p];
-    // an edge in any channel of the reference view (its C padded planes, HWp apart)
+    // an edge in any channel of the padded reference view (colour: one float4 per pixel, the
+    // channels interleaved)
     bool edge = false;
     if (edge_t > 0.f && !boundless) {
-        const float *q = ref_pad + (size_t)(p / W + P) * Wp + (p % W + P);
-        for (int ch = 0; ch < C && !edge; ch++) edge = sobel_edge(q + ch * HWp, Wp, edge_t);
+        const int sx = C == 1 ? 1 : 4;
+        const float *q = ref_pad + ((size_t)(p / W + P) * Wp + (p % W + P)) * sx;
+        for (int ch = 0; ch < C && !edge; ch++) edge = sobel_edge(q + ch, sx, sx * Wp, edge_t);
     }
     int a, n;
     if (v < 0 || edge) {
@@ -185,9 +187,9 @@ cudaError_t launch_fill(cudaStream_t s, const int *Fin, int *Fout, int H, int W)
     return cudaGetLastError();
 }
 cudaError_t launch_windows(cudaStream_t s, const int *F, int N, int G, int Lc, int R, int *lo, int *cnt,
-                           float *dinit, int *cntpad, const float *ref_pad, int C, size_t HWp, int P, int Wp,
+                           float *dinit, int *cntpad, const float *ref_pad, int C, int P, int Wp,
                            int W, float edge_t, int Rfar, int boundless) {
-    windows_kernel<<<(N + 255) / 256, 256, 0, s>>>(F, N, G, Lc, R, lo, cnt, dinit, cntpad, ref_pad, C, HWp, P, Wp,
+    windows_kernel<<<(N + 255) / 256, 256, 0, s>>>(F, N, G, Lc, R, lo, cnt, dinit, cntpad, ref_pad, C, P, Wp,
                                                    W, edge_t, Rfar, boundless);
     return cudaGetLastError();
 }

@@ -62,10 +62,10 @@ struct lfsgm_ctx {
     int *d_otab = nullptr;       // coarse census offsets per (arm view, label), see CoarseArms
     CoarseArms ca{};
     int *d_armviews = nullptr;   // [4][kMaxArmViews]
-    int *d_sel_cross = nullptr;  // planes of the reference and the arm views
+    int *d_sel_cross = nullptr;  // the reference and the arm views
     int n_sel_cross = 0;
-    int *d_sel_all = nullptr;    // planes of every view
-    int *d_sel_rest = nullptr;   // planes of the views that are not cross views
+    int *d_sel_all = nullptr;    // every view
+    int *d_sel_rest = nullptr;   // the views that are not in d_sel_cross
     int n_sel_rest = 0;
     // workspace
     void *ws = nullptr;
@@ -256,7 +256,7 @@ lfsgm_status bind_workspace(lfsgm_ctx *h, void *dptr, size_t bytes, bool owned) 
     h->ticket = (unsigned *)take(4);
     const size_t HWp = (size_t)h->rows.Hp * h->rows.Wp;
     h->cen_pad = (uint64_t *)take((size_t)h->nviews * h->C * HWp * 8);
-    h->views_pad = (float *)take((size_t)h->nviews * h->C * HWp * 4);
+    h->views_pad = (float *)take((size_t)h->nviews * HWp * (h->C > 1 ? 16 : 4));   // colour: float4 per pixel
     h->rows_maps = h->rows.ok && encode_fine_rows_maps(&h->rows, h->views_pad, h->cen_pad, h->nviews);
     h->ccost = take(A * N * h->Lcd * (h->cost8 ? 1 : 2));
     h->csum = (uint16_t *)take(A * N * h->Lcd * 2);
@@ -340,16 +340,13 @@ lfsgm_status lfsgm_create(const lfsgm_config *cfg, void *stream, lfsgm_handle *o
             }
         }
     std::vector<int> armviews(4 * kMaxArmViews, 0), sel_cross, sel_all;
-    auto planes_of = [&](std::vector<int> &sel, int view) {
-        for (int ch = 0; ch < h->C; ch++) sel.push_back(view * h->C + ch);
-    };
-    planes_of(sel_cross, h->ref);
+    sel_cross.push_back(h->ref);
     for (int a = 0; a < h->arms.n_arms; a++)
         for (int i = 0; i < h->arms.nv[a]; i++) {
             armviews[a * kMaxArmViews + i] = h->arms.views[a][i];
-            planes_of(sel_cross, h->arms.views[a][i]);
+            sel_cross.push_back(h->arms.views[a][i]);
         }
-    for (int i = 0; i < h->nviews; i++) planes_of(sel_all, i);
+    for (int i = 0; i < h->nviews; i++) sel_all.push_back(i);
     // the complement of the initial pass's planes (reference and arm views; with the paper's four
     // extreme views the inner cross views are not among them)
     std::vector<char> in_cross(h->nviews, 0);
@@ -358,7 +355,7 @@ lfsgm_status lfsgm_create(const lfsgm_config *cfg, void *stream, lfsgm_handle *o
         for (int i = 0; i < h->arms.nv[a]; i++) in_cross[h->arms.views[a][i]] = 1;
     std::vector<int> sel_rest;
     for (int i = 0; i < h->nviews; i++)
-        if (!in_cross[i]) planes_of(sel_rest, i);
+        if (!in_cross[i]) sel_rest.push_back(i);
     h->n_sel_rest = (int)sel_rest.size();
     if (sel_rest.empty()) sel_rest.push_back(0);          // (never launched: n_sel_rest = 0)
     // per arm: [nv][Lcd] linear offsets ny * Wp + nx of the nearest coarse shifts (0 = padding)
@@ -453,7 +450,7 @@ lfsgm_status lfsgm_workspace_size(lfsgm_handle h, size_t *bytes) {
     size_t b = 0;
     const size_t HWp = (size_t)h->rows.Hp * h->rows.Wp;
     b += align256((size_t)h->nviews * h->C * HWp * 8);   // census words per plane, edge-replicated padding
-    b += align256((size_t)h->nviews * h->C * HWp * 4);   // views per plane, edge-replicated padding
+    b += align256((size_t)h->nviews * HWp * (h->C > 1 ? 16 : 4));   // views, edge-replicated padding
     b += align256(A * N * h->Lcd * (h->cost8 ? 1 : 2));   // coarse cost (bytes when they fit)
     b += align256(A * N * h->Lcd * 2);              // coarse path sums
     b += align256(4 * N * 4);                       // maps
@@ -494,7 +491,7 @@ lfsgm_status lfsgm_initial_disparity(lfsgm_handle h, const float *views, int32_t
     cudaError_t e = cudaSuccess;
     if (!c.boundless) {   // boundary-less: no initial map, the windows kernel writes whole-range windows
         LFSGM_TRY(run(h, "census_cross", [&] {
-            return launch_census_pad(s, views, c.H, c.W, c.census_w, h->rows.P, h->rows.Wp, h->rows.Hp,
+            return launch_census_pad(s, views, c.H, c.W, c.census_w, h->rows.P, h->rows.Wp, h->rows.Hp, h->C,
                                      h->d_sel_cross, h->n_sel_cross, h->cen_pad, h->views_pad);
         }));
         e = cudaMemsetAsync(h->armsum, 0, 4 * 8, s);
@@ -524,9 +521,8 @@ lfsgm_status lfsgm_initial_disparity(lfsgm_handle h, const float *views, int32_t
     }
     LFSGM_TRY(run(h, "windows", [&] {
         return launch_windows(s, fin, N, c.fine_labels, c.coarse_labels, c.fine_radius, lo, cnt, dinit, h->cntpad,
-                              h->views_pad + (size_t)h->ref * h->C * h->rows.Hp * h->rows.Wp, h->C,
-                              (size_t)h->rows.Hp * h->rows.Wp, h->rows.P, h->rows.Wp, c.W, c.edge_threshold,
-                              c.fine_radius_far, c.boundless);
+                              h->views_pad + (size_t)h->ref * h->rows.Hp * h->rows.Wp * (h->C > 1 ? 4 : 1), h->C,
+                              h->rows.P, h->rows.Wp, c.W, c.edge_threshold, c.fine_radius_far, c.boundless);
     }));
     LFSGM_TRY(run(h, "scan_sums", [&] { return launch_scan_sums(s, h->cntpad, N, h->tsum); }));
     LFSGM_TRY(run(h, "scan_top", [&] { return launch_scan_top(s, h->tsum, N); }));
@@ -553,12 +549,12 @@ lfsgm_status cost_volume_impl(lfsgm_handle h, const float *views, const int32_t 
     cudaStream_t s = h->stream;
     if (!cross_done) {
         LFSGM_TRY(run(h, "census_all", [&] {
-            return launch_census_pad(s, views, c.H, c.W, c.census_w, h->rows.P, h->rows.Wp, h->rows.Hp,
-                                     h->d_sel_all, h->nviews * h->C, h->cen_pad, h->views_pad);
+            return launch_census_pad(s, views, c.H, c.W, c.census_w, h->rows.P, h->rows.Wp, h->rows.Hp, h->C,
+                                     h->d_sel_all, h->nviews, h->cen_pad, h->views_pad);
         }));
     } else if (h->n_sel_rest > 0) {
         LFSGM_TRY(run(h, "census_rest", [&] {
-            return launch_census_pad(s, views, c.H, c.W, c.census_w, h->rows.P, h->rows.Wp, h->rows.Hp,
+            return launch_census_pad(s, views, c.H, c.W, c.census_w, h->rows.P, h->rows.Wp, h->rows.Hp, h->C,
                                      h->d_sel_rest, h->n_sel_rest, h->cen_pad, h->views_pad);
         }));
     }

@@ -148,7 +148,7 @@ cudaError_t launch_coarse_wta(cudaStream_t s, const uint16_t *sum, int narms, in
 cudaError_t launch_fuse(cudaStream_t s, const int *maps, int narms, int N, double phi, int *F);
 cudaError_t launch_fill(cudaStream_t s, const int *Fin, int *Fout, int H, int W);
 cudaError_t launch_windows(cudaStream_t s, const int *F, int N, int G, int Lc, int R, int *lo,
-                           int *cnt, float *dinit, int *cntpad, const float *ref_pad, int C, size_t HWp, int P,
+                           int *cnt, float *dinit, int *cntpad, const float *ref_pad, int C, int P,
                            int Wp, int W, float edge_t, int Rfar, int boundless);
 int scan_tiles(int N);   // tiles of the offset scan (tile sums buffer length)
 cudaError_t launch_scan_sums(cudaStream_t s, const int *cntpad, int N, long long *tsum);
@@ -171,8 +171,10 @@ struct RowPlanHost {
 };
 bool plan_fine_rows(int U, int V, int uc, int vc, int H, int W, int G, double dmin, double dmax, RowPlanHost *out);
 bool encode_fine_rows_maps(RowPlanHost *ph, const float *views_pad, const uint64_t *cen_pad, int nviews);
+// Census words (planes view * C + c) and the edge-padded views (C = 1: float planes; C = 3: one
+// float4 per pixel, channels interleaved) of the views listed in d_sel.
 cudaError_t launch_census_pad(cudaStream_t s, const float *views, int H, int W, int census_w, int P, int Wp,
-                              int Hp, const int *d_sel, int nsel, uint64_t *cen_pad, float *views_pad);
+                              int Hp, int C, const int *d_sel, int nsel, uint64_t *cen_pad, float *views_pad);
 bool build_fine_rows_desc(const RowPlanHost *ph, const FineTap *tab, int U, int V, int uc, int vc, int G,
                           float dmin, float fstep, std::vector<unsigned char> &out);
 cudaError_t launch_fine_cost_rows(cudaStream_t s, const RowPlanHost *ph, const float *views_pad,
