@@ -197,3 +197,15 @@ def test_rgb_is_unsupported_without_a_handle(gpu_lib):
         gpu_lib.lfsgm_cost_volume_noalloc(p, x, i, i, o, x)
     with pytest.raises(gpu_lib.LfsgmError):
         gpu_lib.lfsgm_create(dataclasses.replace(p, channels=2))
+
+
+def test_rgb_boundless_with_depth_dependent_radius_variants(gpu_lib):
+    """Colour with the window variants: the boundary-less search (every window the whole range,
+    list kernel only) and, separately, the depth-dependent border threshold."""
+    views, gt, p = _rgb_tiny(3, H=40, W=44, boundless=1)
+    ref = oracle.depth(oracle.make_cfg(p), views, p1f=p.p1_frac, p2f=p.p2_frac)
+    g_label, g_disp, _ = _gpu_depth(gpu_lib, p, views)
+    _check_end_to_end(g_label, g_disp, ref, p)
+    views, gt, p = _rgb_tiny(4, fine_radius=2, fine_radius_far=7)
+    ref = oracle.initial_disparity(oracle.make_cfg(p), views, None, p.p1_frac, p.p2_frac)
+    _check_initial(_run_initial(gpu_lib, p, views), ref, p)
