@@ -76,3 +76,24 @@ def test_depth_host_matches_device(gpu_lib, kind):
         assert np.max(np.abs(dh.numpy() - _np(disp))) < 1e-5
     gpu_lib.lfsgm_sync(h)
     gpu_lib.lfsgm_destroy(h)
+
+
+def test_boundless_and_bounded_light_fields_in_one_batch(gpu_lib):
+    """A batch branch shares its workspace between a boundary-less light field (no initial pass)
+    and bounded ones (their cost stage reuses the initial pass's census planes)."""
+    import torch
+    from lf_helpers import DISP_TOL, TIE_REL, best_of
+    members = [lfsynth.tiny(5, params=lfsynth.tiny_params(boundless=1, H=40, W=48)),
+               lfsynth.tiny(6, params=lfsynth.tiny_params(H=48, W=40, init_views=0)),
+               lfsynth.tiny(7, params=lfsynth.tiny_params(H=36, W=52, fine_radius=3, fine_radius_far=8))]
+    views = [torch.from_numpy(v).cuda() for v, _, _ in members]
+    b = gpu_lib.LightFieldBatch([m[2] for m in members], views, branches=1)
+    disp = [d.cpu().numpy() for d in b.run()]
+    torch.cuda.synchronize()
+    b.close()
+    for d, (v, _, p) in zip(disp, members):
+        ref = oracle.depth(oracle.make_cfg(p), v, p1f=p.p1_frac, p2f=p.p2_frac)
+        best = best_of(ref["Cs"], ref["off"], ref["cnt"], ref["label"], ref["lo"])
+        decided = ref["gap"] > TIE_REL * np.maximum(1.0, np.abs(best))
+        assert decided.sum() > 0.9 * p.N
+        assert np.max(np.abs(d - ref["disp"])[decided]) < DISP_TOL, p.name
