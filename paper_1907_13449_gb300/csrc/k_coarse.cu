@@ -209,31 +209,26 @@ __device__ __forceinline__ void red_words(uint16_t *dst, const uint32_t *v) {
 // below 2^14; labels below 0 read 0x7fff.  The absent labels' sums overflow their halfwords,
 // but a carry only runs into higher, also absent, labels or out of the reduced word, and the
 // WTA reads labels below Lc only.
-// Byte costs (C8): a lane's LPT bytes are one 2/4/8-byte load, widened to halfword pairs by byte
-// permutes, with kAbsent or-ed into the absent labels' halves (their bytes are 0).
+// Byte costs (C8): a lane's LPT bytes are one 2/4/8-byte load, widened to halfword pairs by one
+// byte permute per pair that also puts kAbsent into the absent labels' halves.
 template <int LPT>
 struct BVec;
 template <>
 struct BVec<2> {
     using T = uint16_t;
-    __device__ static void widen(T v, uint32_t *c) { c[0] = __byte_perm((uint32_t)v, 0, 0x4140); }
+    __device__ static void words(T v, uint32_t *w) { w[0] = (uint32_t)v; }
 };
 template <>
 struct BVec<4> {
     using T = uint32_t;
-    __device__ static void widen(T v, uint32_t *c) {
-        c[0] = __byte_perm(v, 0, 0x4140);
-        c[1] = __byte_perm(v, 0, 0x4342);
-    }
+    __device__ static void words(T v, uint32_t *w) { w[0] = v; }
 };
 template <>
 struct BVec<8> {
     using T = uint2;
-    __device__ static void widen(T v, uint32_t *c) {
-        c[0] = __byte_perm(v.x, 0, 0x4140);
-        c[1] = __byte_perm(v.x, 0, 0x4342);
-        c[2] = __byte_perm(v.y, 0, 0x4140);
-        c[3] = __byte_perm(v.y, 0, 0x4342);
+    __device__ static void words(T v, uint32_t *w) {
+        w[0] = v.x;
+        w[1] = v.y;
     }
 };
 
@@ -266,11 +261,17 @@ __global__ void __launch_bounds__(128) coarse_sgm_kernel(const void *__restrict_
     const uint32_t P1 = (uint32_t)__ldg(pen + 2 * arm), P2 = (uint32_t)__ldg(pen + 2 * arm + 1);
     const uint32_t P1P1 = P1 * 0x10001u;
     constexpr uint32_t ABS2 = (uint32_t)kAbsent * 0x10001u;
-    // byte costs: kAbsent in the halves of labels >= Lc (all of them on lanes past Lcd)
-    uint32_t am[NP];
+    // byte costs: one byte permute per label pair widens two bytes to halfwords and puts kAbsent
+    // (= 0x2000: bytes 0x00, 0x20 of the constant operand, selectors 4 and 5) into the halves of
+    // labels >= Lc (all of them on lanes past Lcd)
+    uint32_t bsel[NP];
 #pragma unroll
-    for (int j = 0; j < NP; j++)
-        am[j] = (k0 + 2 * j < Lc && act ? 0u : (uint32_t)kAbsent) | (k0 + 2 * j + 1 < Lc && act ? 0u : (uint32_t)kAbsent << 16);
+    for (int j = 0; j < NP; j++) {
+        const int b = (2 * j) & 3;                                   // byte of label 2j in its word
+        const uint32_t lo = (k0 + 2 * j < Lc && act) ? (uint32_t)b | (4u << 4) : 0x54u;
+        const uint32_t hi = (k0 + 2 * j + 1 < Lc && act) ? (uint32_t)(b + 1) | (4u << 4) : 0x54u;
+        bsel[j] = lo | (hi << 8);
+    }
     // cost and sum pointers step along the scanline; the cost rows of the next four steps are in
     // flight (a ring of four registers, indexed statically by unrolling the steps by four)
     const long long dstep = ((long long)dy * W + dx) * Lcd;
@@ -285,9 +286,10 @@ __global__ void __launch_bounds__(128) coarse_sgm_kernel(const void *__restrict_
     };
     auto words = [&](const T &v, uint32_t *c) {
         if constexpr (C8) {
-            BVec<LPT>::widen(v, c);
+            uint32_t src[(NP + 1) / 2];
+            BVec<LPT>::words(v, src);
 #pragma unroll
-            for (int j = 0; j < NP; j++) c[j] |= am[j];
+            for (int j = 0; j < NP; j++) c[j] = __byte_perm(src[j / 2], (uint32_t)kAbsent, bsel[j]);
         } else {
             words_of<LPT>(v, c);
         }

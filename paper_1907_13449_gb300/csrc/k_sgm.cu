@@ -163,12 +163,14 @@ __global__ void __launch_bounds__(32 * kSgmWarps) fine_sgm_kernel(const float *_
                         if (j >= n) break;
                         float Lv = cc[u];
                         if (pn != 0) {
-                            // slots of the predecessor, clamped to [-1, pn]: out of range reads a
-                            // sentinel (+inf), so an absent label drops out of the minimum
-                            const int i = l + j - plo;
-                            const float v0 = bufA[min(max(i, -1), pn)];
-                            const float vm = bufA[min(max(i - 1, -1), pn)];
-                            const float vp = bufA[min(max(i + 1, -1), pn)];
+                            // predecessor slot s read at row[s + 1] with s + 1 clamped (unsigned) to
+                            // pn + 1: any slot outside [0, pn) lands on a sentinel (+inf), so an
+                            // absent label drops out of the minimum
+                            const unsigned k1 = (unsigned)(l + j - plo + 1), top = (unsigned)pn + 1u;
+                            const float *row = bufA - 1;
+                            const float v0 = row[min(k1, top)];
+                            const float vm = row[min(k1 - 1u, top)];
+                            const float vp = row[min(k1 + 1u, top)];
                             const float t = fminf(fminf(m + P2, v0), fminf(vm, vp) + P1);
                             Lv = cc[u] + (t - m);
                         }
