@@ -40,7 +40,7 @@ FP32_LANES_PER_SM = 128
 # DRAM bytes (read + write) per launch from one ncu capture of the bench workload, with the
 # SHA-256 prefix of the kernel's source at capture time; a changed source reports null.
 NCU_TRAFFIC = {
-    "fine_cost": {"bytes": 315897344, "workload": "bench", "channels": 1,
+    "fine_cost": {"bytes": 315831808, "workload": "bench", "channels": 1,
                   "source": "paper_1907_13449_gb300/csrc/k_fine_cost.cu",
                   "sha256_16": "bd10d5badb8fb004", "capture": "profiles/fine_cost_rows_bench_9x9x512x512.md"},
 }
