@@ -152,31 +152,38 @@ __global__ void __launch_bounds__(32 * kSgmWarps) fine_sgm_kernel(const float *_
                 }
                 const long long o = 4ll * ofs;
                 float lmin = INF;
-                // sixteen 32-label chunks per round: their cost loads are in flight together
+                // sixteen 32-label chunks per round: their cost loads are in flight together, and
+                // every chunk reads the predecessor row before any chunk stores its own (the
+                // compiler cannot tell bufA from bufB, so a store between them would order the
+                // chunks one after another)
                 for (int j0 = lane; j0 < n; j0 += 512) {
                     float cc[16];
 #pragma unroll
                     for (int u = 0; u < 16; u++) cc[u] = j0 + 32 * u < n ? __ldg(cost + o + j0 + 32 * u) : 0.f;
+                    if (pn != 0) {
+                        // predecessor slot s read at row[s + 1] with s + 1 clamped (unsigned) to
+                        // pn + 1: any slot outside [0, pn) lands on a sentinel (+inf), so an absent
+                        // label drops out of the minimum (labels j >= n read in-bounds slots too)
+                        const unsigned top = (unsigned)pn + 1u;
+                        const float *row = bufA - 1;
 #pragma unroll
-                    for (int u = 0; u < 16; u++) {
-                        const int j = j0 + 32 * u;
-                        if (j >= n) break;
-                        float Lv = cc[u];
-                        if (pn != 0) {
-                            // predecessor slot s read at row[s + 1] with s + 1 clamped (unsigned) to
-                            // pn + 1: any slot outside [0, pn) lands on a sentinel (+inf), so an
-                            // absent label drops out of the minimum
-                            const unsigned k1 = (unsigned)(l + j - plo + 1), top = (unsigned)pn + 1u;
-                            const float *row = bufA - 1;
+                        for (int u = 0; u < 16; u++) {
+                            if (j0 + 32 * u >= n) break;
+                            const unsigned k1 = (unsigned)(l + j0 + 32 * u - plo + 1);
                             const float v0 = row[min(k1, top)];
                             const float vm = row[min(k1 - 1u, top)];
                             const float vp = row[min(k1 + 1u, top)];
                             const float t = fminf(fminf(m + P2, v0), fminf(vm, vp) + P1);
-                            Lv = cc[u] + (t - m);
+                            cc[u] = cc[u] + (t - m);
                         }
-                        bufB[j] = Lv;
-                        lmin = fminf(lmin, Lv);
-                        atomicAdd(agg + o + j, Lv);
+                    }
+#pragma unroll
+                    for (int u = 0; u < 16; u++) {
+                        const int j = j0 + 32 * u;
+                        if (j >= n) break;
+                        bufB[j] = cc[u];
+                        lmin = fminf(lmin, cc[u]);
+                        atomicAdd(agg + o + j, cc[u]);
                     }
                 }
                 m = warp_min(lmin);
