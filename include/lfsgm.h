@@ -25,6 +25,8 @@
  * labels lo[p] .. lo[p]+cnt[p]-1; slot j of pixel p is at cost[off[p] + j].
  * off[p] is a multiple of 4 (16-byte aligned rows), off[p+1] - off[p] >= cnt[p];
  * the padding slots are written with 0 and never read.  off has N+1 entries.
+ * Rows are read and written as 16-byte vectors, so the cost, agg and grad_cost buffers
+ * must start on a 16-byte boundary (LFSGM_ERR_INVALID_ARG otherwise, before any launch).
  */
 #ifndef LFSGM_H
 #define LFSGM_H

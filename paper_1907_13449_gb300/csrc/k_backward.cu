@@ -39,10 +39,52 @@ __global__ void softargmin_backward_kernel(const float *__restrict__ agg, const 
     if (!window_ok(l, n, G, off[p + 1] - o, status)) return;
     const int npad = (int)min((long long)((n + 3) & ~3), off[p + 1] - o);
     const float *s = agg + o;
+    const float it = 1.f / tau;
+    if (n <= 32 && (o & 3) == 0 && npad == ((n + 3) & ~3)) {
+        // the window in registers (8 vector loads issued together) and the two output rows written
+        // as vectors; the same operations in the same order as the general form below
+        float v[32];
+        const float4 *r = reinterpret_cast<const float4 *>(s);
+#pragma unroll
+        for (int q = 0; q < 8; q++) {
+            const float4 w = 4 * q < n ? __ldg(r + q) : make_float4(0.f, 0.f, 0.f, 0.f);
+            v[4 * q] = w.x;
+            v[4 * q + 1] = w.y;
+            v[4 * q + 2] = w.z;
+            v[4 * q + 3] = w.w;
+        }
+        float mn = v[0];
+#pragma unroll
+        for (int j = 1; j < 32; j++)
+            if (j < n) mn = fminf(mn, v[j]);
+        float z = 0.f, num = 0.f;
+#pragma unroll
+        for (int j = 0; j < 32; j++)
+            if (j < n) {
+                const float w = expf((mn - v[j]) * it);
+                z += w;
+                num = fmaf(w, (float)j, num);
+            }
+        const float jbar = num / z;
+        const float k = gdisp[p] * (-it) * (float)step / z;
+        float4 *g4 = reinterpret_cast<float4 *>(gCs + o), *c4 = reinterpret_cast<float4 *>(gcost + o);
+#pragma unroll
+        for (int q = 0; q < 8; q++)
+            if (4 * q < npad) {
+                float g[4];
+#pragma unroll
+                for (int e = 0; e < 4; e++) {
+                    const int j = 4 * q + e;
+                    g[e] = j < n ? k * expf((mn - v[j]) * it) * ((float)j - jbar) : 0.f;
+                }
+                g4[q] = make_float4(g[0], g[1], g[2], g[3]);
+                c4[q] = make_float4(0.f, 0.f, 0.f, 0.f);
+            }
+        return;
+    }
     float mn = s[0];
     for (int j = 1; j < n; j++) mn = fminf(mn, s[j]);
     // FP32 weights after subtracting the minimum; d_g - dhat = (j - jbar) * step
-    const float it = 1.f / tau;
     float z = 0.f, num = 0.f;
     for (int j = 0; j < n; j++) {
         const float w = expf((mn - s[j]) * it);

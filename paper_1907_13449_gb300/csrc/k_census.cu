@@ -103,59 +103,118 @@ __device__ __forceinline__ void census_word2(const float *t, int ld, float c0, f
 // the planes view * C + c), and the padded view is written interleaved, one float4 (the C
 // channels and a zero) per pixel, so that a bilinear tap of all channels is one 16-byte load.
 template <int HALF, int C>
-__global__ void __launch_bounds__(TX *TY / 2) census_pad_kernel(const float *__restrict__ views, int H, int W, int P,
-                                                                int Wp, int Hp, const int *__restrict__ sel,
-                                                                uint64_t *__restrict__ cen_pad,
-                                                                float *__restrict__ views_pad) {
+__device__ __forceinline__ void census_pad_body(const float *__restrict__ views, int H, int W, int P, int Wp, int Hp,
+                                                const int *__restrict__ sel, uint64_t *__restrict__ cen_pad,
+                                                float *__restrict__ views_pad) {
     constexpr int SW = TX + 2 * HALF, SH = TY + 2 * HALF;
     __shared__ float tile[SH][SW + 1];
     const size_t HW = (size_t)H * W, HWp = (size_t)Hp * Wp;
     const int view = sel[blockIdx.z];
     const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
-    const int tid = threadIdx.y * TX + threadIdx.x;
     const int x = x0 + threadIdx.x, ty0 = 2 * threadIdx.y, y = y0 + ty0;
     const bool inb = x < W && y < H;
     const int xa = x == 0 ? 0 : x + P, xb = x == W - 1 ? Wp - 1 : x + P;
-    float cv[2][C];
+    // tile fill: thread (tx, ty) loads column tx of tile rows ty, ty + 4, ..., and the first 2 HALF
+    // lanes also load the halo columns 32 .. SW-1 (clamped coordinates)
+    const int gx0 = min(max(x0 + (int)threadIdx.x - HALF, 0), W - 1);
+    const int gx1 = min(max(x0 + TX + (int)threadIdx.x - HALF, 0), W - 1);
+    const bool halo = threadIdx.x < 2 * HALF;
+    float cv[2][C] = {};
 #pragma unroll
     for (int ch = 0; ch < C; ch++) {
         const float *img = views + ((size_t)view * C + ch) * HW;
         if (ch) __syncthreads();                                   // the previous channel's tile is used up
-        for (int i = tid; i < SH * SW; i += TX * TY / 2) {
-            int ty = i / SW, tx = i - ty * SW;
-            int gy = min(max(y0 + ty - HALF, 0), H - 1);
-            int gx = min(max(x0 + tx - HALF, 0), W - 1);
-            tile[ty][tx] = __ldg(img + (size_t)gy * W + gx) + 0.0f;   // -0 becomes +0 (see census_word)
+#pragma unroll
+        for (int ty = threadIdx.y; ty < SH; ty += TY / 2) {
+            const float *src = img + (size_t)min(max(y0 + ty - HALF, 0), H - 1) * W;
+            tile[ty][threadIdx.x] = __ldg(src + gx0) + 0.0f;       // -0 becomes +0 (see census_word)
+            if (halo) tile[ty][TX + threadIdx.x] = __ldg(src + gx1) + 0.0f;
         }
         __syncthreads();
+        uint64_t w[2] = {0ull, 0ull};
         if (inb) {
             const float c0 = tile[ty0 + HALF][threadIdx.x + HALF], c1 = tile[ty0 + 1 + HALF][threadIdx.x + HALF];
-            uint64_t w[2];
             census_word2<HALF>(&tile[ty0][threadIdx.x], SW + 1, c0, c1, w[0], w[1]);
             cv[0][ch] = c0;
             cv[1][ch] = c1;
+        }
+        // the census words of this channel, and with the last channel the padded view
+        auto put = [&](uint64_t *cp, size_t q, uint64_t word, const float *val) {
+            cp[q] = word;
+            if (ch == C - 1) {
+                if constexpr (C == 1)
+                    views_pad[(size_t)view * HWp + q] = val[0];
+                else
+                    reinterpret_cast<float4 *>(views_pad)[(size_t)view * HWp + q] =
+                        make_float4(val[0], val[1], val[2], 0.f);
+            }
+        };
+        if constexpr (C == 1) {
+            // A warp is one thread row, so y and yr are the same on all its lanes.  A pixel that is
+            // not on the left or right border writes one padded column (one position inside, the
+            // padding rows above or below it on the top and bottom rows), its lanes side by side;
+            // the rectangle of a left or right border pixel is written by the whole warp, lanes
+            // along x (a lane alone would write (P+1)^2 positions at a corner).
+            if (y < H) {
+                uint64_t *cp = cen_pad + (size_t)view * HWp;
+                const bool xedge = inb && (x == 0 || x == W - 1);
+#pragma unroll
+                for (int r = 0; r < 2; r++) {
+                    const int yr = y + r;
+                    if (yr >= H) break;
+                    const int ya = yr == 0 ? 0 : yr + P, yb = yr == H - 1 ? Hp - 1 : yr + P;
+                    if (inb && !xedge)
+                        for (int yy = ya; yy <= yb; yy++) put(cp, (size_t)yy * Wp + xa, w[r], cv[r]);
+                    unsigned m = __ballot_sync(0xffffffffu, xedge);
+                    while (m) {
+                        const int src = __ffs(m) - 1;
+                        m &= m - 1;
+                        const uint64_t ws = __shfl_sync(0xffffffffu, w[r], src);
+                        const int sa = __shfl_sync(0xffffffffu, xa, src), sb = __shfl_sync(0xffffffffu, xb, src);
+                        const float vs = __shfl_sync(0xffffffffu, cv[r][0], src);
+                        for (int yy = ya; yy <= yb; yy++)
+                            for (int xx = sa + (int)threadIdx.x; xx <= sb; xx += 32)
+                                put(cp, (size_t)yy * Wp + xx, ws, &vs);
+                    }
+                }
+            }
+        } else if (inb) {
+            // colour: each lane writes its own pixel's rectangle (measured faster here than the
+            // warp-wide border writes, which raise the register count of the three-channel kernel)
             uint64_t *cp = cen_pad + ((size_t)view * C + ch) * HWp;
-            // the census words of this channel, and with the last channel the padded view
 #pragma unroll
             for (int r = 0; r < 2; r++) {
                 const int yr = y + r;
                 if (yr >= H) break;
+                if (xa == xb && yr != 0 && yr != H - 1) {             // interior: one padded position
+                    put(cp, (size_t)(yr + P) * Wp + xa, w[r], cv[r]);
+                    continue;
+                }
                 const int ya = yr == 0 ? 0 : yr + P, yb = yr == H - 1 ? Hp - 1 : yr + P;
                 for (int yy = ya; yy <= yb; yy++)
-                    for (int xx = xa; xx <= xb; xx++) {
-                        const size_t q = (size_t)yy * Wp + xx;
-                        cp[q] = w[r];
-                        if (ch == C - 1) {
-                            if constexpr (C == 1)
-                                views_pad[(size_t)view * HWp + q] = cv[r][0];
-                            else
-                                reinterpret_cast<float4 *>(views_pad)[(size_t)view * HWp + q] =
-                                    make_float4(cv[r][0], cv[r][1], cv[r][2], 0.f);
-                        }
-                    }
+                    for (int xx = xa; xx <= xb; xx++) put(cp, (size_t)yy * Wp + xx, w[r], cv[r]);
             }
         }
     }
+}
+
+// Grey: 16 CTAs of 128 threads per SM (32 registers).  Colour: the compiler's own register count.
+template <int HALF>
+__global__ void __launch_bounds__(TX *TY / 2, 16) census_pad_kernel(const float *__restrict__ views, int H, int W,
+                                                                    int P, int Wp, int Hp,
+                                                                    const int *__restrict__ sel,
+                                                                    uint64_t *__restrict__ cen_pad,
+                                                                    float *__restrict__ views_pad) {
+    census_pad_body<HALF, 1>(views, H, W, P, Wp, Hp, sel, cen_pad, views_pad);
+}
+
+template <int HALF>
+__global__ void __launch_bounds__(TX *TY / 2) census_pad_rgb_kernel(const float *__restrict__ views, int H, int W,
+                                                                    int P, int Wp, int Hp,
+                                                                    const int *__restrict__ sel,
+                                                                    uint64_t *__restrict__ cen_pad,
+                                                                    float *__restrict__ views_pad) {
+    census_pad_body<HALF, 3>(views, H, W, P, Wp, Hp, sel, cen_pad, views_pad);
 }
 
 }  // namespace
@@ -164,11 +223,11 @@ cudaError_t launch_census_pad(cudaStream_t s, const float *views, int H, int W, 
                               int C, const int *d_sel, int nsel, uint64_t *cen_pad, float *views_pad) {
     dim3 block(TX, TY / 2), grid((W + TX - 1) / TX, (H + TY - 1) / TY, nsel);
     if (C == 3) {
-        if (census_w == 5) census_pad_kernel<2, 3><<<grid, block, 0, s>>>(views, H, W, P, Wp, Hp, d_sel, cen_pad, views_pad);
-        else census_pad_kernel<3, 3><<<grid, block, 0, s>>>(views, H, W, P, Wp, Hp, d_sel, cen_pad, views_pad);
+        if (census_w == 5) census_pad_rgb_kernel<2><<<grid, block, 0, s>>>(views, H, W, P, Wp, Hp, d_sel, cen_pad, views_pad);
+        else census_pad_rgb_kernel<3><<<grid, block, 0, s>>>(views, H, W, P, Wp, Hp, d_sel, cen_pad, views_pad);
     } else {
-        if (census_w == 5) census_pad_kernel<2, 1><<<grid, block, 0, s>>>(views, H, W, P, Wp, Hp, d_sel, cen_pad, views_pad);
-        else census_pad_kernel<3, 1><<<grid, block, 0, s>>>(views, H, W, P, Wp, Hp, d_sel, cen_pad, views_pad);
+        if (census_w == 5) census_pad_kernel<2><<<grid, block, 0, s>>>(views, H, W, P, Wp, Hp, d_sel, cen_pad, views_pad);
+        else census_pad_kernel<3><<<grid, block, 0, s>>>(views, H, W, P, Wp, Hp, d_sel, cen_pad, views_pad);
     }
     return cudaGetLastError();
 }

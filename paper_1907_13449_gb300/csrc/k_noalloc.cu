@@ -96,7 +96,7 @@ __global__ void noalloc_tables_kernel(FineTap *tab, int *sel, int U, int V, int 
 extern "C" lfsgm_status lfsgm_cost_volume_noalloc(const lfsgm_config *cfg, void *stream, const float *views,
                                                   const int32_t *lo, const int32_t *cnt, const int64_t *off,
                                                   float *cost) {
-    if (!cfg || !views || !lo || !cnt || !off || !cost) return LFSGM_ERR_INVALID_ARG;
+    if (!cfg || !views || !lo || !cnt || !off || !cost || ((uintptr_t)cost & 15) != 0) return LFSGM_ERR_INVALID_ARG;
     const lfsgm_config &c = *cfg;
     const int uc = c.uc < 0 ? (c.U - 1) / 2 : c.uc, vc = c.vc < 0 ? (c.V - 1) / 2 : c.vc;
     if (c.U < 1 || c.V < 1 || c.U * c.V < 2 || c.U > 64 || c.V > 64 || c.H < 1 || c.W < 1 ||

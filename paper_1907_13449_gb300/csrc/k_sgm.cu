@@ -223,7 +223,7 @@ __global__ void __launch_bounds__(256) cost_partial_kernel(const float *__restri
     for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < N; p += gridDim.x * blockDim.x) {
         const long long o = off[p];
         const int n = cnt[p];
-        if (!window_ok(0, n, G, off[p + 1] - o, status)) continue;
+        if (!window_ok(0, n, G, off[p + 1] - o, status) || !row_aligned(o, status)) continue;
         const float4 *r = reinterpret_cast<const float4 *>(cost + o);
         float ps = 0.f;
         if (n <= 32) {
@@ -237,9 +237,18 @@ __global__ void __launch_bounds__(256) cost_partial_kernel(const float *__restri
                       (j + 3 < n ? v[q].w : 0.f);
             }
         } else {
-            for (int j = 0; j < n; j += 4) {
-                const float4 v = __ldg(r + (j >> 2));
-                ps += v.x + (j + 1 < n ? v.y : 0.f) + (j + 2 < n ? v.z : 0.f) + (j + 3 < n ? v.w : 0.f);
+            // 32-slot chunks as 8 vector loads issued together, added in the same order
+            for (int j0 = 0; j0 < n; j0 += 32) {
+                float4 v[8];
+#pragma unroll
+                for (int q = 0; q < 8; q++) v[q] = j0 + 4 * q < n ? __ldg(r + (j0 >> 2) + q) : make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+                for (int q = 0; q < 8; q++) {
+                    const int j = j0 + 4 * q;
+                    if (j < n)
+                        ps += v[q].x + (j + 1 < n ? v[q].y : 0.f) + (j + 2 < n ? v[q].z : 0.f) +
+                              (j + 3 < n ? v[q].w : 0.f);
+                }
             }
         }
         s += (double)ps;

@@ -19,7 +19,7 @@ __global__ void wta_kernel(const float *__restrict__ agg, const int *__restrict_
     if (p >= N) return;
     const float *s = agg + off[p];
     const int n = cnt[p], l = lo[p];
-    if (!window_ok(l, n, G, off[p + 1] - off[p], status)) {
+    if (!window_ok(l, n, G, off[p + 1] - off[p], status) || !row_aligned(off[p], status)) {
         if (label) label[p] = -1;
         if (disp) disp[p] = __int_as_float(0x7fc00000);
         return;
@@ -54,15 +54,41 @@ __global__ void wta_kernel(const float *__restrict__ agg, const int *__restrict_
                 }
         }
     } else {
-        for (int j = 1; j < n; j++) {
-            const float v = s[j];
-            if (v < bv) { bv = v; b = j; }
+        // 32-slot chunks of the row as 8 vector loads issued together, used in slot order (slot 0
+        // compares equal to bv and changes nothing)
+        const float4 *r = reinterpret_cast<const float4 *>(s);
+        for (int j0 = 0; j0 < n; j0 += 32) {
+            float4 w[8];
+#pragma unroll
+            for (int q = 0; q < 8; q++) w[q] = j0 + 4 * q < n ? __ldg(r + (j0 >> 2) + q) : make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+            for (int q = 0; q < 8; q++) {
+                const float c4[4] = {w[q].x, w[q].y, w[q].z, w[q].w};
+#pragma unroll
+                for (int e = 0; e < 4; e++) {
+                    const int j = j0 + 4 * q + e;
+                    if (j < n && c4[e] < bv) { bv = c4[e]; b = j; }
+                }
+            }
         }
         if (mode == 2 && disp) {
-            for (int j = 0; j < n; j++) {
-                const float w = expf((bv - s[j]) * it);
-                num = fmaf(w, (float)j, num);
-                den += w;
+            for (int j0 = 0; j0 < n; j0 += 32) {
+                float4 w[8];
+#pragma unroll
+                for (int q = 0; q < 8; q++) w[q] = j0 + 4 * q < n ? __ldg(r + (j0 >> 2) + q) : make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+                for (int q = 0; q < 8; q++) {
+                    const float c4[4] = {w[q].x, w[q].y, w[q].z, w[q].w};
+#pragma unroll
+                    for (int e = 0; e < 4; e++) {
+                        const int j = j0 + 4 * q + e;
+                        if (j < n) {
+                            const float wt = expf((bv - c4[e]) * it);
+                            num = fmaf(wt, (float)j, num);
+                            den += wt;
+                        }
+                    }
+                }
             }
         }
     }

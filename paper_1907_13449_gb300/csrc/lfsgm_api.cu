@@ -29,6 +29,10 @@ struct ProfRec {
 
 size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
+// Windowed rows (cost, agg, grad_cost) are read and written as 16-byte vectors: their base must be
+// 16-byte aligned, or the off[p] multiple-of-4 rows would not be.
+bool aligned16(const void *p) { return ((uintptr_t)p & 15) == 0; }
+
 // ---- shift split of a*d (see lfsgm.h): snap 2s to an integer within 2e-9, then floor / round-half-up
 void shift_split(int a, double d, int &o, double &f, int &n) {
     double s = (double)a * d;
@@ -544,6 +548,7 @@ lfsgm_status cost_volume_impl(lfsgm_handle h, const float *views, const int32_t 
                               const int64_t *off, float *cost, bool cross_done) {
     if (!h) return LFSGM_ERR_INVALID_ARG;
     if (!views || !lo || !cnt || !off || !cost) return fail(h, LFSGM_ERR_INVALID_ARG, "null buffer");
+    if (!aligned16(cost)) return fail(h, LFSGM_ERR_INVALID_ARG, "cost must be 16-byte aligned");
     LFSGM_TRY(ensure_workspace(h));
     const lfsgm_config &c = h->cfg;
     cudaStream_t s = h->stream;
@@ -610,6 +615,7 @@ lfsgm_status lfsgm_sgm_aggregate(lfsgm_handle h, const float *cost, const int32_
                                  const int64_t *off, float P1, float P2, float *agg) {
     if (!h) return LFSGM_ERR_INVALID_ARG;
     if (!cost || !lo || !cnt || !off || !agg) return fail(h, LFSGM_ERR_INVALID_ARG, "null buffer");
+    if (!aligned16(cost) || !aligned16(agg)) return fail(h, LFSGM_ERR_INVALID_ARG, "cost and agg must be 16-byte aligned");
     const bool derived = P1 < 0.f;
     if (!derived && !(P1 >= 0.f && P2 >= P1 && std::isfinite(P2)))
         return fail(h, LFSGM_ERR_INVALID_ARG, "need 0 <= P1 <= P2 (Eq. 8), got %g %g", P1, P2);
@@ -643,6 +649,7 @@ lfsgm_status lfsgm_wta_subpixel(lfsgm_handle h, const float *agg, const int32_t 
                                 const int64_t *off, int32_t *label, float *disp) {
     if (!h) return LFSGM_ERR_INVALID_ARG;
     if (!agg || !lo || !cnt || !off || (!label && !disp)) return fail(h, LFSGM_ERR_INVALID_ARG, "null buffer");
+    if (!aligned16(agg)) return fail(h, LFSGM_ERR_INVALID_ARG, "agg must be 16-byte aligned");
     LFSGM_TRY(ensure_workspace(h));
     const lfsgm_config &c = h->cfg;
     const double step = (c.dmax - c.dmin) / (double)(c.fine_labels - 1);
@@ -665,6 +672,8 @@ lfsgm_status lfsgm_backward(lfsgm_handle h, const float *views, const float *cos
     if (!h) return LFSGM_ERR_INVALID_ARG;
     if (!cost || !lo || !cnt || !off || !grad_disp || !grad_cost || !grad_P1 || !grad_P2 || (grad_views && !views))
         return fail(h, LFSGM_ERR_INVALID_ARG, "null buffer");
+    if (!aligned16(cost) || !aligned16(grad_cost))
+        return fail(h, LFSGM_ERR_INVALID_ARG, "cost and grad_cost must be 16-byte aligned");
     if (!(P1 >= 0.f && P2 >= P1 && std::isfinite(P2)))
         return fail(h, LFSGM_ERR_INVALID_ARG, "backward needs explicit penalties 0 <= P1 <= P2, got %g %g", P1, P2);
     LFSGM_TRY(ensure_workspace(h));

@@ -27,6 +27,13 @@ __device__ __forceinline__ bool window_ok(int l, int n, int G, long long row, in
     return ok;
 }
 
+// A windowed row read as 16-byte vectors must start on a multiple of 4 slots (the layout's rule).
+__device__ __forceinline__ bool row_aligned(long long o, int *status) {
+    const bool ok = (o & 3) == 0;
+    if (!ok && status) atomicExch(status, 7);
+    return ok;
+}
+
 // One 16-byte read-only load of a table entry.
 __device__ __forceinline__ FineTap load_tap(const FineTap *t) {
     const int4 w = __ldg(reinterpret_cast<const int4 *>(t));

@@ -433,6 +433,13 @@ def test_argument_errors_are_reported(gpu_lib, tiny_case):
         gpu_lib.lfsgm_initial_disparity(h, x, 5, 1, i, i, o)
     with pytest.raises(TypeError):
         gpu_lib.lfsgm_cost_volume(h, x, x, i, o, x)
+    # windowed rows are read and written as 16-byte vectors: a shifted base is refused on the host
+    with pytest.raises(gpu_lib.LfsgmError, match="16-byte aligned"):
+        gpu_lib.lfsgm_wta_subpixel(h, x[1:], i, i, o, i, x)
+    with pytest.raises(gpu_lib.LfsgmError, match="16-byte aligned"):
+        gpu_lib.lfsgm_sgm_aggregate(h, x, i, i, o, -1.0, -1.0, x[2:])
+    with pytest.raises(gpu_lib.LfsgmError, match="16-byte aligned"):
+        gpu_lib.lfsgm_cost_volume(h, x, i, i, o, x[3:])
     gpu_lib.lfsgm_sync(h)
     gpu_lib.lfsgm_destroy(h)
 
