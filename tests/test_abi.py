@@ -112,6 +112,27 @@ def test_null_arguments_rejected(lib):
     assert lib.lfsgm_launch_count(None) == -1
 
 
+def _cuda_present():
+    try:
+        import torch
+        return torch.cuda.is_available()
+    except Exception:
+        return False
+
+
+@pytest.mark.skipif(_cuda_present(), reason="placeholder pointers are only passed where no GPU can be reached")
+def test_noalloc_rejects_a_misaligned_cost_before_any_cuda_call(lib):
+    """Windowed rows are written as 16-byte vectors, so the allocation-free entry point refuses a
+    cost buffer off a 16-byte boundary before it touches CUDA (INVALID_ARG = 1; with the check
+    missing it would reach the CUDA runtime and fail differently)."""
+    import lfsynth
+    import paper_1907_13449_gb300 as lf
+    cfg = lf.make_config(lfsynth.tiny_params())
+    ptr = [C.c_void_p(v) for v in (256, 512, 768, 1024)]
+    assert lib.lfsgm_cost_volume_noalloc(C.byref(cfg), None, *ptr, C.c_void_p(4096 + 4)) == 1
+    assert lib.lfsgm_cost_volume_noalloc(C.byref(cfg), None, *ptr, C.c_void_p(4096 + 8)) == 1
+
+
 def test_batch_arguments_rejected_before_any_cuda_call(lib):
     import lfsynth
     import paper_1907_13449_gb300 as lf
