@@ -186,7 +186,6 @@ lfsgm_status validate(const lfsgm_config &c, char *why, size_t n) {
     if (c.paths != 0 && c.paths != 8 && c.paths != 16) BAD("paths must be 8 or 16");
     if (c.channels != 0 && c.channels != 1 && c.channels != 3) BAD("channels must be 1 or 3");
     if (c.boundless != 0 && c.boundless != 1) BAD("boundless must be 0 or 1");
-    if (c.fine_radius_far > 0 && c.fine_radius < 0) BAD("fine_radius must be >= 0");
     if (!(c.edge_threshold >= 0.f) || !std::isfinite(c.edge_threshold)) BAD("edge_threshold must be finite and >= 0");
     const double md = std::fmax(std::fabs(c.dmin), std::fabs(c.dmax));
     if (md * (std::max(c.U, c.V)) > 30000.0) BAD("shifts exceed the 16-bit table range");
