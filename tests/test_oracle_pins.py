@@ -286,6 +286,43 @@ def _cfg1(G=41, dmin=-2.0, dmax=2.0):
     return oracle.make_cfg(p)
 
 
+def _wta_int_row(row):
+    Cs = np.ascontiguousarray(np.asarray(row, np.int64).reshape(1, -1))
+    return int(oracle.wta_int(Cs)[0])
+
+
+def test_coarse_wta_hand_cases_lowest_label_on_ties():
+    """Eq. 10 on the integer coarse sums: D(p) = argmin_k C_s(p,k).  The paper does not say which
+    label wins a tie; the reading is the lowest one.  Hand cases put the tie at the first label,
+    in the middle, at the last two labels, and across the whole row."""
+    cases = [
+        ([5, 5, 7, 9], 0),                       # tie at the first label
+        ([9, 3, 8, 3, 4], 1),                    # tie in the middle, later copy ignored
+        ([8, 6, 9, 2, 2], 3),                    # tie on the last two labels
+        ([4, 4, 4, 4, 4, 4], 0),                 # every label ties
+        ([7], 0),                                # one label
+        ([9, 8, 7, 6, 5, 1], 5),                 # strict minimum on the last label
+        ([1, 2, 3, 4], 0),                       # strict minimum on the first label
+        ([3, 1, 2, 1, 1, 0, 0], 5),              # the lowest value wins before any tie rule
+        ([2 ** 40 + 1, 2 ** 40, 2 ** 40 + 2], 1),  # int64 sums, beyond 32 bits
+    ]
+    for row, want in cases:
+        assert _wta_int_row(row) == want, (row, want)
+
+
+def test_coarse_wta_matches_first_minimum_brute_force():
+    """Random integer rows with many ties (values from a small range) against numpy.argmin, whose
+    documented rule returns the first occurrence of the minimum, and against a scan for the
+    smallest index whose value equals the row minimum."""
+    rng = np.random.default_rng(131)
+    for L, hi in [(2, 2), (3, 3), (16, 4), (100, 6), (256, 3), (97, 1000)]:
+        Cs = rng.integers(0, hi, size=(400, L)).astype(np.int64)
+        got = oracle.wta_int(Cs)
+        assert np.array_equal(got, np.argmin(Cs, axis=1))
+        first = np.array([int(np.flatnonzero(r == r.min())[0]) for r in Cs])
+        assert np.array_equal(got, first)
+
+
 def test_subpixel_recovers_parabola_vertex():
     cfg = _cfg1()
     step = 4.0 / 40
