@@ -33,8 +33,9 @@ sys.path.insert(0, ROOT)
 
 METRIC = "ms per 9x9x512^2 light field (cost+SGM)"
 PEAKS_FALLBACK = {"hbm_gbs": 6800.0, "sm_max_mhz": 2070.0}
-N_SM = 152
-FP32_LANES_PER_SM = 128
+FP32_LANES_PER_SM = 128      # 4 sub-partitions x 32 lanes issue one 32-bit lane op each per clock
+L2_NOTE = "GPU arm: L2 flushed (256 MB write) before every step; CPU arm: not applicable"
+PENALTY_NOTE = "P1 = 0.05 mean cost, P2 = 0.5 mean cost (coarse: per arm, integer)"
 
 
 # DRAM bytes (read + write) per launch from one ncu capture of the bench workload, with the
@@ -42,7 +43,7 @@ FP32_LANES_PER_SM = 128
 NCU_TRAFFIC = {
     "fine_cost": {"bytes": 315831808, "workload": "bench", "channels": 1,
                   "source": "paper_1907_13449_gb300/csrc/k_fine_cost.cu",
-                  "sha256_16": "bd10d5badb8fb004", "capture": "profiles/fine_cost_rows_bench_9x9x512x512.md"},
+                  "sha256_16": "bd10d5badb8fb004"},
 }
 
 
@@ -159,12 +160,14 @@ def hbm_bytes_cost_sgm(p, nnz_active):
 
 def alu_ops_per_cell_view(p):
     """Algorithmic 32-bit lane operations per (active cell, non-reference view) of the cost volume:
-    per channel a bilinear sample (3 lerps, 2 ops each), the difference and its absolute-value
-    accumulation, or for colour its squared accumulation (2 ops); colour adds one square root.
-    The census term is left out: Hamming distances are piecewise constant in the label, so only
-    the distinct nearest offsets of a window need a popcount (a few per pixel and view, under a
-    tenth of the l2 work), which keeps this count a lower bound."""
-    return 8 * p.channels + (1 if p.channels > 1 else 0)
+    per channel a bilinear sample at 4 ops (one horizontal and one vertical lerp of 2 ops each, the
+    other row's horizontal lerp being shared with the adjacent row), the difference, and its
+    absolute-value accumulation -- 6 ops, the upper end of the 4-6 instructions per sample of the
+    algorithmic count -- or for colour the squared accumulation of each channel's difference plus
+    one square root and one add per view.  The census term is left out: Hamming distances are
+    piecewise constant in the label, so only the distinct nearest offsets of a window need a
+    popcount (a few per pixel and view, under a tenth of the l2 work)."""
+    return 6 * p.channels + (2 if p.channels > 1 else 0)
 
 
 def alu_ops_cost(p, nnz_active):
@@ -357,12 +360,15 @@ def run_ours(args, ws, rank, local):
         hot.append("fine_cost_wide")      # colour: every window goes through the list kernel
     dom = max((k for k in kernels if k in hot), key=lambda k: kernels[k]["ms_total"])
     mhz = (clocks or {}).get("sm_mhz") or peaks.get("sm_max_mhz", 2070.0)
+    n_sm = torch.cuda.get_device_properties(dev).multi_processor_count
     by = hbm_bytes_cost_sgm(p, active)
+    hbm_total = by["cost_volume"] + by["sgm_aggregate"]
+    hbm_model_frac = round(hbm_total / (peaks["hbm_gbs"] * 1e9) * 1e3 / value, 4)
     if dom in ("fine_cost", "fine_cost_wide"):
         # the row kernel computes row_cells of the active cells, the list kernel the rest
         # (colour: every cell goes through the list kernel)
         ops = alu_ops_cost(p, row_cells if dom == "fine_cost" else active - row_cells)
-        peak_ops = N_SM * FP32_LANES_PER_SM * mhz * 1e6
+        peak_ops = n_sm * FP32_LANES_PER_SM * mhz * 1e6
         ach = ops / (kernels[dom]["ms_avg"] * 1e-3)
         roof = {"kernel": dom, "bound": "alu", "achieved": round(ach / 1e12, 3),
                 "peak": round(peak_ops / 1e12, 3), "unit": "T 32-bit lane-ops/s",
@@ -370,22 +376,23 @@ def run_ours(args, ws, rank, local):
                 "lane_ops_per_cell_view": alu_ops_per_cell_view(p),
                 "frac": round(ach / peak_ops, 4), "traffic": ncu_traffic(dom, args.workload, p.channels),
                 "algorithmic_bytes": by["cost_volume"],
-                "peak_basis": f"{N_SM} SMs x {FP32_LANES_PER_SM} FP32 lanes x {mhz:.0f} MHz (median SM clock under load)"}
+                "sms": n_sm, "sm_mhz": mhz,
+                "peak_basis": f"{n_sm} SMs (cudaDevAttrMultiProcessorCount) x {FP32_LANES_PER_SM} FP32 lanes x "
+                              f"{mhz:.0f} MHz (median SM clock sampled during the timed region)",
+                "hbm_frac_of_cost_sgm": hbm_model_frac}
     else:
         b = by["sgm_aggregate"] if dom == "fine_sgm" else by["cost_volume"]
         ach = b / (kernels[dom]["ms_avg"] * 1e-3) / 1e9
         roof = {"kernel": dom, "bound": "hbm", "achieved": round(ach, 1), "peak": peaks["hbm_gbs"],
                 "unit": "GB/s", "frac": round(ach / peaks["hbm_gbs"], 4), "traffic": ncu_traffic(dom, args.workload, p.channels)}
-    hbm_total = by["cost_volume"] + by["sgm_aggregate"]
     hbm_model = {"bytes_per_lf": hbm_total, "roofline_ms": round(hbm_total / (peaks["hbm_gbs"] * 1e9) * 1e3, 4),
-                 "frac": round(hbm_total / (peaks["hbm_gbs"] * 1e9) * 1e3 / value, 4),
+                 "frac": hbm_model_frac,
                  "peak_gbs": peaks["hbm_gbs"], "peak_source": peaks["_source"]}
     out = {
         "metric": METRIC, "value": round(value, 4), "unit": "ms", "n_gpus": ws, "steps": K,
         "warmup": args.warmup, "ms_per_step": round(step_ms / K, 4), "higher_is_better": False,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": workload_label(p), "l2": "flushed (256 MB write) before every step",
-                   "penalties": "P1 = 0.05 mean cost, P2 = 0.5 mean cost (coarse: per arm, integer)",
+        "config": {"workload": workload_label(p), "l2": L2_NOTE, "penalties": PENALTY_NOTE,
                    "parallelism": f"replicas x{ws}"},
         "gcell_per_s": round(active / (value * 1e-3) / 1e9, 2),
         "value_stats": {"median": round(statistics.median(stage_each), 4), "min": round(stage_each[0], 4),
@@ -403,9 +410,10 @@ def run_ours(args, ws, rank, local):
         "hbm_model": hbm_model,
         "clocks": clocks,
         "gpu_launches": int(launches),
-        "e2e": {"value": round(e2e_ms, 4), "unit": "ms per light field: host->device views, whole method, "
-                "device->host disparity + label", "h2d_bytes_per_step": int(views_np.nbytes),
-                "d2h_bytes_per_step": int(dh.numel() * 4 + lh.numel() * 4)},
+        "e2e": {"value": round(e2e_ms, 4), "unit": "ms", "h2d_bytes_per_step": int(views_np.nbytes),
+                "d2h_bytes_per_step": int(dh.numel() * 4 + lh.numel() * 4),
+                "scope": "per light field through lfsgm_depth_host: host->device views, the whole method "
+                         "(initial pass, cost volume, SGM, WTA + sub-pixel), device->host disparity + label"},
     }
     if args.backward:
         out["backward"] = run_backward(args, dev, views, p)
@@ -648,7 +656,8 @@ def run_reference(args, ws, rank):
     return {"impl": "reference", "metric": METRIC, "value": round(v, 1), "unit": "ms", "n_gpus": ws,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(statistics.mean(samples) * 1e3, 1),
             "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "config": {"workload": workload_label(p), "parallelism": "host cores"},
+            "data": "synthetic", "config": {"workload": workload_label(p), "l2": L2_NOTE, "penalties": PENALTY_NOTE,
+                                            "parallelism": "host cores"},
             "cpu_baseline": cb, "e2e": {"value": round(v, 1), "unit": "ms", "h2d_bytes_per_step": 0,
                                         "d2h_bytes_per_step": 0}}
 

@@ -23,8 +23,10 @@
  *
  * Windowed cost layout ("CSR", part of this ABI): pixel p = y*W + x has the fine
  * labels lo[p] .. lo[p]+cnt[p]-1; slot j of pixel p is at cost[off[p] + j].
- * off[p] is a multiple of 4 (16-byte aligned rows), off[p+1] - off[p] >= cnt[p];
- * the padding slots are written with 0 and never read.  off has N+1 entries.
+ * off[p] is a multiple of 4 for every p in [0, N], off[N] included (16-byte aligned rows
+ * whose lengths are whole 4-slot groups), and off[p+1] - off[p] >= cnt[p]; the padding
+ * slots are written with 0 and never read.  off has N+1 entries.  A kernel that meets a
+ * row breaking these rules skips that pixel and latches LFSGM_ERR_DEVICE_CHECK.
  * Rows are read and written as 16-byte vectors, so the cost, agg and grad_cost buffers
  * must start on a 16-byte boundary (LFSGM_ERR_INVALID_ARG otherwise, before any launch).
  */

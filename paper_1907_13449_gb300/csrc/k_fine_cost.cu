@@ -83,37 +83,48 @@ __global__ void __launch_bounds__(256) fine_cost_generic(const float *__restrict
 //
 // Staging.  The views and census words are read from edge-replicated padded copies (a read at
 // a padded position equals the clamped read), so every tile a warp needs lies inside the padded
-// image.  Per view, one lane issues two TMA tile loads (a box of view values and a box of census
-// words around the row segment, x rounded down to the 16-byte boundary) and a bulk copy of the
-// KW table entries, all completing on one mbarrier; two stages are in flight, so view v+1 streams
-// in while view v is computed.  Waits are bounded: on expiry LFSGM_ERR_TIMEOUT is latched.
+// image.  Per view, one lane issues a TMA tile load of the view values around the row segment
+// (x rounded down to the 16-byte boundary) and a bulk copy of the range's descriptor on one
+// mbarrier, two stages deep, so view v+1 streams in while view v is computed; the census words
+// around the segment come as a third tile on a second mbarrier, into one buffer that is refilled
+// for view v+1 as soon as view v's census breakpoints have been read.  Waits are bounded: on
+// expiry LFSGM_ERR_TIMEOUT is latched.
 //
 // Compute.  The range splits into segments at the labels where the bilinear cell (integer shift)
 // changes.  Inside a segment the fractional shift grows linearly with the label (a*d is linear in
-// d), so the bilinear sample is a quadratic polynomial in the label index i,
+// d), so the bilinear sample minus I_ref(p) is a quadratic polynomial in the label index i,
 // s(i) = A + i (B + i C).  A short loop over the segments writes each lane's (A, B, C) to shared
-// memory; the label loop is branch-free: per label one broadcast load of the segment offset, one
-// 16-byte load of the lane's coefficients, two FMAs for the sample, two for |I_ref - s| and the
-// sum.  The census term is a step function of the label: its Hamming distances are added as
-// integer differences at the census breakpoints and prefix-summed once at the end.
+// memory; everything about a segment that is the same for all lanes (its fractions, their
+// products with the view's shift factors, its first label) comes precomputed with the
+// descriptor.  The label loop runs in blocks of four labels: a block in which no segment starts
+// (the common case: segments span 8-36 labels) evaluates its labels with the coefficients in
+// registers, two FMAs and one |.|-add per label; a block with a segment start reloads the lane's
+// coefficients from shared memory at that label.  The l2 weight multiplies the sums once at the
+// end.  The census term is a step function of the label: its Hamming distances are added as
+// integer differences at the census breakpoints (a shared-memory atomic into per-lane words that
+// hold two labels' 16-bit differences) and prefix-summed once at the end.
 struct RowPlan {
     int P, Wp, Hp;                    // padding and padded sizes
     int bwf, bhf, bwc, bhc;           // TMA boxes (elements): view values, census words
     int seg_cap;                      // most segments (and census breakpoints) in one label range
-    int ds_stride;                    // bytes of one (view, g0) descriptor
-    int o_rf, o_rc, o_ds, stage;      // byte offsets of stage 0's buffers in a warp's slice; stage 1 at +stage
-    int o_coef, o_cdiff, o_mbar, warp_bytes;
+    int ds_stride;                    // bytes of one (view, g0) descriptor slot
+    int o_rf, o_ds, stage;            // view tile and descriptor of stage 0 in a warp's slice; stage 1 at +stage
+    int o_rc;                         // census tile (one buffer: refilled once its breakpoints are read)
+    int o_cab, o_cc, o_cdiff, o_mbar, warp_bytes;
 };
 
 // Descriptor of the label range [g0, g0+KW) of one view (built on the host, see
 // build_fine_rows_desc): everything about the range that does not depend on the row segment.
-//   bytes  0..15  int16 xf, yf, xc, yc: tile origins relative to (x0, y); uint8 nseg, ncen
+//   bytes  0..7   int16 xf, yf, xc, yc: tile origins relative to (x0, y)
+//   bytes  8..11  uint8 nseg, ncen; uint16 nbytes (bytes of this descriptor, a multiple of 16)
+//   bytes 12..15  float ax * ay
 //   bytes 16..23  uint64 smask: bit i set where label i starts a segment (bit 0 always)
 //   bytes 24..31  float ax, ay: the view's (u-uc) * step and (v-vc) * step
-//   bytes 32..    int4 seg[seg_cap]: tile offset of the segment's (0,0) tap for lane 0, first
-//                 label, fx, fy (float bits)
-//   then          uint32 cen[seg_cap]: census breakpoint label | tile offset of its word << 8
-constexpr int kDsMask = 16, kDsAxy = 24, kDsSegs = 32;
+//   bytes 32..    per segment 32 bytes: int tile offset of the (0,0) tap for lane 0, float first
+//                 label fi, fx, fy; float fx*fy, fx*ay + fy*ax, -2 fi, 0
+//   then          per census breakpoint 16 bytes: int tile offset of its word for lane 0, byte
+//                 offset of its 32-bit difference word (label / 2) * 128, shift 16 * (label & 1), 0
+constexpr int kDsMask = 16, kDsAxy = 24, kDsSegs = 32, kDsSegBytes = 32, kDsCenBytes = 16;
 
 __device__ __forceinline__ unsigned smem_u32(const void *p) { return (unsigned)__cvta_generic_to_shared(p); }
 
@@ -136,7 +147,7 @@ __device__ __forceinline__ void push_chunks(int2 *list, int *count, int p, int n
 }
 
 template <int KW>
-__global__ void __launch_bounds__(128, 4) fine_cost_rows(const __grid_constant__ CUtensorMap tm_v,
+__global__ void __launch_bounds__(128, 5) fine_cost_rows(const __grid_constant__ CUtensorMap tm_v,
                                                          const __grid_constant__ CUtensorMap tm_c,
                                                          const unsigned char *__restrict__ desc, int G, int U, int V,
                                                          int H, int W, int ref, const int *__restrict__ lo,
@@ -144,16 +155,17 @@ __global__ void __launch_bounds__(128, 4) fine_cost_rows(const __grid_constant__
                                                          const long long *__restrict__ off,
                                                          const float *__restrict__ views_pad,
                                                          const uint64_t *__restrict__ cen_pad, float wl2, float wc,
-                                                         float fstep, float *__restrict__ cost,
+                                                         float *__restrict__ cost,
                                                          int *__restrict__ status, int2 *__restrict__ list,
                                                          int *__restrict__ list_count, RowPlan pl) {
-    static_assert(KW > 32 && KW <= 64, "two 32-bit masks cover the label range");
+    static_assert(KW > 32 && KW <= 64 && KW % 4 == 0, "two 32-bit masks cover the label range, blocks of 4");
     extern __shared__ __align__(128) unsigned char smem[];
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5, wpb = blockDim.x >> 5;
     unsigned char *wb = smem + (size_t)wib * pl.warp_bytes;
-    unsigned char *coef = wb + pl.o_coef;                   // float4 (A, B, C, -) [seg_cap][32]
-    short *cdiff = (short *)(wb + pl.o_cdiff);              // [KW][32] census steps (|sum| <= views x 48)
-    const unsigned mbar0 = smem_u32(wb + pl.o_mbar);
+    float2 *cab = (float2 *)(wb + pl.o_cab) + lane;         // (A, B) [seg_cap][32]
+    float *ccq = (float *)(wb + pl.o_cc) + lane;            // C [seg_cap][32]
+    int *cdw = (int *)(wb + pl.o_cdiff) + lane;             // [KW / 2][32] two labels' census steps
+    const unsigned mbar0 = smem_u32(wb + pl.o_mbar);        // stages 0, 1 at +0, +8; census tile at +16
     const int nviews = U * V;
     const size_t HWp = (size_t)pl.Hp * pl.Wp;
     const int tiles_x = (W + 31) >> 5;
@@ -200,122 +212,155 @@ __global__ void __launch_bounds__(128, 4) fine_cost_rows(const __grid_constant__
     if (lane == 0) {
         asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(mbar0));
         asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(mbar0 + 8));
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(mbar0 + 16));
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     __syncwarp();
-    const unsigned tx_bytes = (unsigned)(pl.bwf * pl.bhf * 4 + pl.bwc * pl.bhc * 8 + pl.ds_stride);
+    const unsigned tile_bytes = (unsigned)(pl.bwf * pl.bhf * 4), cen_bytes = (unsigned)(pl.bwc * pl.bhc * 8);
     auto dsc_of = [&](int view) { return desc + ((size_t)view * G + g0) * pl.ds_stride; };
-    // tile origins (relative int16 quads) of the next views, read one view ahead of their issue
-    auto origins = [&](int view) { return __ldg(reinterpret_cast<const int2 *>(dsc_of(view))); };
-    auto issue = [&](int view, int2 org, int st) {
+    // the first 16 bytes of the next views' descriptors (tile origins, counts, size), read one
+    // view ahead of their issue
+    auto head = [&](int view) { return __ldg(reinterpret_cast<const int4 *>(dsc_of(view))); };
+    auto issue = [&](int view, int4 hd, int st) {
         if (lane != 0) return;
-        const int xf = x0 + (int)(short)(org.x & 0xffff), yf = y + (org.x >> 16);
-        const int xc = x0 + (int)(short)(org.y & 0xffff), yc = y + (org.y >> 16);
+        const int xf = x0 + (int)(short)(hd.x & 0xffff), yf = y + (hd.x >> 16);
+        const unsigned nb = min((unsigned)hd.z >> 16, (unsigned)pl.ds_stride) & ~15u;
         const unsigned mb = mbar0 + 8 * st;
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(mb), "r"(tx_bytes) : "memory");
+        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(mb), "r"(tile_bytes + nb) : "memory");
         asm volatile("cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];"
                      ::"r"(smem_u32(wb + pl.o_rf + st * pl.stage)), "l"((unsigned long long)&tm_v), "r"(xf), "r"(yf), "r"(view), "r"(mb)
                      : "memory");
+        if (nb > 0)
+            asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+                         ::"r"(smem_u32(wb + pl.o_ds + st * pl.stage)), "l"(dsc_of(view)), "r"(nb), "r"(mb)
+                         : "memory");
+    };
+    auto issue_cen = [&](int view, int4 hd) {
+        if (lane != 0) return;
+        const int xc = x0 + (int)(short)(hd.y & 0xffff), yc = y + (hd.y >> 16);
+        const unsigned mb = mbar0 + 16;
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(mb), "r"(cen_bytes) : "memory");
         asm volatile("cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];"
-                     ::"r"(smem_u32(wb + pl.o_rc + st * pl.stage)), "l"((unsigned long long)&tm_c), "r"(xc), "r"(yc), "r"(view), "r"(mb)
-                     : "memory");
-        asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
-                     ::"r"(smem_u32(wb + pl.o_ds + st * pl.stage)), "l"(dsc_of(view)), "r"(pl.ds_stride), "r"(mb)
+                     ::"r"(smem_u32(wb + pl.o_rc)), "l"((unsigned long long)&tm_c), "r"(xc), "r"(yc), "r"(view), "r"(mb)
                      : "memory");
     };
     float acc[KW];
 #pragma unroll
-    for (int i = 0; i < KW; i++) {
-        acc[i] = 0.f;
-        cdiff[i * 32 + lane] = 0;
-    }
+    for (int i = 0; i < KW; i++) acc[i] = 0.f;
+#pragma unroll
+    for (int i = 0; i < KW / 2; i++) cdw[32 * i] = 0;
     const int nv = nviews - 1;                      // every view but the reference
     auto view_of = [&](int vi) { return vi + (vi >= ref); };
-    issue(view_of(0), origins(view_of(0)), 0);
-    int2 org_next = nv > 1 ? origins(view_of(1)) : make_int2(0, 0);
+    {
+        const int4 h0 = head(view_of(0));
+        issue(view_of(0), h0, 0);
+        issue_cen(view_of(0), h0);
+    }
+    int4 hd_next = nv > 1 ? head(view_of(1)) : make_int4(0, 0, 0, 0);
     bool ok = true;
     for (int vi = 0; vi < nv; vi++) {
-        const int view = view_of(vi);
         const int st = vi & 1;
-        if (vi + 1 < nv) {
-            issue(view_of(vi + 1), org_next, st ^ 1);
-            if (vi + 2 < nv) org_next = origins(view_of(vi + 2));
-        }
-        if (!mbar_wait(mbar0 + 8 * st, (unsigned)(vi >> 1) & 1u)) {
+        if (vi + 1 < nv) issue(view_of(vi + 1), hd_next, st ^ 1);
+        if (!mbar_wait(mbar0 + 8 * st, (unsigned)(vi >> 1) & 1u) || !mbar_wait(mbar0 + 16, (unsigned)vi & 1u)) {
             if (lane == 0) atomicExch(status, 6);
             // let the copies still in flight land (bounded) before the warp's shared memory is released
+            mbar_wait(mbar0 + 8 * st, (unsigned)(vi >> 1) & 1u);
+            mbar_wait(mbar0 + 16, (unsigned)vi & 1u);
             if (vi + 1 < nv) mbar_wait(mbar0 + 8 * (st ^ 1), (unsigned)((vi + 1) >> 1) & 1u);
             ok = false;
             break;
         }
         const float *rf = (const float *)(wb + pl.o_rf + st * pl.stage);
-        const uint64_t *rc = (const uint64_t *)(wb + pl.o_rc + st * pl.stage);
+        const uint64_t *rc = (const uint64_t *)(wb + pl.o_rc);
         const unsigned char *ds = wb + pl.o_ds + st * pl.stage;
         const int4 hdr = *(const int4 *)ds;
         const int nseg = hdr.z & 0xff, ncen = (hdr.z >> 8) & 0xff;
-        if (nseg < 1 || nseg > pl.seg_cap || ncen > pl.seg_cap) {
+        const bool good = nseg >= 1 && nseg <= pl.seg_cap && ncen <= pl.seg_cap &&
+                          kDsSegs + nseg * kDsSegBytes + ncen * kDsCenBytes <= ((hdr.z >> 16) & 0xffff);
+        // census: integer steps at the census breakpoints
+        if (good) {
+            const int4 *ce = (const int4 *)(ds + kDsSegs + nseg * kDsSegBytes);
+            int prev = 0;
+            for (int b = 0; b < ncen; b++) {
+                const int4 e = ce[b];
+                const int h = __popcll(cr ^ rc[e.x + lane]);
+                atomicAdd((int *)((char *)cdw + e.y), (int)((unsigned)(h - prev) << e.z));
+                prev = h;
+            }
+        }
+        __syncwarp();                                  // every lane has read the census tile
+        if (vi + 1 < nv) {
+            issue_cen(view_of(vi + 1), hd_next);
+            if (vi + 2 < nv) hd_next = head(view_of(vi + 2));
+        }
+        if (!good) {
             if (lane == 0) atomicExch(status, 7);      // cannot happen: the host checked every descriptor
             __syncwarp();
             continue;
         }
-        const int4 *segs = (const int4 *)(ds + kDsSegs);
-        const unsigned *cens = (const unsigned *)(ds + kDsSegs + pl.seg_cap * 16);
-        // census: integer steps at the census breakpoints
-        {
-            int prev = 0;
-            for (int b = 0; b < ncen; b++) {
-                const unsigned e = cens[b];
-                const int h = __popcll(cr ^ rc[(e >> 8) + lane]);
-                cdiff[(e & 0xff) * 32 + lane] += (short)(h - prev);
-                prev = h;
-            }
-        }
-        // l2 term: per cell segment this lane's sample polynomial in the absolute label index
+        // l2 term: per cell segment this lane's sample polynomial (minus I_ref) in the label index
         const float2 axy = *(const float2 *)(ds + kDsAxy);
-        const float ax = axy.x, ay = axy.y;
+        const float axay = __int_as_float(hdr.w);
+        const float4 *sg = (const float4 *)(ds + kDsSegs);
         for (int sgi = 0; sgi < nseg; sgi++) {
-            const int4 sd = segs[sgi];
-            const float tfx = __int_as_float(sd.z), tfy = __int_as_float(sd.w);
-            const float *q = rf + sd.x + lane;
+            const float4 d0 = sg[2 * sgi], d1 = sg[2 * sgi + 1];
+            const float *q = rf + __float_as_int(d0.x) + lane;
             const float i00 = q[0], i10 = q[1], i01 = q[pl.bwf], i11 = q[pl.bwf + 1];
             const float c1 = i10 - i00, c2 = i01 - i00, c3 = (i11 - i01) - c1;
-            // s(t) = c0 + c1 fx + c2 fy + c3 fx fy, fx = fx0 + ax t, fy = fy0 + ay t, t = i' - i
-            const float a0 = fmaf(c3 * tfx, tfy, fmaf(c2, tfy, fmaf(c1, tfx, i00)));
-            const float b0 = fmaf(c3, fmaf(tfx, ay, tfy * ax), fmaf(c2, ay, c1 * ax));
-            const float Cq = c3 * ax * ay;
-            const float fi = (float)sd.y;
-            *(float4 *)(coef + sgi * 512 + lane * 16) =
-                make_float4(fmaf(fi, fmaf(fi, Cq, -b0), a0), fmaf(-2.f * fi, Cq, b0), Cq, 0.f);
+            // s(t) - I_ref = (c0 - I_ref) + c1 fx + c2 fy + c3 fx fy, fx = fx0 + ax t, fy = fy0 + ay t,
+            // t = i - fi: value a0, slope b0 and curvature Cq at t = 0, then in powers of i
+            const float a0 = fmaf(c3, d1.x, fmaf(c2, d0.w, fmaf(c1, d0.z, i00 - Iref)));
+            const float b0 = fmaf(c3, d1.y, fmaf(c2, axy.y, c1 * axy.x));
+            const float Cq = c3 * axay;
+            const float fi = d0.y;
+            cab[32 * sgi] = make_float2(fmaf(fi, fmaf(fi, Cq, -b0), a0), fmaf(d1.z, Cq, b0));
+            ccq[32 * sgi] = Cq;
         }
-        __syncwarp();
-        // the lane's coefficients of the current segment stay in registers; a new segment's are
-        // loaded where the (warp-uniform) start mask has a bit
+        // (each lane reads back only its own coefficients: no warp synchronisation needed)
         const uint2 smask = *(const uint2 *)(ds + kDsMask);
-        // (one predicated pointer step and load per label, the mask bit tested against an
-        // immediate: no branch, and the load stays where it is)
-        unsigned cp = smem_u32(coef + lane * 16) - 512u;
+        unsigned cpab = smem_u32(cab) - 256u, cpc = smem_u32(ccq) - 128u;
         float4 cf = make_float4(0.f, 0.f, 0.f, 0.f);
 #pragma unroll
-        for (int i = 0; i < KW; i++) {
-            asm volatile("{\n .reg .pred p;\n .reg .b32 t;\n and.b32 t, %5, %6;\n setp.ne.u32 p, t, 0;\n"
-                         " @p add.u32 %4, %4, 512;\n @p ld.shared.v4.f32 {%0, %1, %2, %3}, [%4];\n}"
-                         : "+f"(cf.x), "+f"(cf.y), "+f"(cf.z), "+f"(cf.w), "+r"(cp)
-                         : "r"(i < 32 ? smask.x : smask.y), "r"(1u << (i & 31)));
-            const float fi = (float)i;
-            const float smp = fmaf(fi, fmaf(fi, cf.z, cf.y), cf.x);
-            acc[i] = fmaf(wl2, fabsf(Iref - smp), acc[i]);
+        for (int k = 0; k < KW / 4; k++) {
+            const unsigned bits = (k < 8 ? smask.x >> (4 * k) : smask.y >> (4 * k - 32)) & 0xfu;
+            if (bits == 0) {
+#pragma unroll
+                for (int e = 0; e < 4; e++) {
+                    const float fi = (float)(4 * k + e);
+                    acc[4 * k + e] += fabsf(fmaf(fi, fmaf(fi, cf.z, cf.y), cf.x));
+                }
+            } else {
+#pragma unroll
+                for (int e = 0; e < 4; e++) {
+                    // a segment starts at this label: step to its coefficients (predicated, no branch)
+                    asm volatile("{\n .reg .pred p;\n .reg .b32 t;\n and.b32 t, %5, %6;\n setp.ne.u32 p, t, 0;\n"
+                                 " @p add.u32 %3, %3, 256;\n @p add.u32 %4, %4, 128;\n"
+                                 " @p ld.shared.v2.f32 {%0, %1}, [%3];\n @p ld.shared.f32 %2, [%4];\n}"
+                                 : "+f"(cf.x), "+f"(cf.y), "+f"(cf.z), "+r"(cpab), "+r"(cpc)
+                                 : "r"(bits), "r"(1u << e));
+                    const float fi = (float)(4 * k + e);
+                    acc[4 * k + e] += fabsf(fmaf(fi, fmaf(fi, cf.z, cf.y), cf.x));
+                }
+            }
         }
         __syncwarp();
     }
     if (!ok) return;
+    __syncwarp();
     if (fits) {
         int run = 0;
 #pragma unroll
-        for (int i = 0; i < KW; i++) {
-            run += cdiff[i * 32 + lane];
+        for (int i = 0; i < KW; i += 2) {
+            // the word holds d(i) + d(i+1) 2^16 (two's complement, |d| < 2^15): split it exactly
+            const int w = cdw[16 * i];
+            const int d0 = (int)(short)(w & 0xffff), d1 = (w - d0) >> 16;
+            run += d0;
             const int g = g0 + i;
-            if (g >= l && g < l + n) cost[o + (g - l)] = fmaf(wc, (float)run, acc[i]);
+            if (g >= l && g < l + n) cost[o + (g - l)] = fmaf(wc, (float)run, wl2 * acc[i]);
+            run += d1;
+            if (g + 1 >= l && g + 1 < l + n) cost[o + (g + 1 - l)] = fmaf(wc, (float)run, wl2 * acc[i + 1]);
         }
     }
 }
@@ -439,21 +484,27 @@ bool plan_fine_rows(int U, int V, int uc, int vc, int H, int W, int G, double dm
     pl.bwc = (spx + 35 + 1) & ~1;
     pl.bhc = spy + 3;
     pl.seg_cap = min(kRowKW, spx + spy + 3);
-    pl.ds_stride = (kDsSegs + pl.seg_cap * 20 + 15) & ~15;
+    pl.ds_stride = (kDsSegs + pl.seg_cap * (kDsSegBytes + kDsCenBytes) + 15) & ~15;
     int o = 0;
-    pl.o_mbar = o;
-    o += 128;
     pl.o_rf = o;
-    pl.o_rc = pl.o_rf + r128(pl.bwf * pl.bhf * 4);
-    pl.o_ds = pl.o_rc + r128(pl.bwc * pl.bhc * 8);
-    pl.stage = pl.o_ds + r128(pl.ds_stride) - pl.o_rf;
+    pl.o_ds = pl.o_rf + r128(pl.bwf * pl.bhf * 4);
+    pl.stage = r128(pl.o_ds + pl.ds_stride - pl.o_rf);
     o = pl.o_rf + 2 * pl.stage;
-    pl.o_coef = o;
-    o += r128(pl.seg_cap * 512);
+    pl.o_rc = o;
+    o += r128(pl.bwc * pl.bhc * 8);
+    pl.o_cab = o;
+    o += pl.seg_cap * 256;
+    pl.o_cc = o;
+    o += pl.seg_cap * 128;
     pl.o_cdiff = o;
-    o += r128(kRowKW * 64);
+    o += kRowKW / 2 * 128;
+    pl.o_mbar = o;
+    o += 32;
+    o = r128(o);
     pl.warp_bytes = o;
-    out->ok = pl.bwf <= 256 && pl.bwc <= 256 && pl.bhf <= 256 && pl.bhc <= 256 && pl.warp_bytes <= 48 * 1024;
+    // the census steps of one label, summed over the views, must fit 16 bits (at most 48 bits a word)
+    out->ok = pl.bwf <= 256 && pl.bwc <= 256 && pl.bhf <= 256 && pl.bhc <= 256 && pl.warp_bytes <= 48 * 1024 &&
+              (U * V - 1) * 48 < 32768 && pl.ds_stride < 65536;
     static_assert(sizeof(RowPlan) <= sizeof(out->raw), "plan storage");
     memcpy(out->raw, &pl, sizeof(pl));
     out->P = pl.P;
@@ -511,26 +562,33 @@ bool build_fine_rows_desc(const RowPlanHost *ph, const FineTap *tab, int U, int 
                 return false;
             const int16_t org[4] = {(int16_t)xf, (int16_t)(yf), (int16_t)xc, (int16_t)yc};
             memcpy(d, org, 8);
-            d[8] = (unsigned char)segstart.size();
-            d[9] = (unsigned char)censtart.size();
+            const int nseg = (int)segstart.size(), ncen = (int)censtart.size();
+            d[8] = (unsigned char)nseg;
+            d[9] = (unsigned char)ncen;
+            const uint16_t nbytes = (uint16_t)((kDsSegs + nseg * kDsSegBytes + ncen * kDsCenBytes + 15) & ~15);
+            memcpy(d + 10, &nbytes, 2);
+            // the view's disparity-to-shift factors (u-uc) * step, (v-vc) * step and their product
+            const float ax = a * fstep, ay = b * fstep, axay = ax * ay;
+            memcpy(d + 12, &axay, 4);
             uint64_t smask = 0;
             for (int i : segstart) smask |= 1ull << i;
             memcpy(d + kDsMask, &smask, 8);
-            // the view's disparity-to-shift factors (u-uc) * step, (v-vc) * step, as the kernel's FP32
-            const float axy[2] = {a * fstep, b * fstep};
+            const float axy[2] = {ax, ay};
             memcpy(d + kDsAxy, axy, 8);
-            int32_t *seg = (int32_t *)(d + kDsSegs);
-            for (size_t k = 0; k < segstart.size(); k++) {
+            for (int k = 0; k < nseg; k++) {
                 const FineTap &w = t[segstart[k]];
-                seg[4 * k] = (byf + w.oy) * pl.bwf + (bxf + w.ox);
-                seg[4 * k + 1] = segstart[k];
-                memcpy(&seg[4 * k + 2], &w.fx, 4);
-                memcpy(&seg[4 * k + 3], &w.fy, 4);
+                unsigned char *e = d + kDsSegs + k * kDsSegBytes;
+                const int32_t toff = (byf + w.oy) * pl.bwf + (bxf + w.ox);
+                const float f[7] = {(float)segstart[k], w.fx, w.fy, w.fx * w.fy, std::fmaf(w.fx, ay, w.fy * ax),
+                                    -2.f * (float)segstart[k], 0.f};
+                memcpy(e, &toff, 4);
+                memcpy(e + 4, f, 28);
             }
-            uint32_t *cen = (uint32_t *)(d + kDsSegs + pl.seg_cap * 16);
-            for (size_t k = 0; k < censtart.size(); k++) {
+            for (int k = 0; k < ncen; k++) {
                 const FineTap &w = t[censtart[k]];
-                cen[k] = (uint32_t)censtart[k] | ((uint32_t)((byc + w.ny) * pl.bwc + (bxc + w.nx)) << 8);
+                const int32_t e4[4] = {(byc + w.ny) * pl.bwc + (bxc + w.nx), (censtart[k] >> 1) * 128,
+                                       16 * (censtart[k] & 1), 0};
+                memcpy(d + kDsSegs + nseg * kDsSegBytes + k * kDsCenBytes, e4, 16);
             }
         }
     }
@@ -584,9 +642,10 @@ cudaError_t launch_fine_cost_rows(cudaStream_t s, const RowPlanHost *ph, const f
     if (e != cudaSuccess) return e;
     const long long tasks = (long long)((W + 31) / 32) * H;
     const unsigned grid = (unsigned)((tasks + wpb - 1) / wpb);
+    (void)fstep;
     fine_cost_rows<kRowKW><<<grid, 32 * wpb, smem, s>>>(*(const CUtensorMap *)ph->tm_v, *(const CUtensorMap *)ph->tm_c,
                                                         desc, G, U, V, H, W, ref, lo, cnt, off, views_pad, cen_pad, wl2,
-                                                        wc, fstep, cost, status, list, list_count, pl);
+                                                        wc, cost, status, list, list_count, pl);
     return cudaGetLastError();
 }
 

@@ -14,6 +14,15 @@
 // and the predecessor minimum m is one redux.sync.min.f32 per pixel.  The 8 or 16 directions run
 // concurrently and add into agg (zeroed by the caller) with float atomics.
 //
+// Reproducible sum over the directions.  The aggregate C_s(p,g) = sum_r L_r(p,g) must not depend on
+// the order in which the directions' atomics arrive.  Every exact L_r(p,g) lies in [0, B] with
+// B = C(p,g) + P2 (the bracket is at most P2 above m), and B depends only on the cell.  Each
+// direction clamps its FP32 L_r to B (removing rounding beyond the exact bound) and rounds it to a
+// multiple of q = 2^(floor(log2 B) + 1 + log2(paths) - 24) before adding it.  Then every partial sum
+// is a multiple of q no larger than paths x 2^(floor(log2 B) + 1) = 2^24 q, so it is exactly
+// representable: each addition is exact, and the sum is the same in any order.  The rounding moves
+// an addend by at most q / 2 <= 2^-21 B (8 paths) or 2^-20 B (16 paths).
+//
 // Derived penalties: per-block partial sums (double) of the active slots, then one block
 // adds the partials in a fixed order, so the mean is deterministic.
 #include "lfsgm_internal.cuh"
@@ -24,6 +33,15 @@ namespace lfsgm {
 namespace {
 
 constexpr int kSgmWarps = 4;
+
+// L rounded to a multiple of q (see above); B = C + P2 of the cell.  With M = 1.5 x 2^(floor(log2 B)
+// + 23 - qsh), qsh = 23 - log2(paths), every x in [0, B] gives x + M in M's binade, whose spacing
+// is q: fl(x + M) - M is x rounded to a multiple of q (half to even), and the subtraction is exact.
+// mk = (23 - qsh) << 23 | 1 << 22 puts M's exponent and its leading fraction bit in place.
+__device__ __forceinline__ float det_addend(float L, float B, int mk) {
+    const float M = __int_as_float((__float_as_int(B) & 0x7f800000) + mk);
+    return __fsub_rn(__fadd_rn(fminf(L, B), M), M);
+}
 
 __device__ __forceinline__ float warp_min(float v) {
     float r;
@@ -39,7 +57,7 @@ __global__ void __launch_bounds__(32 * kSgmWarps) fine_sgm_kernel(const float *_
                                                                   const float *__restrict__ pen,
                                                                   int G, ScanTable st, float *__restrict__ agg,
                                                                   int *__restrict__ status,
-    const int *__restrict__ order) {
+                                                                  const int *__restrict__ order, int mk) {
     extern __shared__ float sm[];
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
     const int gw = blockIdx.x * kSgmWarps + wib;
@@ -125,7 +143,7 @@ __global__ void __launch_bounds__(32 * kSgmWarps) fine_sgm_kernel(const float *_
                     Lv = c + (t - m);
                 }
                 const bool act = lane < n;
-                if (act) atomicAdd(agg + 4ll * ofs + lane, Lv);
+                if (act) atomicAdd(agg + 4ll * ofs + lane, det_addend(Lv, c + P2, mk));
                 prev = act ? Lv : INF;
                 m = warp_min(prev);
                 plo = l;
@@ -174,7 +192,17 @@ __global__ void __launch_bounds__(32 * kSgmWarps) fine_sgm_kernel(const float *_
                             const float vm = row[min(k1 - 1u, top)];
                             const float vp = row[min(k1 + 1u, top)];
                             const float t = fminf(fminf(m + P2, v0), fminf(vm, vp) + P1);
-                            cc[u] = cc[u] + (t - m);
+                            const float Ln = cc[u] + (t - m);
+                            // the cell's cost cc[u] bounds its path costs (the global atomic does
+                            // not order the shared-memory reads of the other chunks)
+                            atomicAdd(agg + o + j0 + 32 * u, det_addend(Ln, cc[u] + P2, mk));
+                            cc[u] = Ln;
+                        }
+                    } else {
+#pragma unroll
+                        for (int u = 0; u < 16; u++) {
+                            if (j0 + 32 * u >= n) break;
+                            atomicAdd(agg + o + j0 + 32 * u, det_addend(cc[u], cc[u] + P2, mk));
                         }
                     }
 #pragma unroll
@@ -183,7 +211,6 @@ __global__ void __launch_bounds__(32 * kSgmWarps) fine_sgm_kernel(const float *_
                         if (j >= n) break;
                         bufB[j] = cc[u];
                         lmin = fminf(lmin, cc[u]);
-                        atomicAdd(agg + o + j, cc[u]);
                     }
                 }
                 m = warp_min(lmin);
@@ -223,7 +250,9 @@ __global__ void __launch_bounds__(256) cost_partial_kernel(const float *__restri
     for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < N; p += gridDim.x * blockDim.x) {
         const long long o = off[p];
         const int n = cnt[p];
-        if (!window_ok(0, n, G, off[p + 1] - o, status) || !row_aligned(o, status)) continue;
+        if (!window_ok(0, n, G, off[p + 1] - o, status) || !row_aligned(o, status) ||
+            !row_aligned(off[p + 1], status))
+            continue;
         const float4 *r = reinterpret_cast<const float4 *>(cost + o);
         float ps = 0.f;
         if (n <= 32) {
@@ -329,7 +358,11 @@ cudaError_t launch_fine_sgm(cudaStream_t s, const float *cost, const int *lo, co
                                              (int)smem);
         if (e != cudaSuccess) return e;
     }
-    fine_sgm_kernel<<<grid, 32 * kSgmWarps, smem, s>>>(cost, lo, cnt, off, H, W, Gs, pen, G, st, agg, status, order);
+    int lp = 0;
+    while ((1 << lp) < paths) lp++;
+    const int mk = (lp << 23) | (1 << 22);       // (23 - qsh) << 23 with qsh = 23 - log2(paths)
+    fine_sgm_kernel<<<grid, 32 * kSgmWarps, smem, s>>>(cost, lo, cnt, off, H, W, Gs, pen, G, st, agg, status, order,
+                                                       mk);
     return cudaGetLastError();
 }
 

@@ -19,7 +19,10 @@ __global__ void wta_kernel(const float *__restrict__ agg, const int *__restrict_
     if (p >= N) return;
     const float *s = agg + off[p];
     const int n = cnt[p], l = lo[p];
-    if (!window_ok(l, n, G, off[p + 1] - off[p], status) || !row_aligned(off[p], status)) {
+    // both ends of the row on a 4-slot boundary: the row then holds round4(n) slots, which the
+    // vector loads below read
+    if (!window_ok(l, n, G, off[p + 1] - off[p], status) || !row_aligned(off[p], status) ||
+        !row_aligned(off[p + 1], status)) {
         if (label) label[p] = -1;
         if (disp) disp[p] = __int_as_float(0x7fc00000);
         return;

@@ -1,27 +1,42 @@
 """GPU adjoint (lfsgm_backward, through the C ABI) against the oracle's FP64 adjoint, which is
 itself pinned by finite differences (tests/test_oracle_adjoint.py).
 
-The GPU aggregates in FP32 and feeds exp(-C_s / tau); a relative error e of C_s becomes
-~e C_s / tau (about 1e3 e here) in the softmax weights, so gradients are compared with a tolerance
-of 1e-3 of the largest oracle gradient (observed: ~3e-4); the adjoint's arithmetic itself is
-pinned in FP64 by finite differences."""
-GRAD_TOL = 1e-3
+Every gradient element is compared with the oracle's: |gpu - oracle| <= rel * scale + abs * G, with
+scale = max(|x|, mean |x| over the element's group) -- the group being the pixel's window for
+dLoss/dcost and the view plane for dLoss/dviews -- and G the largest oracle gradient of that kind.
+
+Tolerances.  The GPU aggregates in FP32 and feeds exp(-C_s / tau) into the soft-argmin.  An
+absolute error e of C_s becomes a relative error e / tau of the weights, and e is a few FP32
+unit roundoffs u of C_s, so the weights carry ~u C_s / tau: with tau = 0.1 and C_s up to 550
+(grey) or 1350 (colour) here, 3e-4 .. 8e-4.  The SGM adjoint then adds contributions of either
+sign; where they cancel, an element keeps the FP32 rounding of the terms it summed, which is a
+fraction of the largest gradient rather than of its own size.  Hence the relative part
+grad_tol = 16 u max(C_s) / tau (lf_helpers) plus GRAD_ABS of the largest gradient.  Measured, the
+needed relative part is 0 (the absolute part covers it) for 99 % of the elements; its maximum is
+1.5e-3 in dcost and 2.1e-3 in dviews (grey, against a bar of 5.2e-3 .. 5.8e-3) and 6.1e-3
+(colour, against 1.1e-2).  dLoss/dP1 and dLoss/dP2 sum signed adjoints over every cell and
+direction; each summand carries the weights' relative error, which does not cancel with the
+sum, so their bar adds GRAD_MASS of sum |dLoss/dcost| (measured: 1.4e-5 of it at worst).  Where
+C_s / tau is of order one (views of small contrast, tau = 1) the same kernels are held to
+GRAD_TOL_EXACT per element."""
 import numpy as np
 import pytest
 
 import lfsynth
 import oracle
-from lf_helpers import gather, pad4_offsets
+from lf_helpers import (GRAD_ABS, GRAD_MASS, GRAD_TOL_P, err_stats, gather, grad_tol, group_rel_err, needed_rel,
+                        pad4_offsets)
 
 pytestmark = pytest.mark.gpu
 TAU = 0.1
+GRAD_TOL_EXACT = 1e-5    # per element, C_s / tau ~ 1
 
 
-def _setup(seed=2024):
+def _setup(seed=2024, contrast=1.0, w_census=1.0 / 24, tau=TAU):
     p = lfsynth.LFParams(U=7, V=7, H=32, W=32, census_w=5, dmin=-1.0, dmax=1.0, coarse_labels=9,
-                         fine_labels=41, fine_radius=8, w_l2=1.0, w_census=1.0 / 24, subpixel=2, softmin_tau=TAU)
+                         fine_labels=41, fine_radius=8, w_l2=1.0, w_census=w_census, subpixel=2, softmin_tau=tau)
     rng = np.random.default_rng(seed)
-    views = rng.uniform(0.0, 1.0, (7, 7, 32, 32)).astype(np.float32)
+    views = (contrast * rng.uniform(0.0, 1.0, (7, 7, 32, 32))).astype(np.float32)
     lo = np.full(p.N, 12, np.int32)
     cnt = np.full(p.N, 16, np.int32)
     gd = rng.normal(size=p.N).astype(np.float32)
@@ -37,36 +52,82 @@ def _gpu_holder(lf, p, lo, cnt):
     return L
 
 
-def test_backward_matches_oracle_adjoint(gpu_lib):
+def _run_gpu_backward(lf, p, views, lo, cnt, P1, P2, gd, tau):
+    """dLoss/dcost (active slots), dP1, dP2, dLoss/dviews from the library."""
     import torch
-    p, views, lo, cnt, gd = _setup()
-    cfg = oracle.make_cfg(p)
-    off_o, cost_o = oracle.cost_volume(cfg, views, lo, cnt)
-    P1, P2 = np.float32(0.05 * cost_o.mean()), np.float32(0.5 * cost_o.mean())
-    gC_o, g1_o, g2_o, gV_o = oracle.backward(cfg, views, lo, cnt, cost_o, float(P1), float(P2), gd, TAU)
-
-    L = _gpu_holder(gpu_lib, p, lo, cnt)
+    L = _gpu_holder(lf, p, lo, cnt)
     vd = torch.from_numpy(views).cuda()
     L.cost_volume(vd)
     gcost = torch.empty_like(L.cost)
     gviews = torch.empty_like(vd)
     g1 = torch.zeros(1, device="cuda")
     g2 = torch.zeros(1, device="cuda")
-    gpu_lib.lfsgm_backward(L.h, vd, L.cost, L.lo, L.cnt, L.off, float(P1), float(P2), torch.from_numpy(gd).cuda(),
-                           gcost, g1, g2, gviews)
-    gpu_lib.lfsgm_sync(L.h)
-    off = pad4_offsets(cnt)
-    gC = gather(gcost.cpu().numpy(), off, cnt)
-    scale = np.abs(gC_o).max()
-    assert np.abs(gC - gC_o).max() <= GRAD_TOL * scale, (np.abs(gC - gC_o).max(), scale)
-    assert abs(g1.item() - g1_o) <= GRAD_TOL * max(abs(g1_o), 1e-3), (g1.item(), g1_o)
-    assert abs(g2.item() - g2_o) <= GRAD_TOL * max(abs(g2_o), 1e-3), (g2.item(), g2_o)
-    gV = gviews.cpu().numpy()
-    vs = np.abs(gV_o).max()
-    assert np.abs(gV - gV_o).max() <= GRAD_TOL * vs, (np.abs(gV - gV_o).max(), vs)
-    # exact invariant: per-pixel sums of dLoss/dcost vanish (normalised SGM + shift-invariant softmax)
-    assert np.abs(gC.reshape(p.N, 16).sum(1)).max() <= 1e-5 * scale * 16
+    lf.lfsgm_backward(L.h, vd, L.cost, L.lo, L.cnt, L.off, float(P1), float(P2), torch.from_numpy(gd).cuda(),
+                      gcost, g1, g2, gviews)
+    lf.lfsgm_sync(L.h)
+    gC = gather(gcost.cpu().numpy(), pad4_offsets(cnt), cnt)
+    out = gC, g1.item(), g2.item(), gviews.cpu().numpy()
     L.close()
+    return out
+
+
+def _cs_max(p, lo, cnt, off_o, cost_o, P1, P2):
+    return oracle.sgm_bounded(p.H, p.W, lo, cnt, off_o, cost_o, float(P1), float(P2), p.paths).max()
+
+
+def _elem_errors(p, cnt, gC, gC_o, gV, gV_o, abs_frac=GRAD_ABS):
+    """The relative tolerance each element needs beside the absolute part (dcost, dviews)."""
+    planes = np.full(p.U * p.V * p.channels, p.H * p.W)
+    return needed_rel(gC, gC_o, cnt, abs_frac), needed_rel(gV, gV_o, planes, abs_frac)
+
+
+def _penalties(cost_o):
+    return np.float32(0.05 * cost_o.mean()), np.float32(0.5 * cost_o.mean())
+
+
+def test_backward_matches_oracle_adjoint(gpu_lib):
+    p, views, lo, cnt, gd = _setup()
+    cfg = oracle.make_cfg(p)
+    off_o, cost_o = oracle.cost_volume(cfg, views, lo, cnt)
+    P1, P2 = _penalties(cost_o)
+    gC_o, g1_o, g2_o, gV_o = oracle.backward(cfg, views, lo, cnt, cost_o, float(P1), float(P2), gd, TAU)
+    gC, g1, g2, gV = _run_gpu_backward(gpu_lib, p, views, lo, cnt, P1, P2, gd, TAU)
+    eC, eV = _elem_errors(p, cnt, gC, gC_o, gV, gV_o)
+    tol = grad_tol(_cs_max(p, lo, cnt, off_o, cost_o, P1, P2), TAU)
+    print(f"backward 7x7x32x32 tau 0.1, bar {tol:.2e}, needed relative tolerance: dcost", err_stats(eC),
+          "dviews", err_stats(eV), "plain relative error: dcost", err_stats(group_rel_err(gC, gC_o, cnt)))
+    assert eC.max() <= tol, err_stats(eC)
+    assert eV.max() <= tol, err_stats(eV)
+    assert abs(g1 - g1_o) <= GRAD_TOL_P * max(abs(g1_o), 1e-3), (g1, g1_o)
+    assert abs(g2 - g2_o) <= GRAD_TOL_P * max(abs(g2_o), 1e-3), (g2, g2_o)
+    # exact invariant: per-pixel sums of dLoss/dcost vanish (normalised SGM + shift-invariant softmax)
+    scale = np.abs(gC_o).max()
+    assert np.abs(gC.reshape(p.N, 16).sum(1)).max() <= 1e-5 * scale * 16
+
+
+@pytest.mark.parametrize("seed", [2024, 7])
+def test_backward_low_amplification_matches_oracle_per_element(gpu_lib, seed):
+    """Views of contrast 0.01, a small census weight and tau = 1 keep C_s / tau near one, so FP32
+    rounding of the aggregate is not amplified by the softmax: every element of dLoss/dcost and
+    dLoss/dviews agrees with the FP64 adjoint to GRAD_TOL_EXACT of its scale."""
+    tau = 1.0
+    p, views, lo, cnt, gd = _setup(seed=seed, contrast=0.01, w_census=1e-4, tau=tau)
+    cfg = oracle.make_cfg(p)
+    off_o, cost_o = oracle.cost_volume(cfg, views, lo, cnt)
+    P1, P2 = _penalties(cost_o)
+    gC_o, g1_o, g2_o, gV_o = oracle.backward(cfg, views, lo, cnt, cost_o, float(P1), float(P2), gd, tau)
+    gC, g1, g2, gV = _run_gpu_backward(gpu_lib, p, views, lo, cnt, P1, P2, gd, tau)
+    # dcost: purely relative; dviews: plus 1e-6 of the largest view gradient (each view pixel sums
+    # ~10^2 signed FP32 terms, measured 1.8e-5 of its scale at worst without that part)
+    eC, _ = _elem_errors(p, cnt, gC, gC_o, gV, gV_o, abs_frac=0.0)
+    _, eV = _elem_errors(p, cnt, gC, gC_o, gV, gV_o, abs_frac=1e-6)
+    print(f"backward low amplification seed {seed}: dcost", err_stats(eC), "dviews", err_stats(eV),
+          "dP1", g1, g1_o, "dP2", g2, g2_o)
+    assert eC.max() <= GRAD_TOL_EXACT, err_stats(eC)
+    assert eV.max() <= GRAD_TOL_EXACT, err_stats(eV)
+    mass = np.abs(gC_o).sum()
+    assert abs(g1 - g1_o) <= GRAD_TOL_EXACT * (abs(g1_o) + 1e-3 * mass), (g1, g1_o)
+    assert abs(g2 - g2_o) <= GRAD_TOL_EXACT * (abs(g2_o) + 1e-3 * mass), (g2, g2_o)
 
 
 def _ragged_case(kind, seed=77):
@@ -92,37 +153,60 @@ def _ragged_case(kind, seed=77):
 @pytest.mark.parametrize("kind", ["mixed", "wide_range", "mixed_16_paths"])
 def test_backward_ragged_windows_match_oracle(gpu_lib, kind):
     import dataclasses
-
-    import torch
     p, views, lo, cnt, gd = _ragged_case(kind.replace("_16_paths", ""))
     if kind.endswith("16_paths"):
         p = dataclasses.replace(p, paths=16)
     cfg = oracle.make_cfg(p)
     off_o, cost_o = oracle.cost_volume(cfg, views, lo, cnt)
-    P1, P2 = np.float32(0.05 * cost_o.mean()), np.float32(0.5 * cost_o.mean())
+    P1, P2 = _penalties(cost_o)
     gC_o, g1_o, g2_o, gV_o = oracle.backward(cfg, views, lo, cnt, cost_o, float(P1), float(P2), gd, TAU)
-    L = _gpu_holder(gpu_lib, p, lo, cnt)
-    vd = torch.from_numpy(views).cuda()
-    L.cost_volume(vd)
-    gcost = torch.empty_like(L.cost)
-    gviews = torch.empty_like(vd)
-    g1 = torch.zeros(1, device="cuda")
-    g2 = torch.zeros(1, device="cuda")
-    gpu_lib.lfsgm_backward(L.h, vd, L.cost, L.lo, L.cnt, L.off, float(P1), float(P2), torch.from_numpy(gd).cuda(),
-                           gcost, g1, g2, gviews)
-    gpu_lib.lfsgm_sync(L.h)
-    gC = gather(gcost.cpu().numpy(), pad4_offsets(cnt), cnt)
-    assert np.abs(gC - gC_o).max() <= GRAD_TOL * np.abs(gC_o).max()
-    # dLoss/dP1, dLoss/dP2 are signed sums over every cell and direction; FP32 errors of relative
-    # size ~1e-4 in the summed adjoints add up in proportion to their total magnitude (scale:
-    # sum |dLoss/dC|), which dominates where the sum cancels (here |dLoss/dP1| ~ 1e-3 sum |dLoss/dC|)
-    mass = 2e-3 * np.abs(gC_o).sum()
-    assert abs(g1.item() - g1_o) <= GRAD_TOL * (abs(g1_o) + mass), (g1.item(), g1_o, mass)
-    assert abs(g2.item() - g2_o) <= GRAD_TOL * (abs(g2_o) + mass), (g2.item(), g2_o, mass)
-    gV = gviews.cpu().numpy()
-    vs = np.abs(gV_o).max()
-    assert np.abs(gV - gV_o).max() <= GRAD_TOL * vs, (kind, np.abs(gV - gV_o).max(), vs)
-    L.close()
+    gC, g1, g2, gV = _run_gpu_backward(gpu_lib, p, views, lo, cnt, P1, P2, gd, TAU)
+    eC, eV = _elem_errors(p, cnt, gC, gC_o, gV, gV_o)
+    tol = grad_tol(_cs_max(p, lo, cnt, off_o, cost_o, P1, P2), TAU)
+    print(f"backward ragged {kind}, bar {tol:.2e}, needed relative tolerance: dcost", err_stats(eC),
+          "dviews", err_stats(eV))
+    assert eC.max() <= tol, err_stats(eC)
+    assert eV.max() <= tol, err_stats(eV)
+    # dLoss/dP1, dLoss/dP2 are signed sums over every cell and direction (see the module docstring)
+    mass = GRAD_MASS / GRAD_TOL_P * np.abs(gC_o).sum()
+    assert abs(g1 - g1_o) <= GRAD_TOL_P * (abs(g1_o) + mass), (g1, g1_o, mass)
+    assert abs(g2 - g2_o) <= GRAD_TOL_P * (abs(g2_o) + mass), (g2, g2_o, mass)
+
+
+def test_backward_bench_band_matches_oracle(gpu_lib):
+    """Rows 192..255 of the 9x9 x 512x512 bench light field (census 7x7, 401 fine labels), with the
+    31-label windows of the oracle's own initial pass on that band: the GPU adjoint against the FP64
+    adjoint at the bench configuration (tau = 0.1).
+
+    On a real scene a few decisions of the adjoint sit on a kink: the SGM minimum has near-ties
+    (two branches within FP32 rounding of each other), and |I_ref - sample| has samples within
+    FP32 rounding of I_ref.  There the FP32 and FP64 adjoints pick different subgradients, both
+    correct.  So the per-element bar of the other tests must hold for all but 1e-4 of the elements
+    (measured: 6 of 1.1 M cost gradients, 19 of 2.7 M view gradients), and the total absolute
+    difference must stay below 1e-3 of the total gradient mass (measured 1.5e-4, 1.7e-4)."""
+    views_full, _, pb = lfsynth.bench()
+    y0, rows = 192, 64
+    band = np.ascontiguousarray(views_full[:, :, y0:y0 + rows, :])
+    p = lfsynth.LFParams(**{**pb.__dict__, "H": rows, "subpixel": 2, "softmin_tau": TAU})
+    cfg = oracle.make_cfg(p)
+    init = oracle.initial_disparity(cfg, band, None, p.p1_frac, p.p2_frac)
+    lo, cnt = init["lo"].astype(np.int32), init["cnt"].astype(np.int32)
+    off_o, cost_o = oracle.cost_volume(cfg, band, lo, cnt, init["census"])
+    P1, P2 = _penalties(cost_o)
+    gd = np.random.default_rng(11).normal(size=p.N).astype(np.float32)
+    gC_o, g1_o, g2_o, gV_o = oracle.backward(cfg, band, lo, cnt, cost_o, float(P1), float(P2), gd, TAU)
+    gC, g1, g2, gV = _run_gpu_backward(gpu_lib, p, band, lo, cnt, P1, P2, gd, TAU)
+    eC, eV = _elem_errors(p, cnt, gC, gC_o, gV, gV_o)
+    tol = grad_tol(_cs_max(p, lo, cnt, off_o, cost_o, P1, P2), TAU)
+    print(f"backward bench band, bar {tol:.2e}, needed relative tolerance: dcost", err_stats(eC), "dviews",
+          err_stats(eV), "beyond the bar:", int((eC > tol).sum()), int((eV > tol).sum()),
+          "dP1", g1, g1_o, "dP2", g2, g2_o)
+    for e, g, o in ((eC, gC, gC_o), (eV, gV, gV_o)):
+        assert np.mean(e > tol) <= 1e-4, err_stats(e)
+        assert np.abs(g.astype(np.float64).reshape(-1) - o.reshape(-1)).sum() <= 1e-3 * np.abs(o).sum()
+    mass = GRAD_MASS / GRAD_TOL_P * np.abs(gC_o).sum()
+    assert abs(g1 - g1_o) <= GRAD_TOL_P * (abs(g1_o) + mass), (g1, g1_o, mass)
+    assert abs(g2 - g2_o) <= GRAD_TOL_P * (abs(g2_o) + mass), (g2, g2_o, mass)
 
 
 def test_autograd_functions_match_direct_call(gpu_lib):
@@ -141,10 +225,10 @@ def test_autograd_functions_match_direct_call(gpu_lib):
     P2b = torch.tensor(2.5, device="cuda", requires_grad=True)
     disp2 = gpu_lib.sgm_softargmin(cost, P1b, P2b, L)
     (disp2 * g).sum().backward()
-    # two forward runs differ only in the float-atomic order of the 8 directions' sums
-    assert torch.allclose(disp, disp2, rtol=0.0, atol=1e-4)
-    assert abs(P1.grad.item() - P1b.grad.item()) <= GRAD_TOL * max(1.0, abs(P1b.grad.item()))
-    assert abs(P2.grad.item() - P2b.grad.item()) <= GRAD_TOL * max(1.0, abs(P2b.grad.item()))
+    # the aggregate is deterministic, so both routes give the same disparities
+    assert torch.equal(disp, disp2)
+    assert abs(P1.grad.item() - P1b.grad.item()) <= GRAD_TOL_P * max(1.0, abs(P1b.grad.item()))
+    assert abs(P2.grad.item() - P2b.grad.item()) <= GRAD_TOL_P * max(1.0, abs(P2b.grad.item()))
     assert torch.isfinite(vd.grad).all() and vd.grad.abs().sum() > 0
     # soft-argmin forward agrees with the oracle
     cfg = oracle.make_cfg(p)
@@ -182,8 +266,8 @@ def test_backward_bench_shape_invariants(gpu_lib):
     sums = np.add.reduceat(gC.astype(np.float64), starts)
     scale = np.add.reduceat(np.abs(gC).astype(np.float64), starts)
     # the sums vanish in exact arithmetic; in FP32 the adjoint is carried along 512-step paths
-    # (8 of them per pixel) and the softmax weights inherit the float-atomic order of the
-    # aggregate amplified by C_s / tau, so residuals of order n * eps_32 ~ 3e-5 of the global
-    # scale occur (observed 0.9e-5 .. 1.7e-5)
+    # (8 of them per pixel) and the softmax weights carry FP32 rounding of the aggregate
+    # amplified by C_s / tau, so residuals of order n * eps_32 ~ 3e-5 of the global scale occur
+    # (observed 0.9e-5 .. 1.7e-5)
     assert np.abs(sums).max() <= 1e-4 * scale.max(), (np.abs(sums).max(), scale.max())
     L.close()

@@ -83,8 +83,9 @@ def test_batch_matches_single_light_field_launches(gpu_lib, mix):
         gpu_lib.lfsgm_depth(h, torch.from_numpy(views).cuda(), one, None)
         gpu_lib.lfsgm_sync(h)
         gpu_lib.lfsgm_destroy(h)
-        # float atomics in the SGM sum: equal up to the last bits where the decision is clear
-        assert np.max(np.abs(one.cpu().numpy() - d)[decided]) < 1e-4, p.name
+        # every stage is deterministic (the SGM's direction sum included), so the batch reproduces
+        # the single launches bit for bit
+        assert np.array_equal(one.cpu().numpy(), d, equal_nan=True), p.name
 
 
 def test_batch_runs_repeatedly(gpu_lib, mix):
@@ -95,8 +96,8 @@ def test_batch_runs_repeatedly(gpu_lib, mix):
     for _ in range(3):
         b.run()
     b.times()
-    for a, c, (_, _, _, decided) in zip(first, b.disp, mix[:3]):
-        assert torch.max(torch.abs(a - c)[torch.from_numpy(decided).cuda()]).item() < 1e-4
+    for a, c in zip(first, b.disp):
+        assert torch.equal(torch.nan_to_num(a, nan=-1e30), torch.nan_to_num(c, nan=-1e30))
     b.close()
 
 
