@@ -57,9 +57,20 @@ __global__ void __launch_bounds__(TX *TY) census_kernel(const float *__restrict_
     cen[(size_t)view * HW + (size_t)y * W + x] = census_word<HALF>(&tile[threadIdx.y][threadIdx.x], SW + 1, c);
 }
 
+// (v - c0, v - c1) as one packed FP32 subtraction (sm_100+): each half is rounded exactly as the
+// scalar subtraction would be, so the signs are the same.
+__device__ __forceinline__ void sub_pair(float v, float c0, float c1, uint32_t &d0, uint32_t &d1) {
+    unsigned long long r;
+    asm("{\n .reg .b64 va, vc;\n mov.b64 va, {%1, %1};\n mov.b64 vc, {%2, %3};\n sub.rn.f32x2 %0, va, vc;\n}"
+        : "=l"(r) : "f"(v), "f"(c0), "f"(c1));
+    d0 = (uint32_t)r;
+    d1 = (uint32_t)(r >> 32);
+}
+
 // Census words of the two vertically adjacent pixels whose windows start at t and t + ld: every
 // tile value of the union of the two windows is read once, and each word takes its own neighbours
-// in descending order (rows bottom-up, columns right to left), as census_word does.
+// in descending order (rows bottom-up, columns right to left), as census_word does.  Where a tile
+// value is a neighbour of both pixels, the two differences are one packed subtraction.
 template <int HALF>
 __device__ __forceinline__ void census_word2(const float *t, int ld, float c0, float c1, uint64_t &w0,
                                              uint64_t &w1) {
@@ -70,23 +81,21 @@ __device__ __forceinline__ void census_word2(const float *t, int ld, float c0, f
 #pragma unroll
         for (int rx = WN - 1; rx >= 0; rx--) {
             const float v = t[ry * ld + rx];
-            if (ry < WN) {
-                const int q = ry * WN + rx;
-                if (q != CEN) {
-                    const int k = q < CEN ? q : q - 1;
-                    const uint32_t d = __float_as_uint(v - c0);
-                    if (k >= 32) hi0 = __funnelshift_l(d, hi0, 1);
-                    else lo0 = __funnelshift_l(d, lo0, 1);
-                }
+            const int q0 = ry * WN + rx, q1 = (ry - 1) * WN + rx;
+            const bool use0 = ry < WN && q0 != CEN, use1 = ry >= 1 && q1 != CEN;
+            uint32_t d0 = 0, d1 = 0;
+            if (use0 && use1) sub_pair(v, c0, c1, d0, d1);
+            else if (use0) d0 = __float_as_uint(v - c0);
+            else if (use1) d1 = __float_as_uint(v - c1);
+            if (use0) {
+                const int k = q0 < CEN ? q0 : q0 - 1;
+                if (k >= 32) hi0 = __funnelshift_l(d0, hi0, 1);
+                else lo0 = __funnelshift_l(d0, lo0, 1);
             }
-            if (ry >= 1) {
-                const int q = (ry - 1) * WN + rx;
-                if (q != CEN) {
-                    const int k = q < CEN ? q : q - 1;
-                    const uint32_t d = __float_as_uint(v - c1);
-                    if (k >= 32) hi1 = __funnelshift_l(d, hi1, 1);
-                    else lo1 = __funnelshift_l(d, lo1, 1);
-                }
+            if (use1) {
+                const int k = q1 < CEN ? q1 : q1 - 1;
+                if (k >= 32) hi1 = __funnelshift_l(d1, hi1, 1);
+                else lo1 = __funnelshift_l(d1, lo1, 1);
             }
         }
     }
