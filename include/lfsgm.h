@@ -203,7 +203,8 @@ lfsgm_status lfsgm_depth(lfsgm_handle h, const float *views, float *disp, int32_
  * Each light field i has its own configuration cfgs[i], views[i] ([V][U][C][H][W] float32, device)
  * and output disp[i] ([H*W] float32, device); the pointers are baked into the graph at creation.
  * The pipeline of lfsgm_depth (derived penalties) runs for every light field; light fields are
- * spread over `branches` concurrent streams forked from `stream` (longest work first), branches
+ * spread over `branches` concurrent streams forked from `stream` (balanced by longest work first;
+ * each branch then runs its light fields shortest first), branches
  * <= 0 lets an autotuner time K in {1,2,4,8,16} and keep the fastest.  Scratch is allocated at
  * creation (per branch, sized for its largest member).  lfsgm_batch_run enqueues one graph launch;
  * lfsgm_batch_times synchronises and returns, per light field, the start and end of its pipeline
@@ -219,6 +220,22 @@ lfsgm_status lfsgm_batch_times(lfsgm_batch b, double *start_ms, double *end_ms, 
 int64_t lfsgm_batch_kernel_nodes(lfsgm_batch b);    /* kernel nodes in the batch's graph */
 const char *lfsgm_batch_last_error(lfsgm_batch b);  /* NULL: error of the last failed create */
 lfsgm_status lfsgm_batch_destroy(lfsgm_batch b);
+
+/* A batch whose scratch lives in caller memory (not in the paper): for a serving process that
+ * keeps its device memory in its own pool.  lfsgm_batch_workspace_size returns, from the
+ * configurations alone (no device work), the bytes a batch of these light fields needs with
+ * `branches` branches (branches <= 0: the most any autotuned branch count needs).
+ * lfsgm_batch_create_ws is lfsgm_batch_create with that scratch taken from ws (device memory,
+ * 256-byte aligned, ws_bytes long, caller-owned, valid until lfsgm_batch_destroy): the branches'
+ * workspaces, window maps, labels, cost volumes and aggregates, and the timing stamps.  With
+ * branches <= 0 the autotuner tries only the branch counts whose scratch fits ws_bytes.  The
+ * per-light-field tables (shift tables, row descriptors) stay library-owned, as for a handle given
+ * a workspace with lfsgm_set_workspace.  Errors: LFSGM_ERR_WORKSPACE if ws is misaligned or
+ * too small (lfsgm_batch_last_error(NULL) gives the size needed), otherwise as lfsgm_batch_create. */
+lfsgm_status lfsgm_batch_workspace_size(int32_t n, const lfsgm_config *cfgs, int32_t branches, size_t *bytes);
+lfsgm_status lfsgm_batch_create_ws(int32_t n, const lfsgm_config *cfgs, const float *const *views,
+                                   float *const *disp, void *stream, int32_t branches, void *ws, size_t ws_bytes,
+                                   lfsgm_batch *out);
 
 /* The bounded cost volume (same result as lfsgm_cost_volume) for callers that may not
  * allocate device memory.  The paper has no counterpart: this is a deployment variant.

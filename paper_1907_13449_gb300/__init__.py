@@ -64,7 +64,7 @@ EXPORTS = ["lfsgm_create", "lfsgm_destroy", "lfsgm_workspace_size", "lfsgm_set_w
            "lfsgm_launch_count", "lfsgm_set_profiling", "lfsgm_kernel_times", "lfsgm_depth_host",
            "lfsgm_depth", "lfsgm_cost_volume_noalloc", "lfsgm_batch_create", "lfsgm_batch_run",
            "lfsgm_batch_times", "lfsgm_batch_kernel_nodes", "lfsgm_batch_last_error",
-           "lfsgm_batch_destroy", "lfsgm_median_filter"]
+           "lfsgm_batch_destroy", "lfsgm_median_filter", "lfsgm_batch_workspace_size", "lfsgm_batch_create_ws"]
 
 
 def load(build_if_missing: bool = False):
@@ -103,6 +103,8 @@ def load(build_if_missing: bool = False):
         L.lfsgm_depth.argtypes = [vp, vp, vp, vp]
         L.lfsgm_cost_volume_noalloc.argtypes = [P(Config), vp, vp, vp, vp, vp, vp]
         L.lfsgm_batch_create.argtypes = [i32, P(Config), P(vp), P(vp), vp, i32, P(vp)]
+        L.lfsgm_batch_workspace_size.argtypes = [i32, P(Config), i32, P(C.c_size_t)]
+        L.lfsgm_batch_create_ws.argtypes = [i32, P(Config), P(vp), P(vp), vp, i32, vp, C.c_size_t, P(vp)]
         L.lfsgm_batch_run.argtypes = [vp]
         L.lfsgm_batch_times.argtypes = [vp, P(C.c_double), P(C.c_double), P(i32)]
         L.lfsgm_batch_kernel_nodes.argtypes = [vp]
@@ -302,24 +304,47 @@ def _bcheck(st: int, b=None):
         raise LfsgmError(st, (load().lfsgm_batch_last_error(b) or b"").decode())
 
 
-def lfsgm_batch_create(cfgs, views, disp, stream=None, branches=0):
+def _configs(cfgs):
+    n = len(cfgs)
+    return n, (Config * n)(*[c if isinstance(c, Config) else make_config(c) for c in cfgs])
+
+
+def lfsgm_batch_create(cfgs, views, disp, stream=None, branches=0, ws=None):
     """One CUDA graph running the whole depth pipeline of every light field.  ``cfgs``: list of
     Config (or parameter objects); ``views``/``disp``: lists of device float32 tensors
     ([V,U,H,W] and [H*W]) whose addresses are baked into the graph.  ``branches`` <= 0 lets the
-    library time 1, 2, 4, 8, 16 concurrent branches and keep the fastest."""
+    library time 1, 2, 4, 8, 16 concurrent branches and keep the fastest.  ``ws``: an optional
+    caller-owned device buffer (uint8 tensor, lfsgm_batch_workspace_size bytes) for the scratch
+    (lfsgm_batch_create_ws)."""
     import torch
-    n = len(cfgs)
+    n, arr = _configs(cfgs)
     if n < 1 or len(views) != n or len(disp) != n:
         raise ValueError("need equally long, non-empty cfgs, views and disp")
-    arr = (Config * n)(*[c if isinstance(c, Config) else make_config(c) for c in cfgs])
     vptr = (C.c_void_p * n)(*[_ptr(v, torch.float32, "views") for v in views])
     dptr = (C.c_void_p * n)(*[_ptr(d, torch.float32, "disp") for d in disp])
     if stream is None:
         stream = torch.cuda.current_stream()
     b = C.c_void_p()
-    _bcheck(load().lfsgm_batch_create(n, arr, vptr, dptr, C.c_void_p(stream.cuda_stream), int(branches),
-                                      C.byref(b)), None)
+    if ws is None:
+        _bcheck(load().lfsgm_batch_create(n, arr, vptr, dptr, C.c_void_p(stream.cuda_stream), int(branches),
+                                          C.byref(b)), None)
+    else:
+        _bcheck(load().lfsgm_batch_create_ws(n, arr, vptr, dptr, C.c_void_p(stream.cuda_stream), int(branches),
+                                             _ptr(ws, torch.uint8, "ws"), ws.numel(), C.byref(b)), None)
     return b
+
+
+def lfsgm_batch_create_ws(cfgs, views, disp, ws, stream=None, branches=0):
+    """lfsgm_batch_create with the scratch in the caller's buffer ``ws`` (uint8 device tensor)."""
+    return lfsgm_batch_create(cfgs, views, disp, stream, branches, ws=ws)
+
+
+def lfsgm_batch_workspace_size(cfgs, branches=0) -> int:
+    """Bytes of caller-owned scratch a batch of these configurations needs (no device work)."""
+    n, arr = _configs(cfgs)
+    out = C.c_size_t()
+    _bcheck(load().lfsgm_batch_workspace_size(n, arr, int(branches), C.byref(out)), None)
+    return int(out.value)
 
 
 def lfsgm_batch_run(b):
@@ -353,13 +378,14 @@ def lfsgm_batch_destroy(b):
 class LightFieldBatch:
     """Owns the batch graph, the output disparity maps and references to the input views."""
 
-    def __init__(self, params, views, branches=0, stream=None):
+    def __init__(self, params, views, branches=0, stream=None, ws=None):
         import torch
         self.params = list(params)
         self.views = [v.contiguous() for v in views]
         self.disp = [torch.empty(p.H * p.W, dtype=torch.float32, device=v.device)
                      for p, v in zip(self.params, self.views)]
-        self.b = lfsgm_batch_create(self.params, self.views, self.disp, stream, branches)
+        self.ws = ws                  # caller-owned scratch (kept alive with the batch)
+        self.b = lfsgm_batch_create(self.params, self.views, self.disp, stream, branches, ws=ws)
         self.n = len(self.params)
 
     def run(self):

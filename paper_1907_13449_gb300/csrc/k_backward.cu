@@ -144,10 +144,14 @@ __global__ void __launch_bounds__(32 * kBwdWarps) sgm_backward_kernel(
         }
     };
 
-    // forward recompute: branch codes and argmin slots
+    // forward recompute: branch codes and argmin slots.  Narrow steps (this window and the
+    // predecessor's at most 32 labels) keep the predecessor row in registers, one slot per lane,
+    // and take its neighbours by shuffles; wider ones use the rows in shared memory.
     int plo = 0, pn = 0;
     float m = 0.f;
     bool first = true;
+    float prev = INF;                          // predecessor row by slot (narrow form)
+    bool in_smem = false;                      // the predecessor row is in bufA (general form)
     int cw, co, nw = 0, no = 0;
     fetch(0, cw, co, status);
     if (len > 32) fetch(32, nw, no, status);
@@ -165,6 +169,42 @@ __global__ void __launch_bounds__(32 * kBwdWarps) sgm_backward_kernel(
         if (n == 0) {
             first = true;
             continue;
+        }
+        if (n <= 32 && (first || pn <= 32)) {
+            if (!first && in_smem) prev = lane < pn ? bufA[lane] : INF;
+            const float c = lane < n ? __ldg(cost + o + lane) : 0.f;
+            float Lv = c;
+            unsigned cd = 4;
+            if (!first) {
+                // the same candidates in the same order as the general form: P2, same, g-1, g+1
+                const int i = lane + (l - plo);
+                const float v0 = __shfl_sync(0xffffffffu, prev, i & 31);
+                const float vm = __shfl_sync(0xffffffffu, prev, (i - 1) & 31);
+                const float vp = __shfl_sync(0xffffffffu, prev, (i + 1) & 31);
+                float t = m + P2;
+                cd = 3;
+                if ((unsigned)i < (unsigned)pn && v0 < t) { t = v0; cd = 0; }
+                if ((unsigned)(i - 1) < (unsigned)pn && vm + P1 < t) { t = vm + P1; cd = 1; }
+                if ((unsigned)(i + 1) < (unsigned)pn && vp + P1 < t) { t = vp + P1; cd = 2; }
+                Lv = c + (t - m);
+            }
+            if (lane < n) code[o + lane] = (unsigned char)cd;
+            const float bv = lane < n ? Lv : INF;
+            float mv;
+            asm volatile("redux.sync.min.f32 %0, %1, 0xffffffff;" : "=f"(mv) : "f"(bv));
+            const int slot = __reduce_min_sync(0xffffffffu, bv == mv ? (unsigned)lane : 0x7fffffffu);
+            if (lane == 0) am[p] = slot;
+            m = mv;
+            prev = bv;
+            in_smem = false;
+            plo = l;
+            pn = n;
+            first = false;
+            continue;
+        }
+        if (!first && !in_smem) {
+            if (lane < pn) bufA[lane] = prev;
+            __syncwarp();
         }
         float bv = INF;
         int bj = 0x7fffffff;
@@ -207,6 +247,7 @@ __global__ void __launch_bounds__(32 * kBwdWarps) sgm_backward_kernel(
         float *tmp = bufA;
         bufA = bufB;
         bufB = tmp;
+        in_smem = true;
         plo = l;
         pn = n;
         first = false;
@@ -215,7 +256,9 @@ __global__ void __launch_bounds__(32 * kBwdWarps) sgm_backward_kernel(
 
     // reverse sweep (blocks of metadata in descending order; step k-1 is in this block or the one below)
     float gp1 = 0.f, gp2 = 0.f;
-    bool have_inc = false;       // bufA holds the incoming adjoint of the current pixel
+    bool have_inc = false;       // the current pixel has an incoming adjoint (from its successor)
+    bool inc_smem = false;       // ... held in bufA by slot (general form), else in inc, one slot per lane
+    float inc = 0.f;
     {
         const int kb0 = (len - 1) & ~31;
         fetch(kb0, cw, co, nullptr);
@@ -242,6 +285,42 @@ __global__ void __launch_bounds__(32 * kBwdWarps) sgm_backward_kernel(
             q = (int)(p0 + (long long)(k - 1) * dpix);
             ql = wq & 0xffff;
             qn = wq >> 16;
+        }
+        if (n <= 32 && qn <= 32) {
+            // narrow: lambda and the branch code of slot j on lane j; q's incoming adjoint by shuffles
+            const bool act = lane < n;
+            float in_v = 0.f;
+            if (have_inc) in_v = inc_smem ? (act ? bufA[lane] : 0.f) : inc;
+            const float gv = act ? __ldg(gCs + o + lane) : 0.f;
+            const unsigned cd = act ? code[o + lane] : 4u;
+            const float lv = act ? gv + in_v : 0.f;
+            if (act) atomicAdd(gcost + o + lane, lv);
+            if (cd == 1 || cd == 2) gp1 += lv;
+            if (cd == 3) gp2 += lv;
+            const float dm = warp_sum((cd == 3 ? lv : 0.f) - lv);
+            if (q >= 0) {
+                const int qa = am[q];
+                const int j0 = lane + (ql - l), j1 = j0 + 1, j2 = j0 - 1;
+                const float l0 = __shfl_sync(0xffffffffu, lv, j0 & 31), l1 = __shfl_sync(0xffffffffu, lv, j1 & 31);
+                const float l2 = __shfl_sync(0xffffffffu, lv, j2 & 31);
+                const unsigned c0 = __shfl_sync(0xffffffffu, cd, j0 & 31), c1 = __shfl_sync(0xffffffffu, cd, j1 & 31);
+                const unsigned c2 = __shfl_sync(0xffffffffu, cd, j2 & 31);
+                float v = 0.f;
+                if ((unsigned)j0 < (unsigned)n && c0 == 0) v += l0;
+                if ((unsigned)j1 < (unsigned)n && c1 == 1) v += l1;
+                if ((unsigned)j2 < (unsigned)n && c2 == 2) v += l2;
+                if (lane == qa) v += dm;
+                inc = lane < qn ? v : 0.f;
+                inc_smem = false;
+                have_inc = true;
+            } else {
+                have_inc = false;
+            }
+            continue;
+        }
+        if (have_inc && !inc_smem) {
+            if (lane < n) bufA[lane] = inc;
+            __syncwarp();
         }
         float dm = 0.f;
         for (int j0 = lane; j0 < n; j0 += 256) {
@@ -290,6 +369,7 @@ __global__ void __launch_bounds__(32 * kBwdWarps) sgm_backward_kernel(
             bufA = bufB;
             bufB = tmp;
             have_inc = true;
+            inc_smem = true;
         } else {
             have_inc = false;
         }
@@ -411,128 +491,156 @@ __global__ void __launch_bounds__(256) views_backward_kernel(const float *__rest
     }
 }
 
-// Narrow windows (cnt <= 32) by tiles of 32 x 8 pixels, one warp per row and a lane per pixel:
-// for every view the lanes walk their windows, sum the tap gradients in registers while the
-// bilinear cell stays the same, and add them into a shared-memory box covering the tile's tap
-// footprint (the tile's label range [gmin, gmax] fixes it: the integer shift is monotone in the
-// label); the box is then added to the view with one atomic per non-zero element.  Taps outside
-// the box (a tile whose label range is too wide for it) go to global memory directly.
-constexpr int kVbRows = 8, kVbBoxW = 96, kVbBoxH = 24;
+// Narrow windows by rows, as the forward's row kernel: a CTA of kVrWarps warps covers kVrWarps
+// consecutive rows of one 32-pixel column, a warp one row (lane = pixel) and the KVR-label range
+// [g0, g0 + KVR) that holds the most of its windows; the windows outside it go to the item list.
+// For a view, the range splits into segments where the bilinear cell (integer shift) changes;
+// inside a segment of labels t = 0, 1, ... the fractional shift is fx + ax t, fy + ay t, so
+//   - the sample minus I_ref is the quadratic a0 + b0 t + Cq t^2 (from the cell's four taps), and
+//     its sign gives g(t) = dLoss/dC * w_l2 * sign(I_ref - sample) for the reference pixel;
+//   - a corner's tap gradient -sum_t g(t) w_corner(t) is a combination of the moments sum g,
+//     sum g t, sum g t^2 (the corner weights are products of fx + ax t and fy + ay t),
+// so a lane adds three moments per label and converts them into four tap gradients once per
+// segment.  The tap gradients of the CTA go into one shared-memory box over its tap footprint,
+// added to the view with one global atomic per non-zero element once the view is done.  Taps
+// outside the box (clamped at the image border, or a label range too wide for it) go to global
+// memory directly.
+constexpr int kVrWarps = 8, KVR = 36, kVrBoxW = 96, kVrBoxH = 24;
 
-__global__ void __launch_bounds__(32 * kVbRows) views_backward_tile_kernel(
-    const float *__restrict__ views, const FineTap *__restrict__ tab, int G, int nviews, int H, int W, int ref,
+__global__ void __launch_bounds__(32 * kVrWarps) views_backward_rows_kernel(
+    const float *__restrict__ views, const FineTap *__restrict__ tab, int G, int U, int V, int H, int W, int ref,
     const int *__restrict__ lo, const int *__restrict__ cnt, const long long *__restrict__ off, float wl2,
-    const float *__restrict__ gcost, float *__restrict__ gviews) {
-    __shared__ float box[kVbBoxH * kVbBoxW];
-    __shared__ float gcs[kVbRows][32][32];        // [row][label][lane]
-    __shared__ int red[2][kVbRows];
+    float fstep, const float *__restrict__ gcost, float *__restrict__ gviews, int2 *__restrict__ list,
+    int *__restrict__ list_count) {
+    __shared__ float box[kVrBoxH * kVrBoxW];
+    __shared__ float gcs[kVrWarps][KVR][32];       // [row][label of the range][lane]
+    __shared__ int red[2][kVrWarps];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    const int x0 = blockIdx.x * 32, ty0 = blockIdx.y * kVbRows;
+    const int x0 = blockIdx.x * 32, ty0 = blockIdx.y * kVrWarps;
     const int x = x0 + lane, y = ty0 + w;
     const size_t N = (size_t)H * W;
-    bool act = false;
+    const int nviews = U * V;
     int l = 0, n = 0;
-    size_t p = 0;
+    long long o = 0;
+    bool nar = false;
     if (x < W && y < H) {
-        p = (size_t)y * W + x;
+        const size_t p = (size_t)y * W + x;
         l = __ldg(lo + p);
         n = __ldg(cnt + p);
-        const long long o = __ldg(off + p);
-        act = n <= 32 && window_ok(l, n, G, __ldg(off + p + 1) - o, nullptr);
-        for (int j = 0; j < 32; j++) gcs[w][j][lane] = (act && j < n) ? wl2 * __ldg(gcost + o + j) : 0.f;
-    } else {
-        for (int j = 0; j < 32; j++) gcs[w][j][lane] = 0.f;
+        o = __ldg(off + p);
+        nar = n <= 32 && window_ok(l, n, G, __ldg(off + p + 1) - o, nullptr);
     }
-    int gmn = act ? l : 0x7fffffff, gmx = act ? l + n - 1 : -1;
-    for (int o = 16; o > 0; o >>= 1) {
-        gmn = min(gmn, __shfl_xor_sync(0xffffffffu, gmn, o));
-        gmx = max(gmx, __shfl_xor_sync(0xffffffffu, gmx, o));
+    int g0;
+    const int best = row_range<KVR>(l, n, nar, g0);  // warp-uniform (rows past H: no window, -1)
+    const bool fits = best > 0 && nar && l >= g0 && l + n <= g0 + KVR;
+    if (nar && !fits) push_chunks(list, list_count, y * W + x, n);
+#pragma unroll 4
+    for (int j = 0; j < KVR; j++) {
+        const int k = g0 + j - l;
+        gcs[w][j][lane] = (fits && k >= 0 && k < n) ? wl2 * __ldg(gcost + o + k) : 0.f;
     }
     if (lane == 0) {
-        red[0][w] = gmn;
-        red[1][w] = gmx;
+        red[0][w] = best > 0 ? g0 : 0x7fffffff;
+        red[1][w] = best > 0 ? min(g0 + KVR - 1, G - 1) : -1;
     }
-    for (int e = threadIdx.x; e < kVbBoxH * kVbBoxW; e += blockDim.x) box[e] = 0.f;
+    for (int e = threadIdx.x; e < kVrBoxH * kVrBoxW; e += blockDim.x) box[e] = 0.f;
     __syncthreads();
-    gmn = red[0][0];
-    gmx = red[1][0];
-    for (int k = 1; k < kVbRows; k++) {
+    int gmn = red[0][0], gmx = red[1][0];
+    for (int k = 1; k < kVrWarps; k++) {
         gmn = min(gmn, red[0][k]);
         gmx = max(gmx, red[1][k]);
     }
-    if (gmx < 0) return;                               // no narrow window in the tile (uniform)
-    const float Iref = act ? __ldg(views + (size_t)ref * N + p) : 0.f;
+    if (gmx < 0) return;                               // no range in the CTA (uniform)
+    const bool any = best > 0;                         // warp-uniform
+    const float Iref = fits ? __ldg(views + (size_t)ref * N + (size_t)y * W + x) : 0.f;
     float gref = 0.f;
-    for (int vi = 0; vi < nviews - 1; vi++) {
-        const int view = vi + (vi >= ref);
+    for (int view = 0; view < nviews; view++) {
+        if (view == ref) continue;
+        const float ax = (float)(view % U - (ref % U)) * fstep, ay = (float)(view / U - (ref / U)) * fstep;
         const FineTap ta = load_tap(tab + (size_t)view * G + gmn), tb = load_tap(tab + (size_t)view * G + gmx);
         const int bx0 = x0 + min(ta.ox, tb.ox), by0 = ty0 + min(ta.oy, tb.oy);
-        const int bw = 32 + abs(tb.ox - ta.ox) + 1, bh = kVbRows + abs(tb.oy - ta.oy) + 1;
-        const bool use_box = bw <= kVbBoxW && bh <= kVbBoxH;
+        const int bw = 32 + abs(tb.ox - ta.ox) + 1, bh = kVrWarps + abs(tb.oy - ta.oy) + 1;
+        const bool use_box = bw <= kVrBoxW && bh <= kVrBoxH;
         const float *I = views + (size_t)view * N;
         float *gI = gviews + (size_t)view * N;
         auto add = [&](int xc, int yc, float v) {
             if (v == 0.f) return;
             const int bx = xc - bx0, by = yc - by0;
             if (use_box && (unsigned)bx < (unsigned)bw && (unsigned)by < (unsigned)bh)
-                atomicAdd(&box[by * kVbBoxW + bx], v);
+                atomicAdd(&box[by * kVrBoxW + bx], v);
             else
                 atomicAdd(gI + (size_t)yc * W + xc, v);
         };
-        if (act) {
-            int cx = 0x7fffffff, cy = 0, xa = 0, xb = 0, ya = 0, yb = 0;
-            float a00 = 0.f, a10 = 0.f, a01 = 0.f, a11 = 0.f;
-            const FineTap *tt = tab + (size_t)view * G + l;
-            for (int j = 0; j < n; j++) {
-                const FineTap t = load_tap(tt + j);
-                if (t.ox != cx || t.oy != cy) {
-                    if (cx != 0x7fffffff) {
-                        add(xa, ya, a00);
-                        add(xb, ya, a10);
-                        add(xa, yb, a01);
-                        add(xb, yb, a11);
+        if (any) {
+            // the range's labels: lane j holds label g0 + j, lanes 0 .. KVR-33 also label g0 + 32 + lane
+            const FineTap t0 = load_tap(tab + (size_t)view * G + min(g0 + lane, G - 1));
+            FineTap t1 = t0;
+            if (lane < KVR - 32) t1 = load_tap(tab + (size_t)view * G + min(g0 + 32 + lane, G - 1));
+            const int c0 = (int)t0.ox * 65536 + (int)t0.oy, c1 = (int)t1.ox * 65536 + (int)t1.oy;
+            const int p0 = __shfl_up_sync(0xffffffffu, c0, 1), p1 = __shfl_up_sync(0xffffffffu, c1, 1);
+            const int c31 = __shfl_sync(0xffffffffu, c0, 31);
+            const unsigned m0 = __ballot_sync(0xffffffffu, lane == 0 || c0 != p0);
+            const unsigned m1 = __ballot_sync(0xffffffffu, lane < KVR - 32 && (lane == 0 ? c1 != c31 : c1 != p1));
+            // segments of the range in label order
+            int js = 0;
+            while (js < KVR) {
+                const int nx = js + 1;
+                const unsigned r0 = nx < 32 ? (m0 & (0xffffffffu << nx)) : 0u;
+                const unsigned r1 = nx < 32 ? m1 : (m1 & (0xffffffffu << (nx - 32)));
+                const int je = r0 ? __ffs(r0) - 1 : (r1 ? 32 + __ffs(r1) - 1 : KVR);
+                // the segment's cell and fractions (label js, from the lane that holds it)
+                const int src = js & 31;
+                const bool hi = js >= 32;
+                const int ox = __shfl_sync(0xffffffffu, hi ? t1.ox : t0.ox, src);
+                const int oy = __shfl_sync(0xffffffffu, hi ? t1.oy : t0.oy, src);
+                const float fx = __shfl_sync(0xffffffffu, hi ? t1.fx : t0.fx, src);
+                const float fy = __shfl_sync(0xffffffffu, hi ? t1.fy : t0.fy, src);
+                const int xa = min(max(x + ox, 0), W - 1), xb = min(max(x + ox + 1, 0), W - 1);
+                const int ya = min(max(y + oy, 0), H - 1), yb = min(max(y + oy + 1, 0), H - 1);
+                float S0 = 0.f, S1 = 0.f, S2 = 0.f;
+                if (fits) {
+                    const float i00 = __ldg(I + (size_t)ya * W + xa), i10 = __ldg(I + (size_t)ya * W + xb);
+                    const float i01 = __ldg(I + (size_t)yb * W + xa), i11 = __ldg(I + (size_t)yb * W + xb);
+                    const float cx = i10 - i00, cy = i01 - i00, cxy = (i11 - i01) - cx;
+                    const float a0 = fmaf(cxy * fx, fy, fmaf(cy, fy, fmaf(cx, fx, i00 - Iref)));
+                    const float b0 = fmaf(cxy, fmaf(fx, ay, fy * ax), fmaf(cy, ay, cx * ax));
+                    const float cq = cxy * ax * ay;
+                    float t = 0.f;
+                    for (int j = js; j < je; j++, t += 1.f) {
+                        const float gc = gcs[w][j][lane];
+                        const float e = fmaf(t, fmaf(t, cq, b0), a0);        // sample - I_ref
+                        const float g = e < 0.f ? gc : (e > 0.f ? -gc : 0.f);
+                        const float gt = g * t;
+                        S0 += g;
+                        S1 += gt;
+                        S2 = fmaf(gt, t, S2);
                     }
-                    cx = t.ox;
-                    cy = t.oy;
-                    xa = min(max(x + cx, 0), W - 1);
-                    xb = min(max(x + cx + 1, 0), W - 1);
-                    ya = min(max(y + cy, 0), H - 1);
-                    yb = min(max(y + cy + 1, 0), H - 1);
-                    a00 = a10 = a01 = a11 = 0.f;
+                    gref += S0;
+                    // -sum g w for the corners: w11 = XY, w10 = X (1 - Y), w01 = (1 - X) Y, w00 = (1 - X)(1 - Y)
+                    const float GX = fmaf(ax, S1, fx * S0), GY = fmaf(ay, S1, fy * S0);
+                    const float GXY = fmaf(ax * ay, S2, fmaf(fmaf(fx, ay, fy * ax), S1, fx * fy * S0));
+                    add(xa, ya, -(S0 - GX - GY + GXY));
+                    add(xb, ya, -(GX - GXY));
+                    add(xa, yb, -(GY - GXY));
+                    add(xb, yb, -GXY);
                 }
-                const float gc = gcs[w][j][lane];
-                if (gc == 0.f) continue;
-                const float top = (1.f - t.fx) * __ldg(I + (size_t)ya * W + xa) + t.fx * __ldg(I + (size_t)ya * W + xb);
-                const float bot = (1.f - t.fx) * __ldg(I + (size_t)yb * W + xa) + t.fx * __ldg(I + (size_t)yb * W + xb);
-                const float d = Iref - ((1.f - t.fy) * top + t.fy * bot);
-                const float g = d > 0.f ? gc : (d < 0.f ? -gc : 0.f);
-                gref += g;
-                a00 -= g * (1.f - t.fy) * (1.f - t.fx);
-                a10 -= g * (1.f - t.fy) * t.fx;
-                a01 -= g * t.fy * (1.f - t.fx);
-                a11 -= g * t.fy * t.fx;
-            }
-            if (cx != 0x7fffffff) {
-                add(xa, ya, a00);
-                add(xb, ya, a10);
-                add(xa, yb, a01);
-                add(xb, yb, a11);
+                js = je;
             }
         }
         __syncthreads();
         if (use_box) {
             for (int e = threadIdx.x; e < bw * bh; e += blockDim.x) {
                 const int by = e / bw, bx = e - by * bw;
-                const float v = box[by * kVbBoxW + bx];
+                const float v = box[by * kVrBoxW + bx];
                 if (v != 0.f) {
                     atomicAdd(gI + (size_t)(by0 + by) * W + (bx0 + bx), v);
-                    box[by * kVbBoxW + bx] = 0.f;
+                    box[by * kVrBoxW + bx] = 0.f;
                 }
             }
         }
         __syncthreads();
     }
-    if (act && gref != 0.f) atomicAdd(gviews + (size_t)ref * N + p, gref);
+    if (fits && gref != 0.f) atomicAdd(gviews + (size_t)ref * N + (size_t)y * W + x, gref);
 }
 
 }  // namespace
@@ -562,9 +670,10 @@ cudaError_t launch_sgm_backward(cudaStream_t s, const float *cost, const int *lo
     return cudaGetLastError();
 }
 
-cudaError_t launch_views_backward(cudaStream_t s, const float *views, const FineTap *tab, int G, int nviews, int C,
+cudaError_t launch_views_backward(cudaStream_t s, const float *views, const FineTap *tab, int G, int U, int V, int C,
                                   int H, int W, int ref, const int *lo, const int *cnt, const long long *off,
-                                  float wl2, const float *gcost, float *gviews, const int2 *list, const int *count) {
+                                  float wl2, float fstep, const float *gcost, float *gviews, int2 *list, int *count) {
+    const int nviews = U * V;
     int dev = 0, sms = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
@@ -574,12 +683,20 @@ cudaError_t launch_views_backward(cudaStream_t s, const float *views, const Fine
                                                          gviews, list, count);
         return cudaGetLastError();
     }
-    dim3 grid((W + 31) / 32, (H + kVbRows - 1) / kVbRows);
-    views_backward_tile_kernel<<<grid, 32 * kVbRows, 0, s>>>(views, tab, G, nviews, H, W, ref, lo, cnt, off, wl2, gcost,
-                                                             gviews);
-    cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess) return e;
-    // windows wider than 32 labels (the list holds their chunks)
+    dim3 grid((W + 31) / 32, (H + kVrWarps - 1) / kVrWarps);
+    views_backward_rows_kernel<<<grid, 32 * kVrWarps, 0, s>>>(views, tab, G, U, V, H, W, ref, lo, cnt, off, wl2,
+                                                              fstep, gcost, gviews, list, count);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_views_backward_list(cudaStream_t s, const float *views, const FineTap *tab, int G, int nviews,
+                                       int H, int W, int ref, const int *lo, const int *cnt, const long long *off,
+                                       float wl2, const float *gcost, float *gviews, const int2 *list,
+                                       const int *count) {
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    // windows wider than 32 labels and narrow ones outside their row's range (the list holds their chunks)
     views_backward_kernel<1><<<sms * 8, 256, 0, s>>>(views, tab, G, nviews, H, W, ref, lo, cnt, off, wl2, gcost, gviews,
                                                      list, count);
     return cudaGetLastError();

@@ -138,14 +138,6 @@ __device__ __forceinline__ bool mbar_wait(unsigned mbar, unsigned parity) {
     return false;
 }
 
-// Append (pixel, chunk of 32 labels) work items for a window of n labels (rounded up to whole
-// 4-slot groups, which the list kernel pads with zeros).
-__device__ __forceinline__ void push_chunks(int2 *list, int *count, int p, int n) {
-    const int nch = (n + 31) >> 5;
-    const int k = atomicAdd(count, nch);
-    for (int c = 0; c < nch; c++) list[k + c] = make_int2(p, c);
-}
-
 template <int KW>
 __global__ void __launch_bounds__(128, 5) fine_cost_rows(const __grid_constant__ CUtensorMap tm_v,
                                                          const __grid_constant__ CUtensorMap tm_c,
@@ -187,16 +179,8 @@ __global__ void __launch_bounds__(128, 5) fine_cost_rows(const __grid_constant__
         }
     }
     // the label range covering the most windows (ties: the lowest start); the others go to the list
-    int g0 = 0, best_fit = -1;
-    for (int c = 0; c < 32; c++) {
-        const int cl = __shfl_sync(0xffffffffu, l, c);
-        if (!__shfl_sync(0xffffffffu, nar, c)) continue;
-        const int fit = __popc(__ballot_sync(0xffffffffu, nar && l >= cl && l + n <= cl + KW));
-        if (fit > best_fit || (fit == best_fit && cl < g0)) {
-            best_fit = fit;
-            g0 = cl;
-        }
-    }
+    int g0;
+    const int best_fit = row_range<KW>(l, n, nar, g0);
     if (best_fit <= 0) return;
     const bool fits = nar && l >= g0 && l + n <= g0 + KW;
     if (nar && !fits) push_chunks(list, list_count, y * W + x, n);

@@ -279,14 +279,12 @@ lfsgm_status bind_workspace(lfsgm_ctx *h, void *dptr, size_t bytes, bool owned) 
     if (e != cudaSuccess) return cuda_fail(h, e, "status clear");
     return LFSGM_OK;
 }
-}  // namespace
 
-extern "C" {
-
-lfsgm_status lfsgm_create(const lfsgm_config *cfg, void *stream, lfsgm_handle *out) {
-    if (!cfg || !out) return LFSGM_ERR_INVALID_ARG;
-    *out = nullptr;
-    lfsgm_config c = *cfg;
+// The host-side part of handle creation: defaults, validation and every size the workspace layout
+// depends on (no device memory, no tables).  lfsgm_create continues from here; the batch workspace
+// query uses it alone.
+lfsgm_status plan_handle(const lfsgm_config &cin, lfsgm_ctx *h) {
+    lfsgm_config c = cin;
     if (c.paths == 0) c.paths = 8;
     if (c.channels == 0) c.channels = 1;
     if (c.uc < 0) c.uc = (c.U - 1) / 2;
@@ -296,9 +294,7 @@ lfsgm_status lfsgm_create(const lfsgm_config *cfg, void *stream, lfsgm_handle *o
         g_create_err = why;
         return LFSGM_ERR_INVALID_ARG;
     }
-    lfsgm_ctx *h = new lfsgm_ctx();
     h->cfg = c;
-    h->stream = (cudaStream_t)stream;
     h->N = c.H * c.W;
     h->nviews = c.U * c.V;
     h->C = c.channels;
@@ -313,9 +309,27 @@ lfsgm_status lfsgm_create(const lfsgm_config *cfg, void *stream, lfsgm_handle *o
     const long long p2max = (long long)std::floor(c.p2_frac * (double)cmax + 0.5);
     if (!c.boundless && (long long)c.paths * (cmax + std::max(p2max, 1LL)) >= 65536) {
         g_create_err = "coarse path sums would overflow 16 bits (too many arm views x census bits)";
-        delete h;
         return LFSGM_ERR_UNSUPPORTED;
     }
+    return LFSGM_OK;
+}
+}  // namespace
+
+extern "C" {
+
+lfsgm_status lfsgm_create(const lfsgm_config *cfg, void *stream, lfsgm_handle *out) {
+    if (!cfg || !out) return LFSGM_ERR_INVALID_ARG;
+    *out = nullptr;
+    lfsgm_ctx *h = new lfsgm_ctx();
+    {
+        const lfsgm_status st = plan_handle(*cfg, h);
+        if (st != LFSGM_OK) {
+            delete h;
+            return st;
+        }
+    }
+    const lfsgm_config &c = h->cfg;
+    h->stream = (cudaStream_t)stream;
     // shift tables in double precision
     std::vector<FineTap> fine((size_t)h->nviews * c.fine_labels);
     std::vector<short2> coarse((size_t)h->nviews * c.coarse_labels);
@@ -714,9 +728,15 @@ lfsgm_status lfsgm_backward(lfsgm_handle h, const float *views, const float *cos
                                    h->C > 1 ? 0 : 32);
         }));
         LFSGM_TRY(run(h, "views_backward", [&] {
-            return launch_views_backward(s, views, h->d_fine, c.fine_labels, h->nviews, h->C, c.H, c.W, h->ref, lo,
-                                         cnt, o, c.w_l2, grad_cost, grad_views, h->wide_list, h->wide_count);
+            return launch_views_backward(s, views, h->d_fine, c.fine_labels, c.U, c.V, h->C, c.H, c.W, h->ref, lo,
+                                         cnt, o, c.w_l2, (float)((c.dmax - c.dmin) / (double)(c.fine_labels - 1)),
+                                         grad_cost, grad_views, h->wide_list, h->wide_count);
         }));
+        if (h->C == 1)
+            LFSGM_TRY(run(h, "views_backward_list", [&] {
+                return launch_views_backward_list(s, views, h->d_fine, c.fine_labels, h->nviews, c.H, c.W, h->ref, lo,
+                                                  cnt, o, c.w_l2, grad_cost, grad_views, h->wide_list, h->wide_count);
+            }));
     }
     e = cudaMemcpyAsync(grad_P1, h->b_gp, 4, cudaMemcpyDeviceToDevice, s);
     if (e == cudaSuccess) e = cudaMemcpyAsync(grad_P2, h->b_gp + 1, 4, cudaMemcpyDeviceToDevice, s);
@@ -873,7 +893,8 @@ lfsgm_status lfsgm_depth_host(lfsgm_handle h, const float *views_host, float *di
 // batch -- every stage of every light field plus a %globaltimer stamp before and after each light
 // field -- is captured once into a CUDA graph, so a batch is one graph launch.  Branch count and
 // assignment come from a small autotuner: longest-job-first assignment for each candidate K in
-// {1, 2, 4, 8, 16}, each timed on the device, the fastest kept (or K given by the caller).
+// {1, 2, 4, 8, 16} (each branch then runs its light fields shortest first), each timed on the
+// device, the fastest kept (or K given by the caller).
 
 namespace {
 
@@ -891,6 +912,64 @@ struct BranchBufs {
     float *cost = nullptr, *agg = nullptr;
 };
 
+// Longest-job-first assignment of work items to K branches (each to the least-loaded branch), then
+// each branch's items shortest first: the branch's total time is the same, and more light fields
+// complete early (lower median completion time).
+std::vector<std::vector<int>> batch_assign(const std::vector<double> &work, int K) {
+    const int n = (int)work.size();
+    std::vector<std::vector<int>> plan(K);
+    std::vector<int> idx(n);
+    for (int i = 0; i < n; i++) idx[i] = i;
+    std::stable_sort(idx.begin(), idx.end(), [&](int a, int c) { return work[a] > work[c]; });
+    std::vector<double> load(K, 0.0);
+    for (int i : idx) {
+        const int k = (int)(std::min_element(load.begin(), load.end()) - load.begin());
+        plan[k].push_back(i);
+        load[k] += work[i];
+    }
+    for (auto &pl : plan) std::stable_sort(pl.begin(), pl.end(), [&](int a, int c) { return work[a] < work[c]; });
+    return plan;
+}
+
+// Sizes that the scratch of a batch branch depends on, per light field.
+struct LfSizes {
+    size_t ws = 0, N = 0;
+    int64_t nnz = 0;
+    double work = 0.0;
+};
+
+LfSizes lf_sizes(lfsgm_ctx *h) {
+    LfSizes z;
+    lfsgm_workspace_size(h, &z.ws);
+    lfsgm_max_nnz(h, &z.nnz);
+    z.N = (size_t)h->N;
+    const lfsgm_config &c = h->cfg;
+    z.work = (double)h->N * ((double)h->nviews * h->C * (2 * c.fine_radius + 1) + 4.0 * c.coarse_labels);
+    return z;
+}
+
+// Bytes of one branch's scratch (workspace, window map, labels, cost and aggregate), and of the
+// %globaltimer stamps of n light fields; every piece starts on a 256-byte boundary.
+size_t branch_bytes(size_t ws, size_t N, int64_t nnz) {
+    return align256(ws) + 3 * align256(N * 4) + align256((N + 1) * 8) + 2 * align256((size_t)nnz * 4);
+}
+size_t stamp_bytes(int n) { return align256((1 + 2 * (size_t)n) * 8); }
+
+size_t batch_bytes(const std::vector<LfSizes> &z, const std::vector<std::vector<int>> &plan) {
+    size_t total = stamp_bytes((int)z.size());
+    for (const auto &pl : plan) {
+        size_t ws = 0, N = 0;
+        int64_t nnz = 0;
+        for (int i : pl) {
+            ws = std::max(ws, z[i].ws);
+            N = std::max(N, z[i].N);
+            nnz = std::max(nnz, z[i].nnz);
+        }
+        if (!pl.empty()) total += branch_bytes(ws, N, nnz);
+    }
+    return total;
+}
+
 }  // namespace
 
 struct lfsgm_batch_ctx {
@@ -899,6 +978,10 @@ struct lfsgm_batch_ctx {
     std::vector<const float *> views;
     std::vector<float *> disp;
     std::vector<double> work;           // work estimate per light field (scheduling)
+    std::vector<LfSizes> sizes;         // scratch sizes per light field
+    void *ext = nullptr;                // caller-owned scratch (lfsgm_batch_create_ws), else null
+    size_t ext_bytes = 0;
+    void *own = nullptr;                // the library's allocation of the branches' scratch
     cudaStream_t main = nullptr;       // the caller's stream: graph launches go here
     cudaStream_t cap = nullptr;        // private stream the graph is captured from
     int branches = 0;
@@ -931,10 +1014,8 @@ void batch_release_plan(lfsgm_batch_ctx *b) {
     if (b->graph) cudaGraphDestroy(b->graph);
     b->exec = nullptr;
     b->graph = nullptr;
-    for (auto &x : b->bb) {
-        cudaFree(x.ws);
-        cudaFree(x.lo); cudaFree(x.cnt); cudaFree(x.label); cudaFree(x.off); cudaFree(x.cost); cudaFree(x.agg);
-    }
+    if (b->own) cudaFree(b->own);
+    b->own = nullptr;
     b->bb.clear();
     for (auto s : b->bs) cudaStreamDestroy(s);
     for (auto e : b->join) cudaEventDestroy(e);
@@ -946,20 +1027,25 @@ void batch_release_plan(lfsgm_batch_ctx *b) {
     }
 }
 
-// Longest-job-first assignment of the light fields to K branches, then buffers, streams and graph.
+// Assignment of the light fields to K branches, then buffers (caller-owned or one allocation),
+// streams and graph.
 lfsgm_status batch_build(lfsgm_batch_ctx *b, int K) {
     batch_release_plan(b);
     b->branches = K;
-    b->plan.assign(K, {});
-    std::vector<int> idx(b->n);
-    for (int i = 0; i < b->n; i++) idx[i] = i;
-    std::sort(idx.begin(), idx.end(), [&](int a, int c) { return b->work[a] > b->work[c]; });
-    std::vector<double> load(K, 0.0);
-    for (int i : idx) {
-        const int k = (int)(std::min_element(load.begin(), load.end()) - load.begin());
-        b->plan[k].push_back(i);
-        load[k] += b->work[i];
+    b->plan = batch_assign(b->work, K);
+    const size_t total = batch_bytes(b->sizes, b->plan);
+    char *base = nullptr;
+    if (b->ext) {
+        if (total > b->ext_bytes)
+            return bfail(b, LFSGM_ERR_WORKSPACE, "batch workspace of %zu bytes is too small: %d branches need %zu",
+                         b->ext_bytes, K, total);
+        base = (char *)b->ext + stamp_bytes(b->n);      // the stamps sit at the start
+    } else {
+        const cudaError_t e = cudaMalloc(&b->own, total - stamp_bytes(b->n));
+        if (e != cudaSuccess) return bfail(b, LFSGM_ERR_NO_MEMORY, "batch buffers: %s", cudaGetErrorString(e));
+        base = (char *)b->own;
     }
+    auto take = [&](size_t n) { char *q = base; base += align256(n); return (void *)q; };
     b->bb.assign(K, BranchBufs());
     b->bs.assign(K, nullptr);
     b->join.assign(K, nullptr);
@@ -967,25 +1053,22 @@ lfsgm_status batch_build(lfsgm_batch_ctx *b, int K) {
         size_t ws = 0, N = 0;
         int64_t nnz = 0;
         for (int i : b->plan[k]) {
-            size_t w = 0;
-            lfsgm_workspace_size(b->h[i], &w);
-            int64_t m = 0;
-            lfsgm_max_nnz(b->h[i], &m);
-            ws = std::max(ws, w);
-            N = std::max(N, (size_t)b->h[i]->N);
-            nnz = std::max(nnz, m);
+            ws = std::max(ws, b->sizes[i].ws);
+            N = std::max(N, b->sizes[i].N);
+            nnz = std::max(nnz, b->sizes[i].nnz);
         }
         BranchBufs &x = b->bb[k];
         cudaError_t e = cudaStreamCreateWithFlags(&b->bs[k], cudaStreamNonBlocking);
         if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->join[k], cudaEventDisableTiming);
-        if (ws > 0 && e == cudaSuccess) e = cudaMalloc(&x.ws, ws);
-        if (N > 0 && e == cudaSuccess) e = cudaMalloc((void **)&x.lo, N * 4);
-        if (N > 0 && e == cudaSuccess) e = cudaMalloc((void **)&x.cnt, N * 4);
-        if (N > 0 && e == cudaSuccess) e = cudaMalloc((void **)&x.label, N * 4);
-        if (N > 0 && e == cudaSuccess) e = cudaMalloc((void **)&x.off, (N + 1) * 8);
-        if (nnz > 0 && e == cudaSuccess) e = cudaMalloc((void **)&x.cost, (size_t)nnz * 4);
-        if (nnz > 0 && e == cudaSuccess) e = cudaMalloc((void **)&x.agg, (size_t)nnz * 4);
-        if (e != cudaSuccess) return bfail(b, LFSGM_ERR_NO_MEMORY, "batch buffers: %s", cudaGetErrorString(e));
+        if (e != cudaSuccess) return bfail(b, LFSGM_ERR_CUDA, "batch streams: %s", cudaGetErrorString(e));
+        if (b->plan[k].empty()) continue;
+        x.ws = take(ws);
+        x.lo = (int *)take(N * 4);
+        x.cnt = (int *)take(N * 4);
+        x.label = (int *)take(N * 4);
+        x.off = (long long *)take((N + 1) * 8);
+        x.cost = (float *)take((size_t)nnz * 4);
+        x.agg = (float *)take((size_t)nnz * 4);
         x.ws_bytes = ws;
         for (int i : b->plan[k]) {
             b->h[i]->stream = b->bs[k];
@@ -1064,14 +1147,26 @@ float batch_time_ms(lfsgm_batch_ctx *b, int reps) {
 
 extern "C" {
 
-lfsgm_status lfsgm_batch_create(int32_t n, const lfsgm_config *cfgs, const float *const *views, float *const *disp,
-                                void *stream, int32_t branches, lfsgm_batch *out) {
+}  // extern "C"
+
+namespace {
+
+const int kBatchK[] = {1, 2, 4, 8, 16};
+
+lfsgm_status batch_create(int32_t n, const lfsgm_config *cfgs, const float *const *views, float *const *disp,
+                          void *stream, int32_t branches, void *ws, size_t ws_bytes, lfsgm_batch *out) {
     if (!out) return LFSGM_ERR_INVALID_ARG;
     *out = nullptr;
     if (n < 1 || !cfgs || !views || !disp) return LFSGM_ERR_INVALID_ARG;
+    if (ws && ((uintptr_t)ws & 255)) {
+        g_create_err = "batch workspace must be 256-byte aligned";
+        return LFSGM_ERR_WORKSPACE;
+    }
     lfsgm_batch_ctx *b = new lfsgm_batch_ctx();
     b->n = n;
     b->main = (cudaStream_t)stream;
+    b->ext = ws;
+    b->ext_bytes = ws ? ws_bytes : 0;
     for (int i = 0; i < n; i++) {
         if (!views[i] || !disp[i]) {
             g_create_err = "null views or disp pointer";
@@ -1088,10 +1183,12 @@ lfsgm_status lfsgm_batch_create(int32_t n, const lfsgm_config *cfgs, const float
         b->h.push_back(h);
         b->views.push_back(views[i]);
         b->disp.push_back(disp[i]);
-        const lfsgm_config &c = h->cfg;
-        b->work.push_back((double)h->N * ((double)h->nviews * h->C * (2 * c.fine_radius + 1) + 4.0 * c.coarse_labels));
+        b->sizes.push_back(lf_sizes(h));
+        b->work.push_back(b->sizes.back().work);
     }
-    cudaError_t e = cudaMalloc((void **)&b->stamps, (1 + 2 * (size_t)n) * 8);
+    cudaError_t e = cudaSuccess;
+    if (b->ext) b->stamps = (unsigned long long *)b->ext;
+    else e = cudaMalloc((void **)&b->stamps, stamp_bytes(n));
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaMemset(b->stamps, 0, (1 + 2 * (size_t)n) * 8);
@@ -1100,14 +1197,16 @@ lfsgm_status lfsgm_batch_create(int32_t n, const lfsgm_config *cfgs, const float
         lfsgm_batch_destroy(b);
         return LFSGM_ERR_CUDA;
     }
-    lfsgm_status st;
+    lfsgm_status st = LFSGM_OK;
     if (branches > 0) {
         st = batch_build(b, std::min(branches, n));
     } else {
-        int bestK = 1;
+        // autotune K (with a caller workspace: the K whose scratch fits it)
+        int bestK = 0;
         float best = 1e30f;
-        for (int K : {1, 2, 4, 8, 16}) {
+        for (int K : kBatchK) {
             if (K > n) break;
+            if (b->ext && batch_bytes(b->sizes, batch_assign(b->work, K)) > b->ext_bytes) continue;
             st = batch_build(b, K);
             if (st != LFSGM_OK) break;
             batch_time_ms(b, 1);                      // warm-up
@@ -1117,7 +1216,10 @@ lfsgm_status lfsgm_batch_create(int32_t n, const lfsgm_config *cfgs, const float
                 bestK = K;
             }
         }
-        st = batch_build(b, bestK);
+        if (st == LFSGM_OK && bestK == 0)
+            st = bfail(b, LFSGM_ERR_WORKSPACE, "batch workspace of %zu bytes is too small for one branch",
+                       b->ext_bytes);
+        if (st == LFSGM_OK) st = batch_build(b, bestK);
     }
     if (st != LFSGM_OK) {
         g_create_err = b->err;
@@ -1126,6 +1228,51 @@ lfsgm_status lfsgm_batch_create(int32_t n, const lfsgm_config *cfgs, const float
     }
     *out = b;
     return LFSGM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+lfsgm_status lfsgm_batch_create(int32_t n, const lfsgm_config *cfgs, const float *const *views, float *const *disp,
+                                void *stream, int32_t branches, lfsgm_batch *out) {
+    return batch_create(n, cfgs, views, disp, stream, branches, nullptr, 0, out);
+}
+
+lfsgm_status lfsgm_batch_workspace_size(int32_t n, const lfsgm_config *cfgs, int32_t branches, size_t *bytes) {
+    if (!bytes || n < 1 || !cfgs) return LFSGM_ERR_INVALID_ARG;
+    std::vector<LfSizes> z;
+    std::vector<double> work;
+    for (int i = 0; i < n; i++) {
+        lfsgm_ctx tmp;
+        const lfsgm_status st = plan_handle(cfgs[i], &tmp);
+        if (st != LFSGM_OK) {
+            g_create_err = "light field " + std::to_string(i) + ": " + g_create_err;
+            return st;
+        }
+        z.push_back(lf_sizes(&tmp));
+        work.push_back(z.back().work);
+    }
+    size_t need = 0;
+    if (branches > 0) {
+        need = batch_bytes(z, batch_assign(work, std::min((int)branches, (int)n)));
+    } else {
+        for (int K : kBatchK)
+            if (K <= n) need = std::max(need, batch_bytes(z, batch_assign(work, K)));
+    }
+    *bytes = need;
+    return LFSGM_OK;
+}
+
+lfsgm_status lfsgm_batch_create_ws(int32_t n, const lfsgm_config *cfgs, const float *const *views,
+                                   float *const *disp, void *stream, int32_t branches, void *ws, size_t ws_bytes,
+                                   lfsgm_batch *out) {
+    if (!ws) {
+        if (out) *out = nullptr;
+        g_create_err = "null batch workspace";
+        return LFSGM_ERR_INVALID_ARG;
+    }
+    return batch_create(n, cfgs, views, disp, stream, branches, ws, ws_bytes, out);
 }
 
 lfsgm_status lfsgm_batch_run(lfsgm_batch b) {
@@ -1162,7 +1309,7 @@ lfsgm_status lfsgm_batch_destroy(lfsgm_batch b) {
     if (!b->h.empty() || b->stamps) cudaDeviceSynchronize();
     batch_release_plan(b);
     for (auto *h : b->h) lfsgm_destroy(h);
-    cudaFree(b->stamps);
+    if (!b->ext) cudaFree(b->stamps);
     if (b->fork) cudaEventDestroy(b->fork);
     if (b->cap) cudaStreamDestroy(b->cap);
     delete b;

@@ -34,6 +34,32 @@ __device__ __forceinline__ bool row_aligned(long long o, int *status) {
     return ok;
 }
 
+// The KW-label range [g0, g0 + KW) that holds the most windows of at most 32 labels (nar) of a
+// warp's 32 pixels (ties: the lowest start; candidates are the lanes' own window starts, in lane
+// order).  Returns the number of windows it holds (-1 when no lane has a narrow window).
+template <int KW>
+__device__ __forceinline__ int row_range(int l, int n, bool nar, int &g0) {
+    int best = -1;
+    g0 = 0;
+    for (int c = 0; c < 32; c++) {
+        const int cl = __shfl_sync(0xffffffffu, l, c);
+        if (!__shfl_sync(0xffffffffu, nar, c)) continue;
+        const int fit = __popc(__ballot_sync(0xffffffffu, nar && l >= cl && l + n <= cl + KW));
+        if (fit > best || (fit == best && cl < g0)) {
+            best = fit;
+            g0 = cl;
+        }
+    }
+    return best;
+}
+
+// Append (pixel, chunk of 32 labels) work items for a window of n labels.
+__device__ __forceinline__ void push_chunks(int2 *list, int *count, int p, int n) {
+    const int nch = (n + 31) >> 5;
+    const int k = atomicAdd(count, nch);
+    for (int c = 0; c < nch; c++) list[k + c] = make_int2(p, c);
+}
+
 // One 16-byte read-only load of a table entry.
 __device__ __forceinline__ FineTap load_tap(const FineTap *t) {
     const int4 w = __ldg(reinterpret_cast<const int4 *>(t));
@@ -217,9 +243,14 @@ cudaError_t launch_sgm_backward(cudaStream_t s, const float *cost, const int *lo
                                 const long long *off, int H, int W, int G, float P1, float P2, const float *gCs,
                                 unsigned char *codes, int *amin, size_t nnz_cap, float *gcost, float *gP,
                                 int *status, const int *order, int paths);
-cudaError_t launch_views_backward(cudaStream_t s, const float *views, const FineTap *tab, int G, int nviews, int C,
+cudaError_t launch_views_backward(cudaStream_t s, const float *views, const FineTap *tab, int G, int U, int V, int C,
                                   int H, int W, int ref, const int *lo, const int *cnt, const long long *off,
-                                  float wl2, const float *gcost, float *gviews, const int2 *list, const int *count);
+                                  float wl2, float fstep, const float *gcost, float *gviews, int2 *list, int *count);
+// Grey: the items of the list (wide windows, and narrow ones the row kernel left) after launch_views_backward.
+cudaError_t launch_views_backward_list(cudaStream_t s, const float *views, const FineTap *tab, int G, int nviews,
+                                       int H, int W, int ref, const int *lo, const int *cnt, const long long *off,
+                                       float wl2, const float *gcost, float *gviews, const int2 *list,
+                                       const int *count);
 
 constexpr int kPartialBlocks = 1024;
 

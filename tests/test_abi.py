@@ -148,3 +148,20 @@ def test_batch_arguments_rejected_before_any_cuda_call(lib):
     assert lib.lfsgm_batch_create(2, cfgs, ptrs, ptrs, None, 0, C.byref(out)) == 1
     msg = lib.lfsgm_batch_last_error(None).decode()
     assert msg.startswith("light field 0") and "fine_labels" in msg
+
+
+def test_batch_workspace_size_is_host_only(lib):
+    """lfsgm_batch_workspace_size plans from the configurations alone (no GPU here): more
+    branches need at least as much scratch, the autotuner's bound covers every candidate, and an
+    invalid configuration is refused."""
+    import lfsynth
+    import paper_1907_13449_gb300 as lf
+    params = [lfsynth.tiny_params(), lfsynth.bench_params(), lfsynth.tiny_params(census_w=7)]
+    one = lf.lfsgm_batch_workspace_size(params, branches=1)
+    two = lf.lfsgm_batch_workspace_size(params, branches=2)
+    three = lf.lfsgm_batch_workspace_size(params, branches=3)
+    auto = lf.lfsgm_batch_workspace_size(params, branches=0)
+    assert 0 < one <= two <= three and auto >= max(one, two)
+    assert one % 256 == 0
+    with pytest.raises(lf.LfsgmError):
+        lf.lfsgm_batch_workspace_size([lfsynth.tiny_params(census_w=9)], branches=1)

@@ -107,3 +107,42 @@ def test_batch_rejects_an_invalid_member(gpu_lib, mix):
     views = [torch.from_numpy(mix[0][1]).cuda(), torch.zeros(25 * 64 * 64, device="cuda")]
     with pytest.raises(gpu_lib.LfsgmError, match="light field 1"):
         gpu_lib.LightFieldBatch([mix[0][0], bad], views, branches=1)
+
+
+def test_batch_in_caller_workspace_matches_library_scratch(gpu_lib, mix):
+    """lfsgm_batch_create_ws: the scratch of every branch in one caller-owned buffer of the size
+    lfsgm_batch_workspace_size reports; the disparities equal those of the library-allocated
+    batch bit for bit, and a buffer one byte short is refused with LFSGM_ERR_WORKSPACE."""
+    import torch
+    params = [m[0] for m in mix]
+    views = [torch.from_numpy(v).cuda() for _, v, _, _ in mix]
+    ref = gpu_lib.LightFieldBatch(params, views, branches=2)
+    want = [d.clone() for d in ref.run()]
+    torch.cuda.synchronize()
+    ref.close()
+    need = gpu_lib.lfsgm_batch_workspace_size(params, branches=2)
+    ws = torch.empty(need + 256, dtype=torch.uint8, device="cuda")
+    off = (-ws.data_ptr()) % 256
+    ws = ws[off:off + need]
+    b = gpu_lib.LightFieldBatch(params, views, branches=2, ws=ws)
+    for _ in range(2):
+        got = b.run()
+        torch.cuda.synchronize()
+        for a, c in zip(want, got):
+            assert torch.equal(torch.nan_to_num(a, nan=-1e30), torch.nan_to_num(c, nan=-1e30))
+    s, e, k = b.times()
+    assert k == 2 and np.all(e > s)
+    b.close()
+    with pytest.raises(gpu_lib.LfsgmError, match="too small"):
+        gpu_lib.LightFieldBatch(params, views, branches=2, ws=ws[:need - 1])
+    # autotuned branch count inside a buffer sized for every candidate
+    need_all = gpu_lib.lfsgm_batch_workspace_size(params, branches=0)
+    assert need_all >= need
+    ws2 = torch.empty(need_all + 256, dtype=torch.uint8, device="cuda")
+    off = (-ws2.data_ptr()) % 256
+    b = gpu_lib.LightFieldBatch(params, views, branches=0, ws=ws2[off:off + need_all])
+    got = b.run()
+    torch.cuda.synchronize()
+    for a, c in zip(want, got):
+        assert torch.equal(torch.nan_to_num(a, nan=-1e30), torch.nan_to_num(c, nan=-1e30))
+    b.close()

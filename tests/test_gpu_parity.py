@@ -433,14 +433,17 @@ def test_sgm_aggregate_is_reproducible_at_bench_shape(gpu_lib, paths):
     vd = torch.from_numpy(views).cuda()
     L.initial(vd)
     L.cost_volume(vd)
+    nnz = int(L.off[-1].item())
     runs = []
     for _ in range(3):
         L.aggregate(-1.0, -1.0)
         torch.cuda.synchronize()
-        runs.append(L.agg.clone())
+        runs.append(L.agg[:nnz].clone())
     gpu_lib.lfsgm_sync(L.h)
     L.close()
-    assert torch.equal(runs[0], runs[1]) and torch.equal(runs[0], runs[2])
+    for r in runs[1:]:
+        diff = torch.nonzero(runs[0] != r).flatten()
+        assert diff.numel() == 0, (int(diff.numel()), diff[:8].tolist(), runs[0][diff[:8]].tolist(), r[diff[:8]].tolist())
 
 
 def test_argument_errors_are_reported(gpu_lib, tiny_case):
