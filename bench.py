@@ -174,14 +174,14 @@ def alu_ops_cost(p, nnz_active):
     return nnz_active * (p.U * p.V - 1) * alu_ops_per_cell_view(p)
 
 
-ROW_KW = 36      # label span of the row cost kernel (kRowKW in k_fine_cost.cu)
+ROW_KW = 36      # default label span of the row cost kernel's ranges (36 or 44, lfsgm_set_tuning)
 
 
-def row_kernel_cells(lo, cnt, H, W):
+def row_kernel_cells(lo, cnt, H, W, kw=ROW_KW):
     """Cells the row cost kernel computes (the rest go to the list kernel): per run of 32 pixels
-    of a row it takes the ROW_KW-label range [g0, g0 + ROW_KW) that holds the most windows of at
-    most 32 labels (ties: the lowest start, candidates in lane order) and computes the windows
-    inside it -- the kernel's own selection, replayed on the host from the window map."""
+    of a row it takes the kw-label range [g0, g0 + kw) that holds the most windows of at most 32
+    labels (ties: the lowest start, candidates in lane order) and computes the windows inside it --
+    the kernel's own selection, replayed on the host from the window map."""
     import numpy as np
     lo = lo.reshape(H, W).astype(np.int64)
     cnt = cnt.reshape(H, W).astype(np.int64)
@@ -195,11 +195,11 @@ def row_kernel_cells(lo, cnt, H, W):
     g0 = np.zeros(l.shape[0], np.int64)
     for c in range(32):
         cl = l[:, c]
-        fit = (nar & (l >= cl[:, None]) & (l + n <= cl[:, None] + ROW_KW)).sum(1)
+        fit = (nar & (l >= cl[:, None]) & (l + n <= cl[:, None] + kw)).sum(1)
         take = nar[:, c] & ((fit > best) | ((fit == best) & (cl < g0)))
         best = np.where(take, fit, best)
         g0 = np.where(take, cl, g0)
-    fits = nar & (l >= g0[:, None]) & (l + n <= g0[:, None] + ROW_KW) & (best[:, None] > 0)
+    fits = nar & (l >= g0[:, None]) & (l + n <= g0[:, None] + kw) & (best[:, None] > 0)
     return int((n * fits).sum())
 
 
@@ -235,6 +235,8 @@ def run_ours(args, ws, rank, local):
     if ws > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=dev)
+    # the library's autotuner picks the speed knobs for this shape (untimed)
+    row_kw, list_ctas = lf.lfsgm_autotune(L.h, views)
 
     def step(events=None):
         L.initial(views)
@@ -253,7 +255,7 @@ def run_ours(args, ws, rank, local):
     nnz = int(L.off[-1].item())
     cnt = L.cnt.cpu().numpy()
     active = int(cnt.sum())
-    row_cells = row_kernel_cells(L.lo.cpu().numpy(), cnt, p.H, p.W) if p.channels == 1 else 0
+    row_cells = row_kernel_cells(L.lo.cpu().numpy(), cnt, p.H, p.W, row_kw) if p.channels == 1 else 0
 
     lf.lfsgm_set_profiling(L.h, True)
     lf.lfsgm_kernel_times(L.h)          # drop anything recorded so far
@@ -395,6 +397,8 @@ def run_ours(args, ws, rank, local):
         "config": {"workload": workload_label(p), "l2": L2_NOTE, "penalties": PENALTY_NOTE,
                    "parallelism": f"replicas x{ws}"},
         "gcell_per_s": round(active / (value * 1e-3) / 1e9, 2),
+        "tuning": {"row_kw": row_kw, "list_ctas_per_sm": list_ctas,
+                   "note": "speed knobs picked by lfsgm_autotune on this light field before the timed region"},
         "value_stats": {"median": round(statistics.median(stage_each), 4), "min": round(stage_each[0], 4),
                         "p99": round(stage_each[min(len(stage_each) - 1, int(0.99 * len(stage_each)))], 4),
                         "unit": "ms, cost+SGM per step on this rank"},
@@ -514,6 +518,11 @@ def run_batch(args, dev):
     t0 = time.perf_counter()
     B = lf.LightFieldBatch(params, views, branches=args.batch_branches, stream=stream)
     tune_s = time.perf_counter() - t0
+    kw, lc = B.knobs()
+    knobs = {}
+    for i, p in enumerate(params):
+        knobs.setdefault(lfsynth.BATCH_CLASSES[i % 4]["name"], set()).add((int(kw[i]), int(lc[i])))
+    knobs = {k: sorted(v) for k, v in knobs.items()}
     for _ in range(2):
         B.run()
     torch.cuda.synchronize()
@@ -560,6 +569,7 @@ def run_batch(args, dev):
     pct = lambda a, q: round(float(np.percentile(a, q)), 3)
     return {"lfs": n, "classes": [c["name"] for c in lfsynth.BATCH_CLASSES],
             "branches": int(k), "graph_kernel_nodes": int(nodes), "runs": R,
+            "knobs": {"per_class_row_kw_list_ctas": knobs},
             "lf_per_s": round(n / (batch_ms * 1e-3), 1), "ms_per_batch": round(batch_ms, 3),
             "p50_ms": pct(done, 50), "p99_ms": pct(done, 99),
             "latency": "completion time of each light field after the batch starts (all submitted at once)",

@@ -102,6 +102,22 @@ lfsgm_status lfsgm_destroy(lfsgm_handle h);
 lfsgm_status lfsgm_workspace_size(lfsgm_handle h, size_t *bytes);
 lfsgm_status lfsgm_set_workspace(lfsgm_handle h, void *dptr, size_t bytes);
 
+/* Speed knobs (not in the paper): the label span of the row cost kernel's ranges (row_kw 36 or
+ * 44; 0 = 36), and the CTAs per SM of the (pixel, chunk) list kernel (list_ctas_per_sm 1..64;
+ * 0 = the default, 12 grey / 24 colour).  A wider span sends fewer windows to the list kernel
+ * and computes more labels per row.  Changing the span rebuilds the row descriptors on the host
+ * and synchronises the handle's stream; results change only in the last bits (a window moves
+ * between the row and the list kernel, which add the views in different FP32 orders).  The
+ * batch autotuner sets these per shape class.  Errors: LFSGM_ERR_INVALID_ARG for other values. */
+lfsgm_status lfsgm_set_tuning(lfsgm_handle h, int32_t row_kw, int32_t list_ctas_per_sm);
+
+/* Picks the speed knobs for this handle's shape on a representative light field (views: device,
+ * as for lfsgm_depth): one initial pass, then the cost stage is timed with the row kernel's label
+ * span 36 and 44 and, with the better one, with the list kernel's CTAs per SM 8, 16 and 24
+ * against the default; the fastest setting is kept (lfsgm_set_tuning) and returned in row_kw and
+ * list_ctas_per_sm (host, nullable).  Synchronous; uses the buffers of lfsgm_depth. */
+lfsgm_status lfsgm_autotune(lfsgm_handle h, const float *views, int32_t *row_kw, int32_t *list_ctas_per_sm);
+
 /* Upper bound of off[N] for this config (every pixel with a whole-range window). */
 lfsgm_status lfsgm_max_nnz(lfsgm_handle h, int64_t *nnz);
 
@@ -205,7 +221,8 @@ lfsgm_status lfsgm_depth(lfsgm_handle h, const float *views, float *disp, int32_
  * The pipeline of lfsgm_depth (derived penalties) runs for every light field; light fields are
  * spread over `branches` concurrent streams forked from `stream` (balanced by longest work first;
  * each branch then runs its light fields shortest first), branches
- * <= 0 lets an autotuner time K in {1,2,4,8,16} and keep the fastest.  Scratch is allocated at
+ * <= 0 lets an autotuner pick the speed knobs per shape class (lfsgm_batch_knobs), then time K in
+ * {1,2,4,8,16} and keep the fastest.  Scratch is allocated at
  * creation (per branch, sized for its largest member).  lfsgm_batch_run enqueues one graph launch;
  * lfsgm_batch_times synchronises and returns, per light field, the start and end of its pipeline
  * in ms after the batch started (%globaltimer stamps inside the graph), and the branch count.
@@ -217,6 +234,11 @@ lfsgm_status lfsgm_batch_create(int32_t n, const lfsgm_config *cfgs, const float
                                 float *const *disp, void *stream, int32_t branches, lfsgm_batch *out);
 lfsgm_status lfsgm_batch_run(lfsgm_batch b);
 lfsgm_status lfsgm_batch_times(lfsgm_batch b, double *start_ms, double *end_ms, int32_t *branches);
+/* The speed knobs (see lfsgm_set_tuning) each light field of the batch runs with: the autotuner
+ * (branches <= 0 at creation) times, per shape class, the cost stage of one member with the row
+ * kernel's label span 36 and 44 and then the list kernel's CTAs per SM, and sets the fastest on
+ * every member.  row_kw, list_ctas_per_sm: host int32 [n], nullable. */
+lfsgm_status lfsgm_batch_knobs(lfsgm_batch b, int32_t *row_kw, int32_t *list_ctas_per_sm);
 int64_t lfsgm_batch_kernel_nodes(lfsgm_batch b);    /* kernel nodes in the batch's graph */
 const char *lfsgm_batch_last_error(lfsgm_batch b);  /* NULL: error of the last failed create */
 lfsgm_status lfsgm_batch_destroy(lfsgm_batch b);

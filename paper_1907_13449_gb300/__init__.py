@@ -64,7 +64,8 @@ EXPORTS = ["lfsgm_create", "lfsgm_destroy", "lfsgm_workspace_size", "lfsgm_set_w
            "lfsgm_launch_count", "lfsgm_set_profiling", "lfsgm_kernel_times", "lfsgm_depth_host",
            "lfsgm_depth", "lfsgm_cost_volume_noalloc", "lfsgm_batch_create", "lfsgm_batch_run",
            "lfsgm_batch_times", "lfsgm_batch_kernel_nodes", "lfsgm_batch_last_error",
-           "lfsgm_batch_destroy", "lfsgm_median_filter", "lfsgm_batch_workspace_size", "lfsgm_batch_create_ws"]
+           "lfsgm_batch_destroy", "lfsgm_median_filter", "lfsgm_batch_workspace_size", "lfsgm_batch_create_ws",
+           "lfsgm_set_tuning", "lfsgm_batch_knobs", "lfsgm_autotune"]
 
 
 def load(build_if_missing: bool = False):
@@ -104,6 +105,9 @@ def load(build_if_missing: bool = False):
         L.lfsgm_cost_volume_noalloc.argtypes = [P(Config), vp, vp, vp, vp, vp, vp]
         L.lfsgm_batch_create.argtypes = [i32, P(Config), P(vp), P(vp), vp, i32, P(vp)]
         L.lfsgm_batch_workspace_size.argtypes = [i32, P(Config), i32, P(C.c_size_t)]
+        L.lfsgm_set_tuning.argtypes = [vp, i32, i32]
+        L.lfsgm_autotune.argtypes = [vp, vp, P(i32), P(i32)]
+        L.lfsgm_batch_knobs.argtypes = [vp, P(i32), P(i32)]
         L.lfsgm_batch_create_ws.argtypes = [i32, P(Config), P(vp), P(vp), vp, i32, vp, C.c_size_t, P(vp)]
         L.lfsgm_batch_run.argtypes = [vp]
         L.lfsgm_batch_times.argtypes = [vp, P(C.c_double), P(C.c_double), P(i32)]
@@ -347,6 +351,31 @@ def lfsgm_batch_workspace_size(cfgs, branches=0) -> int:
     return int(out.value)
 
 
+def lfsgm_set_tuning(h, row_kw=0, list_ctas_per_sm=0):
+    """Speed knobs of a handle: the row cost kernel's label span (36 or 44; 0 = 36) and the list
+    kernel's CTAs per SM (0 = default)."""
+    _check(load().lfsgm_set_tuning(h, int(row_kw), int(list_ctas_per_sm)), h)
+
+
+def lfsgm_autotune(h, views):
+    """Tune the handle's speed knobs on ``views`` (device tensor); returns (row_kw, list_ctas_per_sm)."""
+    import torch
+    kw = C.c_int32()
+    lc = C.c_int32()
+    _check(load().lfsgm_autotune(h, _ptr(views, torch.float32, "views"), C.byref(kw), C.byref(lc)), h)
+    return int(kw.value), int(lc.value)
+
+
+def lfsgm_batch_knobs(b, n):
+    """(row_kw, list_ctas_per_sm) per light field of a batch, as numpy int32 arrays."""
+    import numpy as np
+    kw = np.zeros(n, np.int32)
+    lc = np.zeros(n, np.int32)
+    _bcheck(load().lfsgm_batch_knobs(b, kw.ctypes.data_as(C.POINTER(C.c_int32)),
+                                     lc.ctypes.data_as(C.POINTER(C.c_int32))), b)
+    return kw, lc
+
+
 def lfsgm_batch_run(b):
     _bcheck(load().lfsgm_batch_run(b), b)
 
@@ -394,6 +423,9 @@ class LightFieldBatch:
 
     def times(self):
         return lfsgm_batch_times(self.b, self.n)
+
+    def knobs(self):
+        return lfsgm_batch_knobs(self.b, self.n)
 
     @property
     def kernel_nodes(self):

@@ -605,8 +605,25 @@ __global__ void __launch_bounds__(32 * kVrWarps) views_backward_rows_kernel(
                     const float a0 = fmaf(cxy * fx, fy, fmaf(cy, fy, fmaf(cx, fx, i00 - Iref)));
                     const float b0 = fmaf(cxy, fmaf(fx, ay, fy * ax), fmaf(cy, ay, cx * ax));
                     const float cq = cxy * ax * ay;
+                    // two interleaved sets of moments (even and odd labels) for instruction-level parallelism
+                    float T0 = 0.f, T1 = 0.f, T2 = 0.f;
                     float t = 0.f;
-                    for (int j = js; j < je; j++, t += 1.f) {
+                    int j = js;
+                    for (; j + 1 < je; j += 2, t += 2.f) {
+                        const float gc0 = gcs[w][j][lane], gc1 = gcs[w][j + 1][lane];
+                        const float t1 = t + 1.f;
+                        const float e0 = fmaf(t, fmaf(t, cq, b0), a0), e1 = fmaf(t1, fmaf(t1, cq, b0), a0);
+                        const float g0 = e0 < 0.f ? gc0 : (e0 > 0.f ? -gc0 : 0.f);
+                        const float g1 = e1 < 0.f ? gc1 : (e1 > 0.f ? -gc1 : 0.f);
+                        const float gt0 = g0 * t, gt1 = g1 * t1;
+                        S0 += g0;
+                        S1 += gt0;
+                        S2 = fmaf(gt0, t, S2);
+                        T0 += g1;
+                        T1 += gt1;
+                        T2 = fmaf(gt1, t1, T2);
+                    }
+                    if (j < je) {
                         const float gc = gcs[w][j][lane];
                         const float e = fmaf(t, fmaf(t, cq, b0), a0);        // sample - I_ref
                         const float g = e < 0.f ? gc : (e > 0.f ? -gc : 0.f);
@@ -615,6 +632,9 @@ __global__ void __launch_bounds__(32 * kVrWarps) views_backward_rows_kernel(
                         S1 += gt;
                         S2 = fmaf(gt, t, S2);
                     }
+                    S0 += T0;
+                    S1 += T1;
+                    S2 += T2;
                     gref += S0;
                     // -sum g w for the corners: w11 = XY, w10 = X (1 - Y), w01 = (1 - X) Y, w00 = (1 - X)(1 - Y)
                     const float GX = fmaf(ax, S1, fx * S0), GY = fmaf(ay, S1, fy * S0);

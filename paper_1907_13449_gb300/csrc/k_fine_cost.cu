@@ -111,6 +111,7 @@ struct RowPlan {
     int o_rf, o_ds, stage;            // view tile and descriptor of stage 0 in a warp's slice; stage 1 at +stage
     int o_rc;                         // census tile (one buffer: refilled once its breakpoints are read)
     int o_cab, o_cc, o_cdiff, o_mbar, warp_bytes;
+    int kw;                           // label span of a row's range (a kernel instantiation)
 };
 
 // Descriptor of the label range [g0, g0+KW) of one view (built on the host, see
@@ -436,7 +437,6 @@ __global__ void __launch_bounds__(32 * kListWarps) fine_cost_list(const float *_
     }
 }
 
-constexpr int kRowKW = 36;
 
 __global__ void list_all_kernel(const int *__restrict__ lo, const int *__restrict__ cnt,
                                 const long long *__restrict__ off, int G, int2 *list, int *count, int N,
@@ -451,8 +451,11 @@ int r128(int x) { return (x + 127) & ~127; }
 }  // namespace
 
 // Padding, TMA boxes and the per-warp shared-memory layout of the row kernel for one config.
-bool plan_fine_rows(int U, int V, int uc, int vc, int H, int W, int G, double dmin, double dmax, RowPlanHost *out) {
+bool plan_fine_rows(int U, int V, int uc, int vc, int H, int W, int G, double dmin, double dmax, int kw,
+                    RowPlanHost *out) {
     RowPlan pl{};
+    const int kRowKW = kw == 44 ? 44 : 36;
+    pl.kw = kRowKW;
     const double md = fmax(fabs(dmin), fabs(dmax));
     const int amax = max(max(uc, U - 1 - uc), max(vc, V - 1 - vc));
     pl.P = (int)ceil(amax * md) + 3;
@@ -506,6 +509,7 @@ bool build_fine_rows_desc(const RowPlanHost *ph, const FineTap *tab, int U, int 
                           float fstep, std::vector<unsigned char> &out) {
     RowPlan pl;
     memcpy(&pl, ph->raw, sizeof(pl));
+    const int kRowKW = pl.kw;
     const int nviews = U * V;
     const size_t bytes = (size_t)nviews * G * pl.ds_stride;
     if (bytes > ((size_t)512 << 20)) return false;
@@ -622,14 +626,15 @@ cudaError_t launch_fine_cost_rows(cudaStream_t s, const RowPlanHost *ph, const f
     memcpy(&pl, ph->raw, sizeof(pl));
     const int wpb = 4;
     const size_t smem = (size_t)wpb * pl.warp_bytes;
-    cudaError_t e = cudaFuncSetAttribute(fine_cost_rows<kRowKW>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    auto kern = pl.kw == 44 ? fine_cost_rows<44> : fine_cost_rows<36>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     const long long tasks = (long long)((W + 31) / 32) * H;
     const unsigned grid = (unsigned)((tasks + wpb - 1) / wpb);
     (void)fstep;
-    fine_cost_rows<kRowKW><<<grid, 32 * wpb, smem, s>>>(*(const CUtensorMap *)ph->tm_v, *(const CUtensorMap *)ph->tm_c,
-                                                        desc, G, U, V, H, W, ref, lo, cnt, off, views_pad, cen_pad, wl2,
-                                                        wc, cost, status, list, list_count, pl);
+    kern<<<grid, 32 * wpb, smem, s>>>(*(const CUtensorMap *)ph->tm_v, *(const CUtensorMap *)ph->tm_c, desc, G, U, V, H,
+                                      W, ref, lo, cnt, off, views_pad, cen_pad, wl2, wc, cost, status, list, list_count,
+                                      pl);
     return cudaGetLastError();
 }
 
@@ -642,18 +647,19 @@ cudaError_t launch_list_all(cudaStream_t s, const int *lo, const int *cnt, const
 cudaError_t launch_fine_cost_list(cudaStream_t s, const float *views_pad, const uint64_t *cen_pad, int P, int Wp,
                                   int Hp, const int4 *ltab, int G, int nviews, int C, int W, int ref,
                                   const int *lo, const int *cnt, const long long *off, float wl2, float wc,
-                                  float *cost, const int2 *list, const int *count) {
+                                  float *cost, const int2 *list, const int *count, int ctas_per_sm) {
     int dev = 0, sms = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    // grid-stride over the items: 12 CTAs per SM for the grey residue (a few ten thousand items),
-    // 24 for colour, where every window is an item (measured best of 12 / 16 / 24)
+    // grid-stride over the items: by default 12 CTAs per SM for the grey residue (a few ten
+    // thousand items), 24 for colour, where every window is an item (measured best of 12 / 16 / 24)
+    const int k = ctas_per_sm > 0 ? ctas_per_sm : (C == 3 ? 24 : 12);
     if (C == 3)
-        fine_cost_list<3><<<sms * 24, 32 * kListWarps, 0, s>>>(views_pad, cen_pad, P, Wp, Hp, ltab, G, nviews, W, ref,
-                                                              lo, cnt, off, wl2, wc, cost, list, count);
+        fine_cost_list<3><<<sms * k, 32 * kListWarps, 0, s>>>(views_pad, cen_pad, P, Wp, Hp, ltab, G, nviews, W, ref,
+                                                             lo, cnt, off, wl2, wc, cost, list, count);
     else
-        fine_cost_list<1><<<sms * 12, 32 * kListWarps, 0, s>>>(views_pad, cen_pad, P, Wp, Hp, ltab, G, nviews, W, ref,
-                                                              lo, cnt, off, wl2, wc, cost, list, count);
+        fine_cost_list<1><<<sms * k, 32 * kListWarps, 0, s>>>(views_pad, cen_pad, P, Wp, Hp, ltab, G, nviews, W, ref,
+                                                             lo, cnt, off, wl2, wc, cost, list, count);
     return cudaGetLastError();
 }
 

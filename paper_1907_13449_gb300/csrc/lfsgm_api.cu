@@ -58,6 +58,9 @@ struct lfsgm_ctx {
     int N = 0, nviews = 0, ref = 0, nbits = 0, Lcd = 0;
     int C = 1;                            // colour channels; images are planes view * C + c
     ArmList arms{};
+    // tuning knobs (lfsgm_set_tuning): label span of the row kernel's ranges, list-kernel CTAs per SM
+    int row_kw = 36, list_ctas = 0;
+    std::vector<FineTap> h_fine;          // host copy of the shift table (row descriptors are rebuilt from it)
     // device tables
     FineTap *d_fine = nullptr;
     unsigned char *d_rowdesc = nullptr;   // row-kernel descriptors per (view, g0)
@@ -301,7 +304,7 @@ lfsgm_status plan_handle(const lfsgm_config &cin, lfsgm_ctx *h) {
     h->ref = c.vc * c.U + c.uc;
     h->nbits = c.census_w * c.census_w - 1;
     h->Lcd = coarse_stride(c.coarse_labels);
-    plan_fine_rows(c.U, c.V, c.uc, c.vc, c.H, c.W, c.fine_labels, c.dmin, c.dmax, &h->rows);
+    plan_fine_rows(c.U, c.V, c.uc, c.vc, c.H, c.W, c.fine_labels, c.dmin, c.dmax, h->row_kw, &h->rows);
     build_arms(h);
     // the packed coarse sums hold (paths) x (C + P2) per 16-bit half
     const long long cmax = (long long)max_arm_views(h) * h->nbits * h->C;
@@ -427,6 +430,7 @@ lfsgm_status lfsgm_create(const lfsgm_config *cfg, void *stream, lfsgm_handle *o
             h->rows.ok = false;      // every window then goes through the list kernel
         }
     }
+    h->h_fine = std::move(fine);
     ALLOC_COPY(h->d_otab, otab);
     ALLOC_COPY(h->d_armviews, armviews);
     ALLOC_COPY(h->d_sel_cross, sel_cross);
@@ -484,6 +488,42 @@ lfsgm_status lfsgm_workspace_size(lfsgm_handle h, size_t *bytes) {
 lfsgm_status lfsgm_set_workspace(lfsgm_handle h, void *dptr, size_t bytes) {
     if (!h || !dptr) return LFSGM_ERR_INVALID_ARG;
     return bind_workspace(h, dptr, bytes, false);
+}
+
+lfsgm_status lfsgm_set_tuning(lfsgm_handle h, int32_t row_kw, int32_t list_ctas_per_sm) {
+    if (!h) return LFSGM_ERR_INVALID_ARG;
+    if ((row_kw != 0 && row_kw != 36 && row_kw != 44) || list_ctas_per_sm < 0 || list_ctas_per_sm > 64)
+        return fail(h, LFSGM_ERR_INVALID_ARG, "tuning: row_kw must be 0, 36 or 44, list_ctas_per_sm in [0, 64]");
+    h->list_ctas = list_ctas_per_sm;
+    const int kw = row_kw == 0 ? 36 : row_kw;
+    if (kw == h->row_kw) return LFSGM_OK;
+    const lfsgm_config &c = h->cfg;
+    // new plan and descriptors for the new label span; the padding and the workspace layout do not
+    // depend on it, so a bound workspace keeps its buffers and only the tensor maps are re-encoded
+    RowPlanHost rows{};
+    plan_fine_rows(c.U, c.V, c.uc, c.vc, c.H, c.W, c.fine_labels, c.dmin, c.dmax, kw, &rows);
+    std::vector<unsigned char> desc;
+    const float fstep = (float)((c.dmax - c.dmin) / (double)(c.fine_labels - 1));
+    bool ok = rows.ok && h->C == 1 &&
+              build_fine_rows_desc(&rows, h->h_fine.data(), c.U, c.V, c.uc, c.vc, c.fine_labels, (float)c.dmin, fstep,
+                                   desc);
+    unsigned char *d = nullptr;
+    if (ok) {
+        cudaError_t e = cudaMalloc(&d, desc.size());
+        if (e == cudaSuccess) e = cudaMemcpy(d, desc.data(), desc.size(), cudaMemcpyHostToDevice);
+        if (e != cudaSuccess) {
+            cudaFree(d);
+            return cuda_fail(h, e, "row descriptors");
+        }
+    }
+    if (h->stream) cudaStreamSynchronize(h->stream);     // no launch of the old plan is in flight
+    cudaFree(h->d_rowdesc);
+    h->d_rowdesc = d;
+    rows.ok = ok;
+    h->rows = rows;
+    h->row_kw = kw;
+    h->rows_maps = h->ws && h->rows.ok && encode_fine_rows_maps(&h->rows, h->views_pad, h->cen_pad, h->nviews);
+    return LFSGM_OK;
 }
 
 lfsgm_status lfsgm_max_nnz(lfsgm_handle h, int64_t *nnz) {
@@ -595,7 +635,7 @@ lfsgm_status cost_volume_impl(lfsgm_handle h, const float *views, const int32_t 
     LFSGM_TRY(run(h, "fine_cost_wide", [&] {
         return launch_fine_cost_list(s, h->views_pad, h->cen_pad, h->rows.P, h->rows.Wp, h->rows.Hp, h->d_ltab,
                                      c.fine_labels, h->nviews, h->C, c.W, h->ref, lo, cnt, (const long long *)off,
-                                     c.w_l2, c.w_census, cost, h->wide_list, h->wide_count);
+                                     c.w_l2, c.w_census, cost, h->wide_list, h->wide_count, h->list_ctas);
     }));
     return LFSGM_OK;
 }
@@ -795,7 +835,7 @@ lfsgm_status lfsgm_kernel_times(lfsgm_handle h, const char **names, float *ms, i
 namespace {
 // The whole method on device views; `wait` (nullable) is an event the cost stage waits for (views
 // that only the cost stage reads may still be arriving while the initial pass runs).
-lfsgm_status depth_chain(lfsgm_handle h, const float *views, float *disp, int32_t *label, cudaEvent_t wait) {
+lfsgm_status depth_buffers(lfsgm_handle h) {
     const size_t N = (size_t)h->N;
     int64_t maxnnz = 0;
     lfsgm_max_nnz(h, &maxnnz);
@@ -809,6 +849,67 @@ lfsgm_status depth_chain(lfsgm_handle h, const float *views, float *disp, int32_
         if (e == cudaSuccess) e = cudaMalloc((void **)&h->o_agg, (size_t)maxnnz * 4);
         if (e != cudaSuccess) return fail(h, LFSGM_ERR_NO_MEMORY, "depth buffers: %s", cudaGetErrorString(e));
     }
+    return LFSGM_OK;
+}
+
+// The speed knobs of one handle: with the windows of one initial pass of `views` in (lo, cnt, off),
+// time the cost stage (best of two after a warm-up) for the row kernel's label span 36 and 44 and
+// then, with the better span, for the list kernel's CTAs per SM 8, 16, 24 against the default;
+// keep the fastest.  kw, lc: the choice.
+lfsgm_status tune_handle(lfsgm_handle h, const float *views, int32_t *lo, int32_t *cnt, int64_t *off, float *cost,
+                         int &kw_out, int &lc_out) {
+    LFSGM_TRY(lfsgm_initial_disparity(h, views, 0, 0, lo, cnt, off, nullptr, nullptr, nullptr));
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
+        if (e0) cudaEventDestroy(e0);
+        return fail(h, LFSGM_ERR_CUDA, "tuning events");
+    }
+    auto time_cost = [&](int kw, int lc, float &ms) -> lfsgm_status {
+        lfsgm_status st = lfsgm_set_tuning(h, kw, lc);
+        float best = 1e30f;
+        for (int r = 0; r < 3 && st == LFSGM_OK; r++) {
+            cudaEventRecord(e0, h->stream);
+            st = cost_volume_impl(h, views, lo, cnt, off, cost, !h->cfg.boundless);
+            cudaEventRecord(e1, h->stream);
+            cudaEventSynchronize(e1);
+            float t = 0.f;
+            cudaEventElapsedTime(&t, e0, e1);
+            if (r > 0) best = std::min(best, t);
+        }
+        ms = best;
+        return st;
+    };
+    int best_kw = 36, best_lc = 0;
+    float best_ms = 1e30f;
+    lfsgm_status st = LFSGM_OK;
+    for (int kw : {36, 44}) {
+        float ms = 0.f;
+        st = time_cost(kw, 0, ms);
+        if (st != LFSGM_OK) break;
+        if (ms < best_ms) {
+            best_ms = ms;
+            best_kw = kw;
+        }
+    }
+    for (int lc : {8, 16, 24}) {
+        if (st != LFSGM_OK) break;
+        float ms = 0.f;
+        st = time_cost(best_kw, lc, ms);
+        if (st == LFSGM_OK && ms < best_ms) {
+            best_ms = ms;
+            best_lc = lc;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (st == LFSGM_OK) st = lfsgm_set_tuning(h, best_kw, best_lc);
+    kw_out = best_kw;
+    lc_out = best_lc;
+    return st;
+}
+
+lfsgm_status depth_chain(lfsgm_handle h, const float *views, float *disp, int32_t *label, cudaEvent_t wait) {
+    LFSGM_TRY(depth_buffers(h));
     int64_t *off = (int64_t *)h->o_off;
     LFSGM_TRY(lfsgm_initial_disparity(h, views, 0, 0, h->o_lo, h->o_cnt, off, nullptr, nullptr, nullptr));
     if (wait) {
@@ -828,6 +929,17 @@ lfsgm_status lfsgm_depth(lfsgm_handle h, const float *views, float *disp, int32_
     if (!h) return LFSGM_ERR_INVALID_ARG;
     if (!views) return fail(h, LFSGM_ERR_INVALID_ARG, "null views");
     return depth_chain(h, views, disp, label, nullptr);
+}
+
+lfsgm_status lfsgm_autotune(lfsgm_handle h, const float *views, int32_t *row_kw, int32_t *list_ctas_per_sm) {
+    if (!h) return LFSGM_ERR_INVALID_ARG;
+    if (!views) return fail(h, LFSGM_ERR_INVALID_ARG, "null views");
+    LFSGM_TRY(depth_buffers(h));
+    int kw = 36, lc = 0;
+    LFSGM_TRY(tune_handle(h, views, h->o_lo, h->o_cnt, (int64_t *)h->o_off, h->o_cost, kw, lc));
+    if (row_kw) *row_kw = kw;
+    if (list_ctas_per_sm) *list_ctas_per_sm = lc;
+    return LFSGM_OK;
 }
 
 lfsgm_status lfsgm_depth_host(lfsgm_handle h, const float *views_host, float *disp_host, int32_t *label_host) {
@@ -1124,6 +1236,27 @@ lfsgm_status batch_build(lfsgm_batch_ctx *b, int K) {
     return LFSGM_OK;
 }
 
+// Speed knobs per shape class (light fields with the same configuration), on the buffers of a
+// one-branch plan: the first member is tuned (tune_handle) and every member gets its setting.
+lfsgm_status batch_tune_knobs(lfsgm_batch_ctx *b) {
+    if (b->branches != 1 || b->bb.empty()) return LFSGM_OK;
+    BranchBufs &x = b->bb[0];
+    std::vector<int> done(b->n, 0);
+    for (int i = 0; i < b->n; i++) {
+        if (done[i]) continue;
+        lfsgm_ctx *h = b->h[i];
+        int kw = 36, lc = 0;
+        lfsgm_status st = tune_handle(h, b->views[i], x.lo, x.cnt, (int64_t *)x.off, x.cost, kw, lc);
+        for (int j = i; j < b->n && st == LFSGM_OK; j++)
+            if (!done[j] && memcmp(&b->h[j]->cfg, &h->cfg, sizeof(lfsgm_config)) == 0) {
+                st = lfsgm_set_tuning(b->h[j], kw, lc);
+                done[j] = 1;
+            }
+        if (st != LFSGM_OK) return bfail(b, st, "tuning light field %d: %s", i, h->err.c_str());
+    }
+    return LFSGM_OK;
+}
+
 float batch_time_ms(lfsgm_batch_ctx *b, int reps) {
     cudaEvent_t a, c;
     cudaEventCreate(&a);
@@ -1201,10 +1334,16 @@ lfsgm_status batch_create(int32_t n, const lfsgm_config *cfgs, const float *cons
     if (branches > 0) {
         st = batch_build(b, std::min(branches, n));
     } else {
-        // autotune K (with a caller workspace: the K whose scratch fits it)
+        // speed knobs per shape class on a one-branch plan, then the branch count K (with a caller
+        // workspace: the K whose scratch fits it)
+        if (!b->ext || batch_bytes(b->sizes, batch_assign(b->work, 1)) <= b->ext_bytes) {
+            st = batch_build(b, 1);
+            if (st == LFSGM_OK) st = batch_tune_knobs(b);
+        }
         int bestK = 0;
         float best = 1e30f;
         for (int K : kBatchK) {
+            if (st != LFSGM_OK) break;
             if (K > n) break;
             if (b->ext && batch_bytes(b->sizes, batch_assign(b->work, K)) > b->ext_bytes) continue;
             st = batch_build(b, K);
@@ -1279,6 +1418,15 @@ lfsgm_status lfsgm_batch_run(lfsgm_batch b) {
     if (!b || !b->exec) return LFSGM_ERR_INVALID_ARG;
     const cudaError_t e = cudaGraphLaunch(b->exec, b->main);
     if (e != cudaSuccess) return bfail(b, LFSGM_ERR_CUDA, "graph launch: %s", cudaGetErrorString(e));
+    return LFSGM_OK;
+}
+
+lfsgm_status lfsgm_batch_knobs(lfsgm_batch b, int32_t *row_kw, int32_t *list_ctas_per_sm) {
+    if (!b) return LFSGM_ERR_INVALID_ARG;
+    for (int i = 0; i < b->n; i++) {
+        if (row_kw) row_kw[i] = b->h[i]->row_kw;
+        if (list_ctas_per_sm) list_ctas_per_sm[i] = b->h[i]->list_ctas;
+    }
     return LFSGM_OK;
 }
 

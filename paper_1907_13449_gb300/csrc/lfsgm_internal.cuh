@@ -202,7 +202,9 @@ struct RowPlanHost {
     bool ok;
     int P, Wp, Hp;                         // padding and padded sizes
 };
-bool plan_fine_rows(int U, int V, int uc, int vc, int H, int W, int G, double dmin, double dmax, RowPlanHost *out);
+// kw: the label span of a row's range, 36 or 44 (two instantiations of the row kernel).
+bool plan_fine_rows(int U, int V, int uc, int vc, int H, int W, int G, double dmin, double dmax, int kw,
+                    RowPlanHost *out);
 bool encode_fine_rows_maps(RowPlanHost *ph, const float *views_pad, const uint64_t *cen_pad, int nviews);
 // Census words (planes view * C + c) and the edge-padded views (C = 1: float planes; C = 3: one
 // float4 per pixel, channels interleaved) of the views listed in d_sel.
@@ -219,7 +221,8 @@ cudaError_t launch_list_all(cudaStream_t s, const int *lo, const int *cnt, const
 cudaError_t launch_fine_cost_list(cudaStream_t s, const float *views_pad, const uint64_t *cen_pad, int P, int Wp,
                                   int Hp, const int4 *ltab, int G, int nviews, int C, int W, int ref,
                                   const int *lo, const int *cnt, const long long *off, float wl2, float wc,
-                                  float *cost, const int2 *list, const int *count);
+                                  float *cost, const int2 *list, const int *count,
+                                  int ctas_per_sm = 0);
 
 // Mean cost over the active slots and the derived penalties pen = (p1f, p2f) x mean, in one launch:
 // partial holds nblocks sums followed by nblocks counts; ticket (zero between launches) picks the

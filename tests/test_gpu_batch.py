@@ -68,10 +68,19 @@ def test_batch_single_branch_reuses_buffers_across_shapes(gpu_lib, mix):
 
 
 def test_batch_autotuned_times_are_consistent(gpu_lib, mix):
-    disp, start, end, k, _ = _batch(gpu_lib, mix, branches=0)
+    import torch
+    views = [torch.from_numpy(v).cuda() for _, v, _, _ in mix]
+    b = gpu_lib.LightFieldBatch([m[0] for m in mix], views, branches=0)
+    disp = [d.cpu().numpy() for d in b.run()]
+    torch.cuda.synchronize()
+    start, end, k = b.times()
+    kw, lc = b.knobs()
+    b.close()
     assert k in (1, 2, 4, 8)
     _check_vs_oracle(disp, mix)
     assert np.all(start >= 0.0) and np.all(end > start)
+    # the autotuner picked a row span and list CTAs per shape class (the same for equal configs)
+    assert set(kw.tolist()) <= {36, 44} and set(lc.tolist()) <= {0, 8, 16, 24}
 
 
 def test_batch_matches_single_light_field_launches(gpu_lib, mix):

@@ -108,9 +108,11 @@ def test_initial_disparity_variants(gpu_lib, variant):
 
 
 # ----------------------------------------------------------------------- cost volume
-def _gpu_cost(lf, p, views, lo, cnt):
+def _gpu_cost(lf, p, views, lo, cnt, row_kw=0):
     import torch
     h = lf.lfsgm_create(p)
+    if row_kw:
+        lf.lfsgm_set_tuning(h, row_kw, 16)
     off = pad4_offsets(cnt)
     cost = torch.full((int(off[-1]),), float("nan"), dtype=torch.float32, device="cuda")
     lf.lfsgm_cost_volume(h, _dev(views), _dev(lo, torch.int32), _dev(cnt, torch.int32), _dev(off), cost)
@@ -129,6 +131,20 @@ def test_cost_volume_tiny(gpu_lib, tiny_case):
     off, c = _gpu_cost(gpu_lib, p, views, ref["lo"], ref["cnt"])
     err = csr_rel_err(gather(c, off, ref["cnt"]), ref["cost"], ref["cnt"])
     assert err < RTOL, err
+
+
+@pytest.mark.parametrize("row_kw", [36, 44])
+def test_cost_volume_with_each_row_span(gpu_lib, tiny_case, row_kw):
+    """The speed knobs (row kernel label span 36 / 44, list kernel CTAs per SM) change which kernel
+    computes a window, not the cost: both match the oracle (Eq. 12 + Eq. 15)."""
+    views, gt, p, cfg, ref = tiny_case
+    off, c = _gpu_cost(gpu_lib, p, views, ref["lo"], ref["cnt"], row_kw=row_kw)
+    err = csr_rel_err(gather(c, off, ref["cnt"]), ref["cost"], ref["cnt"])
+    assert err < RTOL, err
+    h = gpu_lib.lfsgm_create(p)
+    with pytest.raises(gpu_lib.LfsgmError, match="row_kw"):
+        gpu_lib.lfsgm_set_tuning(h, 40, 0)
+    gpu_lib.lfsgm_destroy(h)
 
 
 def test_cost_census_only_is_exact(gpu_lib):
