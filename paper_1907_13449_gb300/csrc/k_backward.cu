@@ -107,7 +107,7 @@ __global__ void __launch_bounds__(32 * kBwdWarps) sgm_backward_kernel(
     const long long *__restrict__ off, int H, int W, int G, int Gs, float P1, float P2, ScanTable st,
     const float *__restrict__ gCs, unsigned char *__restrict__ codes, int *__restrict__ amin, size_t nnz_cap,
     float *__restrict__ gcost, float *__restrict__ gP, int *__restrict__ status,
-    const int *__restrict__ order) {
+    const int *__restrict__ order, int recompute) {
     extern __shared__ float sm[];
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
     const int gw = blockIdx.x * kBwdWarps + wib;
@@ -144,7 +144,8 @@ __global__ void __launch_bounds__(32 * kBwdWarps) sgm_backward_kernel(
         }
     };
 
-    // forward recompute: branch codes and argmin slots.  Narrow steps (this window and the
+    // forward recompute: branch codes and argmin slots (skipped when the forward SGM recorded them).
+    // Narrow steps (this window and the
     // predecessor's at most 32 labels) keep the predecessor row in registers, one slot per lane,
     // and take its neighbours by shuffles; wider ones use the rows in shared memory.
     int plo = 0, pn = 0;
@@ -155,7 +156,7 @@ __global__ void __launch_bounds__(32 * kBwdWarps) sgm_backward_kernel(
     int cw, co, nw = 0, no = 0;
     fetch(0, cw, co, status);
     if (len > 32) fetch(32, nw, no, status);
-    for (int k = 0; k < len; k++) {
+    for (int k = 0; k < (recompute ? len : 0); k++) {
         const int kk = k & 31;
         if (kk == 0 && k > 0) {
             cw = nw;
@@ -259,18 +260,39 @@ __global__ void __launch_bounds__(32 * kBwdWarps) sgm_backward_kernel(
     bool have_inc = false;       // the current pixel has an incoming adjoint (from its successor)
     bool inc_smem = false;       // ... held in bufA by slot (general form), else in inc, one slot per lane
     float inc = 0.f;
+    // the argmin slot of each step of a block, fetched with its metadata (written above by this warp)
+    auto fetch_am = [&](int kb) {
+        const int kq = kb + lane;
+        return (kq >= 0 && kq < len) ? am[(int)(p0 + (long long)kq * dpix)] : 0;
+    };
+    int ca = 0, na = 0;
     {
         const int kb0 = (len - 1) & ~31;
         fetch(kb0, cw, co, nullptr);
-        if (kb0 >= 32) fetch(kb0 - 32, nw, no, nullptr);
+        ca = fetch_am(kb0);
+        if (kb0 >= 32) {
+            fetch(kb0 - 32, nw, no, nullptr);
+            na = fetch_am(kb0 - 32);
+        }
     }
+    // the dLoss/dC_s row and branch codes of the next step (k - 1), loaded one step ahead when it
+    // is narrow
+    bool pf_ok = false;
+    float pf_g = 0.f;
+    unsigned pf_c = 4u;
     for (int k = len - 1; k >= 0; k--) {
         const int kb = k & ~31, kk = k & 31;
         if (kk == 31 && k < len - 1) {       // entered a lower block
             cw = nw;
             co = no;
-            if (kb >= 32) fetch(kb - 32, nw, no, nullptr);
+            ca = na;
+            if (kb >= 32) {
+                fetch(kb - 32, nw, no, nullptr);
+                na = fetch_am(kb - 32);
+            }
         }
+        const bool have_pf = pf_ok;
+        pf_ok = false;
         const int win = __shfl_sync(0xffffffffu, cw, kk), ofs = __shfl_sync(0xffffffffu, co, kk);
         // predecessor on the path: step k - 1 (this block, or lane 31 of the block below)
         const int wq = __shfl_sync(0xffffffffu, kk > 0 ? cw : nw, (kk + 31) & 31);
@@ -291,15 +313,22 @@ __global__ void __launch_bounds__(32 * kBwdWarps) sgm_backward_kernel(
             const bool act = lane < n;
             float in_v = 0.f;
             if (have_inc) in_v = inc_smem ? (act ? bufA[lane] : 0.f) : inc;
-            const float gv = act ? __ldg(gCs + o + lane) : 0.f;
-            const unsigned cd = act ? code[o + lane] : 4u;
+            const float gv = have_pf ? pf_g : (act ? __ldg(gCs + o + lane) : 0.f);
+            const unsigned cd = have_pf ? pf_c : (act ? (unsigned)code[o + lane] : 4u);
+            if (q >= 0) {
+                // q's row one step ahead (its window is narrow here)
+                const int oq = __shfl_sync(0xffffffffu, kk > 0 ? co : no, (kk + 31) & 31);
+                pf_g = lane < qn ? __ldg(gCs + 4ll * oq + lane) : 0.f;
+                pf_c = lane < qn ? (unsigned)code[4ll * oq + lane] : 4u;
+                pf_ok = true;
+            }
             const float lv = act ? gv + in_v : 0.f;
             if (act) atomicAdd(gcost + o + lane, lv);
             if (cd == 1 || cd == 2) gp1 += lv;
             if (cd == 3) gp2 += lv;
             const float dm = warp_sum((cd == 3 ? lv : 0.f) - lv);
             if (q >= 0) {
-                const int qa = am[q];
+                const int qa = __shfl_sync(0xffffffffu, kk > 0 ? ca : na, (kk + 31) & 31);
                 const int j0 = lane + (ql - l), j1 = j0 + 1, j2 = j0 - 1;
                 const float l0 = __shfl_sync(0xffffffffu, lv, j0 & 31), l1 = __shfl_sync(0xffffffffu, lv, j1 & 31);
                 const float l2 = __shfl_sync(0xffffffffu, lv, j2 & 31);
@@ -649,12 +678,16 @@ __global__ void __launch_bounds__(32 * kVrWarps) views_backward_rows_kernel(
         }
         __syncthreads();
         if (use_box) {
-            for (int e = threadIdx.x; e < bw * bh; e += blockDim.x) {
-                const int by = e / bw, bx = e - by * bw;
-                const float v = box[by * kVrBoxW + bx];
-                if (v != 0.f) {
-                    atomicAdd(gI + (size_t)(by0 + by) * W + (bx0 + bx), v);
-                    box[by * kVrBoxW + bx] = 0.f;
+            // a warp per box row, lanes along it
+            for (int by = w; by < bh; by += kVrWarps) {
+                float *brow = box + by * kVrBoxW;
+                float *grow = gI + (size_t)(by0 + by) * W + bx0;
+                for (int bx = lane; bx < bw; bx += 32) {
+                    const float v = brow[bx];
+                    if (v != 0.f) {
+                        atomicAdd(grow + bx, v);
+                        brow[bx] = 0.f;
+                    }
                 }
             }
         }
@@ -675,7 +708,8 @@ cudaError_t launch_softargmin_backward(cudaStream_t s, const float *agg, const i
 
 cudaError_t launch_sgm_backward(cudaStream_t s, const float *cost, const int *lo, const int *cnt, const long long *off,
                                 int H, int W, int G, float P1, float P2, const float *gCs, unsigned char *codes,
-                                int *amin, size_t nnz_cap, float *gcost, float *gP, int *status, const int *order, int paths) {
+                                int *amin, size_t nnz_cap, float *gcost, float *gP, int *status, const int *order, int paths,
+                                bool recompute) {
     const ScanTable st = make_scan_table(H, W, paths);
     const int Gs = (G + 31) & ~31;
     const size_t smem = (size_t)kBwdWarps * 4 * Gs * sizeof(float);   // bufA, bufB, lambda, codes per warp
@@ -686,7 +720,7 @@ cudaError_t launch_sgm_backward(cudaStream_t s, const float *cost, const int *lo
         if (e != cudaSuccess) return e;
     }
     sgm_backward_kernel<<<grid, 32 * kBwdWarps, smem, s>>>(cost, lo, cnt, off, H, W, G, Gs, P1, P2, st, gCs, codes,
-                                                           amin, nnz_cap, gcost, gP, status, order);
+                                                           amin, nnz_cap, gcost, gP, status, order, recompute ? 1 : 0);
     return cudaGetLastError();
 }
 

@@ -49,6 +49,11 @@ __device__ __forceinline__ float warp_min(float v) {
     return r;
 }
 
+// REC: also record, for the adjoint, each cell's winning branch (0 same label, 1 label-1, 2 label+1,
+// 3 m+P2, 4 path start; the first of P2, same, g-1, g+1 that equals the minimum, as the adjoint's
+// own recurrence decides it) in codes[r * nnz_cap + slot] and each pixel's lowest minimising slot
+// in amin[r * N + p].
+template <bool REC>
 __global__ void __launch_bounds__(32 * kSgmWarps) fine_sgm_kernel(const float *__restrict__ cost,
                                                                   const int *__restrict__ lo,
                                                                   const int *__restrict__ cnt,
@@ -57,7 +62,9 @@ __global__ void __launch_bounds__(32 * kSgmWarps) fine_sgm_kernel(const float *_
                                                                   const float *__restrict__ pen,
                                                                   int G, ScanTable st, float *__restrict__ agg,
                                                                   int *__restrict__ status,
-                                                                  const int *__restrict__ order, int mk) {
+                                                                  const int *__restrict__ order, int mk,
+                                                                  unsigned char *__restrict__ codes,
+                                                                  int *__restrict__ amin, size_t nnz_cap) {
     extern __shared__ float sm[];
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
     const int gw = blockIdx.x * kSgmWarps + wib;
@@ -68,6 +75,8 @@ __global__ void __launch_bounds__(32 * kSgmWarps) fine_sgm_kernel(const float *_
     int x0, y0;
     scan_start(r, s, H, W, x0, y0);
     const int len = scan_steps(x0, y0, dx, dy, H, W);
+    unsigned char *code = REC ? codes + (size_t)r * nnz_cap : nullptr;
+    int *am = REC ? amin + (size_t)r * H * W : nullptr;
     // rows by slot with one sentinel slot on each side (slot -1 and slot n hold +inf), Gs + 2 floats
     float *bufA = sm + (size_t)wib * 2 * (Gs + 2) + 1;   // predecessor's path costs, general steps
     float *bufB = bufA + (Gs + 2);                       // this pixel's
@@ -129,6 +138,7 @@ __global__ void __launch_bounds__(32 * kSgmWarps) fine_sgm_kernel(const float *_
                 float c1 = 0.f;
                 if (n1 <= 32 && lane < n1) c1 = __ldg(cost + 4ll * ofs1 + lane);
                 float Lv = c;
+                unsigned cd = 4;
                 if (pn != 0) {
                     const int s0 = lane + (l - plo);     // slot of this label in the predecessor
                     const float v0 = __shfl_sync(0xffffffffu, prev, s0 & 31);
@@ -138,14 +148,21 @@ __global__ void __launch_bounds__(32 * kSgmWarps) fine_sgm_kernel(const float *_
                     // is monotone); an absent neighbour is +inf
                     const float a = (unsigned)(s0 - 1) < (unsigned)pn ? vm : INF;
                     const float b = (unsigned)(s0 + 1) < (unsigned)pn ? vp : INF;
+                    const float v = (unsigned)s0 < (unsigned)pn ? v0 : INF;
                     float t = fminf(m + P2, fminf(a, b) + P1);
-                    if ((unsigned)s0 < (unsigned)pn) t = fminf(t, v0);
+                    t = fminf(t, v);
+                    if (REC) cd = t == m + P2 ? 3u : (t == v ? 0u : (t == a + P1 ? 1u : 2u));
                     Lv = c + (t - m);
                 }
                 const bool act = lane < n;
                 if (act) atomicAdd(agg + 4ll * ofs + lane, det_addend(Lv, c + P2, mk));
                 prev = act ? Lv : INF;
                 m = warp_min(prev);
+                if (REC) {
+                    if (act) code[4ll * ofs + lane] = (unsigned char)cd;
+                    const int slot = (int)__reduce_min_sync(0xffffffffu, prev == m ? (unsigned)lane : 0x7fffffffu);
+                    if (lane == 0) am[p0 + (long long)k * dpix] = slot;
+                }
                 plo = l;
                 pn = n;
                 l = win1 & 0xffff;
@@ -170,6 +187,7 @@ __global__ void __launch_bounds__(32 * kSgmWarps) fine_sgm_kernel(const float *_
                 }
                 const long long o = 4ll * ofs;
                 float lmin = INF;
+                int lslot = 0x7fffffff;
                 // sixteen 32-label chunks per round: their cost loads are in flight together, and
                 // every chunk reads the predecessor row before any chunk stores its own (the
                 // compiler cannot tell bufA from bufB, so a store between them would order the
@@ -192,6 +210,8 @@ __global__ void __launch_bounds__(32 * kSgmWarps) fine_sgm_kernel(const float *_
                             const float vm = row[min(k1 - 1u, top)];
                             const float vp = row[min(k1 + 1u, top)];
                             const float t = fminf(fminf(m + P2, v0), fminf(vm, vp) + P1);
+                            if (REC)
+                                code[o + j0 + 32 * u] = t == m + P2 ? 3 : (t == v0 ? 0 : (t == vm + P1 ? 1 : 2));
                             const float Ln = cc[u] + (t - m);
                             // the cell's cost cc[u] bounds its path costs (the global atomic does
                             // not order the shared-memory reads of the other chunks)
@@ -203,6 +223,7 @@ __global__ void __launch_bounds__(32 * kSgmWarps) fine_sgm_kernel(const float *_
                         for (int u = 0; u < 16; u++) {
                             if (j0 + 32 * u >= n) break;
                             atomicAdd(agg + o + j0 + 32 * u, det_addend(cc[u], cc[u] + P2, mk));
+                            if (REC) code[o + j0 + 32 * u] = 4;
                         }
                     }
 #pragma unroll
@@ -210,10 +231,15 @@ __global__ void __launch_bounds__(32 * kSgmWarps) fine_sgm_kernel(const float *_
                         const int j = j0 + 32 * u;
                         if (j >= n) break;
                         bufB[j] = cc[u];
+                        if (REC && cc[u] < lmin) lslot = j;      // slots ascend: the first minimum
                         lmin = fminf(lmin, cc[u]);
                     }
                 }
                 m = warp_min(lmin);
+                if (REC) {
+                    const int slot = (int)__reduce_min_sync(0xffffffffu, lmin == m ? (unsigned)lslot : 0x7fffffffu);
+                    if (lane == 0) am[p0 + (long long)k * dpix] = slot;
+                }
                 if (lane == 0) bufB[n] = INF;
                 __syncwarp();
                 float *tmp = bufA;
@@ -348,21 +374,22 @@ void build_scan_order(int H, int W, int paths, std::vector<int> &order) {
 
 cudaError_t launch_fine_sgm(cudaStream_t s, const float *cost, const int *lo, const int *cnt,
                             const long long *off, int H, int W, int G, const float *pen, float *agg,
-                            int *status, const int *order, int paths) {
+                            int *status, const int *order, int paths, unsigned char *codes, int *amin,
+                            size_t nnz_cap) {
     const ScanTable st = make_scan_table(H, W, paths);
     const int Gs = (G + 31) & ~31;
     const size_t smem = (size_t)kSgmWarps * 2 * (Gs + 2) * sizeof(float);
     const unsigned grid = (unsigned)((st.cum[paths] + kSgmWarps - 1) / kSgmWarps);
+    auto kern = codes ? fine_sgm_kernel<true> : fine_sgm_kernel<false>;
     if (smem > 48 * 1024) {
-        cudaError_t e = cudaFuncSetAttribute(fine_sgm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)smem);
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
     }
     int lp = 0;
     while ((1 << lp) < paths) lp++;
     const int mk = (lp << 23) | (1 << 22);       // (23 - qsh) << 23 with qsh = 23 - log2(paths)
-    fine_sgm_kernel<<<grid, 32 * kSgmWarps, smem, s>>>(cost, lo, cnt, off, H, W, Gs, pen, G, st, agg, status, order,
-                                                       mk);
+    kern<<<grid, 32 * kSgmWarps, smem, s>>>(cost, lo, cnt, off, H, W, Gs, pen, G, st, agg, status, order, mk, codes,
+                                            amin, nnz_cap);
     return cudaGetLastError();
 }
 

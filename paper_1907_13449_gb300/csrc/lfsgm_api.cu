@@ -745,8 +745,20 @@ lfsgm_status lfsgm_backward(lfsgm_handle h, const float *views, const float *cos
     }
     const long long *o = (const long long *)off;
     const double step = (c.dmax - c.dmin) / (double)(c.fine_labels - 1);
-    // aggregate (the forward of the SGM, recomputed)
-    LFSGM_TRY(lfsgm_sgm_aggregate(h, cost, lo, cnt, off, P1, P2, h->b_agg));
+    // aggregate (the forward of the SGM, recomputed), recording each cell's winning branch and each
+    // pixel's argmin slot per direction for the adjoint
+    LFSGM_TRY(run(h, "set_penalties", [&] {
+        set_pen_kernel<<<1, 1, 0, s>>>(h->fpen, P1, P2);
+        return cudaGetLastError();
+    }));
+    LFSGM_TRY(run(h, "zero_agg", [&] {
+        zero_csr_kernel<<<1216, 256, 0, s>>>(h->b_agg, o, h->N);
+        return cudaGetLastError();
+    }));
+    LFSGM_TRY(run(h, "fine_sgm_record", [&] {
+        return launch_fine_sgm(s, cost, lo, cnt, o, c.H, c.W, c.fine_labels, h->fpen, h->b_agg, h->status,
+                               h->d_order, c.paths, h->b_codes, h->b_amin, (size_t)cap);
+    }));
     LFSGM_TRY(run(h, "softargmin_backward", [&] {
         return launch_softargmin_backward(s, h->b_agg, lo, cnt, o, h->N, c.fine_labels, c.dmin, step, c.softmin_tau,
                                           grad_disp, h->b_gcs, grad_cost, h->status);
@@ -756,7 +768,8 @@ lfsgm_status lfsgm_backward(lfsgm_handle h, const float *views, const float *cos
     if (e != cudaSuccess) return cuda_fail(h, e, "memset");
     LFSGM_TRY(run(h, "sgm_backward", [&] {
         return launch_sgm_backward(s, cost, lo, cnt, o, c.H, c.W, c.fine_labels, P1, P2, h->b_gcs, h->b_codes,
-                                   h->b_amin, (size_t)cap, grad_cost, h->b_gp, h->status, h->d_order, c.paths);
+                                   h->b_amin, (size_t)cap, grad_cost, h->b_gp, h->status, h->d_order, c.paths,
+                                   false);
     }));
     if (grad_views) {
         // the (pixel, 32-label chunk) items of windows wider than 32 labels; narrower ones by tiles

@@ -232,7 +232,8 @@ cudaError_t launch_cost_partial_sums(cudaStream_t s, const float *cost, const in
                                      double p1f, double p2f, float *pen, unsigned *ticket, int *status);
 cudaError_t launch_fine_sgm(cudaStream_t s, const float *cost, const int *lo, const int *cnt,
                             const long long *off, int H, int W, int G, const float *pen, float *agg,
-                            int *status, const int *order, int paths);
+                            int *status, const int *order, int paths,
+                            unsigned char *codes = nullptr, int *amin = nullptr, size_t nnz_cap = 0);
 
 cudaError_t launch_median3(cudaStream_t s, const float *in, float *out, int H, int W);
 cudaError_t launch_wta(cudaStream_t s, const float *agg, const int *lo, const int *cnt,
@@ -245,7 +246,8 @@ cudaError_t launch_softargmin_backward(cudaStream_t s, const float *agg, const i
 cudaError_t launch_sgm_backward(cudaStream_t s, const float *cost, const int *lo, const int *cnt,
                                 const long long *off, int H, int W, int G, float P1, float P2, const float *gCs,
                                 unsigned char *codes, int *amin, size_t nnz_cap, float *gcost, float *gP,
-                                int *status, const int *order, int paths);
+                                int *status, const int *order, int paths,
+                                bool recompute = true);
 cudaError_t launch_views_backward(cudaStream_t s, const float *views, const FineTap *tab, int G, int U, int V, int C,
                                   int H, int W, int ref, const int *lo, const int *cnt, const long long *off,
                                   float wl2, float fstep, const float *gcost, float *gviews, int2 *list, int *count);
