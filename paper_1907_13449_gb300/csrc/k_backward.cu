@@ -22,80 +22,52 @@ namespace {
 
 constexpr int kBwdWarps = 4;
 
+// gc with its sign flipped where e > 0 (the sign bit of e is clear): gc * sign(-e) for e != 0.
+__device__ __forceinline__ float sign_of_neg(float gc, float e) {
+    return __int_as_float(__float_as_int(gc) ^ (~__float_as_int(e) & 0x80000000));
+}
+
 __device__ __forceinline__ float warp_sum(float v) {
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
     return v;
 }
 
-__global__ void softargmin_backward_kernel(const float *__restrict__ agg, const int *__restrict__ lo,
-                                           const int *__restrict__ cnt, const long long *__restrict__ off, int N,
-                                           int G, double dmin, double step, float tau,
-                                           const float *__restrict__ gdisp, float *__restrict__ gCs,
-                                           float *__restrict__ gcost, int *__restrict__ status) {
-    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+// One warp per pixel, lane j on window slot j (wider windows in 32-slot chunks): the minimum by
+// redux.sync, the softmax normaliser z and sum_j w_j j by warp sums, both rows written coalesced.
+__global__ void __launch_bounds__(256) softargmin_backward_kernel(const float *__restrict__ agg,
+                                                                  const int *__restrict__ lo,
+                                                                  const int *__restrict__ cnt,
+                                                                  const long long *__restrict__ off, int N, int G,
+                                                                  double dmin, double step, float tau,
+                                                                  const float *__restrict__ gdisp,
+                                                                  float *__restrict__ gCs, float *__restrict__ gcost,
+                                                                  int *__restrict__ status) {
+    const int lane = threadIdx.x & 31;
+    const long long p = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     if (p >= N) return;
     const long long o = off[p];
     const int n = cnt[p], l = lo[p];
-    if (!window_ok(l, n, G, off[p + 1] - o, status)) return;
+    if (!window_ok(l, n, G, off[p + 1] - o, lane == 0 ? status : nullptr)) return;   // uniform per warp
     const int npad = (int)min((long long)((n + 3) & ~3), off[p + 1] - o);
     const float *s = agg + o;
     const float it = 1.f / tau;
-    if (n <= 32 && (o & 3) == 0 && npad == ((n + 3) & ~3)) {
-        // the window in registers (8 vector loads issued together) and the two output rows written
-        // as vectors; the same operations in the same order as the general form below
-        float v[32];
-        const float4 *r = reinterpret_cast<const float4 *>(s);
-#pragma unroll
-        for (int q = 0; q < 8; q++) {
-            const float4 w = 4 * q < n ? __ldg(r + q) : make_float4(0.f, 0.f, 0.f, 0.f);
-            v[4 * q] = w.x;
-            v[4 * q + 1] = w.y;
-            v[4 * q + 2] = w.z;
-            v[4 * q + 3] = w.w;
-        }
-        float mn = v[0];
-#pragma unroll
-        for (int j = 1; j < 32; j++)
-            if (j < n) mn = fminf(mn, v[j]);
-        float z = 0.f, num = 0.f;
-#pragma unroll
-        for (int j = 0; j < 32; j++)
-            if (j < n) {
-                const float w = expf((mn - v[j]) * it);
-                z += w;
-                num = fmaf(w, (float)j, num);
-            }
-        const float jbar = num / z;
-        const float k = gdisp[p] * (-it) * (float)step / z;
-        float4 *g4 = reinterpret_cast<float4 *>(gCs + o), *c4 = reinterpret_cast<float4 *>(gcost + o);
-#pragma unroll
-        for (int q = 0; q < 8; q++)
-            if (4 * q < npad) {
-                float g[4];
-#pragma unroll
-                for (int e = 0; e < 4; e++) {
-                    const int j = 4 * q + e;
-                    g[e] = j < n ? k * expf((mn - v[j]) * it) * ((float)j - jbar) : 0.f;
-                }
-                g4[q] = make_float4(g[0], g[1], g[2], g[3]);
-                c4[q] = make_float4(0.f, 0.f, 0.f, 0.f);
-            }
-        return;
-    }
-    float mn = s[0];
-    for (int j = 1; j < n; j++) mn = fminf(mn, s[j]);
+    const float INF = __int_as_float(0x7f800000);
+    float mn = INF;
+    for (int j = lane; j < n; j += 32) mn = fminf(mn, __ldg(s + j));
+    asm volatile("redux.sync.min.f32 %0, %1, 0xffffffff;" : "=f"(mn) : "f"(mn));
     // FP32 weights after subtracting the minimum; d_g - dhat = (j - jbar) * step
     float z = 0.f, num = 0.f;
-    for (int j = 0; j < n; j++) {
-        const float w = expf((mn - s[j]) * it);
+    for (int j = lane; j < n; j += 32) {
+        const float w = expf((mn - __ldg(s + j)) * it);
         z += w;
         num = fmaf(w, (float)j, num);
     }
+    z = warp_sum(z);
+    num = warp_sum(num);
     const float jbar = num / z;
     const float k = gdisp[p] * (-it) * (float)step / z;
-    for (int j = 0; j < npad; j++) {
-        float g = 0.f;
-        if (j < n) g = k * expf((mn - s[j]) * it) * ((float)j - jbar);
+    for (int j = lane; j < npad; j += 32) {
+        const float g = j < n ? k * expf((mn - __ldg(s + j)) * it) * ((float)j - jbar) : 0.f;
         gCs[o + j] = g;
         gcost[o + j] = 0.f;
     }
@@ -642,8 +614,8 @@ __global__ void __launch_bounds__(32 * kVrWarps) views_backward_rows_kernel(
                         const float gc0 = gcs[w][j][lane], gc1 = gcs[w][j + 1][lane];
                         const float t1 = t + 1.f;
                         const float e0 = fmaf(t, fmaf(t, cq, b0), a0), e1 = fmaf(t1, fmaf(t1, cq, b0), a0);
-                        const float g0 = e0 < 0.f ? gc0 : (e0 > 0.f ? -gc0 : 0.f);
-                        const float g1 = e1 < 0.f ? gc1 : (e1 > 0.f ? -gc1 : 0.f);
+                        const float g0 = e0 != 0.f ? sign_of_neg(gc0, e0) : 0.f;
+                        const float g1 = e1 != 0.f ? sign_of_neg(gc1, e1) : 0.f;
                         const float gt0 = g0 * t, gt1 = g1 * t1;
                         S0 += g0;
                         S1 += gt0;
@@ -655,7 +627,7 @@ __global__ void __launch_bounds__(32 * kVrWarps) views_backward_rows_kernel(
                     if (j < je) {
                         const float gc = gcs[w][j][lane];
                         const float e = fmaf(t, fmaf(t, cq, b0), a0);        // sample - I_ref
-                        const float g = e < 0.f ? gc : (e > 0.f ? -gc : 0.f);
+                        const float g = e != 0.f ? sign_of_neg(gc, e) : 0.f;
                         const float gt = g * t;
                         S0 += g;
                         S1 += gt;
@@ -665,13 +637,28 @@ __global__ void __launch_bounds__(32 * kVrWarps) views_backward_rows_kernel(
                     S1 += T1;
                     S2 += T2;
                     gref += S0;
-                    // -sum g w for the corners: w11 = XY, w10 = X (1 - Y), w01 = (1 - X) Y, w00 = (1 - X)(1 - Y)
-                    const float GX = fmaf(ax, S1, fx * S0), GY = fmaf(ay, S1, fy * S0);
-                    const float GXY = fmaf(ax * ay, S2, fmaf(fmaf(fx, ay, fy * ax), S1, fx * fy * S0));
-                    add(xa, ya, -(S0 - GX - GY + GXY));
-                    add(xb, ya, -(GX - GXY));
-                    add(xa, yb, -(GY - GXY));
-                    add(xb, yb, -GXY);
+                    if (S0 != 0.f || S1 != 0.f || S2 != 0.f) {
+                        // -sum g w for the corners: w11 = XY, w10 = X (1 - Y), w01 = (1 - X) Y, w00 = (1 - X)(1 - Y)
+                        const float GX = fmaf(ax, S1, fx * S0), GY = fmaf(ay, S1, fy * S0);
+                        const float GXY = fmaf(ax * ay, S2, fmaf(fmaf(fx, ay, fy * ax), S1, fx * fy * S0));
+                        const float v00 = -(S0 - GX - GY + GXY), v10 = -(GX - GXY), v01 = -(GY - GXY), v11 = -GXY;
+                        const int bxa = xa - bx0, bya = ya - by0;
+                        if (use_box && (unsigned)bxa < (unsigned)bw && (unsigned)(xb - bx0) < (unsigned)bw &&
+                            (unsigned)bya < (unsigned)bh && (unsigned)(yb - by0) < (unsigned)bh) {
+                            // the whole cell in the box: four shared-memory adds
+                            float *c00 = box + bya * kVrBoxW + bxa;
+                            const int dxb = xb - xa, dyb = (yb - ya) * kVrBoxW;
+                            atomicAdd(c00, v00);
+                            atomicAdd(c00 + dxb, v10);
+                            atomicAdd(c00 + dyb, v01);
+                            atomicAdd(c00 + dyb + dxb, v11);
+                        } else {
+                            add(xa, ya, v00);
+                            add(xb, ya, v10);
+                            add(xa, yb, v01);
+                            add(xb, yb, v11);
+                        }
+                    }
                 }
                 js = je;
             }
@@ -701,8 +688,8 @@ __global__ void __launch_bounds__(32 * kVrWarps) views_backward_rows_kernel(
 cudaError_t launch_softargmin_backward(cudaStream_t s, const float *agg, const int *lo, const int *cnt,
                                        const long long *off, int N, int G, double dmin, double step, float tau,
                                        const float *gdisp, float *gCs, float *gcost, int *status) {
-    softargmin_backward_kernel<<<(N + 255) / 256, 256, 0, s>>>(agg, lo, cnt, off, N, G, dmin, step, tau, gdisp, gCs,
-                                                               gcost, status);
+    softargmin_backward_kernel<<<(unsigned)(((long long)N * 32 + 255) / 256), 256, 0, s>>>(
+        agg, lo, cnt, off, N, G, dmin, step, tau, gdisp, gCs, gcost, status);
     return cudaGetLastError();
 }
 
