@@ -186,6 +186,26 @@ lfsgm_status lfsgm_backward(lfsgm_handle h, const float *views, const float *cos
                             float P1, float P2, const float *grad_disp, float *grad_cost,
                             float *grad_P1, float *grad_P2, float *grad_views);
 
+/* Training form of the two calls above (not in the paper): lfsgm_sgm_aggregate_record is
+ * lfsgm_sgm_aggregate on explicit penalties 0 <= P1 <= P2 (agg bit-identical to it) that also
+ * records, in the handle's backward scratch, each cell's winning branch of Eq. 9 and each pixel's
+ * argmin slot per direction; lfsgm_backward_recorded is lfsgm_backward on that record and on the
+ * recorded aggregate, so the SGM is not run again.  The record is the handle's last one: it
+ * belongs to the cost, agg, lo, cnt and off pointers and the penalties of the recording call, and
+ * lfsgm_backward_recorded returns LFSGM_ERR_INVALID_ARG (nothing launched) when any of them
+ * differs, or when another lfsgm_sgm_aggregate_record or lfsgm_backward has run on the handle
+ * since.  The caller keeps those buffers unchanged in between (the handle checks the pointers,
+ * not the contents).  Asynchronous on the handle's stream; the backward scratch is allocated on
+ * first use, as by lfsgm_backward. */
+lfsgm_status lfsgm_sgm_aggregate_record(lfsgm_handle h, const float *cost, const int32_t *lo,
+                                        const int32_t *cnt, const int64_t *off, float P1, float P2,
+                                        float *agg);
+lfsgm_status lfsgm_backward_recorded(lfsgm_handle h, const float *views, const float *cost,
+                                     const float *agg, const int32_t *lo, const int32_t *cnt,
+                                     const int64_t *off, float P1, float P2,
+                                     const float *grad_disp, float *grad_cost, float *grad_P1,
+                                     float *grad_P2, float *grad_views);
+
 /* Waits for the handle's stream and returns the latched device status (then clears it). */
 lfsgm_status lfsgm_sync(lfsgm_handle h);
 

@@ -65,7 +65,8 @@ EXPORTS = ["lfsgm_create", "lfsgm_destroy", "lfsgm_workspace_size", "lfsgm_set_w
            "lfsgm_depth", "lfsgm_cost_volume_noalloc", "lfsgm_batch_create", "lfsgm_batch_run",
            "lfsgm_batch_times", "lfsgm_batch_kernel_nodes", "lfsgm_batch_last_error",
            "lfsgm_batch_destroy", "lfsgm_median_filter", "lfsgm_batch_workspace_size", "lfsgm_batch_create_ws",
-           "lfsgm_set_tuning", "lfsgm_batch_knobs", "lfsgm_autotune"]
+           "lfsgm_set_tuning", "lfsgm_batch_knobs", "lfsgm_autotune", "lfsgm_sgm_aggregate_record",
+           "lfsgm_backward_recorded"]
 
 
 def load(build_if_missing: bool = False):
@@ -93,6 +94,8 @@ def load(build_if_missing: bool = False):
         L.lfsgm_sgm_aggregate.argtypes = [vp, vp, vp, vp, vp, f32, f32, vp]
         L.lfsgm_wta_subpixel.argtypes = [vp, vp, vp, vp, vp, vp, vp]
         L.lfsgm_backward.argtypes = [vp, vp, vp, vp, vp, vp, f32, f32, vp, vp, vp, vp, vp]
+        L.lfsgm_sgm_aggregate_record.argtypes = [vp, vp, vp, vp, vp, f32, f32, vp]
+        L.lfsgm_backward_recorded.argtypes = [vp, vp, vp, vp, vp, vp, vp, f32, f32, vp, vp, vp, vp, vp]
         L.lfsgm_sync.argtypes = [vp]
         L.lfsgm_last_error.argtypes = [vp]
         L.lfsgm_last_error.restype = C.c_char_p
@@ -239,6 +242,27 @@ def lfsgm_backward(h, views, cost, lo, cnt, off, P1, P2, grad_disp, grad_cost, g
                                  _ptr(grad_disp, f, "grad_disp"), _ptr(grad_cost, f, "grad_cost"),
                                  _ptr(grad_P1, f, "grad_P1"), _ptr(grad_P2, f, "grad_P2"),
                                  _ptr(grad_views, f, "grad_views")), h)
+
+
+def lfsgm_sgm_aggregate_record(h, cost, lo, cnt, off, P1, P2, agg):
+    """lfsgm_sgm_aggregate on explicit penalties that also records the branches for
+    lfsgm_backward_recorded."""
+    import torch
+    _check(load().lfsgm_sgm_aggregate_record(h, _ptr(cost, torch.float32, "cost"), _ptr(lo, torch.int32, "lo"),
+                                             _ptr(cnt, torch.int32, "cnt"), _ptr(off, torch.int64, "off"),
+                                             float(P1), float(P2), _ptr(agg, torch.float32, "agg")), h)
+
+
+def lfsgm_backward_recorded(h, views, cost, agg, lo, cnt, off, P1, P2, grad_disp, grad_cost, grad_P1, grad_P2,
+                            grad_views=None):
+    import torch
+    f = torch.float32
+    _check(load().lfsgm_backward_recorded(h, _ptr(views, f, "views"), _ptr(cost, f, "cost"), _ptr(agg, f, "agg"),
+                                          _ptr(lo, torch.int32, "lo"), _ptr(cnt, torch.int32, "cnt"),
+                                          _ptr(off, torch.int64, "off"), float(P1), float(P2),
+                                          _ptr(grad_disp, f, "grad_disp"), _ptr(grad_cost, f, "grad_cost"),
+                                          _ptr(grad_P1, f, "grad_P1"), _ptr(grad_P2, f, "grad_P2"),
+                                          _ptr(grad_views, f, "grad_views")), h)
 
 
 def lfsgm_median_filter(h, disp, out):
@@ -454,23 +478,24 @@ def _autograd():
         @staticmethod
         def forward(ctx, cost, P1, P2, L):
             p1, p2 = float(P1), float(P2)
+            cost = cost.contiguous()
             agg = torch.empty_like(cost)
-            lfsgm_sgm_aggregate(L.h, cost, L.lo, L.cnt, L.off, p1, p2, agg)
+            lfsgm_sgm_aggregate_record(L.h, cost, L.lo, L.cnt, L.off, p1, p2, agg)
+            L.recorded = (cost.data_ptr(), agg.data_ptr(), (p1, p2))
             disp = torch.empty(L.N, dtype=torch.float32, device=cost.device)
             lfsgm_wta_subpixel(L.h, agg, L.lo, L.cnt, L.off, None, disp)
-            ctx.save_for_backward(cost)
+            ctx.save_for_backward(cost, agg)
             ctx.pen, ctx.L = (p1, p2), L
             return disp
 
         @staticmethod
         def backward(ctx, gdisp):
-            (cost,) = ctx.saved_tensors
+            cost, agg = ctx.saved_tensors
             L = ctx.L
             gcost = torch.empty_like(cost)
             gp = torch.zeros(2, dtype=torch.float32, device=cost.device)
-            lfsgm_backward(L.h, None, cost, L.lo, L.cnt, L.off, ctx.pen[0], ctx.pen[1], gdisp.contiguous(), gcost,
-                           gp[0:1], gp[1:2], None)
-            return gcost, gp[0], gp[1], None
+            _backward_saved(L, None, cost, agg, ctx.pen, gdisp.contiguous(), gcost, gp, None)
+            return _needed(ctx, gcost, gp[0], gp[1])
 
     class DepthFromViews(torch.autograd.Function):
         """disp = soft-argmin(SGM(cost_volume(views); P1, P2)) on the windows held by ``L``;
@@ -480,27 +505,43 @@ def _autograd():
         def forward(ctx, views, P1, P2, L):
             p1, p2 = float(P1), float(P2)
             L.cost_volume(views)
-            cost = L.cost
+            cost = L.cost.clone()            # L.cost is overwritten by the next forward
             agg = torch.empty_like(cost)
-            lfsgm_sgm_aggregate(L.h, cost, L.lo, L.cnt, L.off, p1, p2, agg)
+            lfsgm_sgm_aggregate_record(L.h, cost, L.lo, L.cnt, L.off, p1, p2, agg)
+            L.recorded = (cost.data_ptr(), agg.data_ptr(), (p1, p2))
             disp = torch.empty(L.N, dtype=torch.float32, device=views.device)
             lfsgm_wta_subpixel(L.h, agg, L.lo, L.cnt, L.off, None, disp)
-            ctx.save_for_backward(views, cost.clone())
+            ctx.save_for_backward(views, cost, agg)
             ctx.pen, ctx.L = (p1, p2), L
             return disp
 
         @staticmethod
         def backward(ctx, gdisp):
-            views, cost = ctx.saved_tensors
+            views, cost, agg = ctx.saved_tensors
             L = ctx.L
             gcost = torch.empty_like(cost)
             gviews = torch.empty_like(views)
             gp = torch.zeros(2, dtype=torch.float32, device=views.device)
-            lfsgm_backward(L.h, views, cost, L.lo, L.cnt, L.off, ctx.pen[0], ctx.pen[1], gdisp.contiguous(), gcost,
-                           gp[0:1], gp[1:2], gviews)
-            return gviews, gp[0], gp[1], None
+            _backward_saved(L, views, cost, agg, ctx.pen, gdisp.contiguous(), gcost, gp, gviews)
+            return _needed(ctx, gviews, gp[0], gp[1])
 
     return SGMSoftArgmin, DepthFromViews
+
+
+def _needed(ctx, *grads):
+    """The gradients of the inputs that want one (plain-number penalties get None)."""
+    return tuple(g if need else None for g, need in zip(grads, ctx.needs_input_grad)) + (None,)
+
+
+def _backward_saved(L, views, cost, agg, pen, gdisp, gcost, gp, gviews):
+    """The backward on the forward's record when it is still the handle's last one (one handle
+    records one forward at a time), else with the SGM recomputed."""
+    if L.recorded == (cost.data_ptr(), agg.data_ptr(), pen):
+        lfsgm_backward_recorded(L.h, views, cost, agg, L.lo, L.cnt, L.off, pen[0], pen[1], gdisp, gcost, gp[0:1],
+                                gp[1:2], gviews)
+    else:
+        lfsgm_backward(L.h, views, cost, L.lo, L.cnt, L.off, pen[0], pen[1], gdisp, gcost, gp[0:1], gp[1:2], gviews)
+        L.recorded = None             # lfsgm_backward records over the handle's scratch
 
 
 def sgm_softargmin(cost, P1, P2, L):
@@ -524,6 +565,7 @@ class LightFieldDepth:
         self.device = torch.device(device)
         self.stream = stream or torch.cuda.current_stream(self.device)
         self.h = lfsgm_create(params, self.stream)
+        self.recorded = None          # (cost, agg, penalties) of the handle's SGM record, if still valid
         N = params.H * params.W
         self.N = N
         self.max_nnz = lfsgm_max_nnz(self.h)

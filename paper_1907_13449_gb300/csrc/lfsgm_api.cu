@@ -106,6 +106,14 @@ struct lfsgm_ctx {
     float *b_agg = nullptr, *b_gcs = nullptr, *b_gp = nullptr;
     unsigned char *b_codes = nullptr;
     int *b_amin = nullptr;
+    // what the branch codes and argmin slots were recorded from (lfsgm_sgm_aggregate_record)
+    struct {
+        bool valid = false;
+        const float *cost = nullptr, *agg = nullptr;
+        const int32_t *lo = nullptr, *cnt = nullptr;
+        const int64_t *off = nullptr;
+        float P1 = 0.f, P2 = 0.f;
+    } rec;
     // accounting
     long long launches = 0;
     bool profiling = false;
@@ -719,48 +727,57 @@ lfsgm_status lfsgm_median_filter(lfsgm_handle h, const float *disp, float *out) 
     return run(h, "median_filter", [&] { return launch_median3(h->stream, disp, out, h->cfg.H, h->cfg.W); });
 }
 
-lfsgm_status lfsgm_backward(lfsgm_handle h, const float *views, const float *cost, const int32_t *lo,
-                            const int32_t *cnt, const int64_t *off, float P1, float P2, const float *grad_disp,
-                            float *grad_cost, float *grad_P1, float *grad_P2, float *grad_views) {
-    if (!h) return LFSGM_ERR_INVALID_ARG;
-    if (!cost || !lo || !cnt || !off || !grad_disp || !grad_cost || !grad_P1 || !grad_P2 || (grad_views && !views))
-        return fail(h, LFSGM_ERR_INVALID_ARG, "null buffer");
-    if (!aligned16(cost) || !aligned16(grad_cost))
-        return fail(h, LFSGM_ERR_INVALID_ARG, "cost and grad_cost must be 16-byte aligned");
-    if (!(P1 >= 0.f && P2 >= P1 && std::isfinite(P2)))
-        return fail(h, LFSGM_ERR_INVALID_ARG, "backward needs explicit penalties 0 <= P1 <= P2, got %g %g", P1, P2);
-    LFSGM_TRY(ensure_workspace(h));
-    const lfsgm_config &c = h->cfg;
-    cudaStream_t s = h->stream;
-    const size_t N = (size_t)h->N;
+static lfsgm_status backward_scratch(lfsgm_handle h) {
+    if (h->b_agg) return LFSGM_OK;
     int64_t cap = 0;
     lfsgm_max_nnz(h, &cap);
-    if (!h->b_agg) {
-        cudaError_t e = cudaMalloc((void **)&h->b_agg, (size_t)cap * 4);
-        if (e == cudaSuccess) e = cudaMalloc((void **)&h->b_gcs, (size_t)cap * 4);
-        if (e == cudaSuccess) e = cudaMalloc((void **)&h->b_codes, (size_t)cap * c.paths);
-        if (e == cudaSuccess) e = cudaMalloc((void **)&h->b_amin, N * (size_t)c.paths * 4);
-        if (e == cudaSuccess) e = cudaMalloc((void **)&h->b_gp, 2 * 4);
-        if (e != cudaSuccess) return fail(h, LFSGM_ERR_NO_MEMORY, "backward scratch: %s", cudaGetErrorString(e));
-    }
+    cudaError_t e = cudaMalloc((void **)&h->b_agg, (size_t)cap * 4);
+    if (e == cudaSuccess) e = cudaMalloc((void **)&h->b_gcs, (size_t)cap * 4);
+    if (e == cudaSuccess) e = cudaMalloc((void **)&h->b_codes, (size_t)cap * h->cfg.paths);
+    if (e == cudaSuccess) e = cudaMalloc((void **)&h->b_amin, (size_t)h->N * h->cfg.paths * 4);
+    if (e == cudaSuccess) e = cudaMalloc((void **)&h->b_gp, 2 * 4);
+    if (e != cudaSuccess) return fail(h, LFSGM_ERR_NO_MEMORY, "backward scratch: %s", cudaGetErrorString(e));
+    return LFSGM_OK;
+}
+
+// The SGM of Eq. 8-9 on explicit penalties into agg, recording each cell's winning branch and each
+// pixel's argmin slot per direction into the handle's backward scratch.
+static lfsgm_status aggregate_recording(lfsgm_handle h, const float *cost, const int32_t *lo, const int32_t *cnt,
+                                        const int64_t *off, float P1, float P2, float *agg) {
+    const lfsgm_config &c = h->cfg;
+    cudaStream_t s = h->stream;
     const long long *o = (const long long *)off;
-    const double step = (c.dmax - c.dmin) / (double)(c.fine_labels - 1);
-    // aggregate (the forward of the SGM, recomputed), recording each cell's winning branch and each
-    // pixel's argmin slot per direction for the adjoint
+    int64_t cap = 0;
+    lfsgm_max_nnz(h, &cap);
+    h->rec.valid = false;
     LFSGM_TRY(run(h, "set_penalties", [&] {
         set_pen_kernel<<<1, 1, 0, s>>>(h->fpen, P1, P2);
         return cudaGetLastError();
     }));
     LFSGM_TRY(run(h, "zero_agg", [&] {
-        zero_csr_kernel<<<1216, 256, 0, s>>>(h->b_agg, o, h->N);
+        zero_csr_kernel<<<1216, 256, 0, s>>>(agg, o, h->N);
         return cudaGetLastError();
     }));
-    LFSGM_TRY(run(h, "fine_sgm_record", [&] {
-        return launch_fine_sgm(s, cost, lo, cnt, o, c.H, c.W, c.fine_labels, h->fpen, h->b_agg, h->status,
-                               h->d_order, c.paths, h->b_codes, h->b_amin, (size_t)cap);
-    }));
+    return run(h, "fine_sgm_record", [&] {
+        return launch_fine_sgm(s, cost, lo, cnt, o, c.H, c.W, c.fine_labels, h->fpen, agg, h->status, h->d_order,
+                               c.paths, h->b_codes, h->b_amin, (size_t)cap);
+    });
+}
+
+// soft-argmin adjoint, SGM adjoint on the recorded branches, l2 term -> views
+static lfsgm_status backward_from_record(lfsgm_handle h, const float *views, const float *cost, const float *agg,
+                                         const int32_t *lo, const int32_t *cnt, const int64_t *off, float P1,
+                                         float P2, const float *grad_disp, float *grad_cost, float *grad_P1,
+                                         float *grad_P2, float *grad_views) {
+    const lfsgm_config &c = h->cfg;
+    cudaStream_t s = h->stream;
+    const size_t N = (size_t)h->N;
+    int64_t cap = 0;
+    lfsgm_max_nnz(h, &cap);
+    const long long *o = (const long long *)off;
+    const double step = (c.dmax - c.dmin) / (double)(c.fine_labels - 1);
     LFSGM_TRY(run(h, "softargmin_backward", [&] {
-        return launch_softargmin_backward(s, h->b_agg, lo, cnt, o, h->N, c.fine_labels, c.dmin, step, c.softmin_tau,
+        return launch_softargmin_backward(s, agg, lo, cnt, o, h->N, c.fine_labels, c.dmin, step, c.softmin_tau,
                                           grad_disp, h->b_gcs, grad_cost, h->status);
     }));
     cudaError_t e = cudaMemsetAsync(h->b_gp, 0, 8, s);
@@ -782,8 +799,8 @@ lfsgm_status lfsgm_backward(lfsgm_handle h, const float *views, const float *cos
         }));
         LFSGM_TRY(run(h, "views_backward", [&] {
             return launch_views_backward(s, views, h->d_fine, c.fine_labels, c.U, c.V, h->C, c.H, c.W, h->ref, lo,
-                                         cnt, o, c.w_l2, (float)((c.dmax - c.dmin) / (double)(c.fine_labels - 1)),
-                                         grad_cost, grad_views, h->wide_list, h->wide_count);
+                                         cnt, o, c.w_l2, (float)step, grad_cost, grad_views, h->wide_list,
+                                         h->wide_count);
         }));
         if (h->C == 1)
             LFSGM_TRY(run(h, "views_backward_list", [&] {
@@ -795,6 +812,67 @@ lfsgm_status lfsgm_backward(lfsgm_handle h, const float *views, const float *cos
     if (e == cudaSuccess) e = cudaMemcpyAsync(grad_P2, h->b_gp + 1, 4, cudaMemcpyDeviceToDevice, s);
     if (e != cudaSuccess) return cuda_fail(h, e, "penalty gradients");
     return LFSGM_OK;
+}
+
+static bool penalties_ok(float P1, float P2) { return P1 >= 0.f && P2 >= P1 && std::isfinite(P2); }
+
+lfsgm_status lfsgm_sgm_aggregate_record(lfsgm_handle h, const float *cost, const int32_t *lo, const int32_t *cnt,
+                                        const int64_t *off, float P1, float P2, float *agg) {
+    if (!h) return LFSGM_ERR_INVALID_ARG;
+    if (!cost || !lo || !cnt || !off || !agg) return fail(h, LFSGM_ERR_INVALID_ARG, "null buffer");
+    if (!aligned16(cost) || !aligned16(agg)) return fail(h, LFSGM_ERR_INVALID_ARG, "cost and agg must be 16-byte aligned");
+    if (!penalties_ok(P1, P2))
+        return fail(h, LFSGM_ERR_INVALID_ARG, "recording needs explicit penalties 0 <= P1 <= P2, got %g %g", P1, P2);
+    LFSGM_TRY(ensure_workspace(h));
+    LFSGM_TRY(backward_scratch(h));
+    LFSGM_TRY(aggregate_recording(h, cost, lo, cnt, off, P1, P2, agg));
+    h->rec.valid = true;
+    h->rec.cost = cost;
+    h->rec.agg = agg;
+    h->rec.lo = lo;
+    h->rec.cnt = cnt;
+    h->rec.off = off;
+    h->rec.P1 = P1;
+    h->rec.P2 = P2;
+    return LFSGM_OK;
+}
+
+lfsgm_status lfsgm_backward(lfsgm_handle h, const float *views, const float *cost, const int32_t *lo,
+                            const int32_t *cnt, const int64_t *off, float P1, float P2, const float *grad_disp,
+                            float *grad_cost, float *grad_P1, float *grad_P2, float *grad_views) {
+    if (!h) return LFSGM_ERR_INVALID_ARG;
+    if (!cost || !lo || !cnt || !off || !grad_disp || !grad_cost || !grad_P1 || !grad_P2 || (grad_views && !views))
+        return fail(h, LFSGM_ERR_INVALID_ARG, "null buffer");
+    if (!aligned16(cost) || !aligned16(grad_cost))
+        return fail(h, LFSGM_ERR_INVALID_ARG, "cost and grad_cost must be 16-byte aligned");
+    if (!penalties_ok(P1, P2))
+        return fail(h, LFSGM_ERR_INVALID_ARG, "backward needs explicit penalties 0 <= P1 <= P2, got %g %g", P1, P2);
+    LFSGM_TRY(ensure_workspace(h));
+    LFSGM_TRY(backward_scratch(h));
+    // the forward of the SGM recomputed into the handle's own aggregate, with its record
+    LFSGM_TRY(aggregate_recording(h, cost, lo, cnt, off, P1, P2, h->b_agg));
+    return backward_from_record(h, views, cost, h->b_agg, lo, cnt, off, P1, P2, grad_disp, grad_cost, grad_P1,
+                                grad_P2, grad_views);
+}
+
+lfsgm_status lfsgm_backward_recorded(lfsgm_handle h, const float *views, const float *cost, const float *agg,
+                                     const int32_t *lo, const int32_t *cnt, const int64_t *off, float P1, float P2,
+                                     const float *grad_disp, float *grad_cost, float *grad_P1, float *grad_P2,
+                                     float *grad_views) {
+    if (!h) return LFSGM_ERR_INVALID_ARG;
+    if (!cost || !agg || !lo || !cnt || !off || !grad_disp || !grad_cost || !grad_P1 || !grad_P2 ||
+        (grad_views && !views))
+        return fail(h, LFSGM_ERR_INVALID_ARG, "null buffer");
+    if (!aligned16(cost) || !aligned16(grad_cost))
+        return fail(h, LFSGM_ERR_INVALID_ARG, "cost and grad_cost must be 16-byte aligned");
+    const auto &r = h->rec;
+    if (!r.valid || r.cost != cost || r.agg != agg || r.lo != lo || r.cnt != cnt || r.off != off || r.P1 != P1 ||
+        r.P2 != P2)
+        return fail(h, LFSGM_ERR_INVALID_ARG,
+                    "no record of lfsgm_sgm_aggregate_record on these cost, agg, window buffers and penalties");
+    LFSGM_TRY(ensure_workspace(h));
+    return backward_from_record(h, views, cost, agg, lo, cnt, off, P1, P2, grad_disp, grad_cost, grad_P1, grad_P2,
+                                grad_views);
 }
 
 lfsgm_status lfsgm_sync(lfsgm_handle h) {

@@ -52,8 +52,9 @@ def _gpu_holder(lf, p, lo, cnt):
     return L
 
 
-def _run_gpu_backward(lf, p, views, lo, cnt, P1, P2, gd, tau):
-    """dLoss/dcost (active slots), dP1, dP2, dLoss/dviews from the library."""
+def _run_gpu_backward(lf, p, views, lo, cnt, P1, P2, gd, tau, recorded=False):
+    """dLoss/dcost (active slots), dP1, dP2, dLoss/dviews from the library: lfsgm_backward, or with
+    recorded=True the training form (lfsgm_sgm_aggregate_record, then lfsgm_backward_recorded)."""
     import torch
     L = _gpu_holder(lf, p, lo, cnt)
     vd = torch.from_numpy(views).cuda()
@@ -62,8 +63,13 @@ def _run_gpu_backward(lf, p, views, lo, cnt, P1, P2, gd, tau):
     gviews = torch.empty_like(vd)
     g1 = torch.zeros(1, device="cuda")
     g2 = torch.zeros(1, device="cuda")
-    lf.lfsgm_backward(L.h, vd, L.cost, L.lo, L.cnt, L.off, float(P1), float(P2), torch.from_numpy(gd).cuda(),
-                      gcost, g1, g2, gviews)
+    if recorded:
+        lf.lfsgm_sgm_aggregate_record(L.h, L.cost, L.lo, L.cnt, L.off, float(P1), float(P2), L.agg)
+        lf.lfsgm_backward_recorded(L.h, vd, L.cost, L.agg, L.lo, L.cnt, L.off, float(P1), float(P2),
+                                   torch.from_numpy(gd).cuda(), gcost, g1, g2, gviews)
+    else:
+        lf.lfsgm_backward(L.h, vd, L.cost, L.lo, L.cnt, L.off, float(P1), float(P2), torch.from_numpy(gd).cuda(),
+                          gcost, g1, g2, gviews)
     lf.lfsgm_sync(L.h)
     gC = gather(gcost.cpu().numpy(), pad4_offsets(cnt), cnt)
     out = gC, g1.item(), g2.item(), gviews.cpu().numpy()
@@ -85,13 +91,14 @@ def _penalties(cost_o):
     return np.float32(0.05 * cost_o.mean()), np.float32(0.5 * cost_o.mean())
 
 
-def test_backward_matches_oracle_adjoint(gpu_lib):
+@pytest.mark.parametrize("recorded", [False, True], ids=["recompute", "recorded"])
+def test_backward_matches_oracle_adjoint(gpu_lib, recorded):
     p, views, lo, cnt, gd = _setup()
     cfg = oracle.make_cfg(p)
     off_o, cost_o = oracle.cost_volume(cfg, views, lo, cnt)
     P1, P2 = _penalties(cost_o)
     gC_o, g1_o, g2_o, gV_o = oracle.backward(cfg, views, lo, cnt, cost_o, float(P1), float(P2), gd, TAU)
-    gC, g1, g2, gV = _run_gpu_backward(gpu_lib, p, views, lo, cnt, P1, P2, gd, TAU)
+    gC, g1, g2, gV = _run_gpu_backward(gpu_lib, p, views, lo, cnt, P1, P2, gd, TAU, recorded)
     eC, eV = _elem_errors(p, cnt, gC, gC_o, gV, gV_o)
     tol = grad_tol(_cs_max(p, lo, cnt, off_o, cost_o, P1, P2), TAU)
     print(f"backward 7x7x32x32 tau 0.1, bar {tol:.2e}, needed relative tolerance: dcost", err_stats(eC),
@@ -150,9 +157,12 @@ def _ragged_case(kind, seed=77):
     return p, views, lo, cnt, gd
 
 
-@pytest.mark.parametrize("kind", ["mixed", "wide_range", "mixed_16_paths"])
+@pytest.mark.parametrize("kind", ["mixed", "wide_range", "mixed_16_paths", "mixed_recorded",
+                                  "mixed_16_paths_recorded"])
 def test_backward_ragged_windows_match_oracle(gpu_lib, kind):
     import dataclasses
+    recorded = kind.endswith("_recorded")
+    kind = kind.replace("_recorded", "")
     p, views, lo, cnt, gd = _ragged_case(kind.replace("_16_paths", ""))
     if kind.endswith("16_paths"):
         p = dataclasses.replace(p, paths=16)
@@ -160,7 +170,7 @@ def test_backward_ragged_windows_match_oracle(gpu_lib, kind):
     off_o, cost_o = oracle.cost_volume(cfg, views, lo, cnt)
     P1, P2 = _penalties(cost_o)
     gC_o, g1_o, g2_o, gV_o = oracle.backward(cfg, views, lo, cnt, cost_o, float(P1), float(P2), gd, TAU)
-    gC, g1, g2, gV = _run_gpu_backward(gpu_lib, p, views, lo, cnt, P1, P2, gd, TAU)
+    gC, g1, g2, gV = _run_gpu_backward(gpu_lib, p, views, lo, cnt, P1, P2, gd, TAU, recorded)
     eC, eV = _elem_errors(p, cnt, gC, gC_o, gV, gV_o)
     tol = grad_tol(_cs_max(p, lo, cnt, off_o, cost_o, P1, P2), TAU)
     print(f"backward ragged {kind}, bar {tol:.2e}, needed relative tolerance: dcost", err_stats(eC),
@@ -195,18 +205,19 @@ def test_backward_bench_band_matches_oracle(gpu_lib):
     P1, P2 = _penalties(cost_o)
     gd = np.random.default_rng(11).normal(size=p.N).astype(np.float32)
     gC_o, g1_o, g2_o, gV_o = oracle.backward(cfg, band, lo, cnt, cost_o, float(P1), float(P2), gd, TAU)
-    gC, g1, g2, gV = _run_gpu_backward(gpu_lib, p, band, lo, cnt, P1, P2, gd, TAU)
-    eC, eV = _elem_errors(p, cnt, gC, gC_o, gV, gV_o)
     tol = grad_tol(_cs_max(p, lo, cnt, off_o, cost_o, P1, P2), TAU)
-    print(f"backward bench band, bar {tol:.2e}, needed relative tolerance: dcost", err_stats(eC), "dviews",
-          err_stats(eV), "beyond the bar:", int((eC > tol).sum()), int((eV > tol).sum()),
-          "dP1", g1, g1_o, "dP2", g2, g2_o)
-    for e, g, o in ((eC, gC, gC_o), (eV, gV, gV_o)):
-        assert np.mean(e > tol) <= 1e-4, err_stats(e)
-        assert np.abs(g.astype(np.float64).reshape(-1) - o.reshape(-1)).sum() <= 1e-3 * np.abs(o).sum()
-    mass = GRAD_MASS / GRAD_TOL_P * np.abs(gC_o).sum()
-    assert abs(g1 - g1_o) <= GRAD_TOL_P * (abs(g1_o) + mass), (g1, g1_o, mass)
-    assert abs(g2 - g2_o) <= GRAD_TOL_P * (abs(g2_o) + mass), (g2, g2_o, mass)
+    for recorded in (False, True):
+        gC, g1, g2, gV = _run_gpu_backward(gpu_lib, p, band, lo, cnt, P1, P2, gd, TAU, recorded)
+        eC, eV = _elem_errors(p, cnt, gC, gC_o, gV, gV_o)
+        print(f"backward bench band (recorded {recorded}), bar {tol:.2e}, needed relative tolerance: dcost",
+              err_stats(eC), "dviews", err_stats(eV), "beyond the bar:", int((eC > tol).sum()),
+              int((eV > tol).sum()), "dP1", g1, g1_o, "dP2", g2, g2_o)
+        for e, g, o in ((eC, gC, gC_o), (eV, gV, gV_o)):
+            assert np.mean(e > tol) <= 1e-4, err_stats(e)
+            assert np.abs(g.astype(np.float64).reshape(-1) - o.reshape(-1)).sum() <= 1e-3 * np.abs(o).sum()
+        mass = GRAD_MASS / GRAD_TOL_P * np.abs(gC_o).sum()
+        assert abs(g1 - g1_o) <= GRAD_TOL_P * (abs(g1_o) + mass), (g1, g1_o, mass)
+        assert abs(g2 - g2_o) <= GRAD_TOL_P * (abs(g2_o) + mass), (g2, g2_o, mass)
 
 
 def test_autograd_functions_match_direct_call(gpu_lib):
@@ -270,4 +281,98 @@ def test_backward_bench_shape_invariants(gpu_lib):
     # amplified by C_s / tau, so residuals of order n * eps_32 ~ 3e-5 of the global scale occur
     # (observed 0.9e-5 .. 1.7e-5)
     assert np.abs(sums).max() <= 1e-4 * scale.max(), (np.abs(sums).max(), scale.max())
+    L.close()
+
+
+def test_recorded_aggregate_and_backward_agree_with_the_plain_calls(gpu_lib):
+    """lfsgm_sgm_aggregate_record writes the same aggregate as lfsgm_sgm_aggregate, bit for bit, and
+    lfsgm_backward_recorded gives lfsgm_backward's gradients: the same kernels on the same branch
+    record, up to the order of the atomic additions into dLoss/dcost and dLoss/dviews."""
+    import torch
+    p, views, lo, cnt, gd = _ragged_case("mixed", seed=5)
+    L = _gpu_holder(gpu_lib, p, lo, cnt)
+    vd = torch.from_numpy(views).cuda()
+    L.cost_volume(vd)
+    P1, P2 = 0.2, 1.7
+    agg_plain = torch.empty_like(L.cost)
+    gpu_lib.lfsgm_sgm_aggregate(L.h, L.cost, L.lo, L.cnt, L.off, P1, P2, agg_plain)
+    gpu_lib.lfsgm_sgm_aggregate_record(L.h, L.cost, L.lo, L.cnt, L.off, P1, P2, L.agg)
+    nnz = int(L.off[-1].item())
+    assert torch.equal(agg_plain[:nnz], L.agg[:nnz])
+    g = torch.from_numpy(gd).cuda()
+    out = []
+    for recorded in (True, False):
+        gcost = torch.zeros_like(L.cost)
+        gviews = torch.empty_like(vd)
+        gp = torch.zeros(2, device="cuda")
+        if recorded:
+            gpu_lib.lfsgm_backward_recorded(L.h, vd, L.cost, L.agg, L.lo, L.cnt, L.off, P1, P2, g, gcost, gp[0:1],
+                                            gp[1:2], gviews)
+        else:
+            gpu_lib.lfsgm_backward(L.h, vd, L.cost, L.lo, L.cnt, L.off, P1, P2, g, gcost, gp[0:1], gp[1:2], gviews)
+        gpu_lib.lfsgm_sync(L.h)
+        out.append((gcost[:nnz].double(), gviews.double(), gp.double()))
+    for a, b in zip(out[0], out[1]):
+        assert (a - b).abs().max().item() <= 1e-5 * max(b.abs().max().item(), 1e-30), (a - b).abs().max()
+    L.close()
+
+
+def test_recorded_backward_refuses_a_stale_record(gpu_lib):
+    """lfsgm_backward_recorded returns an error, and launches nothing, unless the handle's last
+    record was taken on the same buffers and penalties (another recording or an lfsgm_backward
+    in between replaces it)."""
+    import torch
+    p, views, lo, cnt, gd = _setup(seed=3)
+    L = _gpu_holder(gpu_lib, p, lo, cnt)
+    vd = torch.from_numpy(views).cuda()
+    L.cost_volume(vd)
+    g = torch.from_numpy(gd).cuda()
+    gcost = torch.empty_like(L.cost)
+    gp = torch.zeros(2, device="cuda")
+    other = L.cost.clone()
+
+    def recorded(cost=None, agg=None, P1=0.3, P2=2.5):
+        gpu_lib.lfsgm_backward_recorded(L.h, None, L.cost if cost is None else cost, L.agg if agg is None else agg,
+                                        L.lo, L.cnt, L.off, P1, P2, g, gcost, gp[0:1], gp[1:2], None)
+
+    with pytest.raises(RuntimeError):
+        recorded()                                    # nothing recorded yet
+    gpu_lib.lfsgm_sgm_aggregate_record(L.h, L.cost, L.lo, L.cnt, L.off, 0.3, 2.5, L.agg)
+    n0 = gpu_lib.lfsgm_launch_count(L.h)
+    for kw in ({"P1": 0.31}, {"P2": 2.4}, {"cost": other}, {"agg": torch.empty_like(L.agg)}):
+        with pytest.raises(RuntimeError):
+            recorded(**kw)
+    assert gpu_lib.lfsgm_launch_count(L.h) == n0
+    recorded()
+    recorded()                                        # the record survives its backward
+    gpu_lib.lfsgm_backward(L.h, None, L.cost, L.lo, L.cnt, L.off, 0.3, 2.5, g, gcost, gp[0:1], gp[1:2], None)
+    with pytest.raises(RuntimeError):
+        recorded()                                    # lfsgm_backward recorded over it
+    gpu_lib.lfsgm_sync(L.h)
+    L.close()
+
+
+def test_autograd_interleaved_forwards_fall_back_to_recompute(gpu_lib):
+    """Two forwards on one handle before their backwards: the second forward's record replaces the
+    first's, so the first backward recomputes the SGM; both match a single forward + backward."""
+    import torch
+    p, views, lo, cnt, gd = _setup(seed=9)
+    L = _gpu_holder(gpu_lib, p, lo, cnt)
+    vd = torch.from_numpy(views).cuda()
+    L.cost_volume(vd)
+    g = torch.from_numpy(gd).cuda()
+    grads = []
+    for pen in ((0.3, 2.5), (0.2, 1.5)):
+        c = L.cost.clone().requires_grad_(True)
+        (gpu_lib.sgm_softargmin(c, *pen, L) * g).sum().backward()
+        grads.append(c.grad)
+    c1 = L.cost.clone().requires_grad_(True)
+    c2 = L.cost.clone().requires_grad_(True)
+    d1 = gpu_lib.sgm_softargmin(c1, 0.3, 2.5, L)
+    d2 = gpu_lib.sgm_softargmin(c2, 0.2, 1.5, L)
+    (d1 * g).sum().backward()                         # record of d2 on the handle: recomputes
+    (d2 * g).sum().backward()                         # its own record was replaced: recomputes
+    nnz = int(L.off[-1].item())
+    for a, b in ((c1.grad, grads[0]), (c2.grad, grads[1])):
+        assert (a[:nnz] - b[:nnz]).abs().max().item() <= 1e-5 * b[:nnz].abs().max().item()
     L.close()
