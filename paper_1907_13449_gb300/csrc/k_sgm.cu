@@ -6,9 +6,10 @@
 // alignment (slot i = lo(p) + j - lo(p-r)) is three shuffles with bounds checks: labels outside
 // the predecessor's window are absent from the minimum (Sec. III-E).  Wider windows take the
 // general form with L' in a per-warp shared-memory row (chunks of 32 slots).  Window metadata
-// is fetched 32 pixels at a time (one per lane, the next block one block ahead); a ballot over a
-// block finds the steps that need the general form, and the narrow steps between them run in a
-// tight loop with the next cost row one step ahead.  The step is the
+// is fetched 32 pixels at a time (one per lane, the next block one block ahead) and also kept in a
+// per-warp ring of 64 steps in shared memory; a ballot over a block finds the steps that need the
+// general form, and the narrow steps between them run in a tight loop that reads the next step's
+// metadata from the ring (one broadcast load) and its cost row one step ahead.  The step is the
 // normalised recurrence
 //   L(p,g) = C(p,g) + (min(L'(g), L'(g-1)+P1, L'(g+1)+P1, m+P2) - m),   m = min L',
 // and the predecessor minimum m is one redux.sync.min.f32 per pixel.  The 8 or 16 directions run
@@ -80,6 +81,9 @@ __global__ void __launch_bounds__(32 * kSgmWarps) fine_sgm_kernel(const float *_
     // rows by slot with one sentinel slot on each side (slot -1 and slot n hold +inf), Gs + 2 floats
     float *bufA = sm + (size_t)wib * 2 * (Gs + 2) + 1;   // predecessor's path costs, general steps
     float *bufB = bufA + (Gs + 2);                       // this pixel's
+    // the metadata of this block of 32 steps and the next one, by step mod 64 (read by the narrow
+    // steps with one broadcast load)
+    int2 *meta = reinterpret_cast<int2 *>(sm + (size_t)kSgmWarps * 2 * (Gs + 2)) + wib * 64;
     const float P1 = __ldg(pen), P2 = __ldg(pen + 1);
     const float INF = __int_as_float(0x7f800000);
     if (lane == 0) {
@@ -108,6 +112,9 @@ __global__ void __launch_bounds__(32 * kSgmWarps) fine_sgm_kernel(const float *_
     int cw, co, nw = 0, no = 0;                // this block's and the next block's metadata
     fetch(0, cw, co);
     if (len > 32) fetch(32, nw, no);
+    meta[lane] = make_int2(cw, co);
+    meta[32 + lane] = make_int2(nw, no);
+    __syncwarp();
     int plo = 0, pn = 0;                       // predecessor window; pn = 0: the path (re)starts
     float prev = INF, m = 0.f;                 // predecessor row (one slot per lane) and its minimum
     bool in_smem = false;                      // the predecessor row is in bufA (after a general step)
@@ -128,15 +135,14 @@ __global__ void __launch_bounds__(32 * kSgmWarps) fine_sgm_kernel(const float *_
             int l = win & 0xffff, n = win >> 16;
             float c = lane < n ? __ldg(cost + 4ll * ofs + lane) : 0.f;
             for (; k < kend; k++) {
-                const int src = k + 1 - kb;     // 1 .. 32: the next step's lane in this or the next block
-                int win1 = 0, ofs1 = 0;
-                if (k + 1 < len) {
-                    win1 = __shfl_sync(0xffffffffu, src < 32 ? cw : nw, src & 31);
-                    ofs1 = __shfl_sync(0xffffffffu, src < 32 ? co : no, src & 31);
-                }
+                // the next step's metadata (from the ring; past the end of the scanline it is zero:
+                // no window) and cost row (a wide row has more than 32 slots, so its first 32 are
+                // in bounds too)
+                const int2 mt = meta[(k + 1) & 63];
+                const int win1 = mt.x, ofs1 = mt.y;
                 const int n1 = win1 >> 16;
                 float c1 = 0.f;
-                if (n1 <= 32 && lane < n1) c1 = __ldg(cost + 4ll * ofs1 + lane);
+                if (lane < n1) c1 = __ldg(cost + 4ll * ofs1 + lane);
                 float Lv = c;
                 unsigned cd = 4;
                 if (pn != 0) {
@@ -202,13 +208,7 @@ __global__ void __launch_bounds__(32 * kSgmWarps) fine_sgm_kernel(const float *_
                         // label drops out of the minimum (labels j >= n read in-bounds slots too)
                         const unsigned top = (unsigned)pn + 1u;
                         const float *row = bufA - 1;
-#pragma unroll
-                        for (int u = 0; u < 16; u++) {
-                            if (j0 + 32 * u >= n) break;
-                            const unsigned k1 = (unsigned)(l + j0 + 32 * u - plo + 1);
-                            const float v0 = row[min(k1, top)];
-                            const float vm = row[min(k1 - 1u, top)];
-                            const float vp = row[min(k1 + 1u, top)];
+                        auto step = [&](int u, float v0, float vm, float vp) {
                             const float t = fminf(fminf(m + P2, v0), fminf(vm, vp) + P1);
                             if (REC)
                                 code[o + j0 + 32 * u] = t == m + P2 ? 3 : (t == v0 ? 0 : (t == vm + P1 ? 1 : 2));
@@ -217,6 +217,24 @@ __global__ void __launch_bounds__(32 * kSgmWarps) fine_sgm_kernel(const float *_
                             // not order the shared-memory reads of the other chunks)
                             atomicAdd(agg + o + j0 + 32 * u, det_addend(Ln, cc[u] + P2, mk));
                             cc[u] = Ln;
+                        };
+                        if (l == plo && n == pn) {
+                            // the same window as the predecessor (a run of whole-range windows):
+                            // slot j's neighbours are slots j - 1 and j + 1, and the sentinels at
+                            // slots -1 and pn stand in for the absent ones
+                            const float *q = bufA + j0;
+#pragma unroll
+                            for (int u = 0; u < 16; u++) {
+                                if (j0 + 32 * u >= n) break;
+                                step(u, q[32 * u], q[32 * u - 1], q[32 * u + 1]);
+                            }
+                        } else {
+#pragma unroll
+                            for (int u = 0; u < 16; u++) {
+                                if (j0 + 32 * u >= n) break;
+                                const unsigned k1 = (unsigned)(l + j0 + 32 * u - plo + 1);
+                                step(u, row[min(k1, top)], row[min(k1 - 1u, top)], row[min(k1 + 1u, top)]);
+                            }
                         }
                     } else {
 #pragma unroll
@@ -256,7 +274,14 @@ __global__ void __launch_bounds__(32 * kSgmWarps) fine_sgm_kernel(const float *_
         if ((k & 31) == 0 && k < len) {       // next block of metadata
             cw = nw;
             co = no;
-            if (k + 32 < len) fetch(k + 32, nw, no);
+            if (k + 32 < len) {
+                fetch(k + 32, nw, no);
+            } else {
+                nw = 0;
+                no = 0;
+            }
+            meta[(k + 32 + lane) & 63] = make_int2(nw, no);   // the slots of the block just finished
+            __syncwarp();
         }
     }
 }
@@ -378,7 +403,7 @@ cudaError_t launch_fine_sgm(cudaStream_t s, const float *cost, const int *lo, co
                             size_t nnz_cap) {
     const ScanTable st = make_scan_table(H, W, paths);
     const int Gs = (G + 31) & ~31;
-    const size_t smem = (size_t)kSgmWarps * 2 * (Gs + 2) * sizeof(float);
+    const size_t smem = (size_t)kSgmWarps * (2 * (Gs + 2) * sizeof(float) + 64 * sizeof(int2));
     const unsigned grid = (unsigned)((st.cum[paths] + kSgmWarps - 1) / kSgmWarps);
     auto kern = codes ? fine_sgm_kernel<true> : fine_sgm_kernel<false>;
     if (smem > 48 * 1024) {
