@@ -67,60 +67,69 @@ __device__ __forceinline__ void sub_pair(float v, float c0, float c1, uint32_t &
     d1 = (uint32_t)(r >> 32);
 }
 
-// Census words of the two vertically adjacent pixels whose windows start at t and t + ld: every
-// tile value of the union of the two windows is read once, and each word takes its own neighbours
-// in descending order (rows bottom-up, columns right to left), as census_word does.  Where a tile
-// value is a neighbour of both pixels, the two differences are one packed subtraction.
-template <int HALF>
-__device__ __forceinline__ void census_word2(const float *t, int ld, float c0, float c1, uint64_t &w0,
-                                             uint64_t &w1) {
+// Census words of PPT vertically adjacent pixels whose windows start at t, t + ld, ...: every tile
+// value of the union of their windows is read once, and each word takes its own neighbours in
+// descending order (rows bottom-up, columns right to left), as census_word does.  Where a tile
+// value is a neighbour of both pixels of a pair (0, 1), (2, 3), ..., the two differences are one
+// packed subtraction.
+template <int HALF, int PPT>
+__device__ __forceinline__ void census_words(const float *t, int ld, const float (&c)[PPT], uint64_t (&w)[PPT]) {
+    static_assert(PPT % 2 == 0, "pixels in pairs");
     constexpr int WN = 2 * HALF + 1, CEN = HALF * WN + HALF;
-    uint32_t lo0 = 0, hi0 = 0, lo1 = 0, hi1 = 0;
+    uint32_t lo[PPT], hi[PPT];
 #pragma unroll
-    for (int ry = WN; ry >= 0; ry--) {                 // union row: window row ry of pixel 0, ry - 1 of pixel 1
+    for (int i = 0; i < PPT; i++) lo[i] = hi[i] = 0;
+#pragma unroll
+    for (int ry = WN + PPT - 2; ry >= 0; ry--) {       // union row: window row ry - i of pixel i
 #pragma unroll
         for (int rx = WN - 1; rx >= 0; rx--) {
             const float v = t[ry * ld + rx];
-            const int q0 = ry * WN + rx, q1 = (ry - 1) * WN + rx;
-            const bool use0 = ry < WN && q0 != CEN, use1 = ry >= 1 && q1 != CEN;
-            uint32_t d0 = 0, d1 = 0;
-            if (use0 && use1) sub_pair(v, c0, c1, d0, d1);
-            else if (use0) d0 = __float_as_uint(v - c0);
-            else if (use1) d1 = __float_as_uint(v - c1);
-            if (use0) {
-                const int k = q0 < CEN ? q0 : q0 - 1;
-                if (k >= 32) hi0 = __funnelshift_l(d0, hi0, 1);
-                else lo0 = __funnelshift_l(d0, lo0, 1);
-            }
-            if (use1) {
-                const int k = q1 < CEN ? q1 : q1 - 1;
-                if (k >= 32) hi1 = __funnelshift_l(d1, hi1, 1);
-                else lo1 = __funnelshift_l(d1, lo1, 1);
+#pragma unroll
+            for (int i = 0; i < PPT; i += 2) {
+                const int r0 = ry - i, r1 = ry - i - 1;
+                const int q0 = r0 * WN + rx, q1 = r1 * WN + rx;
+                const bool use0 = r0 >= 0 && r0 < WN && q0 != CEN, use1 = r1 >= 0 && r1 < WN && q1 != CEN;
+                uint32_t d0 = 0, d1 = 0;
+                if (use0 && use1) sub_pair(v, c[i], c[i + 1], d0, d1);
+                else if (use0) d0 = __float_as_uint(v - c[i]);
+                else if (use1) d1 = __float_as_uint(v - c[i + 1]);
+                if (use0) {
+                    const int k = q0 < CEN ? q0 : q0 - 1;
+                    if (k >= 32) hi[i] = __funnelshift_l(d0, hi[i], 1);
+                    else lo[i] = __funnelshift_l(d0, lo[i], 1);
+                }
+                if (use1) {
+                    const int k = q1 < CEN ? q1 : q1 - 1;
+                    if (k >= 32) hi[i + 1] = __funnelshift_l(d1, hi[i + 1], 1);
+                    else lo[i + 1] = __funnelshift_l(d1, lo[i + 1], 1);
+                }
             }
         }
     }
-    w0 = ((uint64_t)hi0 << 32) | lo0;
-    w1 = ((uint64_t)hi1 << 32) | lo1;
+#pragma unroll
+    for (int i = 0; i < PPT; i++) w[i] = ((uint64_t)hi[i] << 32) | lo[i];
 }
 
 // Same transform, written into edge-replicated padded images: word and value of pixel (x,y) go to
 // (x+P, y+P), and border pixels also fill the padding rows/columns next to them, so that a read
 // at any padded position (xp, yp) returns the word/value of pixel (clamp(xp-P), clamp(yp-P)) --
 // exactly the clamped read of the unpadded image.  Padded row stride Wp, Hp rows per view.
-// A 32 x 4 thread block covers a 32 x 8 tile: each thread takes two vertically adjacent pixels.
+// A 32 x 4 thread block covers a 32 x 4 PPT tile: each thread takes PPT vertically adjacent pixels
+// (grey 4: the tile's halo rows and the union windows are shared by more pixels; colour 2).
 // Colour (C = 3): one block per view transforms the C channel planes in turn (census words go to
 // the planes view * C + c), and the padded view is written interleaved, one float4 (the C
 // channels and a zero) per pixel, so that a bilinear tap of all channels is one 16-byte load.
-template <int HALF, int C>
+template <int HALF, int C, int PPT>
 __device__ __forceinline__ void census_pad_body(const float *__restrict__ views, int H, int W, int P, int Wp, int Hp,
                                                 const int *__restrict__ sel, uint64_t *__restrict__ cen_pad,
                                                 float *__restrict__ views_pad) {
-    constexpr int SW = TX + 2 * HALF, SH = TY + 2 * HALF;
+    constexpr int BY = 4, TYB = BY * PPT;              // thread rows, tile rows
+    constexpr int SW = TX + 2 * HALF, SH = TYB + 2 * HALF;
     __shared__ float tile[SH][SW + 1];
     const size_t HW = (size_t)H * W, HWp = (size_t)Hp * Wp;
     const int view = sel[blockIdx.z];
-    const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
-    const int x = x0 + threadIdx.x, ty0 = 2 * threadIdx.y, y = y0 + ty0;
+    const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TYB;
+    const int x = x0 + threadIdx.x, ty0 = PPT * threadIdx.y, y = y0 + ty0;
     const bool inb = x < W && y < H;
     const int xa = x == 0 ? 0 : x + P, xb = x == W - 1 ? Wp - 1 : x + P;
     // tile fill: thread (tx, ty) loads column tx of tile rows ty, ty + 4, ..., and the first 2 HALF
@@ -128,24 +137,29 @@ __device__ __forceinline__ void census_pad_body(const float *__restrict__ views,
     const int gx0 = min(max(x0 + (int)threadIdx.x - HALF, 0), W - 1);
     const int gx1 = min(max(x0 + TX + (int)threadIdx.x - HALF, 0), W - 1);
     const bool halo = threadIdx.x < 2 * HALF;
-    float cv[2][C] = {};
+    float cv[PPT][C] = {};
 #pragma unroll
     for (int ch = 0; ch < C; ch++) {
         const float *img = views + ((size_t)view * C + ch) * HW;
         if (ch) __syncthreads();                                   // the previous channel's tile is used up
 #pragma unroll
-        for (int ty = threadIdx.y; ty < SH; ty += TY / 2) {
+        for (int ty = threadIdx.y; ty < SH; ty += BY) {
             const float *src = img + (size_t)min(max(y0 + ty - HALF, 0), H - 1) * W;
             tile[ty][threadIdx.x] = __ldg(src + gx0) + 0.0f;       // -0 becomes +0 (see census_word)
             if (halo) tile[ty][TX + threadIdx.x] = __ldg(src + gx1) + 0.0f;
         }
         __syncthreads();
-        uint64_t w[2] = {0ull, 0ull};
+        uint64_t w[PPT];
+#pragma unroll
+        for (int i = 0; i < PPT; i++) w[i] = 0ull;
         if (inb) {
-            const float c0 = tile[ty0 + HALF][threadIdx.x + HALF], c1 = tile[ty0 + 1 + HALF][threadIdx.x + HALF];
-            census_word2<HALF>(&tile[ty0][threadIdx.x], SW + 1, c0, c1, w[0], w[1]);
-            cv[0][ch] = c0;
-            cv[1][ch] = c1;
+            float c[PPT];
+#pragma unroll
+            for (int i = 0; i < PPT; i++) {
+                c[i] = tile[ty0 + i + HALF][threadIdx.x + HALF];
+                cv[i][ch] = c[i];
+            }
+            census_words<HALF, PPT>(&tile[ty0][threadIdx.x], SW + 1, c, w);
         }
         // the census words of this channel, and with the last channel the padded view
         auto put = [&](uint64_t *cp, size_t q, uint64_t word, const float *val) {
@@ -168,7 +182,7 @@ __device__ __forceinline__ void census_pad_body(const float *__restrict__ views,
                 uint64_t *cp = cen_pad + (size_t)view * HWp;
                 const bool xedge = inb && (x == 0 || x == W - 1);
 #pragma unroll
-                for (int r = 0; r < 2; r++) {
+                for (int r = 0; r < PPT; r++) {
                     const int yr = y + r;
                     if (yr >= H) break;
                     const int ya = yr == 0 ? 0 : yr + P, yb = yr == H - 1 ? Hp - 1 : yr + P;
@@ -192,7 +206,7 @@ __device__ __forceinline__ void census_pad_body(const float *__restrict__ views,
             // warp-wide border writes, which raise the register count of the three-channel kernel)
             uint64_t *cp = cen_pad + ((size_t)view * C + ch) * HWp;
 #pragma unroll
-            for (int r = 0; r < 2; r++) {
+            for (int r = 0; r < PPT; r++) {
                 const int yr = y + r;
                 if (yr >= H) break;
                 if (xa == xb && yr != 0 && yr != H - 1) {             // interior: one padded position
@@ -207,30 +221,33 @@ __device__ __forceinline__ void census_pad_body(const float *__restrict__ views,
     }
 }
 
-// Grey: 16 CTAs of 128 threads per SM (32 registers).  Colour: the compiler's own register count.
+// Grey: 4 pixels per thread, 12 CTAs of 128 threads per SM.  Colour: 2 pixels per thread, the
+// compiler's own register count.
+constexpr int kPptGrey = 4, kPptRgb = 2;
 template <int HALF>
-__global__ void __launch_bounds__(TX *TY / 2, 16) census_pad_kernel(const float *__restrict__ views, int H, int W,
+__global__ void __launch_bounds__(TX * 4, 12) census_pad_kernel(const float *__restrict__ views, int H, int W,
                                                                     int P, int Wp, int Hp,
                                                                     const int *__restrict__ sel,
                                                                     uint64_t *__restrict__ cen_pad,
                                                                     float *__restrict__ views_pad) {
-    census_pad_body<HALF, 1>(views, H, W, P, Wp, Hp, sel, cen_pad, views_pad);
+    census_pad_body<HALF, 1, kPptGrey>(views, H, W, P, Wp, Hp, sel, cen_pad, views_pad);
 }
 
 template <int HALF>
-__global__ void __launch_bounds__(TX *TY / 2) census_pad_rgb_kernel(const float *__restrict__ views, int H, int W,
+__global__ void __launch_bounds__(TX * 4) census_pad_rgb_kernel(const float *__restrict__ views, int H, int W,
                                                                     int P, int Wp, int Hp,
                                                                     const int *__restrict__ sel,
                                                                     uint64_t *__restrict__ cen_pad,
                                                                     float *__restrict__ views_pad) {
-    census_pad_body<HALF, 3>(views, H, W, P, Wp, Hp, sel, cen_pad, views_pad);
+    census_pad_body<HALF, 3, kPptRgb>(views, H, W, P, Wp, Hp, sel, cen_pad, views_pad);
 }
 
 }  // namespace
 
 cudaError_t launch_census_pad(cudaStream_t s, const float *views, int H, int W, int census_w, int P, int Wp, int Hp,
                               int C, const int *d_sel, int nsel, uint64_t *cen_pad, float *views_pad) {
-    dim3 block(TX, TY / 2), grid((W + TX - 1) / TX, (H + TY - 1) / TY, nsel);
+    const int rows = 4 * (C == 3 ? kPptRgb : kPptGrey);
+    dim3 block(TX, 4), grid((W + TX - 1) / TX, (H + rows - 1) / rows, nsel);
     if (C == 3) {
         if (census_w == 5) census_pad_rgb_kernel<2><<<grid, block, 0, s>>>(views, H, W, P, Wp, Hp, d_sel, cen_pad, views_pad);
         else census_pad_rgb_kernel<3><<<grid, block, 0, s>>>(views, H, W, P, Wp, Hp, d_sel, cen_pad, views_pad);
