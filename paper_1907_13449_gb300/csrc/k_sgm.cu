@@ -8,9 +8,9 @@
 // general form with L' in a per-warp shared-memory row (chunks of 32 slots).  Window metadata
 // is fetched 32 pixels at a time (one per lane, the next block one block ahead) and also kept in a
 // per-warp ring of 64 steps in shared memory; a ballot over a block finds the steps that need the
-// general form, and the narrow steps between them run in a tight loop that reads the next step's
-// metadata from the ring (one broadcast load) and its cost row one step ahead.  The step is the
-// normalised recurrence
+// general form, and the narrow steps between them run in a tight loop that reads the metadata of
+// the step after next from the ring (one broadcast load) and loads cost rows two steps ahead.
+// The step is the normalised recurrence
 //   L(p,g) = C(p,g) + (min(L'(g), L'(g-1)+P1, L'(g+1)+P1, m+P2) - m),   m = min L',
 // and the predecessor minimum m is one redux.sync.min.f32 per pixel.  The 8 or 16 directions run
 // concurrently and add into agg (zeroed by the caller) with float atomics.
@@ -129,20 +129,22 @@ __global__ void __launch_bounds__(32 * kSgmWarps) fine_sgm_kernel(const float *_
         int kend = ahead ? kb + __ffs(ahead) - 1 : kbend;
         if (pn > 32) kend = k;                 // a wide predecessor: the general form takes this step
         if (k < kend) {
-            // narrow steps: the predecessor row in registers, the next cost row one step ahead
+            // narrow steps: the predecessor row in registers, cost rows two steps ahead
             int ofs = __shfl_sync(0xffffffffu, co, k - kb);
             const int win = __shfl_sync(0xffffffffu, cw, k - kb);
             int l = win & 0xffff, n = win >> 16;
             float c = lane < n ? __ldg(cost + 4ll * ofs + lane) : 0.f;
+            int2 mt1 = meta[(k + 1) & 63];
+            float c1 = lane < (mt1.x >> 16) ? __ldg(cost + 4ll * mt1.y + lane) : 0.f;
             for (; k < kend; k++) {
-                // the next step's metadata (from the ring; past the end of the scanline it is zero:
-                // no window) and cost row (a wide row has more than 32 slots, so its first 32 are
-                // in bounds too)
-                const int2 mt = meta[(k + 1) & 63];
-                const int win1 = mt.x, ofs1 = mt.y;
+                // the metadata of the step after next (from the ring; past the end of the scanline
+                // it is zero: no window) and its cost row (a wide row has more than 32 slots, so its
+                // first 32 are in bounds too): cost rows two steps ahead
+                const int2 mt2 = meta[(k + 2) & 63];
+                float c2 = 0.f;
+                if (lane < (mt2.x >> 16)) c2 = __ldg(cost + 4ll * mt2.y + lane);
+                const int win1 = mt1.x, ofs1 = mt1.y;
                 const int n1 = win1 >> 16;
-                float c1 = 0.f;
-                if (lane < n1) c1 = __ldg(cost + 4ll * ofs1 + lane);
                 float Lv = c;
                 unsigned cd = 4;
                 if (pn != 0) {
@@ -175,6 +177,8 @@ __global__ void __launch_bounds__(32 * kSgmWarps) fine_sgm_kernel(const float *_
                 n = n1;
                 ofs = ofs1;
                 c = c1;
+                c1 = c2;
+                mt1 = mt2;
             }
             in_smem = false;
         }
