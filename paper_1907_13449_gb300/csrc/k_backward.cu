@@ -247,11 +247,11 @@ __global__ void __launch_bounds__(32 * kBwdWarps) sgm_backward_kernel(
             na = fetch_am(kb0 - 32);
         }
     }
-    // the dLoss/dC_s row and branch codes of the next step (k - 1), loaded one step ahead when it
-    // is narrow
-    bool pf_ok = false;
-    float pf_g = 0.f;
-    unsigned pf_c = 4u;
+    // the dLoss/dC_s row and branch codes of narrow windows, loaded two steps ahead: pf1 for step
+    // k - 1, pf2 for step k - 2
+    bool pf1_ok = false, pf2_ok = false;
+    float pf1_g = 0.f, pf2_g = 0.f;
+    unsigned pf1_c = 4u, pf2_c = 4u;
     for (int k = len - 1; k >= 0; k--) {
         const int kb = k & ~31, kk = k & 31;
         if (kk == 31 && k < len - 1) {       // entered a lower block
@@ -263,8 +263,24 @@ __global__ void __launch_bounds__(32 * kBwdWarps) sgm_backward_kernel(
                 na = fetch_am(kb - 32);
             }
         }
-        const bool have_pf = pf_ok;
-        pf_ok = false;
+        const bool have_pf = pf1_ok;
+        const float pre_g = pf1_g;
+        const unsigned pre_c = pf1_c;
+        pf1_ok = pf2_ok;
+        pf1_g = pf2_g;
+        pf1_c = pf2_c;
+        pf2_ok = false;
+        if (k >= 2) {
+            // step k - 2: this block, or lane 30 / 31 of the block below
+            const int w2 = __shfl_sync(0xffffffffu, kk >= 2 ? cw : nw, (kk + 30) & 31);
+            const int o2 = __shfl_sync(0xffffffffu, kk >= 2 ? co : no, (kk + 30) & 31);
+            const int n2 = w2 >> 16;
+            if (n2 > 0 && n2 <= 32) {
+                pf2_g = lane < n2 ? __ldg(gCs + 4ll * o2 + lane) : 0.f;
+                pf2_c = lane < n2 ? (unsigned)__ldg(code + 4ll * o2 + lane) : 4u;
+                pf2_ok = true;
+            }
+        }
         const int win = __shfl_sync(0xffffffffu, cw, kk), ofs = __shfl_sync(0xffffffffu, co, kk);
         // predecessor on the path: step k - 1 (this block, or lane 31 of the block below)
         const int wq = __shfl_sync(0xffffffffu, kk > 0 ? cw : nw, (kk + 31) & 31);
@@ -285,15 +301,8 @@ __global__ void __launch_bounds__(32 * kBwdWarps) sgm_backward_kernel(
             const bool act = lane < n;
             float in_v = 0.f;
             if (have_inc) in_v = inc_smem ? (act ? bufA[lane] : 0.f) : inc;
-            const float gv = have_pf ? pf_g : (act ? __ldg(gCs + o + lane) : 0.f);
-            const unsigned cd = have_pf ? pf_c : (act ? (unsigned)code[o + lane] : 4u);
-            if (q >= 0) {
-                // q's row one step ahead (its window is narrow here)
-                const int oq = __shfl_sync(0xffffffffu, kk > 0 ? co : no, (kk + 31) & 31);
-                pf_g = lane < qn ? __ldg(gCs + 4ll * oq + lane) : 0.f;
-                pf_c = lane < qn ? (unsigned)code[4ll * oq + lane] : 4u;
-                pf_ok = true;
-            }
+            const float gv = have_pf ? pre_g : (act ? __ldg(gCs + o + lane) : 0.f);
+            const unsigned cd = have_pf ? pre_c : (act ? (unsigned)code[o + lane] : 4u);
             const float lv = act ? gv + in_v : 0.f;
             if (act) atomicAdd(gcost + o + lane, lv);
             if (cd == 1 || cd == 2) gp1 += lv;
