@@ -651,9 +651,17 @@ cudaError_t launch_fine_cost_list(cudaStream_t s, const float *views_pad, const 
     int dev = 0, sms = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    // grid-stride over the items: by default 12 CTAs per SM for the grey residue (a few ten
-    // thousand items), 24 for colour, where every window is an item (measured best of 12 / 16 / 24)
-    const int k = ctas_per_sm > 0 ? ctas_per_sm : (C == 3 ? 24 : 12);
+    // grid-stride over the items, by default with exactly the CTAs that are resident at once: the
+    // warps then sweep the list (pixel order) once, together, and the views around the rows in
+    // flight stay in L2; a second wave would sweep the whole image again (colour: 9 resident CTAs
+    // per SM, 4.35 ms, against 4.92 ms with 24 and 6.48 ms with 12)
+    int k = ctas_per_sm;
+    if (k <= 0) {
+        const cudaError_t e = C == 3 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&k, fine_cost_list<3>, 32 * kListWarps, 0)
+                                     : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&k, fine_cost_list<1>, 32 * kListWarps, 0);
+        if (e != cudaSuccess) return e;
+        k = max(k, 1);
+    }
     if (C == 3)
         fine_cost_list<3><<<sms * k, 32 * kListWarps, 0, s>>>(views_pad, cen_pad, P, Wp, Hp, ltab, G, nviews, W, ref,
                                                              lo, cnt, off, wl2, wc, cost, list, count);
