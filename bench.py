@@ -255,7 +255,7 @@ def run_ours(args, ws, rank, local):
     nnz = int(L.off[-1].item())
     cnt = L.cnt.cpu().numpy()
     active = int(cnt.sum())
-    row_cells = row_kernel_cells(L.lo.cpu().numpy(), cnt, p.H, p.W, row_kw) if p.channels == 1 else 0
+    row_cells = row_kernel_cells(L.lo.cpu().numpy(), cnt, p.H, p.W, row_kw)
 
     lf.lfsgm_set_profiling(L.h, True)
     lf.lfsgm_kernel_times(L.h)          # drop anything recorded so far
@@ -357,9 +357,9 @@ def run_ours(args, ws, rank, local):
     K = args.steps
     value = ms_per_lf(stage_ms, K, ws)          # whole-job ms per light field (cost+SGM)
     # dominant kernel of the cost+SGM stages and its roofline
-    hot = ["fine_cost", "fine_sgm", "census_all", "cost_partial_sums", "zero_agg"]
-    if p.channels > 1:
-        hot.append("fine_cost_wide")      # colour: every window goes through the list kernel
+    hot = ["fine_cost", "fine_cost_wide", "fine_sgm", "census_all", "cost_partial_sums", "zero_agg"]
+    if "fine_cost" not in kernels:
+        row_cells = 0                     # no row-kernel plan for this shape: every window in the list
     dom = max((k for k in kernels if k in hot), key=lambda k: kernels[k]["ms_total"])
     mhz = (clocks or {}).get("sm_mhz") or peaks.get("sm_max_mhz", 2070.0)
     n_sm = torch.cuda.get_device_properties(dev).multi_processor_count
@@ -368,7 +368,6 @@ def run_ours(args, ws, rank, local):
     hbm_model_frac = round(hbm_total / (peaks["hbm_gbs"] * 1e9) * 1e3 / value, 4)
     if dom in ("fine_cost", "fine_cost_wide"):
         # the row kernel computes row_cells of the active cells, the list kernel the rest
-        # (colour: every cell goes through the list kernel)
         ops = alu_ops_cost(p, row_cells if dom == "fine_cost" else active - row_cells)
         peak_ops = n_sm * FP32_LANES_PER_SM * mhz * 1e6
         ach = ops / (kernels[dom]["ms_avg"] * 1e-3)

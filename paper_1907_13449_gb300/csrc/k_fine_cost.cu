@@ -103,6 +103,13 @@ __global__ void __launch_bounds__(256) fine_cost_generic(const float *__restrict
 // end.  The census term is a step function of the label: its Hamming distances are added as
 // integer differences at the census breakpoints (a shared-memory atomic into per-lane words that
 // hold two labels' 16-bit differences) and prefix-summed once at the end.
+//
+// Colour (C = 3, Sec. III-B/C).  The view tile is the padded float4 pixels (channels interleaved,
+// a 4-D tensor map) and the census tile the view's three census planes (box depth 3).  The channels
+// go one after another through the same segment and label loops: a channel's sample differences
+// e_c(i) are squared into per-label sums, and the label's l2 term is the square root of the sum
+// over the channels (the Euclidean norm of the colour difference); the census steps add the three
+// channels' Hamming distances.
 struct RowPlan {
     int P, Wp, Hp;                    // padding and padded sizes
     int bwf, bhf, bwc, bhc;           // TMA boxes (elements): view values, census words
@@ -112,6 +119,7 @@ struct RowPlan {
     int o_rc;                         // census tile (one buffer: refilled once its breakpoints are read)
     int o_cab, o_cc, o_cdiff, o_mbar, warp_bytes;
     int kw;                           // label span of a row's range (a kernel instantiation)
+    int C;                            // channels: 1, or 3 (float4 view tiles, three census planes)
 };
 
 // Descriptor of the label range [g0, g0+KW) of one view (built on the host, see
@@ -139,8 +147,8 @@ __device__ __forceinline__ bool mbar_wait(unsigned mbar, unsigned parity) {
     return false;
 }
 
-template <int KW>
-__global__ void __launch_bounds__(128, 5) fine_cost_rows(const __grid_constant__ CUtensorMap tm_v,
+template <int KW, int C>
+__global__ void __launch_bounds__(128, C == 1 ? 5 : 2) fine_cost_rows(const __grid_constant__ CUtensorMap tm_v,
                                                          const __grid_constant__ CUtensorMap tm_c,
                                                          const unsigned char *__restrict__ desc, int G, int U, int V,
                                                          int H, int W, int ref, const int *__restrict__ lo,
@@ -185,12 +193,22 @@ __global__ void __launch_bounds__(128, 5) fine_cost_rows(const __grid_constant__
     if (best_fit <= 0) return;
     const bool fits = nar && l >= g0 && l + n <= g0 + KW;
     if (nar && !fits) push_chunks(list, list_count, y * W + x, n);
-    float Iref = 0.f;
-    uint64_t cr = 0;
+    float Iref = 0.f, Iref1 = 0.f, Iref2 = 0.f;           // the reference pixel (channels 1, 2: colour)
+    uint64_t cr[C];
+#pragma unroll
+    for (int ch = 0; ch < C; ch++) cr[ch] = 0;
     if (fits) {
         const size_t pp = (size_t)(y + pl.P) * pl.Wp + (x + pl.P);
-        Iref = __ldg(views_pad + (size_t)ref * HWp + pp);
-        cr = __ldg(cen_pad + (size_t)ref * HWp + pp);
+        if constexpr (C == 1) {
+            Iref = __ldg(views_pad + (size_t)ref * HWp + pp);
+        } else {
+            const float4 iv = __ldg(reinterpret_cast<const float4 *>(views_pad) + (size_t)ref * HWp + pp);
+            Iref = iv.x;
+            Iref1 = iv.y;
+            Iref2 = iv.z;
+        }
+#pragma unroll
+        for (int ch = 0; ch < C; ch++) cr[ch] = __ldg(cen_pad + ((size_t)ref * C + ch) * HWp + pp);
         const int npad = (int)min((long long)((n + 3) & ~3), row);
         for (int j = n; j < npad; j++) cost[o + j] = 0.f;
     }
@@ -201,7 +219,8 @@ __global__ void __launch_bounds__(128, 5) fine_cost_rows(const __grid_constant__
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     __syncwarp();
-    const unsigned tile_bytes = (unsigned)(pl.bwf * pl.bhf * 4), cen_bytes = (unsigned)(pl.bwc * pl.bhc * 8);
+    const unsigned tile_bytes = (unsigned)(pl.bwf * pl.bhf * 4 * (C == 1 ? 1 : 4));
+    const unsigned cen_bytes = (unsigned)(pl.bwc * pl.bhc * 8 * C);
     auto dsc_of = [&](int view) { return desc + ((size_t)view * G + g0) * pl.ds_stride; };
     // the first 16 bytes of the next views' descriptors (tile origins, counts, size), read one
     // view ahead of their issue
@@ -213,9 +232,14 @@ __global__ void __launch_bounds__(128, 5) fine_cost_rows(const __grid_constant__
         const unsigned mb = mbar0 + 8 * st;
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(mb), "r"(tile_bytes + nb) : "memory");
-        asm volatile("cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];"
-                     ::"r"(smem_u32(wb + pl.o_rf + st * pl.stage)), "l"((unsigned long long)&tm_v), "r"(xf), "r"(yf), "r"(view), "r"(mb)
-                     : "memory");
+        if constexpr (C == 1)
+            asm volatile("cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];"
+                         ::"r"(smem_u32(wb + pl.o_rf + st * pl.stage)), "l"((unsigned long long)&tm_v), "r"(xf), "r"(yf), "r"(view), "r"(mb)
+                         : "memory");
+        else                                       // {channel, x, y, view} of the float4 pixels
+            asm volatile("cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, %5}], [%6];"
+                         ::"r"(smem_u32(wb + pl.o_rf + st * pl.stage)), "l"((unsigned long long)&tm_v), "r"(0), "r"(xf), "r"(yf), "r"(view), "r"(mb)
+                         : "memory");
         if (nb > 0)
             asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
                          ::"r"(smem_u32(wb + pl.o_ds + st * pl.stage)), "l"(dsc_of(view)), "r"(nb), "r"(mb)
@@ -228,7 +252,7 @@ __global__ void __launch_bounds__(128, 5) fine_cost_rows(const __grid_constant__
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(mb), "r"(cen_bytes) : "memory");
         asm volatile("cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];"
-                     ::"r"(smem_u32(wb + pl.o_rc)), "l"((unsigned long long)&tm_c), "r"(xc), "r"(yc), "r"(view), "r"(mb)
+                     ::"r"(smem_u32(wb + pl.o_rc)), "l"((unsigned long long)&tm_c), "r"(xc), "r"(yc), "r"(view * C), "r"(mb)
                      : "memory");
     };
     float acc[KW];
@@ -270,7 +294,9 @@ __global__ void __launch_bounds__(128, 5) fine_cost_rows(const __grid_constant__
             int prev = 0;
             for (int b = 0; b < ncen; b++) {
                 const int4 e = ce[b];
-                const int h = __popcll(cr ^ rc[e.x + lane]);
+                int h = 0;
+#pragma unroll
+                for (int ch = 0; ch < C; ch++) h += __popcll(cr[ch] ^ rc[ch * pl.bwc * pl.bhc + e.x + lane]);
                 atomicAdd((int *)((char *)cdw + e.y), (int)((unsigned)(h - prev) << e.z));
                 prev = h;
             }
@@ -289,46 +315,62 @@ __global__ void __launch_bounds__(128, 5) fine_cost_rows(const __grid_constant__
         const float2 axy = *(const float2 *)(ds + kDsAxy);
         const float axay = __int_as_float(hdr.w);
         const float4 *sg = (const float4 *)(ds + kDsSegs);
-        for (int sgi = 0; sgi < nseg; sgi++) {
-            const float4 d0 = sg[2 * sgi], d1 = sg[2 * sgi + 1];
-            const float *q = rf + __float_as_int(d0.x) + lane;
-            const float i00 = q[0], i10 = q[1], i01 = q[pl.bwf], i11 = q[pl.bwf + 1];
-            const float c1 = i10 - i00, c2 = i01 - i00, c3 = (i11 - i01) - c1;
-            // s(t) - I_ref = (c0 - I_ref) + c1 fx + c2 fy + c3 fx fy, fx = fx0 + ax t, fy = fy0 + ay t,
-            // t = i - fi: value a0, slope b0 and curvature Cq at t = 0, then in powers of i
-            const float a0 = fmaf(c3, d1.x, fmaf(c2, d0.w, fmaf(c1, d0.z, i00 - Iref)));
-            const float b0 = fmaf(c3, d1.y, fmaf(c2, axy.y, c1 * axy.x));
-            const float Cq = c3 * axay;
-            const float fi = d0.y;
-            cab[32 * sgi] = make_float2(fmaf(fi, fmaf(fi, Cq, -b0), a0), fmaf(d1.z, Cq, b0));
-            ccq[32 * sgi] = Cq;
-        }
-        // (each lane reads back only its own coefficients: no warp synchronisation needed)
         const uint2 smask = *(const uint2 *)(ds + kDsMask);
-        unsigned cpab = smem_u32(cab) - 256u, cpc = smem_u32(ccq) - 128u;
-        float4 cf = make_float4(0.f, 0.f, 0.f, 0.f);
+        // one channel (tile values rfc[tstride * pixel]): the segments' coefficients, then the label
+        // loop, which hands each label's sample difference e to op(label, e)
+        auto channel = [&](const float *rfc, int tstride, float Ic, auto &&op) {
+            for (int sgi = 0; sgi < nseg; sgi++) {
+                const float4 d0 = sg[2 * sgi], d1 = sg[2 * sgi + 1];
+                const float *q = rfc + tstride * (__float_as_int(d0.x) + lane);
+                const float i00 = q[0], i10 = q[tstride], i01 = q[tstride * pl.bwf], i11 = q[tstride * (pl.bwf + 1)];
+                const float c1 = i10 - i00, c2 = i01 - i00, c3 = (i11 - i01) - c1;
+                // s(t) - I_ref = (c0 - I_ref) + c1 fx + c2 fy + c3 fx fy, fx = fx0 + ax t, fy = fy0 + ay t,
+                // t = i - fi: value a0, slope b0 and curvature Cq at t = 0, then in powers of i
+                const float a0 = fmaf(c3, d1.x, fmaf(c2, d0.w, fmaf(c1, d0.z, i00 - Ic)));
+                const float b0 = fmaf(c3, d1.y, fmaf(c2, axy.y, c1 * axy.x));
+                const float Cq = c3 * axay;
+                const float fi = d0.y;
+                cab[32 * sgi] = make_float2(fmaf(fi, fmaf(fi, Cq, -b0), a0), fmaf(d1.z, Cq, b0));
+                ccq[32 * sgi] = Cq;
+            }
+            // (each lane reads back only its own coefficients: no warp synchronisation needed)
+            unsigned cpab = smem_u32(cab) - 256u, cpc = smem_u32(ccq) - 128u;
+            float4 cf = make_float4(0.f, 0.f, 0.f, 0.f);
 #pragma unroll
-        for (int k = 0; k < KW / 4; k++) {
-            const unsigned bits = (k < 8 ? smask.x >> (4 * k) : smask.y >> (4 * k - 32)) & 0xfu;
-            if (bits == 0) {
+            for (int k = 0; k < KW / 4; k++) {
+                const unsigned bits = (k < 8 ? smask.x >> (4 * k) : smask.y >> (4 * k - 32)) & 0xfu;
+                if (bits == 0) {
 #pragma unroll
-                for (int e = 0; e < 4; e++) {
-                    const float fi = (float)(4 * k + e);
-                    acc[4 * k + e] += fabsf(fmaf(fi, fmaf(fi, cf.z, cf.y), cf.x));
-                }
-            } else {
+                    for (int e = 0; e < 4; e++) {
+                        const float fi = (float)(4 * k + e);
+                        op(4 * k + e, fmaf(fi, fmaf(fi, cf.z, cf.y), cf.x));
+                    }
+                } else {
 #pragma unroll
-                for (int e = 0; e < 4; e++) {
-                    // a segment starts at this label: step to its coefficients (predicated, no branch)
-                    asm volatile("{\n .reg .pred p;\n .reg .b32 t;\n and.b32 t, %5, %6;\n setp.ne.u32 p, t, 0;\n"
-                                 " @p add.u32 %3, %3, 256;\n @p add.u32 %4, %4, 128;\n"
-                                 " @p ld.shared.v2.f32 {%0, %1}, [%3];\n @p ld.shared.f32 %2, [%4];\n}"
-                                 : "+f"(cf.x), "+f"(cf.y), "+f"(cf.z), "+r"(cpab), "+r"(cpc)
-                                 : "r"(bits), "r"(1u << e));
-                    const float fi = (float)(4 * k + e);
-                    acc[4 * k + e] += fabsf(fmaf(fi, fmaf(fi, cf.z, cf.y), cf.x));
+                    for (int e = 0; e < 4; e++) {
+                        // a segment starts at this label: step to its coefficients (predicated, no branch)
+                        asm volatile("{\n .reg .pred p;\n .reg .b32 t;\n and.b32 t, %5, %6;\n setp.ne.u32 p, t, 0;\n"
+                                     " @p add.u32 %3, %3, 256;\n @p add.u32 %4, %4, 128;\n"
+                                     " @p ld.shared.v2.f32 {%0, %1}, [%3];\n @p ld.shared.f32 %2, [%4];\n}"
+                                     : "+f"(cf.x), "+f"(cf.y), "+f"(cf.z), "+r"(cpab), "+r"(cpc)
+                                     : "r"(bits), "r"(1u << e));
+                        const float fi = (float)(4 * k + e);
+                        op(4 * k + e, fmaf(fi, fmaf(fi, cf.z, cf.y), cf.x));
+                    }
                 }
             }
+            __syncwarp();      // the next channel's coefficients overwrite these (a memory barrier)
+        };
+        if constexpr (C == 1) {
+            channel(rf, 1, Iref, [&](int i, float e) { acc[i] += fabsf(e); });
+        } else {
+            // squared colour differences per label, then their norm
+            float sq[KW];
+            channel(rf, 4, Iref, [&](int i, float e) { sq[i] = e * e; });
+            channel(rf + 1, 4, Iref1, [&](int i, float e) { sq[i] = fmaf(e, e, sq[i]); });
+            channel(rf + 2, 4, Iref2, [&](int i, float e) { sq[i] = fmaf(e, e, sq[i]); });
+#pragma unroll
+            for (int i = 0; i < KW; i++) acc[i] += sqrtf(sq[i]);
         }
         __syncwarp();
     }
@@ -451,11 +493,12 @@ int r128(int x) { return (x + 127) & ~127; }
 }  // namespace
 
 // Padding, TMA boxes and the per-warp shared-memory layout of the row kernel for one config.
-bool plan_fine_rows(int U, int V, int uc, int vc, int H, int W, int G, double dmin, double dmax, int kw,
+bool plan_fine_rows(int U, int V, int uc, int vc, int H, int W, int G, double dmin, double dmax, int kw, int C,
                     RowPlanHost *out) {
     RowPlan pl{};
     const int kRowKW = kw == 44 ? 44 : 36;
     pl.kw = kRowKW;
+    pl.C = C;
     const double md = fmax(fabs(dmin), fabs(dmax));
     const int amax = max(max(uc, U - 1 - uc), max(vc, V - 1 - vc));
     pl.P = (int)ceil(amax * md) + 3;
@@ -474,11 +517,11 @@ bool plan_fine_rows(int U, int V, int uc, int vc, int H, int W, int G, double dm
     pl.ds_stride = (kDsSegs + pl.seg_cap * (kDsSegBytes + kDsCenBytes) + 15) & ~15;
     int o = 0;
     pl.o_rf = o;
-    pl.o_ds = pl.o_rf + r128(pl.bwf * pl.bhf * 4);
+    pl.o_ds = pl.o_rf + r128(pl.bwf * pl.bhf * 4 * (C == 1 ? 1 : 4));     // colour: float4 pixels
     pl.stage = r128(pl.o_ds + pl.ds_stride - pl.o_rf);
     o = pl.o_rf + 2 * pl.stage;
     pl.o_rc = o;
-    o += r128(pl.bwc * pl.bhc * 8);
+    o += r128(pl.bwc * pl.bhc * 8 * C);                                       // one plane per channel
     pl.o_cab = o;
     o += pl.seg_cap * 256;
     pl.o_cc = o;
@@ -489,9 +532,10 @@ bool plan_fine_rows(int U, int V, int uc, int vc, int H, int W, int G, double dm
     o += 32;
     o = r128(o);
     pl.warp_bytes = o;
-    // the census steps of one label, summed over the views, must fit 16 bits (at most 48 bits a word)
+    // the census steps of one label, summed over the views and channels, must fit 16 bits (at most 48
+    // bits a word); colour runs the 36-label span only
     out->ok = pl.bwf <= 256 && pl.bwc <= 256 && pl.bhf <= 256 && pl.bhc <= 256 && pl.warp_bytes <= 48 * 1024 &&
-              (U * V - 1) * 48 < 32768 && pl.ds_stride < 65536;
+              (U * V - 1) * 48 * C < 32768 && pl.ds_stride < 65536 && (C == 1 || (C == 3 && kRowKW == 36));
     static_assert(sizeof(RowPlan) <= sizeof(out->raw), "plan storage");
     memcpy(out->raw, &pl, sizeof(pl));
     out->P = pl.P;
@@ -596,8 +640,17 @@ bool encode_fine_rows_maps(RowPlanHost *ph, const float *views_pad, const uint64
             return false;
         encode = (PFN_cuTensorMapEncodeTiled_v12000)fn;
     }
-    const cuuint32_t estr[3] = {1, 1, 1};
-    {
+    const cuuint32_t estr[4] = {1, 1, 1, 1};
+    if (pl.C == 3) {
+        // float4 pixels (the fourth float is padding): {channel, x, y, view}
+        const cuuint64_t dims[4] = {4, (cuuint64_t)pl.Wp, (cuuint64_t)pl.Hp, (cuuint64_t)nviews};
+        const cuuint64_t strides[3] = {16, (cuuint64_t)pl.Wp * 16, (cuuint64_t)pl.Wp * pl.Hp * 16};
+        const cuuint32_t box[4] = {4, (cuuint32_t)pl.bwf, (cuuint32_t)pl.bhf, 1};
+        if (encode((CUtensorMap *)ph->tm_v, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, (void *)views_pad, dims, strides, box,
+                   estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                   CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+            return false;
+    } else {
         const cuuint64_t dims[3] = {(cuuint64_t)pl.Wp, (cuuint64_t)pl.Hp, (cuuint64_t)nviews};
         const cuuint64_t strides[2] = {(cuuint64_t)pl.Wp * 4, (cuuint64_t)pl.Wp * pl.Hp * 4};
         const cuuint32_t box[3] = {(cuuint32_t)pl.bwf, (cuuint32_t)pl.bhf, 1};
@@ -607,9 +660,10 @@ bool encode_fine_rows_maps(RowPlanHost *ph, const float *views_pad, const uint64
             return false;
     }
     {
-        const cuuint64_t dims[3] = {(cuuint64_t)pl.Wp, (cuuint64_t)pl.Hp, (cuuint64_t)nviews};
+        // census planes view * C + c: a view's C planes are one box of depth C
+        const cuuint64_t dims[3] = {(cuuint64_t)pl.Wp, (cuuint64_t)pl.Hp, (cuuint64_t)nviews * pl.C};
         const cuuint64_t strides[2] = {(cuuint64_t)pl.Wp * 8, (cuuint64_t)pl.Wp * pl.Hp * 8};
-        const cuuint32_t box[3] = {(cuuint32_t)pl.bwc, (cuuint32_t)pl.bhc, 1};
+        const cuuint32_t box[3] = {(cuuint32_t)pl.bwc, (cuuint32_t)pl.bhc, (cuuint32_t)pl.C};
         if (encode((CUtensorMap *)ph->tm_c, CU_TENSOR_MAP_DATA_TYPE_UINT64, 3, (void *)cen_pad, dims, strides, box,
                    estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
                    CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
@@ -624,9 +678,11 @@ cudaError_t launch_fine_cost_rows(cudaStream_t s, const RowPlanHost *ph, const f
                                   float fstep, float *cost, int *status, int2 *list, int *list_count) {
     RowPlan pl;
     memcpy(&pl, ph->raw, sizeof(pl));
-    const int wpb = 4;
+    // warps (row segments) per CTA: colour 2 (22 KB of shared memory per warp: five CTAs, ten warps
+    // per SM; four warps per CTA fit two CTAs, eight warps, and ran 12 % slower)
+    const int wpb = pl.C == 3 ? 2 : 4;
     const size_t smem = (size_t)wpb * pl.warp_bytes;
-    auto kern = pl.kw == 44 ? fine_cost_rows<44> : fine_cost_rows<36>;
+    auto kern = pl.C == 3 ? fine_cost_rows<36, 3> : (pl.kw == 44 ? fine_cost_rows<44, 1> : fine_cost_rows<36, 1>);
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     const long long tasks = (long long)((W + 31) / 32) * H;

@@ -312,7 +312,7 @@ lfsgm_status plan_handle(const lfsgm_config &cin, lfsgm_ctx *h) {
     h->ref = c.vc * c.U + c.uc;
     h->nbits = c.census_w * c.census_w - 1;
     h->Lcd = coarse_stride(c.coarse_labels);
-    plan_fine_rows(c.U, c.V, c.uc, c.vc, c.H, c.W, c.fine_labels, c.dmin, c.dmax, h->row_kw, &h->rows);
+    plan_fine_rows(c.U, c.V, c.uc, c.vc, c.H, c.W, c.fine_labels, c.dmin, c.dmax, h->row_kw, h->C, &h->rows);
     build_arms(h);
     // the packed coarse sums hold (paths) x (C + P2) per 16-bit half
     const long long cmax = (long long)max_arm_views(h) * h->nbits * h->C;
@@ -427,7 +427,6 @@ lfsgm_status lfsgm_create(const lfsgm_config *cfg, void *stream, lfsgm_handle *o
         }
         ALLOC_COPY(h->d_ltab, ltab);
     }
-    if (h->C > 1) h->rows.ok = false;   // colour: every window through the list kernel
     if (h->rows.ok) {
         std::vector<unsigned char> desc;
         const float fstep = (float)((c.dmax - c.dmin) / (double)(c.fine_labels - 1));
@@ -509,10 +508,10 @@ lfsgm_status lfsgm_set_tuning(lfsgm_handle h, int32_t row_kw, int32_t list_ctas_
     // new plan and descriptors for the new label span; the padding and the workspace layout do not
     // depend on it, so a bound workspace keeps its buffers and only the tensor maps are re-encoded
     RowPlanHost rows{};
-    plan_fine_rows(c.U, c.V, c.uc, c.vc, c.H, c.W, c.fine_labels, c.dmin, c.dmax, kw, &rows);
+    plan_fine_rows(c.U, c.V, c.uc, c.vc, c.H, c.W, c.fine_labels, c.dmin, c.dmax, kw, h->C, &rows);
     std::vector<unsigned char> desc;
     const float fstep = (float)((c.dmax - c.dmin) / (double)(c.fine_labels - 1));
-    bool ok = rows.ok && h->C == 1 &&
+    bool ok = rows.ok &&
               build_fine_rows_desc(&rows, h->h_fine.data(), c.U, c.V, c.uc, c.vc, c.fine_labels, (float)c.dmin, fstep,
                                    desc);
     unsigned char *d = nullptr;

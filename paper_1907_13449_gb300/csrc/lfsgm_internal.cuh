@@ -202,8 +202,9 @@ struct RowPlanHost {
     bool ok;
     int P, Wp, Hp;                         // padding and padded sizes
 };
-// kw: the label span of a row's range, 36 or 44 (two instantiations of the row kernel).
-bool plan_fine_rows(int U, int V, int uc, int vc, int H, int W, int G, double dmin, double dmax, int kw,
+// kw: the label span of a row's range, 36 or 44 (two instantiations of the row kernel); C: channels
+// (colour: span 36 only; any other span leaves the plan not ok, and every window to the list kernel).
+bool plan_fine_rows(int U, int V, int uc, int vc, int H, int W, int G, double dmin, double dmax, int kw, int C,
                     RowPlanHost *out);
 bool encode_fine_rows_maps(RowPlanHost *ph, const float *views_pad, const uint64_t *cen_pad, int nviews);
 // Census words (planes view * C + c) and the edge-padded views (C = 1: float planes; C = 3: one
