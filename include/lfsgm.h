@@ -103,8 +103,9 @@ lfsgm_status lfsgm_workspace_size(lfsgm_handle h, size_t *bytes);
 lfsgm_status lfsgm_set_workspace(lfsgm_handle h, void *dptr, size_t bytes);
 
 /* Speed knobs (not in the paper): the label span of the row cost kernel's ranges (row_kw 36 or
- * 44; 0 = 36), and the CTAs per SM of the (pixel, chunk) list kernel (list_ctas_per_sm 1..64;
- * 0 = the default, 12 grey / 24 colour).  A wider span sends fewer windows to the list kernel
+ * 44; 0 = 36; colour light fields run span 36 only, and with 44 send every window to the list
+ * kernel), and the CTAs per SM of the (pixel, chunk) list kernel (list_ctas_per_sm 1..64; 0 = the
+ * default: the CTAs resident at once, one wave).  A wider span sends fewer windows to the list kernel
  * and computes more labels per row.  Changing the span rebuilds the row descriptors on the host
  * and synchronises the handle's stream; results change only in the last bits (a window moves
  * between the row and the list kernel, which add the views in different FP32 orders).  The
