@@ -291,10 +291,14 @@ __global__ void __launch_bounds__(32 * kSgmWarps) fine_sgm_kernel(const float *_
 }
 
 // Per-block sums of the active costs and slot counts (rows are 16-byte aligned, read as float4;
-// slots past cnt are masked, so padding is never read into the sum).  Each thread adds its pixels
-// in a fixed order (windows of up to 32 slots with all their loads issued together), the block
-// adds its warps in a fixed order, and the last block to finish (ticket counter) adds the block
-// partials in block order and writes the penalties: the mean is deterministic.
+// slots past cnt are masked, so padding is never read into the sum).  The warps take 32
+// consecutive pixels at a time, a lane its pixel: a lane sums its row's first 32 slots (8 vector
+// loads issued together), and the slots past 32 of a few wide rows in the warp are then summed by
+// the whole warp, one row after another (a lane a vector, the lanes' parts added in a fixed
+// order), so that one wide row does not hold its warp for a dependent load per 32 slots.  Each
+// lane adds its pixels in a fixed order, the block adds its warps in a fixed order, and the last
+// block to finish (ticket counter) adds the block partials in block order and writes the
+// penalties: the mean is deterministic.
 __global__ void __launch_bounds__(256) cost_partial_kernel(const float *__restrict__ cost,
                                                            const int *__restrict__ cnt,
                                                            const long long *__restrict__ off, int N, int G,
@@ -302,30 +306,39 @@ __global__ void __launch_bounds__(256) cost_partial_kernel(const float *__restri
                                                            float *__restrict__ pen, unsigned *__restrict__ ticket,
                                                            int *__restrict__ status) {
     double s = 0.0, c = 0.0;
-    for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < N; p += gridDim.x * blockDim.x) {
-        const long long o = off[p];
-        const int n = cnt[p];
-        if (!window_ok(0, n, G, off[p + 1] - o, status) || !row_aligned(o, status) ||
-            !row_aligned(off[p + 1], status))
-            continue;
+    const int lane0 = threadIdx.x & 31;
+    const int wstride = gridDim.x * blockDim.x;
+    for (int base = blockIdx.x * blockDim.x + (threadIdx.x & ~31); base < N; base += wstride) {
+        const int p = base + lane0;
+        long long o = 0;
+        int n = 0;
+        if (p < N) {
+            o = off[p];
+            n = cnt[p];
+            if (!window_ok(0, n, G, off[p + 1] - o, status) || !row_aligned(o, status) ||
+                !row_aligned(off[p + 1], status))
+                n = 0;
+        }
         const float4 *r = reinterpret_cast<const float4 *>(cost + o);
+        float4 v[8];
+#pragma unroll
+        for (int q = 0; q < 8; q++) v[q] = 4 * q < n ? __ldg(r + q) : make_float4(0.f, 0.f, 0.f, 0.f);
         float ps = 0.f;
-        if (n <= 32) {
-            float4 v[8];
 #pragma unroll
-            for (int q = 0; q < 8; q++) v[q] = 4 * q < n ? __ldg(r + q) : make_float4(0.f, 0.f, 0.f, 0.f);
+        for (int q = 0; q < 8; q++) {
+            const int j = 4 * q;
+            ps += (j < n ? v[q].x : 0.f) + (j + 1 < n ? v[q].y : 0.f) + (j + 2 < n ? v[q].z : 0.f) +
+                  (j + 3 < n ? v[q].w : 0.f);
+        }
+        // the slots past 32 of this warp's wide rows: a few are summed by the whole warp, one row at
+        // a time; when most rows are wide (whole-range searches) each lane sums its own in 32-slot
+        // chunks of 8 vector loads issued together
+        unsigned wide = __ballot_sync(0xffffffffu, n > 32);
+        if (__popc(wide) > 4) {
+            for (int j0 = 32; j0 < n; j0 += 32) {
 #pragma unroll
-            for (int q = 0; q < 8; q++) {
-                const int j = 4 * q;
-                ps += (j < n ? v[q].x : 0.f) + (j + 1 < n ? v[q].y : 0.f) + (j + 2 < n ? v[q].z : 0.f) +
-                      (j + 3 < n ? v[q].w : 0.f);
-            }
-        } else {
-            // 32-slot chunks as 8 vector loads issued together, added in the same order
-            for (int j0 = 0; j0 < n; j0 += 32) {
-                float4 v[8];
-#pragma unroll
-                for (int q = 0; q < 8; q++) v[q] = j0 + 4 * q < n ? __ldg(r + (j0 >> 2) + q) : make_float4(0.f, 0.f, 0.f, 0.f);
+                for (int q = 0; q < 8; q++)
+                    v[q] = j0 + 4 * q < n ? __ldg(r + (j0 >> 2) + q) : make_float4(0.f, 0.f, 0.f, 0.f);
 #pragma unroll
                 for (int q = 0; q < 8; q++) {
                     const int j = j0 + 4 * q;
@@ -334,6 +347,22 @@ __global__ void __launch_bounds__(256) cost_partial_kernel(const float *__restri
                               (j + 3 < n ? v[q].w : 0.f);
                 }
             }
+            wide = 0u;
+        }
+        while (wide) {
+            const int src = __ffs(wide) - 1;
+            wide &= wide - 1;
+            const long long ow = __shfl_sync(0xffffffffu, o, src);
+            const int nw = __shfl_sync(0xffffffffu, n, src);
+            const float4 *rw = reinterpret_cast<const float4 *>(cost + ow);
+            float t = 0.f;
+            for (int j = 32 + 4 * lane0; j < nw; j += 128) {
+                const float4 a = __ldg(rw + (j >> 2));
+                t += a.x + (j + 1 < nw ? a.y : 0.f) + (j + 2 < nw ? a.z : 0.f) + (j + 3 < nw ? a.w : 0.f);
+            }
+#pragma unroll
+            for (int k = 16; k > 0; k >>= 1) t += __shfl_xor_sync(0xffffffffu, t, k);
+            if (lane0 == src) ps += t;
         }
         s += (double)ps;
         c += n;
@@ -363,13 +392,24 @@ __global__ void __launch_bounds__(256) cost_partial_kernel(const float *__restri
     }
     __syncthreads();
     if (!last || wid != 0) return;
-    // the last block: all partials are written; add them in block order
+    // the last block: all partials are written; add them in block order (a lane every 32nd, eight
+    // of them loaded together: one L2 round trip per 256 partials instead of one per 32)
     const int nb = gridDim.x;
     s = 0.0;
     c = 0.0;
-    for (int i = lane; i < nb; i += 32) {
-        s += __ldcg(partial + i);
-        c += __ldcg(partial + nb + i);
+    for (int i0 = lane; i0 < nb; i0 += 256) {
+        double sv[8], cv[8];
+#pragma unroll
+        for (int u = 0; u < 8; u++) {
+            const int i = i0 + 32 * u;
+            sv[u] = i < nb ? __ldcg(partial + i) : 0.0;
+            cv[u] = i < nb ? __ldcg(partial + nb + i) : 0.0;
+        }
+#pragma unroll
+        for (int u = 0; u < 8; u++) {
+            s += sv[u];
+            c += cv[u];
+        }
     }
     for (int k = 16; k > 0; k >>= 1) {
         s += __shfl_down_sync(0xffffffffu, s, k);
