@@ -237,6 +237,7 @@ def run_ours(args, ws, rank, local):
         dist.init_process_group("nccl", device_id=dev)
     # the library's autotuner picks the speed knobs for this shape (untimed)
     row_kw, list_ctas = lf.lfsgm_autotune(L.h, views) if args.autotune else (36, 0)
+    sgm_warps = lf.lfsgm_get_tuning(L.h)[2]
 
     def step(events=None):
         L.initial(views)
@@ -396,7 +397,7 @@ def run_ours(args, ws, rank, local):
         "config": {"workload": workload_label(p), "l2": L2_NOTE, "penalties": PENALTY_NOTE,
                    "parallelism": f"replicas x{ws}"},
         "gcell_per_s": round(active / (value * 1e-3) / 1e9, 2),
-        "tuning": {"row_kw": row_kw, "list_ctas_per_sm": list_ctas,
+        "tuning": {"row_kw": row_kw, "list_ctas_per_sm": list_ctas, "sgm_warps": sgm_warps,
                    "note": "speed knobs picked by lfsgm_autotune on this light field before the timed region"},
         "value_stats": {"median": round(statistics.median(stage_each), 4), "min": round(stage_each[0], 4),
                         "p99": round(stage_each[min(len(stage_each) - 1, int(0.99 * len(stage_each)))], 4),
@@ -538,10 +539,10 @@ def run_batch(args, dev):
     t0 = time.perf_counter()
     B = lf.LightFieldBatch(params, views, branches=args.batch_branches, stream=stream)
     tune_s = time.perf_counter() - t0
-    kw, lc = B.knobs()
+    kw, lc, sw = B.knobs()
     knobs = {}
     for i, p in enumerate(params):
-        knobs.setdefault(lfsynth.BATCH_CLASSES[i % 4]["name"], set()).add((int(kw[i]), int(lc[i])))
+        knobs.setdefault(lfsynth.BATCH_CLASSES[i % 4]["name"], set()).add((int(kw[i]), int(lc[i]), int(sw[i])))
     knobs = {k: sorted(v) for k, v in knobs.items()}
     for _ in range(2):
         B.run()
@@ -589,7 +590,7 @@ def run_batch(args, dev):
     pct = lambda a, q: round(float(np.percentile(a, q)), 3)
     return {"lfs": n, "classes": [c["name"] for c in lfsynth.BATCH_CLASSES],
             "branches": int(k), "graph_kernel_nodes": int(nodes), "runs": R,
-            "knobs": {"per_class_row_kw_list_ctas": knobs},
+            "knobs": {"per_class_row_kw_list_ctas_sgm_warps": knobs},
             "lf_per_s": round(n / (batch_ms * 1e-3), 1), "ms_per_batch": round(batch_ms, 3),
             "p50_ms": pct(done, 50), "p99_ms": pct(done, 99),
             "latency": "completion time of each light field after the batch starts (all submitted at once)",

@@ -112,11 +112,24 @@ lfsgm_status lfsgm_set_workspace(lfsgm_handle h, void *dptr, size_t bytes);
  * batch autotuner sets these per shape class.  Errors: LFSGM_ERR_INVALID_ARG for other values. */
 lfsgm_status lfsgm_set_tuning(lfsgm_handle h, int32_t row_kw, int32_t list_ctas_per_sm);
 
+/* Speed knob of the fine SGM (not in the paper): the warps, one scanline each, of a CTA of the
+ * bounded SGM kernel, 2, 4 or 8 (0 = 4).  The aggregate is the same bit for bit for every value
+ * (the direction sum is order-independent); only the time changes, with the light field's shape
+ * (the bench light field runs best with 8, whole-range Middlebury-shaped windows with 4).
+ * lfsgm_get_tuning reads the handle's three knobs (NULL outputs are skipped).  lfsgm_autotune
+ * also picks this one, after the cost knobs, by timing lfsgm_sgm_aggregate with derived
+ * penalties.  Errors: LFSGM_ERR_INVALID_ARG for other values. */
+lfsgm_status lfsgm_set_sgm_warps(lfsgm_handle h, int32_t warps_per_cta);
+lfsgm_status lfsgm_get_tuning(lfsgm_handle h, int32_t *row_kw, int32_t *list_ctas_per_sm,
+                              int32_t *sgm_warps);
+
 /* Picks the speed knobs for this handle's shape on a representative light field (views: device,
  * as for lfsgm_depth): one initial pass, then the cost stage is timed with the row kernel's label
  * span 36 and 44 and, with the better one, with the list kernel's CTAs per SM 8, 16 and 24
  * against the default; the fastest setting is kept (lfsgm_set_tuning) and returned in row_kw and
- * list_ctas_per_sm (host, nullable).  Synchronous; uses the buffers of lfsgm_depth. */
+ * list_ctas_per_sm (host, nullable).  Then lfsgm_sgm_aggregate (derived penalties) is timed with
+ * 4, 8 and 2 SGM warps per CTA and the fastest kept (lfsgm_set_sgm_warps; read it back with
+ * lfsgm_get_tuning).  Synchronous; uses the buffers of lfsgm_depth. */
 lfsgm_status lfsgm_autotune(lfsgm_handle h, const float *views, int32_t *row_kw, int32_t *list_ctas_per_sm);
 
 /* Upper bound of off[N] for this config (every pixel with a whole-range window). */
@@ -255,11 +268,12 @@ lfsgm_status lfsgm_batch_create(int32_t n, const lfsgm_config *cfgs, const float
                                 float *const *disp, void *stream, int32_t branches, lfsgm_batch *out);
 lfsgm_status lfsgm_batch_run(lfsgm_batch b);
 lfsgm_status lfsgm_batch_times(lfsgm_batch b, double *start_ms, double *end_ms, int32_t *branches);
-/* The speed knobs (see lfsgm_set_tuning) each light field of the batch runs with: the autotuner
- * (branches <= 0 at creation) times, per shape class, the cost stage of one member with the row
- * kernel's label span 36 and 44 and then the list kernel's CTAs per SM, and sets the fastest on
- * every member.  row_kw, list_ctas_per_sm: host int32 [n], nullable. */
+/* The speed knobs (see lfsgm_set_tuning, lfsgm_set_sgm_warps) each light field of the batch runs
+ * with: the autotuner (branches <= 0 at creation) tunes one member of each shape class as
+ * lfsgm_autotune does and sets its knobs on every member.  row_kw, list_ctas_per_sm,
+ * warps_per_cta: host int32 [n] (nullable in lfsgm_batch_knobs). */
 lfsgm_status lfsgm_batch_knobs(lfsgm_batch b, int32_t *row_kw, int32_t *list_ctas_per_sm);
+lfsgm_status lfsgm_batch_sgm_warps(lfsgm_batch b, int32_t *warps_per_cta);
 int64_t lfsgm_batch_kernel_nodes(lfsgm_batch b);    /* kernel nodes in the batch's graph */
 const char *lfsgm_batch_last_error(lfsgm_batch b);  /* NULL: error of the last failed create */
 lfsgm_status lfsgm_batch_destroy(lfsgm_batch b);

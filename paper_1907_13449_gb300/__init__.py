@@ -66,7 +66,7 @@ EXPORTS = ["lfsgm_create", "lfsgm_destroy", "lfsgm_workspace_size", "lfsgm_set_w
            "lfsgm_batch_times", "lfsgm_batch_kernel_nodes", "lfsgm_batch_last_error",
            "lfsgm_batch_destroy", "lfsgm_median_filter", "lfsgm_batch_workspace_size", "lfsgm_batch_create_ws",
            "lfsgm_set_tuning", "lfsgm_batch_knobs", "lfsgm_autotune", "lfsgm_sgm_aggregate_record",
-           "lfsgm_backward_recorded"]
+           "lfsgm_backward_recorded", "lfsgm_set_sgm_warps", "lfsgm_get_tuning", "lfsgm_batch_sgm_warps"]
 
 
 def load(build_if_missing: bool = False):
@@ -96,6 +96,9 @@ def load(build_if_missing: bool = False):
         L.lfsgm_backward.argtypes = [vp, vp, vp, vp, vp, vp, f32, f32, vp, vp, vp, vp, vp]
         L.lfsgm_sgm_aggregate_record.argtypes = [vp, vp, vp, vp, vp, f32, f32, vp]
         L.lfsgm_backward_recorded.argtypes = [vp, vp, vp, vp, vp, vp, vp, f32, f32, vp, vp, vp, vp, vp]
+        L.lfsgm_set_sgm_warps.argtypes = [vp, i32]
+        L.lfsgm_get_tuning.argtypes = [vp, P(i32), P(i32), P(i32)]
+        L.lfsgm_batch_sgm_warps.argtypes = [vp, vp]
         L.lfsgm_sync.argtypes = [vp]
         L.lfsgm_last_error.argtypes = [vp]
         L.lfsgm_last_error.restype = C.c_char_p
@@ -390,6 +393,26 @@ def lfsgm_autotune(h, views):
     return int(kw.value), int(lc.value)
 
 
+def lfsgm_set_sgm_warps(h, warps_per_cta=0):
+    """Speed knob of the fine SGM: scanlines (warps) per CTA, 2, 4 or 8 (0 = 4)."""
+    _check(load().lfsgm_set_sgm_warps(h, int(warps_per_cta)), h)
+
+
+def lfsgm_get_tuning(h):
+    """The handle's speed knobs: (row_kw, list_ctas_per_sm, sgm_warps)."""
+    kw, lc, sw = C.c_int32(), C.c_int32(), C.c_int32()
+    _check(load().lfsgm_get_tuning(h, C.byref(kw), C.byref(lc), C.byref(sw)), h)
+    return int(kw.value), int(lc.value), int(sw.value)
+
+
+def lfsgm_batch_sgm_warps(b, n):
+    """The fine SGM's warps per CTA of each light field of a batch (numpy int32 array)."""
+    import numpy as np
+    w = np.zeros(n, np.int32)
+    _bcheck(load().lfsgm_batch_sgm_warps(b, w.ctypes.data_as(C.c_void_p)), b)
+    return w
+
+
 def lfsgm_batch_knobs(b, n):
     """(row_kw, list_ctas_per_sm) per light field of a batch, as numpy int32 arrays."""
     import numpy as np
@@ -449,7 +472,9 @@ class LightFieldBatch:
         return lfsgm_batch_times(self.b, self.n)
 
     def knobs(self):
-        return lfsgm_batch_knobs(self.b, self.n)
+        """(row_kw, list_ctas_per_sm, sgm_warps) per light field, numpy int32 arrays."""
+        kw, lc = lfsgm_batch_knobs(self.b, self.n)
+        return kw, lc, lfsgm_batch_sgm_warps(self.b, self.n)
 
     @property
     def kernel_nodes(self):

@@ -33,7 +33,7 @@
 namespace lfsgm {
 namespace {
 
-constexpr int kSgmWarps = 4;
+constexpr int kSgmWarps = 4;      // default warps (scanlines) per CTA; 2, 4 or 8 (a speed knob)
 
 // L rounded to a multiple of q (see above); B = C + P2 of the cell.  With M = 1.5 x 2^(floor(log2 B)
 // + 23 - qsh), qsh = 23 - log2(paths), every x in [0, B] gives x + M in M's binade, whose spacing
@@ -54,8 +54,8 @@ __device__ __forceinline__ float warp_min(float v) {
 // 3 m+P2, 4 path start; the first of P2, same, g-1, g+1 that equals the minimum, as the adjoint's
 // own recurrence decides it) in codes[r * nnz_cap + slot] and each pixel's lowest minimising slot
 // in amin[r * N + p].
-template <bool REC>
-__global__ void __launch_bounds__(32 * kSgmWarps) fine_sgm_kernel(const float *__restrict__ cost,
+template <bool REC, int WPC>
+__global__ void __launch_bounds__(32 * WPC) fine_sgm_kernel(const float *__restrict__ cost,
                                                                   const int *__restrict__ lo,
                                                                   const int *__restrict__ cnt,
                                                                   const long long *__restrict__ off,
@@ -68,7 +68,8 @@ __global__ void __launch_bounds__(32 * kSgmWarps) fine_sgm_kernel(const float *_
                                                                   int *__restrict__ amin, size_t nnz_cap) {
     extern __shared__ float sm[];
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
-    const int gw = blockIdx.x * kSgmWarps + wib;
+    constexpr int wpc = WPC;
+    const int gw = blockIdx.x * wpc + wib;
     if (gw >= st.cum[st.paths]) return;
     const int rs = __ldg(order + gw);            // longest scanlines first
     const int r = rs & 15, s = rs >> 4;
@@ -83,7 +84,7 @@ __global__ void __launch_bounds__(32 * kSgmWarps) fine_sgm_kernel(const float *_
     float *bufB = bufA + (Gs + 2);                       // this pixel's
     // the metadata of this block of 32 steps and the next one, by step mod 64 (read by the narrow
     // steps with one broadcast load)
-    int2 *meta = reinterpret_cast<int2 *>(sm + (size_t)kSgmWarps * 2 * (Gs + 2)) + wib * 64;
+    int2 *meta = reinterpret_cast<int2 *>(sm + (size_t)wpc * 2 * (Gs + 2)) + wib * 64;
     const float P1 = __ldg(pen), P2 = __ldg(pen + 1);
     const float INF = __int_as_float(0x7f800000);
     if (lane == 0) {
@@ -444,12 +445,15 @@ void build_scan_order(int H, int W, int paths, std::vector<int> &order) {
 cudaError_t launch_fine_sgm(cudaStream_t s, const float *cost, const int *lo, const int *cnt,
                             const long long *off, int H, int W, int G, const float *pen, float *agg,
                             int *status, const int *order, int paths, unsigned char *codes, int *amin,
-                            size_t nnz_cap) {
+                            size_t nnz_cap, int warps_per_cta) {
+    const int wpc = warps_per_cta == 2 || warps_per_cta == 8 ? warps_per_cta : kSgmWarps;
     const ScanTable st = make_scan_table(H, W, paths);
     const int Gs = (G + 31) & ~31;
-    const size_t smem = (size_t)kSgmWarps * (2 * (Gs + 2) * sizeof(float) + 64 * sizeof(int2));
-    const unsigned grid = (unsigned)((st.cum[paths] + kSgmWarps - 1) / kSgmWarps);
-    auto kern = codes ? fine_sgm_kernel<true> : fine_sgm_kernel<false>;
+    const size_t smem = (size_t)wpc * (2 * (Gs + 2) * sizeof(float) + 64 * sizeof(int2));
+    const unsigned grid = (unsigned)((st.cum[paths] + wpc - 1) / wpc);
+    // one instantiation per CTA size, each with its own register budget (launch bounds)
+    auto kern = codes ? (wpc == 2 ? fine_sgm_kernel<true, 2> : wpc == 8 ? fine_sgm_kernel<true, 8> : fine_sgm_kernel<true, 4>)
+                      : (wpc == 2 ? fine_sgm_kernel<false, 2> : wpc == 8 ? fine_sgm_kernel<false, 8> : fine_sgm_kernel<false, 4>);
     if (smem > 48 * 1024) {
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
@@ -457,7 +461,7 @@ cudaError_t launch_fine_sgm(cudaStream_t s, const float *cost, const int *lo, co
     int lp = 0;
     while ((1 << lp) < paths) lp++;
     const int mk = (lp << 23) | (1 << 22);       // (23 - qsh) << 23 with qsh = 23 - log2(paths)
-    kern<<<grid, 32 * kSgmWarps, smem, s>>>(cost, lo, cnt, off, H, W, Gs, pen, G, st, agg, status, order, mk, codes,
+    kern<<<grid, 32 * wpc, smem, s>>>(cost, lo, cnt, off, H, W, Gs, pen, G, st, agg, status, order, mk, codes,
                                             amin, nnz_cap);
     return cudaGetLastError();
 }

@@ -59,7 +59,7 @@ struct lfsgm_ctx {
     int C = 1;                            // colour channels; images are planes view * C + c
     ArmList arms{};
     // tuning knobs (lfsgm_set_tuning): label span of the row kernel's ranges, list-kernel CTAs per SM
-    int row_kw = 36, list_ctas = 0;
+    int row_kw = 36, list_ctas = 0, sgm_warps = 4;
     std::vector<FineTap> h_fine;          // host copy of the shift table (row descriptors are rebuilt from it)
     // device tables
     FineTap *d_fine = nullptr;
@@ -533,6 +533,22 @@ lfsgm_status lfsgm_set_tuning(lfsgm_handle h, int32_t row_kw, int32_t list_ctas_
     return LFSGM_OK;
 }
 
+lfsgm_status lfsgm_set_sgm_warps(lfsgm_handle h, int32_t warps_per_cta) {
+    if (!h) return LFSGM_ERR_INVALID_ARG;
+    if (warps_per_cta != 0 && warps_per_cta != 2 && warps_per_cta != 4 && warps_per_cta != 8)
+        return fail(h, LFSGM_ERR_INVALID_ARG, "tuning: warps_per_cta must be 0, 2, 4 or 8");
+    h->sgm_warps = warps_per_cta == 0 ? 4 : warps_per_cta;
+    return LFSGM_OK;
+}
+
+lfsgm_status lfsgm_get_tuning(lfsgm_handle h, int32_t *row_kw, int32_t *list_ctas_per_sm, int32_t *sgm_warps) {
+    if (!h) return LFSGM_ERR_INVALID_ARG;
+    if (row_kw) *row_kw = h->row_kw;
+    if (list_ctas_per_sm) *list_ctas_per_sm = h->list_ctas;
+    if (sgm_warps) *sgm_warps = h->sgm_warps;
+    return LFSGM_OK;
+}
+
 lfsgm_status lfsgm_max_nnz(lfsgm_handle h, int64_t *nnz) {
     if (!h || !nnz) return LFSGM_ERR_INVALID_ARG;
     *nnz = (int64_t)h->N * ((h->cfg.fine_labels + 3) & ~3);
@@ -700,7 +716,7 @@ lfsgm_status lfsgm_sgm_aggregate(lfsgm_handle h, const float *cost, const int32_
     }));
     LFSGM_TRY(run(h, "fine_sgm", [&] {
         return launch_fine_sgm(s, cost, lo, cnt, o, c.H, c.W, c.fine_labels, h->fpen, agg, h->status, h->d_order,
-                               c.paths);
+                               c.paths, nullptr, nullptr, 0, h->sgm_warps);
     }));
     return LFSGM_OK;
 }
@@ -759,7 +775,7 @@ static lfsgm_status aggregate_recording(lfsgm_handle h, const float *cost, const
     }));
     return run(h, "fine_sgm_record", [&] {
         return launch_fine_sgm(s, cost, lo, cnt, o, c.H, c.W, c.fine_labels, h->fpen, agg, h->status, h->d_order,
-                               c.paths, h->b_codes, h->b_amin, (size_t)cap);
+                               c.paths, h->b_codes, h->b_amin, (size_t)cap, h->sgm_warps);
     });
 }
 
@@ -947,7 +963,7 @@ lfsgm_status depth_buffers(lfsgm_handle h) {
 // then, with the better span, for the list kernel's CTAs per SM 8, 16, 24 against the default;
 // keep the fastest.  kw, lc: the choice.
 lfsgm_status tune_handle(lfsgm_handle h, const float *views, int32_t *lo, int32_t *cnt, int64_t *off, float *cost,
-                         int &kw_out, int &lc_out) {
+                         float *agg, int &kw_out, int &lc_out) {
     LFSGM_TRY(lfsgm_initial_disparity(h, views, 0, 0, lo, cnt, off, nullptr, nullptr, nullptr));
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
@@ -990,9 +1006,32 @@ lfsgm_status tune_handle(lfsgm_handle h, const float *views, int32_t *lo, int32_
             best_lc = lc;
         }
     }
+    if (st == LFSGM_OK) st = lfsgm_set_tuning(h, best_kw, best_lc);
+    // the SGM's warps (scanlines) per CTA, on the cost volume of the chosen knobs (derived penalties)
+    if (st == LFSGM_OK) st = cost_volume_impl(h, views, lo, cnt, off, cost, !h->cfg.boundless);
+    int best_w = 4;
+    float best_sgm = 1e30f;
+    for (int w : {4, 8, 2}) {
+        if (st != LFSGM_OK) break;
+        st = lfsgm_set_sgm_warps(h, w);
+        float best = 1e30f;
+        for (int r = 0; r < 3 && st == LFSGM_OK; r++) {
+            cudaEventRecord(e0, h->stream);
+            st = lfsgm_sgm_aggregate(h, cost, lo, cnt, off, -1.f, -1.f, agg);
+            cudaEventRecord(e1, h->stream);
+            cudaEventSynchronize(e1);
+            float t = 0.f;
+            cudaEventElapsedTime(&t, e0, e1);
+            if (r > 0) best = std::min(best, t);
+        }
+        if (st == LFSGM_OK && best < best_sgm) {
+            best_sgm = best;
+            best_w = w;
+        }
+    }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
-    if (st == LFSGM_OK) st = lfsgm_set_tuning(h, best_kw, best_lc);
+    if (st == LFSGM_OK) st = lfsgm_set_sgm_warps(h, best_w);
     kw_out = best_kw;
     lc_out = best_lc;
     return st;
@@ -1026,7 +1065,7 @@ lfsgm_status lfsgm_autotune(lfsgm_handle h, const float *views, int32_t *row_kw,
     if (!views) return fail(h, LFSGM_ERR_INVALID_ARG, "null views");
     LFSGM_TRY(depth_buffers(h));
     int kw = 36, lc = 0;
-    LFSGM_TRY(tune_handle(h, views, h->o_lo, h->o_cnt, (int64_t *)h->o_off, h->o_cost, kw, lc));
+    LFSGM_TRY(tune_handle(h, views, h->o_lo, h->o_cnt, (int64_t *)h->o_off, h->o_cost, h->o_agg, kw, lc));
     if (row_kw) *row_kw = kw;
     if (list_ctas_per_sm) *list_ctas_per_sm = lc;
     return LFSGM_OK;
@@ -1336,10 +1375,11 @@ lfsgm_status batch_tune_knobs(lfsgm_batch_ctx *b) {
         if (done[i]) continue;
         lfsgm_ctx *h = b->h[i];
         int kw = 36, lc = 0;
-        lfsgm_status st = tune_handle(h, b->views[i], x.lo, x.cnt, (int64_t *)x.off, x.cost, kw, lc);
+        lfsgm_status st = tune_handle(h, b->views[i], x.lo, x.cnt, (int64_t *)x.off, x.cost, x.agg, kw, lc);
         for (int j = i; j < b->n && st == LFSGM_OK; j++)
             if (!done[j] && memcmp(&b->h[j]->cfg, &h->cfg, sizeof(lfsgm_config)) == 0) {
                 st = lfsgm_set_tuning(b->h[j], kw, lc);
+                if (st == LFSGM_OK) st = lfsgm_set_sgm_warps(b->h[j], h->sgm_warps);
                 done[j] = 1;
             }
         if (st != LFSGM_OK) return bfail(b, st, "tuning light field %d: %s", i, h->err.c_str());
@@ -1517,6 +1557,12 @@ lfsgm_status lfsgm_batch_knobs(lfsgm_batch b, int32_t *row_kw, int32_t *list_cta
         if (row_kw) row_kw[i] = b->h[i]->row_kw;
         if (list_ctas_per_sm) list_ctas_per_sm[i] = b->h[i]->list_ctas;
     }
+    return LFSGM_OK;
+}
+
+lfsgm_status lfsgm_batch_sgm_warps(lfsgm_batch b, int32_t *warps_per_cta) {
+    if (!b || !warps_per_cta) return LFSGM_ERR_INVALID_ARG;
+    for (int i = 0; i < b->n; i++) warps_per_cta[i] = b->h[i]->sgm_warps;
     return LFSGM_OK;
 }
 

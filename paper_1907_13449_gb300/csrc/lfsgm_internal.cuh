@@ -234,7 +234,8 @@ cudaError_t launch_cost_partial_sums(cudaStream_t s, const float *cost, const in
 cudaError_t launch_fine_sgm(cudaStream_t s, const float *cost, const int *lo, const int *cnt,
                             const long long *off, int H, int W, int G, const float *pen, float *agg,
                             int *status, const int *order, int paths,
-                            unsigned char *codes = nullptr, int *amin = nullptr, size_t nnz_cap = 0);
+                            unsigned char *codes = nullptr, int *amin = nullptr, size_t nnz_cap = 0,
+                            int warps_per_cta = 4);
 
 cudaError_t launch_median3(cudaStream_t s, const float *in, float *out, int H, int W);
 cudaError_t launch_wta(cudaStream_t s, const float *agg, const int *lo, const int *cnt,

@@ -438,8 +438,9 @@ def test_depth_host_matches_device(gpu_lib, tiny_case):
 
 @pytest.mark.parametrize("paths", [8, 16])
 def test_sgm_aggregate_is_reproducible_at_bench_shape(gpu_lib, paths):
-    """9x9 x 512x512, 31-label windows: two aggregations of the same cost volume are bit-identical
-    (the 8 or 16 directions add into C_s with atomics in whatever order they arrive)."""
+    """9x9 x 512x512, 31-label windows: aggregations of the same cost volume are bit-identical (the
+    8 or 16 directions add into C_s with atomics in whatever order they arrive), also across the
+    SGM's warps-per-CTA speed knob."""
     import dataclasses
 
     import torch
@@ -451,11 +452,17 @@ def test_sgm_aggregate_is_reproducible_at_bench_shape(gpu_lib, paths):
     L.cost_volume(vd)
     nnz = int(L.off[-1].item())
     runs = []
-    for _ in range(3):
+    # three runs with the default CTA size, then one with each other size of the SGM's speed knob:
+    # a scanline's arithmetic does not depend on which CTA runs it
+    for w in (0, 0, 0, 2, 8):
+        gpu_lib.lfsgm_set_sgm_warps(L.h, w)
         L.aggregate(-1.0, -1.0)
         torch.cuda.synchronize()
         runs.append(L.agg[:nnz].clone())
+    assert gpu_lib.lfsgm_get_tuning(L.h)[2] == 8
     gpu_lib.lfsgm_sync(L.h)
+    with pytest.raises(gpu_lib.LfsgmError):
+        gpu_lib.lfsgm_set_sgm_warps(L.h, 3)
     L.close()
     for r in runs[1:]:
         diff = torch.nonzero(runs[0] != r).flatten()
