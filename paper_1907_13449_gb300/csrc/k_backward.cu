@@ -692,6 +692,185 @@ __global__ void __launch_bounds__(32 * kVrWarps) views_backward_rows_kernel(
     if (fits && gref != 0.f) atomicAdd(gviews + (size_t)ref * N + (size_t)y * W + x, gref);
 }
 
+// Colour form of the rows kernel (C = 3, planar views [view * 3 + c]).  The l2 term is the norm of
+// the colour difference, so label t gives channel c the gradient g_c = dLoss/dC * w_l2 * Delta_c /
+// |Delta| (0 where the colours agree), Delta_c = I_ref,c - sample_c = -e_c(t) with e_c the
+// channel's sample-minus-reference quadratic; each channel keeps its own three moments and its own
+// shared-memory box.  Four warps (rows) per CTA, so that the three boxes and the labels' dLoss/dC
+// fit the 48 KB of static shared memory.
+constexpr int kVrWarpsRgb = 4;
+
+__global__ void __launch_bounds__(32 * kVrWarpsRgb) views_backward_rows_rgb_kernel(
+    const float *__restrict__ views, const FineTap *__restrict__ tab, int G, int U, int V, int H, int W, int ref,
+    const int *__restrict__ lo, const int *__restrict__ cnt, const long long *__restrict__ off, float wl2,
+    float fstep, const float *__restrict__ gcost, float *__restrict__ gviews, int2 *__restrict__ list,
+    int *__restrict__ list_count) {
+    constexpr int C = 3, NW = kVrWarpsRgb;
+    __shared__ float box[C][kVrBoxH * kVrBoxW];
+    __shared__ float gcs[NW][KVR][32];             // [row][label of the range][lane]
+    __shared__ int red[2][NW];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int x0 = blockIdx.x * 32, ty0 = blockIdx.y * NW;
+    const int x = x0 + lane, y = ty0 + w;
+    const size_t N = (size_t)H * W;
+    const int nviews = U * V;
+    int l = 0, n = 0;
+    long long o = 0;
+    bool nar = false;
+    if (x < W && y < H) {
+        const size_t p = (size_t)y * W + x;
+        l = __ldg(lo + p);
+        n = __ldg(cnt + p);
+        o = __ldg(off + p);
+        nar = n <= 32 && window_ok(l, n, G, __ldg(off + p + 1) - o, nullptr);
+    }
+    int g0;
+    const int best = row_range<KVR>(l, n, nar, g0);  // warp-uniform (rows past H: no window, -1)
+    const bool fits = best > 0 && nar && l >= g0 && l + n <= g0 + KVR;
+    if (nar && !fits) push_chunks(list, list_count, y * W + x, n);
+#pragma unroll 4
+    for (int j = 0; j < KVR; j++) {
+        const int k = g0 + j - l;
+        gcs[w][j][lane] = (fits && k >= 0 && k < n) ? wl2 * __ldg(gcost + o + k) : 0.f;
+    }
+    if (lane == 0) {
+        red[0][w] = best > 0 ? g0 : 0x7fffffff;
+        red[1][w] = best > 0 ? min(g0 + KVR - 1, G - 1) : -1;
+    }
+    for (int e = threadIdx.x; e < C * kVrBoxH * kVrBoxW; e += blockDim.x) (&box[0][0])[e] = 0.f;
+    __syncthreads();
+    int gmn = red[0][0], gmx = red[1][0];
+    for (int k = 1; k < NW; k++) {
+        gmn = min(gmn, red[0][k]);
+        gmx = max(gmx, red[1][k]);
+    }
+    if (gmx < 0) return;                               // no range in the CTA (uniform)
+    const bool any = best > 0;                         // warp-uniform
+    float Iref[C], gref[C];
+#pragma unroll
+    for (int c = 0; c < C; c++) {
+        Iref[c] = fits ? __ldg(views + ((size_t)ref * C + c) * N + (size_t)y * W + x) : 0.f;
+        gref[c] = 0.f;
+    }
+    for (int view = 0; view < nviews; view++) {
+        if (view == ref) continue;
+        const float ax = (float)(view % U - (ref % U)) * fstep, ay = (float)(view / U - (ref / U)) * fstep;
+        const FineTap ta = load_tap(tab + (size_t)view * G + gmn), tb = load_tap(tab + (size_t)view * G + gmx);
+        const int bx0 = x0 + min(ta.ox, tb.ox), by0 = ty0 + min(ta.oy, tb.oy);
+        const int bw = 32 + abs(tb.ox - ta.ox) + 1, bh = NW + abs(tb.oy - ta.oy) + 1;
+        const bool use_box = bw <= kVrBoxW && bh <= kVrBoxH;
+        const float *I = views + (size_t)view * C * N;             // channel c at + c N
+        float *gI = gviews + (size_t)view * C * N;
+        if (any) {
+            // the range's labels: lane j holds label g0 + j, lanes 0 .. KVR-33 also label g0 + 32 + lane
+            const FineTap t0 = load_tap(tab + (size_t)view * G + min(g0 + lane, G - 1));
+            FineTap t1 = t0;
+            if (lane < KVR - 32) t1 = load_tap(tab + (size_t)view * G + min(g0 + 32 + lane, G - 1));
+            const int c0 = (int)t0.ox * 65536 + (int)t0.oy, c1 = (int)t1.ox * 65536 + (int)t1.oy;
+            const int p0 = __shfl_up_sync(0xffffffffu, c0, 1), p1 = __shfl_up_sync(0xffffffffu, c1, 1);
+            const int c31 = __shfl_sync(0xffffffffu, c0, 31);
+            const unsigned m0 = __ballot_sync(0xffffffffu, lane == 0 || c0 != p0);
+            const unsigned m1 = __ballot_sync(0xffffffffu, lane < KVR - 32 && (lane == 0 ? c1 != c31 : c1 != p1));
+            int js = 0;
+            while (js < KVR) {
+                const int nx = js + 1;
+                const unsigned r0 = nx < 32 ? (m0 & (0xffffffffu << nx)) : 0u;
+                const unsigned r1 = nx < 32 ? m1 : (m1 & (0xffffffffu << (nx - 32)));
+                const int je = r0 ? __ffs(r0) - 1 : (r1 ? 32 + __ffs(r1) - 1 : KVR);
+                const int src = js & 31;
+                const bool hi = js >= 32;
+                const int ox = __shfl_sync(0xffffffffu, hi ? t1.ox : t0.ox, src);
+                const int oy = __shfl_sync(0xffffffffu, hi ? t1.oy : t0.oy, src);
+                const float fx = __shfl_sync(0xffffffffu, hi ? t1.fx : t0.fx, src);
+                const float fy = __shfl_sync(0xffffffffu, hi ? t1.fy : t0.fy, src);
+                const int xa = min(max(x + ox, 0), W - 1), xb = min(max(x + ox + 1, 0), W - 1);
+                const int ya = min(max(y + oy, 0), H - 1), yb = min(max(y + oy + 1, 0), H - 1);
+                if (fits) {
+                    float a0[C], b0[C], cq[C], S0[C], S1[C], S2[C];
+#pragma unroll
+                    for (int c = 0; c < C; c++) {
+                        const float *Ic = I + (size_t)c * N;
+                        const float i00 = __ldg(Ic + (size_t)ya * W + xa), i10 = __ldg(Ic + (size_t)ya * W + xb);
+                        const float i01 = __ldg(Ic + (size_t)yb * W + xa), i11 = __ldg(Ic + (size_t)yb * W + xb);
+                        const float cx = i10 - i00, cy = i01 - i00, cxy = (i11 - i01) - cx;
+                        a0[c] = fmaf(cxy * fx, fy, fmaf(cy, fy, fmaf(cx, fx, i00 - Iref[c])));
+                        b0[c] = fmaf(cxy, fmaf(fx, ay, fy * ax), fmaf(cy, ay, cx * ax));
+                        cq[c] = cxy * ax * ay;
+                        S0[c] = S1[c] = S2[c] = 0.f;
+                    }
+                    float t = 0.f;
+                    for (int j = js; j < je; j++, t += 1.f) {
+                        const float gc = gcs[w][j][lane];
+                        float e[C], sq = 0.f;
+#pragma unroll
+                        for (int c = 0; c < C; c++) {
+                            e[c] = fmaf(t, fmaf(t, cq[c], b0[c]), a0[c]);      // sample - I_ref
+                            sq = fmaf(e[c], e[c], sq);
+                        }
+                        const float sc = sq > 0.f ? -gc * rsqrtf(sq) : 0.f;    // g_c = sc e_c
+#pragma unroll
+                        for (int c = 0; c < C; c++) {
+                            const float g = sc * e[c], gt = g * t;
+                            S0[c] += g;
+                            S1[c] += gt;
+                            S2[c] = fmaf(gt, t, S2[c]);
+                        }
+                    }
+                    const int bxa = xa - bx0, bya = ya - by0;
+                    const bool inbox = use_box && (unsigned)bxa < (unsigned)bw && (unsigned)(xb - bx0) < (unsigned)bw &&
+                                       (unsigned)bya < (unsigned)bh && (unsigned)(yb - by0) < (unsigned)bh;
+#pragma unroll
+                    for (int c = 0; c < C; c++) {
+                        gref[c] += S0[c];
+                        if (S0[c] == 0.f && S1[c] == 0.f && S2[c] == 0.f) continue;
+                        // -sum g w for the corners: w11 = XY, w10 = X (1 - Y), w01 = (1 - X) Y, w00 = (1 - X)(1 - Y)
+                        const float GX = fmaf(ax, S1[c], fx * S0[c]), GY = fmaf(ay, S1[c], fy * S0[c]);
+                        const float GXY = fmaf(ax * ay, S2[c], fmaf(fmaf(fx, ay, fy * ax), S1[c], fx * fy * S0[c]));
+                        const float v00 = -(S0[c] - GX - GY + GXY), v10 = -(GX - GXY), v01 = -(GY - GXY), v11 = -GXY;
+                        if (inbox) {
+                            float *c00 = box[c] + bya * kVrBoxW + bxa;
+                            const int dxb = xb - xa, dyb = (yb - ya) * kVrBoxW;
+                            atomicAdd(c00, v00);
+                            atomicAdd(c00 + dxb, v10);
+                            atomicAdd(c00 + dyb, v01);
+                            atomicAdd(c00 + dyb + dxb, v11);
+                        } else {
+                            float *g = gI + (size_t)c * N;
+                            if (v00 != 0.f) atomicAdd(g + (size_t)ya * W + xa, v00);
+                            if (v10 != 0.f) atomicAdd(g + (size_t)ya * W + xb, v10);
+                            if (v01 != 0.f) atomicAdd(g + (size_t)yb * W + xa, v01);
+                            if (v11 != 0.f) atomicAdd(g + (size_t)yb * W + xb, v11);
+                        }
+                    }
+                }
+                js = je;
+            }
+        }
+        __syncthreads();
+        if (use_box) {
+            // a warp per box row (of each channel), lanes along it
+            for (int r = w; r < C * bh; r += NW) {
+                const int c = r / bh, by = r - c * bh;
+                float *brow = box[c] + by * kVrBoxW;
+                float *grow = gI + (size_t)c * N + (size_t)(by0 + by) * W + bx0;
+                for (int bx = lane; bx < bw; bx += 32) {
+                    const float v = brow[bx];
+                    if (v != 0.f) {
+                        atomicAdd(grow + bx, v);
+                        brow[bx] = 0.f;
+                    }
+                }
+            }
+        }
+        __syncthreads();
+    }
+    if (fits) {
+#pragma unroll
+        for (int c = 0; c < C; c++)
+            if (gref[c] != 0.f) atomicAdd(gviews + ((size_t)ref * C + c) * N + (size_t)y * W + x, gref[c]);
+    }
+}
+
 }  // namespace
 
 cudaError_t launch_softargmin_backward(cudaStream_t s, const float *agg, const int *lo, const int *cnt,
@@ -728,9 +907,9 @@ cudaError_t launch_views_backward(cudaStream_t s, const float *views, const Fine
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     if (C == 3) {
-        // colour: the list holds every window's chunks
-        views_backward_kernel<3><<<sms * 8, 256, 0, s>>>(views, tab, G, nviews, H, W, ref, lo, cnt, off, wl2, gcost,
-                                                         gviews, list, count);
+        dim3 grid((W + 31) / 32, (H + kVrWarpsRgb - 1) / kVrWarpsRgb);
+        views_backward_rows_rgb_kernel<<<grid, 32 * kVrWarpsRgb, 0, s>>>(views, tab, G, U, V, H, W, ref, lo, cnt, off,
+                                                                        wl2, fstep, gcost, gviews, list, count);
         return cudaGetLastError();
     }
     dim3 grid((W + 31) / 32, (H + kVrWarps - 1) / kVrWarps);
@@ -740,15 +919,19 @@ cudaError_t launch_views_backward(cudaStream_t s, const float *views, const Fine
 }
 
 cudaError_t launch_views_backward_list(cudaStream_t s, const float *views, const FineTap *tab, int G, int nviews,
-                                       int H, int W, int ref, const int *lo, const int *cnt, const long long *off,
-                                       float wl2, const float *gcost, float *gviews, const int2 *list,
-                                       const int *count) {
+                                       int C, int H, int W, int ref, const int *lo, const int *cnt,
+                                       const long long *off, float wl2, const float *gcost, float *gviews,
+                                       const int2 *list, const int *count) {
     int dev = 0, sms = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     // windows wider than 32 labels and narrow ones outside their row's range (the list holds their chunks)
-    views_backward_kernel<1><<<sms * 8, 256, 0, s>>>(views, tab, G, nviews, H, W, ref, lo, cnt, off, wl2, gcost, gviews,
-                                                     list, count);
+    if (C == 3)
+        views_backward_kernel<3><<<sms * 8, 256, 0, s>>>(views, tab, G, nviews, H, W, ref, lo, cnt, off, wl2, gcost,
+                                                         gviews, list, count);
+    else
+        views_backward_kernel<1><<<sms * 8, 256, 0, s>>>(views, tab, G, nviews, H, W, ref, lo, cnt, off, wl2, gcost,
+                                                         gviews, list, count);
     return cudaGetLastError();
 }
 

@@ -804,24 +804,22 @@ static lfsgm_status backward_from_record(lfsgm_handle h, const float *views, con
                                    false);
     }));
     if (grad_views) {
-        // the (pixel, 32-label chunk) items of windows wider than 32 labels; narrower ones by tiles
-        // (grey); colour windows all go through the item list
+        // the (pixel, 32-label chunk) items of windows wider than 32 labels; narrower ones by rows,
+        // which add the windows outside their row's label range to the items
         e = cudaMemsetAsync(h->wide_count, 0, 4, s);
         if (e != cudaSuccess) return cuda_fail(h, e, "memset");
         LFSGM_TRY(run(h, "list_all", [&] {
-            return launch_list_all(s, lo, cnt, o, c.fine_labels, h->wide_list, h->wide_count, h->N, h->status,
-                                   h->C > 1 ? 0 : 32);
+            return launch_list_all(s, lo, cnt, o, c.fine_labels, h->wide_list, h->wide_count, h->N, h->status, 32);
         }));
         LFSGM_TRY(run(h, "views_backward", [&] {
             return launch_views_backward(s, views, h->d_fine, c.fine_labels, c.U, c.V, h->C, c.H, c.W, h->ref, lo,
                                          cnt, o, c.w_l2, (float)step, grad_cost, grad_views, h->wide_list,
                                          h->wide_count);
         }));
-        if (h->C == 1)
-            LFSGM_TRY(run(h, "views_backward_list", [&] {
-                return launch_views_backward_list(s, views, h->d_fine, c.fine_labels, h->nviews, c.H, c.W, h->ref, lo,
-                                                  cnt, o, c.w_l2, grad_cost, grad_views, h->wide_list, h->wide_count);
-            }));
+        LFSGM_TRY(run(h, "views_backward_list", [&] {
+            return launch_views_backward_list(s, views, h->d_fine, c.fine_labels, h->nviews, h->C, c.H, c.W, h->ref,
+                                              lo, cnt, o, c.w_l2, grad_cost, grad_views, h->wide_list, h->wide_count);
+        }));
     }
     e = cudaMemcpyAsync(grad_P1, h->b_gp, 4, cudaMemcpyDeviceToDevice, s);
     if (e == cudaSuccess) e = cudaMemcpyAsync(grad_P2, h->b_gp + 1, 4, cudaMemcpyDeviceToDevice, s);

@@ -255,9 +255,9 @@ cudaError_t launch_views_backward(cudaStream_t s, const float *views, const Fine
                                   float wl2, float fstep, const float *gcost, float *gviews, int2 *list, int *count);
 // Grey: the items of the list (wide windows, and narrow ones the row kernel left) after launch_views_backward.
 cudaError_t launch_views_backward_list(cudaStream_t s, const float *views, const FineTap *tab, int G, int nviews,
-                                       int H, int W, int ref, const int *lo, const int *cnt, const long long *off,
-                                       float wl2, const float *gcost, float *gviews, const int2 *list,
-                                       const int *count);
+                                       int C, int H, int W, int ref, const int *lo, const int *cnt,
+                                       const long long *off, float wl2, const float *gcost, float *gviews,
+                                       const int2 *list, const int *count);
 
 constexpr int kPartialBlocks = 1024;
 
