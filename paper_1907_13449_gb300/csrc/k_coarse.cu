@@ -77,15 +77,19 @@ struct CVec<8> {
 // present label's path cost (at most C + P2) stays below 2^13 = kAbsent for 8 and 16 paths.
 constexpr int kAbsent = 0x2000;
 
-// One warp per run of 32 pixels of a row and one arm, lane = pixel: a label's shift is the same
-// for every pixel, so for each (label, view) the 32 lanes read 32 consecutive words -- one
-// coalesced 256-byte access.  Labels go 4 at a time (their offsets are one uniform 16-byte load),
-// and each lane stores its pixel's 4 costs as one 8-byte word (a staging tile in shared memory
-// made the stores coalesced but took the L1 capacity the census gathers live on: 0.42 vs 0.34 ms
-// on 9x9 x 512x512).  Lanes past the end of the row repeat the last pixel and are not stored.
-// OT = uint8_t when every cost fits a byte (arm views x census bits x channels <= 255): half the
-// bytes for the eight sweeps of the SGM to read; padding labels then hold 0 and the SGM marks
-// them absent itself.
+// One warp per run of 32 pixels of a row and one arm, lane = pixel.  A label's shift is the same
+// for every pixel, and a view's nearest shift changes only every few labels (a view at distance d
+// has about 2 d |dmax - dmin| + 1 distinct shifts over the labels), so a view's Hamming distance
+// is a step function of the label: the warp finds the steps of a view 32 labels at a time (lane =
+// label, a ballot of the labels whose offset differs from the previous one) and, for each step,
+// reads the 32 pixels' words at the new offset (one coalesced 256-byte access), and adds the
+// change of each pixel's distance to that label's entry of the lane's own difference column in
+// shared memory (two labels' 16-bit differences a word).  A prefix sum over the labels then gives
+// each pixel's costs, stored 4 labels a word (staging them in shared memory to write the warp's
+// contiguous rows coalesced took a third of the CTAs per SM and was slower: 0.31 vs 0.24 ms).
+// Lanes past the end of the row repeat the last pixel and are not stored.  OT = uint8_t when every cost fits a byte (arm views x census bits x
+// channels <= 255): half the bytes for the eight sweeps of the SGM to read; padding labels then
+// hold 0 and the SGM marks them absent itself.
 template <int C, typename OT>
 __global__ void __launch_bounds__(128) coarse_cost_kernel(const uint64_t *__restrict__ cen_pad, size_t HWp, int Wp,
                                                           int P, int H, int W, int ref,
@@ -93,6 +97,7 @@ __global__ void __launch_bounds__(128) coarse_cost_kernel(const uint64_t *__rest
                                                           const int *__restrict__ otab, CoarseArms ca, int Lc,
                                                           int Lcd, OT *__restrict__ out,
                                                           unsigned long long *__restrict__ armsum) {
+    extern __shared__ int cdiff[];                 // [warp][Lcd / 2][32]
     const int a = blockIdx.y;
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const int runs_x = (W + 31) >> 5;
@@ -103,45 +108,66 @@ __global__ void __launch_bounds__(128) coarse_cost_kernel(const uint64_t *__rest
     const int nv = ca.nv[a];
     const int *views = armviews + a * kMaxArmViews;
     const int *ot = otab + ca.tab_off[a];
+    int *cd = cdiff + (size_t)w * (Lcd / 2) * 32 + lane;
+    for (int i = 0; i < Lcd / 2; i++) cd[32 * i] = 0;
     uint64_t r[C];
 #pragma unroll
     for (int ch = 0; ch < C; ch++) r[ch] = __ldg(cen_pad + ((size_t)ref * C + ch) * HWp + base);
+    for (int v = 0; v < nv; v++) {
+        const size_t vb = (size_t)__ldg(views + v) * C;
+        int hp = 0, oprev = 0;
+        for (int k0 = 0; k0 < Lc; k0 += 32) {
+            const int k = k0 + lane;
+            const int o = k < Lc ? __ldg(ot + v * Lcd + k) : 0;
+            const int up = __shfl_up_sync(0xffffffffu, o, 1);
+            const int before = lane == 0 ? oprev : up;
+            unsigned steps = __ballot_sync(0xffffffffu, k < Lc && (k == 0 || o != before));
+            oprev = __shfl_sync(0xffffffffu, o, 31);
+            while (steps) {
+                const int b = __ffs(steps) - 1;
+                steps &= steps - 1;
+                const int off = __shfl_sync(0xffffffffu, o, b);
+                int h = 0;
+#pragma unroll
+                for (int ch = 0; ch < C; ch++) h += __popcll(r[ch] ^ __ldg(cen_pad + (vb + ch) * HWp + base + off));
+                const int kb = k0 + b;
+                cd[32 * (kb >> 1)] += (int)((unsigned)(h - hp) << (16 * (kb & 1)));
+                hp = h;
+            }
+        }
+    }
     OT *O = out + ((size_t)a * H * W + (size_t)y * W + min(x0 + lane, W - 1)) * Lcd;
     const bool store = x0 + lane < W;
     unsigned long long total = 0;
+    int run = 0;
     for (int k0 = 0; k0 < Lcd; k0 += 4) {
-        int c0 = 0, c1 = 0, c2 = 0, c3 = 0;
-        if (k0 < Lc) {
-            for (int v = 0; v < nv; v++) {
-                const int4 o = __ldg(reinterpret_cast<const int4 *>(ot + v * Lcd + k0));
-                const size_t vb = (size_t)__ldg(views + v) * C;
+        int c[4];
 #pragma unroll
-                for (int ch = 0; ch < C; ch++) {
-                    const uint64_t *q = cen_pad + (vb + ch) * HWp + base;
-                    c0 += __popcll(r[ch] ^ __ldg(q + o.x));
-                    c1 += __popcll(r[ch] ^ __ldg(q + o.y));
-                    c2 += __popcll(r[ch] ^ __ldg(q + o.z));
-                    c3 += __popcll(r[ch] ^ __ldg(q + o.w));
-                }
-            }
-            if (k0 + 1 >= Lc) c1 = 0;
-            if (k0 + 2 >= Lc) c2 = 0;
-            if (k0 + 3 >= Lc) c3 = 0;
+        for (int q = 0; q < 2; q++) {
+            // the word holds d(k) + d(k+1) 2^16 (two's complement, |d| < 2^15): split it exactly
+            const int wd = cd[32 * ((k0 >> 1) + q)];
+            const int d0 = (int)(short)(wd & 0xffff), d1 = (wd - d0) >> 16;
+            run += d0;
+            c[2 * q] = run;
+            run += d1;
+            c[2 * q + 1] = run;
         }
-        if (store) total += (unsigned)(c0 + c1 + c2 + c3);
+#pragma unroll
+        for (int q = 0; q < 4; q++)
+            if (k0 + q >= Lc) c[q] = 0;
+        if (store) total += (unsigned)(c[0] + c[1] + c[2] + c[3]);
         if constexpr (sizeof(OT) == 1) {
             if (store)
                 *reinterpret_cast<uint32_t *>(O + k0) =
-                    (uint32_t)c0 | ((uint32_t)c1 << 8) | ((uint32_t)c2 << 16) | ((uint32_t)c3 << 24);
+                    (uint32_t)c[0] | ((uint32_t)c[1] << 8) | ((uint32_t)c[2] << 16) | ((uint32_t)c[3] << 24);
         } else {
             // padding labels (k >= Lc) hold kAbsent, above every path cost of a present label
-            if (k0 + 0 >= Lc) c0 = kAbsent;
-            if (k0 + 1 >= Lc) c1 = kAbsent;
-            if (k0 + 2 >= Lc) c2 = kAbsent;
-            if (k0 + 3 >= Lc) c3 = kAbsent;
+#pragma unroll
+            for (int q = 0; q < 4; q++)
+                if (k0 + q >= Lc) c[q] = kAbsent;
             if (store)
-                *reinterpret_cast<uint2 *>(O + k0) = make_uint2((uint32_t)c0 | ((uint32_t)c1 << 16),
-                                                                (uint32_t)c2 | ((uint32_t)c3 << 16));
+                *reinterpret_cast<uint2 *>(O + k0) = make_uint2((uint32_t)c[0] | ((uint32_t)c[1] << 16),
+                                                                (uint32_t)c[2] | ((uint32_t)c[3] << 16));
         }
     }
     for (int o = 16; o > 0; o >>= 1) total += __shfl_down_sync(0xffffffffu, total, o);
@@ -395,12 +421,24 @@ cudaError_t launch_coarse_cost(cudaStream_t s, const uint64_t *cen_pad, int P, i
     const size_t HWp = (size_t)Hp * Wp;
     const long long tasks = (long long)((W + 31) / 32) * H;
     dim3 grid((unsigned)((tasks + 3) / 4), (unsigned)ca.n_arms);
+    // the warps' label-difference columns (Lcd is a multiple of 4)
+    const size_t smem = (size_t)4 * (Lcd / 2) * 32 * sizeof(int);
     if (out8) {
         auto kern = C == 3 ? coarse_cost_kernel<3, uint8_t> : coarse_cost_kernel<1, uint8_t>;
-        kern<<<grid, 128, 0, s>>>(cen_pad, HWp, Wp, P, H, W, ref, armviews, otab, ca, Lc, Lcd, (uint8_t *)out, armsum);
+        if (smem > 48 * 1024) {
+            const cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            if (e != cudaSuccess) return e;
+        }
+        kern<<<grid, 128, smem, s>>>(cen_pad, HWp, Wp, P, H, W, ref, armviews, otab, ca, Lc, Lcd, (uint8_t *)out,
+                                     armsum);
     } else {
         auto kern = C == 3 ? coarse_cost_kernel<3, uint16_t> : coarse_cost_kernel<1, uint16_t>;
-        kern<<<grid, 128, 0, s>>>(cen_pad, HWp, Wp, P, H, W, ref, armviews, otab, ca, Lc, Lcd, (uint16_t *)out, armsum);
+        if (smem > 48 * 1024) {
+            const cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            if (e != cudaSuccess) return e;
+        }
+        kern<<<grid, 128, smem, s>>>(cen_pad, HWp, Wp, P, H, W, ref, armviews, otab, ca, Lc, Lcd, (uint16_t *)out,
+                                     armsum);
     }
     return cudaGetLastError();
 }
