@@ -137,11 +137,14 @@ constexpr int kDsMask = 16, kDsAxy = 24, kDsSegs = 32, kDsSegBytes = 32, kDsCenB
 
 __device__ __forceinline__ unsigned smem_u32(const void *p) { return (unsigned)__cvta_generic_to_shared(p); }
 
+// Bounded wait on an mbarrier phase: each try_wait may suspend the thread for up to 200 ns (a hint;
+// it returns as soon as the phase completes), so a wait polls a few times instead of spinning, and
+// 2^20 tries bound it to about 0.2 s.
 __device__ __forceinline__ bool mbar_wait(unsigned mbar, unsigned parity) {
     for (int it = 0; it < (1 << 20); it++) {
         unsigned done;
-        asm volatile("{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
-                     : "=r"(done) : "r"(mbar), "r"(parity) : "memory");
+        asm volatile("{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n selp.u32 %0, 1, 0, p;\n}"
+                     : "=r"(done) : "r"(mbar), "r"(parity), "n"(200) : "memory");
         if (done) return true;
     }
     return false;
