@@ -123,16 +123,32 @@ __global__ void __launch_bounds__(128) coarse_cost_kernel(const uint64_t *__rest
             const int before = lane == 0 ? oprev : up;
             unsigned steps = __ballot_sync(0xffffffffu, k < Lc && (k == 0 || o != before));
             oprev = __shfl_sync(0xffffffffu, o, 31);
+            // the steps four at a time: their word loads are issued together, then their distances
             while (steps) {
-                const int b = __ffs(steps) - 1;
-                steps &= steps - 1;
-                const int off = __shfl_sync(0xffffffffu, o, b);
-                int h = 0;
+                int bs[4];
+                uint64_t wv[4][C];
 #pragma unroll
-                for (int ch = 0; ch < C; ch++) h += __popcll(r[ch] ^ __ldg(cen_pad + (vb + ch) * HWp + base + off));
-                const int kb = k0 + b;
-                cd[32 * (kb >> 1)] += (int)((unsigned)(h - hp) << (16 * (kb & 1)));
-                hp = h;
+                for (int u = 0; u < 4; u++) {
+                    bs[u] = steps ? __ffs(steps) - 1 : -1;          // warp-uniform
+                    steps &= steps - 1;
+                }
+#pragma unroll
+                for (int u = 0; u < 4; u++) {
+                    const int off = __shfl_sync(0xffffffffu, o, bs[u] & 31);
+#pragma unroll
+                    for (int ch = 0; ch < C; ch++)
+                        wv[u][ch] = bs[u] >= 0 ? __ldg(cen_pad + (vb + ch) * HWp + base + off) : 0ull;
+                }
+#pragma unroll
+                for (int u = 0; u < 4; u++) {
+                    if (bs[u] < 0) break;
+                    int h = 0;
+#pragma unroll
+                    for (int ch = 0; ch < C; ch++) h += __popcll(r[ch] ^ wv[u][ch]);
+                    const int kb = k0 + bs[u];
+                    cd[32 * (kb >> 1)] += (int)((unsigned)(h - hp) << (16 * (kb & 1)));
+                    hp = h;
+                }
             }
         }
     }
