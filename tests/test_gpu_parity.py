@@ -535,3 +535,35 @@ def test_plenoptic_shape_full_parity(gpu_lib):
     cfg = oracle.make_cfg(p)
     ref = oracle.depth(cfg, views, p1f=p.p1_frac, p2f=p.p2_frac)
     _full_parity(gpu_lib, views, p, ref)
+
+
+def test_autotune_picks_valid_knobs_and_keeps_the_depth(gpu_lib, tiny_case):
+    """lfsgm_autotune sets the handle's three speed knobs to values from their candidate sets
+    (lfsgm_get_tuning reads them back), and the depth afterwards is the default knobs' depth: bit
+    for bit with the default label span (the list kernel's CTA count and the SGM's CTA size do
+    not change the arithmetic), else to rounding (a window may move between the row and the list
+    kernel, which add the views in different FP32 orders)."""
+    import torch
+    views, gt, p, cfg, ref = tiny_case
+    h = gpu_lib.lfsgm_create(p)
+    vd = _dev(views)
+    label0 = torch.empty(p.N, dtype=torch.int32, device="cuda")
+    disp0 = torch.empty(p.N, dtype=torch.float32, device="cuda")
+    gpu_lib.lfsgm_depth(h, vd, disp0, label0)
+    kw, lc = gpu_lib.lfsgm_autotune(h, vd)
+    assert kw in (36, 44) and lc in (0, 8, 16, 24)
+    tuned = gpu_lib.lfsgm_get_tuning(h)
+    assert tuned[:2] == (kw, lc) and tuned[2] in (2, 4, 8)
+    label1 = torch.empty_like(label0)
+    disp1 = torch.empty_like(disp0)
+    gpu_lib.lfsgm_depth(h, vd, disp1, label1)
+    gpu_lib.lfsgm_sync(h)
+    gpu_lib.lfsgm_destroy(h)
+    d0, d1, l0, l1 = _np(disp0), _np(disp1), _np(label0), _np(label1)
+    if kw == 36:
+        assert np.array_equal(l0, l1) and np.array_equal(d0, d1, equal_nan=True)
+    else:
+        same = l0 == l1
+        assert np.mean(same) >= 0.99
+        ok = same & np.isfinite(d0) & np.isfinite(d1)
+        assert np.abs(d0[ok] - d1[ok]).max() <= 1e-3
