@@ -105,8 +105,10 @@ lfsgm_status lfsgm_set_workspace(lfsgm_handle h, void *dptr, size_t bytes);
 /* Speed knobs (not in the paper): the label span of the row cost kernel's ranges (row_kw 36 or
  * 44; 0 = 36; colour light fields run span 36 only, and with 44 send every window to the list
  * kernel), and the CTAs per SM of the (pixel, chunk) list kernel (list_ctas_per_sm 1..64; 0 = the
- * default: the CTAs resident at once, one wave).  A wider span sends fewer windows to the list kernel
- * and computes more labels per row.  Changing the span rebuilds the row descriptors on the host
+ * default: the CTAs resident at once, one wave; grey light fields run a 32-register form of the
+ * kernel for the default and 16 or more, a 40-register one below 16).  A wider span sends fewer
+ * windows to the list kernel and computes more labels per row.  Changing the span rebuilds the
+ * row descriptors on the host
  * and synchronises the handle's stream; results change only in the last bits (a window moves
  * between the row and the list kernel, which add the views in different FP32 orders).  The
  * batch autotuner sets these per shape class.  Errors: LFSGM_ERR_INVALID_ARG for other values. */
@@ -125,7 +127,7 @@ lfsgm_status lfsgm_get_tuning(lfsgm_handle h, int32_t *row_kw, int32_t *list_cta
 
 /* Picks the speed knobs for this handle's shape on a representative light field (views: device,
  * as for lfsgm_depth): one initial pass, then the cost stage is timed with the row kernel's label
- * span 36 and 44 and, with the better one, with the list kernel's CTAs per SM 8, 16 and 24
+ * span 36 and 44 and, with the better one, with the list kernel's CTAs per SM 8, 12 and 24
  * against the default; the fastest setting is kept (lfsgm_set_tuning) and returned in row_kw and
  * list_ctas_per_sm (host, nullable).  Then lfsgm_sgm_aggregate (derived penalties) is timed with
  * 4, 8 and 2 SGM warps per CTA and the fastest kept (lfsgm_set_sgm_warps; read it back with

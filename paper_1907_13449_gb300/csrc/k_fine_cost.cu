@@ -406,8 +406,12 @@ __global__ void __launch_bounds__(128, C == 1 ? 5 : 2) fine_cost_rows(const __gr
 // (Sec. III-B/C).
 constexpr int kListWarps = 4;
 
-template <int C>
-__global__ void __launch_bounds__(32 * kListWarps) fine_cost_list(const float *__restrict__ views_pad,
+// LEAN (grey): 32 registers for 16 CTAs of 128 threads per SM (a few spilled bytes); the grey
+// list is latency-bound, and the extra warps took the bench light field's list from 0.241 to
+// 0.193 ms, while the all-wide Middlebury-shaped list runs best with 40 registers and 12 CTAs
+// (0.697 vs 0.722 ms): the speed knob picks.
+template <int C, bool LEAN>
+__global__ void __launch_bounds__(32 * kListWarps, C == 3 ? 9 : (LEAN ? 16 : 12)) fine_cost_list(const float *__restrict__ views_pad,
                                                       const uint64_t *__restrict__ cen_pad, int P, int Wp, int Hp,
                                                       const int4 *__restrict__ ltab, int G, int nviews,
                                                       int W, int ref, const int *__restrict__ lo,
@@ -714,19 +718,17 @@ cudaError_t launch_fine_cost_list(cudaStream_t s, const float *views_pad, const 
     // warps then sweep the list (pixel order) once, together, and the views around the rows in
     // flight stay in L2; a second wave would sweep the whole image again (colour: 9 resident CTAs
     // per SM, 4.35 ms, against 4.92 ms with 24 and 6.48 ms with 12)
+    // grey: the lean instantiation by default and for 16 or more CTAs per SM, the other one below
+    const bool lean = C == 1 && (ctas_per_sm <= 0 || ctas_per_sm >= 16);
+    auto kern = C == 3 ? fine_cost_list<3, false> : (lean ? fine_cost_list<1, true> : fine_cost_list<1, false>);
     int k = ctas_per_sm;
     if (k <= 0) {
-        const cudaError_t e = C == 3 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&k, fine_cost_list<3>, 32 * kListWarps, 0)
-                                     : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&k, fine_cost_list<1>, 32 * kListWarps, 0);
+        const cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&k, kern, 32 * kListWarps, 0);
         if (e != cudaSuccess) return e;
         k = max(k, 1);
     }
-    if (C == 3)
-        fine_cost_list<3><<<sms * k, 32 * kListWarps, 0, s>>>(views_pad, cen_pad, P, Wp, Hp, ltab, G, nviews, W, ref,
-                                                             lo, cnt, off, wl2, wc, cost, list, count);
-    else
-        fine_cost_list<1><<<sms * k, 32 * kListWarps, 0, s>>>(views_pad, cen_pad, P, Wp, Hp, ltab, G, nviews, W, ref,
-                                                             lo, cnt, off, wl2, wc, cost, list, count);
+    kern<<<sms * k, 32 * kListWarps, 0, s>>>(views_pad, cen_pad, P, Wp, Hp, ltab, G, nviews, W, ref, lo, cnt, off, wl2,
+                                             wc, cost, list, count);
     return cudaGetLastError();
 }
 

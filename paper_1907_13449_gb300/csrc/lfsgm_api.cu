@@ -958,7 +958,7 @@ lfsgm_status depth_buffers(lfsgm_handle h) {
 
 // The speed knobs of one handle: with the windows of one initial pass of `views` in (lo, cnt, off),
 // time the cost stage (best of two after a warm-up) for the row kernel's label span 36 and 44 and
-// then, with the better span, for the list kernel's CTAs per SM 8, 16, 24 against the default;
+// then, with the better span, for the list kernel's CTAs per SM 8, 12, 24 against the default;
 // keep the fastest.  kw, lc: the choice.
 lfsgm_status tune_handle(lfsgm_handle h, const float *views, int32_t *lo, int32_t *cnt, int64_t *off, float *cost,
                          float *agg, int &kw_out, int &lc_out) {
@@ -995,7 +995,7 @@ lfsgm_status tune_handle(lfsgm_handle h, const float *views, int32_t *lo, int32_
             best_kw = kw;
         }
     }
-    for (int lc : {8, 16, 24}) {
+    for (int lc : {8, 12, 24}) {
         if (st != LFSGM_OK) break;
         float ms = 0.f;
         st = time_cost(best_kw, lc, ms);
