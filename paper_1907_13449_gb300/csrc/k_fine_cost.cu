@@ -409,9 +409,9 @@ constexpr int kListWarps = 4;
 // LEAN (grey): 32 registers for 16 CTAs of 128 threads per SM (a few spilled bytes); the grey
 // list is latency-bound, and the extra warps took the bench light field's list from 0.241 to
 // 0.193 ms, while the all-wide Middlebury-shaped list runs best with 40 registers and 12 CTAs
-// (0.697 vs 0.722 ms): the speed knob picks.
+// (0.697 vs 0.722 ms): the speed knob picks.  Colour: 12 CTAs per SM (0.42 -> 0.37 ms against 9).
 template <int C, bool LEAN>
-__global__ void __launch_bounds__(32 * kListWarps, C == 3 ? 9 : (LEAN ? 16 : 12)) fine_cost_list(const float *__restrict__ views_pad,
+__global__ void __launch_bounds__(32 * kListWarps, C == 3 ? 12 : (LEAN ? 16 : 12)) fine_cost_list(const float *__restrict__ views_pad,
                                                       const uint64_t *__restrict__ cen_pad, int P, int Wp, int Hp,
                                                       const int4 *__restrict__ ltab, int G, int nviews,
                                                       int W, int ref, const int *__restrict__ lo,
