@@ -125,13 +125,26 @@ lfsgm_status lfsgm_set_sgm_warps(lfsgm_handle h, int32_t warps_per_cta);
 lfsgm_status lfsgm_get_tuning(lfsgm_handle h, int32_t *row_kw, int32_t *list_ctas_per_sm,
                               int32_t *sgm_warps);
 
+/* Speed knob of the fine SGM (not in the paper): a scanline that crosses at least min_wide
+ * windows wider than 32 labels (0 = none, the default; lfsgm_autotune tries 24) runs on all the
+ * warps of one CTA, which share each wide step's 32-label chunks, instead of on one warp.  Such
+ * scanlines (along image borders, where the initial pass leaves whole-range windows) otherwise
+ * outlast all others; the CTA's other warps wait while its first runs the narrow steps, so the
+ * split pays only where a few scanlines are much longer than the rest.  Each
+ * lfsgm_sgm_aggregate then first lists them (one small kernel after zeroing agg); when more than
+ * 256 qualify (most windows wide), none is split.  The aggregate is the same bit for bit with any
+ * value.  lfsgm_get_sgm_split reads it back.  Errors: LFSGM_ERR_INVALID_ARG for a negative value. */
+lfsgm_status lfsgm_set_sgm_split(lfsgm_handle h, int32_t min_wide);
+lfsgm_status lfsgm_get_sgm_split(lfsgm_handle h, int32_t *min_wide);
+
 /* Picks the speed knobs for this handle's shape on a representative light field (views: device,
  * as for lfsgm_depth): one initial pass, then the cost stage is timed with the row kernel's label
  * span 36 and 44 and, with the better one, with the list kernel's CTAs per SM 8, 12 and 24
  * against the default; the fastest setting is kept (lfsgm_set_tuning) and returned in row_kw and
  * list_ctas_per_sm (host, nullable).  Then lfsgm_sgm_aggregate (derived penalties) is timed with
- * 4, 8 and 2 SGM warps per CTA and the fastest kept (lfsgm_set_sgm_warps; read it back with
- * lfsgm_get_tuning).  Synchronous; uses the buffers of lfsgm_depth. */
+ * 4, 8 and 2 SGM warps per CTA, each with the split off and at threshold 24 (lfsgm_set_sgm_split), and
+ * the fastest pair kept (lfsgm_set_sgm_warps; read the warps back with lfsgm_get_tuning).
+ * Synchronous; uses the buffers of lfsgm_depth. */
 lfsgm_status lfsgm_autotune(lfsgm_handle h, const float *views, int32_t *row_kw, int32_t *list_ctas_per_sm);
 
 /* Upper bound of off[N] for this config (every pixel with a whole-range window). */

@@ -66,7 +66,8 @@ EXPORTS = ["lfsgm_create", "lfsgm_destroy", "lfsgm_workspace_size", "lfsgm_set_w
            "lfsgm_batch_times", "lfsgm_batch_kernel_nodes", "lfsgm_batch_last_error",
            "lfsgm_batch_destroy", "lfsgm_median_filter", "lfsgm_batch_workspace_size", "lfsgm_batch_create_ws",
            "lfsgm_set_tuning", "lfsgm_batch_knobs", "lfsgm_autotune", "lfsgm_sgm_aggregate_record",
-           "lfsgm_backward_recorded", "lfsgm_set_sgm_warps", "lfsgm_get_tuning", "lfsgm_batch_sgm_warps"]
+           "lfsgm_backward_recorded", "lfsgm_set_sgm_warps", "lfsgm_get_tuning", "lfsgm_batch_sgm_warps",
+           "lfsgm_set_sgm_split", "lfsgm_get_sgm_split"]
 
 
 def load(build_if_missing: bool = False):
@@ -97,6 +98,8 @@ def load(build_if_missing: bool = False):
         L.lfsgm_sgm_aggregate_record.argtypes = [vp, vp, vp, vp, vp, f32, f32, vp]
         L.lfsgm_backward_recorded.argtypes = [vp, vp, vp, vp, vp, vp, vp, f32, f32, vp, vp, vp, vp, vp]
         L.lfsgm_set_sgm_warps.argtypes = [vp, i32]
+        L.lfsgm_set_sgm_split.argtypes = [vp, i32]
+        L.lfsgm_get_sgm_split.argtypes = [vp, C.POINTER(i32)]
         L.lfsgm_get_tuning.argtypes = [vp, P(i32), P(i32), P(i32)]
         L.lfsgm_batch_sgm_warps.argtypes = [vp, vp]
         L.lfsgm_sync.argtypes = [vp]
@@ -396,6 +399,19 @@ def lfsgm_autotune(h, views):
 def lfsgm_set_sgm_warps(h, warps_per_cta=0):
     """Speed knob of the fine SGM: scanlines (warps) per CTA, 2, 4 or 8 (0 = 4)."""
     _check(load().lfsgm_set_sgm_warps(h, int(warps_per_cta)), h)
+
+
+def lfsgm_set_sgm_split(h, min_wide=0):
+    """Speed knob of the fine SGM: scanlines crossing at least min_wide windows wider than 32
+    labels run on all warps of a CTA (0: none)."""
+    _check(load().lfsgm_set_sgm_split(h, int(min_wide)), h)
+
+
+def lfsgm_get_sgm_split(h):
+    """The handle's SGM split threshold (0: off)."""
+    v = C.c_int32()
+    _check(load().lfsgm_get_sgm_split(h, C.byref(v)), h)
+    return int(v.value)
 
 
 def lfsgm_get_tuning(h):

@@ -34,6 +34,7 @@ namespace lfsgm {
 namespace {
 
 constexpr int kSgmWarps = 4;      // default warps (scanlines) per CTA; 2, 4 or 8 (a speed knob)
+constexpr int kSplitCap = 256;    // most scanlines split across a CTA's warps (more qualify: none is)
 
 // L rounded to a multiple of q (see above); B = C + P2 of the cell.  With M = 1.5 x 2^(floor(log2 B)
 // + 23 - qsh), qsh = 23 - log2(paths), every x in [0, B] gives x + M in M's binade, whose spacing
@@ -50,28 +51,27 @@ __device__ __forceinline__ float warp_min(float v) {
     return r;
 }
 
+// One scanline of direction r = rs & 15, number s = rs >> 4.  NW = 1: one warp, its own rows by
+// slot (bufA, bufB) and metadata ring.  SPLIT (NW = the CTA's warps): the CTA's warps share the
+// rows; warp 0 alone runs the narrow steps (the predecessor row in its registers), and every
+// general step (a window or predecessor wider than 32 labels, or an invalid window) is spread over
+// the warps by 32-slot chunk (warp w takes chunks w, w + NW, ...), the predecessor minimum taken
+// over the warps' minima through xm ([2][NW] minima, [2][NW] slots for REC, then the minimum that
+// warp 0 hands over after narrow steps), with one CTA barrier per general step (two after narrow
+// steps).  Every cell gets the same value either way.
 // REC: also record, for the adjoint, each cell's winning branch (0 same label, 1 label-1, 2 label+1,
 // 3 m+P2, 4 path start; the first of P2, same, g-1, g+1 that equals the minimum, as the adjoint's
 // own recurrence decides it) in codes[r * nnz_cap + slot] and each pixel's lowest minimising slot
 // in amin[r * N + p].
-template <bool REC, int WPC>
-__global__ void __launch_bounds__(32 * WPC) fine_sgm_kernel(const float *__restrict__ cost,
-                                                                  const int *__restrict__ lo,
-                                                                  const int *__restrict__ cnt,
-                                                                  const long long *__restrict__ off,
-                                                                  int H, int W, int Gs,
-                                                                  const float *__restrict__ pen,
-                                                                  int G, ScanTable st, float *__restrict__ agg,
-                                                                  int *__restrict__ status,
-                                                                  const int *__restrict__ order, int mk,
-                                                                  unsigned char *__restrict__ codes,
-                                                                  int *__restrict__ amin, size_t nnz_cap) {
-    extern __shared__ float sm[];
-    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
-    constexpr int wpc = WPC;
-    const int gw = blockIdx.x * wpc + wib;
-    if (gw >= st.cum[st.paths]) return;
-    const int rs = __ldg(order + gw);            // longest scanlines first
+template <bool REC, bool SPLIT, int NW>
+__device__ __forceinline__ void sgm_scanline(const float *__restrict__ cost, const int *__restrict__ lo,
+                                             const int *__restrict__ cnt, const long long *__restrict__ off,
+                                             int H, int W, float P1, float P2, int G, float *__restrict__ agg,
+                                             int *__restrict__ status, int rs, int mk,
+                                             unsigned char *__restrict__ codes, int *__restrict__ amin,
+                                             size_t nnz_cap, float *bufA, float *bufB, int2 *meta, float *xm,
+                                             int wib) {
+    const int lane = threadIdx.x & 31;
     const int r = rs & 15, s = rs >> 4;
     const int dx = dir_dx(r), dy = dir_dy(r);
     int x0, y0;
@@ -79,15 +79,9 @@ __global__ void __launch_bounds__(32 * WPC) fine_sgm_kernel(const float *__restr
     const int len = scan_steps(x0, y0, dx, dy, H, W);
     unsigned char *code = REC ? codes + (size_t)r * nnz_cap : nullptr;
     int *am = REC ? amin + (size_t)r * H * W : nullptr;
-    // rows by slot with one sentinel slot on each side (slot -1 and slot n hold +inf), Gs + 2 floats
-    float *bufA = sm + (size_t)wib * 2 * (Gs + 2) + 1;   // predecessor's path costs, general steps
-    float *bufB = bufA + (Gs + 2);                       // this pixel's
-    // the metadata of this block of 32 steps and the next one, by step mod 64 (read by the narrow
-    // steps with one broadcast load)
-    int2 *meta = reinterpret_cast<int2 *>(sm + (size_t)wpc * 2 * (Gs + 2)) + wib * 64;
-    const float P1 = __ldg(pen), P2 = __ldg(pen + 1);
     const float INF = __int_as_float(0x7f800000);
-    if (lane == 0) {
+    const bool lead = !SPLIT || wib == 0;        // the warp that runs the narrow steps
+    if (SPLIT ? threadIdx.x == 0 : lane == 0) {
         bufA[-1] = INF;
         bufB[-1] = INF;
     }
@@ -115,10 +109,12 @@ __global__ void __launch_bounds__(32 * WPC) fine_sgm_kernel(const float *__restr
     if (len > 32) fetch(32, nw, no);
     meta[lane] = make_int2(cw, co);
     meta[32 + lane] = make_int2(nw, no);
-    __syncwarp();
+    if (SPLIT) __syncthreads();                // the sentinels
+    else __syncwarp();
     int plo = 0, pn = 0;                       // predecessor window; pn = 0: the path (re)starts
     float prev = INF, m = 0.f;                 // predecessor row (one slot per lane) and its minimum
     bool in_smem = false;                      // the predecessor row is in bufA (after a general step)
+    int gpar = 0;                              // SPLIT: which half of xm this general step uses
     int k = 0;
     while (k < len) {
         const int kb = k & ~31;
@@ -129,6 +125,15 @@ __global__ void __launch_bounds__(32 * WPC) fine_sgm_kernel(const float *__restr
         const unsigned ahead = bad & (0xffffffffu << (k - kb));
         int kend = ahead ? kb + __ffs(ahead) - 1 : kbend;
         if (pn > 32) kend = k;                 // a wide predecessor: the general form takes this step
+        if (k < kend && !lead) {
+            // SPLIT: the other warps skip to the next general step, knowing only the last narrow
+            // step's window
+            const int wl = __shfl_sync(0xffffffffu, cw, kend - 1 - kb);
+            plo = wl & 0xffff;
+            pn = wl >> 16;
+            k = kend;
+            in_smem = false;
+        }
         if (k < kend) {
             // narrow steps: the predecessor row in registers, cost rows two steps ahead
             int ofs = __shfl_sync(0xffffffffu, co, k - kb);
@@ -192,21 +197,33 @@ __global__ void __launch_bounds__(32 * WPC) fine_sgm_kernel(const float *__restr
                 pn = 0;
             } else {
                 if (pn != 0 && !in_smem) {
-                    if (lane < pn) bufA[lane] = prev;
-                    if (lane == 0) bufA[pn] = INF;
-                    __syncwarp();
+                    // the narrow steps' last row (and, SPLIT, its minimum) to shared memory
+                    if (lead) {
+                        if (lane < pn) bufA[lane] = prev;
+                        if (lane == 0) {
+                            bufA[pn] = INF;
+                            if (SPLIT) xm[4 * NW] = m;
+                        }
+                    }
+                    if (SPLIT) {
+                        __syncthreads();
+                        m = xm[4 * NW];
+                    } else {
+                        __syncwarp();
+                    }
                 }
                 const long long o = 4ll * ofs;
                 float lmin = INF;
                 int lslot = 0x7fffffff;
-                // sixteen 32-label chunks per round: their cost loads are in flight together, and
-                // every chunk reads the predecessor row before any chunk stores its own (the
-                // compiler cannot tell bufA from bufB, so a store between them would order the
+                // sixteen of this warp's 32-label chunks per round: their cost loads are in flight
+                // together, and every chunk reads the predecessor row before any chunk stores its own
+                // (the compiler cannot tell bufA from bufB, so a store between them would order the
                 // chunks one after another)
-                for (int j0 = lane; j0 < n; j0 += 512) {
+                constexpr int CS = 32 * NW;            // slot stride between a warp's chunks
+                for (int j0 = 32 * (SPLIT ? wib : 0) + lane; j0 < n; j0 += 16 * CS) {
                     float cc[16];
 #pragma unroll
-                    for (int u = 0; u < 16; u++) cc[u] = j0 + 32 * u < n ? __ldg(cost + o + j0 + 32 * u) : 0.f;
+                    for (int u = 0; u < 16; u++) cc[u] = j0 + CS * u < n ? __ldg(cost + o + j0 + CS * u) : 0.f;
                     if (pn != 0) {
                         // predecessor slot s read at row[s + 1] with s + 1 clamped (unsigned) to
                         // pn + 1: any slot outside [0, pn) lands on a sentinel (+inf), so an absent
@@ -216,11 +233,11 @@ __global__ void __launch_bounds__(32 * WPC) fine_sgm_kernel(const float *__restr
                         auto step = [&](int u, float v0, float vm, float vp) {
                             const float t = fminf(fminf(m + P2, v0), fminf(vm, vp) + P1);
                             if (REC)
-                                code[o + j0 + 32 * u] = t == m + P2 ? 3 : (t == v0 ? 0 : (t == vm + P1 ? 1 : 2));
+                                code[o + j0 + CS * u] = t == m + P2 ? 3 : (t == v0 ? 0 : (t == vm + P1 ? 1 : 2));
                             const float Ln = cc[u] + (t - m);
                             // the cell's cost cc[u] bounds its path costs (the global atomic does
                             // not order the shared-memory reads of the other chunks)
-                            atomicAdd(agg + o + j0 + 32 * u, det_addend(Ln, cc[u] + P2, mk));
+                            atomicAdd(agg + o + j0 + CS * u, det_addend(Ln, cc[u] + P2, mk));
                             cc[u] = Ln;
                         };
                         if (l == plo && n == pn) {
@@ -230,45 +247,68 @@ __global__ void __launch_bounds__(32 * WPC) fine_sgm_kernel(const float *__restr
                             const float *q = bufA + j0;
 #pragma unroll
                             for (int u = 0; u < 16; u++) {
-                                if (j0 + 32 * u >= n) break;
-                                step(u, q[32 * u], q[32 * u - 1], q[32 * u + 1]);
+                                if (j0 + CS * u >= n) break;
+                                step(u, q[CS * u], q[CS * u - 1], q[CS * u + 1]);
                             }
                         } else {
 #pragma unroll
                             for (int u = 0; u < 16; u++) {
-                                if (j0 + 32 * u >= n) break;
-                                const unsigned k1 = (unsigned)(l + j0 + 32 * u - plo + 1);
+                                if (j0 + CS * u >= n) break;
+                                const unsigned k1 = (unsigned)(l + j0 + CS * u - plo + 1);
                                 step(u, row[min(k1, top)], row[min(k1 - 1u, top)], row[min(k1 + 1u, top)]);
                             }
                         }
                     } else {
 #pragma unroll
                         for (int u = 0; u < 16; u++) {
-                            if (j0 + 32 * u >= n) break;
-                            atomicAdd(agg + o + j0 + 32 * u, det_addend(cc[u], cc[u] + P2, mk));
-                            if (REC) code[o + j0 + 32 * u] = 4;
+                            if (j0 + CS * u >= n) break;
+                            atomicAdd(agg + o + j0 + CS * u, det_addend(cc[u], cc[u] + P2, mk));
+                            if (REC) code[o + j0 + CS * u] = 4;
                         }
                     }
 #pragma unroll
                     for (int u = 0; u < 16; u++) {
-                        const int j = j0 + 32 * u;
+                        const int j = j0 + CS * u;
                         if (j >= n) break;
                         bufB[j] = cc[u];
-                        if (REC && cc[u] < lmin) lslot = j;      // slots ascend: the first minimum
+                        if (REC && cc[u] < lmin) lslot = j;      // a lane's slots ascend: its first minimum
                         lmin = fminf(lmin, cc[u]);
                     }
                 }
-                m = warp_min(lmin);
-                if (REC) {
-                    const int slot = (int)__reduce_min_sync(0xffffffffu, lmin == m ? (unsigned)lslot : 0x7fffffffu);
-                    if (lane == 0) am[p0 + (long long)k * dpix] = slot;
+                if (SPLIT) {
+                    // the warps' minima (and lowest minimising slots) through xm, then the minimum
+                    const float wm = warp_min(lmin);
+                    int ws = 0;
+                    if (REC) ws = (int)__reduce_min_sync(0xffffffffu, lmin == wm ? (unsigned)lslot : 0x7fffffffu);
+                    if (lane == 0) {
+                        xm[gpar * NW + wib] = wm;
+                        if (REC) reinterpret_cast<int *>(xm)[2 * NW + gpar * NW + wib] = ws;
+                        if (wib == 0) bufB[n] = INF;
+                    }
+                    __syncthreads();
+                    const float mv = lane < NW ? xm[gpar * NW + lane] : INF;
+                    m = warp_min(mv);
+                    if (REC) {
+                        const unsigned sv = lane < NW && mv == m
+                                                ? (unsigned)reinterpret_cast<const int *>(xm)[2 * NW + gpar * NW + lane]
+                                                : 0x7fffffffu;
+                        const int slot = (int)__reduce_min_sync(0xffffffffu, sv);
+                        if (wib == 0 && lane == 0) am[p0 + (long long)k * dpix] = slot;
+                    }
+                    gpar ^= 1;
+                } else {
+                    m = warp_min(lmin);
+                    if (REC) {
+                        const int slot = (int)__reduce_min_sync(0xffffffffu, lmin == m ? (unsigned)lslot : 0x7fffffffu);
+                        if (lane == 0) am[p0 + (long long)k * dpix] = slot;
+                    }
+                    if (lane == 0) bufB[n] = INF;
+                    __syncwarp();
                 }
-                if (lane == 0) bufB[n] = INF;
-                __syncwarp();
                 float *tmp = bufA;
                 bufA = bufB;
                 bufB = tmp;
-                prev = lane < n ? bufA[lane] : INF;   // for a following narrow step
+                if (lead) prev = lane < n ? bufA[lane] : INF;   // for a following narrow step
                 in_smem = true;
                 plo = l;
                 pn = n;
@@ -287,6 +327,102 @@ __global__ void __launch_bounds__(32 * WPC) fine_sgm_kernel(const float *__restr
             }
             meta[(k + 32 + lane) & 63] = make_int2(nw, no);   // the slots of the block just finished
             __syncwarp();
+        }
+    }
+}
+
+// One warp per scanline, WPC warps per CTA; with split (not null), the first scap CTAs take one
+// listed scanline each with all their warps (sgm_scanline SPLIT), and the other warps skip the
+// listed ones.  split: [0] scanlines listed, [1 .. scap] the list (rs), then a mark per scanline
+// (sgm_split_kernel); more than scap listed: none is split.
+// Resident CTAs per SM that the register budget must allow: what the one-warp path reaches on its
+// own (72 registers without the record, 96 with it; 8 warps: 80 and 128), so that the split path
+// (more registers) does not lower the occupancy of every CTA.
+__host__ __device__ constexpr int sgm_min_ctas(bool rec, int wpc) {
+    return rec ? (wpc == 2 ? 10 : wpc == 4 ? 5 : 2) : (wpc == 2 ? 14 : wpc == 4 ? 7 : 3);
+}
+
+template <bool REC, int WPC>
+__global__ void __launch_bounds__(32 * WPC, sgm_min_ctas(REC, WPC)) fine_sgm_kernel(const float *__restrict__ cost,
+                                                                  const int *__restrict__ lo,
+                                                                  const int *__restrict__ cnt,
+                                                                  const long long *__restrict__ off,
+                                                                  int H, int W, int Gs,
+                                                                  const float *__restrict__ pen,
+                                                                  int G, ScanTable st, float *__restrict__ agg,
+                                                                  int *__restrict__ status,
+                                                                  const int *__restrict__ order, int mk,
+                                                                  unsigned char *__restrict__ codes,
+                                                                  int *__restrict__ amin, size_t nnz_cap,
+                                                                  const int *__restrict__ split, int scap) {
+    extern __shared__ float sm[];
+    const int wib = threadIdx.x >> 5;
+    // rows by slot with one sentinel slot on each side (slot -1 and slot n hold +inf), Gs + 2 floats,
+    // two per warp; then per warp a ring of the metadata of this block of 32 steps and the next one,
+    // by step mod 64 (read by the narrow steps with one broadcast load); then xm (SPLIT)
+    int2 *meta = reinterpret_cast<int2 *>(sm + (size_t)WPC * 2 * (Gs + 2)) + wib * 64;
+    float *xm = sm + (size_t)WPC * 2 * (Gs + 2) + WPC * 128;
+    const float P1 = __ldg(pen), P2 = __ldg(pen + 1);
+    const int total = st.cum[st.paths];
+    const int nsplit = split ? __ldg(split) : 0;
+    const bool on = split && nsplit <= scap;
+    if ((int)blockIdx.x < scap) {
+        if (!on || (int)blockIdx.x >= nsplit) return;
+        float *bufA = sm + 1;
+        sgm_scanline<REC, true, WPC>(cost, lo, cnt, off, H, W, P1, P2, G, agg, status, __ldg(split + 1 + blockIdx.x),
+                                     mk, codes, amin, nnz_cap, bufA, bufA + (Gs + 2), meta, xm, wib);
+        return;
+    }
+    const int gw = ((int)blockIdx.x - scap) * WPC + wib;
+    if (gw >= total) return;
+    const int rs = __ldg(order + gw);            // longest scanlines first
+    if (on && __ldg(split + 1 + scap + st.cum[rs & 15] + (rs >> 4))) return;
+    float *bufA = sm + (size_t)wib * 2 * (Gs + 2) + 1;
+    sgm_scanline<REC, false, 1>(cost, lo, cnt, off, H, W, P1, P2, G, agg, status, rs, mk, codes, amin, nnz_cap,
+                                bufA, bufA + (Gs + 2), meta, xm, wib);
+}
+
+// The scanlines to split: one warp per scanline counts the windows wider than 32 labels on it
+// (128 steps per round, their loads issued together) and marks it (mark[id] = 1 when listed, 0
+// otherwise, for every scanline); one that reaches min_wide is listed (split[0] zeroed before,
+// up to scap of them: the list's order does not matter, every scanline's values are its own).
+__global__ void sgm_split_kernel(const int *__restrict__ cnt, int H, int W, ScanTable st, int min_wide, int scap,
+                                 int *__restrict__ split) {
+    const int lane = threadIdx.x & 31;
+    const int total = st.cum[st.paths];
+    int *mark = split + 1 + scap;
+    const int nwarps = (gridDim.x * blockDim.x) >> 5;
+    for (int id = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; id < total; id += nwarps) {
+        int r = 0;
+        while (r + 1 < st.paths && id >= st.cum[r + 1]) r++;
+        const int s = id - st.cum[r];
+        const int dx = dir_dx(r), dy = dir_dy(r);
+        int x0, y0;
+        scan_start(r, s, H, W, x0, y0);
+        const int len = scan_steps(x0, y0, dx, dy, H, W);
+        const long long p0 = (long long)y0 * W + x0, dp = (long long)dy * W + dx;
+        int c = 0;
+        for (int k0 = 0; k0 < len; k0 += 128) {
+            int v[4];
+#pragma unroll
+            for (int u = 0; u < 4; u++) {
+                const int k = k0 + 32 * u + lane;
+                v[u] = k < len ? __ldg(cnt + p0 + k * dp) : 0;
+            }
+#pragma unroll
+            for (int u = 0; u < 4; u++) c += v[u] > 32;
+        }
+        c = (int)__reduce_add_sync(0xffffffffu, (unsigned)c);
+        if (lane == 0) {
+            int listed = 0;
+            if (c >= min_wide) {
+                const int pos = atomicAdd(split, 1);
+                if (pos < scap) {
+                    split[1 + pos] = (s << 4) | r;
+                    listed = 1;
+                }
+            }
+            mark[id] = listed;
         }
     }
 }
@@ -442,15 +578,30 @@ void build_scan_order(int H, int W, int paths, std::vector<int> &order) {
     });
 }
 
+int sgm_split_ints(int H, int W, int paths) {
+    return 1 + kSplitCap + make_scan_table(H, W, paths).cum[paths];
+}
+
+cudaError_t launch_sgm_split(cudaStream_t s, const int *cnt, int H, int W, int paths, int min_wide, int *split) {
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const ScanTable st = make_scan_table(H, W, paths);
+    const int want = (st.cum[paths] + 7) / 8;                 // a warp per scanline
+    sgm_split_kernel<<<min(want, sms * 8), 256, 0, s>>>(cnt, H, W, st, min_wide, kSplitCap, split);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_fine_sgm(cudaStream_t s, const float *cost, const int *lo, const int *cnt,
                             const long long *off, int H, int W, int G, const float *pen, float *agg,
                             int *status, const int *order, int paths, unsigned char *codes, int *amin,
-                            size_t nnz_cap, int warps_per_cta) {
+                            size_t nnz_cap, int warps_per_cta, const int *split) {
     const int wpc = warps_per_cta == 2 || warps_per_cta == 8 ? warps_per_cta : kSgmWarps;
     const ScanTable st = make_scan_table(H, W, paths);
     const int Gs = (G + 31) & ~31;
-    const size_t smem = (size_t)wpc * (2 * (Gs + 2) * sizeof(float) + 64 * sizeof(int2));
-    const unsigned grid = (unsigned)((st.cum[paths] + wpc - 1) / wpc);
+    const size_t smem = (size_t)wpc * (2 * (Gs + 2) * sizeof(float) + 64 * sizeof(int2)) + (size_t)(4 * wpc + 4) * 4;
+    const int scap = split ? kSplitCap : 0;
+    const unsigned grid = (unsigned)(scap + (st.cum[paths] + wpc - 1) / wpc);
     // one instantiation per CTA size, each with its own register budget (launch bounds)
     auto kern = codes ? (wpc == 2 ? fine_sgm_kernel<true, 2> : wpc == 8 ? fine_sgm_kernel<true, 8> : fine_sgm_kernel<true, 4>)
                       : (wpc == 2 ? fine_sgm_kernel<false, 2> : wpc == 8 ? fine_sgm_kernel<false, 8> : fine_sgm_kernel<false, 4>);
@@ -462,7 +613,7 @@ cudaError_t launch_fine_sgm(cudaStream_t s, const float *cost, const int *lo, co
     while ((1 << lp) < paths) lp++;
     const int mk = (lp << 23) | (1 << 22);       // (23 - qsh) << 23 with qsh = 23 - log2(paths)
     kern<<<grid, 32 * wpc, smem, s>>>(cost, lo, cnt, off, H, W, Gs, pen, G, st, agg, status, order, mk, codes,
-                                            amin, nnz_cap);
+                                      amin, nnz_cap, split, scap);
     return cudaGetLastError();
 }
 

@@ -60,6 +60,9 @@ struct lfsgm_ctx {
     ArmList arms{};
     // tuning knobs (lfsgm_set_tuning): label span of the row kernel's ranges, list-kernel CTAs per SM
     int row_kw = 36, list_ctas = 0, sgm_warps = 4;
+    // scanlines that cross at least this many windows wider than 32 labels run split across a CTA's
+    // warps (lfsgm_set_sgm_split; 0: none)
+    int sgm_split = 0;
     std::vector<FineTap> h_fine;          // host copy of the shift table (row descriptors are rebuilt from it)
     // device tables
     FineTap *d_fine = nullptr;
@@ -94,6 +97,7 @@ struct lfsgm_ctx {
     double *partial = nullptr;
     unsigned *ticket = nullptr;           // last-block counter of the penalty mean (zero between launches)
     long long *tsum = nullptr;
+    int *split = nullptr;                 // SGM scanlines split across a CTA (sgm_split_ints)
     int *status = nullptr;
     // buffers of the whole-method entry points (owned, allocated on first use)
     int *o_lo = nullptr, *o_cnt = nullptr, *o_label = nullptr;
@@ -285,6 +289,7 @@ lfsgm_status bind_workspace(lfsgm_ctx *h, void *dptr, size_t bytes, bool owned) 
     h->fpen = (float *)take(2 * 4);
     h->partial = (double *)take(2 * kPartialBlocks * 8);
     h->tsum = (long long *)take((size_t)scan_tiles(h->N) * 8);
+    h->split = (int *)take((size_t)sgm_split_ints(h->cfg.H, h->cfg.W, h->cfg.paths) * 4);
     cudaError_t e = cudaMemsetAsync(h->status, 0, 4, h->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(h->ticket, 0, 4, h->stream);
     if (e != cudaSuccess) return cuda_fail(h, e, "status clear");
@@ -488,6 +493,7 @@ lfsgm_status lfsgm_workspace_size(lfsgm_handle h, size_t *bytes) {
     b += align256(4 * 8) + align256(8 * 4) + align256(2 * 4);
     b += align256(2 * kPartialBlocks * 8) + 2 * align256(4);   // partials; status word and ticket
     b += align256((size_t)scan_tiles(h->N) * 8);    // offset-scan tile sums
+    b += align256((size_t)sgm_split_ints(h->cfg.H, h->cfg.W, h->cfg.paths) * 4);   // SGM scanlines to split
     *bytes = b;
     return LFSGM_OK;
 }
@@ -538,6 +544,19 @@ lfsgm_status lfsgm_set_sgm_warps(lfsgm_handle h, int32_t warps_per_cta) {
     if (warps_per_cta != 0 && warps_per_cta != 2 && warps_per_cta != 4 && warps_per_cta != 8)
         return fail(h, LFSGM_ERR_INVALID_ARG, "tuning: warps_per_cta must be 0, 2, 4 or 8");
     h->sgm_warps = warps_per_cta == 0 ? 4 : warps_per_cta;
+    return LFSGM_OK;
+}
+
+lfsgm_status lfsgm_set_sgm_split(lfsgm_handle h, int32_t min_wide) {
+    if (!h) return LFSGM_ERR_INVALID_ARG;
+    if (min_wide < 0) return fail(h, LFSGM_ERR_INVALID_ARG, "tuning: min_wide must be >= 0");
+    h->sgm_split = min_wide;
+    return LFSGM_OK;
+}
+
+lfsgm_status lfsgm_get_sgm_split(lfsgm_handle h, int32_t *min_wide) {
+    if (!h || !min_wide) return LFSGM_ERR_INVALID_ARG;
+    *min_wide = h->sgm_split;
     return LFSGM_OK;
 }
 
@@ -674,10 +693,25 @@ lfsgm_status lfsgm_cost_volume(lfsgm_handle h, const float *views, const int32_t
 }  // extern "C"
 
 namespace {
-__global__ void zero_csr_kernel(float *a, const long long *off, int N) {
+// The aggregate's rows (and the first nz ints of the SGM's split table) to zero.
+__global__ void zero_csr_kernel(float *a, const long long *off, int N, int *z, int nz) {
     const long long n = off[N];
     for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
         a[i] = 0.f;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nz; i += gridDim.x * blockDim.x) z[i] = 0;
+}
+
+// Zero the aggregate, then (with the split knob on) list the SGM scanlines to split.
+lfsgm_status sgm_prologue(lfsgm_ctx *h, float *agg, const int32_t *cnt, const long long *o) {
+    cudaStream_t s = h->stream;
+    const lfsgm_config &c = h->cfg;
+    const int nz = h->sgm_split > 0 ? 1 : 0;      // the split table's list count
+    LFSGM_TRY(run(h, "zero_agg", [&] {
+        zero_csr_kernel<<<1216, 256, 0, s>>>(agg, o, h->N, h->split, nz);
+        return cudaGetLastError();
+    }));
+    if (nz == 0) return LFSGM_OK;
+    return run(h, "sgm_split", [&] { return launch_sgm_split(s, cnt, c.H, c.W, c.paths, h->sgm_split, h->split); });
 }
 __global__ void set_pen_kernel(float *pen, float P1, float P2) {
     pen[0] = P1;
@@ -710,13 +744,10 @@ lfsgm_status lfsgm_sgm_aggregate(lfsgm_handle h, const float *cost, const int32_
             return cudaGetLastError();
         }));
     }
-    LFSGM_TRY(run(h, "zero_agg", [&] {
-        zero_csr_kernel<<<1216, 256, 0, s>>>(agg, o, h->N);
-        return cudaGetLastError();
-    }));
+    LFSGM_TRY(sgm_prologue(h, agg, cnt, o));
     LFSGM_TRY(run(h, "fine_sgm", [&] {
         return launch_fine_sgm(s, cost, lo, cnt, o, c.H, c.W, c.fine_labels, h->fpen, agg, h->status, h->d_order,
-                               c.paths, nullptr, nullptr, 0, h->sgm_warps);
+                               c.paths, nullptr, nullptr, 0, h->sgm_warps, h->sgm_split > 0 ? h->split : nullptr);
     }));
     return LFSGM_OK;
 }
@@ -769,13 +800,11 @@ static lfsgm_status aggregate_recording(lfsgm_handle h, const float *cost, const
         set_pen_kernel<<<1, 1, 0, s>>>(h->fpen, P1, P2);
         return cudaGetLastError();
     }));
-    LFSGM_TRY(run(h, "zero_agg", [&] {
-        zero_csr_kernel<<<1216, 256, 0, s>>>(agg, o, h->N);
-        return cudaGetLastError();
-    }));
+    LFSGM_TRY(sgm_prologue(h, agg, cnt, o));
     return run(h, "fine_sgm_record", [&] {
         return launch_fine_sgm(s, cost, lo, cnt, o, c.H, c.W, c.fine_labels, h->fpen, agg, h->status, h->d_order,
-                               c.paths, h->b_codes, h->b_amin, (size_t)cap, h->sgm_warps);
+                               c.paths, h->b_codes, h->b_amin, (size_t)cap, h->sgm_warps,
+                               h->sgm_split > 0 ? h->split : nullptr);
     });
 }
 
@@ -959,7 +988,8 @@ lfsgm_status depth_buffers(lfsgm_handle h) {
 // The speed knobs of one handle: with the windows of one initial pass of `views` in (lo, cnt, off),
 // time the cost stage (best of two after a warm-up) for the row kernel's label span 36 and 44 and
 // then, with the better span, for the list kernel's CTAs per SM 8, 12, 24 against the default;
-// keep the fastest.  kw, lc: the choice.
+// keep the fastest; then the SGM's warps per CTA and split threshold the same way.  kw, lc: the
+// cost knobs chosen.
 lfsgm_status tune_handle(lfsgm_handle h, const float *views, int32_t *lo, int32_t *cnt, int64_t *off, float *cost,
                          float *agg, int &kw_out, int &lc_out) {
     LFSGM_TRY(lfsgm_initial_disparity(h, views, 0, 0, lo, cnt, off, nullptr, nullptr, nullptr));
@@ -1007,29 +1037,34 @@ lfsgm_status tune_handle(lfsgm_handle h, const float *views, int32_t *lo, int32_
     if (st == LFSGM_OK) st = lfsgm_set_tuning(h, best_kw, best_lc);
     // the SGM's warps (scanlines) per CTA, on the cost volume of the chosen knobs (derived penalties)
     if (st == LFSGM_OK) st = cost_volume_impl(h, views, lo, cnt, off, cost, !h->cfg.boundless);
-    int best_w = 4;
+    // and whether scanlines that cross many wide windows run split across a CTA (off or threshold 24)
+    int best_w = 4, best_sp = 0;
     float best_sgm = 1e30f;
-    for (int w : {4, 8, 2}) {
-        if (st != LFSGM_OK) break;
-        st = lfsgm_set_sgm_warps(h, w);
-        float best = 1e30f;
-        for (int r = 0; r < 3 && st == LFSGM_OK; r++) {
-            cudaEventRecord(e0, h->stream);
-            st = lfsgm_sgm_aggregate(h, cost, lo, cnt, off, -1.f, -1.f, agg);
-            cudaEventRecord(e1, h->stream);
-            cudaEventSynchronize(e1);
-            float t = 0.f;
-            cudaEventElapsedTime(&t, e0, e1);
-            if (r > 0) best = std::min(best, t);
+    for (int w : {4, 8, 2})
+        for (int sp : {0, 24}) {
+            if (st != LFSGM_OK) break;
+            st = lfsgm_set_sgm_warps(h, w);
+            if (st == LFSGM_OK) st = lfsgm_set_sgm_split(h, sp);
+            float best = 1e30f;
+            for (int r = 0; r < 3 && st == LFSGM_OK; r++) {
+                cudaEventRecord(e0, h->stream);
+                st = lfsgm_sgm_aggregate(h, cost, lo, cnt, off, -1.f, -1.f, agg);
+                cudaEventRecord(e1, h->stream);
+                cudaEventSynchronize(e1);
+                float t = 0.f;
+                cudaEventElapsedTime(&t, e0, e1);
+                if (r > 0) best = std::min(best, t);
+            }
+            if (st == LFSGM_OK && best < best_sgm) {
+                best_sgm = best;
+                best_w = w;
+                best_sp = sp;
+            }
         }
-        if (st == LFSGM_OK && best < best_sgm) {
-            best_sgm = best;
-            best_w = w;
-        }
-    }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     if (st == LFSGM_OK) st = lfsgm_set_sgm_warps(h, best_w);
+    if (st == LFSGM_OK) st = lfsgm_set_sgm_split(h, best_sp);
     kw_out = best_kw;
     lc_out = best_lc;
     return st;
@@ -1378,6 +1413,7 @@ lfsgm_status batch_tune_knobs(lfsgm_batch_ctx *b) {
             if (!done[j] && memcmp(&b->h[j]->cfg, &h->cfg, sizeof(lfsgm_config)) == 0) {
                 st = lfsgm_set_tuning(b->h[j], kw, lc);
                 if (st == LFSGM_OK) st = lfsgm_set_sgm_warps(b->h[j], h->sgm_warps);
+                if (st == LFSGM_OK) st = lfsgm_set_sgm_split(b->h[j], h->sgm_split);
                 done[j] = 1;
             }
         if (st != LFSGM_OK) return bfail(b, st, "tuning light field %d: %s", i, h->err.c_str());

@@ -112,6 +112,21 @@ __host__ __device__ inline void scan_start(int r, int s, int H, int W, int &x, i
     }
     (void)ax;
 }
+// The scanline of direction r through pixel (x, y): walk back to its start pixel (the last one
+// before p - r leaves the image), then invert scan_start.
+__host__ __device__ inline int scan_index(int r, int x, int y, int H, int W) {
+    const int dx = dir_dx(r), dy = dir_dy(r);
+    const int tx = dx > 0 ? x / dx : (dx < 0 ? (W - 1 - x) / (-dx) : 0x7fffffff);
+    const int ty = dy > 0 ? y / dy : (dy < 0 ? (H - 1 - y) / (-dy) : 0x7fffffff);
+    const int t = tx < ty ? tx : ty;
+    const int xs = x - t * dx, ys = y - t * dy;
+    const int ay = abs(dy), by = ay < H ? ay : H;
+    if (dy > 0 && ys < by) return ys * W + xs;
+    if (dy < 0 && H - 1 - ys < by) return (H - 1 - ys) * W + xs;
+    const int j = dx > 0 ? xs : W - 1 - xs;
+    const int k = dy > 0 ? ys - by : (dy < 0 ? H - 1 - by - ys : ys);
+    return by * W + j * (H - by) + k;
+}
 
 // Cumulative scanline counts of the first `paths` directions (cum[paths] = total).
 struct ScanTable {
@@ -231,11 +246,18 @@ cudaError_t launch_fine_cost_list(cudaStream_t s, const float *views_pad, const 
 cudaError_t launch_cost_partial_sums(cudaStream_t s, const float *cost, const int *cnt,
                                      const long long *off, int N, int G, double *partial, int nblocks,
                                      double p1f, double p2f, float *pen, unsigned *ticket, int *status);
+// split (may be null): the scanlines that launch_sgm_split listed run split across a CTA's warps
+// (the same values, faster when a few scanlines cross many wide windows).
 cudaError_t launch_fine_sgm(cudaStream_t s, const float *cost, const int *lo, const int *cnt,
                             const long long *off, int H, int W, int G, const float *pen, float *agg,
                             int *status, const int *order, int paths,
                             unsigned char *codes = nullptr, int *amin = nullptr, size_t nnz_cap = 0,
-                            int warps_per_cta = 4);
+                            int warps_per_cta = 4, const int *split = nullptr);
+// Ints of the split table of launch_fine_sgm for an H x W image and `paths` directions; its first
+// int must be zero before launch_sgm_split, which lists the scanlines that cross at least min_wide
+// windows wider than 32 labels.
+int sgm_split_ints(int H, int W, int paths);
+cudaError_t launch_sgm_split(cudaStream_t s, const int *cnt, int H, int W, int paths, int min_wide, int *split);
 
 cudaError_t launch_median3(cudaStream_t s, const float *in, float *out, int H, int W);
 cudaError_t launch_wta(cudaStream_t s, const float *agg, const int *lo, const int *cnt,

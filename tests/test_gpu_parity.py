@@ -278,6 +278,80 @@ def test_sgm_ragged_and_wide_windows(gpu_lib, shape, paths):
     assert err < RTOL, err
 
 
+_DIRS = [(1, 0), (-1, 0), (0, 1), (0, -1), (1, 1), (-1, -1), (1, -1), (-1, 1),
+         (2, 1), (-2, -1), (2, -1), (-2, 1), (1, 2), (-1, -2), (1, -2), (-1, 2)]
+
+
+def _wide_per_scanline(wide, paths):
+    """Windows wider than 32 labels on each scanline (keyed by direction and start pixel: walk back
+    from a pixel until its predecessor leaves the image)."""
+    H, W = wide.shape
+    counts = {}
+    for y, x in zip(*np.nonzero(wide)):
+        for r, (dx, dy) in enumerate(_DIRS[:paths]):
+            tx = x // dx if dx > 0 else ((W - 1 - x) // -dx if dx < 0 else 1 << 30)
+            ty = y // dy if dy > 0 else ((H - 1 - y) // -dy if dy < 0 else 1 << 30)
+            t = min(tx, ty)
+            key = (r, x - t * dx, y - t * dy)
+            counts[key] = counts.get(key, 0) + 1
+    return np.array(list(counts.values()))
+
+
+@pytest.mark.parametrize("paths", [8, 16])
+def test_sgm_split_scanlines_give_the_same_bits(gpu_lib, paths):
+    """lfsgm_set_sgm_split: a scanline that crosses many windows wider than 32 labels runs on all the
+    warps of a CTA, which share each wide step's chunks.  Whole wide rows (one of whole-range
+    windows, one the image's last) and columns, a narrow run inside a wide row, and scattered wide
+    windows: the aggregate is the same bit for bit with the split off (the default), at the
+    autotuner's threshold, at one that splits more scanlines, and at ones that qualify too many
+    (none split), also in the recording form; and it matches the oracle."""
+    import torch
+    H, W, G = 40, 56, 150
+    p = lfsynth.LFParams(U=3, V=3, H=H, W=W, census_w=5, dmin=-2.0, dmax=2.0, coarse_labels=32,
+                         fine_labels=G, fine_radius=5, paths=paths)
+    rng = np.random.default_rng(4056 + paths)
+    lo = rng.integers(0, G, H * W).astype(np.int32)
+    cnt = np.minimum(rng.integers(1, 33, H * W), G - lo).astype(np.int32)
+    wide = (rng.random(H * W) < 0.04).reshape(H, W)
+    wide[[3, 17, H - 1], :] = True
+    wide[:, [0, 41]] = True
+    wide[3, 10:30] = False
+    wide = wide.ravel()
+    lo[wide] = rng.integers(0, 20, wide.sum())
+    cnt[wide] = np.minimum(rng.integers(33, G + 1, wide.sum()), G - lo[wide])
+    lo.reshape(H, W)[17, :] = 0                      # a run of identical whole-range windows
+    cnt.reshape(H, W)[17, :] = G
+    per = _wide_per_scanline((cnt > 32).reshape(H, W), paths)
+    assert 1 <= np.sum(per >= 24) <= 256 and np.sum(per >= 1) > 256    # split at 24, too many at 1
+    off_o = oracle.offsets(cnt)
+    cost = rng.uniform(0, 30, int(off_o[-1])).astype(np.float32)
+    P1, P2 = np.float32(1.7), np.float32(9.5)
+    o_Cs = oracle.sgm_bounded(H, W, lo, cnt, off_o, cost.astype(np.float64), float(P1), float(P2), paths)
+    off = pad4_offsets(cnt)
+    full = np.zeros(int(off[-1]), np.float32)
+    full[np.repeat(off[:-1], cnt) + (np.arange(int(np.sum(cnt))) - np.repeat(np.cumsum(cnt) - cnt, cnt))] = cost
+    cd, lod, cntd, offd = _dev(full), _dev(lo, torch.int32), _dev(cnt, torch.int32), _dev(off)
+    h = gpu_lib.lfsgm_create(p)
+    runs = []
+    for min_wide, warps, rec in ((0, 4, False), (24, 4, False), (24, 8, False), (24, 2, False), (6, 4, False),
+                                 (3, 8, False), (1, 4, False), (0, 4, True), (24, 8, True), (6, 2, True)):
+        gpu_lib.lfsgm_set_sgm_split(h, min_wide)
+        gpu_lib.lfsgm_set_sgm_warps(h, warps)
+        agg = torch.full_like(cd, float("nan"))
+        (gpu_lib.lfsgm_sgm_aggregate_record if rec else gpu_lib.lfsgm_sgm_aggregate)(h, cd, lod, cntd, offd, P1, P2, agg)
+        runs.append(((min_wide, warps, rec), agg))
+    with pytest.raises(gpu_lib.LfsgmError):
+        gpu_lib.lfsgm_set_sgm_split(h, -1)
+    gpu_lib.lfsgm_sync(h)
+    gpu_lib.lfsgm_destroy(h)
+    base = runs[0][1]
+    for knobs, agg in runs[1:]:
+        diff = torch.nonzero(base != agg).flatten()
+        assert diff.numel() == 0, (knobs, int(diff.numel()), diff[:8].tolist())
+    err = csr_rel_err(gather(_np(base), off, cnt), o_Cs, cnt)
+    assert err < RTOL, err
+
+
 def test_sgm_derived_penalties(gpu_lib, tiny_case):
     views, gt, p, cfg, ref = tiny_case
     c32 = ref["cost"].astype(np.float32)
@@ -460,6 +534,12 @@ def test_sgm_aggregate_is_reproducible_at_bench_shape(gpu_lib, paths):
         torch.cuda.synchronize()
         runs.append(L.agg[:nnz].clone())
     assert gpu_lib.lfsgm_get_tuning(L.h)[2] == 8
+    # and with the border scanlines that cross many whole-range windows split across a CTA's warps
+    assert gpu_lib.lfsgm_get_sgm_split(L.h) == 0
+    gpu_lib.lfsgm_set_sgm_split(L.h, 24)
+    L.aggregate(-1.0, -1.0)
+    torch.cuda.synchronize()
+    runs.append(L.agg[:nnz].clone())
     gpu_lib.lfsgm_sync(L.h)
     with pytest.raises(gpu_lib.LfsgmError):
         gpu_lib.lfsgm_set_sgm_warps(L.h, 3)
@@ -554,6 +634,7 @@ def test_autotune_picks_valid_knobs_and_keeps_the_depth(gpu_lib, tiny_case):
     assert kw in (36, 44) and lc in (0, 8, 12, 24)
     tuned = gpu_lib.lfsgm_get_tuning(h)
     assert tuned[:2] == (kw, lc) and tuned[2] in (2, 4, 8)
+    assert gpu_lib.lfsgm_get_sgm_split(h) in (0, 24)
     label1 = torch.empty_like(label0)
     disp1 = torch.empty_like(disp0)
     gpu_lib.lfsgm_depth(h, vd, disp1, label1)
