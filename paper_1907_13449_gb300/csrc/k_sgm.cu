@@ -13,7 +13,9 @@
 // The step is the normalised recurrence
 //   L(p,g) = C(p,g) + (min(L'(g), L'(g-1)+P1, L'(g+1)+P1, m+P2) - m),   m = min L',
 // and the predecessor minimum m is one redux.sync.min.f32 per pixel.  The 8 or 16 directions run
-// concurrently and add into agg (zeroed by the caller) with float atomics.
+// concurrently and add into agg (zeroed by the caller) with float atomics.  Optionally the few
+// scanlines that cross many wide windows (a speed knob) run on all the warps of a CTA each, which
+// share the wide steps' chunks (sgm_scanline SPLIT); a small kernel lists them first.
 //
 // Reproducible sum over the directions.  The aggregate C_s(p,g) = sum_r L_r(p,g) must not depend on
 // the order in which the directions' atomics arrive.  Every exact L_r(p,g) lies in [0, B] with
