@@ -220,9 +220,10 @@ def test_cost_volume_max_fine_labels(gpu_lib):
 
 
 # ------------------------------------------------------------------------------ SGM
-def _gpu_sgm(lf, p, cost32, lo, cnt, P1, P2):
+def _gpu_sgm(lf, p, cost32, lo, cnt, P1, P2, split=0):
     import torch
     h = lf.lfsgm_create(p)
+    lf.lfsgm_set_sgm_split(h, split)
     off = pad4_offsets(cnt)
     full = np.zeros(int(off[-1]), np.float32)
     full[np.repeat(off[:-1], cnt) + (np.arange(int(np.sum(cnt))) - np.repeat(np.cumsum(cnt) - cnt, cnt))] = cost32
@@ -276,6 +277,9 @@ def test_sgm_ragged_and_wide_windows(gpu_lib, shape, paths):
     off, agg = _gpu_sgm(gpu_lib, p, cost, lo, cnt, P1, P2)
     err = csr_rel_err(gather(agg, off, cnt), o_Cs, cnt)
     assert err < RTOL, err
+    # scanlines crossing two or more wide windows split across a CTA's warps: the same bits
+    _, agg2 = _gpu_sgm(gpu_lib, p, cost, lo, cnt, P1, P2, split=2)
+    assert np.array_equal(agg, agg2, equal_nan=True)
 
 
 _DIRS = [(1, 0), (-1, 0), (0, 1), (0, -1), (1, 1), (-1, -1), (1, -1), (-1, 1),
