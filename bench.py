@@ -237,6 +237,14 @@ def run_ours(args, ws, rank, local):
         dist.init_process_group("nccl", device_id=dev)
     # the library's autotuner picks the speed knobs for this shape (untimed)
     row_kw, list_ctas = lf.lfsgm_autotune(L.h, views) if args.autotune else (36, 0)
+    if args.sgm_warps is not None:
+        lf.lfsgm_set_sgm_warps(L.h, args.sgm_warps)
+    if args.sgm_split is not None:
+        lf.lfsgm_set_sgm_split(L.h, args.sgm_split)
+    knob_note = ("speed knobs picked by lfsgm_autotune on this light field before the timed region"
+                 if args.autotune else "the library's default speed knobs (no autotuning)")
+    if args.sgm_warps is not None or args.sgm_split is not None:
+        knob_note += "; SGM knobs fixed on the command line"
     sgm_warps = lf.lfsgm_get_tuning(L.h)[2]
     sgm_split = lf.lfsgm_get_sgm_split(L.h)
 
@@ -399,7 +407,7 @@ def run_ours(args, ws, rank, local):
                    "parallelism": f"replicas x{ws}"},
         "gcell_per_s": round(active / (value * 1e-3) / 1e9, 2),
         "tuning": {"row_kw": row_kw, "list_ctas_per_sm": list_ctas, "sgm_warps": sgm_warps, "sgm_split": sgm_split,
-                   "note": "speed knobs picked by lfsgm_autotune on this light field before the timed region"},
+                   "note": knob_note},
         "value_stats": {"median": round(statistics.median(stage_each), 4), "min": round(stage_each[0], 4),
                         "p99": round(stage_each[min(len(stage_each) - 1, int(0.99 * len(stage_each)))], 4),
                         "unit": "ms, cost+SGM per step on this rank"},
@@ -708,6 +716,10 @@ def main():
     ap.add_argument("--no-backward", dest="backward", action="store_false")
     ap.add_argument("--no-autotune", dest="autotune", action="store_false",
                     help="default speed knobs instead of lfsgm_autotune (fixed kernel choice for profiling)")
+    ap.add_argument("--sgm-warps", type=int, default=None, choices=[2, 4, 8],
+                    help="fix the fine SGM's warps per CTA (after the autotuner, if it runs)")
+    ap.add_argument("--sgm-split", type=int, default=None,
+                    help="fix the fine SGM's split threshold (0: off; after the autotuner, if it runs)")
     ap.add_argument("--channels", type=int, default=1, choices=[1, 3],
                     help="colour channels of the rendered light field (3: RGB, Sec. III-B/C)")
     args = ap.parse_args()

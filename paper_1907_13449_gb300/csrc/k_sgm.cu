@@ -395,12 +395,19 @@ __global__ void sgm_split_kernel(const int *__restrict__ cnt, int H, int W, Scan
     int *mark = split + 1 + scap;
     const int nwarps = (gridDim.x * blockDim.x) >> 5;
     for (int id = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; id < total; id += nwarps) {
-        int r = 0;
-        while (r + 1 < st.paths && id >= st.cum[r + 1]) r++;
-        const int s = id - st.cum[r];
-        const int dx = dir_dx(r), dy = dir_dy(r);
+        // the direction: unrolled compares with the table (a run-time index would copy it to the stack)
+        int r = 0, base = 0;
+#pragma unroll
+        for (int q = 1; q < kMaxPaths; q++)
+            if (q < st.paths && id >= st.cum[q]) {
+                r = q;
+                base = st.cum[q];
+            }
+        const int s = id - base;
+        int dx, dy;
+        dir_of(r, dx, dy);
         int x0, y0;
-        scan_start(r, s, H, W, x0, y0);
+        scan_start_d(dx, dy, s, H, W, x0, y0);
         const int len = scan_steps(x0, y0, dx, dy, H, W);
         const long long p0 = (long long)y0 * W + x0, dp = (long long)dy * W + dx;
         int c = 0;

@@ -96,9 +96,17 @@ __host__ __device__ inline int n_scanlines(int r, int H, int W) {
     const int bx = ax < W ? ax : W, by = ay < H ? ay : H;
     return by * W + bx * (H - by);
 }
-// Start pixel of scanline s of direction r.
-__host__ __device__ inline void scan_start(int r, int s, int H, int W, int &x, int &y) {
-    const int dx = dir_dx(r), dy = dir_dy(r), ax = abs(dx), ay = abs(dy);
+// The same table as bit fields of two constants, for kernels that index it with a run-time r and
+// would otherwise copy it to the stack: direction pair k = r >> 1 is (bx_k, by_k - 2) (x in 2-bit
+// fields, y in 3-bit fields), negated for odd r.
+__host__ __device__ inline void dir_of(int r, int &dx, int &dy) {
+    const int k = r >> 1, sg = (r & 1) ? -1 : 1;
+    dx = sg * (int)((0x5A51u >> (2 * k)) & 3u);
+    dy = sg * ((int)((0x10B2DAu >> (3 * k)) & 7u) - 2);
+}
+// Start pixel of scanline s of the direction (dx, dy).
+__host__ __device__ inline void scan_start_d(int dx, int dy, int s, int H, int W, int &x, int &y) {
+    const int ay = abs(dy);
     const int by = ay < H ? ay : H;
     if (s < by * W) {
         const int i = s / W;
@@ -111,7 +119,10 @@ __host__ __device__ inline void scan_start(int r, int s, int H, int W, int &x, i
         x = dx > 0 ? j : W - 1 - j;
         y = dy > 0 ? by + k : (dy < 0 ? H - 1 - by - k : k);
     }
-    (void)ax;
+}
+// Start pixel of scanline s of direction r.
+__host__ __device__ inline void scan_start(int r, int s, int H, int W, int &x, int &y) {
+    scan_start_d(dir_dx(r), dir_dy(r), s, H, W, x, y);
 }
 // The scanline of direction r through pixel (x, y): walk back to its start pixel (the last one
 // before p - r leaves the image), then invert scan_start.

@@ -1,5 +1,6 @@
 // Host check of the SGM scanline tables (lfsgm_internal.cuh), built and run by test_scanlines.py.
-// For each (H, W) on the command line and each of the 16 directions r it walks every scanline s
+// It prints the number of directions whose bit-field form (dir_of) differs from the table, then,
+// for each (H, W) on the command line and each of the 16 directions r, it walks every scanline s
 // from scan_start(r, s) for scan_steps pixels and prints one line
 //   H W r n_scanlines covered twice missing bad_index bad_ends
 // covered: pixels visited; twice: pixels visited more than once; missing: pixels never visited;
@@ -14,6 +15,14 @@
 using namespace lfsgm;
 
 int main(int argc, char **argv) {
+    // first line: directions whose bit-field form (dir_of) differs from the table
+    int bad_dirs = 0;
+    for (int r = 0; r < kMaxPaths; r++) {
+        int dx, dy;
+        dir_of(r, dx, dy);
+        bad_dirs += dx != dir_dx(r) || dy != dir_dy(r);
+    }
+    printf("%d\n", bad_dirs);
     for (int a = 1; a + 1 < argc; a += 2) {
         const int H = atoi(argv[a]), W = atoi(argv[a + 1]);
         for (int r = 0; r < kMaxPaths; r++) {

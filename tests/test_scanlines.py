@@ -2,8 +2,9 @@
 kernels and the split listing kernel use): built with the host compiler and checked against a
 brute-force count.  For every direction of Sec. IV-C (8 and 16 paths) and image shapes down to
 1 x 1: each pixel lies on exactly one scanline, a scanline starts where the predecessor p - r
-leaves the image and ends where p + r does, scan_index inverts scan_start, and the number of
-scanlines equals the number of pixels whose predecessor is outside the image."""
+leaves the image and ends where p + r does, scan_index inverts scan_start, the number of
+scanlines equals the number of pixels whose predecessor is outside the image, and the bit-field
+form of the direction table agrees with it."""
 import os
 import shutil
 import subprocess
@@ -34,12 +35,17 @@ def table(tmp_path_factory):
                     os.path.join(HERE, "scanline_check.cpp"), "-o", exe], check=True)
     args = [str(v) for hw in SHAPES for v in hw]
     out = subprocess.run([exe, *args], check=True, capture_output=True, text=True).stdout
-    rows = {}
-    for line in out.split("\n"):
+    lines = out.split("\n")
+    rows = {"bad_dirs": int(lines[0])}
+    for line in lines[1:]:
         if line.strip():
             H, W, r, ns, covered, twice, missing, bad_index, bad_ends = map(int, line.split())
             rows[(H, W, r)] = (ns, covered, twice, missing, bad_index, bad_ends)
     return rows
+
+
+def test_direction_bit_fields_match_the_table(table):
+    assert table["bad_dirs"] == 0
 
 
 @pytest.mark.parametrize("shape", SHAPES)
