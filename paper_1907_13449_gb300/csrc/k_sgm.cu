@@ -388,13 +388,13 @@ __global__ void __launch_bounds__(32 * WPC, sgm_min_ctas(REC, WPC)) fine_sgm_ker
 // (128 steps per round, their loads issued together) and marks it (mark[id] = 1 when listed, 0
 // otherwise, for every scanline); one that reaches min_wide is listed (split[0] zeroed before,
 // up to scap of them: the list's order does not matter, every scanline's values are its own).
-__global__ void sgm_split_kernel(const int *__restrict__ cnt, int H, int W, ScanTable st, int min_wide, int scap,
-                                 int *__restrict__ split) {
+// Warp w0 of nwarps (every lane of the warp calls it).
+__device__ __forceinline__ void split_list(const int *__restrict__ cnt, int H, int W, const ScanTable &st,
+                                           int min_wide, int scap, int *__restrict__ split, int w0, int nwarps) {
     const int lane = threadIdx.x & 31;
     const int total = st.cum[st.paths];
     int *mark = split + 1 + scap;
-    const int nwarps = (gridDim.x * blockDim.x) >> 5;
-    for (int id = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; id < total; id += nwarps) {
+    for (int id = w0; id < total; id += nwarps) {
         // the direction: unrolled compares with the table (a run-time index would copy it to the stack)
         int r = 0, base = 0;
 #pragma unroll
@@ -436,6 +436,12 @@ __global__ void sgm_split_kernel(const int *__restrict__ cnt, int H, int W, Scan
     }
 }
 
+__global__ void sgm_split_kernel(const int *__restrict__ cnt, int H, int W, ScanTable st, int min_wide, int scap,
+                                 int *__restrict__ split) {
+    split_list(cnt, H, W, st, min_wide, scap, split, (blockIdx.x * blockDim.x + threadIdx.x) >> 5,
+               (gridDim.x * blockDim.x) >> 5);
+}
+
 // Per-block sums of the active costs and slot counts (rows are 16-byte aligned, read as float4;
 // slots past cnt are masked, so padding is never read into the sum).  The warps take 32
 // consecutive pixels at a time, a lane its pixel: a lane sums its row's first 32 slots (8 vector
@@ -444,16 +450,24 @@ __global__ void sgm_split_kernel(const int *__restrict__ cnt, int H, int W, Scan
 // order), so that one wide row does not hold its warp for a dependent load per 32 slots.  Each
 // lane adds its pixels in a fixed order, the block adds its warps in a fixed order, and the last
 // block to finish (ticket counter) adds the block partials in block order and writes the
-// penalties: the mean is deterministic.
+// penalties: the mean is deterministic.  The first nb blocks do this; blocks past them (split not
+// null) list the SGM scanlines to split (split_list, split[0] zeroed before), beside them.
 __global__ void __launch_bounds__(256) cost_partial_kernel(const float *__restrict__ cost,
                                                            const int *__restrict__ cnt,
                                                            const long long *__restrict__ off, int N, int G,
-                                                           double *__restrict__ partial, double p1f, double p2f,
-                                                           float *__restrict__ pen, unsigned *__restrict__ ticket,
-                                                           int *__restrict__ status) {
+                                                           double *__restrict__ partial, int nb, double p1f,
+                                                           double p2f, float *__restrict__ pen,
+                                                           unsigned *__restrict__ ticket, int *__restrict__ status,
+                                                           int H, int W, ScanTable st, int min_wide, int scap,
+                                                           int *__restrict__ split) {
+    if ((int)blockIdx.x >= nb) {
+        split_list(cnt, H, W, st, min_wide, scap, split, (((int)blockIdx.x - nb) * blockDim.x + threadIdx.x) >> 5,
+                   (((int)gridDim.x - nb) * blockDim.x) >> 5);
+        return;
+    }
     double s = 0.0, c = 0.0;
     const int lane0 = threadIdx.x & 31;
-    const int wstride = gridDim.x * blockDim.x;
+    const int wstride = nb * blockDim.x;
     for (int base = blockIdx.x * blockDim.x + (threadIdx.x & ~31); base < N; base += wstride) {
         const int p = base + lane0;
         long long o = 0;
@@ -532,15 +546,14 @@ __global__ void __launch_bounds__(256) cost_partial_kernel(const float *__restri
             bc += wc[i];
         }
         partial[blockIdx.x] = b;
-        partial[gridDim.x + blockIdx.x] = bc;
+        partial[nb + blockIdx.x] = bc;
         __threadfence();                                   // partials visible before the ticket
-        last = atomicAdd(ticket, 1u) == gridDim.x - 1;
+        last = atomicAdd(ticket, 1u) == (unsigned)nb - 1;
     }
     __syncthreads();
     if (!last || wid != 0) return;
     // the last block: all partials are written; add them in block order (a lane every 32nd, eight
     // of them loaded together: one L2 round trip per 256 partials instead of one per 32)
-    const int nb = gridDim.x;
     s = 0.0;
     c = 0.0;
     for (int i0 = lane; i0 < nb; i0 += 256) {
@@ -573,8 +586,18 @@ __global__ void __launch_bounds__(256) cost_partial_kernel(const float *__restri
 
 cudaError_t launch_cost_partial_sums(cudaStream_t s, const float *cost, const int *cnt, const long long *off,
                                      int N, int G, double *partial, int nblocks, double p1f, double p2f,
-                                     float *pen, unsigned *ticket, int *status) {
-    cost_partial_kernel<<<nblocks, 256, 0, s>>>(cost, cnt, off, N, G, partial, p1f, p2f, pen, ticket, status);
+                                     float *pen, unsigned *ticket, int *status, int H, int W, int paths,
+                                     int min_wide, int *split) {
+    const ScanTable st = make_scan_table(H, W, paths);
+    int extra = 0;
+    if (split) {
+        int dev = 0, sms = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        extra = std::min((st.cum[paths] + 7) / 8, sms * 8);      // a warp per scanline
+    }
+    cost_partial_kernel<<<nblocks + extra, 256, 0, s>>>(cost, cnt, off, N, G, partial, nblocks, p1f, p2f, pen, ticket,
+                                                        status, H, W, st, min_wide, kSplitCap, split);
     return cudaGetLastError();
 }
 

@@ -701,8 +701,8 @@ __global__ void zero_csr_kernel(float *a, const long long *off, int N, int *z, i
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nz; i += gridDim.x * blockDim.x) z[i] = 0;
 }
 
-// Zero the aggregate, then (with the split knob on) list the SGM scanlines to split.
-lfsgm_status sgm_prologue(lfsgm_ctx *h, float *agg, const int32_t *cnt, const long long *o) {
+// Zero the aggregate, then (with the split knob on, and `list`) list the SGM scanlines to split.
+lfsgm_status sgm_prologue(lfsgm_ctx *h, float *agg, const int32_t *cnt, const long long *o, bool list) {
     cudaStream_t s = h->stream;
     const lfsgm_config &c = h->cfg;
     const int nz = h->sgm_split > 0 ? 1 : 0;      // the split table's list count
@@ -710,7 +710,7 @@ lfsgm_status sgm_prologue(lfsgm_ctx *h, float *agg, const int32_t *cnt, const lo
         zero_csr_kernel<<<1216, 256, 0, s>>>(agg, o, h->N, h->split, nz);
         return cudaGetLastError();
     }));
-    if (nz == 0) return LFSGM_OK;
+    if (nz == 0 || !list) return LFSGM_OK;
     return run(h, "sgm_split", [&] { return launch_sgm_split(s, cnt, c.H, c.W, c.paths, h->sgm_split, h->split); });
 }
 __global__ void set_pen_kernel(float *pen, float P1, float P2) {
@@ -734,17 +734,21 @@ lfsgm_status lfsgm_sgm_aggregate(lfsgm_handle h, const float *cost, const int32_
     cudaStream_t s = h->stream;
     const long long *o = (const long long *)off;
     if (derived) {
+        // zero agg (and the split list's count), then the penalty mean, whose launch also lists the
+        // scanlines to split
+        LFSGM_TRY(sgm_prologue(h, agg, cnt, o, false));
         LFSGM_TRY(run(h, "cost_partial_sums", [&] {
             return launch_cost_partial_sums(s, cost, cnt, o, h->N, c.fine_labels, h->partial, kPartialBlocks,
-                                            c.p1_frac, c.p2_frac, h->fpen, h->ticket, h->status);
+                                            c.p1_frac, c.p2_frac, h->fpen, h->ticket, h->status, c.H, c.W,
+                                            c.paths, h->sgm_split, h->sgm_split > 0 ? h->split : nullptr);
         }));
     } else {
         LFSGM_TRY(run(h, "set_penalties", [&] {
             set_pen_kernel<<<1, 1, 0, s>>>(h->fpen, P1, P2);
             return cudaGetLastError();
         }));
+        LFSGM_TRY(sgm_prologue(h, agg, cnt, o, true));
     }
-    LFSGM_TRY(sgm_prologue(h, agg, cnt, o));
     LFSGM_TRY(run(h, "fine_sgm", [&] {
         return launch_fine_sgm(s, cost, lo, cnt, o, c.H, c.W, c.fine_labels, h->fpen, agg, h->status, h->d_order,
                                c.paths, nullptr, nullptr, 0, h->sgm_warps, h->sgm_split > 0 ? h->split : nullptr);
@@ -800,7 +804,7 @@ static lfsgm_status aggregate_recording(lfsgm_handle h, const float *cost, const
         set_pen_kernel<<<1, 1, 0, s>>>(h->fpen, P1, P2);
         return cudaGetLastError();
     }));
-    LFSGM_TRY(sgm_prologue(h, agg, cnt, o));
+    LFSGM_TRY(sgm_prologue(h, agg, cnt, o, true));
     return run(h, "fine_sgm_record", [&] {
         return launch_fine_sgm(s, cost, lo, cnt, o, c.H, c.W, c.fine_labels, h->fpen, agg, h->status, h->d_order,
                                c.paths, h->b_codes, h->b_amin, (size_t)cap, h->sgm_warps,

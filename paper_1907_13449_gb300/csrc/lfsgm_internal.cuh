@@ -255,9 +255,12 @@ cudaError_t launch_fine_cost_list(cudaStream_t s, const float *views_pad, const 
 // Mean cost over the active slots and the derived penalties pen = (p1f, p2f) x mean, in one launch:
 // partial holds nblocks sums followed by nblocks counts; ticket (zero between launches) picks the
 // block that adds them up.
+// With split (not null, its first int zeroed before), the same launch also lists the SGM
+// scanlines to split, as launch_sgm_split does, in extra blocks.
 cudaError_t launch_cost_partial_sums(cudaStream_t s, const float *cost, const int *cnt,
                                      const long long *off, int N, int G, double *partial, int nblocks,
-                                     double p1f, double p2f, float *pen, unsigned *ticket, int *status);
+                                     double p1f, double p2f, float *pen, unsigned *ticket, int *status,
+                                     int H, int W, int paths, int min_wide, int *split);
 // split (may be null): the scanlines that launch_sgm_split listed run split across a CTA's warps
 // (the same values, faster when a few scanlines cross many wide windows).
 cudaError_t launch_fine_sgm(cudaStream_t s, const float *cost, const int *lo, const int *cnt,
