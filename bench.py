@@ -548,10 +548,10 @@ def run_batch(args, dev):
     t0 = time.perf_counter()
     B = lf.LightFieldBatch(params, views, branches=args.batch_branches, stream=stream)
     tune_s = time.perf_counter() - t0
-    kw, lc, sw = B.knobs()
+    kw, lc, sw, sp = B.knobs()
     knobs = {}
     for i, p in enumerate(params):
-        knobs.setdefault(lfsynth.BATCH_CLASSES[i % 4]["name"], set()).add((int(kw[i]), int(lc[i]), int(sw[i])))
+        knobs.setdefault(lfsynth.BATCH_CLASSES[i % 4]["name"], set()).add((int(kw[i]), int(lc[i]), int(sw[i]), int(sp[i])))
     knobs = {k: sorted(v) for k, v in knobs.items()}
     for _ in range(2):
         B.run()
@@ -599,7 +599,7 @@ def run_batch(args, dev):
     pct = lambda a, q: round(float(np.percentile(a, q)), 3)
     return {"lfs": n, "classes": [c["name"] for c in lfsynth.BATCH_CLASSES],
             "branches": int(k), "graph_kernel_nodes": int(nodes), "runs": R,
-            "knobs": {"per_class_row_kw_list_ctas_sgm_warps": knobs},
+            "knobs": {"per_class_row_kw_list_ctas_sgm_warps_split": knobs},
             "lf_per_s": round(n / (batch_ms * 1e-3), 1), "ms_per_batch": round(batch_ms, 3),
             "p50_ms": pct(done, 50), "p99_ms": pct(done, 99),
             "latency": "completion time of each light field after the batch starts (all submitted at once)",

@@ -283,12 +283,13 @@ lfsgm_status lfsgm_batch_create(int32_t n, const lfsgm_config *cfgs, const float
                                 float *const *disp, void *stream, int32_t branches, lfsgm_batch *out);
 lfsgm_status lfsgm_batch_run(lfsgm_batch b);
 lfsgm_status lfsgm_batch_times(lfsgm_batch b, double *start_ms, double *end_ms, int32_t *branches);
-/* The speed knobs (see lfsgm_set_tuning, lfsgm_set_sgm_warps) each light field of the batch runs
- * with: the autotuner (branches <= 0 at creation) tunes one member of each shape class as
- * lfsgm_autotune does and sets its knobs on every member.  row_kw, list_ctas_per_sm,
- * warps_per_cta: host int32 [n] (nullable in lfsgm_batch_knobs). */
+/* The speed knobs (see lfsgm_set_tuning, lfsgm_set_sgm_warps, lfsgm_set_sgm_split) each light
+ * field of the batch runs with: the autotuner (branches <= 0 at creation) tunes one member of each
+ * shape class as lfsgm_autotune does and sets its knobs on every member.  row_kw,
+ * list_ctas_per_sm, warps_per_cta, min_wide: host int32 [n] (nullable in lfsgm_batch_knobs). */
 lfsgm_status lfsgm_batch_knobs(lfsgm_batch b, int32_t *row_kw, int32_t *list_ctas_per_sm);
 lfsgm_status lfsgm_batch_sgm_warps(lfsgm_batch b, int32_t *warps_per_cta);
+lfsgm_status lfsgm_batch_sgm_split(lfsgm_batch b, int32_t *min_wide);
 int64_t lfsgm_batch_kernel_nodes(lfsgm_batch b);    /* kernel nodes in the batch's graph */
 const char *lfsgm_batch_last_error(lfsgm_batch b);  /* NULL: error of the last failed create */
 lfsgm_status lfsgm_batch_destroy(lfsgm_batch b);

@@ -67,7 +67,7 @@ EXPORTS = ["lfsgm_create", "lfsgm_destroy", "lfsgm_workspace_size", "lfsgm_set_w
            "lfsgm_batch_destroy", "lfsgm_median_filter", "lfsgm_batch_workspace_size", "lfsgm_batch_create_ws",
            "lfsgm_set_tuning", "lfsgm_batch_knobs", "lfsgm_autotune", "lfsgm_sgm_aggregate_record",
            "lfsgm_backward_recorded", "lfsgm_set_sgm_warps", "lfsgm_get_tuning", "lfsgm_batch_sgm_warps",
-           "lfsgm_set_sgm_split", "lfsgm_get_sgm_split"]
+           "lfsgm_set_sgm_split", "lfsgm_get_sgm_split", "lfsgm_batch_sgm_split"]
 
 
 def load(build_if_missing: bool = False):
@@ -102,6 +102,7 @@ def load(build_if_missing: bool = False):
         L.lfsgm_get_sgm_split.argtypes = [vp, C.POINTER(i32)]
         L.lfsgm_get_tuning.argtypes = [vp, P(i32), P(i32), P(i32)]
         L.lfsgm_batch_sgm_warps.argtypes = [vp, vp]
+        L.lfsgm_batch_sgm_split.argtypes = [vp, vp]
         L.lfsgm_sync.argtypes = [vp]
         L.lfsgm_last_error.argtypes = [vp]
         L.lfsgm_last_error.restype = C.c_char_p
@@ -429,6 +430,14 @@ def lfsgm_batch_sgm_warps(b, n):
     return w
 
 
+def lfsgm_batch_sgm_split(b, n):
+    """The fine SGM's split threshold of each light field of a batch (numpy int32 array; 0: off)."""
+    import numpy as np
+    w = np.zeros(n, np.int32)
+    _bcheck(load().lfsgm_batch_sgm_split(b, w.ctypes.data_as(C.c_void_p)), b)
+    return w
+
+
 def lfsgm_batch_knobs(b, n):
     """(row_kw, list_ctas_per_sm) per light field of a batch, as numpy int32 arrays."""
     import numpy as np
@@ -488,9 +497,9 @@ class LightFieldBatch:
         return lfsgm_batch_times(self.b, self.n)
 
     def knobs(self):
-        """(row_kw, list_ctas_per_sm, sgm_warps) per light field, numpy int32 arrays."""
+        """(row_kw, list_ctas_per_sm, sgm_warps, sgm_split) per light field, numpy int32 arrays."""
         kw, lc = lfsgm_batch_knobs(self.b, self.n)
-        return kw, lc, lfsgm_batch_sgm_warps(self.b, self.n)
+        return kw, lc, lfsgm_batch_sgm_warps(self.b, self.n), lfsgm_batch_sgm_split(self.b, self.n)
 
     @property
     def kernel_nodes(self):

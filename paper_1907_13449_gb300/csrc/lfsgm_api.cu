@@ -1604,6 +1604,12 @@ lfsgm_status lfsgm_batch_sgm_warps(lfsgm_batch b, int32_t *warps_per_cta) {
     return LFSGM_OK;
 }
 
+lfsgm_status lfsgm_batch_sgm_split(lfsgm_batch b, int32_t *min_wide) {
+    if (!b || !min_wide) return LFSGM_ERR_INVALID_ARG;
+    for (int i = 0; i < b->n; i++) min_wide[i] = b->h[i]->sgm_split;
+    return LFSGM_OK;
+}
+
 lfsgm_status lfsgm_batch_times(lfsgm_batch b, double *start_ms, double *end_ms, int32_t *branches) {
     if (!b) return LFSGM_ERR_INVALID_ARG;
     cudaError_t e = cudaStreamSynchronize(b->main);

@@ -74,13 +74,14 @@ def test_batch_autotuned_times_are_consistent(gpu_lib, mix):
     disp = [d.cpu().numpy() for d in b.run()]
     torch.cuda.synchronize()
     start, end, k = b.times()
-    kw, lc, sw = b.knobs()
+    kw, lc, sw, sp = b.knobs()
     b.close()
     assert k in (1, 2, 4, 8)
     _check_vs_oracle(disp, mix)
     assert np.all(start >= 0.0) and np.all(end > start)
-    # the autotuner picked a row span, list CTAs and SGM warps per shape class
+    # the autotuner picked a row span, list CTAs, SGM warps and split threshold per shape class
     assert set(kw.tolist()) <= {36, 44} and set(lc.tolist()) <= {0, 8, 12, 24} and set(sw.tolist()) <= {2, 4, 8}
+    assert set(sp.tolist()) <= {0, 24}
 
 
 def test_batch_matches_single_light_field_launches(gpu_lib, mix):
